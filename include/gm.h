@@ -1,0 +1,142 @@
+/*
+ * gm.h -- C ABI of the GB300 builder/applier of discrete Dirichlet-to-Neumann maps.
+ *
+ * Problem (Section 1.1, eq. basic; stencil of Section 6):
+ *     -Lap u + b u_x + c u_y + d u = 0 on the unit square,  u = g on its boundary,
+ * discretised on an n x n grid of UNKNOWN nodes with h = 1/(n+1): node (i, j) sits at
+ * ((i+1)h, (j+1)h) and has flat index i + n*j.  The equation at node k is
+ *     (1/h^2)[4u_k - u_n - u_s - u_w - u_e] + (1/h) b_k [u_e - u_w]
+ *                                          + (1/h) c_k [u_n - u_s] + d_k u_k = 0.
+ * The Dirichlet data g lives on the 4n non-corner "ghost" nodes one step outside the
+ * grid, ordered counter-clockwise from the south-west corner: south (x increasing),
+ * east (y increasing), north (x decreasing), west (y decreasing), n per side.
+ * The Neumann datum returned at ghost k is the outward one-sided flux
+ *     (g_k - u_{k'})/h,  k' = the only unknown next to ghost k,
+ * so the built operator is the dense 4n x 4n matrix T with  dudn = T g.
+ *
+ * Build (Sections 2-3): quad-tree of boxes whose edges are at most `leaf` (Section 2),
+ * leaf Schur complements S = A_bb - A_bi A_ii^{-1} A_ib (Section 3.1, eq. def_schur_nd),
+ * level-by-level pairwise merges (Section 3.2, eq. S_fromtwo_nd; four-child merge as
+ * three pairwise merges, Section 3.3), and the root (Section 3.3 step 4):
+ *     T = (I - P S_root^{-1} B)/h,
+ * with B the ring nodes' weights on the ghosts (negated) and P the ghost-to-ring map.
+ * Solve (Section 1.1): dudn = T g for a batch of Dirichlet vectors.
+ *
+ * Conventions for every entry point:
+ *   - Arrays are FP64.  A pointer may be host memory or device memory of the current
+ *     device; the library detects which (cudaPointerGetAttributes) and copies host
+ *     data through the call's stream.
+ *   - Matrices and vector batches are column-major: vector v of a batch of 4n-vectors
+ *     starts at element v*4n.
+ *   - Inputs are borrowed for the duration of the call only; outputs are caller-owned.
+ *   - Return value: GM_OK (0) or a negative GM_E* code; gm_strerror() names it.
+ *   - Handles are not thread-safe: one thread at a time per handle.
+ *   - `stream` arguments are a cudaStream_t passed as void* (NULL = legacy default).
+ */
+#ifndef GM_H
+#define GM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GM_OK 0
+#define GM_EINVAL (-1)       /* bad argument: sizes, NULL pointers, leaf < 4, ...      */
+#define GM_ENOMEM (-2)       /* a device or pinned-host allocation failed               */
+#define GM_ESINGULAR (-3)    /* an exactly zero / non-finite pivot: the Dirichlet
+                                problem of some box (or of the whole grid) is singular;
+                                gm_info().bad_stage names where                          */
+#define GM_ETIMEOUT (-4)     /* a bounded device-side wait gave up                       */
+#define GM_ECUDA (-5)        /* a CUDA runtime call failed                               */
+#define GM_EUNSUPPORTED (-6) /* valid request this build does not support               */
+
+#define GM_PREC_FP64 0  /* every step in FP64 */
+#define GM_PREC_MIXED 1 /* FP64 pivoting/panels, split-product tensor-core GEMM updates */
+
+typedef struct gm_handle gm_handle;
+
+typedef struct gm_opts {
+    int precision;    /* GM_PREC_FP64 (default) or GM_PREC_MIXED                        */
+    int keep_levels;  /* nonzero: keep every intermediate Schur complement for
+                         gm_get_schur() (costs the memory of all levels)                 */
+    void *stream;     /* cudaStream_t for the build (NULL = legacy default stream)      */
+    int panel_width;  /* pivot panel width of the dense eliminations (0 = default 8)    */
+    int timing;       /* nonzero: time every kernel launch of the build with CUDA events
+                         (per kernel family, reported by gm_info)                       */
+    int reserved[7];
+} gm_opts;
+
+/* Kernel families reported by gm_info when gm_opts.timing is set. */
+#define GM_K_LEAF 0        /* leaf elimination                                          */
+#define GM_K_ASSEMBLE 1    /* gather [M | Z] of the merges, [S | B] of the root          */
+#define GM_K_PANEL 2       /* pivot search and panel factorisation                      */
+#define GM_K_PIVROWS 3     /* row interchanges + triangular solves of the pivot rows    */
+#define GM_K_GJUPDATE 4    /* rank-nb update of all non-pivot rows                      */
+#define GM_K_MERGEUPDATE 5 /* Schur update S_parent = C - Y X with ring scatter          */
+#define GM_K_ROOT 6        /* T = (I - P X)/h                                            */
+#define GM_K_NFAM 7
+
+typedef struct gm_info_t {
+    int n, leaf, levels;          /* grid size, leaf edge, number of tree levels L       */
+    int precision;                /* precision mode the handle was built with            */
+    long long dtn_bytes;          /* device bytes of the DtN matrix                      */
+    long long peak_workspace;     /* largest device workspace the build held             */
+    double min_pivot_ratio;       /* min |pivot| / (4/h^2) over all eliminations         */
+    int bad_stage;                /* stage index of a GM_ESINGULAR failure, else -1      */
+    int launches;                 /* kernels launched by the build                       */
+    double kernel_ms[GM_K_NFAM];      /* device time per kernel family (timing builds)   */
+    double kernel_flops[GM_K_NFAM];   /* algorithmic flops per family (always counted)   */
+    int kernel_launches[GM_K_NFAM];   /* launches per family                             */
+} gm_info_t;
+
+/* Fill *opts with defaults (FP64, no kept levels, default stream). */
+void gm_opts_default(gm_opts *opts);
+
+/*
+ * Build the DtN operator of the problem above (Sections 2-3).
+ *   b, c, d : n*n coefficient values at the unknown nodes, flat index i + n*j.
+ *   n       : grid of unknowns, n >= 2.
+ *   leaf    : largest leaf-box edge (Section 2's N_leaf, as an edge): the tree has the
+ *             smallest L with ceil(n / 2^L) <= leaf.  4 <= leaf <= 17 (the leaf kernel
+ *             keeps a leaf's band and inner-ring solves in shared memory).
+ *   tol     : 0 selects the all-dense build (the only form this library provides;
+ *             any other value returns GM_EUNSUPPORTED).
+ *   out     : receives a new handle that owns all device memory of the operator.
+ * Blocks the calling thread until the build has finished on the device.
+ */
+int gm_build(const double *b, const double *c, const double *d, int n, int leaf, double tol,
+             gm_handle **out);
+int gm_build_ex(const gm_opts *opts, const double *b, const double *c, const double *d, int n,
+                int leaf, double tol, gm_handle **out);
+
+/*
+ * Solve stage (Section 1.1): dudn[:, v] = T g[:, v] for v < batch.
+ *   g, dudn : 4n x batch, column-major, host or device.  They must not overlap.
+ * With device pointers the call is asynchronous on `stream`; with a host pointer it
+ * returns after the result has reached the host.
+ */
+int gm_solve(gm_handle *h, const double *g, double *dudn, int batch, void *stream);
+
+/* Copy the dense 4n x 4n DtN matrix (column-major) to T_out (host or device). */
+int gm_get_dtn(gm_handle *h, double *T_out);
+
+/*
+ * Copy the Schur complement of the box [x0, x0+a) x [y0, y0+b) -- a leaf, a half-box
+ * rectangle of a four-child merge, or a box of any level -- to S_out, an r x r
+ * column-major matrix over the box's ring, r = 2a + 2b - 4, ring ordered
+ * counter-clockwise from the box's south-west corner.  Needs keep_levels at build time
+ * (else GM_EUNSUPPORTED); GM_EINVAL if no such box exists in the tree.
+ */
+int gm_get_schur(gm_handle *h, int x0, int y0, int a, int b, double *S_out);
+
+int gm_info(gm_handle *h, gm_info_t *info);
+
+/* Release the handle and its device memory.  NULL is a no-op. */
+void gm_free(gm_handle *h);
+
+const char *gm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GM_H */

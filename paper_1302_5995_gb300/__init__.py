@@ -1,0 +1,219 @@
+"""GB300 builder and applier of the discrete Dirichlet-to-Neumann map of
+-Lap u + b u_x + c u_y + d u = 0 on the unit square (Gillman & Martinsson's nested
+dissection build, arXiv 1302.5995).
+
+This module is argument marshalling over the C ABI declared in include/gm.h: every
+step of the build and of the solve runs in the CUDA kernels of libgm.so.  Importing it
+fails loudly when that library has not been built; there is no CPU fallback.
+
+    import paper_1302_5995_gb300 as gm
+    op = gm.build(b, c, d, n=512, leaf=16)          # torch CUDA tensors or numpy arrays
+    v = op.solve(g)                                 # g: 4n x B, column j = vector j
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgm.so")
+
+GM_OK, GM_EINVAL, GM_ENOMEM, GM_ESINGULAR, GM_ETIMEOUT, GM_ECUDA, GM_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+PREC_FP64, PREC_MIXED = 0, 1
+
+
+class GmError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("keep_levels", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("panel_width", ctypes.c_int), ("timing", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+K_FAMILIES = ["leaf", "assemble", "panel", "pivrows", "gj_update", "merge_update", "root"]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("leaf", ctypes.c_int), ("levels", ctypes.c_int),
+                ("precision", ctypes.c_int), ("dtn_bytes", ctypes.c_longlong),
+                ("peak_workspace", ctypes.c_longlong), ("min_pivot_ratio", ctypes.c_double),
+                ("bad_stage", ctypes.c_int), ("launches", ctypes.c_int),
+                ("kernel_ms", ctypes.c_double * 7), ("kernel_flops", ctypes.c_double * 7),
+                ("kernel_launches", ctypes.c_int * 7)]
+
+
+#: exported symbols and their (restype, argtypes)
+SIGNATURES = {
+    "gm_opts_default": (None, [ctypes.POINTER(Opts)]),
+    "gm_build": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                      ctypes.POINTER(ctypes.c_void_p)]),
+    "gm_build_ex": (ctypes.c_int, [ctypes.POINTER(Opts)] + [ctypes.c_void_p] * 3
+                    + [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]),
+    "gm_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "gm_get_dtn": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gm_get_schur": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 4 + [ctypes.c_void_p]),
+    "gm_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Info)]),
+    "gm_free": (None, [ctypes.c_void_p]),
+    "gm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libgm.so and declare its signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build the CUDA extension first "
+                          "(python -m paper_1302_5995_gb300.build_ext)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load_library().gm_strerror(code).decode()
+
+
+def _ptr(x):
+    """Raw address of a torch tensor or numpy array (contiguous, float64)."""
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _check_f64(x, what, numel=None):
+    import numpy as np
+    if hasattr(x, "data_ptr"):
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError(f"{what}: need a contiguous float64 tensor")
+        if numel is not None and x.numel() != numel:
+            raise ValueError(f"{what}: expected {numel} elements, got {x.numel()}")
+        return x
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if numel is not None and x.size != numel:
+        raise ValueError(f"{what}: expected {numel} elements, got {x.size}")
+    return x
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class DtN:
+    """A built Dirichlet-to-Neumann operator (owns its device memory)."""
+
+    def __init__(self, handle, n, leaf):
+        self._h = handle
+        self.n = n
+        self.leaf = leaf
+        self._keep = []
+
+    def __del__(self):
+        try:
+            if self._h:
+                load_library().gm_free(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+    def free(self):
+        self.__del__()
+
+    def solve(self, g, out=None, stream=None):
+        """dudn = T g for g of shape (4n, B) stored column by column (vector j contiguous).
+
+        g/out may be torch CUDA tensors (asynchronous on `stream`) or host arrays."""
+        lib = load_library()
+        N = 4 * self.n
+        g = _check_f64(g, "g")
+        B = (g.numel() if hasattr(g, "numel") else g.size) // N
+        if out is None:
+            if hasattr(g, "data_ptr"):
+                import torch
+                out = torch.empty_like(g)
+            else:
+                import numpy as np
+                out = np.empty_like(g)
+        rc = lib.gm_solve(self._h, _ptr(g), _ptr(out), B, _stream_handle(stream))
+        if rc:
+            raise GmError(rc, "gm_solve")
+        return out
+
+    def dtn(self, out=None):
+        """The dense 4n x 4n DtN matrix T.  With `out` (a 4n*4n float64 buffer, host or
+        device) the column-major matrix is written there and `out` is returned."""
+        import numpy as np
+        N = 4 * self.n
+        if out is not None:
+            rc = load_library().gm_get_dtn(self._h, _ptr(out))
+            if rc:
+                raise GmError(rc, "gm_get_dtn")
+            return out
+        buf = np.empty((N, N))
+        rc = load_library().gm_get_dtn(self._h, _ptr(buf))
+        if rc:
+            raise GmError(rc, "gm_get_dtn")
+        return buf.T.copy()
+
+    def schur(self, x0, y0, a, b):
+        """Schur complement of a kept box over its counter-clockwise ring (row-major view
+        of the column-major matrix is its transpose; returned as the matrix itself)."""
+        import numpy as np
+        r = 2 * a + 2 * b - 4
+        out = np.empty((r, r))
+        rc = load_library().gm_get_schur(self._h, x0, y0, a, b, _ptr(out))
+        if rc:
+            raise GmError(rc, "gm_get_schur")
+        return out.T.copy()
+
+    def info(self):
+        inf = Info()
+        rc = load_library().gm_info(self._h, ctypes.byref(inf))
+        if rc:
+            raise GmError(rc, "gm_info")
+        out = {f: getattr(inf, f) for f, _ in Info._fields_}
+        for f in ("kernel_ms", "kernel_flops", "kernel_launches"):
+            out[f] = dict(zip(K_FAMILIES, list(out[f])))
+        return out
+
+
+def build(b, c, d, n, leaf, tol=0.0, precision=PREC_FP64, keep_levels=False, stream=None, panel_width=0,
+          timing=False):
+    """Build the DtN operator for coefficient fields b, c, d (n*n each, index i + n*j)."""
+    lib = load_library()
+    b = _check_f64(b, "b", n * n)
+    c = _check_f64(c, "c", n * n)
+    d = _check_f64(d, "d", n * n)
+    o = Opts()
+    lib.gm_opts_default(ctypes.byref(o))
+    o.precision = precision
+    o.keep_levels = 1 if keep_levels else 0
+    o.stream = _stream_handle(stream)
+    if panel_width:
+        o.panel_width = panel_width
+    o.timing = 1 if timing else 0
+    h = ctypes.c_void_p()
+    rc = lib.gm_build_ex(ctypes.byref(o), _ptr(b), _ptr(c), _ptr(d), n, leaf, float(tol), ctypes.byref(h))
+    if rc:
+        raise GmError(rc, "gm_build")
+    return DtN(h, n, leaf)

@@ -1,0 +1,92 @@
+// Internal structures shared by the host plan builder and the CUDA kernels.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "../../include/gm.h"
+
+namespace gm {
+
+// A rectangle of unknowns [x0, x0+a) x [y0, y0+b).
+struct Box {
+    int x0, y0, a, b;
+};
+
+inline int ring_size(int a, int b) { return 2 * a + 2 * b - 4; }
+
+// Position of local node (i, j) on the ring of an a x b box (counter-clockwise from the
+// south-west corner), or -1 for an interior node.
+inline int ring_pos(int a, int b, int i, int j) {
+    if (j == 0) return i;
+    if (i == a - 1) return a - 1 + j;
+    if (j == b - 1) return (a - 1) + (b - 1) + (a - 1 - i);
+    if (i == 0) return 2 * (a - 1) + (b - 1) + (b - 1 - j);
+    return -1;
+}
+
+// Direction codes of the five-point stencil weights.
+enum { DIR_C = 0, DIR_E = 1, DIR_W = 2, DIR_N = 3, DIR_S = 4 };
+
+// One leaf elimination.
+struct LeafDesc {
+    int x0, y0, a, b;
+    int64_t off;  // S offset (doubles) in the output arena, column-major r x r
+};
+
+// One pairwise merge (eq. S_fromtwo_nd).  Child 1 is west/south, child 2 east/north.
+struct MergeDesc {
+    int64_t s1, s2;  // child Schur complements (input arena offsets)
+    int64_t out;     // parent Schur complement (output arena offset)
+    int64_t ws;      // dense system [M | Z] (workspace offset), column-major, ld = 2*sp
+    int r1, r2, rp;  // ring sizes
+    int sp;          // |P3| = |P4| (interface nodes of each child)
+    int n1, n2;      // |P1|, |P2|; n1 + n2 = rp
+    int orient;      // 0: child 2 east of child 1; 1: child 2 north of child 1
+    int tab;         // offset of this merge's index table (ints)
+    // table layout at tab:
+    //   p3[sp]  p4[sp]  g3[sp]  g4[sp]         ring positions / global flat indices
+    //   p1[n1]  q1[n1]  p2[n2]  q2[n2]         child ring positions / parent ring positions
+    //   x12[8]: (a1, c1, g1, g2) x 2           P1-index, P2-index, global indices of the
+    //                                           two corner couplings across the shared edge
+};
+
+// One dense system handled by the Gauss-Jordan sweep: [M | Z], m x ncol, column-major.
+struct SysDesc {
+    int64_t off;  // workspace offset (doubles)
+    int m;        // order of M (columns eliminated)
+    int ncol;     // m + number of right-hand-side columns
+    int id;       // stage-local id for error reports
+    int pad;
+};
+
+// Device status written by kernels.
+struct Status {
+    int code;                    // 0 or GM_ESINGULAR
+    int where;                   // stage index of the first failure
+    unsigned long long min_piv;  // bit pattern of min |pivot| (positive double)
+};
+
+// One merge stage (all horizontal merges of a level, or all vertical ones).
+struct Stage {
+    int orient;
+    std::vector<MergeDesc> merges;
+    std::vector<int> table;
+    std::vector<Box> in_boxes, out_boxes;  // per merge: child1, child2 / parent
+    int64_t in_doubles, out_doubles, ws_doubles;
+    int max_m, max_ncol, max_rp;
+};
+
+struct Plan {
+    int n, leaf, L;
+    std::vector<LeafDesc> leaves;
+    std::vector<Box> leaf_boxes;
+    int64_t leaf_doubles;
+    std::vector<Stage> stages;  // 2 per level, finest first: H(L), V(L), H(L-1), ...
+    Box root;
+    int r_root;
+};
+
+int build_plan(int n, int leaf, Plan &plan);
+int validate_plan(const Plan &plan);
+
+}  // namespace gm
