@@ -1,0 +1,303 @@
+"""Benchmark: build the DtN operator and solve a batch of Dirichlet vectors.
+
+Workload (one step): the 512 x 512 convection-diffusion-reaction problem (b, c, d smooth
+random Fourier fields, seeds 1-3), leaf boxes 16 x 16, then the solve of 256 Gaussian
+boundary vectors (seed 4).  Metric: build gridpoints/s (n^2 / step time), with solve
+vectors/s, error against the FP64 oracle and p50/p99 step latency alongside.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gm|reference]
+                    [--precision fp64|mixed]
+
+N > 1 runs under torchrun as independent replicas (one problem per GPU, no collective).
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "build gridpoints/s and DtN solve vectors/s (p50/p99 latency) at stated rel. err vs FP64"
+UNIT = "gridpoints/s"
+N_GRID, LEAF, NVEC = 512, 16, 256
+WORKLOAD = ("convection-diffusion-reaction, b,c,d = 8-mode Fourier fields (seeds 1-3), 512x512 grid "
+            "(N=262144), leaf 16x16, build + solve of 256 Gaussian boundary vectors (seed 4)")
+# FP64 peak from unit counts and clock: 152 SMs x 4 FP64 flop/clk/SM (2 DFMA) x 2070 MHz
+SMS, FP64_FLOP_PER_CLK_SM, SM_MAX_MHZ = 152, 4, 2070.0
+FP64_PEAK_TFLOPS = SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+# DRAM traffic of the dominant kernel from an ncu capture (profiles/), per launch, with the
+# source digest it was taken at; reported as null once the kernel source changes.
+TRAFFIC = {}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def source_digest():
+    import hashlib
+    h = hashlib.sha1()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1302_5995_gb300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_1302_5995_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = str(gpu_index)
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", self.gpu], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+                power.append(float(p[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        loaded = [x for x in sm if smax and x > 0.3 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def make_inputs():
+    import numpy as np
+    from paper_1302_5995_gb300 import inputs
+    cfg = inputs.config2(N_GRID, NVEC)
+    Gv = np.ascontiguousarray(cfg["G"].T)  # 256 vectors, each contiguous
+    return cfg, Gv
+
+
+def cpu_oracle_step(cfg):
+    """One step of the oracle: the paper's dense nested dissection in FP64 + the solve."""
+    from oracle import nd_dense
+    t0 = time.perf_counter()
+    T = nd_dense.build(cfg["b"], cfg["c"], cfg["d"], N_GRID, LEAF).T
+    V = nd_dense.solve(T, cfg["G"])
+    return time.perf_counter() - t0, T, V
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cfg, _ = make_inputs()
+    cores = os.cpu_count()
+    for _ in range(args.warmup):
+        cpu_oracle_step(cfg)
+    ts = [cpu_oracle_step(cfg)[0] for _ in range(args.steps)]
+    t = statistics.mean(ts)
+    value = N_GRID * N_GRID / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_GRID, "leaf": LEAF, "nvec": NVEC, "precision": "fp64"},
+        "solve_vectors_per_s": None,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "full workload per step: numpy/LAPACK dense nested dissection "
+                                   "(oracle O2) + T @ G, default BLAS threading on all host cores"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gm(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1302_5995_gb300 import build_ext
+    build_ext.build()
+    import paper_1302_5995_gb300 as gm
+
+    prec = gm.PREC_MIXED if args.precision == "mixed" else gm.PREC_FP64
+    cfg, Gv = make_inputs()
+    n = N_GRID
+    dev = torch.device("cuda", local)
+    b, c, d = (torch.from_numpy(cfg[k]).to(dev) for k in "bcd")
+    G = torch.from_numpy(Gv).to(dev)
+    V = torch.empty_like(G)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    def step(timing):
+        op = gm.build(b, c, d, n, LEAF, precision=prec, stream=stream, timing=timing)
+        op.solve(G, out=V, stream=stream)
+        return op
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(False).free()
+    barrier()
+    # timed region: every step instrumented with per-launch CUDA events (pooled)
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] \
+        if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local)
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    step_ms, build_ms, solve_ms, fam_ms, fam_fl, fam_n, launches = [], [], [], {}, {}, {}, 0
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        barrier()
+        ev[0].record(stream)
+        op = gm.build(b, c, d, n, LEAF, precision=prec, stream=stream, timing=True)
+        ev[1].record(stream)
+        op.solve(G, out=V, stream=stream)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(ev[0].elapsed_time(ev[2]))
+        build_ms.append(ev[0].elapsed_time(ev[1]))
+        solve_ms.append(ev[1].elapsed_time(ev[2]))
+        inf = op.info()
+        launches += inf["launches"] + 1
+        for f in gm.K_FAMILIES:
+            fam_ms[f] = fam_ms.get(f, 0.0) + inf["kernel_ms"][f]
+            fam_fl[f] = fam_fl.get(f, 0.0) + inf["kernel_flops"][f]
+            fam_n[f] = fam_n.get(f, 0) + inf["kernel_launches"][f]
+        op.free()
+    barrier()
+    clk = clocks.stop()
+    t_step = statistics.mean(step_ms)
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+    # accuracy of this run's result against the FP64 oracle (rank 0 only, after timing)
+    result = {}
+    if rank == 0:
+        result["V"] = V.cpu().numpy()
+    # end-to-end through the C ABI with pinned host buffers (copies inside the timing)
+    hb = [torch.from_numpy(cfg[k]).pin_memory() for k in "bcd"]
+    hG = torch.from_numpy(Gv).pin_memory()
+    hV = torch.empty_like(hG).pin_memory()
+    h2d = 3 * n * n * 8 + Gv.size * 8
+    d2h = Gv.size * 8
+    e2e_t = []
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        op = gm.build(hb[0].numpy(), hb[1].numpy(), hb[2].numpy(), n, LEAF, precision=prec, stream=stream)
+        op.solve(hG.numpy(), out=hV.numpy(), stream=stream)
+        t1 = time.perf_counter()
+        op.free()
+        if it >= args.warmup:
+            e2e_t.append(t1 - t0)
+    e2e_step = statistics.mean(e2e_t)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return
+    # error vs the FP64 oracle, and the oracle's own time as the CPU baseline
+    t_cpu, To, Vo = cpu_oracle_step(cfg)
+    Vg = result["V"].reshape(NVEC, 4 * n).T
+    rel_err = float((np.linalg.norm(Vg - Vo, axis=0) / np.linalg.norm(Vo, axis=0)).max())
+    dom = max(fam_ms, key=lambda f: fam_ms[f])
+    achieved = fam_fl[dom] / (fam_ms[dom] * 1e-3) / 1e12
+    peak = FP64_PEAK_TFLOPS
+    tr = TRAFFIC.get(dom)
+    traffic = tr[0] if (tr and tr[1] == source_digest()) else None
+    sorted_ms = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": world * n * n / (t_step * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "leaf": LEAF, "nvec": NVEC, "precision": args.precision,
+                   "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "build_ms": statistics.mean(build_ms), "solve_ms": statistics.mean(solve_ms),
+        "build_gridpoints_per_s": n * n / (statistics.mean(build_ms) * 1e-3) * world,
+        "solve_vectors_per_s": NVEC / (statistics.mean(solve_ms) * 1e-3) * world,
+        "latency_ms": {"p50": sorted_ms[len(sorted_ms) // 2],
+                       "p99": sorted_ms[min(len(sorted_ms) - 1, int(0.99 * len(sorted_ms)))]},
+        "rel_err_vs_fp64_oracle": rel_err,
+        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": "FP64 from unit counts: 152 SMs x 4 flop/clk x 2070 MHz",
+                     "launches_per_step": fam_n[dom] // args.steps,
+                     "ms_per_step": fam_ms[dom] / args.steps},
+        "kernel_ms_per_step": {f: fam_ms[f] / args.steps for f in fam_ms},
+        "cpu_baseline": {"value": n * n / t_cpu, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "one full step: numpy/LAPACK dense nested dissection (oracle O2) + T @ G "
+                                   "of the 256 vectors, default BLAS threading"},
+        "e2e": {"value": world * n * n / e2e_step, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step * 1e3},
+        "clocks": clk,
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gm", "reference"], default="gm")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -156,6 +156,29 @@ int get_plan(int n, int leaf, std::shared_ptr<DevPlan> &out) {
 
 }  // namespace
 
+namespace gm {
+static std::mutex g_ev_mu;
+static std::vector<cudaEvent_t> g_ev_pool;
+cudaEvent_t event_pool_get() {
+    {
+        std::lock_guard<std::mutex> lk(g_ev_mu);
+        if (!g_ev_pool.empty()) {
+            cudaEvent_t e = g_ev_pool.back();
+            g_ev_pool.pop_back();
+            return e;
+        }
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+void event_pool_put(cudaEvent_t e) {
+    if (!e) return;
+    std::lock_guard<std::mutex> lk(g_ev_mu);
+    g_ev_pool.push_back(e);
+}
+}  // namespace gm
+
 struct gm_handle {
     int n = 0, leaf = 0, L = 0, precision = 0;
     double *T = nullptr;  // 4n x 4n column-major

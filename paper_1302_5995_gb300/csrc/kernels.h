@@ -12,8 +12,12 @@
 
 namespace gm {
 
+// Process-wide pool of timing events (created once, reused by every timed build).
+cudaEvent_t event_pool_get();
+void event_pool_put(cudaEvent_t e);
+
 // Per-family launch accounting: algorithmic flops are always counted; with `on`, every
-// launch is bracketed by a pair of CUDA events on its stream.
+// launch is bracketed by a pair of pooled CUDA events on its stream.
 struct KTimer {
     bool on = false;
     double flops[GM_K_NFAM] = {};
@@ -28,17 +32,15 @@ struct KTimer {
     KTimer &operator=(const KTimer &) = delete;
     ~KTimer() {
         for (auto &r : recs) {
-            cudaEventDestroy(r.a);
-            cudaEventDestroy(r.b);
+            event_pool_put(r.a);
+            event_pool_put(r.b);
         }
     }
     void begin(int fam, double fl, cudaStream_t s) {
         flops[fam] += fl;
         launches[fam] += 1;
         if (!on) return;
-        Rec r{fam, nullptr, nullptr};
-        cudaEventCreate(&r.a);
-        cudaEventCreate(&r.b);
+        Rec r{fam, event_pool_get(), event_pool_get()};
         cudaEventRecord(r.a, s);
         recs.push_back(r);
     }
@@ -50,8 +52,8 @@ struct KTimer {
         for (auto &r : recs) {
             float t = 0.f;
             if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.fam] += t;
-            cudaEventDestroy(r.a);
-            cudaEventDestroy(r.b);
+            event_pool_put(r.a);
+            event_pool_put(r.b);
         }
         recs.clear();
         cudaGetLastError();
