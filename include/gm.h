@@ -49,6 +49,7 @@ extern "C" {
 #define GM_ETIMEOUT (-4)     /* a bounded device-side wait gave up                       */
 #define GM_ECUDA (-5)        /* a CUDA runtime call failed                               */
 #define GM_EUNSUPPORTED (-6) /* valid request this build does not support               */
+#define GM_ESCRATCH (-7)     /* request larger than the fixed scratch of gm_solve_static */
 
 #define GM_PREC_FP64 0  /* every step in FP64 */
 #define GM_PREC_MIXED 1 /* FP64 pivoting/panels, split-product tensor-core GEMM updates */
@@ -128,6 +129,25 @@ int gm_get_dtn(gm_handle *h, double *T_out);
  * (else GM_EUNSUPPORTED); GM_EINVAL if no such box exists in the tree.
  */
 int gm_get_schur(gm_handle *h, int x0, int y0, int a, int b, double *S_out);
+
+/*
+ * gm_solve_static -- gm_solve without any device allocation.  The paper has no
+ * counterpart; it exists for callers that cannot let a library allocate device memory:
+ * a serving loop that must not touch the allocator once it runs, or a host application
+ * whose device memory belongs to another runtime's pool.
+ *   Same arguments and result as gm_solve.  Host g / dudn are staged through one fixed
+ *   16 MiB array of device memory inside the library (2^21 doubles; every GPU that loads
+ *   the library holds it until the process exits) instead of freshly allocated buffers;
+ *   device g / dudn are used in place.
+ *   Limit: (4n * batch) doubles for each host-side argument, 2^21 doubles in total, else
+ *   GM_ESCRATCH and nothing is done.
+ *   The first call on a device looks up the array's device address (once per device);
+ *   make that first call before any stream capture.
+ *   All calls share the array and it keeps the last call's contents: calls that overlap
+ *   on the GPU (other streams, other threads) race on it and must be serialised by the
+ *   caller.
+ */
+int gm_solve_static(gm_handle *h, const double *g, double *dudn, int batch, void *stream);
 
 int gm_info(gm_handle *h, gm_info_t *info);
 

@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgm.so")
 
 GM_OK, GM_EINVAL, GM_ENOMEM, GM_ESINGULAR, GM_ETIMEOUT, GM_ECUDA, GM_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+GM_ESCRATCH = -7
 PREC_FP64, PREC_MIXED = 0, 1
 
 
@@ -54,6 +55,8 @@ SIGNATURES = {
     "gm_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "gm_get_dtn": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gm_get_schur": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 4 + [ctypes.c_void_p]),
+    "gm_solve_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_void_p]),
     "gm_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Info)]),
     "gm_free": (None, [ctypes.c_void_p]),
     "gm_strerror": (ctypes.c_char_p, [ctypes.c_int]),

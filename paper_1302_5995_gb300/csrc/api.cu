@@ -189,6 +189,12 @@ struct gm_handle {
     gm_info_t info{};
 };
 
+const double *gm::handle_dtn(gm_handle *h, int *n) {
+    if (!h) return nullptr;
+    *n = h->n;
+    return h->T;
+}
+
 extern "C" {
 
 void gm_opts_default(gm_opts *o) {
@@ -207,6 +213,7 @@ const char *gm_strerror(int code) {
     case GM_ETIMEOUT: return "device wait timed out";
     case GM_ECUDA: return "CUDA runtime error";
     case GM_EUNSUPPORTED: return "unsupported request";
+    case GM_ESCRATCH: return "request exceeds the fixed 16 MiB scratch of gm_solve_static";
     default: return "unknown error";
     }
 }

@@ -87,6 +87,9 @@ struct Plan {
 };
 
 int build_plan(int n, int leaf, Plan &plan);
+
+// The dense DtN matrix of a handle and its grid size (nullptr for a NULL handle).
+const double *handle_dtn(gm_handle *h, int *n);
 int validate_plan(const Plan &plan);
 
 }  // namespace gm
