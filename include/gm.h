@@ -52,7 +52,9 @@ extern "C" {
 #define GM_ESCRATCH (-7)     /* request larger than the fixed scratch of gm_solve_static */
 
 #define GM_PREC_FP64 0  /* every step in FP64 */
-#define GM_PREC_MIXED 1 /* FP64 pivoting/panels, split-product tensor-core GEMM updates */
+#define GM_PREC_MIXED 1 /* double-float (FP32 pair) storage, FP32 pivot search, FP64 pivot
+                           blocks, and every dense update as exact split products of
+                           bf16 integer digits on the tensor cores                       */
 
 typedef struct gm_handle gm_handle;
 
@@ -64,8 +66,24 @@ typedef struct gm_opts {
     int panel_width;  /* pivot panel width of the dense eliminations (0 = default 8)    */
     int timing;       /* nonzero: time every kernel launch of the build with CUDA events
                          (per kernel family, reported by gm_info)                       */
-    int reserved[7];
+    int split_digits; /* GM_PREC_MIXED: 7-bit digits per operand of the split products,
+                         3..6 (0 = default 5); more digits = more accuracy, more work   */
+    int pivoting;     /* GM_PREC_MIXED: GM_PIVOT_AUTO (default), GM_PIVOT_BLOCK or
+                         GM_PIVOT_PARTIAL (see below); GM_PREC_FP64 always uses partial  */
+    int reserved[5];
 } gm_opts;
+
+/* Pivoting of the mixed-precision dense eliminations.
+ *   GM_PIVOT_PARTIAL: partial pivoting over all remaining rows, 16-column panels.
+ *   GM_PIVOT_BLOCK:   64-column blocks; pivots are chosen among the rows of the block
+ *                     (its 64 x 64 pivot block is inverted with partial pivoting).
+ *   GM_PIVOT_AUTO:    block pivoting; if a row below some block held an entry more than
+ *                     16x that block column's pivot (where partial pivoting would have
+ *                     chosen differently), the whole build is redone with partial
+ *                     pivoting.  gm_info().pivot_fallback reports it. */
+#define GM_PIVOT_AUTO 0
+#define GM_PIVOT_BLOCK 1
+#define GM_PIVOT_PARTIAL 2
 
 /* Kernel families reported by gm_info when gm_opts.timing is set. */
 #define GM_K_LEAF 0        /* leaf elimination                                          */
@@ -88,6 +106,8 @@ typedef struct gm_info_t {
     double kernel_ms[GM_K_NFAM];      /* device time per kernel family (timing builds)   */
     double kernel_flops[GM_K_NFAM];   /* algorithmic flops per family (always counted)   */
     int kernel_launches[GM_K_NFAM];   /* launches per family                             */
+    int pivoting;                     /* pivoting actually used (GM_PIVOT_BLOCK/PARTIAL) */
+    int pivot_fallback;               /* 1 if GM_PIVOT_AUTO fell back to partial pivoting */
 } gm_info_t;
 
 /* Fill *opts with defaults (FP64, no kept levels, default stream). */

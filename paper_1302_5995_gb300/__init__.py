@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libgm.so")
 GM_OK, GM_EINVAL, GM_ENOMEM, GM_ESINGULAR, GM_ETIMEOUT, GM_ECUDA, GM_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 GM_ESCRATCH = -7
 PREC_FP64, PREC_MIXED = 0, 1
+PIVOT_AUTO, PIVOT_BLOCK, PIVOT_PARTIAL = 0, 1, 2
 
 
 class GmError(RuntimeError):
@@ -31,7 +32,8 @@ class GmError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("keep_levels", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("panel_width", ctypes.c_int), ("timing", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("panel_width", ctypes.c_int), ("timing", ctypes.c_int), ("split_digits", ctypes.c_int),
+                ("pivoting", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 K_FAMILIES = ["leaf", "assemble", "panel", "pivrows", "gj_update", "merge_update", "root"]
 
@@ -42,7 +44,8 @@ class Info(ctypes.Structure):
                 ("peak_workspace", ctypes.c_longlong), ("min_pivot_ratio", ctypes.c_double),
                 ("bad_stage", ctypes.c_int), ("launches", ctypes.c_int),
                 ("kernel_ms", ctypes.c_double * 7), ("kernel_flops", ctypes.c_double * 7),
-                ("kernel_launches", ctypes.c_int * 7)]
+                ("kernel_launches", ctypes.c_int * 7), ("pivoting", ctypes.c_int),
+                ("pivot_fallback", ctypes.c_int)]
 
 
 #: exported symbols and their (restype, argtypes)
@@ -201,7 +204,7 @@ class DtN:
 
 
 def build(b, c, d, n, leaf, tol=0.0, precision=PREC_FP64, keep_levels=False, stream=None, panel_width=0,
-          timing=False):
+          timing=False, split_digits=0, pivoting=PIVOT_AUTO):
     """Build the DtN operator for coefficient fields b, c, d (n*n each, index i + n*j)."""
     lib = load_library()
     b = _check_f64(b, "b", n * n)
@@ -215,6 +218,8 @@ def build(b, c, d, n, leaf, tol=0.0, precision=PREC_FP64, keep_levels=False, str
     if panel_width:
         o.panel_width = panel_width
     o.timing = 1 if timing else 0
+    o.split_digits = split_digits
+    o.pivoting = pivoting
     h = ctypes.c_void_p()
     rc = lib.gm_build_ex(ctypes.byref(o), _ptr(b), _ptr(c), _ptr(d), n, leaf, float(tol), ctypes.byref(h))
     if rc:

@@ -43,6 +43,9 @@ struct MergeDesc {
     int n1, n2;      // |P1|, |P2|; n1 + n2 = rp
     int orient;      // 0: child 2 east of child 1; 1: child 2 north of child 1
     int tab;         // offset of this merge's index table (ints)
+    int kpad;        // 2*sp rounded up to 16 (row length of this merge's digit planes)
+    int eoff;        // first row of this merge in the stage's exponent vectors (prefix of rp)
+    int64_t doff;    // first element of this merge in the stage's digit planes (rp x kpad)
     // table layout at tab:
     //   p3[sp]  p4[sp]  g3[sp]  g4[sp]         ring positions / global flat indices
     //   p1[n1]  q1[n1]  p2[n2]  q2[n2]         child ring positions / parent ring positions
@@ -56,6 +59,8 @@ struct SysDesc {
     int m;        // order of M (columns eliminated)
     int ncol;     // m + number of right-hand-side columns
     int id;       // stage-local id for error reports
+    int roff;     // first row of this system in per-stage row scratch (prefix sum of m)
+    int coff;     // first column of this system in per-stage column scratch (prefix of ncol)
     int pad;
 };
 
@@ -64,6 +69,8 @@ struct Status {
     int code;                    // 0 or GM_ESINGULAR
     int where;                   // stage index of the first failure
     unsigned long long min_piv;  // bit pattern of min |pivot| (positive double)
+    int growth;                  // block pivoting: a row outside a block would have pivoted
+    int pad;
 };
 
 // One merge stage (all horizontal merges of a level, or all vertical ones).
@@ -73,6 +80,8 @@ struct Stage {
     std::vector<int> table;
     std::vector<Box> in_boxes, out_boxes;  // per merge: child1, child2 / parent
     int64_t in_doubles, out_doubles, ws_doubles;
+    int64_t dig_elems;  // elements of one digit plane of the stage (sum of rp * kpad)
+    int64_t exp_elems;  // rows of the stage's exponent vectors (sum of rp)
     int max_m, max_ncol, max_rp;
 };
 

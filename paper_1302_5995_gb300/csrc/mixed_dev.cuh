@@ -1,0 +1,273 @@
+// Device helpers of the mixed-precision kernels: double-float (df32) arithmetic, the
+// signed 7-bit digit split, mma.sync digit products, and digit-plane GEMM tiles.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "gm_internal.h"
+
+namespace gm {
+
+// ----------------------------------------------------------------------------- df32
+
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return make_float2(s, e);
+}
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {  // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return make_float2(s, e);
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    float2 s = two_sum(a.x, b.x);
+    float2 t = two_sum(a.y, b.y);
+    s.y = __fadd_rn(s.y, t.x);
+    s = fast_two_sum(s.x, s.y);
+    s.y = __fadd_rn(s.y, t.y);
+    return fast_two_sum(s.x, s.y);
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 df_sub(float2 a, float2 b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ float2 df_add_f(float2 a, float b) {
+    float2 s = two_sum(a.x, b);
+    s.y = __fadd_rn(s.y, a.y);
+    return fast_two_sum(s.x, s.y);
+}
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    float p = __fmul_rn(a.x, b.x);
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ float2 df_div(float2 a, float2 b) {
+    float q = __fdiv_rn(a.x, b.x);
+    float2 r = df_sub(a, df_mul(make_float2(q, 0.f), b));
+    float q2 = __fdiv_rn(r.x, b.x);
+    return fast_two_sum(q, q2);
+}
+__device__ __forceinline__ float2 df_from_d(double x) {
+    float hi = __double2float_rn(x);
+    float lo = __double2float_rn(x - (double)hi);
+    return make_float2(hi, lo);
+}
+__device__ __forceinline__ double df_to_d(float2 a) { return (double)a.x + (double)a.y; }
+__device__ __forceinline__ float2 df_scale(float2 a, int p) { return make_float2(ldexpf(a.x, p), ldexpf(a.y, p)); }
+
+// ----------------------------------------------------------------------------- digits
+
+// Exponent e with |x| < 2^e for every x of a set whose largest |hi| is m (0 -> 0).
+__device__ __forceinline__ int exp_of_max(float m) {
+    int e = 0;
+    if (m > 0.f) frexpf(m, &e);
+    return e;
+}
+
+// S signed digits of x 2^(6-e): d_0 + 2^-7 d_1 + ..., |d_s| <= 64.
+template <int S>
+__device__ __forceinline__ void digits(float2 x, int e, float d[S]) {
+    float th = ldexpf(x.x, 6 - e), tl = ldexpf(x.y, 6 - e);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        float q = rintf(th);
+        d[s] = q;
+        float2 r = two_sum(__fsub_rn(th, q), tl);
+        th = __fmul_rn(r.x, 128.f);
+        tl = __fmul_rn(r.y, 128.f);
+    }
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Shared-memory digit tiles: A as [S][BM][KP] (k fastest), B as [S][BN][KP]; KP = 24
+// bf16 (16 used) makes the fragment loads bank-conflict free.
+constexpr int KP = 24;
+
+// One warp accumulates a 32 x 32 block: 2 m16 tiles x 4 n8 tiles, S levels.
+template <int S>
+__device__ __forceinline__ void warp_mma_levels(const __nv_bfloat16 *As, const __nv_bfloat16 *Bs, int BM, int BN,
+                                                int wm, int wn, float acc[S][2][4][4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        uint32_t a[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const __nv_bfloat16 *p = As + ((size_t)s * BM + wm + mt * 16 + g) * KP + 2 * t;
+            a[mt][0] = *(const uint32_t *)(p);
+            a[mt][1] = *(const uint32_t *)(p + 8 * KP);
+            a[mt][2] = *(const uint32_t *)(p + 8);
+            a[mt][3] = *(const uint32_t *)(p + 8 * KP + 8);
+        }
+#pragma unroll
+        for (int u = 0; u < S; ++u) {
+            if (s + u >= S) continue;
+            uint32_t b[4][2];
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const __nv_bfloat16 *p = Bs + ((size_t)u * BN + wn + nt * 8 + g) * KP + 2 * t;
+                b[nt][0] = *(const uint32_t *)(p);
+                b[nt][1] = *(const uint32_t *)(p + 8);
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+                    mma_bf16(acc[s + u][mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b[nt][0], b[nt][1]);
+        }
+    }
+}
+
+// df32 value of one output position from its S exact level sums and the scale.
+template <int S>
+__device__ __forceinline__ float2 combine_levels(const float acc[S][2][4][4], int mt, int nt, int c, int p) {
+    float2 v = make_float2(ldexpf(acc[S - 1][mt][nt][c], -7 * (S - 1)), 0.f);
+#pragma unroll
+    for (int g = S - 2; g >= 0; --g) v = df_add_f(v, ldexpf(acc[g][mt][nt][c], -7 * g));
+    return df_scale(v, p);
+}
+
+// Position within the 32 x 32 warp block of accumulator element (mt, nt, c).
+__device__ __forceinline__ void acc_pos(int mt, int nt, int c, int &r, int &col) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    r = mt * 16 + g + (c >= 2 ? 8 : 0);
+    col = nt * 8 + 2 * t + (c & 1);
+}
+
+// ----------------------------------------------------------------------------- stencil
+
+__device__ __forceinline__ double stencil_w_mx(const double *__restrict__ b, const double *__restrict__ c,
+                                               const double *__restrict__ d, double h, int g, int dir) {
+    double ih2 = 1.0 / (h * h);
+    switch (dir) {
+    case DIR_C: return 4.0 * ih2 + d[g];
+    case DIR_E: return -ih2 + b[g] / h;
+    case DIR_W: return -ih2 - b[g] / h;
+    case DIR_N: return -ih2 + c[g] / h;
+    default: return -ih2 - c[g] / h;
+    }
+}
+
+__device__ __forceinline__ void record_pivot_mx(Status *st, double piv, int stage) {
+    double ap = fabs(piv);
+    if (!(ap > 0.0) || !isfinite(ap)) {
+        if (atomicCAS(&st->code, 0, GM_ESINGULAR) == 0) st->where = stage;
+        return;
+    }
+    atomicMin(&st->min_piv, (unsigned long long)__double_as_longlong(ap));
+}
+
+struct MergeTabMx {
+    const int *p3, *p4, *g3, *g4, *p1, *q1, *p2, *q2, *x12;
+};
+__device__ __forceinline__ MergeTabMx merge_tab_mx(const MergeDesc &M, const int *tab) {
+    const int *t = tab + M.tab;
+    MergeTabMx T;
+    T.p3 = t; T.p4 = t + M.sp; T.g3 = t + 2 * M.sp; T.g4 = t + 3 * M.sp;
+    T.p1 = t + 4 * M.sp; T.q1 = T.p1 + M.n1; T.p2 = T.q1 + M.n1; T.q2 = T.p2 + M.n2;
+    T.x12 = T.q2 + M.n2;
+    return T;
+}
+
+// ----------------------------------------------------------------------------- digit planes
+
+// A digit matrix holds, for each of S digits, a plane of rows x kpad bf16 values
+// (k fastest, zero beyond K), plus one exponent per row: element (s, row, k) is at
+// dig[s * plane + row * kpad + k].  kpad is a multiple of 16.
+
+// One lane-strided warp slices a row of K df32 values, produced by `get(k)`.
+template <int S, class Get>
+__device__ __forceinline__ void warp_slice_row(Get get, int K, int kpad, __nv_bfloat16 *dig, int64_t plane, int64_t row,
+                                               int *ex) {
+    const int lane = threadIdx.x & 31;
+    float mx = 0.f;
+    for (int k = lane; k < K; k += 32) mx = fmaxf(mx, fabsf(get(k).x));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = exp_of_max(mx * 1.0000001f);
+    if (lane == 0) ex[row] = e;
+    for (int k = lane; k < kpad; k += 32) {
+        float d[S];
+        float2 v = k < K ? get(k) : make_float2(0.f, 0.f);
+        digits<S>(v, e, d);
+#pragma unroll
+        for (int s = 0; s < S; ++s) dig[(int64_t)s * plane + row * kpad + k] = __float2bfloat16_rn(d[s]);
+    }
+}
+
+// 64 rows x 16 k of every digit plane into shared memory ([S][64][KP]); 128 threads.
+template <int S>
+__device__ __forceinline__ void load_digit_tile(const __nv_bfloat16 *__restrict__ dig, int64_t plane, int kpad,
+                                                int r0, int nrows, int k0, __nv_bfloat16 *sm) {
+    const int row = threadIdx.x >> 1, half = threadIdx.x & 1;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (row < nrows) v = *(const uint4 *)(dig + (int64_t)s * plane + (int64_t)(r0 + row) * kpad + k0 + half * 8);
+        *(uint4 *)(sm + ((size_t)s * 64 + row) * KP + half * 8) = v;
+    }
+}
+
+// C(i, j) = sum_k A(i, k) B(k, j) for a 64 x 64 tile from two digit matrices (A by rows,
+// B by columns), K in chunks of at most 512 (exact level sums), result in df32 per
+// thread position (see acc_pos); warp w owns rows (w & 1) * 32 and columns (w >> 1) * 32.
+template <int S>
+__device__ __forceinline__ void digit_gemm_tile(const __nv_bfloat16 *__restrict__ Ad, int64_t aplane, int akpad,
+                                                int i0, int M, const int *__restrict__ aex,
+                                                const __nv_bfloat16 *__restrict__ Bd, int64_t bplane, int bkpad,
+                                                int j0, int N, const int *__restrict__ bex, int K,
+                                                __nv_bfloat16 *As, __nv_bfloat16 *Bs, float2 res[2][4][4]) {
+    const int warp = threadIdx.x >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) res[mt][nt][c] = make_float2(0.f, 0.f);
+    const int mrows = min(64, M - i0), ncols = min(64, N - j0);
+    for (int k0 = 0; k0 < K; k0 += 512) {
+        const int kend = min(K, k0 + 512);
+        float acc[S][2][4][4];
+#pragma unroll
+        for (int g = 0; g < S; ++g)
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[g][mt][nt][c] = 0.f;
+        for (int t0 = k0; t0 < kend; t0 += 16) {
+            __syncthreads();
+            load_digit_tile<S>(Ad, aplane, akpad, i0, mrows, t0, As);
+            load_digit_tile<S>(Bd, bplane, bkpad, j0, ncols, t0, Bs);
+            __syncthreads();
+            warp_mma_levels<S>(As, Bs, 64, 64, wm, wn, acc);
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    int r, cl;
+                    acc_pos(mt, nt, c, r, cl);
+                    const int i = min(i0 + wm + r, M - 1), j = min(j0 + wn + cl, N - 1);
+                    float2 u = combine_levels<S>(acc, mt, nt, c, aex[i] + bex[j] - 12);
+                    res[mt][nt][c] = df_add(res[mt][nt][c], u);
+                }
+    }
+}
+
+
+}  // namespace gm

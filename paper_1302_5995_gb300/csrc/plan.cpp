@@ -102,6 +102,12 @@ void add_merge(Stage &st, int n, const Box &c1, int64_t s1, const Box &c2, int64
     int mm = 2 * m.sp, ncol = mm + m.rp;
     m.ws = ws;
     ws += (int64_t)mm * ncol;
+    m.kpad = (mm + 15) / 16 * 16;
+    if (m.kpad == 0) m.kpad = 16;
+    m.doff = st.dig_elems;
+    st.dig_elems += (int64_t)m.rp * m.kpad;
+    m.eoff = (int)st.exp_elems;
+    st.exp_elems += m.rp;
     st.max_m = std::max(st.max_m, mm);
     st.max_ncol = std::max(st.max_ncol, ncol);
     st.max_rp = std::max(st.max_rp, m.rp);
@@ -195,6 +201,8 @@ int validate_plan(const Plan &plan) {
             if (m.out < 0 || m.out + (int64_t)m.rp * m.rp > st.out_doubles) return GM_EINVAL;
             int mm = 2 * m.sp;
             if (m.ws < 0 || m.ws + (int64_t)mm * (mm + m.rp) > st.ws_doubles) return GM_EINVAL;
+            if (m.kpad < mm || m.kpad % 16 || m.doff < 0 || m.doff + (int64_t)m.rp * m.kpad > st.dig_elems) return GM_EINVAL;
+            if (m.eoff < 0 || m.eoff + m.rp > st.exp_elems) return GM_EINVAL;
             const int *t = st.table.data() + m.tab;
             if (m.tab + 4 * m.sp + 2 * m.n1 + 2 * m.n2 + 8 > (int)st.table.size()) return GM_EINVAL;
             const int *p3 = t, *p4 = t + m.sp, *g3 = t + 2 * m.sp, *g4 = t + 3 * m.sp;

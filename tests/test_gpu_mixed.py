@@ -1,0 +1,121 @@
+"""Mixed precision (double-float storage, FP32 pivot search, split-product tensor-core
+updates) against the FP64 oracle.  Stated bound: 1e-8 relative for the 512 x 512
+convection-diffusion-reaction build and its 256 solutions (per-vector 2-norms), the
+same bound for every intermediate Schur complement (max-norm relative)."""
+import numpy as np
+import pytest
+
+from oracle import closed_form as cf
+from oracle import nd_dense
+from paper_1302_5995_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+TOL_MIXED = 1e-8
+
+
+@pytest.fixture(scope="module")
+def gm():
+    from paper_1302_5995_gb300 import build_ext
+    build_ext.build()
+    import paper_1302_5995_gb300 as gm
+    return gm
+
+
+def rel_mat(A, B):
+    return np.abs(A - B).max() / np.abs(B).max()
+
+
+def rel_vec(V, Vo):
+    return (np.linalg.norm(V - Vo, axis=0) / np.linalg.norm(Vo, axis=0)).max()
+
+
+def solve_cols(op, G):
+    B = G.shape[1]
+    return op.solve(np.ascontiguousarray(G.T)).reshape(B, G.shape[0]).T
+
+
+@pytest.mark.parametrize("n,leaf", [(24, 4), (37, 5), (64, 8)])
+def test_mixed_every_level(gm, n, leaf):
+    b, c, d = inputs.convection_fields(n, seeds=(41, 42, 43))
+    op = gm.build(b, c, d, n, leaf, keep_levels=True, precision=gm.PREC_MIXED)
+    ref = nd_dense.build(b, c, d, n, leaf, keep=True)
+    for box, So in ref.schur.items():
+        assert rel_mat(op.schur(box.x0, box.y0, box.a, box.b), So) < TOL_MIXED, box
+    assert rel_mat(op.dtn(), ref.T) < TOL_MIXED
+
+
+@pytest.mark.parametrize("split", [3, 4, 5, 6])
+def test_mixed_digits_control_the_error(gm, split):
+    n, leaf = 128, 16
+    b, c, d = inputs.convection_fields(n)
+    To = nd_dense.build(b, c, d, n, leaf).T
+    op = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED, split_digits=split)
+    err = rel_mat(op.dtn(), To)
+    # each digit carries 7 bits: the error falls by about 2^7 per added digit
+    bound = {3: 1e-4, 4: 1e-7, 5: 1e-9, 6: 1e-11}[split]
+    assert err < bound, err
+
+
+def test_mixed_config2_full_size(gm):
+    import torch
+    cfg = inputs.config2()
+    n = cfg["n"]
+    dev = [torch.from_numpy(cfg[k]).cuda() for k in "bcd"]
+    op = gm.build(*dev, n, cfg["leaf"], precision=gm.PREC_MIXED)
+    To = nd_dense.build(cfg["b"], cfg["c"], cfg["d"], n, cfg["leaf"]).T
+    assert rel_mat(op.dtn(), To) < TOL_MIXED
+    G = torch.from_numpy(np.ascontiguousarray(cfg["G"].T)).cuda()
+    V = op.solve(G)
+    torch.cuda.synchronize()
+    V = V.cpu().numpy().reshape(256, 4 * n).T
+    assert rel_vec(V, To @ cfg["G"]) < TOL_MIXED
+
+
+def test_mixed_laplace_harmonic(gm):
+    cfg = inputs.config1()
+    n = cfg["n"]
+    op = gm.build(cfg["b"], cfg["c"], cfg["d"], n, cfg["leaf"], precision=gm.PREC_MIXED)
+    T = op.dtn()
+    G5, V5 = cf.harmonic_pairs(n)
+    assert np.abs(T @ G5 - V5).max() < TOL_MIXED * np.abs(T).max()
+    V = solve_cols(op, G5)
+    assert np.abs(V - V5).max() < TOL_MIXED * np.abs(T).max()
+
+
+@pytest.mark.parametrize("n,leaf", [(2, 4), (5, 4), (9, 4), (61, 16)])
+def test_mixed_small_and_ragged(gm, n, leaf):
+    b, c, d = inputs.convection_fields(n, seeds=(3, 4, 5))
+    op = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED)
+    assert rel_mat(op.dtn(), nd_dense.build(b, c, d, n, leaf).T) < TOL_MIXED
+
+
+def test_mixed_singular_box_reported(gm):
+    n = 6
+    b, c, d = inputs.laplace_fields(n)
+    h = 1.0 / (n + 1)
+    d = d.copy()
+    d[1 + n * 1] = -4.0 / (h * h)
+    with pytest.raises(gm.GmError) as e:
+        gm.build(b, c, d, n, 4, precision=gm.PREC_MIXED)
+    assert e.value.code == gm.GM_ESINGULAR
+
+
+@pytest.mark.parametrize("piv", ["block", "partial"])
+def test_mixed_pivoting_modes_agree_with_oracle(gm, piv):
+    n, leaf = 100, 13
+    b, c, d = inputs.convection_fields(n, seeds=(71, 72, 73))
+    mode = gm.PIVOT_BLOCK if piv == "block" else gm.PIVOT_PARTIAL
+    op = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED, pivoting=mode)
+    assert op.info()["pivoting"] == mode
+    assert rel_mat(op.dtn(), nd_dense.build(b, c, d, n, leaf).T) < TOL_MIXED
+
+
+def test_mixed_indefinite_helmholtz(gm):
+    """Variable-wavespeed Helmholtz (indefinite): whatever pivoting the automatic mode
+    settles on, the result must meet the bound."""
+    n, leaf = 96, 12
+    k = inputs.nudged_wavenumber(n, leaf)
+    b, c, d = inputs.helmholtz_fields(n, k)
+    op = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED)
+    To = nd_dense.build(b, c, d, n, leaf).T
+    assert rel_mat(op.dtn(), To) < 1e3 * TOL_MIXED * max(1.0, np.abs(To).max() / (4 * (n + 1)))
