@@ -30,9 +30,34 @@ UNIT = "gridpoints/s"
 N_GRID, LEAF, NVEC = 512, 16, 256
 WORKLOAD = ("convection-diffusion-reaction, b,c,d = 8-mode Fourier fields (seeds 1-3), 512x512 grid "
             "(N=262144), leaf 16x16, build + solve of 256 Gaussian boundary vectors (seed 4)")
-# FP64 peak from unit counts and clock: 152 SMs x 4 FP64 flop/clk/SM (2 DFMA) x 2070 MHz
-SMS, FP64_FLOP_PER_CLK_SM, SM_MAX_MHZ = 152, 4, 2070.0
-FP64_PEAK_TFLOPS = SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+# Peaks.  FP64 and FP32 pipes from unit counts and the maximum SM clock:
+#   FP64: 152 SMs x 4 flop/clk/SM (2 DFMA) x 2070 MHz = 1.259 TFLOP/s
+#   FP32: 152 SMs x 256 flop/clk/SM (128 FFMA) x 2070 MHz = 80.5 TFLOP/s
+# Split products: the measured bf16 dense peak divided by the digit-pair products one
+# algorithmic multiply-add costs (S(S+1)/2 for S digits per operand).
+SMS, SM_MAX_MHZ = 152, 2070.0
+FP64_PEAK_TFLOPS = SMS * 4 * SM_MAX_MHZ * 1e6 / 1e12
+FP32_PEAK_TFLOPS = SMS * 256 * SM_MAX_MHZ * 1e6 / 1e12
+SPLIT_DIGITS = 6
+
+
+def bf16_peak_tflops():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def family_roofline(precision, fam):
+    """(bound, peak TFLOP/s, source) of a kernel family in this build."""
+    if precision == "fp64" or fam == "leaf":
+        return "alu", FP64_PEAK_TFLOPS, "FP64 pipe from unit counts: 152 SMs x 4 flop/clk x 2070 MHz"
+    if fam == "panel":
+        return "alu", FP32_PEAK_TFLOPS, "FP32 pipe from unit counts: 152 SMs x 256 flop/clk x 2070 MHz"
+    bf, src = bf16_peak_tflops()
+    pairs = SPLIT_DIGITS * (SPLIT_DIGITS + 1) // 2
+    return "tensor", bf / pairs, (f"bf16 dense peak ({src} {bf:.1f} TFLOP/s) / {pairs} digit-pair products "
+                                  f"per algorithmic multiply-add ({SPLIT_DIGITS} digits)")
 # DRAM traffic of the dominant kernel from an ncu capture (profiles/), per launch, with the
 # source digest it was taken at; reported as null once the kernel source changes.
 TRAFFIC = {}
@@ -165,6 +190,7 @@ def run_gm(args):
     import paper_1302_5995_gb300 as gm
 
     prec = gm.PREC_MIXED if args.precision == "mixed" else gm.PREC_FP64
+    extra = dict(split_digits=SPLIT_DIGITS) if args.precision == "mixed" else {}
     cfg, Gv = make_inputs()
     n = N_GRID
     dev = torch.device("cuda", local)
@@ -175,7 +201,7 @@ def run_gm(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
     def step(timing):
-        op = gm.build(b, c, d, n, LEAF, precision=prec, stream=stream, timing=timing)
+        op = gm.build(b, c, d, n, LEAF, precision=prec, stream=stream, timing=timing, **extra)
         op.solve(G, out=V, stream=stream)
         return op
 
@@ -198,7 +224,7 @@ def run_gm(args):
         flush.fill_(1.0)
         barrier()
         ev[0].record(stream)
-        op = gm.build(b, c, d, n, LEAF, precision=prec, stream=stream, timing=True)
+        op = gm.build(b, c, d, n, LEAF, precision=prec, stream=stream, timing=True, **extra)
         ev[1].record(stream)
         op.solve(G, out=V, stream=stream)
         ev[2].record(stream)
@@ -234,13 +260,34 @@ def run_gm(args):
     for it in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        op = gm.build(hb[0].numpy(), hb[1].numpy(), hb[2].numpy(), n, LEAF, precision=prec, stream=stream)
+        op = gm.build(hb[0].numpy(), hb[1].numpy(), hb[2].numpy(), n, LEAF, precision=prec, stream=stream,
+                      **extra)
         op.solve(hG.numpy(), out=hV.numpy(), stream=stream)
         t1 = time.perf_counter()
         op.free()
         if it >= args.warmup:
             e2e_t.append(t1 - t0)
     e2e_step = statistics.mean(e2e_t)
+    # the plain FP64 GPU path on the same workload, for the equal-accuracy comparison
+    fp64 = None
+    if args.precision == "mixed":
+        fb, fs = [], []
+        for it in range(2 + 3):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            op = gm.build(b, c, d, n, LEAF, precision=gm.PREC_FP64, stream=stream)
+            ev[1].record(stream)
+            op.solve(G, out=V, stream=stream)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            if it >= 2:
+                fb.append(ev[0].elapsed_time(ev[1]))
+                fs.append(ev[1].elapsed_time(ev[2]))
+            op.free()
+        fp64 = {"build_ms": statistics.mean(fb), "solve_ms": statistics.mean(fs),
+                "value": n * n / ((statistics.mean(fb) + statistics.mean(fs)) * 1e-3) * world,
+                "solve_vectors_per_s": NVEC / (statistics.mean(fs) * 1e-3) * world, "steps": 3}
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank != 0:
@@ -251,14 +298,15 @@ def run_gm(args):
     rel_err = float((np.linalg.norm(Vg - Vo, axis=0) / np.linalg.norm(Vo, axis=0)).max())
     dom = max(fam_ms, key=lambda f: fam_ms[f])
     achieved = fam_fl[dom] / (fam_ms[dom] * 1e-3) / 1e12
-    peak = FP64_PEAK_TFLOPS
+    bound, peak, peak_src = family_roofline(args.precision, dom)
     tr = TRAFFIC.get(dom)
     traffic = tr[0] if (tr and tr[1] == source_digest()) else None
     sorted_ms = sorted(step_ms)
     line = {
         "metric": METRIC, "value": world * n * n / (t_step * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "split-f64 (6 bf16 digits, df32 storage)" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "leaf": LEAF, "nvec": NVEC, "precision": args.precision,
                    "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -268,15 +316,20 @@ def run_gm(args):
         "latency_ms": {"p50": sorted_ms[len(sorted_ms) // 2],
                        "p99": sorted_ms[min(len(sorted_ms) - 1, int(0.99 * len(sorted_ms)))]},
         "rel_err_vs_fp64_oracle": rel_err,
-        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": "FP64 from unit counts: 152 SMs x 4 flop/clk x 2070 MHz",
+        "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                      "launches_per_step": fam_n[dom] // args.steps,
                      "ms_per_step": fam_ms[dom] / args.steps},
         "kernel_ms_per_step": {f: fam_ms[f] / args.steps for f in fam_ms},
+        "kernel_roofline": {f: {"bound": family_roofline(args.precision, f)[0],
+                                "achieved_tflops": fam_fl[f] / max(fam_ms[f], 1e-9) / 1e9,
+                                "frac": fam_fl[f] / max(fam_ms[f], 1e-9) / 1e9 / family_roofline(args.precision, f)[1]}
+                            for f in fam_ms if fam_fl[f] > 0},
+        "fp64_path": fp64,
         "cpu_baseline": {"value": n * n / t_cpu, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                          "sample": "one full step: numpy/LAPACK dense nested dissection (oracle O2) + T @ G "
                                    "of the 256 vectors, default BLAS threading"},
+        "rel_err_bound": 1e-8 if args.precision == "mixed" else 1e-10,
         "e2e": {"value": world * n * n / e2e_step, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step * 1e3},
         "clocks": clk,
@@ -291,7 +344,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gm", "reference"], default="gm")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

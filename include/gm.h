@@ -63,7 +63,8 @@ typedef struct gm_opts {
     int keep_levels;  /* nonzero: keep every intermediate Schur complement for
                          gm_get_schur() (costs the memory of all levels)                 */
     void *stream;     /* cudaStream_t for the build (NULL = legacy default stream)      */
-    int panel_width;  /* pivot panel width of the dense eliminations (0 = default 8)    */
+    int panel_width;  /* pivot panel width of the partial-pivoting eliminations
+                         (0 = default: 8 for FP64, 16 for mixed precision)             */
     int timing;       /* nonzero: time every kernel launch of the build with CUDA events
                          (per kernel family, reported by gm_info)                       */
     int split_digits; /* GM_PREC_MIXED: 7-bit digits per operand of the split products,
@@ -129,6 +130,24 @@ int gm_build(const double *b, const double *c, const double *d, int n, int leaf,
              gm_handle **out);
 int gm_build_ex(const gm_opts *opts, const double *b, const double *c, const double *d, int n,
                 int leaf, double tol, gm_handle **out);
+
+/* One problem of a batched build. */
+typedef struct gm_problem {
+    const double *b, *c, *d; /* n*n coefficients each (host or device), index i + n*j */
+    int n, leaf;             /* as for gm_build                                      */
+} gm_problem;
+
+/*
+ * Build `count` independent operators in one sweep (Section 3.3's level-by-level order
+ * applied to all of them together): all leaves in one launch, then for each tree level,
+ * counted from the root, one stage of horizontal and one of vertical pairwise merges over
+ * every problem that has that level, then all roots in one batched elimination.
+ * Problems may differ in n and leaf.  outs[p] receives problem p's handle (freed
+ * separately).  keep_levels is not supported here (GM_EUNSUPPORTED).  On an error no
+ * handle is returned.  The same opts apply to every problem.
+ */
+int gm_build_batch(int count, const gm_problem *probs, const gm_opts *opts, double tol,
+                   gm_handle **outs);
 
 /*
  * Solve stage (Section 1.1): dudn[:, v] = T g[:, v] for v < batch.

@@ -48,6 +48,11 @@ class Info(ctypes.Structure):
                 ("pivot_fallback", ctypes.c_int)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("b", ctypes.c_void_p), ("c", ctypes.c_void_p), ("d", ctypes.c_void_p), ("n", ctypes.c_int),
+                ("leaf", ctypes.c_int)]
+
+
 #: exported symbols and their (restype, argtypes)
 SIGNATURES = {
     "gm_opts_default": (None, [ctypes.POINTER(Opts)]),
@@ -55,6 +60,8 @@ SIGNATURES = {
                                                       ctypes.POINTER(ctypes.c_void_p)]),
     "gm_build_ex": (ctypes.c_int, [ctypes.POINTER(Opts)] + [ctypes.c_void_p] * 3
                     + [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]),
+    "gm_build_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Problem), ctypes.POINTER(Opts), ctypes.c_double,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
     "gm_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "gm_get_dtn": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gm_get_schur": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 4 + [ctypes.c_void_p]),
@@ -203,6 +210,40 @@ class DtN:
         return out
 
 
+def _opts(precision, keep_levels, stream, panel_width, timing, split_digits, pivoting):
+    lib = load_library()
+    o = Opts()
+    lib.gm_opts_default(ctypes.byref(o))
+    o.precision = precision
+    o.keep_levels = 1 if keep_levels else 0
+    o.stream = _stream_handle(stream)
+    o.panel_width = panel_width
+    o.timing = 1 if timing else 0
+    o.split_digits = split_digits
+    o.pivoting = pivoting
+    return o
+
+
+def build_batch(problems, tol=0.0, precision=PREC_FP64, stream=None, panel_width=0, timing=False, split_digits=0,
+                pivoting=PIVOT_AUTO):
+    """Build several operators in one level-by-level sweep.
+
+    problems: list of (b, c, d, n, leaf).  Returns a list of DtN handles."""
+    lib = load_library()
+    arr = (Problem * len(problems))()
+    keep = []
+    for i, (b, c, d, n, leaf) in enumerate(problems):
+        b, c, d = (_check_f64(x, "coefficients", n * n) for x in (b, c, d))
+        keep += [b, c, d]
+        arr[i] = Problem(_ptr(b).value, _ptr(c).value, _ptr(d).value, n, leaf)
+    o = _opts(precision, False, stream, panel_width, timing, split_digits, pivoting)
+    outs = (ctypes.c_void_p * len(problems))()
+    rc = lib.gm_build_batch(len(problems), arr, ctypes.byref(o), float(tol), outs)
+    if rc:
+        raise GmError(rc, "gm_build_batch")
+    return [DtN(ctypes.c_void_p(outs[i]), problems[i][3], problems[i][4]) for i in range(len(problems))]
+
+
 def build(b, c, d, n, leaf, tol=0.0, precision=PREC_FP64, keep_levels=False, stream=None, panel_width=0,
           timing=False, split_digits=0, pivoting=PIVOT_AUTO):
     """Build the DtN operator for coefficient fields b, c, d (n*n each, index i + n*j)."""
@@ -210,16 +251,7 @@ def build(b, c, d, n, leaf, tol=0.0, precision=PREC_FP64, keep_levels=False, str
     b = _check_f64(b, "b", n * n)
     c = _check_f64(c, "c", n * n)
     d = _check_f64(d, "d", n * n)
-    o = Opts()
-    lib.gm_opts_default(ctypes.byref(o))
-    o.precision = precision
-    o.keep_levels = 1 if keep_levels else 0
-    o.stream = _stream_handle(stream)
-    if panel_width:
-        o.panel_width = panel_width
-    o.timing = 1 if timing else 0
-    o.split_digits = split_digits
-    o.pivoting = pivoting
+    o = _opts(precision, keep_levels, stream, panel_width, timing, split_digits, pivoting)
     h = ctypes.c_void_p()
     rc = lib.gm_build_ex(ctypes.byref(o), _ptr(b), _ptr(c), _ptr(d), n, leaf, float(tol), ctypes.byref(h))
     if rc:

@@ -1,12 +1,15 @@
-// C ABI: gm_build / gm_solve / gm_get_dtn / gm_get_schur / gm_info / gm_free.
+// C ABI: gm_build / gm_build_batch / gm_solve / gm_get_dtn / gm_get_schur / gm_info / gm_free.
 //
-// The build runs the paper's level-by-level sweep (Section 3.3): every leaf in one
-// launch, then per level one stage of horizontal pairwise merges and one of vertical
-// ones (each stage batched over all its merges), then the root.  All device memory is
-// taken from the CUDA stream-ordered allocator on the build stream.
+// A build runs the paper's level-by-level sweep (Section 3.3): every leaf of every
+// problem in one launch, then per tree level one stage of horizontal pairwise merges and
+// one of vertical ones -- each stage one batch over all its merges, across all problems
+// of a batched build (stages aligned from the root) -- then all roots in one batch.
+// Every Schur complement of a build lives in one device arena; the rest of the device
+// memory comes from the stream-ordered allocator on the build stream.
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -14,19 +17,31 @@
 #include <tuple>
 #include <vector>
 
+#include "blocked.h"
 #include "gm_internal.h"
 #include "kernels.h"
 #include "mixed.h"
-#include "blocked.h"
 
 using namespace gm;
 
 namespace {
 
-#define CK(x)                                       \
-    do {                                            \
-        cudaError_t _e = (x);                       \
-        if (_e != cudaSuccess) return GM_ECUDA;     \
+// With GM_DEBUG set in the environment, every failing CUDA call is reported on stderr
+// with its source line and the runtime's error string.
+bool debug_on() {
+    static const bool on = getenv("GM_DEBUG") != nullptr;
+    return on;
+}
+
+int cuda_fail(cudaError_t e, const char *what, int line) {
+    if (debug_on()) fprintf(stderr, "gm: api.cu:%d: %s: %s\n", line, what, cudaGetErrorString(e));
+    return GM_ECUDA;
+}
+
+#define CK(x)                                                  \
+    do {                                                       \
+        cudaError_t _e = (x);                                  \
+        if (_e != cudaSuccess) return cuda_fail(_e, #x, __LINE__); \
     } while (0)
 
 bool is_device_ptr(const void *p) {
@@ -64,11 +79,11 @@ struct DBuf {
     template <class T> T *as() const { return (T *)p; }
 };
 
-// Device copy of a plan (cached per (n, leaf) and per device).
+// Device copy of a plan (cached per device and per list of (n, leaf)).
 struct DevStage {
     int orient, nm, max_m, max_ncol, max_rp;
     int sum_rows = 0, sum_cols = 0;
-    int64_t in_doubles, out_doubles, ws_doubles, max_elems;
+    int64_t out_base, out_doubles, ws_doubles, max_elems, dig_elems, exp_elems;
     MergeDesc *d_merges = nullptr;
     int *d_tab = nullptr;
     SysDesc *d_sys = nullptr;
@@ -81,6 +96,8 @@ struct DevPlan {
     std::vector<DevStage> stages;
     SysDesc *d_root_sys = nullptr;
     std::vector<SysDesc> h_root_sys;
+    int64_t root_ws = 0;  // elements of the roots' dense systems
+    int max_root_ncol = 0;
     ~DevPlan() {
         cudaFree(d_leaves);
         for (auto &s : stages) {
@@ -92,8 +109,9 @@ struct DevPlan {
     }
 };
 
+using PlanKey = std::pair<int, std::vector<std::pair<int, int>>>;
 std::mutex g_plan_mu;
-std::map<std::tuple<int, int, int>, std::shared_ptr<DevPlan>> g_plans;
+std::map<PlanKey, std::shared_ptr<DevPlan>> g_plans;
 
 template <class T> int upload(T **dst, const std::vector<T> &v) {
     size_t bytes = v.size() * sizeof(T);
@@ -105,58 +123,88 @@ template <class T> int upload(T **dst, const std::vector<T> &v) {
     return GM_OK;
 }
 
-int get_plan(int n, int leaf, std::shared_ptr<DevPlan> &out) {
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
-    std::lock_guard<std::mutex> lk(g_plan_mu);
-    auto key = std::make_tuple(dev, n, leaf);
-    auto it = g_plans.find(key);
-    if (it != g_plans.end()) {
-        out = it->second;
-        return GM_OK;
+int make_devplan(DevPlan &dp) {
+    int rc;
+    const Plan &P = dp.plan;
+    for (const LeafDesc &l : P.leaves) {
+        dp.max_leaf_a = std::max(dp.max_leaf_a, l.a);
+        dp.max_leaf_b = std::max(dp.max_leaf_b, l.b);
     }
-    auto dp = std::make_shared<DevPlan>();
-    int rc = build_plan(n, leaf, dp->plan);
-    if (rc) return rc;
-    for (const Box &b : dp->plan.leaf_boxes) {
-        dp->max_leaf_a = std::max(dp->max_leaf_a, b.a);
-        dp->max_leaf_b = std::max(dp->max_leaf_b, b.b);
-    }
-    if ((rc = upload(&dp->d_leaves, dp->plan.leaves))) return rc;
-    for (const Stage &st : dp->plan.stages) {
+    if ((rc = upload(&dp.d_leaves, P.leaves))) return rc;
+    for (const Stage &st : P.stages) {
         DevStage ds;
         ds.orient = st.orient;
         ds.nm = (int)st.merges.size();
         ds.max_m = st.max_m;
         ds.max_ncol = st.max_ncol;
         ds.max_rp = st.max_rp;
-        ds.in_doubles = st.in_doubles;
+        ds.out_base = st.out_base;
         ds.out_doubles = st.out_doubles;
         ds.ws_doubles = st.ws_doubles;
+        ds.dig_elems = st.dig_elems;
+        ds.exp_elems = st.exp_elems;
         ds.max_elems = 0;
-        std::vector<SysDesc> sys;
         int roff = 0, coff = 0;
         for (int i = 0; i < ds.nm; ++i) {
             const MergeDesc &m = st.merges[i];
             SysDesc s{m.ws, 2 * m.sp, 2 * m.sp + m.rp, i, roff, coff, 0};
             roff += s.m;
             coff += s.ncol;
-            sys.push_back(s);
+            ds.h_sys.push_back(s);
             ds.max_elems = std::max(ds.max_elems, (int64_t)s.m * s.ncol);
         }
         ds.sum_rows = roff;
         ds.sum_cols = coff;
-        ds.h_sys = sys;
-        dp->stages.push_back(ds);
-        DevStage &d = dp->stages.back();
+        dp.stages.push_back(ds);
+        DevStage &d = dp.stages.back();
         if ((rc = upload(&d.d_merges, st.merges))) return rc;
         if ((rc = upload(&d.d_tab, st.table))) return rc;
-        if ((rc = upload(&d.d_sys, sys))) return rc;
+        if ((rc = upload(&d.d_sys, d.h_sys))) return rc;
     }
-    int r = dp->plan.r_root;
-    std::vector<SysDesc> rs{SysDesc{0, r, r + 4 * n, 0, 0, 0, 0}};
-    dp->h_root_sys = rs;
-    if ((rc = upload(&dp->d_root_sys, rs))) return rc;
+    int roff = 0, coff = 0;
+    int64_t wo = 0;
+    for (size_t i = 0; i < P.roots.size(); ++i) {
+        const RootDesc &r = P.roots[i];
+        SysDesc s{wo, r.r, r.r + 4 * r.n, (int)i, roff, coff, 0};
+        roff += s.m;
+        coff += s.ncol;
+        wo += (int64_t)s.m * s.ncol;
+        dp.max_root_ncol = std::max(dp.max_root_ncol, s.ncol);
+        dp.h_root_sys.push_back(s);
+    }
+    dp.root_ws = wo;
+    return upload(&dp.d_root_sys, dp.h_root_sys);
+}
+
+int get_plan(const std::vector<std::pair<int, int>> &probs, std::shared_ptr<DevPlan> &out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    PlanKey key(dev, probs);
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) {
+        out = it->second;
+        return GM_OK;
+    }
+    auto dp = std::make_shared<DevPlan>();
+    int rc;
+    if (probs.size() == 1) {
+        rc = build_plan(probs[0].first, probs[0].second, dp->plan);
+    } else {
+        std::vector<Plan> singles(probs.size());
+        std::vector<const Plan *> ptrs;
+        std::vector<int64_t> coef;
+        int64_t acc = 0;
+        for (size_t i = 0; i < probs.size(); ++i) {
+            if ((rc = build_plan(probs[i].first, probs[i].second, singles[i]))) return rc;
+            ptrs.push_back(&singles[i]);
+            coef.push_back(acc);
+            acc += (int64_t)probs[i].first * probs[i].first;
+        }
+        rc = build_batch_plan(ptrs, coef, dp->plan);
+    }
+    if (rc) return rc;
+    if ((rc = make_devplan(*dp))) return rc;
     g_plans[key] = dp;
     out = dp;
     return GM_OK;
@@ -189,11 +237,11 @@ void event_pool_put(cudaEvent_t e) {
 
 struct gm_handle {
     int n = 0, leaf = 0, L = 0, precision = 0;
-    double *T = nullptr;      // 4n x 4n column-major
+    double *T = nullptr;            // 4n x 4n column-major
     float2 *Tdf = nullptr;          // mixed precision: T as double-float
     __nv_bfloat16 *tdig = nullptr;  // mixed precision: digit planes of T's rows, for the apply
     int *tex = nullptr;             // mixed precision: row exponents of T
-    int split = 4;            // mixed precision: digits per operand
+    int split = 5;                  // mixed precision: digits per operand
     std::shared_ptr<DevPlan> plan;
     // kept intermediates: box -> device pointer of its Schur complement (FP64, or
     // double-float pairs for a mixed-precision build)
@@ -209,13 +257,324 @@ const double *gm::handle_dtn(gm_handle *h, int *n) {
     return h->T;
 }
 
+extern "C" void gm_free(gm_handle *h);
+
+namespace {
+
+// One build (a single problem or a batch) in either precision.  db/dc/dd are device
+// arrays holding every problem's coefficients at its RootDesc::coef offset.  H[p] is the
+// handle of problem p (allocated by the caller); *growth_out reports the block-pivoting
+// growth flag of a mixed build.
+int run_build(const gm_opts &o, const std::shared_ptr<DevPlan> &dpp, const double *db, const double *dc,
+              const double *dd, std::vector<gm_handle *> &H, int *growth_out) {
+    const DevPlan &dp = *dpp;
+    const Plan &P = dp.plan;
+    cudaStream_t s = (cudaStream_t)o.stream;
+    const bool mixed = o.precision == GM_PREC_MIXED;
+    const bool blockpiv = mixed && o.pivoting != GM_PIVOT_PARTIAL;
+    const int nb = o.panel_width > 0 ? o.panel_width : (mixed ? 16 : 8);
+    if (nb > GJ_MAX_NB) return GM_EINVAL;
+    const int split = o.split_digits ? o.split_digits : 5;
+    if (mixed && (split < 3 || split > 6)) return GM_EINVAL;
+    if (leaf_smem_bytes(dp.max_leaf_a, dp.max_leaf_b) > 220 * 1024) return GM_EUNSUPPORTED;
+    // the leaf kernel gives each inner-ring right-hand side one of 64 thread columns
+    if (2 * (dp.max_leaf_a - 2) + 2 * (dp.max_leaf_b - 2) - 4 > 64) return GM_EUNSUPPORTED;
+    if (mixed && !blockpiv) {
+        int mm = P.r_root;
+        for (const DevStage &ds : dp.stages) mm = std::max(mm, ds.max_m);
+        if ((size_t)mm * nb * sizeof(float) > 200 * 1024) return GM_EUNSUPPORTED;
+    }
+    if (o.keep_levels && H.size() != 1) return GM_EUNSUPPORTED;
+    for (gm_handle *h : H) {
+        h->plan = dpp;
+        h->L = P.L;
+        h->split = split;
+        h->kept_df32 = mixed;
+    }
+    int rc;
+    DBuf stat;
+    if ((rc = stat.alloc(sizeof(Status), s))) return rc;
+    Status st0{0, -1, 0x7ff0000000000000ull, 0, 0};
+    CK(cudaMemcpyAsync(stat.p, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
+    Status *dst = stat.as<Status>();
+    KTimer kt;
+    kt.on = o.timing != 0;
+
+    // the arena: FP64, or double-float pairs (same 8 bytes per element)
+    DBuf arena_buf;
+    void *arena = nullptr;
+    const size_t arena_bytes = (size_t)P.arena_doubles * 8;
+    if (o.keep_levels) {
+        if (cudaMalloc(&arena, arena_bytes ? arena_bytes : 16) != cudaSuccess) {
+            cudaGetLastError();
+            return GM_ENOMEM;
+        }
+        H[0]->kept_bufs.push_back(arena);
+        for (size_t i = 0; i < P.leaves.size(); ++i)
+            H[0]->kept.push_back({P.leaf_boxes[i], (char *)arena + P.leaves[i].off * 8});
+        for (const Stage &st : P.stages)
+            for (size_t i = 0; i < st.merges.size(); ++i)
+                H[0]->kept.push_back({st.out_boxes[i], (char *)arena + st.merges[i].out * 8});
+    } else {
+        if ((rc = arena_buf.alloc(arena_bytes, s))) return rc;
+        arena = arena_buf.p;
+    }
+    double *A64 = (double *)arena;
+    float2 *Adf = (float2 *)arena;
+    int64_t peak = arena_bytes;
+
+    // leaves (Section 3.3 step 2)
+    if (!mixed) {
+        CK(launch_leaf(dp.d_leaves, P.leaves, dp.max_leaf_a, dp.max_leaf_b, db, dc, dd, A64, dst, 0, s, kt));
+    } else {
+        DBuf leaf64;
+        if ((rc = leaf64.alloc(P.leaf_doubles * 8, s))) return rc;
+        CK(launch_leaf(dp.d_leaves, P.leaves, dp.max_leaf_a, dp.max_leaf_b, db, dc, dd, leaf64.as<double>(), dst, 0,
+                       s, kt));
+        CK(mx_convert(leaf64.as<double>(), Adf, P.leaf_doubles, s, kt));
+    }
+
+    // scratch of the sweeps, sized for the largest stage and for the roots
+    int max_nm = (int)P.roots.size(), piv_ld = P.r_root;
+    int64_t max_rows = 0, max_cols = 0, max_plane = 16, max_exp = 1, max_u12 = 0;
+    for (const SysDesc &r : dp.h_root_sys) {
+        max_rows += r.m;
+        max_cols += r.ncol;
+    }
+    max_u12 = (int64_t)max_nm * nb * dp.max_root_ncol;
+    for (size_t si = 0; si < dp.stages.size(); ++si) {
+        const DevStage &ds = dp.stages[si];
+        max_nm = std::max(max_nm, ds.nm);
+        piv_ld = std::max(piv_ld, ds.max_m);
+        max_rows = std::max<int64_t>(max_rows, ds.sum_rows);
+        max_cols = std::max<int64_t>(max_cols, ds.sum_cols);
+        max_plane = std::max<int64_t>(max_plane, ds.dig_elems);
+        max_exp = std::max<int64_t>(max_exp, ds.exp_elems);
+        max_u12 = std::max<int64_t>(max_u12, (int64_t)ds.nm * nb * ds.max_ncol);
+    }
+    DBuf piv, u12;                                          // FP64 sweep
+    DBuf perm, perm_n, a11, fdig, rdig, fex, rex;           // mixed, partial pivoting
+    DBuf ydig, xdig, yex, xex;                              // mixed Schur updates
+    DBuf bxd, bad, bxe, bae, bpmag, bfdig, bfex, brdig, brex;  // mixed, block pivoting
+    MxScratch scr;
+    BlkScratch bscr;
+    if (!mixed) {
+        if ((rc = piv.alloc((size_t)max_nm * piv_ld * sizeof(int), s))) return rc;
+        if ((rc = u12.alloc((size_t)max_u12 * 8, s))) return rc;
+    } else {
+        if ((rc = ydig.alloc((size_t)split * max_plane * 2, s)) || (rc = xdig.alloc((size_t)split * max_plane * 2, s)) ||
+            (rc = yex.alloc((size_t)max_exp * sizeof(int), s)) || (rc = xex.alloc((size_t)max_exp * sizeof(int), s)))
+            return rc;
+        if (blockpiv) {
+            const size_t sq = (size_t)max_nm * 64;
+            if ((rc = bxd.alloc((size_t)split * sq * 64 * 2, s)) || (rc = bad.alloc((size_t)split * sq * 64 * 2, s)) ||
+                (rc = bxe.alloc(sq * sizeof(int), s)) || (rc = bae.alloc(sq * sizeof(int), s)) ||
+                (rc = bpmag.alloc(sq * sizeof(float), s)) ||
+                (rc = bfdig.alloc((size_t)split * max_rows * 64 * 2, s)) ||
+                (rc = bfex.alloc((size_t)max_rows * sizeof(int), s)) ||
+                (rc = brdig.alloc((size_t)split * max_cols * 64 * 2, s)) ||
+                (rc = brex.alloc((size_t)max_cols * sizeof(int), s)))
+                return rc;
+            bscr.x_dig = bxd.as<__nv_bfloat16>();
+            bscr.a11_dig = bad.as<__nv_bfloat16>();
+            bscr.x_ex = bxe.as<int>();
+            bscr.a11_ex = bae.as<int>();
+            bscr.pmag = bpmag.as<float>();
+            bscr.fdig = bfdig.as<__nv_bfloat16>();
+            bscr.fex = bfex.as<int>();
+            bscr.rdig = brdig.as<__nv_bfloat16>();
+            bscr.rex = brex.as<int>();
+            bscr.growth = &dst->growth;
+        } else {
+            if ((rc = perm.alloc((size_t)max_nm * 4 * GJ_MAX_NB * sizeof(int), s)) ||
+                (rc = perm_n.alloc((size_t)max_nm * sizeof(int), s)) ||
+                (rc = a11.alloc((size_t)max_nm * GJ_MAX_NB * GJ_MAX_NB * sizeof(float2), s)) ||
+                (rc = fdig.alloc((size_t)split * max_rows * 16 * 2, s)) ||
+                (rc = rdig.alloc((size_t)split * max_cols * 16 * 2, s)) ||
+                (rc = fex.alloc((size_t)max_rows * sizeof(int), s)) ||
+                (rc = rex.alloc((size_t)max_cols * sizeof(int), s)))
+                return rc;
+            scr.perm = perm.as<int>();
+            scr.perm_n = perm_n.as<int>();
+            scr.a11inv = a11.as<float2>();
+            scr.fdig = fdig.as<__nv_bfloat16>();
+            scr.rdig = rdig.as<__nv_bfloat16>();
+            scr.fex = fex.as<int>();
+            scr.rex = rex.as<int>();
+        }
+    }
+    // one dense sweep over a set of systems: FP64 Gauss-Jordan, or a mixed sweep
+    auto sweep = [&](const SysDesc *d_sys, const std::vector<SysDesc> &h_sys, int max_m, int max_ncol, void *ws,
+                     int sum_rows, int sum_cols, int stage) -> cudaError_t {
+        if (!mixed)
+            return launch_gj_sweep(d_sys, h_sys, max_m, max_ncol, (double *)ws, nb, piv.as<int>(), piv_ld,
+                                   u12.as<double>(), (int64_t)nb * max_ncol, dst, stage, s, kt);
+        if (blockpiv) {
+            bscr.inv_plane = (int64_t)h_sys.size() * 64 * 64;
+            bscr.fplane = (int64_t)sum_rows * 64;
+            bscr.cplane = (int64_t)sum_cols * 64;
+            return blk_gj_sweep(d_sys, h_sys, max_m, max_ncol, (float2 *)ws, split, bscr, dst, stage, s, kt);
+        }
+        scr.fplane = (int64_t)sum_rows * 16;
+        scr.rplane = (int64_t)sum_cols * 16;
+        return mx_gj_sweep(d_sys, h_sys, max_m, max_ncol, (float2 *)ws, nb, split, scr, dst, stage, s, kt);
+    };
+
+    // merge stages (Section 3.3 step 3): per level, horizontal then vertical
+    for (size_t si = 0; si < dp.stages.size(); ++si) {
+        const DevStage &ds = dp.stages[si];
+        const Stage &hs = P.stages[si];
+        if (ds.nm == 0) continue;
+        DBuf ws;
+        if ((rc = ws.alloc(ds.ws_doubles * 8, s))) return rc;
+        peak = std::max(peak, (int64_t)(arena_bytes + ds.ws_doubles * 8));
+        if (!mixed) {
+            CK(launch_merge_assemble(ds.d_merges, ds.nm, ds.d_tab, A64, ws.as<double>(), ds.max_elems, db, dc, dd, 0,
+                                     s, kt));
+            CK(sweep(ds.d_sys, ds.h_sys, ds.max_m, ds.max_ncol, ws.p, ds.sum_rows, ds.sum_cols, (int)si + 1));
+            CK(launch_merge_update(ds.d_merges, hs.merges, ds.d_tab, A64, ws.as<double>(), A64, ds.max_rp, db, dc, dd,
+                                   0, s, kt));
+        } else {
+            CK(mx_merge_assemble(ds.d_merges, ds.nm, ds.d_tab, Adf, ws.as<float2>(), ds.max_elems, db, dc, dd, 0, s,
+                                 kt));
+            CK(sweep(ds.d_sys, ds.h_sys, ds.max_m, ds.max_ncol, ws.p, ds.sum_rows, ds.sum_cols, (int)si + 1));
+            CK(mx_merge_update(ds.d_merges, hs.merges, ds.d_tab, Adf, ws.as<float2>(), Adf, ds.max_rp, split,
+                               ydig.as<__nv_bfloat16>(), yex.as<int>(), xdig.as<__nv_bfloat16>(), xex.as<int>(),
+                               ds.dig_elems, db, dc, dd, 0, s, kt));
+        }
+    }
+
+    // roots (Section 3.3 step 4): X = S_root^{-1} B for every problem in one sweep
+    DBuf rws;
+    if ((rc = rws.alloc(dp.root_ws * 8, s))) return rc;
+    peak = std::max(peak, (int64_t)(arena_bytes + dp.root_ws * 8));
+    int max_r = 0, sum_rr = 0, sum_rc = 0;
+    for (size_t i = 0; i < P.roots.size(); ++i) {
+        const RootDesc &r = P.roots[i];
+        const SysDesc &sy = dp.h_root_sys[i];
+        max_r = std::max(max_r, r.r);
+        sum_rr += sy.m;
+        sum_rc += sy.ncol;
+        if (!mixed)
+            CK(launch_root_assemble(A64 + r.off, r.r, r.n, rws.as<double>() + sy.off, db + r.coef, dc + r.coef,
+                                    dd + r.coef, s, kt));
+        else
+            CK(mx_root_assemble(Adf + r.off, r.r, r.n, rws.as<float2>() + sy.off, db + r.coef, dc + r.coef,
+                                dd + r.coef, s, kt));
+    }
+    CK(sweep(dp.d_root_sys, dp.h_root_sys, max_r, dp.max_root_ncol, rws.p, sum_rr, sum_rc,
+             (int)dp.stages.size() + 1));
+    for (size_t i = 0; i < P.roots.size(); ++i) {
+        const RootDesc &r = P.roots[i];
+        gm_handle *h = H[r.problem];
+        const int nb4 = 4 * r.n;
+        const SysDesc &sy = dp.h_root_sys[i];
+        if (cudaMalloc(&h->T, (size_t)nb4 * nb4 * 8) != cudaSuccess) {
+            cudaGetLastError();
+            return GM_ENOMEM;
+        }
+        if (!mixed) {
+            CK(launch_root_finalize(rws.as<double>() + sy.off, r.r, r.n, h->T, s, kt));
+        } else {
+            const int kpadT = mx_kpad(nb4);
+            if (cudaMalloc(&h->Tdf, (size_t)nb4 * nb4 * sizeof(float2)) != cudaSuccess ||
+                cudaMalloc(&h->tdig, (size_t)split * nb4 * kpadT * 2) != cudaSuccess ||
+                cudaMalloc(&h->tex, (size_t)nb4 * sizeof(int)) != cudaSuccess) {
+                cudaGetLastError();
+                return GM_ENOMEM;
+            }
+            CK(mx_root_finalize(rws.as<float2>() + sy.off, r.r, r.n, h->T, h->Tdf, h->tdig, h->tex, split, s, kt));
+        }
+    }
+    Status st;
+    CK(cudaMemcpyAsync(&st, stat.p, sizeof(st), cudaMemcpyDeviceToHost, s));
+    // release temporaries (stream-ordered) before the final synchronisation
+    for (DBuf *b : {&rws, &piv, &u12, &perm, &perm_n, &a11, &fdig, &rdig, &fex, &rex, &ydig, &xdig, &yex, &xex, &bxd,
+                    &bad, &bxe, &bae, &bpmag, &bfdig, &bfex, &brdig, &brex, &arena_buf, &stat})
+        b->release();
+    CK(cudaStreamSynchronize(s));
+    int launches = 0;
+    gm_info_t info{};
+    for (int f = 0; f < GM_K_NFAM; ++f) {
+        launches += kt.launches[f];
+        info.kernel_launches[f] = kt.launches[f];
+        info.kernel_flops[f] = kt.flops[f];
+    }
+    kt.collect(info.kernel_ms);
+    double mp;
+    memcpy(&mp, &st.min_piv, 8);
+    info.bad_stage = st.code ? st.where : -1;
+    info.launches = launches;
+    info.peak_workspace = peak;
+    info.pivoting = blockpiv ? GM_PIVOT_BLOCK : GM_PIVOT_PARTIAL;
+    info.levels = P.L;
+    info.precision = o.precision;
+    for (gm_handle *h : H) {
+        gm_info_t hi = info;
+        hi.n = h->n;
+        hi.leaf = h->leaf;
+        hi.dtn_bytes = (long long)16 * h->n * h->n * 8;
+        hi.min_pivot_ratio = mp / (4.0 * (h->n + 1.0) * (h->n + 1.0));
+        h->info = hi;
+    }
+    *growth_out = st.growth;
+    if (st.code) return st.code;
+    return GM_OK;
+}
+
+// Build with the automatic pivoting fallback; on failure every handle is freed.
+int build_with_fallback(const gm_opts &o, const std::vector<std::pair<int, int>> &probs, const double *db,
+                        const double *dc, const double *dd, std::vector<gm_handle *> &H) {
+    auto fresh = [&]() {
+        for (gm_handle *h : H) gm_free(h);
+        H.clear();
+        for (const auto &p : probs) {
+            gm_handle *h = new gm_handle();
+            h->n = p.first;
+            h->leaf = p.second;
+            h->precision = o.precision;
+            H.push_back(h);
+        }
+    };
+    std::shared_ptr<DevPlan> dp;
+    int rc = get_plan(probs, dp);
+    if (rc) return rc;
+    fresh();
+    int growth = 0;
+    rc = run_build(o, dp, db, dc, dd, H, &growth);
+    if (o.precision == GM_PREC_MIXED && o.pivoting == GM_PIVOT_AUTO && (growth || rc == GM_ESINGULAR)) {
+        // block pivoting was not safe for these operators: redo with partial pivoting
+        cudaGetLastError();
+        fresh();
+        gm_opts o2 = o;
+        o2.pivoting = GM_PIVOT_PARTIAL;
+        rc = run_build(o2, dp, db, dc, dd, H, &growth);
+        for (gm_handle *h : H) h->info.pivot_fallback = 1;
+    }
+    if (rc) {
+        cudaGetLastError();
+        for (gm_handle *h : H) gm_free(h);
+        H.clear();
+    }
+    return rc;
+}
+
+int check_opts(const gm_opts *opts, gm_opts &o) {
+    gm_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.precision != GM_PREC_FP64 && o.precision != GM_PREC_MIXED) return GM_EINVAL;
+    if (o.pivoting < GM_PIVOT_AUTO || o.pivoting > GM_PIVOT_PARTIAL) return GM_EINVAL;
+    return GM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void gm_opts_default(gm_opts *o) {
     if (!o) return;
     memset(o, 0, sizeof(*o));
     o->precision = GM_PREC_FP64;
-    o->panel_width = 8;
 }
 
 const char *gm_strerror(int code) {
@@ -248,394 +607,6 @@ int gm_build(const double *b, const double *c, const double *d, int n, int leaf,
     return gm_build_ex(&o, b, c, d, n, leaf, tol, out);
 }
 
-static int build_impl(const gm_opts &o, const double *b, const double *c, const double *d, int n, int leaf,
-                      gm_handle *H) {
-    cudaStream_t s = (cudaStream_t)o.stream;
-    int nb = o.panel_width > 0 ? o.panel_width : 8;
-    if (nb > GJ_MAX_NB) return GM_EINVAL;
-    std::shared_ptr<DevPlan> dp;
-    int rc = get_plan(n, leaf, dp);
-    if (rc) return rc;
-    const Plan &P = dp->plan;
-    if (leaf_smem_bytes(dp->max_leaf_a, dp->max_leaf_b) > 220 * 1024) return GM_EUNSUPPORTED;
-    H->plan = dp;
-    H->L = P.L;
-    const size_t N2 = (size_t)n * n;
-    // coefficients on the device
-    DBuf coef;
-    const double *db = b, *dc = c, *dd = d;
-    if (!is_device_ptr(b) || !is_device_ptr(c) || !is_device_ptr(d)) {
-        if ((rc = coef.alloc(3 * N2 * sizeof(double), s))) return rc;
-        double *base = coef.as<double>();
-        CK(cudaMemcpyAsync(base, b, N2 * 8, cudaMemcpyDefault, s));
-        CK(cudaMemcpyAsync(base + N2, c, N2 * 8, cudaMemcpyDefault, s));
-        CK(cudaMemcpyAsync(base + 2 * N2, d, N2 * 8, cudaMemcpyDefault, s));
-        db = base;
-        dc = base + N2;
-        dd = base + 2 * N2;
-    }
-    DBuf stat;
-    if ((rc = stat.alloc(sizeof(Status), s))) return rc;
-    Status st0{0, -1, 0x7ff0000000000000ull, 0, 0};
-    CK(cudaMemcpyAsync(stat.p, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
-    Status *dst = stat.as<Status>();
-    int64_t peak = 0;
-    KTimer kt;
-    kt.on = o.timing != 0;
-    // A level's Schur complements: stream-ordered scratch, or handle-owned when kept.
-    auto alloc_level = [&](size_t bytes, DBuf &owner, double *&ptr) -> int {
-        if (o.keep_levels) {
-            void *p = nullptr;
-            if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
-                cudaGetLastError();
-                return GM_ENOMEM;
-            }
-            H->kept_bufs.push_back(p);
-            ptr = (double *)p;
-            return GM_OK;
-        }
-        int e = owner.alloc(bytes, s);
-        ptr = owner.as<double>();
-        return e;
-    };
-    auto keep = [&](const std::vector<Box> &boxes, const std::vector<int64_t> &offs, double *base) {
-        if (!o.keep_levels) return;
-        for (size_t i = 0; i < boxes.size(); ++i) H->kept.push_back({boxes[i], base + offs[i]});
-    };
-
-    // leaves (Section 3.3 step 2)
-    DBuf cur_buf;
-    double *cur_ptr = nullptr;
-    if ((rc = alloc_level(P.leaf_doubles * 8, cur_buf, cur_ptr))) return rc;
-    CK(launch_leaf(dp->d_leaves, P.leaves, dp->max_leaf_a, dp->max_leaf_b, db, dc, dd, n, cur_ptr, dst, 0, s,
-                   kt));
-    {
-        std::vector<int64_t> offs;
-        for (auto &l : P.leaves) offs.push_back(l.off);
-        keep(P.leaf_boxes, offs, cur_ptr);
-    }
-    // merge stages (Section 3.3 step 3): per level, horizontal then vertical
-    int piv_ld = P.r_root;
-    int64_t max_u12 = (int64_t)nb * (P.r_root + 4 * n);
-    int max_nm = 1;
-    for (const DevStage &ds : dp->stages) {
-        piv_ld = std::max(piv_ld, ds.max_m);
-        max_u12 = std::max(max_u12, (int64_t)ds.nm * nb * ds.max_ncol);
-        max_nm = std::max(max_nm, ds.nm);
-    }
-    DBuf piv, u12;
-    if ((rc = piv.alloc((size_t)max_nm * piv_ld * sizeof(int), s))) return rc;
-    if ((rc = u12.alloc((size_t)max_u12 * 8, s))) return rc;
-    for (size_t si = 0; si < dp->stages.size(); ++si) {
-        const DevStage &ds = dp->stages[si];
-        const Stage &hs = P.stages[si];
-        DBuf nxt_buf, ws;
-        double *nxt_ptr = nullptr;
-        if ((rc = alloc_level(ds.out_doubles * 8, nxt_buf, nxt_ptr))) return rc;
-        if ((rc = ws.alloc(ds.ws_doubles * 8, s))) return rc;
-        peak = std::max(peak, (int64_t)(ds.ws_doubles + ds.out_doubles + ds.in_doubles) * 8);
-        CK(launch_merge_assemble(ds.d_merges, ds.nm, ds.d_tab, cur_ptr, ws.as<double>(), ds.max_elems, db, dc,
-                                 dd, n, s, kt));
-        CK(launch_gj_sweep(ds.d_sys, ds.h_sys, ds.max_m, ds.max_ncol, ws.as<double>(), nb, piv.as<int>(), piv_ld,
-                           u12.as<double>(), (int64_t)nb * ds.max_ncol, dst, (int)si + 1, s, kt));
-        CK(launch_merge_update(ds.d_merges, hs.merges, ds.d_tab, cur_ptr, ws.as<double>(), nxt_ptr, ds.max_rp, db,
-                               dc, dd, n, s, kt));
-        std::vector<int64_t> offs;
-        for (auto &m : hs.merges) offs.push_back(m.out);
-        keep(hs.out_boxes, offs, nxt_ptr);
-        // stream-ordered: the previous level is freed after this stage's kernels
-        cur_buf.release();
-        std::swap(cur_buf.p, nxt_buf.p);
-        std::swap(cur_buf.s, nxt_buf.s);
-        cur_ptr = nxt_ptr;
-    }
-    // root (Section 3.3 step 4): X = S_root^{-1} B, then T = (I - P X)/h
-    const int r = P.r_root, nb4 = 4 * n;
-    DBuf rws;
-    if ((rc = rws.alloc((size_t)r * (r + nb4) * 8, s))) return rc;
-    peak = std::max(peak, (int64_t)r * (r + nb4) * 8);
-    CK(launch_root_assemble(cur_ptr, r, n, rws.as<double>(), db, dc, dd, s, kt));
-    CK(launch_gj_sweep(dp->d_root_sys, dp->h_root_sys, r, r + nb4, rws.as<double>(), nb, piv.as<int>(), piv_ld,
-                       u12.as<double>(), (int64_t)nb * (r + nb4), dst, (int)dp->stages.size() + 1, s, kt));
-    if (cudaMalloc(&H->T, (size_t)nb4 * nb4 * 8) != cudaSuccess) {
-        cudaGetLastError();
-        return GM_ENOMEM;
-    }
-    CK(launch_root_finalize(rws.as<double>(), r, n, H->T, s, kt));
-    Status st;
-    CK(cudaMemcpyAsync(&st, stat.p, sizeof(st), cudaMemcpyDeviceToHost, s));
-    // release temporaries (stream-ordered) before the final synchronisation
-    rws.release();
-    piv.release();
-    u12.release();
-    cur_buf.release();
-    coef.release();
-    stat.release();
-    CK(cudaStreamSynchronize(s));
-    double ih = 4.0 * (n + 1.0) * (n + 1.0);
-    double mp;
-    memcpy(&mp, &st.min_piv, 8);
-    H->info.min_pivot_ratio = mp / ih;
-    H->info.bad_stage = st.code ? st.where : -1;
-    int launches = 0;
-    for (int f = 0; f < GM_K_NFAM; ++f) {
-        launches += kt.launches[f];
-        H->info.kernel_launches[f] = kt.launches[f];
-        H->info.kernel_flops[f] = kt.flops[f];
-    }
-    kt.collect(H->info.kernel_ms);
-    H->info.launches = launches;
-    H->info.peak_workspace = peak;
-    if (st.code) return st.code;
-    return GM_OK;
-}
-
-// Mixed precision (GM_PREC_MIXED): leaves in FP64, converted once to double-float;
-// every stage and the root on double-float data with split-product tensor-core updates.
-static int build_impl_mixed(const gm_opts &o, const double *b, const double *c, const double *d, int n, int leaf,
-                            gm_handle *H, int *growth_out) {
-    const bool blockpiv = o.pivoting != GM_PIVOT_PARTIAL;
-    cudaStream_t s = (cudaStream_t)o.stream;
-    int nb = o.panel_width > 0 ? o.panel_width : 16;
-    if (nb > GJ_MAX_NB) return GM_EINVAL;
-    int split = o.split_digits ? o.split_digits : 5;
-    if (split < 3 || split > 6) return GM_EINVAL;
-    H->split = split;
-    std::shared_ptr<DevPlan> dp;
-    int rc = get_plan(n, leaf, dp);
-    if (rc) return rc;
-    const Plan &P = dp->plan;
-    if (leaf_smem_bytes(dp->max_leaf_a, dp->max_leaf_b) > 220 * 1024) return GM_EUNSUPPORTED;
-    if (!blockpiv && (size_t)(P.r_root) * nb * sizeof(float) > 200 * 1024) return GM_EUNSUPPORTED;
-    H->plan = dp;
-    H->L = P.L;
-    H->kept_df32 = true;
-    const size_t N2 = (size_t)n * n;
-    DBuf coef;
-    const double *db = b, *dc = c, *dd = d;
-    if (!is_device_ptr(b) || !is_device_ptr(c) || !is_device_ptr(d)) {
-        if ((rc = coef.alloc(3 * N2 * sizeof(double), s))) return rc;
-        double *base = coef.as<double>();
-        CK(cudaMemcpyAsync(base, b, N2 * 8, cudaMemcpyDefault, s));
-        CK(cudaMemcpyAsync(base + N2, c, N2 * 8, cudaMemcpyDefault, s));
-        CK(cudaMemcpyAsync(base + 2 * N2, d, N2 * 8, cudaMemcpyDefault, s));
-        db = base;
-        dc = base + N2;
-        dd = base + 2 * N2;
-    }
-    DBuf stat;
-    if ((rc = stat.alloc(sizeof(Status), s))) return rc;
-    Status st0{0, -1, 0x7ff0000000000000ull, 0, 0};
-    CK(cudaMemcpyAsync(stat.p, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
-    Status *dst = stat.as<Status>();
-    int64_t peak = 0;
-    KTimer kt;
-    kt.on = o.timing != 0;
-    auto alloc_level = [&](size_t elems, DBuf &owner, float2 *&ptr) -> int {
-        size_t bytes = elems * sizeof(float2);
-        if (o.keep_levels) {
-            void *p = nullptr;
-            if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
-                cudaGetLastError();
-                return GM_ENOMEM;
-            }
-            H->kept_bufs.push_back(p);
-            ptr = (float2 *)p;
-            return GM_OK;
-        }
-        int e = owner.alloc(bytes, s);
-        ptr = owner.as<float2>();
-        return e;
-    };
-    auto keep = [&](const std::vector<Box> &boxes, const std::vector<int64_t> &offs, float2 *base) {
-        if (!o.keep_levels) return;
-        for (size_t i = 0; i < boxes.size(); ++i) H->kept.push_back({boxes[i], (void *)(base + offs[i])});
-    };
-    // leaves (Section 3.3 step 2) in FP64, then one conversion to double-float
-    DBuf leaf64, cur_buf;
-    if ((rc = leaf64.alloc(P.leaf_doubles * 8, s))) return rc;
-    CK(launch_leaf(dp->d_leaves, P.leaves, dp->max_leaf_a, dp->max_leaf_b, db, dc, dd, n, leaf64.as<double>(), dst,
-                   0, s, kt));
-    float2 *cur_ptr = nullptr;
-    if ((rc = alloc_level(P.leaf_doubles, cur_buf, cur_ptr))) return rc;
-    CK(mx_convert(leaf64.as<double>(), cur_ptr, P.leaf_doubles, s, kt));
-    leaf64.release();
-    {
-        std::vector<int64_t> offs;
-        for (auto &l : P.leaves) offs.push_back(l.off);
-        keep(P.leaf_boxes, offs, cur_ptr);
-    }
-    // scratch of the sweeps (sized for the largest stage or the root) and of the Schur updates
-    int max_nm = 1;
-    int64_t max_rows = P.r_root, max_cols = P.r_root + 4 * n, max_plane = 16, max_exp = 1;
-    for (size_t si = 0; si < dp->stages.size(); ++si) {
-        const DevStage &ds = dp->stages[si];
-        max_nm = std::max(max_nm, ds.nm);
-        max_rows = std::max<int64_t>(max_rows, ds.sum_rows);
-        max_cols = std::max<int64_t>(max_cols, ds.sum_cols);
-        max_plane = std::max<int64_t>(max_plane, P.stages[si].dig_elems);
-        max_exp = std::max<int64_t>(max_exp, P.stages[si].exp_elems);
-    }
-    DBuf perm, perm_n, a11, fdig, rdig, fex, rex, ydig, xdig, yex, xex;
-    if ((rc = perm.alloc((size_t)max_nm * 4 * GJ_MAX_NB * sizeof(int), s))) return rc;
-    if ((rc = perm_n.alloc((size_t)max_nm * sizeof(int), s))) return rc;
-    if ((rc = a11.alloc((size_t)max_nm * GJ_MAX_NB * GJ_MAX_NB * sizeof(float2), s))) return rc;
-    if ((rc = fdig.alloc((size_t)split * max_rows * 16 * 2, s))) return rc;
-    if ((rc = rdig.alloc((size_t)split * max_cols * 16 * 2, s))) return rc;
-    if ((rc = fex.alloc((size_t)max_rows * sizeof(int), s))) return rc;
-    if ((rc = rex.alloc((size_t)max_cols * sizeof(int), s))) return rc;
-    if ((rc = ydig.alloc((size_t)split * max_plane * 2, s))) return rc;
-    if ((rc = xdig.alloc((size_t)split * max_plane * 2, s))) return rc;
-    if ((rc = yex.alloc((size_t)max_exp * sizeof(int), s))) return rc;
-    if ((rc = xex.alloc((size_t)max_exp * sizeof(int), s))) return rc;
-    // block-pivoting scratch
-    DBuf bxd, bad, bxe, bae, bpmag, bfdig, bfex, badig, br0d, bed, brdig, baex, br0e, bee, brex, br0;
-    BlkScratch bscr;
-    if (blockpiv) {
-        const size_t sq = (size_t)max_nm * 64;
-        if ((rc = bxd.alloc((size_t)split * sq * 64 * 2, s)) || (rc = bad.alloc((size_t)split * sq * 64 * 2, s)) ||
-            (rc = bxe.alloc(sq * sizeof(int), s)) || (rc = bae.alloc(sq * sizeof(int), s)) ||
-            (rc = bpmag.alloc(sq * sizeof(float), s)) ||
-            (rc = bfdig.alloc((size_t)split * max_rows * 64 * 2, s)) ||
-            (rc = bfex.alloc((size_t)max_rows * sizeof(int), s)) ||
-            (rc = badig.alloc((size_t)split * max_cols * 64 * 2, s)) ||
-            (rc = br0d.alloc((size_t)split * max_cols * 64 * 2, s)) ||
-            (rc = bed.alloc((size_t)split * max_cols * 64 * 2, s)) ||
-            (rc = brdig.alloc((size_t)split * max_cols * 64 * 2, s)) ||
-            (rc = baex.alloc((size_t)max_cols * sizeof(int), s)) ||
-            (rc = br0e.alloc((size_t)max_cols * sizeof(int), s)) ||
-            (rc = bee.alloc((size_t)max_cols * sizeof(int), s)) ||
-            (rc = brex.alloc((size_t)max_cols * sizeof(int), s)) ||
-            (rc = br0.alloc((size_t)max_cols * 64 * sizeof(float2), s)))
-            return rc;
-        bscr.x_dig = bxd.as<__nv_bfloat16>();
-        bscr.a11_dig = bad.as<__nv_bfloat16>();
-        bscr.x_ex = bxe.as<int>();
-        bscr.a11_ex = bae.as<int>();
-        bscr.pmag = bpmag.as<float>();
-        bscr.fdig = bfdig.as<__nv_bfloat16>();
-        bscr.fex = bfex.as<int>();
-        bscr.adig = badig.as<__nv_bfloat16>();
-        bscr.r0dig = br0d.as<__nv_bfloat16>();
-        bscr.edig = bed.as<__nv_bfloat16>();
-        bscr.rdig = brdig.as<__nv_bfloat16>();
-        bscr.aex = baex.as<int>();
-        bscr.r0ex = br0e.as<int>();
-        bscr.eex = bee.as<int>();
-        bscr.rex = brex.as<int>();
-        bscr.r0 = br0.as<float2>();
-        bscr.growth = &dst->growth;
-    }
-    MxScratch scr;
-    scr.perm = perm.as<int>();
-    scr.perm_n = perm_n.as<int>();
-    scr.a11inv = a11.as<float2>();
-    scr.fdig = fdig.as<__nv_bfloat16>();
-    scr.rdig = rdig.as<__nv_bfloat16>();
-    scr.fex = fex.as<int>();
-    scr.rex = rex.as<int>();
-    for (size_t si = 0; si < dp->stages.size(); ++si) {
-        const DevStage &ds = dp->stages[si];
-        const Stage &hs = P.stages[si];
-        if ((size_t)ds.max_m * nb * sizeof(float) > 200 * 1024) return GM_EUNSUPPORTED;
-        DBuf nxt_buf, ws;
-        float2 *nxt_ptr = nullptr;
-        if ((rc = alloc_level(ds.out_doubles, nxt_buf, nxt_ptr))) return rc;
-        if ((rc = ws.alloc(ds.ws_doubles * sizeof(float2), s))) return rc;
-        peak = std::max(peak, (int64_t)(ds.ws_doubles + ds.out_doubles + ds.in_doubles) * 8);
-        CK(mx_merge_assemble(ds.d_merges, ds.nm, ds.d_tab, cur_ptr, ws.as<float2>(), ds.max_elems, db, dc, dd, n, s,
-                             kt));
-        if (blockpiv) {
-            bscr.inv_plane = (int64_t)ds.nm * 64 * 64;
-            bscr.fplane = (int64_t)ds.sum_rows * 64;
-            bscr.cplane = (int64_t)ds.sum_cols * 64;
-            CK(blk_gj_sweep(ds.d_sys, ds.h_sys, ds.max_m, ds.max_ncol, ws.as<float2>(), split, bscr, dst, (int)si + 1,
-                            s, kt));
-        } else {
-            scr.fplane = (int64_t)ds.sum_rows * 16;
-            scr.rplane = (int64_t)ds.sum_cols * 16;
-            CK(mx_gj_sweep(ds.d_sys, ds.h_sys, ds.max_m, ds.max_ncol, ws.as<float2>(), nb, split, scr, dst,
-                           (int)si + 1, s, kt));
-        }
-        CK(mx_merge_update(ds.d_merges, hs.merges, ds.d_tab, cur_ptr, ws.as<float2>(), nxt_ptr, ds.max_rp, split,
-                           ydig.as<__nv_bfloat16>(), yex.as<int>(), xdig.as<__nv_bfloat16>(), xex.as<int>(),
-                           hs.dig_elems, db, dc, dd, n, s, kt));
-        std::vector<int64_t> offs;
-        for (auto &m : hs.merges) offs.push_back(m.out);
-        keep(hs.out_boxes, offs, nxt_ptr);
-        cur_buf.release();
-        std::swap(cur_buf.p, nxt_buf.p);
-        std::swap(cur_buf.s, nxt_buf.s);
-        cur_ptr = nxt_ptr;
-    }
-    // root (Section 3.3 step 4)
-    const int r = P.r_root, nb4 = 4 * n;
-    DBuf rws;
-    if ((rc = rws.alloc((size_t)r * (r + nb4) * sizeof(float2), s))) return rc;
-    peak = std::max(peak, (int64_t)r * (r + nb4) * 8);
-    CK(mx_root_assemble(cur_ptr, r, n, rws.as<float2>(), db, dc, dd, s, kt));
-    if (blockpiv) {
-        bscr.inv_plane = (int64_t)64 * 64;
-        bscr.fplane = (int64_t)r * 64;
-        bscr.cplane = (int64_t)(r + nb4) * 64;
-        CK(blk_gj_sweep(dp->d_root_sys, dp->h_root_sys, r, r + nb4, rws.as<float2>(), split, bscr, dst,
-                        (int)dp->stages.size() + 1, s, kt));
-    } else {
-        scr.fplane = (int64_t)r * 16;
-        scr.rplane = (int64_t)(r + nb4) * 16;
-        CK(mx_gj_sweep(dp->d_root_sys, dp->h_root_sys, r, r + nb4, rws.as<float2>(), nb, split, scr, dst,
-                       (int)dp->stages.size() + 1, s, kt));
-    }
-    const int kpadT = mx_kpad(nb4);
-    if (cudaMalloc(&H->T, (size_t)nb4 * nb4 * 8) != cudaSuccess ||
-        cudaMalloc(&H->Tdf, (size_t)nb4 * nb4 * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc(&H->tdig, (size_t)split * nb4 * kpadT * 2) != cudaSuccess ||
-        cudaMalloc(&H->tex, (size_t)nb4 * sizeof(int)) != cudaSuccess) {
-        cudaGetLastError();
-        return GM_ENOMEM;
-    }
-    CK(mx_root_finalize(rws.as<float2>(), r, n, H->T, H->Tdf, H->tdig, H->tex, split, s, kt));
-    Status st;
-    CK(cudaMemcpyAsync(&st, stat.p, sizeof(st), cudaMemcpyDeviceToHost, s));
-    rws.release();
-    perm.release();
-    perm_n.release();
-    a11.release();
-    fdig.release();
-    rdig.release();
-    fex.release();
-    rex.release();
-    ydig.release();
-    xdig.release();
-    yex.release();
-    xex.release();
-    for (DBuf *b : {&bxd, &bad, &bxe, &bae, &bpmag, &bfdig, &bfex, &badig, &br0d, &bed, &brdig, &baex, &br0e, &bee,
-                    &brex, &br0})
-        b->release();
-    cur_buf.release();
-    coef.release();
-    stat.release();
-    CK(cudaStreamSynchronize(s));
-    double ih = 4.0 * (n + 1.0) * (n + 1.0);
-    double mp;
-    memcpy(&mp, &st.min_piv, 8);
-    H->info.min_pivot_ratio = mp / ih;
-    H->info.bad_stage = st.code ? st.where : -1;
-    int launches = 0;
-    for (int f = 0; f < GM_K_NFAM; ++f) {
-        launches += kt.launches[f];
-        H->info.kernel_launches[f] = kt.launches[f];
-        H->info.kernel_flops[f] = kt.flops[f];
-    }
-    kt.collect(H->info.kernel_ms);
-    H->info.launches = launches;
-    H->info.peak_workspace = peak;
-    H->info.pivoting = blockpiv ? GM_PIVOT_BLOCK : GM_PIVOT_PARTIAL;
-    *growth_out = st.growth;
-    if (st.code) return st.code;
-    return GM_OK;
-}
-
 int gm_build_ex(const gm_opts *opts, const double *b, const double *c, const double *d, int n, int leaf, double tol,
                 gm_handle **out) {
     if (!out) return GM_EINVAL;
@@ -643,48 +614,63 @@ int gm_build_ex(const gm_opts *opts, const double *b, const double *c, const dou
     if (!b || !c || !d || n < 2 || leaf < 4 || tol < 0) return GM_EINVAL;
     if (tol != 0.0) return GM_EUNSUPPORTED;
     gm_opts o;
-    gm_opts_default(&o);
-    if (opts) o = *opts;
-    if (o.precision != GM_PREC_FP64 && o.precision != GM_PREC_MIXED) return GM_EINVAL;
-    gm_handle *H = new gm_handle();
-    H->n = n;
-    H->leaf = leaf;
-    H->precision = o.precision;
-    int rc;
-    if (o.precision == GM_PREC_MIXED) {
-        if (o.pivoting < GM_PIVOT_AUTO || o.pivoting > GM_PIVOT_PARTIAL) {
-            delete H;
-            return GM_EINVAL;
-        }
-        int growth = 0;
-        rc = build_impl_mixed(o, b, c, d, n, leaf, H, &growth);
-        if (o.pivoting == GM_PIVOT_AUTO && (growth || rc == GM_ESINGULAR)) {
-            // block pivoting was not safe for this operator: redo with partial pivoting
-            gm_free(H);
-            H = new gm_handle();
-            H->n = n;
-            H->leaf = leaf;
-            H->precision = o.precision;
-            gm_opts o2 = o;
-            o2.pivoting = GM_PIVOT_PARTIAL;
-            rc = build_impl_mixed(o2, b, c, d, n, leaf, H, &growth);
-            H->info.pivot_fallback = 1;
-        }
-    } else {
-        rc = build_impl(o, b, c, d, n, leaf, H);
-        H->info.pivoting = GM_PIVOT_PARTIAL;
+    int rc = check_opts(opts, o);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)o.stream;
+    // coefficients on the device (device pointers are used in place)
+    DBuf coef;
+    const double *db = b, *dc = c, *dd = d;
+    const size_t N2 = (size_t)n * n;
+    if (!is_device_ptr(b) || !is_device_ptr(c) || !is_device_ptr(d)) {
+        if ((rc = coef.alloc(3 * N2 * sizeof(double), s))) return rc;
+        double *base = coef.as<double>();
+        CK(cudaMemcpyAsync(base, b, N2 * 8, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(base + N2, c, N2 * 8, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(base + 2 * N2, d, N2 * 8, cudaMemcpyDefault, s));
+        db = base;
+        dc = base + N2;
+        dd = base + 2 * N2;
     }
-    H->info.n = n;
-    H->info.leaf = leaf;
-    H->info.levels = H->L;
-    H->info.precision = o.precision;
-    H->info.dtn_bytes = (long long)16 * n * n * 8;
-    if (rc) {
-        cudaGetLastError();
-        gm_free(H);
-        return rc;
+    std::vector<gm_handle *> H;
+    rc = build_with_fallback(o, {{n, leaf}}, db, dc, dd, H);
+    if (rc) return rc;
+    *out = H[0];
+    return GM_OK;
+}
+
+int gm_build_batch(int count, const gm_problem *probs, const gm_opts *opts, double tol, gm_handle **outs) {
+    if (count <= 0 || !probs || !outs || tol < 0) return GM_EINVAL;
+    for (int i = 0; i < count; ++i) outs[i] = nullptr;
+    if (tol != 0.0) return GM_EUNSUPPORTED;
+    std::vector<std::pair<int, int>> key;
+    int64_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        const gm_problem &p = probs[i];
+        if (!p.b || !p.c || !p.d || p.n < 2 || p.leaf < 4) return GM_EINVAL;
+        key.push_back({p.n, p.leaf});
+        total += (int64_t)p.n * p.n;
     }
-    *out = H;
+    gm_opts o;
+    int rc = check_opts(opts, o);
+    if (rc) return rc;
+    if (o.keep_levels) return GM_EUNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)o.stream;
+    // every problem's coefficients, concatenated in batch order
+    DBuf coef;
+    if ((rc = coef.alloc(3 * (size_t)total * sizeof(double), s))) return rc;
+    double *db = coef.as<double>(), *dc = db + total, *dd = dc + total;
+    int64_t off = 0;
+    for (int i = 0; i < count; ++i) {
+        const size_t bytes = (size_t)probs[i].n * probs[i].n * 8;
+        CK(cudaMemcpyAsync(db + off, probs[i].b, bytes, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(dc + off, probs[i].c, bytes, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(dd + off, probs[i].d, bytes, cudaMemcpyDefault, s));
+        off += (int64_t)probs[i].n * probs[i].n;
+    }
+    std::vector<gm_handle *> H;
+    rc = build_with_fallback(o, key, db, dc, dd, H);
+    if (rc) return rc;
+    for (int i = 0; i < count; ++i) outs[i] = H[i];
     return GM_OK;
 }
 

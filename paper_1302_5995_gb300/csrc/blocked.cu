@@ -35,7 +35,7 @@ constexpr int LDF = NBK + 1;  // padded row length of the df32 shared tiles
 
 // ----------------------------------------------------------------------------- factor
 
-constexpr int FAC_THREADS = 512;
+constexpr int FAC_THREADS = 1024;
 
 template <int S>
 __global__ void __launch_bounds__(FAC_THREADS)
@@ -100,9 +100,15 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
         if (tid < 128) prow[tid] = Aug[p * 129 + tid] * ipv;
         else if (tid < 192) fcol[tid - 128] = Aug[(tid - 128) * 129 + t];
         __syncthreads();
-        for (int e = tid; e < 64 * 128; e += nt) {
-            const int r = e >> 7, c = e & 127;
-            Aug[r * 129 + c] = (r == p) ? prow[c] : Aug[r * 129 + c] - fcol[r] * prow[c];
+        {  // thread owns column c, rows r = g, g + G, ...; eliminated columns (c <= t) stay
+            const int c = tid & 127, G = nt >> 7;
+            if (c > t || c >= 64) {
+                const float pc = prow[c];
+                for (int r = tid >> 7; r < 64; r += G)
+                    Aug[r * 129 + c] = (r == p) ? pc : Aug[r * 129 + c] - fcol[r] * pc;
+            } else if (c == t) {
+                for (int r = tid >> 7; r < 64; r += G) Aug[r * 129 + c] = (r == p) ? 1.f : 0.f;
+            }
         }
         __syncthreads();
     }

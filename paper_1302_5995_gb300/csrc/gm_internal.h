@@ -30,18 +30,24 @@ enum { DIR_C = 0, DIR_E = 1, DIR_W = 2, DIR_N = 3, DIR_S = 4 };
 // One leaf elimination.
 struct LeafDesc {
     int x0, y0, a, b;
-    int64_t off;  // S offset (doubles) in the output arena, column-major r x r
+    int64_t off;   // S offset (doubles) in the output arena, column-major r x r
+    int n;         // grid size of the leaf's problem (h = 1/(n+1))
+    int pad;
+    int64_t coef;  // offset of the problem's coefficients in the b, c, d arrays
 };
 
 // One pairwise merge (eq. S_fromtwo_nd).  Child 1 is west/south, child 2 east/north.
+// All Schur complements of a build live in one arena; offsets are absolute in it.
 struct MergeDesc {
-    int64_t s1, s2;  // child Schur complements (input arena offsets)
-    int64_t out;     // parent Schur complement (output arena offset)
+    int64_t s1, s2;  // child Schur complements (arena offsets)
+    int64_t out;     // parent Schur complement (arena offset)
     int64_t ws;      // dense system [M | Z] (workspace offset), column-major, ld = 2*sp
     int r1, r2, rp;  // ring sizes
     int sp;          // |P3| = |P4| (interface nodes of each child)
     int n1, n2;      // |P1|, |P2|; n1 + n2 = rp
     int orient;      // 0: child 2 east of child 1; 1: child 2 north of child 1
+    int n;           // grid size of the merge's problem (h = 1/(n+1)); the table's global
+                     // node indices already include the problem's coefficient offset
     int tab;         // offset of this merge's index table (ints)
     int kpad;        // 2*sp rounded up to 16 (row length of this merge's digit planes)
     int eoff;        // first row of this merge in the stage's exponent vectors (prefix of rp)
@@ -79,23 +85,39 @@ struct Stage {
     std::vector<MergeDesc> merges;
     std::vector<int> table;
     std::vector<Box> in_boxes, out_boxes;  // per merge: child1, child2 / parent
-    int64_t in_doubles, out_doubles, ws_doubles;
+    int64_t out_base;     // first arena element of this stage's outputs
+    int64_t out_doubles;  // arena elements written by this stage
+    int64_t ws_doubles;   // workspace elements of this stage
     int64_t dig_elems;  // elements of one digit plane of the stage (sum of rp * kpad)
     int64_t exp_elems;  // rows of the stage's exponent vectors (sum of rp)
     int max_m, max_ncol, max_rp;
 };
 
+// Root of one problem of a (possibly batched) plan.
+struct RootDesc {
+    int n, r;        // grid size, root ring size 4n - 4
+    int64_t off;     // S_root offset in the last level's arena
+    int64_t coef;    // offset of the problem's coefficients
+    int problem;     // index in the batch
+};
+
 struct Plan {
     int n, leaf, L;
+    std::vector<RootDesc> roots;
     std::vector<LeafDesc> leaves;
     std::vector<Box> leaf_boxes;
-    int64_t leaf_doubles;
+    int64_t leaf_doubles;   // leaves occupy arena elements [0, leaf_doubles)
+    int64_t arena_doubles;  // every Schur complement of the build
+    int64_t coef_total;     // length of each of the b, c, d arrays (all problems)
     std::vector<Stage> stages;  // 2 per level, finest first: H(L), V(L), H(L-1), ...
     Box root;
     int r_root;
 };
 
 int build_plan(int n, int leaf, Plan &plan);
+// Concatenate the plans of several problems; stages are aligned from the root, so a
+// problem with fewer levels has no merges in the finest stages of the batch.
+int build_batch_plan(const std::vector<const Plan *> &plans, const std::vector<int64_t> &coef_off, Plan &out);
 
 // The dense DtN matrix of a handle and its grid size (nullptr for a NULL handle).
 const double *handle_dtn(gm_handle *h, int *n);

@@ -63,8 +63,8 @@ struct KTimer {
 size_t leaf_smem_bytes(int a, int b);
 
 cudaError_t launch_leaf(const LeafDesc *d_leaves, const std::vector<LeafDesc> &h_leaves, int max_a, int max_b,
-                        const double *b, const double *c, const double *d, int n, double *out, Status *st,
-                        int stage, cudaStream_t s, KTimer &kt);
+                        const double *b, const double *c, const double *d, double *out, Status *st, int stage,
+                        cudaStream_t s, KTimer &kt);
 cudaError_t launch_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys, int max_m, int max_ncol,
                             double *ws, int nb, int *piv, int piv_ld, double *u12, int64_t u12_stride, Status *st,
                             int stage, cudaStream_t s, KTimer &kt);

@@ -23,14 +23,15 @@ namespace gm {
 
 // Weight of the equation at global node g on its neighbour in direction dir (Section 6).
 __device__ __forceinline__ double stencil_w(const double *__restrict__ b, const double *__restrict__ c,
-                                            const double *__restrict__ d, double h, int g, int dir) {
-    double ih2 = 1.0 / (h * h);
+                                            const double *__restrict__ d, double ih, int g, int dir) {
+    // ih = 1/h = n+1 exactly: no FP64 division (a long instruction sequence on GB300)
+    const double ih2 = ih * ih;
     switch (dir) {
     case DIR_C: return 4.0 * ih2 + d[g];
-    case DIR_E: return -ih2 + b[g] / h;
-    case DIR_W: return -ih2 - b[g] / h;
-    case DIR_N: return -ih2 + c[g] / h;
-    default: return -ih2 - c[g] / h;
+    case DIR_E: return -ih2 + b[g] * ih;
+    case DIR_W: return -ih2 - b[g] * ih;
+    case DIR_N: return -ih2 + c[g] * ih;
+    default: return -ih2 - c[g] * ih;
     }
 }
 
@@ -65,16 +66,18 @@ __device__ __forceinline__ void record_pivot(Status *st, double piv, int stage) 
 // unit right-hand sides are the interior nodes next to the ring, because A_ib and
 // A_bi couple each non-corner ring node to exactly one interior node.
 __global__ void __launch_bounds__(LEAF_THREADS)
-k_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf, const double *__restrict__ cf,
-       const double *__restrict__ df, int n, double *__restrict__ out, Status *st, int stage) {
+k_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf0, const double *__restrict__ cf0,
+       const double *__restrict__ df0, double *__restrict__ out, Status *st, int stage) {
     extern __shared__ double sm[];
     const LeafDesc Ld = leaves[blockIdx.x];
+    const int n = Ld.n;
+    const double *bf = bf0 + Ld.coef, *cf = cf0 + Ld.coef, *df = df0 + Ld.coef;
     const int a = Ld.a, bb = Ld.b;
     const int ia = a - 2, ib = bb - 2;
     const int ni = (ia > 0 && ib > 0) ? ia * ib : 0;
     const int r = 2 * a + 2 * bb - 4;
     const int KL = ia, UW = 2 * ia, W = 3 * ia + 1;
-    const double h = 1.0 / (n + 1);
+    const double ih = n + 1.0;  // 1/h
     const int tid = threadIdx.x, nt = blockDim.x;
 
     // inner-ring interior nodes (those with a ring neighbour)
@@ -96,11 +99,11 @@ k_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf, const
             int ii = q % ia, jj = q / ia;
             int g = gnode(ii, jj);
             double *row = band + (size_t)q * W + KL - q;  // row[col] for col in band
-            row[q] = stencil_w(bf, cf, df, h, g, DIR_C);
-            if (ii + 1 < ia) row[q + 1] = stencil_w(bf, cf, df, h, g, DIR_E);
-            if (ii > 0) row[q - 1] = stencil_w(bf, cf, df, h, g, DIR_W);
-            if (jj + 1 < ib) row[q + ia] = stencil_w(bf, cf, df, h, g, DIR_N);
-            if (jj > 0) row[q - ia] = stencil_w(bf, cf, df, h, g, DIR_S);
+            row[q] = stencil_w(bf, cf, df, ih, g, DIR_C);
+            if (ii + 1 < ia) row[q + 1] = stencil_w(bf, cf, df, ih, g, DIR_E);
+            if (ii > 0) row[q - 1] = stencil_w(bf, cf, df, ih, g, DIR_W);
+            if (jj + 1 < ib) row[q + ia] = stencil_w(bf, cf, df, ih, g, DIR_N);
+            if (jj > 0) row[q - ia] = stencil_w(bf, cf, df, ih, g, DIR_S);
             bool edge = (ii == 0 || ii == ia - 1 || jj == 0 || jj == ib - 1);
             inner_id[q] = edge ? 1 : -1;
         }
@@ -138,7 +141,8 @@ k_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf, const
             __syncthreads();
             const double pv = band[(size_t)k * W + KL];
             if (tid == 0) record_pivot(st, pv, stage);
-            for (int rr = k + 1 + tid; rr <= last; rr += nt) band[(size_t)rr * W + KL + k - rr] /= pv;
+            const double ipv = 1.0 / pv;
+            for (int rr = k + 1 + tid; rr <= last; rr += nt) band[(size_t)rr * W + KL + k - rr] *= ipv;
             __syncthreads();
             const int nr = last - k, ncn = cend - k;
             for (int e = tid; e < nr * ncn; e += nt) {
@@ -147,29 +151,45 @@ k_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf, const
             }
             __syncthreads();
         }
-        // one unit right-hand side per inner-ring node; thread t owns column t
-        for (int t = tid; t < nq; t += nt) {
-            for (int q = 0; q < ni; ++q) X[(size_t)q * nq + t] = 0.0;
-            X[(size_t)inner_q[t] * nq + t] = 1.0;
-            for (int k = 0; k < ni; ++k) {
-                int p = piv[k];
-                double xk = X[(size_t)p * nq + t];
-                if (p != k) { X[(size_t)p * nq + t] = X[(size_t)k * nq + t]; X[(size_t)k * nq + t] = xk; }
-                if (xk != 0.0) {
-                    int last = min(k + KL, ni - 1);
-                    for (int rr = k + 1; rr <= last; ++rr)
+        // one unit right-hand side per inner-ring node (column t of X); both sweeps are
+        // column-oriented so that every step updates (row, right-hand side) pairs in parallel
+        for (int e = tid; e < ni * nq; e += nt) X[e] = 0.0;
+        __syncthreads();
+        for (int t = tid; t < nq; t += nt) X[(size_t)inner_q[t] * nq + t] = 1.0;
+        __syncthreads();
+        for (int k = 0; k < ni; ++k) {  // forward: interchange, then eliminate below row k
+            const int p = piv[k];
+            if (p != k)
+                for (int t = tid; t < nq; t += nt) {
+                    double a = X[(size_t)k * nq + t];
+                    X[(size_t)k * nq + t] = X[(size_t)p * nq + t];
+                    X[(size_t)p * nq + t] = a;
+                }
+            __syncthreads();
+            {  // thread -> right-hand side t = tid % 64, rows k+1+g, k+1+g+G, ...
+                const int t = tid & 63, g = tid >> 6, G = nt >> 6, last = min(k + KL, ni - 1);
+                if (t < nq) {
+                    const double xk = X[(size_t)k * nq + t];
+                    for (int rr = k + 1 + g; rr <= last; rr += G)
                         X[(size_t)rr * nq + t] -= band[(size_t)rr * W + KL + k - rr] * xk;
                 }
             }
-            for (int k = ni - 1; k >= 0; --k) {
-                int cend = min(k + UW, ni - 1);
-                double s = X[(size_t)k * nq + t];
-                const double *row = band + (size_t)k * W + KL - k;
-                for (int cc = k + 1; cc <= cend; ++cc) s -= row[cc] * X[(size_t)cc * nq + t];
-                X[(size_t)k * nq + t] = s / row[k];
-            }
+            __syncthreads();
         }
-        __syncthreads();
+        for (int k = ni - 1; k >= 0; --k) {  // backward: divide row k, eliminate above it
+            const double iukk = 1.0 / band[(size_t)k * W + KL];
+            for (int t = tid; t < nq; t += nt) X[(size_t)k * nq + t] *= iukk;
+            __syncthreads();
+            {
+                const int t = tid & 63, g = tid >> 6, G = nt >> 6, r0 = max(0, k - UW);
+                if (t < nq) {
+                    const double xk = X[(size_t)k * nq + t];
+                    for (int rr = r0 + g; rr < k; rr += G)
+                        X[(size_t)rr * nq + t] -= band[(size_t)rr * W + KL + k - rr] * xk;
+                }
+            }
+            __syncthreads();
+        }
     }
     // S[l, m] = A_bb[l, m] - w(l -> ql) (A_ii^{-1})[ql, qm] w(qm -> m)
     double *S = out + Ld.off;
@@ -181,11 +201,11 @@ k_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf, const
         int gl = (Ld.x0 + il) + n * (Ld.y0 + jl);
         double v = 0.0;
         int dx = im - il, dy = jm - jl;
-        if (dx == 0 && dy == 0) v = stencil_w(bf, cf, df, h, gl, DIR_C);
-        else if (dx == 1 && dy == 0) v = stencil_w(bf, cf, df, h, gl, DIR_E);
-        else if (dx == -1 && dy == 0) v = stencil_w(bf, cf, df, h, gl, DIR_W);
-        else if (dx == 0 && dy == 1) v = stencil_w(bf, cf, df, h, gl, DIR_N);
-        else if (dx == 0 && dy == -1) v = stencil_w(bf, cf, df, h, gl, DIR_S);
+        if (dx == 0 && dy == 0) v = stencil_w(bf, cf, df, ih, gl, DIR_C);
+        else if (dx == 1 && dy == 0) v = stencil_w(bf, cf, df, ih, gl, DIR_E);
+        else if (dx == -1 && dy == 0) v = stencil_w(bf, cf, df, ih, gl, DIR_W);
+        else if (dx == 0 && dy == 1) v = stencil_w(bf, cf, df, ih, gl, DIR_N);
+        else if (dx == 0 && dy == -1) v = stencil_w(bf, cf, df, ih, gl, DIR_S);
         if (ni > 0) {
             // interior neighbour of a non-corner ring node, and the direction to it
             auto inner = [&](int i, int j, int &ii, int &jj, int &dir) -> bool {
@@ -201,8 +221,8 @@ k_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf, const
                 int gm_ = gnode(im2, jm2);
                 // direction from the interior node qm back to ring node m is opposite of dm
                 int back = (dm == DIR_N) ? DIR_S : (dm == DIR_S) ? DIR_N : (dm == DIR_E) ? DIR_W : DIR_E;
-                double wl = stencil_w(bf, cf, df, h, gl, dl);
-                double wm = stencil_w(bf, cf, df, h, gm_, back);
+                double wl = stencil_w(bf, cf, df, ih, gl, dl);
+                double wm = stencil_w(bf, cf, df, ih, gm_, back);
                 v -= wl * X[(size_t)ql * nq + inner_id[qm]] * wm;
             }
         }
@@ -447,7 +467,7 @@ k_merge_assemble(const MergeDesc *__restrict__ md, const int *__restrict__ tab, 
     const int64_t tot = (int64_t)mm * ncol;
     const double *S1 = in + M.s1, *S2 = in + M.s2;
     double *A = ws + M.ws;
-    const double h = 1.0 / (n + 1);
+    const double ih = M.n + 1.0;  // 1/h of the merge's problem
     const int d34 = M.orient ? DIR_N : DIR_E, d43 = M.orient ? DIR_S : DIR_W;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
         int t = (int)(e % mm), c = (int)(e / mm);
@@ -455,8 +475,8 @@ k_merge_assemble(const MergeDesc *__restrict__ md, const int *__restrict__ tab, 
         if (c < mm) {
             if (t < sp && c < sp) v = S1[T.p3[t] + (int64_t)M.r1 * T.p3[c]];
             else if (t >= sp && c >= sp) v = S2[T.p4[t - sp] + (int64_t)M.r2 * T.p4[c - sp]];
-            else if (t < sp) v = (c - sp == t) ? stencil_w(bf, cf, df, h, T.g3[t], d34) : 0.0;
-            else v = (c == t - sp) ? stencil_w(bf, cf, df, h, T.g4[t - sp], d43) : 0.0;
+            else if (t < sp) v = (c - sp == t) ? stencil_w(bf, cf, df, ih, T.g3[t], d34) : 0.0;
+            else v = (c == t - sp) ? stencil_w(bf, cf, df, ih, T.g4[t - sp], d43) : 0.0;
         } else {
             int cc = c - mm;
             if (cc < M.n1) v = (t < sp) ? S1[T.p3[t] + (int64_t)M.r1 * T.p1[cc]] : 0.0;
@@ -516,7 +536,7 @@ k_merge_update(const MergeDesc *__restrict__ md, const int *__restrict__ tab, co
         }
         __syncthreads();
     }
-    const double h = 1.0 / (n + 1);
+    const double ih = M.n + 1.0;  // 1/h of the merge's problem
     const int d12 = M.orient ? DIR_N : DIR_E, d21 = M.orient ? DIR_S : DIR_W;
     double *O = out + M.out;
 #pragma unroll
@@ -535,8 +555,8 @@ k_merge_update(const MergeDesc *__restrict__ md, const int *__restrict__ tab, co
             else {
                 for (int e = 0; e < 2; ++e) {
                     const int *x = T.x12 + 4 * e;
-                    if (aa < n1 && aa == x[0] && cc - n1 == x[1]) cval = stencil_w(bf, cf, df, h, x[2], d12);
-                    if (aa >= n1 && aa - n1 == x[1] && cc == x[0]) cval = stencil_w(bf, cf, df, h, x[3], d21);
+                    if (aa < n1 && aa == x[0] && cc - n1 == x[1]) cval = stencil_w(bf, cf, df, ih, x[2], d12);
+                    if (aa >= n1 && aa - n1 == x[1] && cc == x[0]) cval = stencil_w(bf, cf, df, ih, x[3], d21);
                 }
             }
             O[qa + (int64_t)rp * qc] = cval - acc[q][p];
@@ -567,7 +587,7 @@ __global__ void k_root_assemble(const double *__restrict__ S, int r, int n, doub
                                 const double *__restrict__ bf, const double *__restrict__ cf,
                                 const double *__restrict__ df) {
     const int64_t tot = (int64_t)r * (r + 4 * n);
-    const double h = 1.0 / (n + 1);
+    const double ih = n + 1.0;  // 1/h
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
         int row = (int)(e % r), c = (int)(e / r);
         double v;
@@ -575,7 +595,7 @@ __global__ void k_root_assemble(const double *__restrict__ S, int r, int n, doub
         else {
             int k = c - r, g, dir;
             ghost_nb(n, k, g, dir);
-            v = (row == ghost_ring(n, k)) ? -stencil_w(bf, cf, df, h, g, dir) : 0.0;
+            v = (row == ghost_ring(n, k)) ? -stencil_w(bf, cf, df, ih, g, dir) : 0.0;
         }
         ws[e] = v;
     }
@@ -585,12 +605,12 @@ __global__ void k_root_assemble(const double *__restrict__ S, int r, int n, doub
 __global__ void k_root_finalize(const double *__restrict__ ws, int r, int n, double *__restrict__ T) {
     const int nb4 = 4 * n;
     const int64_t tot = (int64_t)nb4 * nb4;
-    const double h = 1.0 / (n + 1);
+    const double ih = n + 1.0;  // 1/h
     const double *X = ws + (size_t)r * r;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
         int k = (int)(e % nb4), kp = (int)(e / nb4);
         double x = X[(size_t)kp * r + ghost_ring(n, k)];
-        T[e] = ((k == kp ? 1.0 : 0.0) - x) / h;
+        T[e] = ((k == kp ? 1.0 : 0.0) - x) * ih;
     }
 }
 
@@ -640,13 +660,12 @@ k_apply(const double *__restrict__ T, const double *__restrict__ G, double *__re
 // ----------------------------------------------------------------------------- launchers
 
 cudaError_t launch_leaf(const LeafDesc *d_leaves, const std::vector<LeafDesc> &h_leaves, int max_a, int max_b,
-                        const double *b, const double *c, const double *d, int n, double *out, Status *st,
-                        int stage, cudaStream_t s, KTimer &kt) {
+                        const double *b, const double *c, const double *d, double *out, Status *st, int stage,
+                        cudaStream_t s, KTimer &kt) {
     size_t smem = leaf_smem_bytes(max_a, max_b);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    // always raise the limit: the default 48 KiB counts static shared memory too
+    cudaError_t e = cudaFuncSetAttribute(k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     // banded LU ~ 4 ni ia^2, one forward + backward solve per inner-ring node ~ 6 ni ia
     double fl = 0.0;
     for (const LeafDesc &L : h_leaves) {
@@ -656,7 +675,7 @@ cudaError_t launch_leaf(const LeafDesc *d_leaves, const std::vector<LeafDesc> &h
         fl += 4.0 * ni * ia * ia + 6.0 * nq * ni * ia;
     }
     kt.begin(GM_K_LEAF, fl, s);
-    k_leaf<<<(int)h_leaves.size(), LEAF_THREADS, smem, s>>>(d_leaves, b, c, d, n, out, st, stage);
+    k_leaf<<<(int)h_leaves.size(), LEAF_THREADS, smem, s>>>(d_leaves, b, c, d, out, st, stage);
     kt.end(s);
     return cudaGetLastError();
 }
@@ -666,6 +685,12 @@ cudaError_t launch_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_
                             int stage, cudaStream_t s, KTimer &kt) {
     const int smem_limit = 200 * 1024;
     const int nsys = (int)h_sys.size();
+    // the panel of the first step is the largest; the default 48 KiB limit counts the
+    // kernel's static shared memory too, so the limit is raised whatever the size
+    {
+        cudaError_t e = cudaFuncSetAttribute(k_gj_panel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
+        if (e != cudaSuccess) return e;
+    }
     for (int k = 0; k < max_m; k += nb) {
         int rows = max_m - k;
         int nbe = nb < rows ? nb : rows;
@@ -680,11 +705,6 @@ cudaError_t launch_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_
         size_t smem = (size_t)rows * nbe * sizeof(double);
         kt.begin(GM_K_PANEL, fl_panel, s);
         if (smem <= (size_t)smem_limit) {
-            if (smem > 48 * 1024) {
-                cudaError_t e = cudaFuncSetAttribute(k_gj_panel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     smem_limit);
-                if (e != cudaSuccess) return e;
-            }
             k_gj_panel<true><<<nsys, GJ_PANEL_THREADS, smem, s>>>(d_sys, ws, k, nb, piv, piv_ld, st, stage);
         } else {
             k_gj_panel<false><<<nsys, GJ_PANEL_THREADS, 0, s>>>(d_sys, ws, k, nb, piv, piv_ld, st, stage);

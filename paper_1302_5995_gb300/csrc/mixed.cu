@@ -60,7 +60,7 @@ k_mx_merge_assemble(const MergeDesc *__restrict__ md, const int *__restrict__ ta
     const int64_t tot = (int64_t)mm * ncol;
     const float2 *S1 = in + M.s1, *S2 = in + M.s2;
     float2 *A = ws + M.ws;
-    const double h = 1.0 / (n + 1);
+    const double ih = M.n + 1.0;  // 1/h of the merge's problem
     const int d34 = M.orient ? DIR_N : DIR_E, d43 = M.orient ? DIR_S : DIR_W;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
         int t = (int)(e % mm), c = (int)(e / mm);
@@ -68,8 +68,8 @@ k_mx_merge_assemble(const MergeDesc *__restrict__ md, const int *__restrict__ ta
         if (c < mm) {
             if (t < sp && c < sp) v = S1[T.p3[t] + (int64_t)M.r1 * T.p3[c]];
             else if (t >= sp && c >= sp) v = S2[T.p4[t - sp] + (int64_t)M.r2 * T.p4[c - sp]];
-            else if (t < sp) { if (c - sp == t) v = df_from_d(stencil_w_mx(bf, cf, df, h, T.g3[t], d34)); }
-            else if (c == t - sp) v = df_from_d(stencil_w_mx(bf, cf, df, h, T.g4[t - sp], d43));
+            else if (t < sp) { if (c - sp == t) v = df_from_d(stencil_w_mx(bf, cf, df, ih, T.g3[t], d34)); }
+            else if (c == t - sp) v = df_from_d(stencil_w_mx(bf, cf, df, ih, T.g4[t - sp], d43));
         } else {
             int cc = c - mm;
             if (cc < M.n1) { if (t < sp) v = S1[T.p3[t] + (int64_t)M.r1 * T.p1[cc]]; }
@@ -400,7 +400,7 @@ k_mx_merge_update(const MergeDesc *__restrict__ md, const int *__restrict__ tab,
     const int64_t eo = M.eoff;
     digit_gemm_tile<S>(ydig + M.doff, plane, M.kpad, a0, rp, yex + eo, xdig + M.doff, plane, M.kpad, c0, rp, xex + eo,
                        2 * M.sp, As, Bs, res);
-    const double h = 1.0 / (n + 1);
+    const double ih = M.n + 1.0;  // 1/h of the merge's problem
     const int d12 = M.orient ? DIR_N : DIR_E, d21 = M.orient ? DIR_S : DIR_W;
     float2 *O = out + M.out;
     const int warp = threadIdx.x >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
@@ -423,9 +423,9 @@ k_mx_merge_update(const MergeDesc *__restrict__ md, const int *__restrict__ tab,
                     for (int e = 0; e < 2; ++e) {
                         const int *x = T.x12 + 4 * e;
                         if (aa < n1 && aa == x[0] && cc - n1 == x[1])
-                            cval = df_from_d(stencil_w_mx(bf, cf, df, h, x[2], d12));
+                            cval = df_from_d(stencil_w_mx(bf, cf, df, ih, x[2], d12));
                         if (aa >= n1 && aa - n1 == x[1] && cc == x[0])
-                            cval = df_from_d(stencil_w_mx(bf, cf, df, h, x[3], d21));
+                            cval = df_from_d(stencil_w_mx(bf, cf, df, ih, x[3], d21));
                     }
                 }
                 O[qa + (int64_t)rp * qc] = df_sub(cval, res[mt][nt][c]);
@@ -451,7 +451,7 @@ __global__ void k_mx_root_assemble(const float2 *__restrict__ S, int r, int n, f
                                    const double *__restrict__ bf, const double *__restrict__ cf,
                                    const double *__restrict__ df) {
     const int64_t tot = (int64_t)r * (r + 4 * n);
-    const double h = 1.0 / (n + 1);
+    const double ih = n + 1.0;  // 1/h
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
         int row = (int)(e % r), c = (int)(e / r);
         float2 v = make_float2(0.f, 0.f);
@@ -459,7 +459,7 @@ __global__ void k_mx_root_assemble(const float2 *__restrict__ S, int r, int n, f
         else {
             int k = c - r, g, dir;
             ghost_nb_mx(n, k, g, dir);
-            if (row == ghost_ring_mx(n, k)) v = df_from_d(-stencil_w_mx(bf, cf, df, h, g, dir));
+            if (row == ghost_ring_mx(n, k)) v = df_from_d(-stencil_w_mx(bf, cf, df, ih, g, dir));
         }
         ws[e] = v;
     }
@@ -569,6 +569,12 @@ cudaError_t mx_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys,
                         KTimer &kt) {
     const int smem_limit = 200 * 1024;
     const int nsys = (int)h_sys.size();
+    // the default 48 KiB limit counts the kernel's static shared memory (about 5 KiB)
+    // too, so the limit is raised whatever the panel size
+    {
+        cudaError_t e = cudaFuncSetAttribute(k_mx_gj_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
+        if (e != cudaSuccess) return e;
+    }
     for (int k = 0; k < max_m; k += nb) {
         int rows = max_m - k;
         int nbe = nb < rows ? nb : rows;
@@ -582,10 +588,6 @@ cudaError_t mx_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys,
         }
         size_t smem = (size_t)rows * nbe * sizeof(float);
         if (smem > (size_t)smem_limit) return cudaErrorInvalidValue;
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k_mx_gj_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
-            if (e != cudaSuccess) return e;
-        }
         kt.begin(GM_K_PANEL, fl_panel, s);
         k_mx_gj_panel<<<nsys, MX_PANEL_THREADS, smem, s>>>(d_sys, ws, k, nb, scr.perm, scr.perm_n, scr.a11inv, st,
                                                            stage);

@@ -149,14 +149,15 @@ __device__ __forceinline__ void acc_pos(int mt, int nt, int c, int &r, int &col)
 // ----------------------------------------------------------------------------- stencil
 
 __device__ __forceinline__ double stencil_w_mx(const double *__restrict__ b, const double *__restrict__ c,
-                                               const double *__restrict__ d, double h, int g, int dir) {
-    double ih2 = 1.0 / (h * h);
+                                               const double *__restrict__ d, double ih, int g, int dir) {
+    // ih = 1/h = n+1 exactly: no FP64 division (a long instruction sequence on GB300)
+    const double ih2 = ih * ih;
     switch (dir) {
     case DIR_C: return 4.0 * ih2 + d[g];
-    case DIR_E: return -ih2 + b[g] / h;
-    case DIR_W: return -ih2 - b[g] / h;
-    case DIR_N: return -ih2 + c[g] / h;
-    default: return -ih2 - c[g] / h;
+    case DIR_E: return -ih2 + b[g] * ih;
+    case DIR_W: return -ih2 - b[g] * ih;
+    case DIR_N: return -ih2 + c[g] * ih;
+    default: return -ih2 - c[g] * ih;
     }
 }
 

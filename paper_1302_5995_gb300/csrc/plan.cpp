@@ -39,6 +39,7 @@ void add_merge(Stage &st, int n, const Box &c1, int64_t s1, const Box &c2, int64
     m.r2 = ring_size(c2.a, c2.b);
     m.rp = ring_size(par.a, par.b);
     m.orient = st.orient;
+    m.n = n;
     std::vector<int> p3, p4, g3, g4, p1, q1, p2, q2;
     auto gidx = [n](int x, int y) { return x + n * y; };
     if (st.orient == 0) {  // shared vertical edge: child 1's east column, child 2's west column
@@ -138,7 +139,7 @@ int build_plan(int n, int leaf, Plan &plan) {
     int64_t acc = 0;
     for (const Box &b : levels[plan.L]) {
         if (b.a < 2 || b.b < 2) return GM_EINVAL;
-        LeafDesc d{b.x0, b.y0, b.a, b.b, acc};
+        LeafDesc d{b.x0, b.y0, b.a, b.b, acc, n, 0, 0};
         off[key(b)] = acc;
         int r = ring_size(b.a, b.b);
         acc += (int64_t)r * r;
@@ -146,13 +147,15 @@ int build_plan(int n, int leaf, Plan &plan) {
         plan.leaf_boxes.push_back(b);
     }
     plan.leaf_doubles = acc;
-    // merge stages, finest level first; per level: horizontal, then vertical
+    // merge stages, finest level first; per level: horizontal, then vertical.  Each stage
+    // writes the next region of the single arena.
+    int64_t base = acc;
     for (int l = plan.L; l >= 1; --l) {
         Stage H{}, V{};
         H.orient = 0;
         V.orient = 1;
         std::map<Key, int64_t> half_off, par_off;
-        int64_t hacc = 0, hws = 0, pacc = 0, vws = 0;
+        int64_t hacc = base, hws = 0, vws = 0;
         for (const Box &p : levels[l - 1]) {
             Box c[4];
             children(p, c);
@@ -163,42 +166,163 @@ int build_plan(int n, int leaf, Plan &plan) {
             half_off[key(north)] = hacc;
             add_merge(H, n, c[2], off.at(key(c[2])), c[3], off.at(key(c[3])), north, hacc, hws);
             hacc += (int64_t)ring_size(north.a, north.b) * ring_size(north.a, north.b);
+        }
+        int64_t pacc = hacc;
+        for (const Box &p : levels[l - 1]) {
+            Box c[4];
+            children(p, c);
+            Box south{p.x0, p.y0, p.a, c[0].b}, north{p.x0, p.y0 + c[0].b, p.a, c[2].b};
             par_off[key(p)] = pacc;
             add_merge(V, n, south, half_off.at(key(south)), north, half_off.at(key(north)), p, pacc, vws);
             pacc += (int64_t)ring_size(p.a, p.b) * ring_size(p.a, p.b);
         }
-        H.in_doubles = acc;
-        H.out_doubles = hacc;
+        H.out_base = base;
+        H.out_doubles = hacc - base;
         H.ws_doubles = hws;
-        V.in_doubles = hacc;
-        V.out_doubles = pacc;
+        V.out_base = hacc;
+        V.out_doubles = pacc - hacc;
         V.ws_doubles = vws;
         plan.stages.push_back(std::move(H));
         plan.stages.push_back(std::move(V));
         off = par_off;
-        acc = pacc;
+        base = pacc;
     }
+    plan.arena_doubles = base;
+    plan.coef_total = (int64_t)n * n;
     plan.root = {0, 0, n, n};
     plan.r_root = ring_size(n, n);
+    plan.roots.push_back(RootDesc{n, plan.r_root, off.at(key(plan.root)), 0, 0});
     return validate_plan(plan);
+}
+
+int build_batch_plan(const std::vector<const Plan *> &plans, const std::vector<int64_t> &coef_off, Plan &out) {
+    out = Plan{};
+    if (plans.empty() || plans.size() != coef_off.size()) return GM_EINVAL;
+    int Lmax = 0;
+    for (const Plan *p : plans) Lmax = std::max(Lmax, p->L);
+    const int NS = 2 * Lmax;
+    out.n = plans[0]->n;
+    out.leaf = plans[0]->leaf;
+    out.L = Lmax;
+    out.stages.resize(NS);
+    for (int s = 0; s < NS; ++s) out.stages[s].orient = s % 2;
+    // global layout: all leaves, then aligned stage 0 of all problems, stage 1, ...
+    int64_t leaves_total = 0;
+    std::vector<int64_t> stage_total(NS, 0);
+    for (const Plan *p : plans) {
+        leaves_total += p->leaf_doubles;
+        const int shift = NS - 2 * p->L;
+        for (size_t si = 0; si < p->stages.size(); ++si) stage_total[shift + si] += p->stages[si].out_doubles;
+    }
+    std::vector<int64_t> stage_base(NS, 0);
+    int64_t acc = leaves_total;
+    for (int s = 0; s < NS; ++s) {
+        stage_base[s] = acc;
+        acc += stage_total[s];
+    }
+    out.arena_doubles = acc;
+    out.leaf_doubles = leaves_total;
+    out.coef_total = 0;
+    for (size_t pi = 0; pi < plans.size(); ++pi)
+        out.coef_total = std::max(out.coef_total, coef_off[pi] + (int64_t)plans[pi]->n * plans[pi]->n);
+    std::vector<int64_t> stage_fill(NS, 0), ws_fill(NS, 0);
+    int64_t leaf_fill = 0;
+    for (size_t pi = 0; pi < plans.size(); ++pi) {
+        const Plan &P = *plans[pi];
+        const int64_t co = coef_off[pi];
+        const int shift = NS - 2 * P.L;
+        // local arena regions of this problem and their global positions
+        std::vector<std::pair<int64_t, int64_t>> lo_hi;  // local [begin, end)
+        std::vector<int64_t> delta;
+        lo_hi.push_back({0, P.leaf_doubles});
+        delta.push_back(leaf_fill);
+        for (size_t si = 0; si < P.stages.size(); ++si) {
+            const Stage &st = P.stages[si];
+            lo_hi.push_back({st.out_base, st.out_base + st.out_doubles});
+            delta.push_back(stage_base[shift + si] + stage_fill[shift + si] - st.out_base);
+        }
+        auto remap = [&](int64_t x) -> int64_t {
+            for (size_t q = 0; q < lo_hi.size(); ++q)
+                if (x >= lo_hi[q].first && x < lo_hi[q].second) return x + delta[q];
+            return -1;
+        };
+        for (const LeafDesc &l : P.leaves) {
+            LeafDesc d = l;
+            d.off = remap(l.off);
+            d.coef = co;
+            out.leaves.push_back(d);
+        }
+        out.leaf_boxes.insert(out.leaf_boxes.end(), P.leaf_boxes.begin(), P.leaf_boxes.end());
+        for (size_t si = 0; si < P.stages.size(); ++si) {
+            const Stage &src = P.stages[si];
+            Stage &dst = out.stages[shift + si];
+            for (const MergeDesc &m0 : src.merges) {
+                MergeDesc m = m0;
+                m.s1 = remap(m0.s1);
+                m.s2 = remap(m0.s2);
+                m.out = remap(m0.out);
+                m.ws = m0.ws + ws_fill[shift + si];
+                m.doff = dst.dig_elems;
+                dst.dig_elems += (int64_t)m.rp * m.kpad;
+                m.eoff = (int)dst.exp_elems;
+                dst.exp_elems += m.rp;
+                const int *t = src.table.data() + m0.tab;
+                const int len = 4 * m.sp + 2 * m.n1 + 2 * m.n2 + 8;
+                std::vector<int> tab(t, t + len);
+                for (int q = 2 * m.sp; q < 4 * m.sp; ++q) tab[q] += (int)co;
+                int *x12 = tab.data() + 4 * m.sp + 2 * m.n1 + 2 * m.n2;
+                x12[2] += (int)co;
+                x12[3] += (int)co;
+                x12[6] += (int)co;
+                x12[7] += (int)co;
+                m.tab = (int)dst.table.size();
+                dst.table.insert(dst.table.end(), tab.begin(), tab.end());
+                dst.merges.push_back(m);
+                dst.max_m = std::max(dst.max_m, 2 * m.sp);
+                dst.max_ncol = std::max(dst.max_ncol, 2 * m.sp + m.rp);
+                dst.max_rp = std::max(dst.max_rp, m.rp);
+            }
+            dst.out_boxes.insert(dst.out_boxes.end(), src.out_boxes.begin(), src.out_boxes.end());
+            dst.in_boxes.insert(dst.in_boxes.end(), src.in_boxes.begin(), src.in_boxes.end());
+            stage_fill[shift + si] += src.out_doubles;
+            ws_fill[shift + si] += src.ws_doubles;
+        }
+        RootDesc rd = P.roots[0];
+        rd.off = remap(rd.off);
+        rd.coef = co;
+        rd.problem = (int)pi;
+        out.roots.push_back(rd);
+        leaf_fill += P.leaf_doubles;
+    }
+    for (int s = 0; s < NS; ++s) {
+        out.stages[s].out_base = stage_base[s];
+        out.stages[s].out_doubles = stage_total[s];
+        out.stages[s].ws_doubles = ws_fill[s];
+    }
+    out.r_root = 0;
+    for (const RootDesc &r : out.roots) out.r_root = std::max(out.r_root, r.r);
+    return validate_plan(out);
 }
 
 // Every gather/scatter index of every stage stays inside its matrix, the parent
 // positions of P1 and P2 form a permutation of the parent ring, and every S block lies
 // inside its arena.
 int validate_plan(const Plan &plan) {
-    int n = plan.n;
+    const int64_t NC = plan.coef_total;
+    if (plan.coef_total > 0x7fffffff) return GM_EUNSUPPORTED;  // node indices are 32-bit
+    for (const RootDesc &r : plan.roots)
+        if (r.off < 0 || r.off + (int64_t)r.r * r.r > plan.arena_doubles || r.r != 4 * r.n - 4) return GM_EINVAL;
     for (const LeafDesc &d : plan.leaves) {
         int r = ring_size(d.a, d.b);
         if (d.off < 0 || d.off + (int64_t)r * r > plan.leaf_doubles) return GM_EINVAL;
-        if (d.x0 < 0 || d.y0 < 0 || d.x0 + d.a > n || d.y0 + d.b > n) return GM_EINVAL;
+        if (d.x0 < 0 || d.y0 < 0 || d.x0 + d.a > d.n || d.y0 + d.b > d.n) return GM_EINVAL;
     }
     for (const Stage &st : plan.stages) {
         for (const MergeDesc &m : st.merges) {
             if (m.n1 + m.sp != m.r1 || m.n2 + m.sp != m.r2 || m.n1 + m.n2 != m.rp) return GM_EINVAL;
-            if (m.s1 < 0 || m.s1 + (int64_t)m.r1 * m.r1 > st.in_doubles) return GM_EINVAL;
-            if (m.s2 < 0 || m.s2 + (int64_t)m.r2 * m.r2 > st.in_doubles) return GM_EINVAL;
-            if (m.out < 0 || m.out + (int64_t)m.rp * m.rp > st.out_doubles) return GM_EINVAL;
+            if (m.s1 < 0 || m.s1 + (int64_t)m.r1 * m.r1 > st.out_base) return GM_EINVAL;
+            if (m.s2 < 0 || m.s2 + (int64_t)m.r2 * m.r2 > st.out_base) return GM_EINVAL;
+            if (m.out < st.out_base || m.out + (int64_t)m.rp * m.rp > st.out_base + st.out_doubles) return GM_EINVAL;
             int mm = 2 * m.sp;
             if (m.ws < 0 || m.ws + (int64_t)mm * (mm + m.rp) > st.ws_doubles) return GM_EINVAL;
             if (m.kpad < mm || m.kpad % 16 || m.doff < 0 || m.doff + (int64_t)m.rp * m.kpad > st.dig_elems) return GM_EINVAL;
@@ -210,7 +334,7 @@ int validate_plan(const Plan &plan) {
             const int *x12 = q2 + m.n2;
             for (int k = 0; k < m.sp; ++k) {
                 if (p3[k] < 0 || p3[k] >= m.r1 || p4[k] < 0 || p4[k] >= m.r2) return GM_EINVAL;
-                if (g3[k] < 0 || g3[k] >= n * n || g4[k] < 0 || g4[k] >= n * n) return GM_EINVAL;
+                if (g3[k] < 0 || g3[k] >= NC || g4[k] < 0 || g4[k] >= NC) return GM_EINVAL;
             }
             std::vector<char> seen(m.rp, 0);
             for (int k = 0; k < m.n1; ++k) {
@@ -224,8 +348,8 @@ int validate_plan(const Plan &plan) {
             for (int e = 0; e < 2; ++e) {
                 if (x12[4 * e] < 0 || x12[4 * e] >= m.n1 || x12[4 * e + 1] < 0 || x12[4 * e + 1] >= m.n2)
                     return GM_EINVAL;
-                if (x12[4 * e + 2] < 0 || x12[4 * e + 2] >= n * n || x12[4 * e + 3] < 0 ||
-                    x12[4 * e + 3] >= n * n)
+                if (x12[4 * e + 2] < 0 || x12[4 * e + 2] >= NC || x12[4 * e + 3] < 0 ||
+                    x12[4 * e + 3] >= NC)
                     return GM_EINVAL;
             }
         }

@@ -233,3 +233,24 @@ def config3(n: int = 1024, leaf: int = 16, angles: int = 32):
     k = nudged_wavenumber(n, leaf)
     b, c, d = helmholtz_fields(n, k)
     return dict(n=n, leaf=leaf, k=k, b=b, c=c, d=d, G=plane_wave_vectors(n, k, angles, 5))
+
+
+def config4(count: int = 64, sizes=(128, 192, 256, 384, 512), leaf: int = 16, seed: int = 6):
+    """Batch of independent problems: n drawn uniformly from `sizes` (seeded); the even
+    positions carry convection-diffusion-reaction fields (Fourier seeds 100 + 3p ...),
+    the odd ones variable-wavespeed Helmholtz at 10 points per wavelength for their own n.
+    Returns a list of dicts with n, leaf, kind, b, c, d."""
+    pick = (SplitMix64(seed).draw(count) % np.uint64(len(sizes))).astype(np.int64)
+    ks = {}
+    out = []
+    for p in range(count):
+        n = int(sizes[pick[p]])
+        if p % 2 == 0:
+            b, c, d = convection_fields(n, seeds=(100 + 3 * p, 101 + 3 * p, 102 + 3 * p))
+            out.append(dict(n=n, leaf=leaf, kind="convection", b=b, c=c, d=d))
+        else:
+            if n not in ks:
+                ks[n] = nudged_wavenumber(n, leaf)
+            b, c, d = helmholtz_fields(n, ks[n])
+            out.append(dict(n=n, leaf=leaf, kind="helmholtz", k=ks[n], b=b, c=c, d=d))
+    return out

@@ -1,0 +1,131 @@
+"""Batched build (several independent problems, uneven n, one launch per stage across
+all of them) against single builds and the FP64 oracle, in both precisions."""
+import numpy as np
+import pytest
+
+from oracle import nd_dense
+from paper_1302_5995_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gm():
+    from paper_1302_5995_gb300 import build_ext
+    build_ext.build()
+    import paper_1302_5995_gb300 as gm
+    return gm
+
+
+def rel_mat(A, B):
+    return np.abs(A - B).max() / np.abs(B).max()
+
+
+def same_as_single(op, single):
+    """Batched and single builds run the same arithmetic per problem, unless the
+    pivoting fallback (taken for the whole batch when any problem needs it) differs."""
+    if op.info()["pivot_fallback"] == single.info()["pivot_fallback"]:
+        return rel_mat(op.dtn(), single.dtn()) < 1e-13
+    return rel_mat(op.dtn(), single.dtn()) < 1e-8
+
+
+def small_mix():
+    """Five problems of uneven size, depth and leaf: one and two tree levels apart,
+    ragged leaves, Laplace / convection / Helmholtz fields."""
+    probs = []
+    b, c, d = inputs.convection_fields(64, seeds=(7, 8, 9))
+    probs.append((b, c, d, 64, 16))
+    b, c, d = inputs.convection_fields(96, seeds=(10, 11, 12))
+    probs.append((b, c, d, 96, 16))
+    k = inputs.nudged_wavenumber(61, 8)
+    b, c, d = inputs.helmholtz_fields(61, k)
+    probs.append((b, c, d, 61, 8))
+    b, c, d = inputs.laplace_fields(40)
+    probs.append((b, c, d, 40, 8))
+    b, c, d = inputs.convection_fields(128, seeds=(13, 14, 15))
+    probs.append((b, c, d, 128, 16))
+    return probs
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
+def test_batch_matches_oracle_and_single_builds(gm, prec, tol):
+    precision = gm.PREC_FP64 if prec == "fp64" else gm.PREC_MIXED
+    probs = small_mix()
+    ops = gm.build_batch(probs, precision=precision)
+    assert len(ops) == len(probs)
+    for op, (b, c, d, n, leaf) in zip(ops, probs):
+        T = op.dtn()
+        assert T.shape == (4 * n, 4 * n)
+        To = nd_dense.build(b, c, d, n, leaf).T
+        assert rel_mat(T, To) < tol, (n, leaf)
+        single = gm.build(b, c, d, n, leaf, precision=precision)
+        assert same_as_single(op, single), (n, leaf)
+        info = op.info()
+        assert info["n"] == n and info["leaf"] == leaf
+
+
+def test_batch_solve_per_problem(gm):
+    probs = small_mix()
+    ops = gm.build_batch(probs, precision=gm.PREC_MIXED)
+    for i, (op, (b, c, d, n, leaf)) in enumerate(zip(ops, probs)):
+        G = inputs.gaussian_vectors(n, 8, 50 + i)
+        V = op.solve(np.ascontiguousarray(G.T)).reshape(8, 4 * n).T
+        Vo = nd_dense.build(b, c, d, n, leaf).T @ G
+        err = (np.linalg.norm(V - Vo, axis=0) / np.linalg.norm(Vo, axis=0)).max()
+        assert err < 1e-8, (n, err)
+
+
+def test_batch_of_one_equals_single(gm):
+    b, c, d = inputs.convection_fields(80, seeds=(21, 22, 23))
+    (op,) = gm.build_batch([(b, c, d, 80, 16)])
+    single = gm.build(b, c, d, 80, 16)
+    assert rel_mat(op.dtn(), single.dtn()) < 1e-14
+
+
+def test_batch_device_coefficients(gm):
+    import torch
+    probs = small_mix()[:3]
+    dev = [tuple(torch.from_numpy(x).cuda() for x in p[:3]) + p[3:] for p in probs]
+    ops_d = gm.build_batch(dev, precision=gm.PREC_MIXED)
+    ops_h = gm.build_batch(probs, precision=gm.PREC_MIXED)
+    for a, b in zip(ops_d, ops_h):
+        assert rel_mat(a.dtn(), b.dtn()) < 1e-14
+
+
+def test_batch_rejects_bad_arguments(gm):
+    b, c, d = inputs.laplace_fields(32)
+    with pytest.raises(gm.GmError):
+        gm.build_batch([])
+    with pytest.raises(gm.GmError):
+        gm.build_batch([(b, c, d, 32, 2)])  # leaf below 4
+    lib = gm.load_library()
+    o = gm.Opts()
+    lib.gm_opts_default(o)
+    o.keep_levels = 1
+    arr = (gm.Problem * 1)(gm.Problem(b.ctypes.data, c.ctypes.data, d.ctypes.data, 32, 8))
+    import ctypes
+    outs = (ctypes.c_void_p * 1)()
+    assert lib.gm_build_batch(1, arr, o, 0.0, outs) == -6  # GM_EUNSUPPORTED
+    assert outs[0] is None
+
+
+def test_config4_subset(gm):
+    """Eight problems of the 64-problem batch recipe (every size, both field kinds) in
+    mixed precision: each equals its single build; those with n <= 192 match the oracle."""
+    cfg = inputs.config4()
+    chosen, seen = [], set()
+    for p in cfg:
+        key = (p["n"], p["kind"])
+        if key not in seen:
+            seen.add(key)
+            chosen.append(p)
+    chosen = chosen[:8]
+    probs = [(p["b"], p["c"], p["d"], p["n"], p["leaf"]) for p in chosen]
+    ops = gm.build_batch(probs, precision=gm.PREC_MIXED, split_digits=6)
+    for op, p in zip(ops, probs):
+        single = gm.build(*p, precision=gm.PREC_MIXED, split_digits=6)
+        assert same_as_single(op, single), p[3]
+    for op, p in zip(ops, probs):
+        if p[3] <= 192:
+            To = nd_dense.build(*p).T
+            assert rel_mat(op.dtn(), To) < 1e-8, p[3]
