@@ -78,10 +78,15 @@ typedef struct gm_opts {
  *   GM_PIVOT_PARTIAL: partial pivoting over all remaining rows, 16-column panels.
  *   GM_PIVOT_BLOCK:   64-column blocks; pivots are chosen among the rows of the block
  *                     (its 64 x 64 pivot block is inverted with partial pivoting).
- *   GM_PIVOT_AUTO:    block pivoting; if a row below some block held an entry more than
- *                     16x that block column's pivot (where partial pivoting would have
- *                     chosen differently), the whole build is redone with partial
- *                     pivoting.  gm_info().pivot_fallback reports it. */
+ *   GM_PIVOT_AUTO:    block pivoting, with a check per problem: if a row below some
+ *                     block held an entry more than 16x that block column's pivot (partial
+ *                     pivoting would have chosen differently), or if the one refinement
+ *                     step of a block solve contracted by less than 2^16 (an ill-
+ *                     conditioned pivot block, as in indefinite Helmholtz problems), that
+ *                     problem is built again in FP64.  Mixed-precision digit products lose
+ *                     about as many digits as such problems amplify, so FP64 is the only
+ *                     safe choice for them.  gm_info().pivot_fallback and .precision
+ *                     report it.  On a batch only the flagged problems are rebuilt. */
 #define GM_PIVOT_AUTO 0
 #define GM_PIVOT_BLOCK 1
 #define GM_PIVOT_PARTIAL 2
@@ -107,8 +112,9 @@ typedef struct gm_info_t {
     double kernel_ms[GM_K_NFAM];      /* device time per kernel family (timing builds)   */
     double kernel_flops[GM_K_NFAM];   /* algorithmic flops per family (always counted)   */
     int kernel_launches[GM_K_NFAM];   /* launches per family                             */
-    int pivoting;                     /* pivoting actually used (GM_PIVOT_BLOCK/PARTIAL) */
-    int pivot_fallback;               /* 1 if GM_PIVOT_AUTO fell back to partial pivoting */
+    int pivoting;                     /* pivoting actually used (GM_PIVOT_BLOCK/PARTIAL;
+                                         PARTIAL for every FP64 build)                    */
+    int pivot_fallback;               /* 1 if GM_PIVOT_AUTO rebuilt this problem in FP64 */
 } gm_info_t;
 
 /* Fill *opts with defaults (FP64, no kept levels, default stream). */

@@ -147,7 +147,7 @@ int make_devplan(DevPlan &dp) {
         int roff = 0, coff = 0;
         for (int i = 0; i < ds.nm; ++i) {
             const MergeDesc &m = st.merges[i];
-            SysDesc s{m.ws, 2 * m.sp, 2 * m.sp + m.rp, i, roff, coff, 0};
+            SysDesc s{m.ws, 2 * m.sp, 2 * m.sp + m.rp, i, roff, coff, m.prob};
             roff += s.m;
             coff += s.ncol;
             ds.h_sys.push_back(s);
@@ -165,7 +165,7 @@ int make_devplan(DevPlan &dp) {
     int64_t wo = 0;
     for (size_t i = 0; i < P.roots.size(); ++i) {
         const RootDesc &r = P.roots[i];
-        SysDesc s{wo, r.r, r.r + 4 * r.n, (int)i, roff, coff, 0};
+        SysDesc s{wo, r.r, r.r + 4 * r.n, (int)i, roff, coff, r.problem};
         roff += s.m;
         coff += s.ncol;
         wo += (int64_t)s.m * s.ncol;
@@ -263,10 +263,10 @@ namespace {
 
 // One build (a single problem or a batch) in either precision.  db/dc/dd are device
 // arrays holding every problem's coefficients at its RootDesc::coef offset.  H[p] is the
-// handle of problem p (allocated by the caller); *growth_out reports the block-pivoting
-// growth flag of a mixed build.
+// handle of problem p (allocated by the caller).  Per problem, code[p] is 0 or
+// GM_ESINGULAR and growth[p] the block-pivoting growth flag of a mixed build.
 int run_build(const gm_opts &o, const std::shared_ptr<DevPlan> &dpp, const double *db, const double *dc,
-              const double *dd, std::vector<gm_handle *> &H, int *growth_out) {
+              const double *dd, std::vector<gm_handle *> &H, std::vector<int> &code, std::vector<int> &growth) {
     const DevPlan &dp = *dpp;
     const Plan &P = dp.plan;
     cudaStream_t s = (cudaStream_t)o.stream;
@@ -292,10 +292,11 @@ int run_build(const gm_opts &o, const std::shared_ptr<DevPlan> &dpp, const doubl
         h->kept_df32 = mixed;
     }
     int rc;
+    const size_t np = H.size();
     DBuf stat;
-    if ((rc = stat.alloc(sizeof(Status), s))) return rc;
-    Status st0{0, -1, 0x7ff0000000000000ull, 0, 0};
-    CK(cudaMemcpyAsync(stat.p, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
+    if ((rc = stat.alloc(np * sizeof(Status), s))) return rc;
+    std::vector<Status> hst(np, Status{0, -1, 0x7ff0000000000000ull, 0, 0});
+    CK(cudaMemcpyAsync(stat.p, hst.data(), np * sizeof(Status), cudaMemcpyHostToDevice, s));
     Status *dst = stat.as<Status>();
     KTimer kt;
     kt.on = o.timing != 0;
@@ -384,7 +385,6 @@ int run_build(const gm_opts &o, const std::shared_ptr<DevPlan> &dpp, const doubl
             bscr.fex = bfex.as<int>();
             bscr.rdig = brdig.as<__nv_bfloat16>();
             bscr.rex = brex.as<int>();
-            bscr.growth = &dst->growth;
         } else {
             if ((rc = perm.alloc((size_t)max_nm * 4 * GJ_MAX_NB * sizeof(int), s)) ||
                 (rc = perm_n.alloc((size_t)max_nm * sizeof(int), s)) ||
@@ -486,8 +486,7 @@ int run_build(const gm_opts &o, const std::shared_ptr<DevPlan> &dpp, const doubl
             CK(mx_root_finalize(rws.as<float2>() + sy.off, r.r, r.n, h->T, h->Tdf, h->tdig, h->tex, split, s, kt));
         }
     }
-    Status st;
-    CK(cudaMemcpyAsync(&st, stat.p, sizeof(st), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hst.data(), stat.p, np * sizeof(Status), cudaMemcpyDeviceToHost, s));
     // release temporaries (stream-ordered) before the final synchronisation
     for (DBuf *b : {&rws, &piv, &u12, &perm, &perm_n, &a11, &fdig, &rdig, &fex, &rex, &ydig, &xdig, &yex, &xex, &bxd,
                     &bad, &bxe, &bae, &bpmag, &bfdig, &bfex, &brdig, &brex, &arena_buf, &stat})
@@ -501,60 +500,119 @@ int run_build(const gm_opts &o, const std::shared_ptr<DevPlan> &dpp, const doubl
         info.kernel_flops[f] = kt.flops[f];
     }
     kt.collect(info.kernel_ms);
-    double mp;
-    memcpy(&mp, &st.min_piv, 8);
-    info.bad_stage = st.code ? st.where : -1;
     info.launches = launches;
     info.peak_workspace = peak;
     info.pivoting = blockpiv ? GM_PIVOT_BLOCK : GM_PIVOT_PARTIAL;
     info.levels = P.L;
     info.precision = o.precision;
-    for (gm_handle *h : H) {
+    code.assign(np, 0);
+    growth.assign(np, 0);
+    int first = GM_OK;
+    for (size_t p = 0; p < np; ++p) {
+        gm_handle *h = H[p];
+        const Status &st = hst[p];
+        double mp;
+        memcpy(&mp, &st.min_piv, 8);
         gm_info_t hi = info;
         hi.n = h->n;
         hi.leaf = h->leaf;
         hi.dtn_bytes = (long long)16 * h->n * h->n * 8;
         hi.min_pivot_ratio = mp / (4.0 * (h->n + 1.0) * (h->n + 1.0));
+        hi.bad_stage = st.code ? st.where : -1;
         h->info = hi;
+        code[p] = st.code;
+        growth[p] = st.growth;
+        if (st.code && first == GM_OK) first = st.code;
     }
-    *growth_out = st.growth;
-    if (st.code) return st.code;
-    return GM_OK;
+    return first;
 }
 
-// Build with the automatic pivoting fallback; on failure every handle is freed.
+gm_handle *new_handle(const std::pair<int, int> &p, int precision) {
+    gm_handle *h = new gm_handle();
+    h->n = p.first;
+    h->leaf = p.second;
+    h->precision = precision;
+    return h;
+}
+
+// Build with the automatic fallback; on failure every handle is freed.  With block
+// pivoting (the mixed-precision default), the problems whose build raised the growth
+// flag or met a singular pivot are built again, alone, in FP64.
 int build_with_fallback(const gm_opts &o, const std::vector<std::pair<int, int>> &probs, const double *db,
                         const double *dc, const double *dd, std::vector<gm_handle *> &H) {
-    auto fresh = [&]() {
+    auto free_all = [&]() {
         for (gm_handle *h : H) gm_free(h);
         H.clear();
-        for (const auto &p : probs) {
-            gm_handle *h = new gm_handle();
-            h->n = p.first;
-            h->leaf = p.second;
-            h->precision = o.precision;
-            H.push_back(h);
-        }
     };
+    free_all();
     std::shared_ptr<DevPlan> dp;
     int rc = get_plan(probs, dp);
     if (rc) return rc;
-    fresh();
-    int growth = 0;
-    rc = run_build(o, dp, db, dc, dd, H, &growth);
-    if (o.precision == GM_PREC_MIXED && o.pivoting == GM_PIVOT_AUTO && (growth || rc == GM_ESINGULAR)) {
-        // block pivoting was not safe for these operators: redo with partial pivoting
-        cudaGetLastError();
-        fresh();
-        gm_opts o2 = o;
-        o2.pivoting = GM_PIVOT_PARTIAL;
-        rc = run_build(o2, dp, db, dc, dd, H, &growth);
-        for (gm_handle *h : H) h->info.pivot_fallback = 1;
+    for (const auto &p : probs) H.push_back(new_handle(p, o.precision));
+    std::vector<int> code, growth;
+    rc = run_build(o, dp, db, dc, dd, H, code, growth);
+    if (o.precision == GM_PREC_MIXED && o.pivoting == GM_PIVOT_AUTO && (rc == GM_OK || rc == GM_ESINGULAR)) {
+        std::vector<int> redo;
+        for (size_t p = 0; p < probs.size(); ++p)
+            if (growth[p] || code[p] == GM_ESINGULAR) redo.push_back((int)p);
+        if (!redo.empty()) {
+            // the mixed-precision build was not safe for these operators: redo them in FP64
+            gm_opts o2 = o;
+            o2.precision = GM_PREC_FP64;
+            o2.pivoting = GM_PIVOT_PARTIAL;
+            o2.panel_width = 0;
+            cudaStream_t s = (cudaStream_t)o.stream;
+            std::vector<std::pair<int, int>> sub;
+            std::vector<int64_t> off(probs.size() + 1, 0);
+            for (size_t p = 0; p < probs.size(); ++p) off[p + 1] = off[p] + (int64_t)probs[p].first * probs[p].first;
+            int64_t total = 0;
+            for (int p : redo) {
+                sub.push_back(probs[p]);
+                total += (int64_t)probs[p].first * probs[p].first;
+            }
+            // the subset's coefficients, concatenated in subset order
+            DBuf coef;
+            const double *sb = db, *sc = dc, *sd = dd;
+            if (redo.size() != probs.size()) {
+                if ((rc = coef.alloc(3 * (size_t)total * sizeof(double), s))) {
+                    free_all();
+                    return rc;
+                }
+                double *b2 = coef.as<double>(), *c2 = b2 + total, *d2 = c2 + total;
+                int64_t at = 0;
+                for (int p : redo) {
+                    const size_t bytes = (size_t)probs[p].first * probs[p].first * 8;
+                    if (cudaMemcpyAsync(b2 + at, db + off[p], bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+                        cudaMemcpyAsync(c2 + at, dc + off[p], bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+                        cudaMemcpyAsync(d2 + at, dd + off[p], bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+                        free_all();
+                        return cuda_fail(cudaGetLastError(), "subset coefficient copy", __LINE__);
+                    }
+                    at += (int64_t)probs[p].first * probs[p].first;
+                }
+                sb = b2;
+                sc = c2;
+                sd = d2;
+            }
+            std::shared_ptr<DevPlan> dps;
+            if ((rc = get_plan(sub, dps))) {
+                free_all();
+                return rc;
+            }
+            std::vector<gm_handle *> Hs;
+            for (const auto &p : sub) Hs.push_back(new_handle(p, GM_PREC_FP64));
+            std::vector<int> code2, growth2;
+            rc = run_build(o2, dps, sb, sc, sd, Hs, code2, growth2);
+            for (size_t q = 0; q < redo.size(); ++q) {
+                gm_free(H[redo[q]]);
+                H[redo[q]] = Hs[q];
+                Hs[q]->info.pivot_fallback = 1;
+            }
+        }
     }
     if (rc) {
         cudaGetLastError();
-        for (gm_handle *h : H) gm_free(h);
-        H.clear();
+        free_all();
     }
     return rc;
 }

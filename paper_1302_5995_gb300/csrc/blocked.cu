@@ -115,7 +115,7 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
     if (tid == 0) {
         float mn = 3.0e38f;
         for (int t = 0; t < nbe; ++t) mn = fminf(mn, pmag[(size_t)blockIdx.x * 64 + t]);
-        record_pivot_mx(st, (double)mn, stage);
+        record_pivot_mx(st + Sy.prob, (double)mn, stage);
     }
     // digit planes of the rows of X0 and of A11 (K = 64), one warp per row
     for (int i = warp; i < 128; i += nt / 32) {
@@ -200,7 +200,7 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
              const __nv_bfloat16 *__restrict__ x_dig, const __nv_bfloat16 *__restrict__ a11_dig, int64_t plane,
              const int *__restrict__ x_ex, const int *__restrict__ a11_ex, __nv_bfloat16 *__restrict__ fdig,
              int64_t fplane, int *__restrict__ fex, __nv_bfloat16 *__restrict__ rdig, int64_t cplane,
-             int *__restrict__ rex, const float *__restrict__ pmag, int *__restrict__ growth) {
+             int *__restrict__ rex, const float *__restrict__ pmag, Status *__restrict__ st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SysDesc Sy = sys[blockIdx.y];
     const int m = Sy.m;
@@ -218,7 +218,7 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
             mx = fmaxf(mx, v);
             if (i >= k + nbe && v > 16.f * pmag[(size_t)blockIdx.y * 64 + t]) grow = true;
         }
-        if (grow) atomicOr(growth, 1);
+        if (grow) atomicOr(&st[Sy.prob].growth, 1);
         const int e = exp_of_max(mx * 1.0000001f);
         const int64_t row = Sy.roff + i;
         fex[row] = e;
@@ -274,6 +274,8 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
             }
     __syncthreads();
     col_exps64(Ad, exB);
+    __shared__ int cmax[64], rmax[64];  // column maxima of |X0 E| and |R| (float bits, >= 0)
+    if (tid < 64) cmax[tid] = rmax[tid] = 0;
     gemm64_gd<S>(xd, plane, xe, Ad, exB, As, Bs, res);  // X0 E
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
@@ -286,9 +288,18 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
                 const int t = wm + r, jj = wn + cl, j = j0 + jj;
                 float2 v = (t < nbe) ? df_add(Rd[t * LDF + jj], res[mt][nt][c]) : make_float2(0.f, 0.f);
                 Rd[t * LDF + jj] = v;
-                if (t < nbe && j < Sy.ncol) W[(size_t)j * m + k + t] = v;
+                if (t < nbe && j < Sy.ncol) {
+                    W[(size_t)j * m + k + t] = v;
+                    atomicMax(&cmax[jj], __float_as_int(fabsf(res[mt][nt][c].x)));
+                    atomicMax(&rmax[jj], __float_as_int(fabsf(v.x)));
+                }
             }
     __syncthreads();
+    // The refinement step leaves an error of about rho^2 |R|, where rho = |X0 E| / |R|
+    // is its contraction factor (kappa(A11) times the FP32 accuracy of X0).  A column
+    // with rho above 2^-16 would keep more than about 2^-32 |R|: raise the flag that sends
+    // the build to partial pivoting.
+    if (tid < 64 && __int_as_float(cmax[tid]) > 0x1p-16f * __int_as_float(rmax[tid])) atomicOr(&st[Sy.prob].growth, 1);
     col_exps64(Rd, exB);
     __syncthreads();
     for (int e = tid; e < 64 * 64; e += 128) {  // column digit planes of R
@@ -388,7 +399,7 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
         BLK_SPLIT_DISPATCH(split, (k_blk_rfused<SS><<<dim3(cb + rb, nsys), 128, rsm, s>>>(
                                       d_sys, ws, k, cb, scr.x_dig, scr.a11_dig, scr.inv_plane, scr.x_ex, scr.a11_ex,
                                       scr.fdig, scr.fplane, scr.fex, scr.rdig, scr.cplane, scr.rex, scr.pmag,
-                                      scr.growth)));
+                                      st)));
         kt.end(s);
         kt.begin(GM_K_GJUPDATE, fl_upd, s);
         BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3((max_m + 63) / 64, (cols + 63) / 64, nsys), 128, 0, s>>>(

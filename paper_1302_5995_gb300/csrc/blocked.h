@@ -24,7 +24,6 @@ struct BlkScratch {
     int64_t cplane = 0;
     int *aex = nullptr, *r0ex = nullptr, *eex = nullptr, *rex = nullptr;
     float2 *r0 = nullptr;              // [sum cols][64]: first approximation of R
-    int *growth = nullptr;             // set when a row below a block had a much larger entry
 };
 
 size_t blk_factor_smem(int split);

@@ -32,7 +32,7 @@ struct LeafDesc {
     int x0, y0, a, b;
     int64_t off;   // S offset (doubles) in the output arena, column-major r x r
     int n;         // grid size of the leaf's problem (h = 1/(n+1))
-    int pad;
+    int prob;      // problem index in the batch (selects its Status)
     int64_t coef;  // offset of the problem's coefficients in the b, c, d arrays
 };
 
@@ -51,6 +51,7 @@ struct MergeDesc {
     int tab;         // offset of this merge's index table (ints)
     int kpad;        // 2*sp rounded up to 16 (row length of this merge's digit planes)
     int eoff;        // first row of this merge in the stage's exponent vectors (prefix of rp)
+    int prob;        // problem index in the batch
     int64_t doff;    // first element of this merge in the stage's digit planes (rp x kpad)
     // table layout at tab:
     //   p3[sp]  p4[sp]  g3[sp]  g4[sp]         ring positions / global flat indices
@@ -67,15 +68,16 @@ struct SysDesc {
     int id;       // stage-local id for error reports
     int roff;     // first row of this system in per-stage row scratch (prefix sum of m)
     int coff;     // first column of this system in per-stage column scratch (prefix of ncol)
-    int pad;
+    int prob;     // problem index in the batch (selects its Status)
 };
 
-// Device status written by kernels.
+// Device status written by kernels, one per problem of a build.
 struct Status {
     int code;                    // 0 or GM_ESINGULAR
     int where;                   // stage index of the first failure
     unsigned long long min_piv;  // bit pattern of min |pivot| (positive double)
-    int growth;                  // block pivoting: a row outside a block would have pivoted
+    int growth;                  // block pivoting was unsafe: a row outside a block would have
+                                 // pivoted, or a block solve's refinement contracted too slowly
     int pad;
 };
 

@@ -140,7 +140,7 @@ k_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf0, cons
             }
             __syncthreads();
             const double pv = band[(size_t)k * W + KL];
-            if (tid == 0) record_pivot(st, pv, stage);
+            if (tid == 0) record_pivot(st + Ld.prob, pv, stage);
             const double ipv = 1.0 / pv;
             for (int rr = k + 1 + tid; rr <= last; rr += nt) band[(size_t)rr * W + KL + k - rr] *= ipv;
             __syncthreads();
@@ -312,7 +312,7 @@ k_gj_panel(const SysDesc *__restrict__ sys, double *__restrict__ ws, int k, int 
         }
         __syncthreads();
         const double pv = P[(size_t)t * ldp + t];
-        if (tid == 0) record_pivot(st, pv, stage);
+        if (tid == 0) record_pivot(st + S.prob, pv, stage);
         const double inv = 1.0 / pv;
         for (int rr = t + 1 + tid; rr < rows; rr += nt) {
             double l = P[(size_t)t * ldp + rr] * inv;

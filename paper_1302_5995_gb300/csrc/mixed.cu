@@ -195,7 +195,7 @@ k_mx_gj_panel(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, i
         const double pv = s_lu[t][t];
         minp = fmin(minp, fabs(pv));
         if (!(fabs(pv) > 0.0) || !isfinite(pv)) {
-            if (tid == 0) record_pivot_mx(st, pv, stage);
+            if (tid == 0) record_pivot_mx(st + S.prob, pv, stage);
         }
         for (int i = t + 1 + tid; i < nbe; i += nt) s_lu[i][t] = s_lu[i][t] / pv;
         __syncthreads();
@@ -206,7 +206,7 @@ k_mx_gj_panel(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, i
         }
         __syncthreads();
     }
-    if (tid == 0 && minp > 0.0 && minp < 1e300) record_pivot_mx(st, minp, stage);
+    if (tid == 0 && minp > 0.0 && minp < 1e300) record_pivot_mx(st + S.prob, minp, stage);
     if (tid < nbe) {  // column tid of A11^{-1}: L y = e_tid, U x = y
         double x[GJ_MAX_NB];
         for (int i = 0; i < nbe; ++i) {

@@ -250,6 +250,7 @@ int build_batch_plan(const std::vector<const Plan *> &plans, const std::vector<i
             LeafDesc d = l;
             d.off = remap(l.off);
             d.coef = co;
+            d.prob = (int)pi;
             out.leaves.push_back(d);
         }
         out.leaf_boxes.insert(out.leaf_boxes.end(), P.leaf_boxes.begin(), P.leaf_boxes.end());
@@ -262,6 +263,7 @@ int build_batch_plan(const std::vector<const Plan *> &plans, const std::vector<i
                 m.s2 = remap(m0.s2);
                 m.out = remap(m0.out);
                 m.ws = m0.ws + ws_fill[shift + si];
+                m.prob = (int)pi;
                 m.doff = dst.dig_elems;
                 dst.dig_elems += (int64_t)m.rp * m.kpad;
                 m.eoff = (int)dst.exp_elems;

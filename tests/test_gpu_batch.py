@@ -22,11 +22,10 @@ def rel_mat(A, B):
 
 
 def same_as_single(op, single):
-    """Batched and single builds run the same arithmetic per problem, unless the
-    pivoting fallback (taken for the whole batch when any problem needs it) differs."""
-    if op.info()["pivot_fallback"] == single.info()["pivot_fallback"]:
-        return rel_mat(op.dtn(), single.dtn()) < 1e-13
-    return rel_mat(op.dtn(), single.dtn()) < 1e-8
+    """Each problem of a batch takes the same path (and the same automatic fallback) as
+    its single build, so the results agree to the last bits."""
+    assert op.info()["pivot_fallback"] == single.info()["pivot_fallback"]
+    return rel_mat(op.dtn(), single.dtn()) < 1e-13
 
 
 def small_mix():
@@ -129,3 +128,20 @@ def test_config4_subset(gm):
         if p[3] <= 192:
             To = nd_dense.build(*p).T
             assert rel_mat(op.dtn(), To) < 1e-8, p[3]
+
+
+def test_batch_fallback_is_per_problem(gm):
+    """Convection problems stay mixed precision, Helmholtz problems of the same batch are
+    rebuilt in FP64; both equal their single builds."""
+    probs = []
+    for n in (128, 192):
+        probs.append(inputs.convection_fields(n, seeds=(n, n + 1, n + 2)) + (n, 16))
+        probs.append(inputs.helmholtz_fields(n, inputs.nudged_wavenumber(n, 16)) + (n, 16))
+    ops = gm.build_batch(probs, precision=gm.PREC_MIXED, split_digits=6)
+    for i, (op, p) in enumerate(zip(ops, probs)):
+        info = op.info()
+        helm = i % 2 == 1
+        assert info["pivot_fallback"] == (1 if helm else 0)
+        assert info["precision"] == (gm.PREC_FP64 if helm else gm.PREC_MIXED)
+        assert same_as_single(op, gm.build(*p, precision=gm.PREC_MIXED, split_digits=6))
+        assert rel_mat(op.dtn(), nd_dense.build(*p).T) < (1e-10 if helm else 1e-8)

@@ -92,9 +92,9 @@ def test_mixed_small_and_ragged(gm, n, leaf):
 def test_mixed_singular_box_reported(gm):
     n = 6
     b, c, d = inputs.laplace_fields(n)
-    h = 1.0 / (n + 1)
     d = d.copy()
-    d[1 + n * 1] = -4.0 / (h * h)
+    # exactly minus the centre weight 4/h^2, which the library forms as 4 (n+1)^2
+    d[1 + n * 1] = -4.0 * (n + 1) ** 2
     with pytest.raises(gm.GmError) as e:
         gm.build(b, c, d, n, 4, precision=gm.PREC_MIXED)
     assert e.value.code == gm.GM_ESINGULAR
@@ -110,12 +110,34 @@ def test_mixed_pivoting_modes_agree_with_oracle(gm, piv):
     assert rel_mat(op.dtn(), nd_dense.build(b, c, d, n, leaf).T) < TOL_MIXED
 
 
-def test_mixed_indefinite_helmholtz(gm):
-    """Variable-wavespeed Helmholtz (indefinite): whatever pivoting the automatic mode
-    settles on, the result must meet the bound."""
+def test_auto_rebuilds_indefinite_helmholtz_in_fp64(gm):
+    """Variable-wavespeed Helmholtz (indefinite): its pivot blocks are ill-conditioned, the
+    block solves' refinement check fires and the automatic mode builds it in FP64."""
     n, leaf = 96, 12
     k = inputs.nudged_wavenumber(n, leaf)
     b, c, d = inputs.helmholtz_fields(n, k)
     op = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED)
+    info = op.info()
+    assert info["pivot_fallback"] == 1 and info["precision"] == gm.PREC_FP64
     To = nd_dense.build(b, c, d, n, leaf).T
-    assert rel_mat(op.dtn(), To) < 1e3 * TOL_MIXED * max(1.0, np.abs(To).max() / (4 * (n + 1)))
+    assert rel_mat(op.dtn(), To) < 1e-10
+
+
+def test_auto_fallback_matches_fp64_build_at_384(gm):
+    """At n = 384 mixed precision with partial pivoting would miss the bound (its digit
+    products lose what the indefinite problem amplifies); the fallback is the FP64 build."""
+    n, leaf = 384, 16
+    b, c, d = inputs.helmholtz_fields(n, inputs.nudged_wavenumber(n, leaf))
+    op = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED, split_digits=6)
+    assert op.info()["pivot_fallback"] == 1
+    assert rel_mat(op.dtn(), gm.build(b, c, d, n, leaf).dtn()) < 1e-14
+
+
+def test_convection_stays_mixed_block_pivoted(gm):
+    n, leaf = 256, 16
+    b, c, d = inputs.convection_fields(n, seeds=(8, 9, 10))
+    op = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED, split_digits=6)
+    info = op.info()
+    assert info["pivot_fallback"] == 0 and info["precision"] == gm.PREC_MIXED
+    assert info["pivoting"] == gm.PIVOT_BLOCK
+    assert rel_mat(op.dtn(), gm.build(b, c, d, n, leaf).dtn()) < TOL_MIXED

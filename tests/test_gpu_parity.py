@@ -171,9 +171,9 @@ def test_singular_box_is_reported_not_faulted(gm):
     Dirichlet problem -> GM_ESINGULAR, and the context stays usable."""
     n = 6  # leaf 4 -> four 3 x 3 leaves; interior node of the south-west leaf is (1, 1)
     b, c, d = inputs.laplace_fields(n)
-    h = 1.0 / (n + 1)
     d = d.copy()
-    d[1 + n * 1] = -4.0 / (h * h)
+    # exactly minus the centre weight 4/h^2, which the library forms as 4 (n+1)^2
+    d[1 + n * 1] = -4.0 * (n + 1) ** 2
     with pytest.raises(gm.GmError) as e:
         gm.build(b, c, d, n, 4)
     assert e.value.code == gm.GM_ESINGULAR
