@@ -68,7 +68,10 @@ typedef struct gm_opts {
     int timing;       /* nonzero: time every kernel launch of the build with CUDA events
                          (per kernel family, reported by gm_info)                       */
     int split_digits; /* GM_PREC_MIXED: 7-bit digits per operand of the split products,
-                         3..6 (0 = default 5); more digits = more accuracy, more work   */
+                         3..6 (0 = default 6); more digits = more accuracy, more work.
+                         The automatic fallback (GM_PIVOT_AUTO) is calibrated for 6:
+                         with fewer digits the digit truncation, amplified by the
+                         problem's conditioning, is not checked.                     */
     int pivoting;     /* GM_PREC_MIXED: GM_PIVOT_AUTO (default), GM_PIVOT_BLOCK or
                          GM_PIVOT_PARTIAL (see below); GM_PREC_FP64 always uses partial  */
     int reserved[5];
@@ -81,7 +84,7 @@ typedef struct gm_opts {
  *   GM_PIVOT_AUTO:    block pivoting, with a check per problem: if a row below some
  *                     block held an entry more than 16x that block column's pivot (partial
  *                     pivoting would have chosen differently), or if the one refinement
- *                     step of a block solve contracted by less than 2^16 (an ill-
+ *                     step of a block solve contracted by less than 2^13 (an ill-
  *                     conditioned pivot block, as in indefinite Helmholtz problems), that
  *                     problem is built again in FP64.  Mixed-precision digit products lose
  *                     about as many digits as such problems amplify, so FP64 is the only
@@ -115,6 +118,8 @@ typedef struct gm_info_t {
     int pivoting;                     /* pivoting actually used (GM_PIVOT_BLOCK/PARTIAL;
                                          PARTIAL for every FP64 build)                    */
     int pivot_fallback;               /* 1 if GM_PIVOT_AUTO rebuilt this problem in FP64 */
+    double refine_ratio;              /* block pivoting: largest |X0 E| / |R| of the one
+                                         refinement step of a block solve (0 otherwise)  */
 } gm_info_t;
 
 /* Fill *opts with defaults (FP64, no kept levels, default stream). */

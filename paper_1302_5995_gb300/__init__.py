@@ -45,7 +45,7 @@ class Info(ctypes.Structure):
                 ("bad_stage", ctypes.c_int), ("launches", ctypes.c_int),
                 ("kernel_ms", ctypes.c_double * 7), ("kernel_flops", ctypes.c_double * 7),
                 ("kernel_launches", ctypes.c_int * 7), ("pivoting", ctypes.c_int),
-                ("pivot_fallback", ctypes.c_int)]
+                ("pivot_fallback", ctypes.c_int), ("refine_ratio", ctypes.c_double)]
 
 
 class Problem(ctypes.Structure):

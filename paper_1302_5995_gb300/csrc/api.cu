@@ -241,7 +241,7 @@ struct gm_handle {
     float2 *Tdf = nullptr;          // mixed precision: T as double-float
     __nv_bfloat16 *tdig = nullptr;  // mixed precision: digit planes of T's rows, for the apply
     int *tex = nullptr;             // mixed precision: row exponents of T
-    int split = 5;                  // mixed precision: digits per operand
+    int split = 6;                  // mixed precision: digits per operand
     std::shared_ptr<DevPlan> plan;
     // kept intermediates: box -> device pointer of its Schur complement (FP64, or
     // double-float pairs for a mixed-precision build)
@@ -261,6 +261,10 @@ extern "C" void gm_free(gm_handle *h);
 
 namespace {
 
+// Largest refinement ratio of a block solve accepted by the automatic mode (its square,
+// about the relative error left by one refinement step, is 2^-26 = 1.5e-8).
+constexpr float kMaxRefineRatio = 0x1p-13f;
+
 // One build (a single problem or a batch) in either precision.  db/dc/dd are device
 // arrays holding every problem's coefficients at its RootDesc::coef offset.  H[p] is the
 // handle of problem p (allocated by the caller).  Per problem, code[p] is 0 or
@@ -274,7 +278,7 @@ int run_build(const gm_opts &o, const std::shared_ptr<DevPlan> &dpp, const doubl
     const bool blockpiv = mixed && o.pivoting != GM_PIVOT_PARTIAL;
     const int nb = o.panel_width > 0 ? o.panel_width : (mixed ? 16 : 8);
     if (nb > GJ_MAX_NB) return GM_EINVAL;
-    const int split = o.split_digits ? o.split_digits : 5;
+    const int split = o.split_digits ? o.split_digits : 6;
     if (mixed && (split < 3 || split > 6)) return GM_EINVAL;
     if (leaf_smem_bytes(dp.max_leaf_a, dp.max_leaf_b) > 220 * 1024) return GM_EUNSUPPORTED;
     // the leaf kernel gives each inner-ring right-hand side one of 64 thread columns
@@ -295,7 +299,7 @@ int run_build(const gm_opts &o, const std::shared_ptr<DevPlan> &dpp, const doubl
     const size_t np = H.size();
     DBuf stat;
     if ((rc = stat.alloc(np * sizeof(Status), s))) return rc;
-    std::vector<Status> hst(np, Status{0, -1, 0x7ff0000000000000ull, 0, 0});
+    std::vector<Status> hst(np, Status{0, -1, 0x7ff0000000000000ull, 0, 0u});
     CK(cudaMemcpyAsync(stat.p, hst.data(), np * sizeof(Status), cudaMemcpyHostToDevice, s));
     Status *dst = stat.as<Status>();
     KTimer kt;
@@ -519,9 +523,13 @@ int run_build(const gm_opts &o, const std::shared_ptr<DevPlan> &dpp, const doubl
         hi.dtn_bytes = (long long)16 * h->n * h->n * 8;
         hi.min_pivot_ratio = mp / (4.0 * (h->n + 1.0) * (h->n + 1.0));
         hi.bad_stage = st.code ? st.where : -1;
+        float rho;
+        memcpy(&rho, &st.rho, 4);
+        hi.refine_ratio = blockpiv ? (double)rho : 0.0;
         h->info = hi;
         code[p] = st.code;
-        growth[p] = st.growth;
+        // a refinement ratio rho leaves an error near rho^2 per block solve
+        growth[p] = st.growth || (blockpiv && !(rho <= kMaxRefineRatio));
         if (st.code && first == GM_OK) first = st.code;
     }
     return first;

@@ -35,106 +35,129 @@ constexpr int LDF = NBK + 1;  // padded row length of the df32 shared tiles
 
 // ----------------------------------------------------------------------------- factor
 
-constexpr int FAC_THREADS = 1024;
+constexpr int FAC_THREADS = 256;
+constexpr int PRS = 36;  // shared stride of the four 32-column groups of the pivot row
 
+// X0 ~ A11^{-1} by Gauss-Jordan on [A11 | I] in FP32 with partial pivoting among the rows
+// of the block.  The 64 x 128 augmented matrix lives in registers: thread (row, cg) holds
+// columns 32 cg .. 32 cg + 31 of one row (four threads per row, eight rows per warp).
+// Rows never move: the pivot row of column t is prow_of[t], and row t of X0 is the right
+// half of that row at the end.  Per column: one warp-level and one block-level argmax,
+// the pivot row scaled into shared memory, and a rank-1 update of the other rows.
 template <int S>
 __global__ void __launch_bounds__(FAC_THREADS)
 k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int k, __nv_bfloat16 *__restrict__ x_dig,
              __nv_bfloat16 *__restrict__ a_dig, int64_t plane, int *__restrict__ x_ex, int *__restrict__ a_ex,
              float *__restrict__ pmag, Status *st, int stage) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *Aug = (float *)smem_raw;                 // [64][129] FP32 [A11 | I]
-    float2 *Adf = (float2 *)(Aug + 64 * 129 + 64);  // [64][LDF] A11 (df32)
-    __shared__ float fcol[64];
-    __shared__ int s_p;
+    float2 *Adf = (float2 *)smem_raw;       // [64][LDF] A11 (df32)
+    float *Xs = (float *)(Adf + 64 * LDF);  // [64][65] rows of X0
+    __shared__ float s_best[8];
+    __shared__ int s_row[8];
+    __shared__ __align__(16) float prow[4 * PRS];
+    __shared__ float s_pm[64];
     const SysDesc Sy = sys[blockIdx.x];
     const int m = Sy.m;
     if (k >= m) return;
     const int nbe = min(NBK, m - k);
     const float2 *W = ws + Sy.off;
-    const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5;
-    for (int e = tid; e < 64 * 64; e += nt) {  // A11, padded with the identity beyond nbe
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int row = tid >> 2, cg = tid & 3;
+    for (int e = tid; e < 64 * 64; e += FAC_THREADS) {  // A11, padded with the identity beyond nbe
         const int i = e % 64, j = e / 64;
-        float2 v = (i < nbe && j < nbe) ? W[(size_t)(k + j) * m + k + i] : make_float2(i == j ? 1.f : 0.f, 0.f);
-        Adf[i * LDF + j] = v;
-        Aug[i * 129 + j] = v.x;
-        Aug[i * 129 + 64 + j] = (i == j) ? 1.f : 0.f;
+        Adf[i * LDF + j] = (i < nbe && j < nbe) ? W[(size_t)(k + j) * m + k + i] : make_float2(i == j ? 1.f : 0.f, 0.f);
     }
     __syncthreads();
-    // Gauss-Jordan on [A11 | I] with partial pivoting among the unused rows; rows are
-    // not moved: pivot row of column t is prow_of[t], and X0 row t is that row's right half.
-    __shared__ int prow_of[64];
-    __shared__ unsigned long long used;
-    __shared__ float prow[128];
-    if (tid == 0) used = 0ull;
-    __syncthreads();
+    float a[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const int c = cg * 32 + j;
+        a[j] = c < 64 ? Adf[row * LDF + c].x : (c - 64 == row ? 1.f : 0.f);
+    }
+    bool used = false;
+    int my_step = 0;
+    // The t loop stays rolled (an unrolled body overflows the instruction cache).  So that
+    // column t is always at a[0] of group t / 32, that group drops its eliminated column
+    // after each step by shifting its registers down (identically in every row).
+#pragma unroll 1
     for (int t = 0; t < 64; ++t) {
-        if (warp == 0) {
-            float best = -1.f;
-            int bi = 64;
-            for (int r = tid; r < 64; r += 32) {
-                if ((used >> r) & 1ull) continue;
-                float v = fabsf(Aug[r * 129 + t]);
-                if (v > best) { best = v; bi = r; }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                float v2 = __shfl_down_sync(0xffffffffu, best, o);
-                int i2 = __shfl_down_sync(0xffffffffu, bi, o);
-                if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
-            }
-            if (tid == 0) {
-                if (bi >= 64) {  // no candidate (cannot happen: 64 - t unused rows remain)
-                    for (bi = 0; bi < 64 && ((used >> bi) & 1ull); ++bi) {}
-                    if (bi >= 64) bi = 0;
-                }
-                s_p = bi;
-                prow_of[t] = bi;
-                used |= 1ull << bi;
-                if (t < nbe) pmag[(size_t)blockIdx.x * 64 + t] = best;
+        const int ct = t >> 5;
+        // multiplier of this row (for the pivot row: the pivot), read before any update
+        const float f = __shfl_sync(0xffffffffu, a[0], (lane & ~3) | ct);
+        // candidates: unused rows (a NaN counts as 0, so an unused row always wins)
+        float v = -1.f;
+        if (!used) {
+            v = fabsf(f);
+            if (!(v == v)) v = 0.f;
+        }
+        int r = row;
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) {
+            const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+            const int r2 = __shfl_xor_sync(0xffffffffu, r, o);
+            if (v2 > v || (v2 == v && r2 < r)) { v = v2; r = r2; }
+        }
+        if (lane == 0) { s_best[warp] = v; s_row[warp] = r; }
+        __syncthreads();
+        float best = s_best[0];
+        int p = s_row[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) {
+            const float v2 = s_best[w];
+            const int r2 = s_row[w];
+            if (v2 > best || (v2 == best && r2 < p)) { best = v2; p = r2; }
+        }
+        if (row == p) {
+            const float ip = 1.f / f;
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+                *(float4 *)&prow[cg * PRS + j] = make_float4(a[j] * ip, a[j + 1] * ip, a[j + 2] * ip, a[j + 3] * ip);
+            used = true;
+            my_step = t;
+            if (cg == 0) {
+                s_pm[t] = fabsf(f);
+                if (t < nbe) pmag[(size_t)blockIdx.x * 64 + t] = fabsf(f);
             }
         }
         __syncthreads();
-        const int p = s_p;
-        const float pv = Aug[p * 129 + t];
-        const float ipv = pv != 0.f ? 1.f / pv : 0.f;
-        if (tid < 128) prow[tid] = Aug[p * 129 + tid] * ipv;
-        else if (tid < 192) fcol[tid - 128] = Aug[(tid - 128) * 129 + t];
-        __syncthreads();
-        {  // thread owns column c, rows r = g, g + G, ...; eliminated columns (c <= t) stay
-            const int c = tid & 127, G = nt >> 7;
-            if (c > t || c >= 64) {
-                const float pc = prow[c];
-                for (int r = tid >> 7; r < 64; r += G)
-                    Aug[r * 129 + c] = (r == p) ? pc : Aug[r * 129 + c] - fcol[r] * pc;
-            } else if (c == t) {
-                for (int r = tid >> 7; r < 64; r += G) Aug[r * 129 + c] = (r == p) ? 1.f : 0.f;
-            }
+        const float g = (row == p) ? 0.f : f;
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+            const float4 q = *(const float4 *)&prow[cg * PRS + j];
+            a[j] = (row == p) ? q.x : fmaf(-g, q.x, a[j]);
+            a[j + 1] = (row == p) ? q.y : fmaf(-g, q.y, a[j + 1]);
+            a[j + 2] = (row == p) ? q.z : fmaf(-g, q.z, a[j + 2]);
+            a[j + 3] = (row == p) ? q.w : fmaf(-g, q.w, a[j + 3]);
         }
-        __syncthreads();
+        if (cg == ct) {
+#pragma unroll
+            for (int j = 0; j < 31; ++j) a[j] = a[j + 1];
+            a[31] = 0.f;
+        }
     }
+    if (cg >= 2) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) Xs[my_step * 65 + (cg - 2) * 32 + j] = a[j];
+    }
+    __syncthreads();
     if (tid == 0) {
         float mn = 3.0e38f;
-        for (int t = 0; t < nbe; ++t) mn = fminf(mn, pmag[(size_t)blockIdx.x * 64 + t]);
+        for (int t = 0; t < nbe; ++t) mn = fminf(mn, s_pm[t]);
         record_pivot_mx(st + Sy.prob, (double)mn, stage);
     }
     // digit planes of the rows of X0 and of A11 (K = 64), one warp per row
-    for (int i = warp; i < 128; i += nt / 32) {
-        if (i < 64) {
-            const int64_t row = (int64_t)blockIdx.x * 64 + i;
-            const int src = prow_of[i];
-            warp_slice_row<S>([&](int q) { return make_float2(Aug[src * 129 + 64 + q], 0.f); }, 64, 64, x_dig,
-                              plane, row, x_ex);
-        } else {
-            const int ii = i - 64;
-            const int64_t row = (int64_t)blockIdx.x * 64 + ii;
-            warp_slice_row<S>([&](int q) { return Adf[ii * LDF + q]; }, 64, 64, a_dig, plane, row, a_ex);
-        }
+    for (int i = warp; i < 128; i += FAC_THREADS / 32) {
+        const int64_t r64 = (int64_t)blockIdx.x * 64 + (i & 63);
+        if (i < 64)
+            warp_slice_row<S>([&](int q) { return make_float2(Xs[i * 65 + q], 0.f); }, 64, 64, x_dig, plane, r64, x_ex);
+        else
+            warp_slice_row<S>([&](int q) { return Adf[(i - 64) * LDF + q]; }, 64, 64, a_dig, plane, r64, a_ex);
     }
 }
 
 size_t blk_factor_smem(int split) {
     (void)split;
-    return (size_t)(64 * 129 + 64) * sizeof(float) + 64 * LDF * sizeof(float2);
+    return (size_t)64 * LDF * sizeof(float2) + (size_t)64 * 65 * sizeof(float);
 }
 
 // ----------------------------------------------------------------------------- R = A11^{-1} A12
@@ -164,6 +187,7 @@ __device__ __forceinline__ void gemm64_gd(const __nv_bfloat16 *__restrict__ adig
             for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[g][mt][nt][c] = 0.f;
+#pragma unroll 1
     for (int t0 = 0; t0 < NBK; t0 += 16) {
         __syncthreads();
         load_digit_tile<S>(adig, plane, NBK, 0, 64, t0, As);
@@ -208,25 +232,36 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
     const int nbe = min(NBK, m - k);
     float2 *W = ws + Sy.off;
     if ((int)blockIdx.x >= cb) {
-        const int i = ((int)blockIdx.x - cb) * 128 + threadIdx.x;
-        if (i >= m) return;
-        const bool inJ = i >= k && i < k + nbe;
+        // a 128 x 64 tile of F through shared memory: read by rows (coalesced over i),
+        // digit planes written by warps along the row (coalesced over t)
+        float2 *Ft = (float2 *)smem_raw;  // [128][LDF]
+        __shared__ int s_ex[128];
+        const int i0 = ((int)blockIdx.x - cb) * 128, i = i0 + threadIdx.x;
+        const bool live = i < m && !(i >= k && i < k + nbe);
         float mx = 0.f;
         bool grow = false;
-        for (int t = 0; t < nbe; ++t) {
-            const float v = inJ ? 0.f : fabsf(W[(size_t)(k + t) * m + i].x);
-            mx = fmaxf(mx, v);
-            if (i >= k + nbe && v > 16.f * pmag[(size_t)blockIdx.y * 64 + t]) grow = true;
+        for (int t = 0; t < NBK; ++t) {
+            const float2 v = (live && t < nbe) ? W[(size_t)(k + t) * m + i] : make_float2(0.f, 0.f);
+            Ft[threadIdx.x * LDF + t] = v;
+            const float av = fabsf(v.x);
+            mx = fmaxf(mx, av);
+            if (t < nbe && i >= k + nbe && av > 16.f * pmag[(size_t)blockIdx.y * 64 + t]) grow = true;
         }
         if (grow) atomicOr(&st[Sy.prob].growth, 1);
         const int e = exp_of_max(mx * 1.0000001f);
-        const int64_t row = Sy.roff + i;
-        fex[row] = e;
-        for (int t = 0; t < NBK; ++t) {
-            float d[S];
-            digits<S>((inJ || t >= nbe) ? make_float2(0.f, 0.f) : W[(size_t)(k + t) * m + i], e, d);
+        s_ex[threadIdx.x] = e;
+        if (i < m) fex[Sy.roff + i] = e;
+        __syncthreads();
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int rr = warp; rr < 128 && i0 + rr < m; rr += 4) {
+            const int64_t row = Sy.roff + i0 + rr;
+            const int er = s_ex[rr];
+            for (int t = lane; t < NBK; t += 32) {
+                float d[S];
+                digits<S>(Ft[rr * LDF + t], er, d);
 #pragma unroll
-            for (int s = 0; s < S; ++s) fdig[(int64_t)s * fplane + row * NBK + t] = __float2bfloat16_rn(d[s]);
+                for (int q = 0; q < S; ++q) fdig[(int64_t)q * fplane + row * NBK + t] = __float2bfloat16_rn(d[q]);
+            }
         }
         return;
     }
@@ -295,11 +330,16 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
                 }
             }
     __syncthreads();
-    // The refinement step leaves an error of about rho^2 |R|, where rho = |X0 E| / |R|
-    // is its contraction factor (kappa(A11) times the FP32 accuracy of X0).  A column
-    // with rho above 2^-16 would keep more than about 2^-32 |R|: raise the flag that sends
-    // the build to partial pivoting.
-    if (tid < 64 && __int_as_float(cmax[tid]) > 0x1p-16f * __int_as_float(rmax[tid])) atomicOr(&st[Sy.prob].growth, 1);
+    // The refinement step leaves an error of about rho^2 |R|, where rho = |X0 E| / |R| is
+    // its contraction factor (kappa(A11) times the FP32 accuracy of X0); the largest rho
+    // of the build is reported, and the host decides whether the build is accurate enough.
+    if (tid < 64 && j0 + tid < Sy.ncol) {
+        const float cm = __int_as_float(cmax[tid]), rm = __int_as_float(rmax[tid]);
+        if (cm > 0.f) {
+            const float rho = rm > 0.f ? cm / rm : __int_as_float(0x7f800000);
+            atomicMax(&st[Sy.prob].rho, __float_as_uint(rho));
+        }
+    }
     col_exps64(Rd, exB);
     __syncthreads();
     for (int e = tid; e < 64 * 64; e += 128) {  // column digit planes of R
@@ -314,17 +354,42 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
     }
 }
 
-size_t blk_rgemm_smem(int split) { return 2 * (size_t)split * 64 * KP * 2 + 2 * 64 * LDF * sizeof(float2); }
+size_t blk_rgemm_smem(int split) {
+    // R part: two digit tiles and two df32 tiles; F part: one 128-row df32 tile
+    return std::max(2 * (size_t)split * 64 * KP * 2 + 2 * 64 * LDF * sizeof(float2), (size_t)128 * LDF * sizeof(float2));
+}
 
 // ----------------------------------------------------------------------------- update
 
+constexpr int KP64 = 72;  // row stride (bf16) of a full-K digit tile: 64 + 8 keeps fragment loads conflict-free
+
+// Rows r0 .. r0 + nrows - 1 of every digit plane (64 k each) into shared [S][64][KP64] by
+// cp.async; rows beyond nrows are zero-filled (their source row is r0, in bounds).
+template <int S>
+__device__ __forceinline__ void cp_async_digits64(const __nv_bfloat16 *__restrict__ dig, int64_t plane, int r0,
+                                                  int nrows, __nv_bfloat16 *sm) {
+    for (int e = threadIdx.x; e < S * 64 * 8; e += blockDim.x) {
+        const int s = e >> 9, rem = e & 511, row = rem >> 3, c = rem & 7;
+        const bool ok = row < nrows;
+        const __nv_bfloat16 *src = dig + (int64_t)s * plane + (int64_t)(r0 + (ok ? row : 0)) * NBK + c * 8;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(sm + ((size_t)s * 64 + row) * KP64 + c * 8);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0));
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+}
+
+size_t blk_update_smem(int split) { return 2 * (size_t)split * 64 * KP64 * sizeof(__nv_bfloat16); }
+
+// W(i, j) -= (F R)(i, j) for a 64 x 64 tile of rows outside J: both digit tiles (K = 64)
+// arrive in one cp.async batch, then four k-steps of split products without barriers.
 template <int S>
 __global__ void __launch_bounds__(128)
 k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, const __nv_bfloat16 *__restrict__ fdig,
              int64_t fplane, const int *__restrict__ fex, const __nv_bfloat16 *__restrict__ rdig, int64_t rplane,
              const int *__restrict__ rex) {
-    __shared__ __align__(16) __nv_bfloat16 As[S * 64 * KP];
-    __shared__ __align__(16) __nv_bfloat16 Bs[S * 64 * KP];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __nv_bfloat16 *As = (__nv_bfloat16 *)smem_raw;  // [S][64][KP64]
+    __nv_bfloat16 *Bs = As + S * 64 * KP64;
     const SysDesc Sy = sys[blockIdx.z];
     const int m = Sy.m;
     if (k >= m) return;
@@ -332,10 +397,23 @@ k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, co
     const int i0 = blockIdx.x * 64, j0 = k + nbe + blockIdx.y * 64;
     if (i0 >= m || j0 >= Sy.ncol) return;
     float2 *W = ws + Sy.off;
-    float2 res[2][4][4];
-    digit_gemm_tile<S>(fdig + (int64_t)Sy.roff * NBK, fplane, NBK, i0, m, fex + Sy.roff, rdig + (int64_t)Sy.coff * NBK,
-                       rplane, NBK, j0, Sy.ncol, rex + Sy.coff, NBK, As, Bs, res);
+    cp_async_digits64<S>(fdig + (int64_t)Sy.roff * NBK, fplane, i0, min(64, m - i0), As);
+    cp_async_digits64<S>(rdig + (int64_t)Sy.coff * NBK, rplane, j0, min(64, Sy.ncol - j0), Bs);
+    asm volatile("cp.async.wait_all;\n" ::);
+    __syncthreads();
     const int warp = threadIdx.x >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
+    float acc[S][2][4][4];
+#pragma unroll
+    for (int g = 0; g < S; ++g)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[g][mt][nt][c] = 0.f;
+#pragma unroll 1
+    for (int kk = 0; kk < NBK; kk += 16) warp_mma_levels<S, KP64>(As + kk, Bs + kk, 64, 64, wm, wn, acc);
+    const int *fe = fex + Sy.roff, *re = rex + Sy.coff;
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -346,8 +424,9 @@ k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, co
                 acc_pos(mt, nt, c, r, cl);
                 const int i = i0 + wm + r, j = j0 + wn + cl;
                 if (i >= m || j >= Sy.ncol || (i >= k && i < k + nbe)) continue;
+                const float2 v = combine_levels<S>(acc, mt, nt, c, fe[i] + re[j] - 12);
                 float2 *p = W + (size_t)j * m + i;
-                *p = df_sub(*p, res[mt][nt][c]);
+                *p = df_sub(*p, v);
             }
 }
 
@@ -368,6 +447,8 @@ static cudaError_t set_blk_attrs(int split) {
     cudaError_t e = cudaFuncSetAttribute(k_blk_factor<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)blk_factor_smem(split));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_blk_update<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk_update_smem(split));
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_blk_rfused<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)blk_rgemm_smem(split));
 }
@@ -378,7 +459,7 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
     cudaError_t e = cudaSuccess;
     BLK_SPLIT_DISPATCH(split, (e = set_blk_attrs<SS>(split)));
     if (e != cudaSuccess) return e;
-    const size_t fsm = blk_factor_smem(split), rsm = blk_rgemm_smem(split);
+    const size_t fsm = blk_factor_smem(split), rsm = blk_rgemm_smem(split), usm = blk_update_smem(split);
     for (int k = 0; k < max_m; k += NBK) {
         double fl_fac = 0, fl_r = 0, fl_upd = 0;
         for (const SysDesc &S : h_sys) {
@@ -402,7 +483,7 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
                                       st)));
         kt.end(s);
         kt.begin(GM_K_GJUPDATE, fl_upd, s);
-        BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3((max_m + 63) / 64, (cols + 63) / 64, nsys), 128, 0, s>>>(
+        BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3((max_m + 63) / 64, (cols + 63) / 64, nsys), 128, usm, s>>>(
                                       d_sys, ws, k, scr.fdig, scr.fplane, scr.fex, scr.rdig, scr.cplane, scr.rex)));
         kt.end(s);
     }

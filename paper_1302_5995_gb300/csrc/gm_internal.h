@@ -76,9 +76,9 @@ struct Status {
     int code;                    // 0 or GM_ESINGULAR
     int where;                   // stage index of the first failure
     unsigned long long min_piv;  // bit pattern of min |pivot| (positive double)
-    int growth;                  // block pivoting was unsafe: a row outside a block would have
-                                 // pivoted, or a block solve's refinement contracted too slowly
-    int pad;
+    int growth;                  // block pivoting: a row outside a block would have pivoted
+    unsigned int rho;            // block pivoting: largest refinement ratio |X0 E| / |R| of a
+                                 // block solve (float bits; ordered like the values)
 };
 
 // One merge stage (all horizontal merges of a level, or all vertical ones).

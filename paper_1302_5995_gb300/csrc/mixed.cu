@@ -329,23 +329,13 @@ k_mx_gj_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, 
     const int i0 = blockIdx.x * 64, j0 = k + nbe + blockIdx.y * 64;
     if (i0 >= m || j0 >= Sy.ncol) return;
     float2 *A = ws + Sy.off;
-    float2 res[2][4][4];
-    digit_gemm_tile<S>(fdig + (int64_t)Sy.roff * 16, fplane, 16, i0, m, fex + Sy.roff, rdig + (int64_t)Sy.coff * 16,
-                       rplane, 16, j0, Sy.ncol, rex + Sy.coff, 16, As, Bs, res);
-    const int warp = threadIdx.x >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                int r, cl;
-                acc_pos(mt, nt, c, r, cl);
-                const int i = i0 + wm + r, j = j0 + wn + cl;
-                if (i >= m || j >= Sy.ncol || (i >= k && i < k + nbe)) continue;
-                float2 *p = A + (size_t)j * m + i;
-                *p = df_sub(*p, res[mt][nt][c]);
-            }
+    digit_gemm_chunks<S>(fdig + (int64_t)Sy.roff * 16, fplane, 16, i0, m, fex + Sy.roff, rdig + (int64_t)Sy.coff * 16,
+                         rplane, 16, j0, Sy.ncol, rex + Sy.coff, 16, As, Bs, [&](int r, int cl, float2 v, bool) {
+                             const int i = i0 + r, j = j0 + cl;
+                             if (i >= m || j >= Sy.ncol || (i >= k && i < k + nbe)) return;
+                             float2 *p = A + (size_t)j * m + i;
+                             *p = df_sub(*p, v);
+                         });
 }
 
 // ----------------------------------------------------------------------------- merge update
@@ -396,40 +386,36 @@ k_mx_merge_update(const MergeDesc *__restrict__ md, const int *__restrict__ tab,
     const MergeTabMx T = merge_tab_mx(M, tab);
     const int n1 = M.n1;
     const float2 *S1 = in + M.s1, *S2 = in + M.s2;
-    float2 res[2][4][4];
     const int64_t eo = M.eoff;
-    digit_gemm_tile<S>(ydig + M.doff, plane, M.kpad, a0, rp, yex + eo, xdig + M.doff, plane, M.kpad, c0, rp, xex + eo,
-                       2 * M.sp, As, Bs, res);
     const double ih = M.n + 1.0;  // 1/h of the merge's problem
     const int d12 = M.orient ? DIR_N : DIR_E, d21 = M.orient ? DIR_S : DIR_W;
     float2 *O = out + M.out;
-    const int warp = threadIdx.x >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                int r, cl;
-                acc_pos(mt, nt, c, r, cl);
-                const int aa = a0 + wm + r, cc = c0 + wn + cl;
-                if (aa >= rp || cc >= rp) continue;
-                int qa = aa < n1 ? T.q1[aa] : T.q2[aa - n1];
-                int qc = cc < n1 ? T.q1[cc] : T.q2[cc - n1];
-                float2 cval = make_float2(0.f, 0.f);
-                if (aa < n1 && cc < n1) cval = S1[T.p1[aa] + (int64_t)M.r1 * T.p1[cc]];
-                else if (aa >= n1 && cc >= n1) cval = S2[T.p2[aa - n1] + (int64_t)M.r2 * T.p2[cc - n1]];
-                else {
-                    for (int e = 0; e < 2; ++e) {
-                        const int *x = T.x12 + 4 * e;
-                        if (aa < n1 && aa == x[0] && cc - n1 == x[1])
-                            cval = df_from_d(stencil_w_mx(bf, cf, df, ih, x[2], d12));
-                        if (aa >= n1 && aa - n1 == x[1] && cc == x[0])
-                            cval = df_from_d(stencil_w_mx(bf, cf, df, ih, x[3], d21));
-                    }
-                }
-                O[qa + (int64_t)rp * qc] = df_sub(cval, res[mt][nt][c]);
+    digit_gemm_chunks<S>(
+        ydig + M.doff, plane, M.kpad, a0, rp, yex + eo, xdig + M.doff, plane, M.kpad, c0, rp, xex + eo, 2 * M.sp, As, Bs,
+        [&](int r, int cl, float2 v, bool first) {
+            const int aa = a0 + r, cc = c0 + cl;
+            if (aa >= rp || cc >= rp) return;
+            const int qa = aa < n1 ? T.q1[aa] : T.q2[aa - n1];
+            const int qc = cc < n1 ? T.q1[cc] : T.q2[cc - n1];
+            float2 *o = O + qa + (int64_t)rp * qc;
+            if (!first) {  // a later K chunk: accumulate into the parent entry
+                *o = df_sub(*o, v);
+                return;
             }
+            float2 cval = make_float2(0.f, 0.f);
+            if (aa < n1 && cc < n1) cval = S1[T.p1[aa] + (int64_t)M.r1 * T.p1[cc]];
+            else if (aa >= n1 && cc >= n1) cval = S2[T.p2[aa - n1] + (int64_t)M.r2 * T.p2[cc - n1]];
+            else {
+                for (int e = 0; e < 2; ++e) {
+                    const int *x = T.x12 + 4 * e;
+                    if (aa < n1 && aa == x[0] && cc - n1 == x[1])
+                        cval = df_from_d(stencil_w_mx(bf, cf, df, ih, x[2], d12));
+                    if (aa >= n1 && aa - n1 == x[1] && cc == x[0])
+                        cval = df_from_d(stencil_w_mx(bf, cf, df, ih, x[3], d21));
+                }
+            }
+            *o = df_sub(cval, v);
+        });
 }
 
 // ----------------------------------------------------------------------------- root
@@ -515,20 +501,13 @@ k_mx_apply(const __nv_bfloat16 *__restrict__ tdig, const int *__restrict__ tex, 
     __shared__ __align__(16) __nv_bfloat16 As[S * 64 * KP];
     __shared__ __align__(16) __nv_bfloat16 Bs[S * 64 * KP];
     const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
-    float2 res[2][4][4];
-    digit_gemm_tile<S>(tdig, tplane, kpad, i0, N, tex, gdig, gplane, kpad, j0, B, gex, N, As, Bs, res);
-    const int warp = threadIdx.x >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                int r, cl;
-                acc_pos(mt, nt, c, r, cl);
-                const int i = i0 + wm + r, j = j0 + wn + cl;
-                if (i < N && j < B) V[(size_t)j * N + i] = df_to_d(res[mt][nt][c]);
-            }
+    digit_gemm_chunks<S>(tdig, tplane, kpad, i0, N, tex, gdig, gplane, kpad, j0, B, gex, N, As, Bs,
+                         [&](int r, int cl, float2 v, bool first) {
+                             const int i = i0 + r, j = j0 + cl;
+                             if (i >= N || j >= B) return;
+                             double *o = V + (size_t)j * N + i;
+                             *o = first ? df_to_d(v) : *o + df_to_d(v);
+                         });
 }
 
 // ----------------------------------------------------------------------------- launchers

@@ -95,8 +95,9 @@ __device__ __forceinline__ void mma_bf16(float c[4], uint32_t a0, uint32_t a1, u
 // bf16 (16 used) makes the fragment loads bank-conflict free.
 constexpr int KP = 24;
 
-// One warp accumulates a 32 x 32 block: 2 m16 tiles x 4 n8 tiles, S levels.
-template <int S>
+// One warp accumulates a 32 x 32 block: 2 m16 tiles x 4 n8 tiles, S levels.  Tiles are
+// [S][rows][LD] (k fastest); the 16 k of this step start at As / Bs.
+template <int S, int LD = KP>
 __device__ __forceinline__ void warp_mma_levels(const __nv_bfloat16 *As, const __nv_bfloat16 *Bs, int BM, int BN,
                                                 int wm, int wn, float acc[S][2][4][4]) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -105,11 +106,11 @@ __device__ __forceinline__ void warp_mma_levels(const __nv_bfloat16 *As, const _
         uint32_t a[2][4];
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
-            const __nv_bfloat16 *p = As + ((size_t)s * BM + wm + mt * 16 + g) * KP + 2 * t;
+            const __nv_bfloat16 *p = As + ((size_t)s * BM + wm + mt * 16 + g) * LD + 2 * t;
             a[mt][0] = *(const uint32_t *)(p);
-            a[mt][1] = *(const uint32_t *)(p + 8 * KP);
+            a[mt][1] = *(const uint32_t *)(p + 8 * LD);
             a[mt][2] = *(const uint32_t *)(p + 8);
-            a[mt][3] = *(const uint32_t *)(p + 8 * KP + 8);
+            a[mt][3] = *(const uint32_t *)(p + 8 * LD + 8);
         }
 #pragma unroll
         for (int u = 0; u < S; ++u) {
@@ -117,7 +118,7 @@ __device__ __forceinline__ void warp_mma_levels(const __nv_bfloat16 *As, const _
             uint32_t b[4][2];
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt) {
-                const __nv_bfloat16 *p = Bs + ((size_t)u * BN + wn + nt * 8 + g) * KP + 2 * t;
+                const __nv_bfloat16 *p = Bs + ((size_t)u * BN + wn + nt * 8 + g) * LD + 2 * t;
                 b[nt][0] = *(const uint32_t *)(p);
                 b[nt][1] = *(const uint32_t *)(p + 8);
             }
@@ -221,22 +222,20 @@ __device__ __forceinline__ void load_digit_tile(const __nv_bfloat16 *__restrict_
 }
 
 // C(i, j) = sum_k A(i, k) B(k, j) for a 64 x 64 tile from two digit matrices (A by rows,
-// B by columns), K in chunks of at most 512 (exact level sums), result in df32 per
-// thread position (see acc_pos); warp w owns rows (w & 1) * 32 and columns (w >> 1) * 32.
-template <int S>
-__device__ __forceinline__ void digit_gemm_tile(const __nv_bfloat16 *__restrict__ Ad, int64_t aplane, int akpad,
-                                                int i0, int M, const int *__restrict__ aex,
-                                                const __nv_bfloat16 *__restrict__ Bd, int64_t bplane, int bkpad,
-                                                int j0, int N, const int *__restrict__ bex, int K,
-                                                __nv_bfloat16 *As, __nv_bfloat16 *Bs, float2 res[2][4][4]) {
+// B by columns), K in chunks of at most 512 (exact level sums).  After each chunk the
+// df32 partial result of every thread position is handed to epi(r, c, value, first),
+// r and c the position in the tile (see acc_pos), first = this is the first chunk; the
+// caller accumulates (so no second register tile is live beside the level sums).
+// Warp w owns rows (w & 1) * 32 and columns (w >> 1) * 32.
+template <int S, class Epi>
+__device__ __forceinline__ void digit_gemm_chunks(const __nv_bfloat16 *__restrict__ Ad, int64_t aplane, int akpad,
+                                                  int i0, int M, const int *__restrict__ aex,
+                                                  const __nv_bfloat16 *__restrict__ Bd, int64_t bplane, int bkpad,
+                                                  int j0, int N, const int *__restrict__ bex, int K,
+                                                  __nv_bfloat16 *As, __nv_bfloat16 *Bs, Epi &&epi) {
     const int warp = threadIdx.x >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) res[mt][nt][c] = make_float2(0.f, 0.f);
     const int mrows = min(64, M - i0), ncols = min(64, N - j0);
+#pragma unroll 1
     for (int k0 = 0; k0 < K; k0 += 512) {
         const int kend = min(K, k0 + 512);
         float acc[S][2][4][4];
@@ -248,6 +247,7 @@ __device__ __forceinline__ void digit_gemm_tile(const __nv_bfloat16 *__restrict_
                 for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
                     for (int c = 0; c < 4; ++c) acc[g][mt][nt][c] = 0.f;
+#pragma unroll 1
         for (int t0 = k0; t0 < kend; t0 += 16) {
             __syncthreads();
             load_digit_tile<S>(Ad, aplane, akpad, i0, mrows, t0, As);
@@ -264,11 +264,9 @@ __device__ __forceinline__ void digit_gemm_tile(const __nv_bfloat16 *__restrict_
                     int r, cl;
                     acc_pos(mt, nt, c, r, cl);
                     const int i = min(i0 + wm + r, M - 1), j = min(j0 + wn + cl, N - 1);
-                    float2 u = combine_levels<S>(acc, mt, nt, c, aex[i] + bex[j] - 12);
-                    res[mt][nt][c] = df_add(res[mt][nt][c], u);
+                    epi(wm + r, wn + cl, combine_levels<S>(acc, mt, nt, c, aex[i] + bex[j] - 12), k0 == 0);
                 }
     }
 }
-
 
 }  // namespace gm
