@@ -232,6 +232,7 @@ class BuildResult:
     L: int
     schur: dict  # Box -> S on its ring (leaves, half-boxes and boxes), if kept
     flops: float
+    S_root: np.ndarray = None  # the root Schur complement (ring of the whole grid)
 
 
 def build(b, c, d, n, leaf, keep=False):
@@ -265,7 +266,7 @@ def build(b, c, d, n, leaf, keep=False):
     r = len(root.ring())
     flops += (2.0 / 3.0) * r**3 + 2.0 * r**2 * 4 * n
     T = root_dtn(prob, S[root])
-    return BuildResult(T=T, L=L, schur=kept, flops=flops)
+    return BuildResult(T=T, L=L, schur=kept, flops=flops, S_root=S[root])
 
 
 def _merge_shapes(parent, kids):
