@@ -74,7 +74,9 @@ typedef struct gm_opts {
                          problem's conditioning, is not checked.                     */
     int pivoting;     /* GM_PREC_MIXED: GM_PIVOT_AUTO (default), GM_PIVOT_BLOCK or
                          GM_PIVOT_PARTIAL (see below); GM_PREC_FP64 always uses partial  */
-    int reserved[5];
+    int hbs_leaf;     /* tol > 0: node size m of the HBS tree over the root ring
+                         (0 = default 64; 2..192)                                       */
+    int reserved[4];
 } gm_opts;
 
 /* Pivoting of the mixed-precision dense eliminations.
@@ -120,6 +122,9 @@ typedef struct gm_info_t {
     int pivot_fallback;               /* 1 if GM_PIVOT_AUTO rebuilt this problem in FP64 */
     double refine_ratio;              /* block pivoting: largest |X0 E| / |R| of the one
                                          refinement step of a block solve (0 otherwise)  */
+    int hbs_levels;                   /* tol > 0: levels L of the root's HBS tree          */
+    int hbs_max_rank;                 /* tol > 0: largest node rank                        */
+    long long hbs_bytes;              /* tol > 0: device bytes of the HBS factors          */
 } gm_info_t;
 
 /* Fill *opts with defaults (FP64, no kept levels, default stream). */
@@ -132,8 +137,12 @@ void gm_opts_default(gm_opts *opts);
  *   leaf    : largest leaf-box edge (Section 2's N_leaf, as an edge): the tree has the
  *             smallest L with ceil(n / 2^L) <= leaf.  4 <= leaf <= 17 (the leaf kernel
  *             keeps a leaf's band and inner-ring solves in shared memory).
- *   tol     : 0 selects the all-dense build (the only form this library provides;
- *             any other value returns GM_EUNSUPPORTED).
+ *   tol     : 0 selects the all-dense build.  tol > 0 keeps the merges dense but
+ *             compresses the root Schur complement to HBS form at local relative
+ *             tolerance tol (Section 4; node size gm_opts.hbs_leaf) and inverts it by
+ *             Algorithm 1 (Section 5); the solve then applies Algorithm 2 instead of a
+ *             dense T.  GM_EUNSUPPORTED if a node's rank reaches 96 (the root does not
+ *             compress enough; build with tol = 0).
  *   out     : receives a new handle that owns all device memory of the operator.
  * Blocks the calling thread until the build has finished on the device.
  */
@@ -168,7 +177,8 @@ int gm_build_batch(int count, const gm_problem *probs, const gm_opts *opts, doub
  */
 int gm_solve(gm_handle *h, const double *g, double *dudn, int batch, void *stream);
 
-/* Copy the dense 4n x 4n DtN matrix (column-major) to T_out (host or device). */
+/* Copy the dense 4n x 4n DtN matrix (column-major) to T_out (host or device).  For an
+ * HBS build (tol > 0) T is formed by applying the solve to the identity. */
 int gm_get_dtn(gm_handle *h, double *T_out);
 
 /*
@@ -196,6 +206,7 @@ int gm_get_schur(gm_handle *h, int x0, int y0, int a, int b, double *S_out);
  *   All calls share the array and it keeps the last call's contents: calls that overlap
  *   on the GPU (other streams, other threads) race on it and must be serialised by the
  *   caller.
+ *   Dense operators only: a handle built with tol > 0 returns GM_EUNSUPPORTED.
  */
 int gm_solve_static(gm_handle *h, const double *g, double *dudn, int batch, void *stream);
 

@@ -19,6 +19,7 @@
 
 #include "blocked.h"
 #include "gm_internal.h"
+#include "hbs.h"
 #include "kernels.h"
 #include "mixed.h"
 
@@ -248,6 +249,7 @@ struct gm_handle {
     std::vector<std::pair<Box, void *>> kept;
     bool kept_df32 = false;
     std::vector<void *> kept_bufs;
+    gm::HbsRoot *hbs = nullptr;     // tol > 0: the root's HBS inverse (no dense T)
     gm_info_t info{};
 };
 
@@ -269,7 +271,7 @@ constexpr float kMaxRefineRatio = 0x1p-13f;
 // arrays holding every problem's coefficients at its RootDesc::coef offset.  H[p] is the
 // handle of problem p (allocated by the caller).  Per problem, code[p] is 0 or
 // GM_ESINGULAR and growth[p] the block-pivoting growth flag of a mixed build.
-int run_build(const gm_opts &o, const std::shared_ptr<DevPlan> &dpp, const double *db, const double *dc,
+int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp, const double *db, const double *dc,
               const double *dd, std::vector<gm_handle *> &H, std::vector<int> &code, std::vector<int> &growth) {
     const DevPlan &dp = *dpp;
     const Plan &P = dp.plan;
@@ -448,8 +450,30 @@ int run_build(const gm_opts &o, const std::shared_ptr<DevPlan> &dpp, const doubl
         }
     }
 
-    // roots (Section 3.3 step 4): X = S_root^{-1} B for every problem in one sweep
     DBuf rws;
+    if (tol > 0.0) {
+        // HBS roots (Sections 4-5): compress every S_root and invert it by Algorithm 1;
+        // the solve applies Algorithm 2 (no dense T)
+        kt.begin(GM_K_ROOT, 0.0, s);
+        for (size_t i = 0; i < P.roots.size(); ++i) {
+            const RootDesc &r = P.roots[i];
+            gm_handle *h = H[r.problem];
+            const double *S64 = A64 + r.off;
+            DBuf conv;
+            if (mixed) {
+                if ((rc = conv.alloc((size_t)r.r * r.r * 8, s))) return rc;
+                CK(hbs_df32_to_f64(Adf + r.off, conv.as<double>(), (int64_t)r.r * r.r, s));
+                S64 = conv.as<double>();
+            }
+            h->hbs = new HbsRoot();
+            if ((rc = hbs_build_root(S64, r.r, r.n, o.hbs_leaf, tol, db + r.coef, dc + r.coef, dd + r.coef, s,
+                                     *h->hbs)))
+                return rc;
+            peak = std::max(peak, (int64_t)(arena_bytes + h->hbs->pool_doubles * 8));
+        }
+        kt.end(s);
+    } else {
+    // roots (Section 3.3 step 4): X = S_root^{-1} B for every problem in one sweep
     if ((rc = rws.alloc(dp.root_ws * 8, s))) return rc;
     peak = std::max(peak, (int64_t)(arena_bytes + dp.root_ws * 8));
     int max_r = 0, sum_rr = 0, sum_rc = 0;
@@ -490,6 +514,7 @@ int run_build(const gm_opts &o, const std::shared_ptr<DevPlan> &dpp, const doubl
             CK(mx_root_finalize(rws.as<float2>() + sy.off, r.r, r.n, h->T, h->Tdf, h->tdig, h->tex, split, s, kt));
         }
     }
+    }
     CK(cudaMemcpyAsync(hst.data(), stat.p, np * sizeof(Status), cudaMemcpyDeviceToHost, s));
     // release temporaries (stream-ordered) before the final synchronisation
     for (DBuf *b : {&rws, &piv, &u12, &perm, &perm_n, &a11, &fdig, &rdig, &fex, &rex, &ydig, &xdig, &yex, &xex, &bxd,
@@ -520,7 +545,12 @@ int run_build(const gm_opts &o, const std::shared_ptr<DevPlan> &dpp, const doubl
         gm_info_t hi = info;
         hi.n = h->n;
         hi.leaf = h->leaf;
-        hi.dtn_bytes = (long long)16 * h->n * h->n * 8;
+        hi.dtn_bytes = h->hbs ? 0 : (long long)16 * h->n * h->n * 8;
+        if (h->hbs) {
+            hi.hbs_levels = h->hbs->L;
+            hi.hbs_max_rank = h->hbs->max_rank;
+            hi.hbs_bytes = h->hbs->pool_doubles * 8;
+        }
         hi.min_pivot_ratio = mp / (4.0 * (h->n + 1.0) * (h->n + 1.0));
         hi.bad_stage = st.code ? st.where : -1;
         float rho;
@@ -546,8 +576,8 @@ gm_handle *new_handle(const std::pair<int, int> &p, int precision) {
 // Build with the automatic fallback; on failure every handle is freed.  With block
 // pivoting (the mixed-precision default), the problems whose build raised the growth
 // flag or met a singular pivot are built again, alone, in FP64.
-int build_with_fallback(const gm_opts &o, const std::vector<std::pair<int, int>> &probs, const double *db,
-                        const double *dc, const double *dd, std::vector<gm_handle *> &H) {
+int build_with_fallback(const gm_opts &o, double tol, const std::vector<std::pair<int, int>> &probs,
+                        const double *db, const double *dc, const double *dd, std::vector<gm_handle *> &H) {
     auto free_all = [&]() {
         for (gm_handle *h : H) gm_free(h);
         H.clear();
@@ -558,7 +588,7 @@ int build_with_fallback(const gm_opts &o, const std::vector<std::pair<int, int>>
     if (rc) return rc;
     for (const auto &p : probs) H.push_back(new_handle(p, o.precision));
     std::vector<int> code, growth;
-    rc = run_build(o, dp, db, dc, dd, H, code, growth);
+    rc = run_build(o, tol, dp, db, dc, dd, H, code, growth);
     if (o.precision == GM_PREC_MIXED && o.pivoting == GM_PIVOT_AUTO && (rc == GM_OK || rc == GM_ESINGULAR)) {
         std::vector<int> redo;
         for (size_t p = 0; p < probs.size(); ++p)
@@ -610,7 +640,7 @@ int build_with_fallback(const gm_opts &o, const std::vector<std::pair<int, int>>
             std::vector<gm_handle *> Hs;
             for (const auto &p : sub) Hs.push_back(new_handle(p, GM_PREC_FP64));
             std::vector<int> code2, growth2;
-            rc = run_build(o2, dps, sb, sc, sd, Hs, code2, growth2);
+            rc = run_build(o2, tol, dps, sb, sc, sd, Hs, code2, growth2);
             for (size_t q = 0; q < redo.size(); ++q) {
                 gm_free(H[redo[q]]);
                 H[redo[q]] = Hs[q];
@@ -630,6 +660,8 @@ int check_opts(const gm_opts *opts, gm_opts &o) {
     if (opts) o = *opts;
     if (o.precision != GM_PREC_FP64 && o.precision != GM_PREC_MIXED) return GM_EINVAL;
     if (o.pivoting < GM_PIVOT_AUTO || o.pivoting > GM_PIVOT_PARTIAL) return GM_EINVAL;
+    if (o.hbs_leaf == 0) o.hbs_leaf = 64;
+    if (o.hbs_leaf < 2 || o.hbs_leaf > 192) return GM_EINVAL;
     return GM_OK;
 }
 
@@ -664,6 +696,10 @@ void gm_free(gm_handle *h) {
     cudaFree(h->tdig);
     cudaFree(h->tex);
     for (void *p : h->kept_bufs) cudaFree(p);
+    if (h->hbs) {
+        gm::hbs_free(*h->hbs);
+        delete h->hbs;
+    }
     delete h;
 }
 
@@ -677,8 +713,7 @@ int gm_build_ex(const gm_opts *opts, const double *b, const double *c, const dou
                 gm_handle **out) {
     if (!out) return GM_EINVAL;
     *out = nullptr;
-    if (!b || !c || !d || n < 2 || leaf < 4 || tol < 0) return GM_EINVAL;
-    if (tol != 0.0) return GM_EUNSUPPORTED;
+    if (!b || !c || !d || n < 2 || leaf < 4 || !(tol >= 0.0)) return GM_EINVAL;
     gm_opts o;
     int rc = check_opts(opts, o);
     if (rc) return rc;
@@ -698,16 +733,15 @@ int gm_build_ex(const gm_opts *opts, const double *b, const double *c, const dou
         dd = base + 2 * N2;
     }
     std::vector<gm_handle *> H;
-    rc = build_with_fallback(o, {{n, leaf}}, db, dc, dd, H);
+    rc = build_with_fallback(o, tol, {{n, leaf}}, db, dc, dd, H);
     if (rc) return rc;
     *out = H[0];
     return GM_OK;
 }
 
 int gm_build_batch(int count, const gm_problem *probs, const gm_opts *opts, double tol, gm_handle **outs) {
-    if (count <= 0 || !probs || !outs || tol < 0) return GM_EINVAL;
+    if (count <= 0 || !probs || !outs || !(tol >= 0.0)) return GM_EINVAL;
     for (int i = 0; i < count; ++i) outs[i] = nullptr;
-    if (tol != 0.0) return GM_EUNSUPPORTED;
     std::vector<std::pair<int, int>> key;
     int64_t total = 0;
     for (int i = 0; i < count; ++i) {
@@ -734,7 +768,7 @@ int gm_build_batch(int count, const gm_problem *probs, const gm_opts *opts, doub
         off += (int64_t)probs[i].n * probs[i].n;
     }
     std::vector<gm_handle *> H;
-    rc = build_with_fallback(o, key, db, dc, dd, H);
+    rc = build_with_fallback(o, tol, key, db, dc, dd, H);
     if (rc) return rc;
     for (int i = 0; i < count; ++i) outs[i] = H[i];
     return GM_OK;
@@ -760,7 +794,10 @@ int gm_solve(gm_handle *h, const double *g, double *dudn, int batch, void *strea
         if (vbuf.alloc(bytes, s)) return GM_ENOMEM;
         dv = vbuf.as<double>();
     }
-    if (h->precision == GM_PREC_MIXED) {
+    if (h->hbs) {
+        const int rc = hbs_apply_dtn(*h->hbs, dg, dv, batch, s);
+        if (rc) return rc;
+    } else if (h->precision == GM_PREC_MIXED) {
         DBuf gdig, gex;
         if (gdig.alloc((size_t)h->split * batch * mx_kpad(N) * 2, s)) return GM_ENOMEM;
         if (gex.alloc((size_t)batch * sizeof(int), s)) return GM_ENOMEM;
@@ -779,6 +816,7 @@ int gm_solve(gm_handle *h, const double *g, double *dudn, int batch, void *strea
 
 int gm_get_dtn(gm_handle *h, double *T_out) {
     if (!h || !T_out) return GM_EINVAL;
+    if (h->hbs) return hbs_dense_dtn(*h->hbs, T_out, nullptr);
     size_t bytes = (size_t)16 * h->n * h->n * 8;
     CK(cudaMemcpy(T_out, h->T, bytes, cudaMemcpyDefault));
     return GM_OK;

@@ -59,7 +59,7 @@ extern "C" int gm_solve_static(gm_handle *h, const double *g, double *dudn, int 
     if (!g || !dudn) return GM_EINVAL;
     int n = 0;
     const double *T = gm::handle_dtn(h, &n);
-    if (!T) return GM_EINVAL;
+    if (!T) return GM_EUNSUPPORTED;  // an HBS build has no dense T
     const size_t N = 4 * (size_t)n, elems = N * (size_t)batch;
     const bool gd = on_device(g), vd = on_device(dudn);
     const size_t need = (gd ? 0 : elems) + (vd ? 0 : elems);

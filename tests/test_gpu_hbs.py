@@ -1,0 +1,129 @@
+"""HBS root on the GPU (rows a6, a8 and the HBS solve of a9): the root Schur complement
+compressed at tol, inverted by Algorithm 1, applied by Algorithm 2, against the dense
+FP64 oracle and the HBS oracle.  HBS parity is a tolerance, not bitwise: both sides
+truncate at tol (the GPU from randomized samples, the oracle from the full block rows),
+so each is within a small multiple of tol of the dense operator."""
+import numpy as np
+import pytest
+
+from oracle import hbs as ohbs
+from oracle import nd_dense
+from paper_1302_5995_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gm():
+    from paper_1302_5995_gb300 import build_ext
+    build_ext.build()
+    import paper_1302_5995_gb300 as gm
+    return gm
+
+
+def rel_mat(A, B):
+    return np.abs(A - B).max() / np.abs(B).max()
+
+
+def rel_vec(V, Vo):
+    return (np.linalg.norm(V - Vo, axis=0) / np.linalg.norm(Vo, axis=0)).max()
+
+
+def solve_cols(op, G):
+    B = G.shape[1]
+    return op.solve(np.ascontiguousarray(G.T)).reshape(B, G.shape[0]).T
+
+
+@pytest.mark.parametrize("fields,n,leaf,m", [("laplace", 64, 8, 32), ("convection", 128, 16, 32),
+                                             ("convection", 96, 12, 24)])
+def test_hbs_root_matches_dense_oracle(gm, fields, n, leaf, m):
+    tol = 1e-9
+    b, c, d = inputs.laplace_fields(n) if fields == "laplace" else inputs.convection_fields(n)
+    res = nd_dense.build(b, c, d, n, leaf)
+    op = gm.build(b, c, d, n, leaf, tol=tol, hbs_leaf=m)
+    info = op.info()
+    assert info["hbs_levels"] >= 1 and 0 < info["hbs_max_rank"] < m + 40
+    T = op.dtn()
+    assert rel_mat(T, res.T) < 100 * tol
+    G = inputs.gaussian_vectors(n, 16, 3)
+    V = solve_cols(op, G)
+    assert rel_vec(V, res.T @ G) < 100 * tol
+    # the oracle's own HBS solve is within the same bound of the dense one
+    Vh = ohbs.dtn_apply(nd_dense.Problem(b, c, d, n), res.S_root, tol, m, G)
+    assert rel_vec(V, Vh) < 200 * tol
+
+
+def test_hbs_ranks_track_the_oracle(gm):
+    """Leaf ranks from randomized samples agree with the oracle's pivoted-QR ranks of
+    the full off-diagonal block rows (within a couple, sampling noise at the cut)."""
+    n, leaf, m, tol = 128, 16, 32, 1e-9
+    b, c, d = inputs.convection_fields(n)
+    S = nd_dense.build(b, c, d, n, leaf).S_root
+    f = ohbs.compress(S, ohbs.HBSTree(S.shape[0], m), tol)
+    kmax_oracle = max(f.rank(t) for t in f.tree.rng if t >= 2)
+    op = gm.build(b, c, d, n, leaf, tol=tol, hbs_leaf=m)
+    assert abs(op.info()["hbs_max_rank"] - kmax_oracle) <= 3
+
+
+def test_hbs_tolerance_controls_error(gm):
+    n, leaf, m = 128, 16, 32
+    b, c, d = inputs.convection_fields(n, seeds=(4, 5, 6))
+    To = nd_dense.build(b, c, d, n, leaf).T
+    errs = {}
+    for tol in (1e-5, 1e-7, 1e-9):
+        op = gm.build(b, c, d, n, leaf, tol=tol, hbs_leaf=m)
+        errs[tol] = rel_mat(op.dtn(), To)
+        assert errs[tol] < 100 * tol, (tol, errs[tol])
+    assert errs[1e-9] < errs[1e-5]
+
+
+def test_hbs_root_on_mixed_build(gm):
+    n, leaf, m, tol = 256, 16, 64, 1e-9
+    b, c, d = inputs.convection_fields(n)
+    dense = gm.build(b, c, d, n, leaf)  # FP64 dense GPU build (parity-tested against the oracle)
+    op = gm.build(b, c, d, n, leaf, tol=tol, hbs_leaf=m, precision=gm.PREC_MIXED)
+    G = inputs.gaussian_vectors(n, 32, 9)
+    assert rel_vec(solve_cols(op, G), dense.dtn() @ G) < 100 * tol
+
+
+def test_hbs_full_size_1024_against_dense_gpu(gm):
+    """The 1024 x 1024 convection problem: HBS root vs the dense FP64 GPU build."""
+    import torch
+    n, leaf, m, tol = 1024, 16, 64, 1e-9
+    b, c, d = (torch.from_numpy(x).cuda() for x in inputs.convection_fields(n))
+    G = torch.from_numpy(inputs.gaussian_vectors(n, 16, 5)).cuda()
+    dense = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED)
+    op = gm.build(b, c, d, n, leaf, tol=tol, hbs_leaf=m, precision=gm.PREC_MIXED)
+    Gt = G.T.contiguous()
+    V1 = torch.empty_like(Gt)
+    V2 = torch.empty_like(Gt)
+    dense.solve(Gt, out=V1)
+    op.solve(Gt, out=V2)
+    torch.cuda.synchronize()
+    a, r = V2.cpu().numpy().T, V1.cpu().numpy().T
+    assert rel_vec(a, r) < 100 * tol
+    assert op.info()["hbs_max_rank"] < 96
+
+
+def test_hbs_batch(gm):
+    probs = [inputs.convection_fields(n, seeds=(n, n + 1, n + 2)) + (n, 16) for n in (96, 128)]
+    ops = gm.build_batch(probs, tol=1e-9)
+    for op, p in zip(ops, probs):
+        To = nd_dense.build(*p).T
+        assert rel_mat(op.dtn(), To) < 1e-7
+
+
+def test_hbs_rejects_what_it_cannot_do(gm):
+    # high-frequency Helmholtz: level-1 ranks above the sampling cap
+    n, leaf = 256, 16
+    b, c, d = inputs.helmholtz_fields(n, inputs.nudged_wavenumber(n, leaf))
+    with pytest.raises(gm.GmError) as e:
+        gm.build(b, c, d, n, leaf, tol=1e-9, hbs_leaf=64)
+    assert e.value.code == gm.GM_EUNSUPPORTED
+    # the no-allocation solve has no HBS form
+    b, c, d = inputs.laplace_fields(64)
+    op = gm.build(b, c, d, 64, 8, tol=1e-9, hbs_leaf=32)
+    lib = gm.load_library()
+    g = np.zeros(256)
+    out = np.zeros(256)
+    assert lib.gm_solve_static(op._h, g.ctypes.data, out.ctypes.data, 1, None) == gm.GM_EUNSUPPORTED

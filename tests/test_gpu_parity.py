@@ -158,9 +158,12 @@ def test_errors_are_reported(gm):
     with pytest.raises(gm.GmError) as e:
         gm.build(b, c, d, n, 3)
     assert e.value.code == gm.GM_EINVAL
-    with pytest.raises(gm.GmError) as e:
+    with pytest.raises(gm.GmError) as e:  # a 28-node root ring is one HBS node: nothing to compress
         gm.build(b, c, d, n, 4, tol=1e-9)
     assert e.value.code == gm.GM_EUNSUPPORTED
+    with pytest.raises(gm.GmError) as e:
+        gm.build(b, c, d, n, 4, tol=-1.0)
+    assert e.value.code == gm.GM_EINVAL
     with pytest.raises(gm.GmError) as e:
         gm.build(b[:1], c[:1], d[:1], 1, 4)
     assert e.value.code == gm.GM_EINVAL
