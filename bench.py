@@ -70,6 +70,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(t, world, device=None):
+    """The step time the job reports: the slowest rank's (all-reduce MAX); ranks are
+    independent replicas, so this is the only collective of the benchmark."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_value(units_per_rank, t_ms, world):
+    """Units all ranks processed (weak scaling: the same workload per rank) per second."""
+    return world * units_per_rank / (t_ms * 1e-3)
+
+
 def source_digest():
     import hashlib
     h = hashlib.sha1()
@@ -241,11 +258,7 @@ def run_gm(args):
         op.free()
     barrier()
     clk = clocks.stop()
-    t_step = statistics.mean(step_ms)
-    if world > 1:
-        tt = torch.tensor([t_step], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(statistics.mean(step_ms), world, dev)
     # accuracy of this run's result against the FP64 oracle (rank 0 only, after timing)
     result = {}
     if rank == 0:
@@ -303,7 +316,7 @@ def run_gm(args):
     traffic = tr[0] if (tr and tr[1] == source_digest()) else None
     sorted_ms = sorted(step_ms)
     line = {
-        "metric": METRIC, "value": world * n * n / (t_step * 1e-3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": whole_job_value(n * n, t_step, world), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "split-f64 (6 bf16 digits, df32 storage)" if args.precision == "mixed" else "f64",
         "data": "synthetic",
