@@ -176,7 +176,7 @@ __device__ __forceinline__ void col_exps64(const float2 *D, int *ex) {
 template <int S>
 __device__ __forceinline__ void gemm64_gd(const __nv_bfloat16 *__restrict__ adig, int64_t plane,
                                           const int *__restrict__ aex, const float2 *D, const int *exB,
-                                          __nv_bfloat16 *As, __nv_bfloat16 *Bs, float2 res[2][4][4]) {
+                                          __nv_bfloat16 *As, __nv_bfloat16 *Bs, float2 res[2][4][4], int kend = NBK) {
     const int tid = threadIdx.x, warp = tid >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
     float acc[S][2][4][4];
 #pragma unroll
@@ -188,7 +188,7 @@ __device__ __forceinline__ void gemm64_gd(const __nv_bfloat16 *__restrict__ adig
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[g][mt][nt][c] = 0.f;
 #pragma unroll 1
-    for (int t0 = 0; t0 < NBK; t0 += 16) {
+    for (int t0 = 0; t0 < kend; t0 += 16) {
         __syncthreads();
         load_digit_tile<S>(adig, plane, NBK, 0, 64, t0, As);
         for (int e = tid; e < 64 * 16; e += 128) {
@@ -281,54 +281,45 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
     col_exps64(Ad, exB);
     const __nv_bfloat16 *xd = x_dig + (int64_t)blockIdx.y * 64 * NBK, *ad = a11_dig + (int64_t)blockIdx.y * 64 * NBK;
     const int *xe = x_ex + blockIdx.y * 64, *ae = a11_ex + blockIdx.y * 64;
-    float2 res[2][4][4];
-    gemm64_gd<S>(xd, plane, xe, Ad, exB, As, Bs, res);  // R0 = X0 A12
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                int r, cl;
-                acc_pos(mt, nt, c, r, cl);
-                Rd[(wm + r) * LDF + wn + cl] = (wm + r < nbe) ? res[mt][nt][c] : make_float2(0.f, 0.f);
-            }
-    __syncthreads();
-    col_exps64(Rd, exB);
-    gemm64_gd<S>(ad, plane, ae, Rd, exB, As, Bs, res);  // A11 R0
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                int r, cl;
-                acc_pos(mt, nt, c, r, cl);
-                float2 *p = Ad + (wm + r) * LDF + wn + cl;
-                *p = (wm + r < nbe) ? df_sub(*p, res[mt][nt][c]) : make_float2(0.f, 0.f);  // E
-            }
-    __syncthreads();
-    col_exps64(Ad, exB);
     __shared__ int cmax[64], rmax[64];  // column maxima of |X0 E| and |R| (float bits, >= 0)
     if (tid < 64) cmax[tid] = rmax[tid] = 0;
-    gemm64_gd<S>(xd, plane, xe, Ad, exB, As, Bs, res);  // X0 E
+    // three dependent products through one (rolled) copy of the split-product body:
+    //   pass 0: R0 = X0 A12 -> Rd;  pass 1: E = A12 - A11 R0 -> Ad;  pass 2: R = R0 + X0 E
+#pragma unroll 1
+    for (int pass = 0; pass < 3; ++pass) {
+        float2 res[2][4][4];
+        // K = nbe: the operands are zero beyond the block's live columns
+        gemm64_gd<S>(pass == 1 ? ad : xd, plane, pass == 1 ? ae : xe, pass == 1 ? Rd : Ad, exB, As, Bs, res,
+                     (nbe + 15) & ~15);
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+        for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
+            for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                int r, cl;
-                acc_pos(mt, nt, c, r, cl);
-                const int t = wm + r, jj = wn + cl, j = j0 + jj;
-                float2 v = (t < nbe) ? df_add(Rd[t * LDF + jj], res[mt][nt][c]) : make_float2(0.f, 0.f);
-                Rd[t * LDF + jj] = v;
-                if (t < nbe && j < Sy.ncol) {
-                    W[(size_t)j * m + k + t] = v;
-                    atomicMax(&cmax[jj], __float_as_int(fabsf(res[mt][nt][c].x)));
-                    atomicMax(&rmax[jj], __float_as_int(fabsf(v.x)));
+                for (int c = 0; c < 4; ++c) {
+                    int r, cl;
+                    acc_pos(mt, nt, c, r, cl);
+                    const int t = wm + r, jj = wn + cl, j = j0 + jj;
+                    if (pass == 0) {
+                        Rd[t * LDF + jj] = (t < nbe) ? res[mt][nt][c] : make_float2(0.f, 0.f);
+                    } else if (pass == 1) {
+                        float2 *q = Ad + t * LDF + jj;
+                        *q = (t < nbe) ? df_sub(*q, res[mt][nt][c]) : make_float2(0.f, 0.f);
+                    } else {
+                        const float2 v = (t < nbe) ? df_add(Rd[t * LDF + jj], res[mt][nt][c]) : make_float2(0.f, 0.f);
+                        Rd[t * LDF + jj] = v;
+                        if (t < nbe && j < Sy.ncol) {
+                            W[(size_t)j * m + k + t] = v;
+                            atomicMax(&cmax[jj], __float_as_int(fabsf(res[mt][nt][c].x)));
+                            atomicMax(&rmax[jj], __float_as_int(fabsf(v.x)));
+                        }
+                    }
                 }
-            }
+        if (pass < 2) {
+            __syncthreads();
+            col_exps64(pass == 0 ? Rd : Ad, exB);  // column scales of the next product's right operand
+        }
+    }
     __syncthreads();
     // The refinement step leaves an error of about rho^2 |R|, where rho = |X0 E| / |R| is
     // its contraction factor (kappa(A11) times the FP32 accuracy of X0); the largest rho
@@ -412,7 +403,7 @@ k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, co
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[g][mt][nt][c] = 0.f;
 #pragma unroll 1
-    for (int kk = 0; kk < NBK; kk += 16) warp_mma_levels<S, KP64>(As + kk, Bs + kk, 64, 64, wm, wn, acc);
+    for (int kk = 0; kk < nbe; kk += 16) warp_mma_levels<S, KP64>(As + kk, Bs + kk, 64, 64, wm, wn, acc);
     const int *fe = fex + Sy.roff, *re = rex + Sy.coff;
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
