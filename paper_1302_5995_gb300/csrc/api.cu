@@ -80,6 +80,30 @@ struct DBuf {
     template <class T> T *as() const { return (T *)p; }
 };
 
+// Second stream and two events for the look-ahead of the blocked sweep (released on
+// scope exit, after the build has synchronised).
+struct LookAhead {
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~LookAhead() {
+        // destroyed before the scratch buffers declared ahead of it: nothing on the second
+        // stream may still read them when they are released (early error returns)
+        if (s2) cudaStreamSynchronize(s2);
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        if (s2) cudaStreamDestroy(s2);
+    }
+    bool create() {
+        if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return true;
+    }
+};
+
 // Device copy of a plan (cached per device and per list of (n, leaf)).
 struct DevStage {
     int orient, nm, max_m, max_ncol, max_rp;
@@ -365,6 +389,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
     DBuf bxd, bad, bxe, bae, bpmag, bfdig, bfex, brdig, brex;  // mixed, block pivoting
     MxScratch scr;
     BlkScratch bscr;
+    LookAhead la;
     if (!mixed) {
         if ((rc = piv.alloc((size_t)max_nm * piv_ld * sizeof(int), s))) return rc;
         if ((rc = u12.alloc((size_t)max_u12 * 8, s))) return rc;
@@ -391,6 +416,10 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             bscr.fex = bfex.as<int>();
             bscr.rdig = brdig.as<__nv_bfloat16>();
             bscr.rex = brex.as<int>();
+            if (!la.create()) return GM_ECUDA;
+            bscr.s2 = la.s2;
+            bscr.ev_r = la.a;
+            bscr.ev_rest = la.b;
         } else {
             if ((rc = perm.alloc((size_t)max_nm * 4 * GJ_MAX_NB * sizeof(int), s)) ||
                 (rc = perm_n.alloc((size_t)max_nm * sizeof(int), s)) ||

@@ -375,9 +375,9 @@ size_t blk_update_smem(int split) { return 2 * (size_t)split * 64 * KP64 * sizeo
 // arrive in one cp.async batch, then four k-steps of split products without barriers.
 template <int S>
 __global__ void __launch_bounds__(128)
-k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, const __nv_bfloat16 *__restrict__ fdig,
-             int64_t fplane, const int *__restrict__ fex, const __nv_bfloat16 *__restrict__ rdig, int64_t rplane,
-             const int *__restrict__ rex) {
+k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, int cb0,
+             const __nv_bfloat16 *__restrict__ fdig, int64_t fplane, const int *__restrict__ fex,
+             const __nv_bfloat16 *__restrict__ rdig, int64_t rplane, const int *__restrict__ rex) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __nv_bfloat16 *As = (__nv_bfloat16 *)smem_raw;  // [S][64][KP64]
     __nv_bfloat16 *Bs = As + S * 64 * KP64;
@@ -385,7 +385,7 @@ k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, co
     const int m = Sy.m;
     if (k >= m) return;
     const int nbe = min(NBK, m - k);
-    const int i0 = blockIdx.x * 64, j0 = k + nbe + blockIdx.y * 64;
+    const int i0 = blockIdx.x * 64, j0 = k + nbe + (blockIdx.y + cb0) * 64;
     if (i0 >= m || j0 >= Sy.ncol) return;
     float2 *W = ws + Sy.off;
     cp_async_digits64<S>(fdig + (int64_t)Sy.roff * NBK, fplane, i0, min(64, m - i0), As);
@@ -451,6 +451,7 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
     BLK_SPLIT_DISPATCH(split, (e = set_blk_attrs<SS>(split)));
     if (e != cudaSuccess) return e;
     const size_t fsm = blk_factor_smem(split), rsm = blk_rgemm_smem(split), usm = blk_update_smem(split);
+    bool pending = false;  // an update of the previous step still runs on the second stream
     for (int k = 0; k < max_m; k += NBK) {
         double fl_fac = 0, fl_r = 0, fl_upd = 0;
         for (const SysDesc &S : h_sys) {
@@ -467,17 +468,42 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
                                       d_sys, ws, k, scr.x_dig, scr.a11_dig, scr.inv_plane, scr.x_ex, scr.a11_ex,
                                       scr.pmag, st, stage)));
         kt.end(s);
+        if (pending) {
+            if ((e = cudaStreamWaitEvent(s, scr.ev_rest, 0)) != cudaSuccess) return e;
+            pending = false;
+        }
         kt.begin(GM_K_PIVROWS, fl_r, s);
         BLK_SPLIT_DISPATCH(split, (k_blk_rfused<SS><<<dim3(cb + rb, nsys), 128, rsm, s>>>(
                                       d_sys, ws, k, cb, scr.x_dig, scr.a11_dig, scr.inv_plane, scr.x_ex, scr.a11_ex,
                                       scr.fdig, scr.fplane, scr.fex, scr.rdig, scr.cplane, scr.rex, scr.pmag,
                                       st)));
         kt.end(s);
-        kt.begin(GM_K_GJUPDATE, fl_upd, s);
-        BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3((max_m + 63) / 64, (cols + 63) / 64, nsys), 128, usm, s>>>(
-                                      d_sys, ws, k, scr.fdig, scr.fplane, scr.fex, scr.rdig, scr.cplane, scr.rex)));
+        const dim3 gu((max_m + 63) / 64, (cols + 63) / 64, nsys);
+        if (!scr.s2 || gu.y < 2) {
+            kt.begin(GM_K_GJUPDATE, fl_upd, s);
+            BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<gu, 128, usm, s>>>(d_sys, ws, k, 0, scr.fdig, scr.fplane, scr.fex,
+                                                                           scr.rdig, scr.cplane, scr.rex)));
+            kt.end(s);
+            continue;
+        }
+        // look-ahead: the next block's 64 columns first (all the next factor reads), then
+        // the rest on the second stream, overlapping the next factor; the next R kernel
+        // waits for both (it rewrites the pivot rows the rest of this update touches)
+        const double fl_next = fl_upd / gu.y;
+        kt.begin(GM_K_GJUPDATE, fl_next, s);
+        BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(gu.x, 1, nsys), 128, usm, s>>>(
+                                      d_sys, ws, k, 0, scr.fdig, scr.fplane, scr.fex, scr.rdig, scr.cplane, scr.rex)));
         kt.end(s);
+        if ((e = cudaEventRecord(scr.ev_r, s)) != cudaSuccess || (e = cudaStreamWaitEvent(scr.s2, scr.ev_r, 0)))
+            return e;
+        kt.begin(GM_K_GJUPDATE, fl_upd - fl_next, scr.s2);
+        BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(gu.x, gu.y - 1, nsys), 128, usm, scr.s2>>>(
+                                      d_sys, ws, k, 1, scr.fdig, scr.fplane, scr.fex, scr.rdig, scr.cplane, scr.rex)));
+        kt.end(scr.s2);
+        if ((e = cudaEventRecord(scr.ev_rest, scr.s2)) != cudaSuccess) return e;
+        pending = true;
     }
+    if (pending && (e = cudaStreamWaitEvent(s, scr.ev_rest, 0)) != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -24,6 +24,8 @@ struct BlkScratch {
     int64_t cplane = 0;
     int *aex = nullptr, *r0ex = nullptr, *eex = nullptr, *rex = nullptr;
     float2 *r0 = nullptr;              // [sum cols][64]: first approximation of R
+    cudaStream_t s2 = nullptr;         // optional second stream for the look-ahead update
+    cudaEvent_t ev_r = nullptr, ev_rest = nullptr;
 };
 
 size_t blk_factor_smem(int split);
