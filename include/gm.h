@@ -125,6 +125,7 @@ typedef struct gm_info_t {
     int hbs_levels;                   /* tol > 0: levels L of the root's HBS tree          */
     int hbs_max_rank;                 /* tol > 0: largest node rank                        */
     long long hbs_bytes;              /* tol > 0: device bytes of the HBS factors          */
+    long long resident_bytes;         /* device bytes the handle holds after the build     */
 } gm_info_t;
 
 /* Fill *opts with defaults (FP64, no kept levels, default stream). */
@@ -211,6 +212,44 @@ int gm_get_schur(gm_handle *h, int x0, int y0, int a, int b, double *S_out);
 int gm_solve_static(gm_handle *h, const double *g, double *dudn, int batch, void *stream);
 
 int gm_info(gm_handle *h, gm_info_t *info);
+
+/*
+ * Serving (the solve stage under load; the paper has no serving layer).  A server owns
+ * the operators added to it and keeps them resident within a device-memory budget.  One
+ * worker thread with its own stream takes every request pending when it wakes, groups
+ * them by operator and runs one solve per operator over their concatenated vectors
+ * (continuous batching), then copies each request's result back.
+ *   gm_server_create : budget_bytes for the resident operators (gm_info.resident_bytes);
+ *                      batching = 0 serves every request by its own solve (the unbatched
+ *                      baseline).  Uses the current device.
+ *   gm_server_add    : takes ownership of h (freed on eviction or destroy) and returns
+ *                      its id.  Least recently used operators not being served are
+ *                      evicted to make room; GM_ENOMEM if it cannot fit.
+ *   gm_server_submit : queue dudn = T g for `batch` vectors (4n x batch column-major,
+ *                      host or device); returns at once.  g and dudn must stay valid
+ *                      until the request completes.  GM_EINVAL for an unknown operator.
+ *   gm_server_wait   : block until request req_id has completed; returns its result code
+ *                      (GM_EINVAL if its operator was evicted before it ran).
+ *   gm_server_sync   : block until nothing is queued or running.
+ *   gm_server_stats  : latency from submission to completion (p50/p99), vectors per
+ *                      second from the first submission to the last completion.
+ * Thread-safe: any thread may submit, add, wait or read statistics.
+ */
+typedef struct gm_server gm_server;
+typedef struct gm_server_stats_t {
+    long long requests, vectors, solves, evictions;
+    int resident_ops, pad;
+    long long resident_bytes;
+    double p50_ms, p99_ms, vectors_per_s;
+} gm_server_stats_t;
+int gm_server_create(long long budget_bytes, int batching, gm_server **out);
+int gm_server_add(gm_server *s, gm_handle *h, int *op_id);
+int gm_server_submit(gm_server *s, int op_id, const double *g, double *dudn, int batch, long long *req_id);
+int gm_server_wait(gm_server *s, long long req_id);
+int gm_server_sync(gm_server *s);
+int gm_server_stats(gm_server *s, gm_server_stats_t *st);
+int gm_server_reset_stats(gm_server *s);
+void gm_server_destroy(gm_server *s);
 
 /* Release the handle and its device memory.  NULL is a no-op. */
 void gm_free(gm_handle *h);

@@ -46,7 +46,14 @@ class Info(ctypes.Structure):
                 ("kernel_ms", ctypes.c_double * 7), ("kernel_flops", ctypes.c_double * 7),
                 ("kernel_launches", ctypes.c_int * 7), ("pivoting", ctypes.c_int),
                 ("pivot_fallback", ctypes.c_int), ("refine_ratio", ctypes.c_double), ("hbs_levels", ctypes.c_int),
-                ("hbs_max_rank", ctypes.c_int), ("hbs_bytes", ctypes.c_longlong)]
+                ("hbs_max_rank", ctypes.c_int), ("hbs_bytes", ctypes.c_longlong), ("resident_bytes", ctypes.c_longlong)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_longlong), ("vectors", ctypes.c_longlong), ("solves", ctypes.c_longlong),
+                ("evictions", ctypes.c_longlong), ("resident_ops", ctypes.c_int), ("pad", ctypes.c_int),
+                ("resident_bytes", ctypes.c_longlong), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("vectors_per_s", ctypes.c_double)]
 
 
 class Problem(ctypes.Structure):
@@ -70,6 +77,15 @@ SIGNATURES = {
                                        ctypes.c_void_p]),
     "gm_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Info)]),
     "gm_free": (None, [ctypes.c_void_p]),
+    "gm_server_create": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "gm_server_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "gm_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_longlong)]),
+    "gm_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
+    "gm_server_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "gm_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
+    "gm_server_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
+    "gm_server_destroy": (None, [ctypes.c_void_p]),
     "gm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -262,3 +278,67 @@ def build(b, c, d, n, leaf, tol=0.0, precision=PREC_FP64, keep_levels=False, str
     if rc:
         raise GmError(rc, "gm_build")
     return DtN(h, n, leaf)
+
+
+class Server:
+    """Serving runtime over resident operators (continuous batching on a worker thread).
+
+    add(op) transfers ownership of a DtN handle to the server; submit() queues a solve and
+    returns a request id; wait(id) blocks until it is done.  Buffers passed to submit()
+    must stay alive until the request completes (the server keeps references here)."""
+
+    def __init__(self, budget_bytes, batching=True):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        rc = lib.gm_server_create(int(budget_bytes), 1 if batching else 0, ctypes.byref(h))
+        if rc:
+            raise GmError(rc, "gm_server_create")
+        self._s = h
+        self._keep = {}
+
+    def add(self, op):
+        oid = ctypes.c_int()
+        rc = load_library().gm_server_add(self._s, op._h, ctypes.byref(oid))
+        if rc:
+            raise GmError(rc, "gm_server_add")
+        op._h = None  # owned by the server now
+        return oid.value
+
+    def submit(self, op_id, g, out, batch):
+        rid = ctypes.c_longlong()
+        rc = load_library().gm_server_submit(self._s, op_id, _ptr(g), _ptr(out), int(batch), ctypes.byref(rid))
+        if rc:
+            raise GmError(rc, "gm_server_submit")
+        self._keep[rid.value] = (g, out)
+        return rid.value
+
+    def wait(self, rid):
+        rc = load_library().gm_server_wait(self._s, rid)
+        self._keep.pop(rid, None)
+        return rc
+
+    def sync(self):
+        load_library().gm_server_sync(self._s)
+        self._keep.clear()
+
+    def stats(self):
+        st = ServerStats()
+        rc = load_library().gm_server_stats(self._s, ctypes.byref(st))
+        if rc:
+            raise GmError(rc, "gm_server_stats")
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_ if f != "pad"}
+
+    def reset_stats(self):
+        load_library().gm_server_reset_stats(self._s)
+
+    def close(self):
+        if self._s:
+            load_library().gm_server_destroy(self._s)
+            self._s = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

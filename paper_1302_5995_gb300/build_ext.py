@@ -51,7 +51,7 @@ def build(verbose=False):
                 print(err, file=sys.stderr)
     if not os.path.exists(OUT) or os.path.getmtime(OUT) < max(os.path.getmtime(o) for o in objs):
         tmp = OUT + f".{os.getpid()}.tmp"
-        cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
+        cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             raise RuntimeError(f"link failed:\n{p.stderr}")

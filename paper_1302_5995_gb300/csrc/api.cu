@@ -579,6 +579,11 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             hi.hbs_levels = h->hbs->L;
             hi.hbs_max_rank = h->hbs->max_rank;
             hi.hbs_bytes = h->hbs->pool_doubles * 8;
+            hi.resident_bytes = hi.hbs_bytes;
+        } else {
+            const long long N = 4LL * h->n;
+            hi.resident_bytes = N * N * 8;
+            if (mixed) hi.resident_bytes += N * N * 8 + (long long)split * N * mx_kpad((int)N) * 2 + N * 4;
         }
         hi.min_pivot_ratio = mp / (4.0 * (h->n + 1.0) * (h->n + 1.0));
         hi.bad_stage = st.code ? st.where : -1;
