@@ -351,6 +351,92 @@ def run_gm(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """Serving workload (solve stage under load): resident operators of mixed sizes and
+    fields, Poisson arrivals of requests with B ~ U{1..64} Gaussian vectors for a uniformly
+    chosen operator, at 0.25x, 0.5x and 0.9x the saturated batched rate; one new operator
+    built and added (evicting the least recently used) every `quota` submitted requests.
+    The same arrivals against the unbatched server (one solve per request) give the
+    baseline.  Prints one JSON line (not the headline metric)."""
+    import numpy as np
+    import torch
+    from paper_1302_5995_gb300 import build_ext, inputs
+    build_ext.build()
+    import paper_1302_5995_gb300 as gm
+
+    rng = np.random.default_rng(7)
+    sizes = [256, 384, 512, 768]
+    ks = {}
+
+    def fields(n, j):
+        if j % 2 == 0:
+            return inputs.convection_fields(n, seeds=(200 + 3 * j, 201 + 3 * j, 202 + 3 * j))
+        if n not in ks:
+            ks[n] = inputs.nudged_wavenumber(n, 16)
+        return inputs.helmholtz_fields(n, ks[n])
+
+    def make_op(j):
+        n = sizes[j % len(sizes)] if j < 8 else int(rng.choice(sizes))
+        b, c, d = (torch.from_numpy(x).cuda() for x in fields(n, j))
+        return gm.build(b, c, d, n, 16, precision=gm.PREC_MIXED), n
+
+    n_ops, quota, per_rate = 8, 150, args.serve_requests
+    vec_pool = {n: torch.from_numpy(inputs.gaussian_vectors(n, 64, 9 + n).T.copy()).pin_memory() for n in sizes}
+
+    def run(batching, rate_req_s):
+        built = [make_op(j) for j in range(n_ops)]
+        budget = sum(op.info()["resident_bytes"] for op, _ in built) + 1
+        srv = gm.Server(budget, batching=batching)
+        live = [(srv.add(op), n) for op, n in built]
+        outs = {n: torch.empty((64, 4 * n), dtype=torch.float64).pin_memory() for n in sizes}
+        ids = []
+        t0 = time.perf_counter()
+        t_next = 0.0
+        extra = n_ops
+        for q in range(per_rate):
+            if rate_req_s:
+                t_next += rng.exponential(1.0 / rate_req_s)
+                while time.perf_counter() - t0 < t_next:
+                    pass
+            k = int(rng.integers(0, len(live)))
+            oid, n = live[k]
+            B = int(rng.integers(1, 65))
+            try:
+                ids.append(srv.submit(oid, vec_pool[n], outs[n], B))
+            except gm.GmError:  # evicted meanwhile
+                pass
+            if (q + 1) % quota == 0:  # a new operator arrives; the LRU one is evicted
+                op, n2 = make_op(extra)
+                extra += 1
+                live.append((srv.add(op), n2))
+                st = srv.stats()
+                if st["evictions"]:
+                    live = live[-st["resident_ops"]:]
+        for rid in ids:
+            srv.wait(rid)
+        st = srv.stats()
+        srv.close()
+        return st
+
+    sat = run(True, 0.0)  # everything at once: the saturated batched throughput
+    mean_b = 32.5
+    sat_req = sat["vectors_per_s"] / mean_b
+    res = {"saturated": {"vectors_per_s": sat["vectors_per_s"], "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"]}}
+    for frac in (0.25, 0.5, 0.9):
+        rate = frac * sat_req
+        bt = run(True, rate)
+        ub = run(False, rate)
+        res[f"{frac}x"] = {"offered_req_s": rate,
+                           "batched": {k: bt[k] for k in ("p50_ms", "p99_ms", "vectors_per_s", "solves", "requests",
+                                                          "evictions")},
+                           "unbatched": {k: ub[k] for k in ("p50_ms", "p99_ms", "vectors_per_s", "solves", "requests",
+                                                            "evictions")}}
+    print(json.dumps({"workload": "serving", "operators": f"{n_ops} resident, n in {sizes}, convection / Helmholtz "
+                      "alternating, mixed precision (automatic FP64 fallback)",
+                      "requests_per_rate": per_rate, "vectors_per_request": "U{1..64}", "arrivals": "Poisson",
+                      "build_every": quota, "results": res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -358,7 +444,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gm", "reference"], default="gm")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--workload", choices=["build", "serving"], default="build",
+                    help="build: the headline build+solve step; serving: the serving workload (not the headline)")
+    ap.add_argument("--serve-requests", type=int, default=600)
     args = ap.parse_args()
+    if args.workload == "serving":
+        run_serving(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
