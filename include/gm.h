@@ -83,7 +83,11 @@ typedef struct gm_opts {
  *   GM_PIVOT_PARTIAL: partial pivoting over all remaining rows, 16-column panels.
  *   GM_PIVOT_BLOCK:   64-column blocks; pivots are chosen among the rows of the block
  *                     (its 64 x 64 pivot block is inverted with partial pivoting).
- *   GM_PIVOT_AUTO:    block pivoting, with a check per problem: if a row below some
+ *   GM_PIVOT_AUTO:    a problem whose reaction term makes the operator indefinite
+ *                     (d < -2 pi^2 everywhere, 2 pi^2 the smallest Dirichlet eigenvalue
+ *                     of -Laplace on the unit square) is built in FP64 from the start;
+ *                     the others
+ *                     use block pivoting, with a check per problem: if a row below some
  *                     block held an entry more than 16x that block column's pivot (partial
  *                     pivoting would have chosen differently), or if the one refinement
  *                     step of a block solve contracted by less than 2^13 (an ill-

@@ -8,6 +8,7 @@
 // memory comes from the stream-ordered allocator on the build stream.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -607,86 +608,143 @@ gm_handle *new_handle(const std::pair<int, int> &p, int precision) {
     return h;
 }
 
-// Build with the automatic fallback; on failure every handle is freed.  With block
-// pivoting (the mixed-precision default), the problems whose build raised the growth
-// flag or met a singular pivot are built again, alone, in FP64.
+// Largest reaction coefficient of each problem (coefficients concatenated, problem p at
+// off[p]): per-block maxima, reduced on the host.
+__global__ void k_max_d(const double *__restrict__ d, const int64_t *__restrict__ off, double *__restrict__ part) {
+    const int p = blockIdx.y;
+    const int64_t lo = off[p], hi = off[p + 1];
+    double v = -1e300;
+    for (int64_t e = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < hi; e += (int64_t)gridDim.x * blockDim.x)
+        v = fmax(v, d[e]);
+    __shared__ double sm[256];
+    sm[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(size_t)p * gridDim.x + blockIdx.x] = sm[0];
+}
+
+int max_reaction(const std::vector<std::pair<int, int>> &probs, const double *dd, cudaStream_t s,
+                 std::vector<double> &maxd) {
+    const int np = (int)probs.size(), nb = 32;
+    std::vector<int64_t> off(np + 1, 0);
+    for (int p = 0; p < np; ++p) off[p + 1] = off[p] + (int64_t)probs[p].first * probs[p].first;
+    DBuf doff, part;
+    int rc;
+    if ((rc = doff.alloc(off.size() * 8, s)) || (rc = part.alloc((size_t)np * nb * 8, s))) return rc;
+    CK(cudaMemcpyAsync(doff.p, off.data(), off.size() * 8, cudaMemcpyHostToDevice, s));
+    k_max_d<<<dim3(nb, np), 256, 0, s>>>(dd, doff.as<int64_t>(), part.as<double>());
+    CK(cudaGetLastError());
+    std::vector<double> h((size_t)np * nb);
+    CK(cudaMemcpyAsync(h.data(), part.p, h.size() * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    maxd.assign(np, -1e300);
+    for (int p = 0; p < np; ++p)
+        for (int b = 0; b < nb; ++b) maxd[p] = std::max(maxd[p], h[(size_t)p * nb + b]);
+    return GM_OK;
+}
+
+// Build the problems listed in `sub` (indices into probs; coefficients of problem p at
+// off[p] of db/dc/dd) as one batch with options o; Hs receives their handles.
+int build_subset(const gm_opts &o, double tol, const std::vector<std::pair<int, int>> &probs,
+                 const std::vector<int64_t> &off, const std::vector<int> &sub, const double *db, const double *dc,
+                 const double *dd, std::vector<gm_handle *> &Hs, std::vector<int> &code, std::vector<int> &growth) {
+    cudaStream_t s = (cudaStream_t)o.stream;
+    std::vector<std::pair<int, int>> keys;
+    int64_t total = 0;
+    for (int p : sub) {
+        keys.push_back(probs[p]);
+        total += (int64_t)probs[p].first * probs[p].first;
+    }
+    DBuf coef;
+    const double *sb = db, *sc = dc, *sd = dd;
+    int rc;
+    if (sub.size() != probs.size()) {  // the subset's coefficients, concatenated in subset order
+        if ((rc = coef.alloc(3 * (size_t)total * sizeof(double), s))) return rc;
+        double *b2 = coef.as<double>(), *c2 = b2 + total, *d2 = c2 + total;
+        int64_t at = 0;
+        for (int p : sub) {
+            const size_t bytes = (size_t)probs[p].first * probs[p].first * 8;
+            CK(cudaMemcpyAsync(b2 + at, db + off[p], bytes, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(c2 + at, dc + off[p], bytes, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(d2 + at, dd + off[p], bytes, cudaMemcpyDeviceToDevice, s));
+            at += (int64_t)probs[p].first * probs[p].first;
+        }
+        sb = b2;
+        sc = c2;
+        sd = d2;
+    }
+    std::shared_ptr<DevPlan> dp;
+    if ((rc = get_plan(keys, dp))) return rc;
+    for (const auto &k : keys) Hs.push_back(new_handle(k, o.precision));
+    return run_build(o, tol, dp, sb, sc, sd, Hs, code, growth);
+}
+
+// Build with the automatic fallback; on failure every handle is freed.  In the mixed-
+// precision default (block pivoting, GM_PIVOT_AUTO), problems whose reaction term makes
+// the operator indefinite -- d below -2 pi^2 everywhere: the first Dirichlet eigenfunction
+// of -Laplace on the unit square (eigenvalue 2 pi^2) then has a negative energy -- are
+// built in FP64 from the start, and the problems whose mixed build raised the growth
+// flag, refined too slowly or met a singular pivot are built again in FP64.
 int build_with_fallback(const gm_opts &o, double tol, const std::vector<std::pair<int, int>> &probs,
                         const double *db, const double *dc, const double *dd, std::vector<gm_handle *> &H) {
-    auto free_all = [&]() {
-        for (gm_handle *h : H) gm_free(h);
-        H.clear();
-    };
-    free_all();
-    std::shared_ptr<DevPlan> dp;
-    int rc = get_plan(probs, dp);
-    if (rc) return rc;
-    for (const auto &p : probs) H.push_back(new_handle(p, o.precision));
-    std::vector<int> code, growth;
-    rc = run_build(o, tol, dp, db, dc, dd, H, code, growth);
-    if (o.precision == GM_PREC_MIXED && o.pivoting == GM_PIVOT_AUTO && (rc == GM_OK || rc == GM_ESINGULAR)) {
-        std::vector<int> redo;
-        for (size_t p = 0; p < probs.size(); ++p)
-            if (growth[p] || code[p] == GM_ESINGULAR) redo.push_back((int)p);
-        if (!redo.empty()) {
-            // the mixed-precision build was not safe for these operators: redo them in FP64
-            gm_opts o2 = o;
-            o2.precision = GM_PREC_FP64;
-            o2.pivoting = GM_PIVOT_PARTIAL;
-            o2.panel_width = 0;
-            cudaStream_t s = (cudaStream_t)o.stream;
-            std::vector<std::pair<int, int>> sub;
-            std::vector<int64_t> off(probs.size() + 1, 0);
-            for (size_t p = 0; p < probs.size(); ++p) off[p + 1] = off[p] + (int64_t)probs[p].first * probs[p].first;
-            int64_t total = 0;
-            for (int p : redo) {
-                sub.push_back(probs[p]);
-                total += (int64_t)probs[p].first * probs[p].first;
+    for (gm_handle *h : H) gm_free(h);
+    H.assign(probs.size(), nullptr);
+    std::vector<int64_t> off(probs.size() + 1, 0);
+    for (size_t p = 0; p < probs.size(); ++p) off[p + 1] = off[p] + (int64_t)probs[p].first * probs[p].first;
+    const bool autom = o.precision == GM_PREC_MIXED && o.pivoting == GM_PIVOT_AUTO;
+    std::vector<int> mixed_set, fp64_set, all;
+    for (size_t p = 0; p < probs.size(); ++p) all.push_back((int)p);
+    int rc = GM_OK;
+    auto finish = [&](int r) {
+        if (r) {
+            cudaGetLastError();
+            for (gm_handle *&h : H) {
+                gm_free(h);
+                h = nullptr;
             }
-            // the subset's coefficients, concatenated in subset order
-            DBuf coef;
-            const double *sb = db, *sc = dc, *sd = dd;
-            if (redo.size() != probs.size()) {
-                if ((rc = coef.alloc(3 * (size_t)total * sizeof(double), s))) {
-                    free_all();
-                    return rc;
-                }
-                double *b2 = coef.as<double>(), *c2 = b2 + total, *d2 = c2 + total;
-                int64_t at = 0;
-                for (int p : redo) {
-                    const size_t bytes = (size_t)probs[p].first * probs[p].first * 8;
-                    if (cudaMemcpyAsync(b2 + at, db + off[p], bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-                        cudaMemcpyAsync(c2 + at, dc + off[p], bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-                        cudaMemcpyAsync(d2 + at, dd + off[p], bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
-                        free_all();
-                        return cuda_fail(cudaGetLastError(), "subset coefficient copy", __LINE__);
-                    }
-                    at += (int64_t)probs[p].first * probs[p].first;
-                }
-                sb = b2;
-                sc = c2;
-                sd = d2;
-            }
-            std::shared_ptr<DevPlan> dps;
-            if ((rc = get_plan(sub, dps))) {
-                free_all();
-                return rc;
-            }
-            std::vector<gm_handle *> Hs;
-            for (const auto &p : sub) Hs.push_back(new_handle(p, GM_PREC_FP64));
-            std::vector<int> code2, growth2;
-            rc = run_build(o2, tol, dps, sb, sc, sd, Hs, code2, growth2);
-            for (size_t q = 0; q < redo.size(); ++q) {
-                gm_free(H[redo[q]]);
-                H[redo[q]] = Hs[q];
-                Hs[q]->info.pivot_fallback = 1;
-            }
+            H.clear();
         }
+        return r;
+    };
+    if (autom) {
+        std::vector<double> maxd;
+        if ((rc = max_reaction(probs, dd, (cudaStream_t)o.stream, maxd))) return finish(rc);
+        const double lam1 = 2.0 * 3.14159265358979323846 * 3.14159265358979323846;
+        for (int p : all) (maxd[p] < -lam1 ? fp64_set : mixed_set).push_back(p);
+    } else {
+        mixed_set = all;  // "mixed" here means: as requested
     }
-    if (rc) {
-        cudaGetLastError();
-        free_all();
+    if (!mixed_set.empty()) {
+        std::vector<gm_handle *> Hs;
+        std::vector<int> code, growth;
+        rc = build_subset(o, tol, probs, off, mixed_set, db, dc, dd, Hs, code, growth);
+        for (size_t q = 0; q < Hs.size(); ++q) H[mixed_set[q]] = Hs[q];
+        if (rc && !(autom && rc == GM_ESINGULAR)) return finish(rc);
+        rc = GM_OK;
+        if (autom)
+            for (size_t q = 0; q < mixed_set.size(); ++q)
+                if (growth[q] || code[q] == GM_ESINGULAR) fp64_set.push_back(mixed_set[q]);
     }
-    return rc;
+    if (!fp64_set.empty()) {
+        std::sort(fp64_set.begin(), fp64_set.end());
+        gm_opts o2 = o;
+        o2.precision = GM_PREC_FP64;
+        o2.pivoting = GM_PIVOT_PARTIAL;
+        o2.panel_width = 0;
+        std::vector<gm_handle *> Hs;
+        std::vector<int> code, growth;
+        rc = build_subset(o2, tol, probs, off, fp64_set, db, dc, dd, Hs, code, growth);
+        for (size_t q = 0; q < Hs.size(); ++q) {
+            gm_free(H[fp64_set[q]]);
+            H[fp64_set[q]] = Hs[q];
+            Hs[q]->info.pivot_fallback = 1;
+        }
+        if (rc) return finish(rc);
+    }
+    return GM_OK;
 }
 
 int check_opts(const gm_opts *opts, gm_opts &o) {
