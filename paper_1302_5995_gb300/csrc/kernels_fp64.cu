@@ -88,7 +88,6 @@ k_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf0, cons
     int *piv = (int *)(X + (size_t)ni * nq);
     int *inner_id = piv + ni;            // ni
     int *inner_q = inner_id + ni;        // nq
-    __shared__ int s_p;
 
     auto gnode = [&](int ii, int jj) { return (Ld.x0 + 1 + ii) + n * (Ld.y0 + 1 + jj); };
 
@@ -115,6 +114,8 @@ k_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf0, cons
         }
         __syncthreads();
         // banded LU with partial pivoting (row interchanges limited to the band)
+        const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+        __shared__ int s_p;
         for (int k = 0; k < ni; ++k) {
             const int last = min(k + KL, ni - 1);
             const int cend = min(k + UW, ni - 1);
@@ -127,7 +128,12 @@ k_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf0, cons
                     int i2 = __shfl_down_sync(0xffffffffu, idx, o);
                     if (v2 > v || (v2 == v && i2 < idx)) { v = v2; idx = i2; }
                 }
-                if (tid == 0) { s_p = idx; piv[k] = idx; }
+                // a NaN column leaves no candidate: keep the diagonal (every access in bounds)
+                if (tid == 0) {
+                    if (idx < k || idx > last) idx = k;
+                    s_p = idx;
+                    piv[k] = idx;
+                }
             }
             __syncthreads();
             const int p = s_p;
@@ -151,45 +157,46 @@ k_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf0, cons
             }
             __syncthreads();
         }
-        // one unit right-hand side per inner-ring node (column t of X); both sweeps are
-        // column-oriented so that every step updates (row, right-hand side) pairs in parallel
+        // one unit right-hand side per inner-ring node (column t of X)
         for (int e = tid; e < ni * nq; e += nt) X[e] = 0.0;
         __syncthreads();
         for (int t = tid; t < nq; t += nt) X[(size_t)inner_q[t] * nq + t] = 1.0;
         __syncthreads();
-        for (int k = 0; k < ni; ++k) {  // forward: interchange, then eliminate below row k
-            const int p = piv[k];
-            if (p != k)
-                for (int t = tid; t < nq; t += nt) {
-                    double a = X[(size_t)k * nq + t];
+        // forward and backward sweeps: the right-hand sides are independent, so each warp
+        // owns up to 8 of them (lanes: 8 columns x 4 row slices) and syncs only itself
+        {
+            const int cpw = (nq + nwarp - 1) / nwarp;  // columns per warp (<= 8: nq <= 64)
+            const int cl = lane & 7, rs = lane >> 3;
+            const int t = warp * cpw + cl;
+            const bool on = cl < cpw && t < nq;
+            for (int k = 0; k < ni; ++k) {  // forward: interchange, then eliminate below row k
+                const int p = piv[k];
+                if (on && rs == 0 && p != k) {
+                    const double a0 = X[(size_t)k * nq + t];
                     X[(size_t)k * nq + t] = X[(size_t)p * nq + t];
-                    X[(size_t)p * nq + t] = a;
+                    X[(size_t)p * nq + t] = a0;
                 }
-            __syncthreads();
-            {  // thread -> right-hand side t = tid % 64, rows k+1+g, k+1+g+G, ...
-                const int t = tid & 63, g = tid >> 6, G = nt >> 6, last = min(k + KL, ni - 1);
-                if (t < nq) {
+                __syncwarp();
+                if (on) {
+                    const int last = min(k + KL, ni - 1);
                     const double xk = X[(size_t)k * nq + t];
-                    for (int rr = k + 1 + g; rr <= last; rr += G)
+                    for (int rr = k + 1 + rs; rr <= last; rr += 4)
                         X[(size_t)rr * nq + t] -= band[(size_t)rr * W + KL + k - rr] * xk;
                 }
+                __syncwarp();
             }
-            __syncthreads();
-        }
-        for (int k = ni - 1; k >= 0; --k) {  // backward: divide row k, eliminate above it
-            const double iukk = 1.0 / band[(size_t)k * W + KL];
-            for (int t = tid; t < nq; t += nt) X[(size_t)k * nq + t] *= iukk;
-            __syncthreads();
-            {
-                const int t = tid & 63, g = tid >> 6, G = nt >> 6, r0 = max(0, k - UW);
-                if (t < nq) {
+            for (int k = ni - 1; k >= 0; --k) {  // backward: divide row k, eliminate above it
+                if (on && rs == 0) X[(size_t)k * nq + t] *= 1.0 / band[(size_t)k * W + KL];
+                __syncwarp();
+                if (on) {
+                    const int r0 = max(0, k - UW);
                     const double xk = X[(size_t)k * nq + t];
-                    for (int rr = r0 + g; rr < k; rr += G)
-                        X[(size_t)rr * nq + t] -= band[(size_t)rr * W + KL + k - rr] * xk;
+                    for (int rr = r0 + rs; rr < k; rr += 4) X[(size_t)rr * nq + t] -= band[(size_t)rr * W + KL + k - rr] * xk;
                 }
+                __syncwarp();
             }
-            __syncthreads();
         }
+        __syncthreads();
     }
     // S[l, m] = A_bb[l, m] - w(l -> ql) (A_ii^{-1})[ql, qm] w(qm -> m)
     double *S = out + Ld.off;
