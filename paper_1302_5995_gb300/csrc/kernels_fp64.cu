@@ -116,9 +116,12 @@ k_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf0, cons
         // banded LU with partial pivoting (row interchanges limited to the band)
         const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
         __shared__ int s_p;
+        // Until the first row interchange every row r reaches at most column r + KL, so
+        // the elimination (and later the backward sweep) can stop there: diagonally
+        // dominant leaves never pay for the 2 KL fill that pivoting could create.
+        bool swapped = false;
         for (int k = 0; k < ni; ++k) {
             const int last = min(k + KL, ni - 1);
-            const int cend = min(k + UW, ni - 1);
             if (tid < 32) {
                 int rr = k + tid;
                 double v = (rr <= last) ? fabs(band[(size_t)rr * W + KL + k - rr]) : -1.0;
@@ -137,6 +140,8 @@ k_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf0, cons
             }
             __syncthreads();
             const int p = s_p;
+            swapped = swapped || p != k;
+            const int cend = min(k + (swapped ? UW : KL), ni - 1);
             if (p != k) {
                 for (int cc = k + tid; cc <= cend; cc += nt) {
                     double *x = &band[(size_t)k * W + KL + cc - k];
@@ -147,8 +152,10 @@ k_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf0, cons
             __syncthreads();
             const double pv = band[(size_t)k * W + KL];
             if (tid == 0) record_pivot(st + Ld.prob, pv, stage);
-            const double ipv = 1.0 / pv;
-            for (int rr = k + 1 + tid; rr <= last; rr += nt) band[(size_t)rr * W + KL + k - rr] *= ipv;
+            if (tid < last - k) {  // only the threads that scale divide (FP64 division is long)
+                const int rr = k + 1 + tid;
+                band[(size_t)rr * W + KL + k - rr] /= pv;
+            }
             __syncthreads();
             const int nr = last - k, ncn = cend - k;
             for (int e = tid; e < nr * ncn; e += nt) {
@@ -157,6 +164,9 @@ k_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf0, cons
             }
             __syncthreads();
         }
+        const int UWe = swapped ? UW : KL;  // upper bandwidth of U
+        double *idg = (double *)(inner_q + nq + (nq & 1));  // reciprocals of U's diagonal
+        for (int k = tid; k < ni; k += nt) idg[k] = 1.0 / band[(size_t)k * W + KL];
         // one unit right-hand side per inner-ring node (column t of X)
         for (int e = tid; e < ni * nq; e += nt) X[e] = 0.0;
         __syncthreads();
@@ -186,10 +196,10 @@ k_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf0, cons
                 __syncwarp();
             }
             for (int k = ni - 1; k >= 0; --k) {  // backward: divide row k, eliminate above it
-                if (on && rs == 0) X[(size_t)k * nq + t] *= 1.0 / band[(size_t)k * W + KL];
+                if (on && rs == 0) X[(size_t)k * nq + t] *= idg[k];
                 __syncwarp();
                 if (on) {
-                    const int r0 = max(0, k - UW);
+                    const int r0 = max(0, k - UWe);
                     const double xk = X[(size_t)k * nq + t];
                     for (int rr = r0 + rs; rr < k; rr += 4) X[(size_t)rr * nq + t] -= band[(size_t)rr * W + KL + k - rr] * xk;
                 }
@@ -243,7 +253,7 @@ size_t leaf_smem_bytes(int a, int b) {
     int nq = 0;
     if (ni > 0) nq = (ia == 1 || ib == 1) ? ni : 2 * ia + 2 * ib - 4;
     int W = 3 * (ia > 0 ? ia : 0) + 1;
-    return (size_t)ni * W * 8 + (size_t)ni * nq * 8 + (size_t)(2 * ni + nq) * 4 + 16;
+    return (size_t)ni * W * 8 + (size_t)ni * nq * 8 + (size_t)(2 * ni + nq + 1) * 4 + (size_t)ni * 8 + 16;
 }
 
 // ----------------------------------------------------------------------------- Gauss-Jordan sweep
