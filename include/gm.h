@@ -74,9 +74,11 @@ typedef struct gm_opts {
                          problem's conditioning, is not checked.                     */
     int pivoting;     /* GM_PREC_MIXED: GM_PIVOT_AUTO (default), GM_PIVOT_BLOCK or
                          GM_PIVOT_PARTIAL (see below); GM_PREC_FP64 always uses partial  */
-    int hbs_leaf;     /* tol > 0: node size m of the HBS tree over the root ring
-                         (0 = default 64; 2..192)                                       */
-    int reserved[4];
+    int hbs_leaf;     /* tol > 0: node size m of the HBS trees (0 = default 64; 2..192) */
+    int hbs_min_edge; /* tol > 0, FP64: pairwise merges whose shared edge has at least
+                         this many nodes solve their interface system by HBS block
+                         elimination (0 = default 128)                                  */
+    int reserved[3];
 } gm_opts;
 
 /* Pivoting of the mixed-precision dense eliminations.
@@ -130,6 +132,8 @@ typedef struct gm_info_t {
     int hbs_max_rank;                 /* tol > 0: largest node rank                        */
     long long hbs_bytes;              /* tol > 0: device bytes of the HBS factors          */
     long long resident_bytes;         /* device bytes the handle holds after the build     */
+    int hbs_merges;                   /* tol > 0: merges solved by HBS block elimination   */
+    int pad2;
 } gm_info_t;
 
 /* Fill *opts with defaults (FP64, no kept levels, default stream). */
@@ -142,12 +146,15 @@ void gm_opts_default(gm_opts *opts);
  *   leaf    : largest leaf-box edge (Section 2's N_leaf, as an edge): the tree has the
  *             smallest L with ceil(n / 2^L) <= leaf.  4 <= leaf <= 17 (the leaf kernel
  *             keeps a leaf's band and inner-ring solves in shared memory).
- *   tol     : 0 selects the all-dense build.  tol > 0 keeps the merges dense but
- *             compresses the root Schur complement to HBS form at local relative
- *             tolerance tol (Section 4; node size gm_opts.hbs_leaf) and inverts it by
- *             Algorithm 1 (Section 5); the solve then applies Algorithm 2 instead of a
- *             dense T.  GM_EUNSUPPORTED if a node's rank reaches 96 (the root does not
- *             compress enough; build with tol = 0).
+ *   tol     : 0 selects the all-dense build.  tol > 0 compresses the root Schur
+ *             complement to HBS form at local relative tolerance tol (Section 4; node
+ *             size gm_opts.hbs_leaf) and inverts it by Algorithm 1 (Section 5); the
+ *             solve then applies Algorithm 2 instead of a dense T.  In FP64 builds the
+ *             pairwise merges with a shared edge of at least gm_opts.hbs_min_edge nodes
+ *             solve their interface system by the accelerated Step 1 (HBS inverses of
+ *             S33 and of its Schur complement; merges whose ranks exceed the cap stay
+ *             dense).  GM_EUNSUPPORTED if a root node's rank reaches 96 (the root does
+ *             not compress enough; build with tol = 0).
  *   out     : receives a new handle that owns all device memory of the operator.
  * Blocks the calling thread until the build has finished on the device.
  */

@@ -247,3 +247,34 @@ def dtn_apply(prob, S_root, tol, m, G):
     inv = invert(compress(S_root, tree, tol))
     G = np.asarray(G, dtype=np.float64).reshape(4 * n, -1)
     return (G - Pm @ apply_inverse(inv, Bm @ G)) / h
+
+
+def step1_interface_solver(tol: float, m: int):
+    """The accelerated merge's Step 1 (Section 5, "Accelerating the nested dissection
+    algorithm"): [S33 A34; A43 S44]^{-1} Z by block elimination, S33 and the Schur
+    complement S44 - A43 S33^{-1} A34 each compressed at tol and inverted by Algorithms
+    1 and 2:
+        X4 = (S44 - A43 S33^{-1} A34)^{-1} (Z4 - A43 S33^{-1} Z3),
+        X3 = S33^{-1} Z3 - S33^{-1} A34 X4.
+    The Schur complement is formed densely and recompressed (the paper's fast HBS
+    addition is deferred to a reference; dense recompression is the reading here)."""
+
+    def inv_apply(A):
+        t = HBSTree(A.shape[0], m)
+        if t.L == 0:
+            return lambda X: np.linalg.solve(A, X)
+        inv = invert(compress(A, t, tol))
+        return lambda X: apply_inverse(inv, X)
+
+    def solve(S33, A34, A43, S44, Z):
+        s3 = S33.shape[0]
+        Z3, Z4 = Z[:s3], Z[s3:]
+        i33 = inv_apply(S33)
+        W3 = i33(Z3)
+        V3 = i33(A34)
+        i44 = inv_apply(S44 - A43 @ V3)
+        X4 = i44(Z4 - A43 @ W3)
+        X3 = W3 - V3 @ X4
+        return np.vstack([X3, X4])
+
+    return solve

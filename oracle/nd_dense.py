@@ -140,12 +140,14 @@ def leaf_schur(prob: Problem, box: Box):
     return A_bb - A_bi @ np.linalg.solve(A_ii, A_ib)
 
 
-def merge_two(prob: Problem, box1: Box, S1, box2: Box, S2, parent: Box):
+def merge_two(prob: Problem, box1: Box, S1, box2: Box, S2, parent: Box, interface_solve=None):
     """Eq. S_fromtwo_nd for two sibling rectangles whose union is `parent`.
 
     box1 is the west (or south) sibling and box2 the east (or north) one.  P1/P2 are
     the nodes of each child's ring that lie on the parent's ring, P3/P4 the ones that
     become interior (eq. partition_we).  Returns the parent's S in its ring order.
+    interface_solve(S33, A34, A43, S44, Z) -> [S33 A34; A43 S44]^{-1} Z replaces the
+    dense solve when given (the HBS Step 1 of the accelerated method).
     """
     r1, r2, rp = box1.ring(), box2.ring(), parent.ring()
     on_parent = set(rp)
@@ -172,7 +174,9 @@ def merge_two(prob: Problem, box1: Box, S1, box2: Box, S2, parent: Box):
     left = np.block([[S13, A14], [A23, S24]])
     mid = np.block([[S33, A34], [A43, S44]])
     right = np.block([[S31, A32], [A41, S42]])
-    if mid.shape[0]:
+    if mid.shape[0] and interface_solve is not None:
+        S = outer - left @ interface_solve(S33, A34, A43, S44, right)
+    elif mid.shape[0]:
         S = outer - left @ np.linalg.solve(mid, right)
     else:
         S = outer
@@ -184,15 +188,21 @@ def merge_two(prob: Problem, box1: Box, S1, box2: Box, S2, parent: Box):
     return out
 
 
-def merge_four(prob: Problem, parent: Box, S_children):
-    """Section 3.3 step 3: a four-child merge as three pairwise merges."""
+def merge_four(prob: Problem, parent: Box, S_children, interface_solve=None, min_edge=None):
+    """Section 3.3 step 3: a four-child merge as three pairwise merges.  With
+    interface_solve, merges whose shared edge has >= min_edge nodes use it."""
     sw, se, nw, ne = parent.children()
     S_sw, S_se, S_nw, S_ne = S_children
     south = Box(parent.x0, parent.y0, parent.a, sw.b)
     north = Box(parent.x0, parent.y0 + sw.b, parent.a, nw.b)
-    S_south = merge_two(prob, sw, S_sw, se, S_se, south)
-    S_north = merge_two(prob, nw, S_nw, ne, S_ne, north)
-    return merge_two(prob, south, S_south, north, S_north, parent), (south, S_south, north, S_north)
+
+    def pick(edge):
+        return interface_solve if interface_solve is not None and edge >= min_edge else None
+
+    S_south = merge_two(prob, sw, S_sw, se, S_se, south, pick(sw.b))
+    S_north = merge_two(prob, nw, S_nw, ne, S_ne, north, pick(nw.b))
+    S = merge_two(prob, south, S_south, north, S_north, parent, pick(parent.a))
+    return S, (south, S_south, north, S_north)
 
 
 def ghost_map(prob: Problem):
@@ -235,8 +245,10 @@ class BuildResult:
     S_root: np.ndarray = None  # the root Schur complement (ring of the whole grid)
 
 
-def build(b, c, d, n, leaf, keep=False):
-    """Full dense build (Section 3.3 steps 1-4).  Returns the 4n x 4n DtN matrix T."""
+def build(b, c, d, n, leaf, keep=False, interface_solve=None, min_edge=None):
+    """Full dense build (Section 3.3 steps 1-4).  Returns the 4n x 4n DtN matrix T.
+    interface_solve / min_edge: the merges whose shared edge has >= min_edge nodes solve
+    their interface system with interface_solve (see merge_two)."""
     prob = Problem(b, c, d, n)
     levels = quad_tree(n, leaf)
     L = len(levels) - 1
@@ -253,7 +265,7 @@ def build(b, c, d, n, leaf, keep=False):
         nxt = {}
         for parent in levels[lev - 1]:
             kids = parent.children()
-            Sp, halves = merge_four(prob, parent, [S[k] for k in kids])
+            Sp, halves = merge_four(prob, parent, [S[k] for k in kids], interface_solve, min_edge)
             nxt[parent] = Sp
             if keep:
                 kept[halves[0]] = halves[1]

@@ -33,7 +33,8 @@ class GmError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("keep_levels", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("panel_width", ctypes.c_int), ("timing", ctypes.c_int), ("split_digits", ctypes.c_int),
-                ("pivoting", ctypes.c_int), ("hbs_leaf", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("pivoting", ctypes.c_int), ("hbs_leaf", ctypes.c_int), ("hbs_min_edge", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 K_FAMILIES = ["leaf", "assemble", "panel", "pivrows", "gj_update", "merge_update", "root"]
 
@@ -46,7 +47,8 @@ class Info(ctypes.Structure):
                 ("kernel_ms", ctypes.c_double * 7), ("kernel_flops", ctypes.c_double * 7),
                 ("kernel_launches", ctypes.c_int * 7), ("pivoting", ctypes.c_int),
                 ("pivot_fallback", ctypes.c_int), ("refine_ratio", ctypes.c_double), ("hbs_levels", ctypes.c_int),
-                ("hbs_max_rank", ctypes.c_int), ("hbs_bytes", ctypes.c_longlong), ("resident_bytes", ctypes.c_longlong)]
+                ("hbs_max_rank", ctypes.c_int), ("hbs_bytes", ctypes.c_longlong), ("resident_bytes", ctypes.c_longlong),
+                ("hbs_merges", ctypes.c_int), ("pad2", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -227,7 +229,7 @@ class DtN:
         return out
 
 
-def _opts(precision, keep_levels, stream, panel_width, timing, split_digits, pivoting, hbs_leaf=0):
+def _opts(precision, keep_levels, stream, panel_width, timing, split_digits, pivoting, hbs_leaf=0, hbs_min_edge=0):
     lib = load_library()
     o = Opts()
     lib.gm_opts_default(ctypes.byref(o))
@@ -239,6 +241,7 @@ def _opts(precision, keep_levels, stream, panel_width, timing, split_digits, piv
     o.split_digits = split_digits
     o.pivoting = pivoting
     o.hbs_leaf = hbs_leaf
+    o.hbs_min_edge = hbs_min_edge
     return o
 
 
@@ -263,7 +266,7 @@ def build_batch(problems, tol=0.0, precision=PREC_FP64, stream=None, panel_width
 
 
 def build(b, c, d, n, leaf, tol=0.0, precision=PREC_FP64, keep_levels=False, stream=None, panel_width=0,
-          timing=False, split_digits=0, pivoting=PIVOT_AUTO, hbs_leaf=0):
+          timing=False, split_digits=0, pivoting=PIVOT_AUTO, hbs_leaf=0, hbs_min_edge=0):
     """Build the DtN operator for coefficient fields b, c, d (n*n each, index i + n*j).
 
     tol > 0 compresses the root Schur complement to HBS form (node size hbs_leaf) and
@@ -272,7 +275,7 @@ def build(b, c, d, n, leaf, tol=0.0, precision=PREC_FP64, keep_levels=False, str
     b = _check_f64(b, "b", n * n)
     c = _check_f64(c, "c", n * n)
     d = _check_f64(d, "d", n * n)
-    o = _opts(precision, keep_levels, stream, panel_width, timing, split_digits, pivoting, hbs_leaf)
+    o = _opts(precision, keep_levels, stream, panel_width, timing, split_digits, pivoting, hbs_leaf, hbs_min_edge)
     h = ctypes.c_void_p()
     rc = lib.gm_build_ex(ctypes.byref(o), _ptr(b), _ptr(c), _ptr(d), n, leaf, float(tol), ctypes.byref(h))
     if rc:

@@ -323,6 +323,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
         h->kept_df32 = mixed;
     }
     int rc;
+    int hbs_merges = 0, hbs_rank = 0;
     const size_t np = H.size();
     DBuf stat;
     if ((rc = stat.alloc(np * sizeof(Status), s))) return rc;
@@ -467,7 +468,44 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
         if (!mixed) {
             CK(launch_merge_assemble(ds.d_merges, ds.nm, ds.d_tab, A64, ws.as<double>(), ds.max_elems, db, dc, dd, 0,
                                      s, kt));
-            CK(sweep(ds.d_sys, ds.h_sys, ds.max_m, ds.max_ncol, ws.p, ds.sum_rows, ds.sum_cols, (int)si + 1));
+            // tol > 0: merges whose shared edge has at least hbs_min_edge nodes solve their
+            // interface system by the accelerated Step 1 (HBS inverses of S33 and of its
+            // Schur complement); the others, and any whose ranks exceed the cap, stay dense
+            std::vector<SysDesc> dense;
+            bool any_hbs = false;
+            for (int i = 0; i < ds.nm; ++i) {
+                const MergeDesc &md = hs.merges[i];
+                if (tol > 0.0 && md.sp + 2 >= o.hbs_min_edge && md.sp > o.hbs_leaf) {
+                    kt.begin(GM_K_PANEL, 0.0, s);
+                    rc = hbs_block_solve(ws.as<double>() + ds.h_sys[i].off, md.sp, md.rp, o.hbs_leaf, tol, s,
+                                         &hbs_rank);
+                    kt.end(s);
+                    if (rc == GM_OK) {
+                        ++hbs_merges;
+                        any_hbs = true;
+                        continue;
+                    }
+                    if (rc != GM_EUNSUPPORTED) return rc;
+                }
+                dense.push_back(ds.h_sys[i]);
+            }
+            if (!any_hbs) {
+                CK(sweep(ds.d_sys, ds.h_sys, ds.max_m, ds.max_ncol, ws.p, ds.sum_rows, ds.sum_cols, (int)si + 1));
+            } else if (!dense.empty()) {
+                int ro = 0, co = 0, mm = 0, mc = 0;
+                for (SysDesc &q : dense) {
+                    q.roff = ro;
+                    q.coff = co;
+                    ro += q.m;
+                    co += q.ncol;
+                    mm = std::max(mm, q.m);
+                    mc = std::max(mc, q.ncol);
+                }
+                DBuf dsub;
+                if ((rc = dsub.alloc(dense.size() * sizeof(SysDesc), s))) return rc;
+                CK(cudaMemcpyAsync(dsub.p, dense.data(), dense.size() * sizeof(SysDesc), cudaMemcpyHostToDevice, s));
+                CK(sweep(dsub.as<SysDesc>(), dense, mm, mc, ws.p, ro, co, (int)si + 1));
+            }
             CK(launch_merge_update(ds.d_merges, hs.merges, ds.d_tab, A64, ws.as<double>(), A64, ds.max_rp, db, dc, dd,
                                    0, s, kt));
         } else {
@@ -576,9 +614,11 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
         hi.n = h->n;
         hi.leaf = h->leaf;
         hi.dtn_bytes = h->hbs ? 0 : (long long)16 * h->n * h->n * 8;
+        hi.hbs_merges = hbs_merges;
+        hi.hbs_max_rank = hbs_rank;
         if (h->hbs) {
             hi.hbs_levels = h->hbs->L;
-            hi.hbs_max_rank = h->hbs->max_rank;
+            hi.hbs_max_rank = std::max(hbs_rank, h->hbs->max_rank);
             hi.hbs_bytes = h->hbs->pool_doubles * 8;
             hi.resident_bytes = hi.hbs_bytes;
         } else {
@@ -754,6 +794,8 @@ int check_opts(const gm_opts *opts, gm_opts &o) {
     if (o.pivoting < GM_PIVOT_AUTO || o.pivoting > GM_PIVOT_PARTIAL) return GM_EINVAL;
     if (o.hbs_leaf == 0) o.hbs_leaf = 64;
     if (o.hbs_leaf < 2 || o.hbs_leaf > 192) return GM_EINVAL;
+    if (o.hbs_min_edge == 0) o.hbs_min_edge = 128;
+    if (o.hbs_min_edge < 4) return GM_EINVAL;
     return GM_OK;
 }
 

@@ -457,12 +457,10 @@ int invert_batch(const std::vector<std::pair<double *, int>> &mats, double *base
 
 }  // namespace
 
-int hbs_build_root(const double *S, int r, int n, int m, double tol, const double *bf, const double *cf,
-                   const double *df, cudaStream_t s, HbsRoot &H) {
-    if (r < 2 || m < 2 || m > QR_MAXP || !(tol > 0.0)) return GM_EINVAL;
+int hbs_factor(const double *S, int lds, int r, int m, double tol, cudaStream_t s, HbsRoot &H) {
+    if (r < 2 || lds < r || m < 2 || m > QR_MAXP || !(tol > 0.0)) return GM_EINVAL;
     const int l = HBS_SAMPLES, KC = HBS_KCAP;
     H.r = r;
-    H.n = n;
     H.m = m;
     H.tol = tol;
     int L = 0;
@@ -545,8 +543,8 @@ int hbs_build_root(const double *S, int r, int n, int m, double tol, const doubl
     k_hbs_normals<<<256, 256, 0, s>>>(P + oOm, (int64_t)r * l, 0x4842530000000001ull);
     k_hbs_normals<<<256, 256, 0, s>>>(P + oPs, (int64_t)r * l, 0x4842530000000002ull);
     HCK(cudaGetLastError());
-    if ((rc = run_gemms({gd(S, r, 0, P + oOm, r, 0, P + oY, r, r, l, r, 1.0, 0.0),
-                         gd(S, r, 1, P + oPs, r, 0, P + oZ, r, r, l, r, 1.0, 0.0)},
+    if ((rc = run_gemms({gd(S, lds, 0, P + oOm, r, 0, P + oY, r, r, l, r, 1.0, 0.0),
+                         gd(S, lds, 1, P + oPs, r, 0, P + oZ, r, r, l, r, 1.0, 0.0)},
                         db, s)))
         return rc;
 
@@ -585,11 +583,11 @@ int hbs_build_root(const double *S, int r, int n, int m, double tol, const doubl
         std::vector<int> nodes, prow;
         for (int t = 1 << L; t < NN; ++t) {
             const int lo = H.lo[t], p = sz(t);
-            const double *Sd = S + lo + (size_t)lo * r;
+            const double *Sd = S + lo + (size_t)lo * lds;
             cp.push_back(cpd(P + oY + lo, r, P + oYs[t], p, p, l, 0));
             cp.push_back(cpd(P + oZ + lo, r, P + oZs[t], p, p, l, 0));
-            g.push_back(gd(Sd, r, 0, P + oOm + lo, r, 0, P + oYs[t], p, p, l, p, -1.0, 1.0));
-            g.push_back(gd(Sd, r, 1, P + oPs + lo, r, 0, P + oZs[t], p, p, l, p, -1.0, 1.0));
+            g.push_back(gd(Sd, lds, 0, P + oOm + lo, r, 0, P + oYs[t], p, p, l, p, -1.0, 1.0));
+            g.push_back(gd(Sd, lds, 1, P + oPs + lo, r, 0, P + oZs[t], p, p, l, p, -1.0, 1.0));
             nodes.push_back(t);
             prow.push_back(p);
         }
@@ -610,13 +608,13 @@ int hbs_build_root(const double *S, int r, int n, int m, double tol, const doubl
         for (int t = 1 << lev; t < (2 << lev); ++t) {
             const int a = 2 * t, b = 2 * t + 1, ka = H.k[a], kb = H.k[b];
             const int sa = sz(a), sb = sz(b);
-            const double *Sab = S + H.lo[a] + (size_t)H.lo[b] * r, *Sba = S + H.lo[b] + (size_t)H.lo[a] * r;
+            const double *Sab = S + H.lo[a] + (size_t)H.lo[b] * lds, *Sba = S + H.lo[b] + (size_t)H.lo[a] * lds;
             // W_ab = Uf_a^T S(I_a, I_b), W_ba = Uf_b^T S(I_b, I_a)
-            g1.push_back(gd(P + oUf[a], sa, 1, Sab, r, 0, P + oWab[t], std::max(ka, 1), ka, sb, sa, 1.0, 0.0));
-            g1.push_back(gd(P + oUf[b], sb, 1, Sba, r, 0, P + oWba[t], std::max(kb, 1), kb, sa, sb, 1.0, 0.0));
+            g1.push_back(gd(P + oUf[a], sa, 1, Sab, lds, 0, P + oWab[t], std::max(ka, 1), ka, sb, sa, 1.0, 0.0));
+            g1.push_back(gd(P + oUf[b], sb, 1, Sba, lds, 0, P + oWba[t], std::max(kb, 1), kb, sa, sb, 1.0, 0.0));
             // X_ab = S(I_a, I_b) Vf_b, X_ba = S(I_b, I_a) Vf_a
-            g1.push_back(gd(Sab, r, 0, P + oVf[b], sb, 0, P + oXab[t], sa, sa, kb, sb, 1.0, 0.0));
-            g1.push_back(gd(Sba, r, 0, P + oVf[a], sa, 0, P + oXba[t], sb, sb, ka, sa, 1.0, 0.0));
+            g1.push_back(gd(Sab, lds, 0, P + oVf[b], sb, 0, P + oXab[t], sa, sa, kb, sb, 1.0, 0.0));
+            g1.push_back(gd(Sba, lds, 0, P + oVf[a], sa, 0, P + oXba[t], sb, sb, ka, sa, 1.0, 0.0));
             // B_tau blocks: H_ab = W_ab Vf_b, H_ba = W_ba Vf_a
             g2.push_back(gd(P + oWab[t], std::max(ka, 1), 0, P + oVf[b], sb, 0, P + oHab[t], std::max(ka, 1), ka, kb,
                             sb, 1.0, 0.0));
@@ -672,7 +670,7 @@ int hbs_build_root(const double *S, int r, int n, int m, double tol, const doubl
             const int q = rows_of(t);
             double *Dq = P + oD[t];  // [D~ | I], q x 2q, ld q
             if (leaf(t)) {
-                cp.push_back(cpd(S + H.lo[t] + (size_t)H.lo[t] * r, r, Dq, q, q, q, 0));
+                cp.push_back(cpd(S + H.lo[t] + (size_t)H.lo[t] * lds, lds, Dq, q, q, q, 0));
             } else {
                 const int a = 2 * t, b = 2 * t + 1, ka = H.k[a], kb = H.k[b];
                 const double *Dha = P + oX[a] + (size_t)ka * ka, *Dhb = P + oX[b] + (size_t)kb * kb;
@@ -735,22 +733,30 @@ int hbs_build_root(const double *S, int r, int n, int m, double tol, const doubl
                                  cpd(nullptr, 1, Dq + (size_t)q * q, q, q, q, 1)};
         if ((rc = run_copies(cp, db, s)) || (rc = invert_batch({{Dq, q}}, P, s))) return rc;
     }
-    // coupling table for the solve
-    k_hbs_couple<<<(r + 255) / 256, 256, 0, s>>>(n, bf, cf, df, (int *)(P + oKK), P + oWW);
-    HCK(cudaGetLastError());
     H.offKK = oKK;
     H.offWW = oWW;
     HCK(cudaStreamSynchronize(s));
     return GM_OK;
 }
 
-int hbs_apply_dtn(HbsRoot &H, const double *g, double *dudn, int B, cudaStream_t s) {
+int hbs_build_root(const double *S, int r, int n, int m, double tol, const double *bf, const double *cf,
+                   const double *df, cudaStream_t s, HbsRoot &H) {
+    int rc = hbs_factor(S, r, r, m, tol, s, H);
+    if (rc) return rc;
+    H.n = n;
+    // coupling table for the solve
+    k_hbs_couple<<<(r + 255) / 256, 256, 0, s>>>(n, bf, cf, df, (int *)(H.pool + H.offKK), H.pool + H.offWW);
+    HCK(cudaGetLastError());
+    HCK(cudaStreamSynchronize(s));
+    return GM_OK;
+}
+
+int hbs_solve(HbsRoot &H, const double *X, int ldx, double *Y, int ldy, int B, cudaStream_t s) {
     if (B <= 0) return GM_OK;
-    const int L = H.L, r = H.r, n = H.n, NN = 1 << (L + 1);
+    const int L = H.L, NN = 1 << (L + 1);
     auto leaf = [&](int t) { return t >= (1 << L); };
-    // scratch: x = B g, y, and per parent the stacked x^ / y^ of its children
+    // scratch: per parent the stacked x^ / y^ of its children
     Bump bp;
-    const int64_t ox = bp.take((int64_t)r * B), oy = bp.take((int64_t)r * B);
     std::vector<int64_t> oXs(NN, 0), oYs(NN, 0);
     std::vector<int> ks(NN, 0);
     for (int t = 1; t < (1 << L); ++t) {
@@ -772,12 +778,10 @@ int hbs_apply_dtn(HbsRoot &H, const double *g, double *dudn, int B, cudaStream_t
     auto ld = [&](int t) { return std::max(ks[t / 2], 1); };
     auto rows_of = [&](int t) { return leaf(t) ? H.hi[t] - H.lo[t] : ks[t]; };
     do {
-        k_hbs_gather<<<256, 256, 0, s>>>(n, B, (const int *)(P + H.offKK), P + H.offWW, g, W + ox);
-        if (cudaGetLastError() != cudaSuccess) { rc = GM_ECUDA; break; }
         // up: x^_t = F_t^T x(I_t) at leaves, F_t^T [x^_a; x^_b] above
         std::vector<GemmDesc> v;
         for (int t = 1 << L; t < NN; ++t)
-            v.push_back(gd(P + H.offFt[t], std::max(H.k[t], 1), 0, W + ox + H.lo[t], r, 0, xh(t), ld(t), H.k[t], B,
+            v.push_back(gd(P + H.offFt[t], std::max(H.k[t], 1), 0, X + H.lo[t], ldx, 0, xh(t), ld(t), H.k[t], B,
                            rows_of(t), 1.0, 0.0));
         if ((rc = run_gemms(v, db, s))) break;
         for (int lev = L - 1; lev >= 1 && rc == GM_OK; --lev) {
@@ -810,15 +814,88 @@ int hbs_apply_dtn(HbsRoot &H, const double *g, double *dudn, int B, cudaStream_t
         std::vector<GemmDesc> v1, v2;
         for (int t = 1 << L; t < NN; ++t) {
             const int q = rows_of(t);
-            v1.push_back(gd(P + H.offE[t], q, 0, yh(t), ld(t), 0, W + oy + H.lo[t], r, q, B, H.k[t], 1.0, 0.0));
-            v2.push_back(gd(P + H.offG[t], q, 0, W + ox + H.lo[t], r, 0, W + oy + H.lo[t], r, q, B, q, 1.0, 1.0));
+            v1.push_back(gd(P + H.offE[t], q, 0, yh(t), ld(t), 0, Y + H.lo[t], ldy, q, B, H.k[t], 1.0, 0.0));
+            v2.push_back(gd(P + H.offG[t], q, 0, X + H.lo[t], ldx, 0, Y + H.lo[t], ldy, q, B, q, 1.0, 1.0));
         }
         if ((rc = run_gemms(v1, db, s)) || (rc = run_gemms(v2, db, s))) break;
-        const int64_t tot = (int64_t)4 * n * B;
-        k_hbs_out<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, s>>>(n, B, g, W + oy, dudn);
-        if (cudaGetLastError() != cudaSuccess) rc = GM_ECUDA;
     } while (0);
     cudaFreeAsync(W, s);
+    return rc;
+}
+
+int hbs_apply_dtn(HbsRoot &H, const double *g, double *dudn, int B, cudaStream_t s) {
+    if (B <= 0) return GM_OK;
+    const int r = H.r, n = H.n;
+    double *W = nullptr;  // x = B g and y = S^{-1} x, r x B each
+    if (cudaMallocAsync((void **)&W, (size_t)2 * r * B * 8, s) != cudaSuccess) {
+        cudaGetLastError();
+        return GM_ENOMEM;
+    }
+    int rc = GM_OK;
+    k_hbs_gather<<<256, 256, 0, s>>>(n, B, (const int *)(H.pool + H.offKK), H.pool + H.offWW, g, W);
+    if (cudaGetLastError() != cudaSuccess) rc = GM_ECUDA;
+    if (rc == GM_OK) rc = hbs_solve(H, W, r, W + (size_t)r * B, r, B, s);
+    if (rc == GM_OK) {
+        const int64_t tot = (int64_t)4 * n * B;
+        k_hbs_out<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, s>>>(n, B, g, W + (size_t)r * B, dudn);
+        if (cudaGetLastError() != cudaSuccess) rc = GM_ECUDA;
+    }
+    cudaFreeAsync(W, s);
+    return rc;
+}
+
+namespace {
+// D = Dsrc - diag(a) V (rows x cols; a read with stride sa)
+__global__ void k_hbs_sub_diag(double *__restrict__ D, int ldd, const double *__restrict__ Dsrc, int ldsrc,
+                               const double *__restrict__ a, int sa, const double *__restrict__ V, int ldv, int rows,
+                               int cols) {
+    const int64_t tot = (int64_t)rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % rows), j = (int)(e / rows);
+        D[i + (size_t)j * ldd] = Dsrc[i + (size_t)j * ldsrc] - a[(size_t)i * sa] * V[i + (size_t)j * ldv];
+    }
+}
+}  // namespace
+
+int hbs_block_solve(double *ws, int sp, int rp, int m, double tol, cudaStream_t s, int *max_rank) {
+    const int M = 2 * sp;
+    HbsRoot H33, H44;
+    double *T = nullptr;
+    const size_t n1 = (size_t)sp * (sp + rp), n2 = (size_t)sp * sp, n3 = (size_t)sp * rp;
+    if (cudaMallocAsync((void **)&T, (n1 + n2 + 3 * n3) * 8, s) != cudaSuccess) {
+        cudaGetLastError();
+        return GM_ENOMEM;
+    }
+    double *VW = T, *T44 = VW + n1, *Z4 = T44 + n2, *X4 = Z4 + n3, *X3 = X4 + n3;
+    const double *V3 = VW, *W3 = VW + n2;
+    int rc = GM_OK;
+    DescBuf db;
+    do {
+        // S33 (top-left sp x sp of [M | Z]) in HBS form, inverted by Algorithm 1
+        if ((rc = hbs_factor(ws, M, sp, m, tol, s, H33))) break;
+        // [V3 W3] = S33^{-1} [A34 Z3]: the columns sp .. of the top rows of [M | Z]
+        if ((rc = hbs_solve(H33, ws + (size_t)sp * M, M, VW, sp, sp + rp, s))) break;
+        // T44 = S44 - A43 V3, Z4' = Z4 - A43 W3 (A43 diagonal: M(sp + i, i))
+        const int bx = (int)std::min<int64_t>(((int64_t)sp * std::max(sp, rp) + 255) / 256, 4096);
+        k_hbs_sub_diag<<<bx, 256, 0, s>>>(T44, sp, ws + sp + (size_t)sp * M, M, ws + sp, M + 1, V3, sp, sp, sp);
+        k_hbs_sub_diag<<<bx, 256, 0, s>>>(Z4, sp, ws + sp + (size_t)M * M, M, ws + sp, M + 1, W3, sp, sp, rp);
+        if (cudaGetLastError() != cudaSuccess) { rc = GM_ECUDA; break; }
+        if ((rc = hbs_factor(T44, sp, sp, m, tol, s, H44))) break;
+        if ((rc = hbs_solve(H44, Z4, sp, X4, sp, rp, s))) break;
+        // X3 = W3 - V3 X4
+        if ((rc = run_copies({cpd(W3, sp, X3, sp, sp, rp, 0)}, db, s))) break;
+        if ((rc = run_gemms({gd(V3, sp, 0, X4, sp, 0, X3, sp, sp, rp, sp, -1.0, 1.0)}, db, s))) break;
+        // X into the right block of [M | Z], as after the dense elimination
+        if ((rc = run_copies({cpd(X3, sp, ws + (size_t)M * M, M, sp, rp, 0),
+                              cpd(X4, sp, ws + sp + (size_t)M * M, M, sp, rp, 0)},
+                             db, s)))
+            break;
+        if (cudaStreamSynchronize(s) != cudaSuccess) rc = GM_ECUDA;
+        if (max_rank) *max_rank = std::max(*max_rank, std::max(H33.max_rank, H44.max_rank));
+    } while (0);
+    hbs_free(H33);
+    hbs_free(H44);
+    cudaFreeAsync(T, s);
     return rc;
 }
 

@@ -26,6 +26,22 @@ struct HbsRoot {
     int max_rank = 0;
 };
 
+// HBS factors of a dense r x r FP64 matrix S (column-major, leading dimension lds,
+// device): compression at relative tolerance tol with node size m (Section 4), then
+// Algorithm 1 (Section 5).  GM_EUNSUPPORTED: a node's rank reached HBS_KCAP, or r <= m.
+int hbs_factor(const double *S, int lds, int r, int m, double tol, cudaStream_t s, HbsRoot &out);
+// Y = S^{-1} X for B columns (Algorithm 2); X, Y device, r x B, leading dimensions ldx, ldy.
+int hbs_solve(HbsRoot &h, const double *X, int ldx, double *Y, int ldy, int B, cudaStream_t s);
+
+// The interface solve of a pairwise merge by the paper's accelerated Step 1: X = M^{-1} Z
+// for M = [S33 A34; A43 S44] by block elimination with HBS inverses of S33 and of its
+// Schur complement T44 = S44 - A43 S33^{-1} A34 (A34, A43 diagonal):
+//   [V3 W3] = S33^{-1} [A34 Z3],  X4 = T44^{-1} (Z4 - A43 W3),  X3 = W3 - V3 X4.
+// ws is the merge's dense system [M | Z] (2 sp rows, ld 2 sp, 2 sp + rp columns); on
+// success its right block holds X, as after the dense elimination; on failure (e.g.
+// GM_EUNSUPPORTED) ws is unchanged.  max_rank (optional) accumulates the largest rank.
+int hbs_block_solve(double *ws, int sp, int rp, int m, double tol, cudaStream_t s, int *max_rank);
+
 // Compress S (r x r FP64, column-major, device) at relative tolerance tol with node size
 // m (2 <= m <= 192), run Algorithm 1, and tabulate the ghost couplings of the ring from
 // b, c, d (n x n each).  GM_EUNSUPPORTED: a node's rank reached HBS_KCAP, or r <= m.

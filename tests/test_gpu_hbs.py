@@ -127,3 +127,21 @@ def test_hbs_rejects_what_it_cannot_do(gm):
     g = np.zeros(256)
     out = np.zeros(256)
     assert lib.gm_solve_static(op._h, g.ctypes.data, out.ctypes.data, 1, None) == gm.GM_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("n,leaf,m,edge", [(128, 16, 16, 32), (192, 12, 16, 48)])
+def test_hbs_interface_solves_in_merges(gm, n, leaf, m, edge):
+    """FP64 build with tol > 0: merges with a shared edge >= `edge` nodes solve their
+    interface systems by HBS block elimination (Step 1), the root by Algorithms 1-2;
+    against the dense oracle and against the oracle running the same Step 1."""
+    from oracle import hbs as ohbs
+    tol = 1e-9
+    b, c, d = inputs.convection_fields(n, seeds=(n + 7, n + 8, n + 9))
+    op = gm.build(b, c, d, n, leaf, tol=tol, hbs_leaf=m, hbs_min_edge=edge)
+    info = op.info()
+    assert info["hbs_merges"] > 0
+    T = op.dtn()
+    To = nd_dense.build(b, c, d, n, leaf).T
+    assert rel_mat(T, To) < 100 * tol
+    Th = nd_dense.build(b, c, d, n, leaf, interface_solve=ohbs.step1_interface_solver(tol, m), min_edge=edge).T
+    assert rel_mat(T, Th) < 100 * tol

@@ -8,7 +8,9 @@
 - the truncated representation of a root Schur complement stays within a small
   multiple of the tolerance, and so does the DtN map computed through it;
 - the printed down-sweep of Algorithm 2 (E_tau applied to x^_tau) is a typo: planting
-  it in a copy of the oracle breaks the inverse, which the y^_tau reading reproduces.
+  it in a copy of the oracle breaks the inverse, which the y^_tau reading reproduces;
+- the accelerated merge's Step 1 (block elimination with HBS inverses) is the exact
+  interface solve without truncation, and a build using it tracks the tolerance.
 """
 import numpy as np
 import pytest
@@ -134,3 +136,26 @@ def test_printed_down_sweep_is_a_typo():
     exact = np.linalg.solve(H, x)
     assert rel(hbs.apply_inverse(inv, x), exact) < 1e-12
     assert rel(_apply_inverse_printed_typo(inv, x), exact) > 1e-3
+
+
+def test_step1_interface_solver_exact_without_truncation():
+    """Step 1's block elimination with untruncated HBS inverses is the exact solve."""
+    rng = np.random.default_rng(9)
+    s3, p = 96, 40
+    S33 = rng.standard_normal((s3, s3)) + s3 * np.eye(s3)
+    S44 = rng.standard_normal((s3, s3)) + s3 * np.eye(s3)
+    A34 = np.diag(rng.standard_normal(s3))
+    A43 = np.diag(rng.standard_normal(s3))
+    Z = rng.standard_normal((2 * s3, p))
+    X = hbs.step1_interface_solver(0.0, 16)(S33, A34, A43, S44, Z)
+    M = np.block([[S33, A34], [A43, S44]])
+    assert rel(X, np.linalg.solve(M, Z)) < 1e-12
+
+
+def test_build_with_hbs_step1_merges_tracks_tolerance():
+    n, leaf = 96, 12
+    b, c, d = inputs.convection_fields(n, seeds=(3, 5, 7))
+    T0 = nd_dense.build(b, c, d, n, leaf).T
+    for tol in (1e-6, 1e-9):
+        T1 = nd_dense.build(b, c, d, n, leaf, interface_solve=hbs.step1_interface_solver(tol, 12), min_edge=24).T
+        assert rel(T1, T0) < 100 * tol
