@@ -78,7 +78,9 @@ typedef struct gm_opts {
     int hbs_min_edge; /* tol > 0, FP64: pairwise merges whose shared edge has at least
                          this many nodes solve their interface system by HBS block
                          elimination (0 = default 128)                                  */
-    int reserved[3];
+    int timing_mask;  /* with timing: time only the families whose bit is set
+                         (bit GM_K_*; 0 = all)                                          */
+    int reserved[2];
 } gm_opts;
 
 /* Pivoting of the mixed-precision dense eliminations.

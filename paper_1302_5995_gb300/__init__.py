@@ -34,7 +34,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("keep_levels", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("panel_width", ctypes.c_int), ("timing", ctypes.c_int), ("split_digits", ctypes.c_int),
                 ("pivoting", ctypes.c_int), ("hbs_leaf", ctypes.c_int), ("hbs_min_edge", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("timing_mask", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 K_FAMILIES = ["leaf", "assemble", "panel", "pivrows", "gj_update", "merge_update", "root"]
 
@@ -230,6 +230,7 @@ class DtN:
 
 
 def _opts(precision, keep_levels, stream, panel_width, timing, split_digits, pivoting, hbs_leaf=0, hbs_min_edge=0):
+    """timing: False, True (every family) or a list of family names to time."""
     lib = load_library()
     o = Opts()
     lib.gm_opts_default(ctypes.byref(o))
@@ -238,6 +239,8 @@ def _opts(precision, keep_levels, stream, panel_width, timing, split_digits, piv
     o.stream = _stream_handle(stream)
     o.panel_width = panel_width
     o.timing = 1 if timing else 0
+    if timing and not isinstance(timing, bool):
+        o.timing_mask = sum(1 << K_FAMILIES.index(f) for f in timing)
     o.split_digits = split_digits
     o.pivoting = pivoting
     o.hbs_leaf = hbs_leaf

@@ -332,6 +332,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
     Status *dst = stat.as<Status>();
     KTimer kt;
     kt.on = o.timing != 0;
+    if (o.timing_mask) kt.mask = (unsigned)o.timing_mask;
 
     // the arena: FP64, or double-float pairs (same 8 bytes per element)
     DBuf arena_buf;

@@ -20,6 +20,8 @@ void event_pool_put(cudaEvent_t e);
 // launch is bracketed by a pair of pooled CUDA events on its stream.
 struct KTimer {
     bool on = false;
+    unsigned mask = ~0u;  // families whose launches are timed (bit f = family f)
+    bool open = false;    // the last begin() recorded an event pair
     double flops[GM_K_NFAM] = {};
     int launches[GM_K_NFAM] = {};
     struct Rec {
@@ -39,13 +41,15 @@ struct KTimer {
     void begin(int fam, double fl, cudaStream_t s) {
         flops[fam] += fl;
         launches[fam] += 1;
-        if (!on) return;
+        open = on && ((mask >> fam) & 1u);
+        if (!open) return;
         Rec r{fam, event_pool_get(), event_pool_get()};
         cudaEventRecord(r.a, s);
         recs.push_back(r);
     }
     void end(cudaStream_t s) {
-        if (on && !recs.empty()) cudaEventRecord(recs.back().b, s);
+        if (open && !recs.empty()) cudaEventRecord(recs.back().b, s);
+        open = false;
     }
     // after the stream has been synchronised
     void collect(double ms[GM_K_NFAM]) {
