@@ -405,20 +405,32 @@ k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
 #pragma unroll 1
     for (int kk = 0; kk < nbe; kk += 16) warp_mma_levels<S, KP64>(As + kk, Bs + kk, 64, 64, wm, wn, acc);
     const int *fe = fex + Sy.roff, *re = rex + Sy.coff;
+    // read-modify-write of W in groups of four: the four loads of a group are issued
+    // together (a load cannot move above an earlier store to W, so one-at-a-time RMW
+    // would pay a full memory latency per element)
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
+        for (int nt = 0; nt < 4; ++nt) {
+            float2 w[4];
+            bool ok[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 int r, cl;
                 acc_pos(mt, nt, c, r, cl);
                 const int i = i0 + wm + r, j = j0 + wn + cl;
-                if (i >= m || j >= Sy.ncol || (i >= k && i < k + nbe)) continue;
-                const float2 v = combine_levels<S>(acc, mt, nt, c, fe[i] + re[j] - 12);
-                float2 *p = W + (size_t)j * m + i;
-                *p = df_sub(*p, v);
+                ok[c] = !(i >= m || j >= Sy.ncol || (i >= k && i < k + nbe));
+                w[c] = ok[c] ? W[(size_t)j * m + i] : make_float2(0.f, 0.f);
             }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (!ok[c]) continue;
+                int r, cl;
+                acc_pos(mt, nt, c, r, cl);
+                const int i = i0 + wm + r, j = j0 + wn + cl;
+                W[(size_t)j * m + i] = df_sub(w[c], combine_levels<S>(acc, mt, nt, c, fe[i] + re[j] - 12));
+            }
+        }
 }
 
 // ----------------------------------------------------------------------------- launcher

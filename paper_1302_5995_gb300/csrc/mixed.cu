@@ -330,11 +330,19 @@ k_mx_gj_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, 
     if (i0 >= m || j0 >= Sy.ncol) return;
     float2 *A = ws + Sy.off;
     digit_gemm_chunks<S>(fdig + (int64_t)Sy.roff * 16, fplane, 16, i0, m, fex + Sy.roff, rdig + (int64_t)Sy.coff * 16,
-                         rplane, 16, j0, Sy.ncol, rex + Sy.coff, 16, As, Bs, [&](int r, int cl, float2 v, bool) {
-                             const int i = i0 + r, j = j0 + cl;
-                             if (i >= m || j >= Sy.ncol || (i >= k && i < k + nbe)) return;
-                             float2 *p = A + (size_t)j * m + i;
-                             *p = df_sub(*p, v);
+                         rplane, 16, j0, Sy.ncol, rex + Sy.coff, 16, As, Bs,
+                         [&](const int *r, const int *cl, const float2 *v, bool) {
+                             float2 w[4];
+                             bool ok[4];
+#pragma unroll
+                             for (int q = 0; q < 4; ++q) {
+                                 const int i = i0 + r[q], j = j0 + cl[q];
+                                 ok[q] = !(i >= m || j >= Sy.ncol || (i >= k && i < k + nbe));
+                                 w[q] = ok[q] ? A[(size_t)j * m + i] : make_float2(0.f, 0.f);
+                             }
+#pragma unroll
+                             for (int q = 0; q < 4; ++q)
+                                 if (ok[q]) A[(size_t)(j0 + cl[q]) * m + i0 + r[q]] = df_sub(w[q], v[q]);
                          });
 }
 
@@ -392,29 +400,41 @@ k_mx_merge_update(const MergeDesc *__restrict__ md, const int *__restrict__ tab,
     float2 *O = out + M.out;
     digit_gemm_chunks<S>(
         ydig + M.doff, plane, M.kpad, a0, rp, yex + eo, xdig + M.doff, plane, M.kpad, c0, rp, xex + eo, 2 * M.sp, As, Bs,
-        [&](int r, int cl, float2 v, bool first) {
-            const int aa = a0 + r, cc = c0 + cl;
-            if (aa >= rp || cc >= rp) return;
-            const int qa = aa < n1 ? T.q1[aa] : T.q2[aa - n1];
-            const int qc = cc < n1 ? T.q1[cc] : T.q2[cc - n1];
-            float2 *o = O + qa + (int64_t)rp * qc;
-            if (!first) {  // a later K chunk: accumulate into the parent entry
-                *o = df_sub(*o, v);
-                return;
-            }
-            float2 cval = make_float2(0.f, 0.f);
-            if (aa < n1 && cc < n1) cval = S1[T.p1[aa] + (int64_t)M.r1 * T.p1[cc]];
-            else if (aa >= n1 && cc >= n1) cval = S2[T.p2[aa - n1] + (int64_t)M.r2 * T.p2[cc - n1]];
-            else {
-                for (int e = 0; e < 2; ++e) {
-                    const int *x = T.x12 + 4 * e;
-                    if (aa < n1 && aa == x[0] && cc - n1 == x[1])
-                        cval = df_from_d(stencil_w_mx(bf, cf, df, ih, x[2], d12));
-                    if (aa >= n1 && aa - n1 == x[1] && cc == x[0])
-                        cval = df_from_d(stencil_w_mx(bf, cf, df, ih, x[3], d21));
+        [&](const int *r, const int *cl, const float2 *v, bool first) {
+            // the four parent positions and their current values (children's entries on
+            // the first chunk, the partial result after), read together
+            float2 cval[4];
+            int64_t off[4];
+            bool ok[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int aa = a0 + r[q], cc = c0 + cl[q];
+                ok[q] = aa < rp && cc < rp;
+                cval[q] = make_float2(0.f, 0.f);
+                off[q] = 0;
+                if (!ok[q]) continue;
+                const int qa = aa < n1 ? T.q1[aa] : T.q2[aa - n1];
+                const int qc = cc < n1 ? T.q1[cc] : T.q2[cc - n1];
+                off[q] = qa + (int64_t)rp * qc;
+                if (!first) {  // a later K chunk: accumulate into the parent entry
+                    cval[q] = O[off[q]];
+                } else if (aa < n1 && cc < n1) {
+                    cval[q] = S1[T.p1[aa] + (int64_t)M.r1 * T.p1[cc]];
+                } else if (aa >= n1 && cc >= n1) {
+                    cval[q] = S2[T.p2[aa - n1] + (int64_t)M.r2 * T.p2[cc - n1]];
+                } else {
+                    for (int e = 0; e < 2; ++e) {
+                        const int *x = T.x12 + 4 * e;
+                        if (aa < n1 && aa == x[0] && cc - n1 == x[1])
+                            cval[q] = df_from_d(stencil_w_mx(bf, cf, df, ih, x[2], d12));
+                        if (aa >= n1 && aa - n1 == x[1] && cc == x[0])
+                            cval[q] = df_from_d(stencil_w_mx(bf, cf, df, ih, x[3], d21));
+                    }
                 }
             }
-            *o = df_sub(cval, v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (ok[q]) O[off[q]] = df_sub(cval[q], v[q]);
         });
 }
 
@@ -502,11 +522,14 @@ k_mx_apply(const __nv_bfloat16 *__restrict__ tdig, const int *__restrict__ tex, 
     __shared__ __align__(16) __nv_bfloat16 Bs[S * 64 * KP];
     const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
     digit_gemm_chunks<S>(tdig, tplane, kpad, i0, N, tex, gdig, gplane, kpad, j0, B, gex, N, As, Bs,
-                         [&](int r, int cl, float2 v, bool first) {
-                             const int i = i0 + r, j = j0 + cl;
-                             if (i >= N || j >= B) return;
-                             double *o = V + (size_t)j * N + i;
-                             *o = first ? df_to_d(v) : *o + df_to_d(v);
+                         [&](const int *r, const int *cl, const float2 *v, bool first) {
+#pragma unroll
+                             for (int q = 0; q < 4; ++q) {
+                                 const int i = i0 + r[q], j = j0 + cl[q];
+                                 if (i >= N || j >= B) continue;
+                                 double *o = V + (size_t)j * N + i;
+                                 *o = first ? df_to_d(v[q]) : *o + df_to_d(v[q]);
+                             }
                          });
 }
 

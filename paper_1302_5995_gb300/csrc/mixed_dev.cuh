@@ -223,9 +223,10 @@ __device__ __forceinline__ void load_digit_tile(const __nv_bfloat16 *__restrict_
 
 // C(i, j) = sum_k A(i, k) B(k, j) for a 64 x 64 tile from two digit matrices (A by rows,
 // B by columns), K in chunks of at most 512 (exact level sums).  After each chunk the
-// df32 partial result of every thread position is handed to epi(r, c, value, first),
-// r and c the position in the tile (see acc_pos), first = this is the first chunk; the
-// caller accumulates (so no second register tile is live beside the level sums).
+// df32 partial results are handed to epi(r[4], c[4], value[4], first) four at a time (one
+// m16 x n8 fragment: r, c the positions in the tile, see acc_pos), first = this is the
+// first chunk; the caller accumulates (so no second register tile is live beside the
+// level sums) and can issue a group's memory reads together.
 // Warp w owns rows (w & 1) * 32 and columns (w >> 1) * 32.
 template <int S, class Epi>
 __device__ __forceinline__ void digit_gemm_chunks(const __nv_bfloat16 *__restrict__ Ad, int64_t aplane, int akpad,
@@ -258,14 +259,20 @@ __device__ __forceinline__ void digit_gemm_chunks(const __nv_bfloat16 *__restric
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
+            for (int nt = 0; nt < 4; ++nt) {
+                int rr[4], cc[4];
+                float2 vv[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     int r, cl;
                     acc_pos(mt, nt, c, r, cl);
                     const int i = min(i0 + wm + r, M - 1), j = min(j0 + wn + cl, N - 1);
-                    epi(wm + r, wn + cl, combine_levels<S>(acc, mt, nt, c, aex[i] + bex[j] - 12), k0 == 0);
+                    rr[c] = wm + r;
+                    cc[c] = wn + cl;
+                    vv[c] = combine_levels<S>(acc, mt, nt, c, aex[i] + bex[j] - 12);
                 }
+                epi(rr, cc, vv, k0 == 0);
+            }
     }
 }
 
