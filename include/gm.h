@@ -64,7 +64,7 @@ typedef struct gm_opts {
                          gm_get_schur() (costs the memory of all levels)                 */
     void *stream;     /* cudaStream_t for the build (NULL = legacy default stream)      */
     int panel_width;  /* pivot panel width of the partial-pivoting eliminations
-                         (0 = default: 8 for FP64, 16 for mixed precision)             */
+                         (0 = default 16, the fastest measured)                        */
     int timing;       /* nonzero: time every kernel launch of the build with CUDA events
                          (per kernel family, reported by gm_info)                       */
     int split_digits; /* GM_PREC_MIXED: 7-bit digits per operand of the split products,

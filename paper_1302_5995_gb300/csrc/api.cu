@@ -303,7 +303,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
     cudaStream_t s = (cudaStream_t)o.stream;
     const bool mixed = o.precision == GM_PREC_MIXED;
     const bool blockpiv = mixed && o.pivoting != GM_PIVOT_PARTIAL;
-    const int nb = o.panel_width > 0 ? o.panel_width : (mixed ? 16 : 8);
+    const int nb = o.panel_width > 0 ? o.panel_width : 16;  // measured best for both paths (n = 256, 512)
     if (nb > GJ_MAX_NB) return GM_EINVAL;
     const int split = o.split_digits ? o.split_digits : 6;
     if (mixed && (split < 3 || split > 6)) return GM_EINVAL;
