@@ -148,7 +148,7 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
     // digit planes of the rows of X0 and of A11 (K = 64), one warp per row
     for (int i = warp; i < 128; i += FAC_THREADS / 32) {
         const int64_t r64 = (int64_t)blockIdx.x * 64 + (i & 63);
-        if (i < 64)  // X0 is FP32: four digits hold it exactly (and only four are read)
+        if (i < 64)  // X0 is FP32: four digits carry it past its accuracy (only four are read)
             warp_slice_row<(S < 4 ? S : 4)>([&](int q) { return make_float2(Xs[i * 65 + q], 0.f); }, 64, 64, x_dig,
                                             plane, r64, x_ex);
         else
@@ -290,10 +290,11 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
     for (int pass = 0; pass < 3; ++pass) {
         float2 res[2][4][4];
         // K = nbe: the operands are zero beyond the block's live columns.  Passes 0 and 2
-        // multiply by the FP32 inverse X0, whose 24-bit values four 7-bit digits hold
-        // exactly; R0 only has to be good to FP32 (the refinement corrects it) and X0 E is
-        // a correction of relative size rho, so four digits of the right operand suffice
-        // there.  E itself (pass 1) is a difference of nearly equal terms: full digits.
+        // multiply by the FP32 inverse X0, which four 7-bit digits carry to 2^-28 of each
+        // row's maximum -- beyond X0's own accuracy; R0 only has to be good to about FP32
+        // (the refinement corrects it) and X0 E is a correction of relative size rho, so
+        // four digits of the right operand suffice there.  E itself (pass 1) is a
+        // difference of nearly equal terms: full digits.
         constexpr int SX = S < 4 ? S : 4;
         if (pass == 1)
             gemm64_gd<S>(ad, plane, ae, Rd, exB, As, Bs, res, (nbe + 15) & ~15);
