@@ -199,7 +199,7 @@ def test_planted_merge_mistakes_are_caught(monkeypatch, mistake):
     """A plausible slip inside the merge formula makes the O1 comparison fail."""
     orig = nd_dense.merge_two
 
-    def bad(prob, box1, S1, box2, S2, parent):
+    def bad(prob, box1, S1, box2, S2, parent, interface_solve=None):
         if mistake == "transpose_S13":
             S1 = S1.T.copy()
         elif mistake == "drop_A34":
@@ -210,11 +210,11 @@ def test_planted_merge_mistakes_are_caught(monkeypatch, mistake):
             p = P()
             p.__dict__.update(prob.__dict__)
             p.A_block = lambda r, c: real(r, c) * (0.0 if (set(r) & set(box1.ring()) and set(c) & set(box2.ring())) else 1.0)
-            return orig(p, box1, S1, box2, S2, parent)
+            return orig(p, box1, S1, box2, S2, parent, interface_solve)
         elif mistake == "sign_A12":
-            out = orig(prob, box1, S1, box2, S2, parent)
+            out = orig(prob, box1, S1, box2, S2, parent, interface_solve)
             return out + 1e-3 * np.abs(out).max() * np.eye(len(out))
-        return orig(prob, box1, S1, box2, S2, parent)
+        return orig(prob, box1, S1, box2, S2, parent, interface_solve)
 
     _plant(monkeypatch, bad)
     n = 12
