@@ -81,23 +81,30 @@ struct DBuf {
     template <class T> T *as() const { return (T *)p; }
 };
 
-// Second stream and two events for the look-ahead of the blocked sweep (released on
-// scope exit, after the build has synchronised).
+// Streams and events for the look-ahead of the blocked sweep (released on scope exit,
+// after the build has synchronised): s1 carries the critical chain at the highest
+// priority, s2 the bulk of each update at the lowest.
 struct LookAhead {
-    cudaStream_t s2 = nullptr;
-    cudaEvent_t a = nullptr, b = nullptr;
+    cudaStream_t s1 = nullptr, s2 = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr, c = nullptr;
     ~LookAhead() {
-        // destroyed before the scratch buffers declared ahead of it: nothing on the second
-        // stream may still read them when they are released (early error returns)
+        // destroyed before the scratch buffers declared ahead of it: nothing on the
+        // look-ahead streams may still read them when they are released (early returns)
+        if (s1) cudaStreamSynchronize(s1);
         if (s2) cudaStreamSynchronize(s2);
-        if (a) cudaEventDestroy(a);
-        if (b) cudaEventDestroy(b);
+        for (cudaEvent_t e : {a, b, c})
+            if (e) cudaEventDestroy(e);
+        if (s1) cudaStreamDestroy(s1);
         if (s2) cudaStreamDestroy(s2);
     }
     bool create() {
-        if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess ||
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&s1, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, least) != cudaSuccess ||
             cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
@@ -405,24 +412,28 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             if ((rc = bxd.alloc((size_t)split * sq * 64 * 2, s)) || (rc = bad.alloc((size_t)split * sq * 64 * 2, s)) ||
                 (rc = bxe.alloc(sq * sizeof(int), s)) || (rc = bae.alloc(sq * sizeof(int), s)) ||
                 (rc = bpmag.alloc(sq * sizeof(float), s)) ||
-                (rc = bfdig.alloc((size_t)split * max_rows * 64 * 2, s)) ||
-                (rc = bfex.alloc((size_t)max_rows * sizeof(int), s)) ||
-                (rc = brdig.alloc((size_t)split * max_cols * 64 * 2, s)) ||
-                (rc = brex.alloc((size_t)max_cols * sizeof(int), s)))
+                (rc = bfdig.alloc(2 * (size_t)split * max_rows * 64 * 2, s)) ||
+                (rc = bfex.alloc(2 * (size_t)max_rows * sizeof(int), s)) ||
+                (rc = brdig.alloc(2 * (size_t)split * max_cols * 64 * 2, s)) ||
+                (rc = brex.alloc(2 * (size_t)max_cols * sizeof(int), s)))
                 return rc;
             bscr.x_dig = bxd.as<__nv_bfloat16>();
             bscr.a11_dig = bad.as<__nv_bfloat16>();
             bscr.x_ex = bxe.as<int>();
             bscr.a11_ex = bae.as<int>();
             bscr.pmag = bpmag.as<float>();
-            bscr.fdig = bfdig.as<__nv_bfloat16>();
-            bscr.fex = bfex.as<int>();
-            bscr.rdig = brdig.as<__nv_bfloat16>();
-            bscr.rex = brex.as<int>();
+            for (int q = 0; q < 2; ++q) {
+                bscr.fdig[q] = bfdig.as<__nv_bfloat16>() + (size_t)q * split * max_rows * 64;
+                bscr.fex[q] = bfex.as<int>() + (size_t)q * max_rows;
+                bscr.rdig[q] = brdig.as<__nv_bfloat16>() + (size_t)q * split * max_cols * 64;
+                bscr.rex[q] = brex.as<int>() + (size_t)q * max_cols;
+            }
             if (!la.create()) return GM_ECUDA;
+            bscr.s1 = la.s1;
             bscr.s2 = la.s2;
             bscr.ev_r = la.a;
             bscr.ev_rest = la.b;
+            bscr.ev_join = la.c;
         } else {
             if ((rc = perm.alloc((size_t)max_nm * 4 * GJ_MAX_NB * sizeof(int), s)) ||
                 (rc = perm_n.alloc((size_t)max_nm * sizeof(int), s)) ||

@@ -38,12 +38,26 @@ constexpr int LDF = NBK + 1;  // padded row length of the df32 shared tiles
 constexpr int FAC_THREADS = 256;
 constexpr int PRS = 36;  // shared stride of the four 32-column groups of the pivot row
 
+// Sort key of a pivot candidate: a larger |v| wins; a NaN counts as 0; a row already used
+// as a pivot never wins (key 0, below the key of every unused row).
+__device__ __forceinline__ unsigned piv_key(float v, int r, unsigned long long used) {
+    if ((used >> r) & 1ull) return 0u;
+    const float a = fabsf(v);
+    return a == a ? __float_as_uint(a) + 1u : 1u;
+}
+
 // X0 ~ A11^{-1} by Gauss-Jordan on [A11 | I] in FP32 with partial pivoting among the rows
 // of the block.  The 64 x 128 augmented matrix lives in registers: thread (row, cg) holds
 // columns 32 cg .. 32 cg + 31 of one row (four threads per row, eight rows per warp).
-// Rows never move: the pivot row of column t is prow_of[t], and row t of X0 is the right
-// half of that row at the end.  Per column: one warp-level and one block-level argmax,
-// the pivot row scaled into shared memory, and a rank-1 update of the other rows.
+// Rows never move: the pivot row of column t is the unused row of largest |entry| (lowest
+// row on ties), and row t of X0 is the right half of that row at the end.
+//
+// One barrier per column.  Every warp keeps its own copy of the current pivot column
+// (rows lane and lane + 32), so it finds the pivot row without talking to the others;
+// the owners of column t + 2 publish it after the update of column t, and each warp
+// brings column t + 1 up to date itself with the same fused multiply-add the owners use
+// (so every copy agrees bit for bit with the registers).  Shared buffers alternate
+// between even and odd columns.
 template <int S>
 __global__ void __launch_bounds__(FAC_THREADS)
 k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int k, __nv_bfloat16 *__restrict__ x_dig,
@@ -52,9 +66,8 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *Adf = (float2 *)smem_raw;       // [64][LDF] A11 (df32)
     float *Xs = (float *)(Adf + 64 * LDF);  // [64][65] rows of X0
-    __shared__ float s_best[8];
-    __shared__ int s_row[8];
-    __shared__ __align__(16) float prow[4 * PRS];
+    __shared__ __align__(16) float prow[2][4 * PRS];  // scaled pivot row, registers' order
+    __shared__ float colb[2][64];                     // a column published by its owners
     __shared__ float s_pm[64];
     const SysDesc Sy = sys[blockIdx.x];
     const int m = Sy.m;
@@ -63,6 +76,7 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
     const float2 *W = ws + Sy.off;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int row = tid >> 2, cg = tid & 3;
+    const unsigned FULL = 0xffffffffu;
     for (int e = tid; e < 64 * 64; e += FAC_THREADS) {  // A11, padded with the identity beyond nbe
         const int i = e % 64, j = e / 64;
         Adf[i * LDF + j] = (i < nbe && j < nbe) ? W[(size_t)(k + j) * m + k + i] : make_float2(i == j ? 1.f : 0.f, 0.f);
@@ -74,65 +88,73 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
         const int c = cg * 32 + j;
         a[j] = c < 64 ? Adf[row * LDF + c].x : (c - 64 == row ? 1.f : 0.f);
     }
-    bool used = false;
+    float k0 = Adf[lane * LDF].x, k1 = Adf[(lane + 32) * LDF].x;  // column 0, this warp's copy
+    if (tid < 64) colb[1][tid] = Adf[tid * LDF + 1].x;            // column 1, read at column 0
+    __syncthreads();
+    const bool hi = warp >= 4;  // this warp's rows are 32 .. 63
+    unsigned long long used = 0ull;
     int my_step = 0;
-    // The t loop stays rolled (an unrolled body overflows the instruction cache).  So that
-    // column t is always at a[0] of group t / 32, that group drops its eliminated column
-    // after each step by shifting its registers down (identically in every row).
+    // The t loop advances four columns at a time (the body unrolled four times), so the
+    // register holding a column is known at compile time: group t / 32 drops the four
+    // columns it has eliminated after each round by shifting its registers down by four
+    // (identically in every row), and column t sits at a[t % 4] of its group.
 #pragma unroll 1
-    for (int t = 0; t < 64; ++t) {
-        const int ct = t >> 5;
-        // multiplier of this row (for the pivot row: the pivot), read before any update
-        const float f = __shfl_sync(0xffffffffu, a[0], (lane & ~3) | ct);
-        // candidates: unused rows (a NaN counts as 0, so an unused row always wins)
-        float v = -1.f;
-        if (!used) {
-            v = fabsf(f);
-            if (!(v == v)) v = 0.f;
-        }
-        int r = row;
+    for (int t0 = 0; t0 < 64; t0 += 4) {
+        const int ct = t0 >> 5;
 #pragma unroll
-        for (int o = 4; o < 32; o <<= 1) {
-            const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
-            const int r2 = __shfl_xor_sync(0xffffffffu, r, o);
-            if (v2 > v || (v2 == v && r2 < r)) { v = v2; r = r2; }
-        }
-        if (lane == 0) { s_best[warp] = v; s_row[warp] = r; }
-        __syncthreads();
-        float best = s_best[0];
-        int p = s_row[0];
+        for (int u = 0; u < 4; ++u) {
+            const int t = t0 + u;
+            // pivot row: the same reduction over the same copy in every warp
+            const unsigned c0 = piv_key(k0, lane, used), c1 = piv_key(k1, lane + 32, used);
+            const unsigned kmax = __reduce_max_sync(FULL, max(c0, c1));
+            const int p = (int)__reduce_min_sync(FULL, c0 == kmax ? (unsigned)lane : (c1 == kmax ? lane + 32u : 64u));
+            used |= 1ull << p;
+            const float piv = __shfl_sync(FULL, (p & 32) ? k1 : k0, p & 31);
+            const float f = __shfl_sync(FULL, hi ? k1 : k0, row & 31);  // this row's multiplier
+            float *pr = prow[t & 1];
+            if (row == p) {
+                const float ip = 1.f / piv;
 #pragma unroll
-        for (int w = 1; w < 8; ++w) {
-            const float v2 = s_best[w];
-            const int r2 = s_row[w];
-            if (v2 > best || (v2 == best && r2 < p)) { best = v2; p = r2; }
-        }
-        if (row == p) {
-            const float ip = 1.f / f;
+                for (int j = 0; j < 32; j += 4)
+                    *(float4 *)&pr[cg * PRS + j] = make_float4(a[j] * ip, a[j + 1] * ip, a[j + 2] * ip, a[j + 3] * ip);
 #pragma unroll
-            for (int j = 0; j < 32; j += 4)
-                *(float4 *)&prow[cg * PRS + j] = make_float4(a[j] * ip, a[j + 1] * ip, a[j + 2] * ip, a[j + 3] * ip);
-            used = true;
-            my_step = t;
-            if (cg == 0) {
-                s_pm[t] = fabsf(f);
-                if (t < nbe) pmag[(size_t)blockIdx.x * 64 + t] = fabsf(f);
+                for (int j = 0; j < 32; ++j) a[j] = 0.f;  // becomes the scaled row below (g = -1)
+                my_step = t;
             }
-        }
-        __syncthreads();
-        const float g = (row == p) ? 0.f : f;
+            if (tid == 0) {
+                s_pm[t] = fabsf(piv);
+                if (t < nbe) pmag[(size_t)blockIdx.x * 64 + t] = fabsf(piv);
+            }
+            __syncthreads();
+            const float g = (row == p) ? -1.f : f;
 #pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-            const float4 q = *(const float4 *)&prow[cg * PRS + j];
-            a[j] = (row == p) ? q.x : fmaf(-g, q.x, a[j]);
-            a[j + 1] = (row == p) ? q.y : fmaf(-g, q.y, a[j + 1]);
-            a[j + 2] = (row == p) ? q.z : fmaf(-g, q.z, a[j + 2]);
-            a[j + 3] = (row == p) ? q.w : fmaf(-g, q.w, a[j + 3]);
+            for (int j = 0; j < 32; j += 4) {
+                const float4 q = *(const float4 *)&pr[cg * PRS + j];
+                a[j] = fmaf(-g, q.x, a[j]);
+                a[j + 1] = fmaf(-g, q.y, a[j + 1]);
+                a[j + 2] = fmaf(-g, q.z, a[j + 2]);
+                a[j + 3] = fmaf(-g, q.w, a[j + 3]);
+            }
+            // the owners of column t + 2 publish it (read by every warp at column t + 1);
+            // it is in this group at a[u + 2], or at a[u - 2] of the next group at t = 30, 31
+            if (t + 2 < 64) {
+                const int cc = (t + 2) >> 5;
+                if (cg == cc) colb[t & 1][row] = (u >= 2 && cc != ct) ? a[u >= 2 ? u - 2 : 0] : a[u + 2];
+            }
+            // every warp: its copy of column t + 1 after this column's update
+            if (t + 1 < 64) {
+                const int g1 = (t + 1) >> 5;
+                const float q1 = pr[g1 * PRS + (g1 == ct ? u + 1 : 0)];
+                const float n0 = colb[(t + 1) & 1][lane], n1 = colb[(t + 1) & 1][lane + 32];
+                k0 = (lane == p) ? q1 : fmaf(-k0, q1, n0);
+                k1 = (lane + 32 == p) ? q1 : fmaf(-k1, q1, n1);
+            }
         }
         if (cg == ct) {
 #pragma unroll
-            for (int j = 0; j < 31; ++j) a[j] = a[j + 1];
-            a[31] = 0.f;
+            for (int j = 0; j < 28; ++j) a[j] = a[j + 4];
+#pragma unroll
+            for (int j = 28; j < 32; ++j) a[j] = 0.f;
         }
     }
     if (cg >= 2) {
@@ -380,11 +402,19 @@ __device__ __forceinline__ void cp_async_digits64(const __nv_bfloat16 *__restric
 
 size_t blk_update_smem(int split) { return 2 * (size_t)split * 64 * KP64 * sizeof(__nv_bfloat16); }
 
+// Which tiles of the update a launch covers.  Tile (ti, tj) holds rows 64 ti .. and the
+// columns 64 tj .. right of J.  The look-ahead splits the update in two:
+//   UPD_NEXT : column tile 0 (the next block's columns) for every row tile, then the next
+//              block's row tile (rows k + 64 ..) for column tiles 1 .. : grid.x = nrt + (column
+//              tiles - 1), everything the next factor and R kernel read;
+//   UPD_REST : every other tile, grid (nrt, column tiles - 1).
+enum { UPD_ALL = 0, UPD_NEXT = 1, UPD_REST = 2 };
+
 // W(i, j) -= (F R)(i, j) for a 64 x 64 tile of rows outside J: both digit tiles (K = 64)
 // arrive in one cp.async batch, then four k-steps of split products without barriers.
 template <int S>
 __global__ void __launch_bounds__(128)
-k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, int cb0,
+k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, int mode, int nrt,
              const __nv_bfloat16 *__restrict__ fdig, int64_t fplane, const int *__restrict__ fex,
              const __nv_bfloat16 *__restrict__ rdig, int64_t rplane, const int *__restrict__ rex) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -394,7 +424,18 @@ k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
     const int m = Sy.m;
     if (k >= m) return;
     const int nbe = min(NBK, m - k);
-    const int i0 = blockIdx.x * 64, j0 = k + nbe + (blockIdx.y + cb0) * 64;
+    int ti = blockIdx.x, tj = blockIdx.y;
+    const int band = k / NBK + 1;  // row tile of the next pivot block
+    if (mode == UPD_NEXT) {
+        if (ti >= nrt) {
+            tj = ti - nrt + 1;
+            ti = band;
+        }
+    } else if (mode == UPD_REST) {
+        if (ti == band) return;
+        ++tj;
+    }
+    const int i0 = ti * 64, j0 = k + nbe + tj * 64;
     if (i0 >= m || j0 >= Sy.ncol) return;
     float2 *W = ws + Sy.off;
     cp_async_digits64<S>(fdig + (int64_t)Sy.roff * NBK, fplane, i0, min(64, m - i0), As);
@@ -472,59 +513,75 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
     BLK_SPLIT_DISPATCH(split, (e = set_blk_attrs<SS>(split)));
     if (e != cudaSuccess) return e;
     const size_t fsm = blk_factor_smem(split), rsm = blk_rgemm_smem(split), usm = blk_update_smem(split);
-    bool pending = false;  // an update of the previous step still runs on the second stream
+    const bool la = scr.s1 && scr.s2;
+    // the chain runs on s1, joined to the caller's stream on entry and exit
+    cudaStream_t c = la ? scr.s1 : s;
+    if (la && ((e = cudaEventRecord(scr.ev_join, s)) != cudaSuccess || (e = cudaStreamWaitEvent(c, scr.ev_join, 0))))
+        return e;
+    const int nrt = (max_m + 63) / 64;
+    bool pending = false;  // the rest of the previous step's update still runs on s2
     for (int k = 0; k < max_m; k += NBK) {
-        double fl_fac = 0, fl_r = 0, fl_upd = 0;
+        const int par = (k / NBK) & 1;
+        double fl_fac = 0, fl_r = 0, fl_upd = 0, fl_next = 0;
         for (const SysDesc &S : h_sys) {
             if (k >= S.m) continue;
-            double nbe = std::min(NBK, S.m - k), cols = S.ncol - k - nbe;
+            const double nbe = std::min(NBK, S.m - k), cols = S.ncol - k - nbe;
             fl_fac += 2.0 * nbe * nbe * nbe;
             fl_r += 2.0 * nbe * nbe * cols;
             fl_upd += 2.0 * (S.m - nbe) * nbe * cols;
+            const double nrow = std::max(0.0, std::min(64.0, (double)S.m - k - 64));  // next pivot rows
+            fl_next += 2.0 * nbe * ((S.m - nbe) * std::min(64.0, cols) + nrow * std::max(0.0, cols - 64));
         }
         const int cols = max_ncol - k;
         const int cb = (cols + 63) / 64, rb = (max_m + 127) / 128;
-        kt.begin(GM_K_PANEL, fl_fac, s);
-        BLK_SPLIT_DISPATCH(split, (k_blk_factor<SS><<<nsys, FAC_THREADS, fsm, s>>>(
+        kt.begin(GM_K_PANEL, fl_fac, c);
+        BLK_SPLIT_DISPATCH(split, (k_blk_factor<SS><<<nsys, FAC_THREADS, fsm, c>>>(
                                       d_sys, ws, k, scr.x_dig, scr.a11_dig, scr.inv_plane, scr.x_ex, scr.a11_ex,
                                       scr.pmag, st, stage)));
-        kt.end(s);
+        kt.end(c);
+        // R writes digit set `par`, which the rest of the update two steps back read: that
+        // finished before the previous step's next-block update (below) started
+        kt.begin(GM_K_PIVROWS, fl_r, c);
+        BLK_SPLIT_DISPATCH(split, (k_blk_rfused<SS><<<dim3(cb + rb, nsys), 128, rsm, c>>>(
+                                      d_sys, ws, k, cb, scr.x_dig, scr.a11_dig, scr.inv_plane, scr.x_ex, scr.a11_ex,
+                                      scr.fdig[par], scr.fplane, scr.fex[par], scr.rdig[par], scr.cplane,
+                                      scr.rex[par], scr.pmag, st)));
+        kt.end(c);
+        const dim3 gu(nrt, cb, nsys);
+        if (la && cb >= 2 && (e = cudaEventRecord(scr.ev_r, c)) != cudaSuccess) return e;
+        // this step's update rewrites tiles the rest of the previous step's update touches
         if (pending) {
-            if ((e = cudaStreamWaitEvent(s, scr.ev_rest, 0)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(c, scr.ev_rest, 0)) != cudaSuccess) return e;
             pending = false;
         }
-        kt.begin(GM_K_PIVROWS, fl_r, s);
-        BLK_SPLIT_DISPATCH(split, (k_blk_rfused<SS><<<dim3(cb + rb, nsys), 128, rsm, s>>>(
-                                      d_sys, ws, k, cb, scr.x_dig, scr.a11_dig, scr.inv_plane, scr.x_ex, scr.a11_ex,
-                                      scr.fdig, scr.fplane, scr.fex, scr.rdig, scr.cplane, scr.rex, scr.pmag,
-                                      st)));
-        kt.end(s);
-        const dim3 gu((max_m + 63) / 64, (cols + 63) / 64, nsys);
-        if (!scr.s2 || gu.y < 2) {
-            kt.begin(GM_K_GJUPDATE, fl_upd, s);
-            BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<gu, 128, usm, s>>>(d_sys, ws, k, 0, scr.fdig, scr.fplane, scr.fex,
-                                                                           scr.rdig, scr.cplane, scr.rex)));
-            kt.end(s);
+        if (!la || cb < 2) {
+            kt.begin(GM_K_GJUPDATE, fl_upd, c);
+            BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<gu, 128, usm, c>>>(d_sys, ws, k, UPD_ALL, nrt, scr.fdig[par],
+                                                                           scr.fplane, scr.fex[par], scr.rdig[par],
+                                                                           scr.cplane, scr.rex[par])));
+            kt.end(c);
             continue;
         }
-        // look-ahead: the next block's 64 columns first (all the next factor reads), then
-        // the rest on the second stream, overlapping the next factor; the next R kernel
-        // waits for both (it rewrites the pivot rows the rest of this update touches)
-        const double fl_next = fl_upd / gu.y;
-        kt.begin(GM_K_GJUPDATE, fl_next, s);
-        BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(gu.x, 1, nsys), 128, usm, s>>>(
-                                      d_sys, ws, k, 0, scr.fdig, scr.fplane, scr.fex, scr.rdig, scr.cplane, scr.rex)));
-        kt.end(s);
-        if ((e = cudaEventRecord(scr.ev_r, s)) != cudaSuccess || (e = cudaStreamWaitEvent(scr.s2, scr.ev_r, 0)))
-            return e;
+        // look-ahead: everything the next factor and R kernel read (the next block's
+        // columns and its pivot rows) on s1, the rest on s2, overlapping the next factor and
+        // R kernel (disjoint tiles, the other digit set)
+        kt.begin(GM_K_GJUPDATE, fl_next, c);
+        BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(nrt + cb - 1, 1, nsys), 128, usm, c>>>(
+                                      d_sys, ws, k, UPD_NEXT, nrt, scr.fdig[par], scr.fplane, scr.fex[par],
+                                      scr.rdig[par], scr.cplane, scr.rex[par])));
+        kt.end(c);
+        if ((e = cudaStreamWaitEvent(scr.s2, scr.ev_r, 0)) != cudaSuccess) return e;
         kt.begin(GM_K_GJUPDATE, fl_upd - fl_next, scr.s2);
-        BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(gu.x, gu.y - 1, nsys), 128, usm, scr.s2>>>(
-                                      d_sys, ws, k, 1, scr.fdig, scr.fplane, scr.fex, scr.rdig, scr.cplane, scr.rex)));
+        BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(nrt, cb - 1, nsys), 128, usm, scr.s2>>>(
+                                      d_sys, ws, k, UPD_REST, nrt, scr.fdig[par], scr.fplane, scr.fex[par],
+                                      scr.rdig[par], scr.cplane, scr.rex[par])));
         kt.end(scr.s2);
         if ((e = cudaEventRecord(scr.ev_rest, scr.s2)) != cudaSuccess) return e;
         pending = true;
     }
-    if (pending && (e = cudaStreamWaitEvent(s, scr.ev_rest, 0)) != cudaSuccess) return e;
+    if (pending && (e = cudaStreamWaitEvent(c, scr.ev_rest, 0)) != cudaSuccess) return e;
+    if (la && ((e = cudaEventRecord(scr.ev_join, c)) != cudaSuccess || (e = cudaStreamWaitEvent(s, scr.ev_join, 0))))
+        return e;
     return cudaGetLastError();
 }
 

@@ -17,15 +17,19 @@ struct BlkScratch {
     int64_t inv_plane = 0;                                // systems * 64 * 64
     int *x_ex = nullptr, *a11_ex = nullptr;               // [systems * 64]
     float *pmag = nullptr;             // [systems][64]: |pivot| of the block elimination
-    __nv_bfloat16 *fdig = nullptr;     // [S][sum rows][64]: rows of F
+    // digit planes of F and R, two sets used by alternate block steps (the update of one
+    // step still reads its set while the next step's R kernel writes the other)
+    __nv_bfloat16 *fdig[2] = {nullptr, nullptr};  // [S][sum rows][64]: rows of F
     int64_t fplane = 0;
-    int *fex = nullptr;
-    __nv_bfloat16 *adig = nullptr, *r0dig = nullptr, *edig = nullptr, *rdig = nullptr;  // [S][sum cols][64]
+    int *fex[2] = {nullptr, nullptr};
+    __nv_bfloat16 *rdig[2] = {nullptr, nullptr};  // [S][sum cols][64]: columns of R
     int64_t cplane = 0;
-    int *aex = nullptr, *r0ex = nullptr, *eex = nullptr, *rex = nullptr;
-    float2 *r0 = nullptr;              // [sum cols][64]: first approximation of R
-    cudaStream_t s2 = nullptr;         // optional second stream for the look-ahead update
-    cudaEvent_t ev_r = nullptr, ev_rest = nullptr;
+    int *rex[2] = {nullptr, nullptr};
+    // look-ahead (optional): the chain factor -> R -> the next block's update runs on s1
+    // (high priority), the rest of each update on s2; events ev_r (R done), ev_rest
+    // (the rest done) and ev_join (entry and exit of the sweep)
+    cudaStream_t s1 = nullptr, s2 = nullptr;
+    cudaEvent_t ev_r = nullptr, ev_rest = nullptr, ev_join = nullptr;
 };
 
 size_t blk_factor_smem(int split);
