@@ -185,13 +185,22 @@ size_t blk_factor_smem(int split) {
 
 // ----------------------------------------------------------------------------- R = A11^{-1} A12
 
-// Column exponents of a 64 x 64 df32 shared tile D[t][jj] (rows t >= nrow count as 0).
+// Warps of the R kernel and of the update: a 2 x 4 grid over the 64 x 64 tile, each warp
+// 32 rows x 16 columns (two n8 tiles) -- eight warps keep two per scheduler, so one
+// warp's dependent latencies hide behind the other's.
+constexpr int W_NT = 2;
+constexpr int TILE_THREADS = 32 * 2 * (64 / (8 * W_NT));  // 256
+
+// Column exponents of a 64 x 64 df32 shared tile D[t][jj] (every thread takes part: P
+// consecutive lanes per column).
 __device__ __forceinline__ void col_exps64(const float2 *D, int *ex) {
-    if (threadIdx.x < 64) {
-        float mx = 0.f;
-        for (int t = 0; t < NBK; ++t) mx = fmaxf(mx, fabsf(D[t * LDF + threadIdx.x].x));
-        ex[threadIdx.x] = exp_of_max(mx * 1.0000001f);
-    }
+    constexpr int P = TILE_THREADS / 64;
+    const int jj = threadIdx.x / P, part = threadIdx.x % P;
+    float mx = 0.f;
+    for (int t = part; t < NBK; t += P) mx = fmaxf(mx, fabsf(D[t * LDF + jj].x));
+#pragma unroll
+    for (int o = 1; o < P; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (part == 0) ex[jj] = exp_of_max(mx * 1.0000001f);
 }
 
 // P = A D for a 64 x 64 x 64 product: A by rows from global digit planes (64 rows at
@@ -199,40 +208,45 @@ __device__ __forceinline__ void col_exps64(const float2 *D, int *ex) {
 template <int S>
 __device__ __forceinline__ void gemm64_gd(const __nv_bfloat16 *__restrict__ adig, int64_t plane,
                                           const int *__restrict__ aex, const float2 *D, const int *exB,
-                                          __nv_bfloat16 *As, __nv_bfloat16 *Bs, float2 res[2][4][4], int kend = NBK) {
-    const int tid = threadIdx.x, warp = tid >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
-    float acc[S][2][4][4];
+                                          __nv_bfloat16 *As, __nv_bfloat16 *Bs, float2 res[2][W_NT][4],
+                                          int kend = NBK) {
+    const int tid = threadIdx.x, warp = tid >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 8 * W_NT;
+    float acc[S][2][W_NT][4];
 #pragma unroll
     for (int g = 0; g < S; ++g)
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
+            for (int nt = 0; nt < W_NT; ++nt)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[g][mt][nt][c] = 0.f;
 #pragma unroll 1
     for (int t0 = 0; t0 < kend; t0 += 16) {
         __syncthreads();
-        load_digit_tile<S>(adig, plane, NBK, 0, 64, t0, As);
-        for (int e = tid; e < 64 * 16; e += 128) {
+        for (int e = tid; e < S * 128; e += TILE_THREADS) {  // 64 rows x 16 k of every plane of A
+            const int q = e >> 7, row = (e >> 1) & 63, half = e & 1;
+            *(uint4 *)(As + ((size_t)q * 64 + row) * KP + half * 8) =
+                *(const uint4 *)(adig + (int64_t)q * plane + (int64_t)row * NBK + t0 + half * 8);
+        }
+        for (int e = tid; e < 64 * 16; e += TILE_THREADS) {
             const int jj = e >> 4, t = e & 15;
             float d[S];
             digits<S>(D[(t0 + t) * LDF + jj], exB[jj], d);
 #pragma unroll
-            for (int s = 0; s < S; ++s) Bs[((size_t)s * 64 + jj) * KP + t] = __float2bfloat16_rn(d[s]);
+            for (int q = 0; q < S; ++q) Bs[((size_t)q * 64 + jj) * KP + t] = __float2bfloat16_rn(d[q]);
         }
         __syncthreads();
-        warp_mma_levels<S>(As, Bs, 64, 64, wm, wn, acc);
+        warp_mma_levels<S, KP, W_NT>(As, Bs, 64, 64, wm, wn, acc);
     }
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
+        for (int nt = 0; nt < W_NT; ++nt)
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 int r, cl;
                 acc_pos(mt, nt, c, r, cl);
-                res[mt][nt][c] = combine_levels<S>(acc, mt, nt, c, aex[wm + r] + exB[wn + cl] - 12);
+                res[mt][nt][c] = combine_levels<S, W_NT>(acc, mt, nt, c, aex[wm + r] + exB[wn + cl] - 12);
             }
 }
 
@@ -242,7 +256,7 @@ __device__ __forceinline__ void gemm64_gd(const __nv_bfloat16 *__restrict__ adig
 // Blocks [cb, cb + rb): 128 rows each: F = W(i, J) (zero inside J) into row digit planes,
 // with the growth check against the block pivots.
 template <int S>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(TILE_THREADS)
 k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, int cb,
              const __nv_bfloat16 *__restrict__ x_dig, const __nv_bfloat16 *__restrict__ a11_dig, int64_t plane,
              const int *__restrict__ x_ex, const int *__restrict__ a11_ex, __nv_bfloat16 *__restrict__ fdig,
@@ -254,29 +268,36 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
     if (k >= m) return;
     const int nbe = min(NBK, m - k);
     float2 *W = ws + Sy.off;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if ((int)blockIdx.x >= cb) {
-        // a 128 x 64 tile of F through shared memory: read by rows (coalesced over i),
-        // digit planes written by warps along the row (coalesced over t)
+        // a 128 x 64 tile of F through shared memory: read by rows (coalesced over i; the
+        // two halves of the block take columns 0-31 and 32-63), digit planes written by
+        // warps along the row (coalesced over t)
         float2 *Ft = (float2 *)smem_raw;  // [128][LDF]
+        __shared__ float s_mx[2][128];
         __shared__ int s_ex[128];
-        const int i0 = ((int)blockIdx.x - cb) * 128, i = i0 + threadIdx.x;
+        const int r = tid & 127, h = tid >> 7;
+        const int i0 = ((int)blockIdx.x - cb) * 128, i = i0 + r;
         const bool live = i < m && !(i >= k && i < k + nbe);
         float mx = 0.f;
         bool grow = false;
-        for (int t = 0; t < NBK; ++t) {
+        for (int t = h * 32; t < h * 32 + 32; ++t) {
             const float2 v = (live && t < nbe) ? W[(size_t)(k + t) * m + i] : make_float2(0.f, 0.f);
-            Ft[threadIdx.x * LDF + t] = v;
+            Ft[r * LDF + t] = v;
             const float av = fabsf(v.x);
             mx = fmaxf(mx, av);
             if (t < nbe && i >= k + nbe && av > 16.f * pmag[(size_t)blockIdx.y * 64 + t]) grow = true;
         }
         if (grow) atomicOr(&st[Sy.prob].growth, 1);
-        const int e = exp_of_max(mx * 1.0000001f);
-        s_ex[threadIdx.x] = e;
-        if (i < m) fex[Sy.roff + i] = e;
+        s_mx[h][r] = mx;
         __syncthreads();
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        for (int rr = warp; rr < 128 && i0 + rr < m; rr += 4) {
+        if (h == 0) {
+            const int e = exp_of_max(fmaxf(mx, s_mx[1][r]) * 1.0000001f);
+            s_ex[r] = e;
+            if (i < m) fex[Sy.roff + i] = e;
+        }
+        __syncthreads();
+        for (int rr = warp; rr < 128 && i0 + rr < m; rr += TILE_THREADS / 32) {
             const int64_t row = Sy.roff + i0 + rr;
             const int er = s_ex[rr];
             for (int t = lane; t < NBK; t += 32) {
@@ -295,8 +316,8 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
     float2 *Ad = (float2 *)(Bs + S * 64 * KP);  // [64][LDF]: A12, then E
     float2 *Rd = Ad + 64 * LDF;                  // [64][LDF]: R0, then R
     __shared__ int exB[64];
-    const int tid = threadIdx.x, warp = tid >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
-    for (int e = tid; e < 64 * 64; e += 128) {
+    const int wm = (warp & 1) * 32, wn = (warp >> 1) * 8 * W_NT;
+    for (int e = tid; e < 64 * 64; e += TILE_THREADS) {
         const int t = e & 63, jj = e >> 6, j = j0 + jj;
         Ad[t * LDF + jj] = (t < nbe && j < Sy.ncol) ? W[(size_t)j * m + k + t] : make_float2(0.f, 0.f);
     }
@@ -310,7 +331,7 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
     //   pass 0: R0 = X0 A12 -> Rd;  pass 1: E = A12 - A11 R0 -> Ad;  pass 2: R = R0 + X0 E
 #pragma unroll 1
     for (int pass = 0; pass < 3; ++pass) {
-        float2 res[2][4][4];
+        float2 res[2][W_NT][4];
         // K = nbe: the operands are zero beyond the block's live columns.  Passes 0 and 2
         // multiply by the FP32 inverse X0, which four 7-bit digits carry to 2^-28 of each
         // row's maximum -- beyond X0's own accuracy; R0 only has to be good to about FP32
@@ -325,7 +346,7 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
+            for (int nt = 0; nt < W_NT; ++nt)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     int r, cl;
@@ -364,7 +385,7 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
     }
     col_exps64(Rd, exB);
     __syncthreads();
-    for (int e = tid; e < 64 * 64; e += 128) {  // column digit planes of R
+    for (int e = tid; e < 64 * 64; e += TILE_THREADS) {  // column digit planes of R
         const int jj = e >> 6, t = e & 63, j = j0 + jj;
         if (j >= Sy.ncol) continue;
         const int64_t row = Sy.coff + j;
@@ -372,7 +393,7 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
         float d[S];
         digits<S>(Rd[t * LDF + jj], exB[jj], d);
 #pragma unroll
-        for (int s = 0; s < S; ++s) rdig[(int64_t)s * cplane + row * NBK + t] = __float2bfloat16_rn(d[s]);
+        for (int q = 0; q < S; ++q) rdig[(int64_t)q * cplane + row * NBK + t] = __float2bfloat16_rn(d[q]);
     }
 }
 
@@ -413,7 +434,7 @@ enum { UPD_ALL = 0, UPD_NEXT = 1, UPD_REST = 2 };
 // W(i, j) -= (F R)(i, j) for a 64 x 64 tile of rows outside J: both digit tiles (K = 64)
 // arrive in one cp.async batch, then four k-steps of split products without barriers.
 template <int S>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(TILE_THREADS)
 k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, int mode, int nrt,
              const __nv_bfloat16 *__restrict__ fdig, int64_t fplane, const int *__restrict__ fex,
              const __nv_bfloat16 *__restrict__ rdig, int64_t rplane, const int *__restrict__ rex) {
@@ -442,18 +463,18 @@ k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
     cp_async_digits64<S>(rdig + (int64_t)Sy.coff * NBK, rplane, j0, min(64, Sy.ncol - j0), Bs);
     asm volatile("cp.async.wait_all;\n" ::);
     __syncthreads();
-    const int warp = threadIdx.x >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
-    float acc[S][2][4][4];
+    const int warp = threadIdx.x >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 8 * W_NT;
+    float acc[S][2][W_NT][4];
 #pragma unroll
     for (int g = 0; g < S; ++g)
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
+            for (int nt = 0; nt < W_NT; ++nt)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[g][mt][nt][c] = 0.f;
 #pragma unroll 1
-    for (int kk = 0; kk < nbe; kk += 16) warp_mma_levels<S, KP64>(As + kk, Bs + kk, 64, 64, wm, wn, acc);
+    for (int kk = 0; kk < nbe; kk += 16) warp_mma_levels<S, KP64, W_NT>(As + kk, Bs + kk, 64, 64, wm, wn, acc);
     const int *fe = fex + Sy.roff, *re = rex + Sy.coff;
     // read-modify-write of W in groups of four: the four loads of a group are issued
     // together (a load cannot move above an earlier store to W, so one-at-a-time RMW
@@ -461,7 +482,7 @@ k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
+        for (int nt = 0; nt < W_NT; ++nt) {
             float2 w[4];
             bool ok[4];
 #pragma unroll
@@ -478,7 +499,7 @@ k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
                 int r, cl;
                 acc_pos(mt, nt, c, r, cl);
                 const int i = i0 + wm + r, j = j0 + wn + cl;
-                W[(size_t)j * m + i] = df_sub(w[c], combine_levels<S>(acc, mt, nt, c, fe[i] + re[j] - 12));
+                W[(size_t)j * m + i] = df_sub(w[c], combine_levels<S, W_NT>(acc, mt, nt, c, fe[i] + re[j] - 12));
             }
         }
 }
@@ -542,7 +563,7 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
         // R writes digit set `par`, which the rest of the update two steps back read: that
         // finished before the previous step's next-block update (below) started
         kt.begin(GM_K_PIVROWS, fl_r, c);
-        BLK_SPLIT_DISPATCH(split, (k_blk_rfused<SS><<<dim3(cb + rb, nsys), 128, rsm, c>>>(
+        BLK_SPLIT_DISPATCH(split, (k_blk_rfused<SS><<<dim3(cb + rb, nsys), TILE_THREADS, rsm, c>>>(
                                       d_sys, ws, k, cb, scr.x_dig, scr.a11_dig, scr.inv_plane, scr.x_ex, scr.a11_ex,
                                       scr.fdig[par], scr.fplane, scr.fex[par], scr.rdig[par], scr.cplane,
                                       scr.rex[par], scr.pmag, st)));
@@ -556,7 +577,7 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
         }
         if (!la || cb < 2) {
             kt.begin(GM_K_GJUPDATE, fl_upd, c);
-            BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<gu, 128, usm, c>>>(d_sys, ws, k, UPD_ALL, nrt, scr.fdig[par],
+            BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<gu, TILE_THREADS, usm, c>>>(d_sys, ws, k, UPD_ALL, nrt, scr.fdig[par],
                                                                            scr.fplane, scr.fex[par], scr.rdig[par],
                                                                            scr.cplane, scr.rex[par])));
             kt.end(c);
@@ -566,13 +587,13 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
         // columns and its pivot rows) on s1, the rest on s2, overlapping the next factor and
         // R kernel (disjoint tiles, the other digit set)
         kt.begin(GM_K_GJUPDATE, fl_next, c);
-        BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(nrt + cb - 1, 1, nsys), 128, usm, c>>>(
+        BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(nrt + cb - 1, 1, nsys), TILE_THREADS, usm, c>>>(
                                       d_sys, ws, k, UPD_NEXT, nrt, scr.fdig[par], scr.fplane, scr.fex[par],
                                       scr.rdig[par], scr.cplane, scr.rex[par])));
         kt.end(c);
         if ((e = cudaStreamWaitEvent(scr.s2, scr.ev_r, 0)) != cudaSuccess) return e;
         kt.begin(GM_K_GJUPDATE, fl_upd - fl_next, scr.s2);
-        BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(nrt, cb - 1, nsys), 128, usm, scr.s2>>>(
+        BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(nrt, cb - 1, nsys), TILE_THREADS, usm, scr.s2>>>(
                                       d_sys, ws, k, UPD_REST, nrt, scr.fdig[par], scr.fplane, scr.fex[par],
                                       scr.rdig[par], scr.cplane, scr.rex[par])));
         kt.end(scr.s2);

@@ -95,11 +95,11 @@ __device__ __forceinline__ void mma_bf16(float c[4], uint32_t a0, uint32_t a1, u
 // bf16 (16 used) makes the fragment loads bank-conflict free.
 constexpr int KP = 24;
 
-// One warp accumulates a 32 x 32 block: 2 m16 tiles x 4 n8 tiles, S levels.  Tiles are
-// [S][rows][LD] (k fastest); the 16 k of this step start at As / Bs.
-template <int S, int LD = KP>
+// One warp accumulates a 32 x (8 NT) block: 2 m16 tiles x NT n8 tiles, S levels.  Tiles
+// are [S][rows][LD] (k fastest); the 16 k of this step start at As / Bs.
+template <int S, int LD = KP, int NT = 4>
 __device__ __forceinline__ void warp_mma_levels(const __nv_bfloat16 *As, const __nv_bfloat16 *Bs, int BM, int BN,
-                                                int wm, int wn, float acc[S][2][4][4]) {
+                                                int wm, int wn, float acc[S][2][NT][4]) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
@@ -115,9 +115,9 @@ __device__ __forceinline__ void warp_mma_levels(const __nv_bfloat16 *As, const _
 #pragma unroll
         for (int u = 0; u < S; ++u) {
             if (s + u >= S) continue;
-            uint32_t b[4][2];
+            uint32_t b[NT][2];
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
+            for (int nt = 0; nt < NT; ++nt) {
                 const __nv_bfloat16 *p = Bs + ((size_t)u * BN + wn + nt * 8 + g) * LD + 2 * t;
                 b[nt][0] = *(const uint32_t *)(p);
                 b[nt][1] = *(const uint32_t *)(p + 8);
@@ -125,22 +125,22 @@ __device__ __forceinline__ void warp_mma_levels(const __nv_bfloat16 *As, const _
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-                for (int nt = 0; nt < 4; ++nt)
+                for (int nt = 0; nt < NT; ++nt)
                     mma_bf16(acc[s + u][mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b[nt][0], b[nt][1]);
         }
     }
 }
 
 // df32 value of one output position from its S exact level sums and the scale.
-template <int S>
-__device__ __forceinline__ float2 combine_levels(const float acc[S][2][4][4], int mt, int nt, int c, int p) {
+template <int S, int NT = 4>
+__device__ __forceinline__ float2 combine_levels(const float acc[S][2][NT][4], int mt, int nt, int c, int p) {
     float2 v = make_float2(ldexpf(acc[S - 1][mt][nt][c], -7 * (S - 1)), 0.f);
 #pragma unroll
     for (int g = S - 2; g >= 0; --g) v = df_add_f(v, ldexpf(acc[g][mt][nt][c], -7 * g));
     return df_scale(v, p);
 }
 
-// Position within the 32 x 32 warp block of accumulator element (mt, nt, c).
+// Position within the warp block of accumulator element (mt, nt, c).
 __device__ __forceinline__ void acc_pos(int mt, int nt, int c, int &r, int &col) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     r = mt * 16 + g + (c >= 2 ? 8 : 0);
