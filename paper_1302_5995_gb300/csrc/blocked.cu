@@ -38,26 +38,67 @@ constexpr int LDF = NBK + 1;  // padded row length of the df32 shared tiles
 constexpr int FAC_THREADS = 256;
 constexpr int PRS = 36;  // shared stride of the four 32-column groups of the pivot row
 
-// Sort key of a pivot candidate: a larger |v| wins; a NaN counts as 0; a row already used
-// as a pivot never wins (key 0, below the key of every unused row).
-__device__ __forceinline__ unsigned piv_key(float v, int r, unsigned long long used) {
-    if ((used >> r) & 1ull) return 0u;
+// Sort key of a pivot candidate in one 32-bit word, for a single warp max-reduction: the
+// top 26 bits are |v| (its float bits with the six lowest cleared; a NaN counts as 0,
+// and 64 is added so every unused row beats a used one), the low six bits 63 - row, so
+// the lowest row wins among candidates equal to 2^-17 relative.  A used row has key 0.
+__device__ __forceinline__ unsigned piv_key(float v, int r, bool used) {
     const float a = fabsf(v);
-    return a == a ? __float_as_uint(a) + 1u : 1u;
+    const unsigned bits = a == a ? __float_as_uint(a) : 0u;
+    return used ? 0u : (((bits & ~63u) + 64u) | (unsigned)(63 - r));
+}
+
+// Digit planes of 64 rows x 64 k from a shared tile: thread (row, segment) cuts 16
+// consecutive entries of its row (the four segments of a row are consecutive lanes, so
+// the row maximum takes two shuffles) and stores them 16 bytes at a time.
+template <int S, class Get>
+__device__ __forceinline__ void slice_rows64(Get get, int r, int seg, __nv_bfloat16 *__restrict__ dig, int64_t plane,
+                                             int64_t r64, int *__restrict__ ex) {
+    float2 v[16];
+    float mx = 0.f;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+        v[c] = get(r, seg * 16 + c);
+        mx = fmaxf(mx, fabsf(v[c].x));
+    }
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+    const int e = exp_of_max(mx * 1.0000001f);
+    if (seg == 0) ex[r64] = e;
+    uint32_t pk[S][8];
+#pragma unroll
+    for (int c = 0; c < 16; c += 2) {
+        float d0[S], d1[S];
+        digits<S>(v[c], e, d0);
+        digits<S>(v[c + 1], e, d1);
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(d0[q], d1[q]);
+            pk[q][c / 2] = *(const uint32_t *)&h;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        uint4 *dst = (uint4 *)(dig + (int64_t)q * plane + r64 * NBK + seg * 16);
+        dst[0] = make_uint4(pk[q][0], pk[q][1], pk[q][2], pk[q][3]);
+        dst[1] = make_uint4(pk[q][4], pk[q][5], pk[q][6], pk[q][7]);
+    }
 }
 
 // X0 ~ A11^{-1} by Gauss-Jordan on [A11 | I] in FP32 with partial pivoting among the rows
 // of the block.  The 64 x 128 augmented matrix lives in registers: thread (row, cg) holds
 // columns 32 cg .. 32 cg + 31 of one row (four threads per row, eight rows per warp).
-// Rows never move: the pivot row of column t is the unused row of largest |entry| (lowest
-// row on ties), and row t of X0 is the right half of that row at the end.
+// Rows never move: the pivot row of column t is the unused row of largest |entry| (the
+// lowest of rows within 2^-17 of it, see piv_key), and row t of X0 is the right half of
+// that row at the end.
 //
 // One barrier per column.  Every warp keeps its own copy of the current pivot column
 // (rows lane and lane + 32), so it finds the pivot row without talking to the others;
-// the owners of column t + 2 publish it after the update of column t, and each warp
-// brings column t + 1 up to date itself with the same fused multiply-add the owners use
-// (so every copy agrees bit for bit with the registers).  Shared buffers alternate
-// between even and odd columns.
+// the pivot row is published unscaled (its threads need nothing but their registers),
+// every row then applies g = f / pivot (the pivot row scales itself); the owners of
+// column t + 2 publish it after the update of column t, and each warp brings column
+// t + 1 up to date itself with the same operations the owners use (so every copy agrees
+// bit for bit with the registers).  Shared buffers alternate between even and odd columns.
 template <int S>
 __global__ void __launch_bounds__(FAC_THREADS)
 k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int k, __nv_bfloat16 *__restrict__ x_dig,
@@ -66,7 +107,7 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *Adf = (float2 *)smem_raw;       // [64][LDF] A11 (df32)
     float *Xs = (float *)(Adf + 64 * LDF);  // [64][65] rows of X0
-    __shared__ __align__(16) float prow[2][4 * PRS];  // scaled pivot row, registers' order
+    __shared__ __align__(16) float prow[2][4 * PRS];  // pivot row (unscaled), registers' order
     __shared__ float colb[2][64];                     // a column published by its owners
     __shared__ float s_pm[64];
     const SysDesc Sy = sys[blockIdx.x];
@@ -77,9 +118,19 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int row = tid >> 2, cg = tid & 3;
     const unsigned FULL = 0xffffffffu;
-    for (int e = tid; e < 64 * 64; e += FAC_THREADS) {  // A11, padded with the identity beyond nbe
-        const int i = e % 64, j = e / 64;
-        Adf[i * LDF + j] = (i < nbe && j < nbe) ? W[(size_t)(k + j) * m + k + i] : make_float2(i == j ? 1.f : 0.f, 0.f);
+    {  // A11, padded with the identity beyond nbe (all loads in flight at once)
+        constexpr int NL = 64 * 64 / FAC_THREADS;
+        float2 v[NL];
+#pragma unroll
+        for (int q = 0; q < NL; ++q) {
+            const int e = tid + q * FAC_THREADS, i = e % 64, j = e / 64;
+            v[q] = (i < nbe && j < nbe) ? W[(size_t)(k + j) * m + k + i] : make_float2(i == j ? 1.f : 0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < NL; ++q) {
+            const int e = tid + q * FAC_THREADS;
+            Adf[(e % 64) * LDF + e / 64] = v[q];
+        }
     }
     __syncthreads();
     float a[32];
@@ -92,7 +143,7 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
     if (tid < 64) colb[1][tid] = Adf[tid * LDF + 1].x;            // column 1, read at column 0
     __syncthreads();
     const bool hi = warp >= 4;  // this warp's rows are 32 .. 63
-    unsigned long long used = 0ull;
+    bool used0 = false, used1 = false;  // rows lane and lane + 32 have been pivots
     int my_step = 0;
     // The t loop advances four columns at a time (the body unrolled four times), so the
     // register holding a column is known at compile time: group t / 32 drops the four
@@ -104,36 +155,42 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int t = t0 + u;
-            // pivot row: the same reduction over the same copy in every warp
-            const unsigned c0 = piv_key(k0, lane, used), c1 = piv_key(k1, lane + 32, used);
-            const unsigned kmax = __reduce_max_sync(FULL, max(c0, c1));
-            const int p = (int)__reduce_min_sync(FULL, c0 == kmax ? (unsigned)lane : (c1 == kmax ? lane + 32u : 64u));
-            used |= 1ull << p;
-            const float piv = __shfl_sync(FULL, (p & 32) ? k1 : k0, p & 31);
-            const float f = __shfl_sync(FULL, hi ? k1 : k0, row & 31);  // this row's multiplier
+            // this row's multiplier, then the pivot row: the same reduction over the same
+            // copy of column t in every warp
+            const float f = __shfl_sync(FULL, hi ? k1 : k0, row & 31);
+            const unsigned key = __reduce_max_sync(FULL, max(piv_key(k0, lane, used0), piv_key(k1, lane + 32, used1)));
+            const int p = 63 - (int)(key & 63u);
+            used0 |= lane == p;
+            used1 |= lane + 32 == p;
             float *pr = prow[t & 1];
-            if (row == p) {
-                const float ip = 1.f / piv;
+            if (warp == (p >> 3)) {  // warp-uniform: only the pivot row's warp enters
+                if (row == p) {
 #pragma unroll
-                for (int j = 0; j < 32; j += 4)
-                    *(float4 *)&pr[cg * PRS + j] = make_float4(a[j] * ip, a[j + 1] * ip, a[j + 2] * ip, a[j + 3] * ip);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) a[j] = 0.f;  // becomes the scaled row below (g = -1)
-                my_step = t;
+                    for (int j = 0; j < 32; j += 4)
+                        *(float4 *)&pr[cg * PRS + j] = make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
+                    my_step = t;
+                }
             }
+            const float piv = __shfl_sync(FULL, (p & 32) ? k1 : k0, p & 31);
+            const float ip = __frcp_rn(piv);
             if (tid == 0) {
                 s_pm[t] = fabsf(piv);
                 if (t < nbe) pmag[(size_t)blockIdx.x * 64 + t] = fabsf(piv);
             }
             __syncthreads();
-            const float g = (row == p) ? -1.f : f;
+            const float g = f * ip;
+            if (warp == (p >> 3) && row == p) {  // the pivot row becomes the scaled row
 #pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-                const float4 q = *(const float4 *)&pr[cg * PRS + j];
-                a[j] = fmaf(-g, q.x, a[j]);
-                a[j + 1] = fmaf(-g, q.y, a[j + 1]);
-                a[j + 2] = fmaf(-g, q.z, a[j + 2]);
-                a[j + 3] = fmaf(-g, q.w, a[j + 3]);
+                for (int j = 0; j < 32; ++j) a[j] *= ip;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    const float4 q = *(const float4 *)&pr[cg * PRS + j];
+                    a[j] = fmaf(-g, q.x, a[j]);
+                    a[j + 1] = fmaf(-g, q.y, a[j + 1]);
+                    a[j + 2] = fmaf(-g, q.z, a[j + 2]);
+                    a[j + 3] = fmaf(-g, q.w, a[j + 3]);
+                }
             }
             // the owners of column t + 2 publish it (read by every warp at column t + 1);
             // it is in this group at a[u + 2], or at a[u - 2] of the next group at t = 30, 31
@@ -146,8 +203,8 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
                 const int g1 = (t + 1) >> 5;
                 const float q1 = pr[g1 * PRS + (g1 == ct ? u + 1 : 0)];
                 const float n0 = colb[(t + 1) & 1][lane], n1 = colb[(t + 1) & 1][lane + 32];
-                k0 = (lane == p) ? q1 : fmaf(-k0, q1, n0);
-                k1 = (lane + 32 == p) ? q1 : fmaf(-k1, q1, n1);
+                k0 = (lane == p) ? q1 * ip : fmaf(-(k0 * ip), q1, n0);
+                k1 = (lane + 32 == p) ? q1 * ip : fmaf(-(k1 * ip), q1, n1);
             }
         }
         if (cg == ct) {
@@ -167,20 +224,36 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
         for (int t = 0; t < nbe; ++t) mn = fminf(mn, s_pm[t]);
         record_pivot_mx(st + Sy.prob, (double)mn, stage);
     }
-    // digit planes of the rows of X0 and of A11 (K = 64), one warp per row
-    for (int i = warp; i < 128; i += FAC_THREADS / 32) {
-        const int64_t r64 = (int64_t)blockIdx.x * 64 + (i & 63);
-        if (i < 64)  // X0 is FP32: four digits carry it past its accuracy (only four are read)
-            warp_slice_row<(S < 4 ? S : 4)>([&](int q) { return make_float2(Xs[i * 65 + q], 0.f); }, 64, 64, x_dig,
-                                            plane, r64, x_ex);
-        else
-            warp_slice_row<S>([&](int q) { return Adf[(i - 64) * LDF + q]; }, 64, 64, a_dig, plane, r64, a_ex);
-    }
+    // digit planes of the rows of X0 (FP32: four digits carry it past its accuracy, and
+    // only four are read) and of A11 (K = 64)
+    const int64_t r64 = (int64_t)blockIdx.x * 64 + row;
+    slice_rows64<(S < 4 ? S : 4)>([&](int r, int c) { return make_float2(Xs[r * 65 + c], 0.f); }, row, cg, x_dig,
+                                  plane, r64, x_ex);
+    slice_rows64<S>([&](int r, int c) { return Adf[r * LDF + c]; }, row, cg, a_dig, plane, r64, a_ex);
 }
 
 size_t blk_factor_smem(int split) {
     (void)split;
     return (size_t)64 * LDF * sizeof(float2) + (size_t)64 * 65 * sizeof(float);
+}
+
+// ----------------------------------------------------------------------------- full-K digit tiles
+
+constexpr int KP64 = 72;  // row stride (bf16) of a full-K digit tile: 64 + 8 keeps fragment loads conflict-free
+
+// Rows r0 .. r0 + nrows - 1 of every digit plane (64 k each) into shared [S][64][KP64] by
+// cp.async; rows beyond nrows are zero-filled (their source row is r0, in bounds).
+template <int S>
+__device__ __forceinline__ void cp_async_digits64(const __nv_bfloat16 *__restrict__ dig, int64_t plane, int r0,
+                                                  int nrows, __nv_bfloat16 *sm) {
+    for (int e = threadIdx.x; e < S * 64 * 8; e += blockDim.x) {
+        const int s = e >> 9, rem = e & 511, row = rem >> 3, c = rem & 7;
+        const bool ok = row < nrows;
+        const __nv_bfloat16 *src = dig + (int64_t)s * plane + (int64_t)(r0 + (ok ? row : 0)) * NBK + c * 8;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(sm + ((size_t)s * 64 + row) * KP64 + c * 8);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0));
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
 }
 
 // ----------------------------------------------------------------------------- R = A11^{-1} A12
@@ -203,14 +276,22 @@ __device__ __forceinline__ void col_exps64(const float2 *D, int *ex) {
     if (part == 0) ex[jj] = exp_of_max(mx * 1.0000001f);
 }
 
-// P = A D for a 64 x 64 x 64 product: A by rows from global digit planes (64 rows at
-// adig, exponents aex), D a df32 shared tile sliced by columns on the fly (exponents exB).
+// P = A D for a 64 x 64 x 64 product: A by rows from a full-K shared digit tile Ak
+// ([S][64][KP64], exponents aex), D a df32 shared tile cut by columns into Bk (same
+// layout, exponents exB) before the k-steps, which then run without barriers.
 template <int S>
-__device__ __forceinline__ void gemm64_gd(const __nv_bfloat16 *__restrict__ adig, int64_t plane,
-                                          const int *__restrict__ aex, const float2 *D, const int *exB,
-                                          __nv_bfloat16 *As, __nv_bfloat16 *Bs, float2 res[2][W_NT][4],
-                                          int kend = NBK) {
+__device__ __forceinline__ void gemm64_full(const __nv_bfloat16 *Ak, const int *__restrict__ aex, const float2 *D,
+                                            const int *exB, __nv_bfloat16 *Bk, float2 res[2][W_NT][4], int kend) {
     const int tid = threadIdx.x, warp = tid >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 8 * W_NT;
+    __syncthreads();  // exB written, the previous product done with Bk
+    for (int e = tid; e < 64 * 64; e += TILE_THREADS) {
+        const int jj = e >> 6, t = e & 63;
+        float d[S];
+        digits<S>(D[t * LDF + jj], exB[jj], d);
+#pragma unroll
+        for (int q = 0; q < S; ++q) Bk[((size_t)q * 64 + jj) * KP64 + t] = __float2bfloat16_rn(d[q]);
+    }
+    __syncthreads();
     float acc[S][2][W_NT][4];
 #pragma unroll
     for (int g = 0; g < S; ++g)
@@ -221,23 +302,7 @@ __device__ __forceinline__ void gemm64_gd(const __nv_bfloat16 *__restrict__ adig
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[g][mt][nt][c] = 0.f;
 #pragma unroll 1
-    for (int t0 = 0; t0 < kend; t0 += 16) {
-        __syncthreads();
-        for (int e = tid; e < S * 128; e += TILE_THREADS) {  // 64 rows x 16 k of every plane of A
-            const int q = e >> 7, row = (e >> 1) & 63, half = e & 1;
-            *(uint4 *)(As + ((size_t)q * 64 + row) * KP + half * 8) =
-                *(const uint4 *)(adig + (int64_t)q * plane + (int64_t)row * NBK + t0 + half * 8);
-        }
-        for (int e = tid; e < 64 * 16; e += TILE_THREADS) {
-            const int jj = e >> 4, t = e & 15;
-            float d[S];
-            digits<S>(D[(t0 + t) * LDF + jj], exB[jj], d);
-#pragma unroll
-            for (int q = 0; q < S; ++q) Bs[((size_t)q * 64 + jj) * KP + t] = __float2bfloat16_rn(d[q]);
-        }
-        __syncthreads();
-        warp_mma_levels<S, KP, W_NT>(As, Bs, 64, 64, wm, wn, acc);
-    }
+    for (int kk = 0; kk < kend; kk += 16) warp_mma_levels<S, KP64, W_NT>(Ak + kk, Bk + kk, 64, 64, wm, wn, acc);
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -311,20 +376,26 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
     }
     const int j0 = k + nbe + blockIdx.x * 64;
     if (j0 >= Sy.ncol) return;
-    __nv_bfloat16 *As = (__nv_bfloat16 *)smem_raw;
-    __nv_bfloat16 *Bs = As + S * 64 * KP;
-    float2 *Ad = (float2 *)(Bs + S * 64 * KP);  // [64][LDF]: A12, then E
-    float2 *Rd = Ad + 64 * LDF;                  // [64][LDF]: R0, then R
+    constexpr int SX = S < 4 ? S : 4;
+    __nv_bfloat16 *Xk = (__nv_bfloat16 *)smem_raw;  // [SX][64][KP64]: rows of X0
+    __nv_bfloat16 *A11k = Xk + SX * 64 * KP64;      // [S][64][KP64]: rows of A11
+    __nv_bfloat16 *Bk = A11k + S * 64 * KP64;       // [S][64][KP64]: columns of the right operand
+    float2 *Ad = (float2 *)(Bk + S * 64 * KP64);   // [64][LDF]: A12, then E
+    float2 *Rd = Ad + 64 * LDF;                     // [64][LDF]: R0, then R
     __shared__ int exB[64];
     const int wm = (warp & 1) * 32, wn = (warp >> 1) * 8 * W_NT;
+    const __nv_bfloat16 *xd = x_dig + (int64_t)blockIdx.y * 64 * NBK, *ad = a11_dig + (int64_t)blockIdx.y * 64 * NBK;
+    const int *xe = x_ex + blockIdx.y * 64, *ae = a11_ex + blockIdx.y * 64;
+    // both left operands (all 64 k) in flight while A12 is read
+    cp_async_digits64<SX>(xd, plane, 0, 64, Xk);
+    cp_async_digits64<S>(ad, plane, 0, 64, A11k);
     for (int e = tid; e < 64 * 64; e += TILE_THREADS) {
         const int t = e & 63, jj = e >> 6, j = j0 + jj;
         Ad[t * LDF + jj] = (t < nbe && j < Sy.ncol) ? W[(size_t)j * m + k + t] : make_float2(0.f, 0.f);
     }
+    asm volatile("cp.async.wait_all;\n" ::);
     __syncthreads();
     col_exps64(Ad, exB);
-    const __nv_bfloat16 *xd = x_dig + (int64_t)blockIdx.y * 64 * NBK, *ad = a11_dig + (int64_t)blockIdx.y * 64 * NBK;
-    const int *xe = x_ex + blockIdx.y * 64, *ae = a11_ex + blockIdx.y * 64;
     __shared__ int cmax[64], rmax[64];  // column maxima of |X0 E| and |R| (float bits, >= 0)
     if (tid < 64) cmax[tid] = rmax[tid] = 0;
     // three dependent products through one (rolled) copy of the split-product body:
@@ -338,11 +409,10 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
         // (the refinement corrects it) and X0 E is a correction of relative size rho, so
         // four digits of the right operand suffice there.  E itself (pass 1) is a
         // difference of nearly equal terms: full digits.
-        constexpr int SX = S < 4 ? S : 4;
         if (pass == 1)
-            gemm64_gd<S>(ad, plane, ae, Rd, exB, As, Bs, res, (nbe + 15) & ~15);
+            gemm64_full<S>(A11k, ae, Rd, exB, Bk, res, (nbe + 15) & ~15);
         else
-            gemm64_gd<SX>(xd, plane, xe, Ad, exB, As, Bs, res, (nbe + 15) & ~15);
+            gemm64_full<SX>(Xk, xe, Ad, exB, Bk, res, (nbe + 15) & ~15);
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -398,28 +468,14 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
 }
 
 size_t blk_rgemm_smem(int split) {
-    // R part: two digit tiles and two df32 tiles; F part: one 128-row df32 tile
-    return std::max(2 * (size_t)split * 64 * KP * 2 + 2 * 64 * LDF * sizeof(float2), (size_t)128 * LDF * sizeof(float2));
+    // R part: three full-K digit tiles (X0 with at most four planes) and two df32 tiles;
+    // F part: one 128-row df32 tile
+    const size_t sx = split < 4 ? split : 4;
+    return std::max((sx + 2 * (size_t)split) * 64 * KP64 * 2 + 2 * 64 * LDF * sizeof(float2),
+                    (size_t)128 * LDF * sizeof(float2));
 }
 
 // ----------------------------------------------------------------------------- update
-
-constexpr int KP64 = 72;  // row stride (bf16) of a full-K digit tile: 64 + 8 keeps fragment loads conflict-free
-
-// Rows r0 .. r0 + nrows - 1 of every digit plane (64 k each) into shared [S][64][KP64] by
-// cp.async; rows beyond nrows are zero-filled (their source row is r0, in bounds).
-template <int S>
-__device__ __forceinline__ void cp_async_digits64(const __nv_bfloat16 *__restrict__ dig, int64_t plane, int r0,
-                                                  int nrows, __nv_bfloat16 *sm) {
-    for (int e = threadIdx.x; e < S * 64 * 8; e += blockDim.x) {
-        const int s = e >> 9, rem = e & 511, row = rem >> 3, c = rem & 7;
-        const bool ok = row < nrows;
-        const __nv_bfloat16 *src = dig + (int64_t)s * plane + (int64_t)(r0 + (ok ? row : 0)) * NBK + c * 8;
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(sm + ((size_t)s * 64 + row) * KP64 + c * 8);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0));
-    }
-    asm volatile("cp.async.commit_group;\n" ::);
-}
 
 size_t blk_update_smem(int split) { return 2 * (size_t)split * 64 * KP64 * sizeof(__nv_bfloat16); }
 
