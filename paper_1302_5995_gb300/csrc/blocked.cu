@@ -477,7 +477,13 @@ size_t blk_rgemm_smem(int split) {
 
 // ----------------------------------------------------------------------------- update
 
-size_t blk_update_smem(int split) { return 2 * (size_t)split * 64 * KP64 * sizeof(__nv_bfloat16); }
+// row stride (float2) of the shared copy of a W tile: 66 keeps the epilogue's reads
+// (eight rows x four column pairs per half warp) free of bank conflicts
+constexpr int WLD = 66;
+
+size_t blk_update_smem(int split) {
+    return 2 * (size_t)split * 64 * KP64 * sizeof(__nv_bfloat16) + (size_t)64 * WLD * sizeof(float2);
+}
 
 // Which tiles of the update a launch covers.  Tile (ti, tj) holds rows 64 ti .. and the
 // columns 64 tj .. right of J.  The look-ahead splits the update in two:
@@ -488,7 +494,9 @@ size_t blk_update_smem(int split) { return 2 * (size_t)split * 64 * KP64 * sizeo
 enum { UPD_ALL = 0, UPD_NEXT = 1, UPD_REST = 2 };
 
 // W(i, j) -= (F R)(i, j) for a 64 x 64 tile of rows outside J: both digit tiles (K = 64)
-// arrive in one cp.async batch, then four k-steps of split products without barriers.
+// and the tile of W arrive by cp.async, then four k-steps of split products without
+// barriers, and the epilogue reads W from shared memory (no memory latency after the
+// products).
 template <int S>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, int mode, int nrt,
@@ -515,9 +523,27 @@ k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
     const int i0 = ti * 64, j0 = k + nbe + tj * 64;
     if (i0 >= m || j0 >= Sy.ncol) return;
     float2 *W = ws + Sy.off;
+    float2 *Wt = (float2 *)(Bs + S * 64 * KP64);  // [64][WLD]: this tile of W, by columns
+    __shared__ int s_fe[64], s_re[64];
     cp_async_digits64<S>(fdig + (int64_t)Sy.roff * NBK, fplane, i0, min(64, m - i0), As);
     cp_async_digits64<S>(rdig + (int64_t)Sy.coff * NBK, rplane, j0, min(64, Sy.ncol - j0), Bs);
-    asm volatile("cp.async.wait_all;\n" ::);
+    // the tile of W itself is only read by the epilogue: its copy overlaps the products
+    for (int e = threadIdx.x; e < 64 * 64; e += TILE_THREADS) {
+        const int jj = e >> 6, ii = e & 63, i = i0 + ii, j = j0 + jj;
+        const bool ok = i < m && j < Sy.ncol;
+        const float2 *src = W + (ok ? (size_t)j * m + i : 0);
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(Wt + jj * WLD + ii);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0));
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+    if (threadIdx.x < 64) {
+        const int i = i0 + threadIdx.x;
+        s_fe[threadIdx.x] = i < m ? fex[Sy.roff + i] : 0;
+    } else if (threadIdx.x < 128) {
+        const int j = j0 + threadIdx.x - 64;
+        s_re[threadIdx.x - 64] = j < Sy.ncol ? rex[Sy.coff + j] : 0;
+    }
+    asm volatile("cp.async.wait_group 1;\n" ::);  // both digit tiles
     __syncthreads();
     const int warp = threadIdx.x >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 8 * W_NT;
     float acc[S][2][W_NT][4];
@@ -531,33 +557,21 @@ k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
                 for (int c = 0; c < 4; ++c) acc[g][mt][nt][c] = 0.f;
 #pragma unroll 1
     for (int kk = 0; kk < nbe; kk += 16) warp_mma_levels<S, KP64, W_NT>(As + kk, Bs + kk, 64, 64, wm, wn, acc);
-    const int *fe = fex + Sy.roff, *re = rex + Sy.coff;
-    // read-modify-write of W in groups of four: the four loads of a group are issued
-    // together (a load cannot move above an earlier store to W, so one-at-a-time RMW
-    // would pay a full memory latency per element)
+    asm volatile("cp.async.wait_group 0;\n" ::);  // the tile of W
+    __syncthreads();
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int nt = 0; nt < W_NT; ++nt) {
-            float2 w[4];
-            bool ok[4];
+        for (int nt = 0; nt < W_NT; ++nt)
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 int r, cl;
                 acc_pos(mt, nt, c, r, cl);
-                const int i = i0 + wm + r, j = j0 + wn + cl;
-                ok[c] = !(i >= m || j >= Sy.ncol || (i >= k && i < k + nbe));
-                w[c] = ok[c] ? W[(size_t)j * m + i] : make_float2(0.f, 0.f);
+                const int ii = wm + r, jj = wn + cl, i = i0 + ii, j = j0 + jj;
+                if (i >= m || j >= Sy.ncol || (i >= k && i < k + nbe)) continue;
+                W[(size_t)j * m + i] =
+                    df_sub(Wt[jj * WLD + ii], combine_levels<S, W_NT>(acc, mt, nt, c, s_fe[ii] + s_re[jj] - 12));
             }
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if (!ok[c]) continue;
-                int r, cl;
-                acc_pos(mt, nt, c, r, cl);
-                const int i = i0 + wm + r, j = j0 + wn + cl;
-                W[(size_t)j * m + i] = df_sub(w[c], combine_levels<S, W_NT>(acc, mt, nt, c, fe[i] + re[j] - 12));
-            }
-        }
 }
 
 // ----------------------------------------------------------------------------- launcher

@@ -380,13 +380,12 @@ k_mx_merge_slice(const MergeDesc *__restrict__ md, const int *__restrict__ tab, 
 
 // S_parent(q(a), q(c)) = C(a, c) - (Y' X)(a, c), C = [S11 A12; A21 S22].
 template <int S>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(PIPE_THREADS)
 k_mx_merge_update(const MergeDesc *__restrict__ md, const int *__restrict__ tab, const float2 *__restrict__ in,
                   float2 *__restrict__ out, const __nv_bfloat16 *__restrict__ ydig, const int *__restrict__ yex,
                   const __nv_bfloat16 *__restrict__ xdig, const int *__restrict__ xex, int64_t plane,
                   const double *__restrict__ bf, const double *__restrict__ cf, const double *__restrict__ df, int n) {
-    __shared__ __align__(16) __nv_bfloat16 As[S * 64 * KP];
-    __shared__ __align__(16) __nv_bfloat16 Bs[S * 64 * KP];
+    extern __shared__ __align__(16) unsigned char smem_raw[];  // pipe_smem_bytes(S)
     const MergeDesc M = md[blockIdx.z];
     const int rp = M.rp;
     const int a0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
@@ -398,8 +397,9 @@ k_mx_merge_update(const MergeDesc *__restrict__ md, const int *__restrict__ tab,
     const double ih = M.n + 1.0;  // 1/h of the merge's problem
     const int d12 = M.orient ? DIR_N : DIR_E, d21 = M.orient ? DIR_S : DIR_W;
     float2 *O = out + M.out;
-    digit_gemm_chunks<S>(
-        ydig + M.doff, plane, M.kpad, a0, rp, yex + eo, xdig + M.doff, plane, M.kpad, c0, rp, xex + eo, 2 * M.sp, As, Bs,
+    digit_gemm_pipe<S>(
+        ydig + M.doff, plane, M.kpad, a0, rp, yex + eo, xdig + M.doff, plane, M.kpad, c0, rp, xex + eo, 2 * M.sp,
+        (__nv_bfloat16 *)smem_raw,
         [&](const int *r, const int *cl, const float2 *v, bool first) {
             // the four parent positions and their current values (children's entries on
             // the first chunk, the partial result after), read together
@@ -622,8 +622,12 @@ cudaError_t mx_merge_update(const MergeDesc *md, const std::vector<MergeDesc> &h
     MX_SPLIT_DISPATCH(split, (k_mx_merge_slice<SS><<<dim3(2 * rb, nm), 128, 0, s>>>(md, tab, in, ws, rb, ydig, yex,
                                                                                       xdig, xex, plane)));
     dim3 g((max_rp + 63) / 64, (max_rp + 63) / 64, nm);
-    MX_SPLIT_DISPATCH(split, (k_mx_merge_update<SS><<<g, 128, 0, s>>>(md, tab, in, out, ydig, yex, xdig, xex, plane, b,
-                                                                        c, d, n)));
+    cudaError_t e = cudaSuccess;
+    MX_SPLIT_DISPATCH(split, (e = cudaFuncSetAttribute(k_mx_merge_update<SS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)pipe_smem_bytes(SS))));
+    if (e != cudaSuccess) return e;
+    MX_SPLIT_DISPATCH(split, (k_mx_merge_update<SS><<<g, PIPE_THREADS, pipe_smem_bytes(SS), s>>>(
+                                 md, tab, in, out, ydig, yex, xdig, xex, plane, b, c, d, n)));
     kt.end(s);
     return cudaGetLastError();
 }

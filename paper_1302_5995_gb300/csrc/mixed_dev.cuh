@@ -276,4 +276,94 @@ __device__ __forceinline__ void digit_gemm_chunks(const __nv_bfloat16 *__restric
     }
 }
 
+// Pipelined variant of digit_gemm_chunks for 256 threads (a 2 x 4 warp grid, 32 x 16 per
+// warp): K-tiles of 32 move by cp.async through a three-stage ring in dynamic shared
+// memory, so the copy of tile t + 2 overlaps the products of tile t (one barrier per
+// tile).  Same K chunks of at most 512 and the same epilogue interface.
+constexpr int PIPE_K = 32, PIPE_KP = 40, PIPE_STAGES = 3, PIPE_THREADS = 256, PIPE_NT = 2;
+// (40 bf16 = 20 words per row: the fragment loads of eight rows x four words hit 32 banks)
+__host__ __device__ constexpr size_t pipe_smem_bytes(int S) {
+    return (size_t)PIPE_STAGES * 2 * S * 64 * PIPE_KP * sizeof(__nv_bfloat16);
+}
+
+// Rows r0 .. r0 + 63 (zero beyond nrows or kpad) of columns t0 .. t0 + 31 of every digit plane.
+template <int S>
+__device__ __forceinline__ void pipe_load(const __nv_bfloat16 *__restrict__ dig, int64_t plane, int kpad, int r0,
+                                          int nrows, int t0, __nv_bfloat16 *sm) {
+    for (int e = threadIdx.x; e < S * 64 * 4; e += PIPE_THREADS) {
+        const int q = e & 3, row = (e >> 2) & 63, s = e >> 8;
+        const int kk = t0 + q * 8;
+        const bool ok = row < nrows && kk < kpad;
+        const __nv_bfloat16 *src = dig + (int64_t)s * plane + (int64_t)(r0 + (ok ? row : 0)) * kpad + (ok ? kk : 0);
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(sm + ((size_t)s * 64 + row) * PIPE_KP + q * 8);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0));
+    }
+}
+
+template <int S, class Epi>
+__device__ __forceinline__ void digit_gemm_pipe(const __nv_bfloat16 *__restrict__ Ad, int64_t aplane, int akpad,
+                                                int i0, int M, const int *__restrict__ aex,
+                                                const __nv_bfloat16 *__restrict__ Bd, int64_t bplane, int bkpad,
+                                                int j0, int N, const int *__restrict__ bex, int K,
+                                                __nv_bfloat16 *smem, Epi &&epi) {
+    const int warp = threadIdx.x >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 8 * PIPE_NT;
+    const int mrows = min(64, M - i0), ncols = min(64, N - j0);
+    const int ntiles = (K + PIPE_K - 1) / PIPE_K;
+    constexpr size_t PLANES = (size_t)S * 64 * PIPE_KP;
+    auto load = [&](int t) {
+        __nv_bfloat16 *st = smem + (size_t)(t % PIPE_STAGES) * 2 * PLANES;
+        pipe_load<S>(Ad, aplane, akpad, i0, mrows, t * PIPE_K, st);
+        pipe_load<S>(Bd, bplane, bkpad, j0, ncols, t * PIPE_K, st + PLANES);
+    };
+#pragma unroll
+    for (int t = 0; t < PIPE_STAGES - 1; ++t) {
+        if (t < ntiles) load(t);
+        asm volatile("cp.async.commit_group;\n" ::);
+    }
+    float acc[S][2][PIPE_NT][4];
+#pragma unroll
+    for (int g = 0; g < S; ++g)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < PIPE_NT; ++nt)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[g][mt][nt][c] = 0.f;
+#pragma unroll 1
+    for (int t = 0; t < ntiles; ++t) {
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(PIPE_STAGES - 2));  // tile t has landed
+        __syncthreads();  // ... for every thread, and tile t - 1's products are done
+        if (t + PIPE_STAGES - 1 < ntiles) load(t + PIPE_STAGES - 1);
+        asm volatile("cp.async.commit_group;\n" ::);
+        const __nv_bfloat16 *As = smem + (size_t)(t % PIPE_STAGES) * 2 * PLANES, *Bs = As + PLANES;
+        warp_mma_levels<S, PIPE_KP, PIPE_NT>(As, Bs, 64, 64, wm, wn, acc);
+        if (t * PIPE_K + 16 < K) warp_mma_levels<S, PIPE_KP, PIPE_NT>(As + 16, Bs + 16, 64, 64, wm, wn, acc);
+        const int tend = (t + 1) * PIPE_K;
+        if (tend % 512 == 0 || t == ntiles - 1) {  // end of a K chunk: hand the results over
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < PIPE_NT; ++nt) {
+                    int rr[4], cc[4];
+                    float2 vv[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        int r, cl;
+                        acc_pos(mt, nt, c, r, cl);
+                        const int i = min(i0 + wm + r, M - 1), j = min(j0 + wn + cl, N - 1);
+                        rr[c] = wm + r;
+                        cc[c] = wn + cl;
+                        vv[c] = combine_levels<S, PIPE_NT>(acc, mt, nt, c, aex[i] + bex[j] - 12);
+                        acc[0][mt][nt][c] = 0.f;
+                    }
+#pragma unroll
+                    for (int g = 1; g < S; ++g)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[g][mt][nt][c] = 0.f;
+                    epi(rr, cc, vv, tend <= 512);
+                }
+        }
+    }
+}
+
 }  // namespace gm
