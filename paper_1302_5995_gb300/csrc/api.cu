@@ -315,6 +315,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
     const int split = o.split_digits ? o.split_digits : 6;
     if (mixed && (split < 3 || split > 6)) return GM_EINVAL;
     if (leaf_smem_bytes(dp.max_leaf_a, dp.max_leaf_b) > 220 * 1024) return GM_EUNSUPPORTED;
+    if (mixed && mx_leaf_smem_bytes(dp.max_leaf_a, dp.max_leaf_b) > 220 * 1024) return GM_EUNSUPPORTED;
     // the leaf kernel gives each inner-ring right-hand side one of 64 thread columns
     if (2 * (dp.max_leaf_a - 2) + 2 * (dp.max_leaf_b - 2) - 4 > 64) return GM_EUNSUPPORTED;
     if (mixed && !blockpiv) {
@@ -368,11 +369,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
     if (!mixed) {
         CK(launch_leaf(dp.d_leaves, P.leaves, dp.max_leaf_a, dp.max_leaf_b, db, dc, dd, A64, dst, 0, s, kt));
     } else {
-        DBuf leaf64;
-        if ((rc = leaf64.alloc(P.leaf_doubles * 8, s))) return rc;
-        CK(launch_leaf(dp.d_leaves, P.leaves, dp.max_leaf_a, dp.max_leaf_b, db, dc, dd, leaf64.as<double>(), dst, 0,
-                       s, kt));
-        CK(mx_convert(leaf64.as<double>(), Adf, P.leaf_doubles, s, kt));
+        CK(mx_leaf(dp.d_leaves, P.leaves, dp.max_leaf_a, dp.max_leaf_b, db, dc, dd, Adf, dst, 0, s, kt));
     }
 
     // scratch of the sweeps, sized for the largest stage and for the roots
