@@ -315,7 +315,9 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
     const int split = o.split_digits ? o.split_digits : 6;
     if (mixed && (split < 3 || split > 6)) return GM_EINVAL;
     if (leaf_smem_bytes(dp.max_leaf_a, dp.max_leaf_b) > 220 * 1024) return GM_EUNSUPPORTED;
-    if (mixed && mx_leaf_smem_bytes(dp.max_leaf_a, dp.max_leaf_b) > 220 * 1024) return GM_EUNSUPPORTED;
+    if (mixed && std::max(mx_leaf_smem_bytes(dp.max_leaf_a, dp.max_leaf_b),
+                          mx_leaf_lines_smem_bytes(dp.max_leaf_a, dp.max_leaf_b)) > 220 * 1024)
+        return GM_EUNSUPPORTED;
     // the leaf kernel gives each inner-ring right-hand side one of 64 thread columns
     if (2 * (dp.max_leaf_a - 2) + 2 * (dp.max_leaf_b - 2) - 4 > 64) return GM_EUNSUPPORTED;
     if (mixed && !blockpiv) {

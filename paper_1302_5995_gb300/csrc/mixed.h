@@ -24,6 +24,7 @@ struct MxScratch {
 
 cudaError_t mx_convert(const double *x, float2 *y, int64_t n, cudaStream_t s, KTimer &kt);
 size_t mx_leaf_smem_bytes(int a, int b);
+size_t mx_leaf_lines_smem_bytes(int a, int b);
 cudaError_t mx_leaf(const LeafDesc *d_leaves, const std::vector<LeafDesc> &h_leaves, int max_a, int max_b,
                     const double *b, const double *c, const double *d, float2 *out, Status *st, int stage,
                     cudaStream_t s, KTimer &kt);

@@ -255,11 +255,256 @@ k_mx_leaf(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf0, c
     }
 }
 
+// ----------------------------------------------------------------------------- by lines
+
+// The same S by block elimination of the interior one grid line at a time (lines
+// jj = 0 .. ib - 1 of ia unknowns each; A_ii is block tridiagonal in this order, with
+// diagonal couplings between neighbouring lines).  With the lines below jj eliminated,
+// the state is
+//   Sig : the Schur complement on the ring (starts as A_bb),
+//   C   : ring -> line jj couplings (r x ia),   C' : line jj -> ring (ia x r),
+//   T   : the line's block (ia x ia),           N  : line jj -> line jj + 1 (diagonal),
+// and eliminating line jj is
+//   [P | Q] = T^{-1} [C' | N]       (Gauss-Jordan with partial pivoting within the line)
+//   Sig    -= C P
+//   T'      = D_{jj+1} - S_{jj+1} Q,   C_next = direct - C Q,   C'_next = direct - S_{jj+1} P
+// (S_{jj+1}: line jj + 1 -> line jj, diagonal).  Fourteen block steps for a 16 x 16 leaf
+// instead of 196 scalar ones, and about a third of the band kernel's shared memory, so
+// several leaves share an SM.  Pivoting stays within a line (like the blocked sweep's
+// block-local pivoting): a pivot far below the line's diagonal scale raises the growth
+// flag, and the automatic mode then rebuilds the problem in FP64.
+//
+// Only ring nodes whose interior neighbour lies in an eliminated line (or the current
+// one) couple to the state; they are listed in line order (tl), so the ones in play
+// after line jj are a prefix of the list.
+
+constexpr int LINE_THREADS = 256;
+
+size_t mx_leaf_lines_smem_bytes(int a, int b) {
+    const int ia = a - 2, ib = b - 2, r = 2 * a + 2 * b - 4;
+    const int ni = (ia > 0 && ib > 0) ? ia * ib : 0;
+    const int WM = 2 * ia + r;
+    return 8 * ((size_t)r * r + 2 * (size_t)ia * WM + 2 * (size_t)r * ia + (size_t)ni * 5 + 2 * (size_t)r +
+                (size_t)ia) +
+           4 * (2 * (size_t)r + 2 * (size_t)ia) + 16;
+}
+
+__global__ void __launch_bounds__(LINE_THREADS)
+k_mx_leaf_lines(const LeafDesc *__restrict__ leaves, const double *__restrict__ bf0, const double *__restrict__ cf0,
+                const double *__restrict__ df0, float2 *__restrict__ out, Status *st, int stage) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const LeafDesc Ld = leaves[blockIdx.x];
+    const int n = Ld.n;
+    const double *bf = bf0 + Ld.coef, *cf = cf0 + Ld.coef, *df = df0 + Ld.coef;
+    const int a = Ld.a, bb = Ld.b, ia = a - 2, ib = bb - 2, r = 2 * a + 2 * bb - 4;
+    const int WM = 2 * ia + r;  // row of M: [T | C' (by ring position) | N]
+    const double ih = n + 1.0;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const unsigned FULL = 0xffffffffu;
+    float2 *Sig = (float2 *)smem_raw;            // r x r, column-major
+    float2 *Mb = Sig + (size_t)r * r;            // 2 x ia x WM
+    float2 *Cb = Mb + 2 * (size_t)ia * WM;       // 2 x r x ia
+    float2 *wint = Cb + 2 * (size_t)r * ia;      // ni x 5: C, E, W, N, S of each interior equation
+    float2 *wdir = wint + (size_t)ia * ib * 5;   // r: ring node -> its interior neighbour
+    float2 *wbak = wdir + r;                     // r: interior neighbour -> ring node
+    float2 *pvs = wbak + r;                      // ia: pivots of the current line
+    int *tl = (int *)(pvs + ia);                 // r: ring nodes in line order
+    int *inner = tl + r;                         // r: interior neighbour (ii + ia jj) or -1
+    int *prow = inner + r;                       // ia: pivot row of each column of T
+    auto gnode = [&](int ii, int jj) { return (Ld.x0 + 1 + ii) + n * (Ld.y0 + 1 + jj); };
+
+    // weights (FP64 stencil, then df32) and the ring's bookkeeping
+    for (int q = tid; q < ia * ib; q += LINE_THREADS) {
+        const int g = gnode(q % ia, q / ia);
+#pragma unroll
+        for (int dir = 0; dir < 5; ++dir) wint[q * 5 + dir] = df_from_d(stencil_w_mx(bf, cf, df, ih, g, dir));
+    }
+    for (int e = tid; e < r * r; e += LINE_THREADS) Sig[e] = make_float2(0.f, 0.f);
+    for (int l = tid; l < r; l += LINE_THREADS) {
+        int il, jl, ii, jj, dir;
+        ring_node_mx(a, bb, l, il, jl);
+        const int gl = (Ld.x0 + il) + n * (Ld.y0 + jl);
+        if (inner_nb(a, bb, il, jl, ii, jj, dir)) {
+            inner[l] = ii + ia * jj;
+            wdir[l] = df_from_d(stencil_w_mx(bf, cf, df, ih, gl, dir));
+            wbak[l] = df_from_d(stencil_w_mx(bf, cf, df, ih, gnode(ii, jj), opposite(dir)));
+        } else {
+            inner[l] = -1;
+        }
+    }
+    __syncthreads();
+    // A_bb: each ring node's own weight and its weights on ring neighbours
+    for (int l = tid; l < r; l += LINE_THREADS) {
+        int il, jl;
+        ring_node_mx(a, bb, l, il, jl);
+        const int gl = (Ld.x0 + il) + n * (Ld.y0 + jl);
+        Sig[l + (size_t)r * l] = df_from_d(stencil_w_mx(bf, cf, df, ih, gl, DIR_C));
+        const int dx[4] = {1, -1, 0, 0}, dy[4] = {0, 0, 1, -1}, dd[4] = {DIR_E, DIR_W, DIR_N, DIR_S};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i2 = il + dx[q], j2 = jl + dy[q];
+            if (i2 < 0 || i2 >= a || j2 < 0 || j2 >= bb) continue;
+            if (!(i2 == 0 || i2 == a - 1 || j2 == 0 || j2 == bb - 1)) continue;  // interior
+            int m;
+            if (j2 == 0) m = i2;
+            else if (i2 == a - 1) m = a - 1 + j2;
+            else if (j2 == bb - 1) m = (a - 1) + (bb - 1) + (a - 1 - i2);
+            else m = 2 * (a - 1) + (bb - 1) + (bb - 1 - j2);
+            Sig[l + (size_t)r * m] = df_from_d(stencil_w_mx(bf, cf, df, ih, gl, dd[q]));
+        }
+    }
+    if (tid == 0) {  // ring nodes with an interior neighbour, by line
+        int c = 0;
+        for (int jj = 0; jj < ib; ++jj)
+            for (int l = 0; l < r; ++l)
+                if (inner[l] >= 0 && inner[l] / ia == jj) tl[c++] = l;
+    }
+    float dmax = 0.f;  // diagonal scale of A_ii (growth check)
+    for (int q = 0; q < ia * ib; ++q) dmax = fmaxf(dmax, fabsf(wint[q * 5 + DIR_C].x));
+    __syncthreads();
+    // number of listed ring nodes in lines 0 .. jj
+    auto in_play = [&](int jj) {
+        int c = 0;
+        for (int l = 0; l < r; ++l) c += (inner[l] >= 0 && inner[l] / ia <= jj);
+        return c;
+    };
+    float2 *M = Mb, *Mn = Mb + (size_t)ia * WM, *C = Cb, *Cn = Cb + (size_t)r * ia;
+    // line 0
+    for (int e = tid; e < ia * WM; e += LINE_THREADS) {
+        const int k = e / WM, c = e % WM;
+        float2 v = make_float2(0.f, 0.f);
+        if (c < ia) {
+            if (c == k) v = wint[k * 5 + DIR_C];
+            else if (c == k + 1) v = wint[k * 5 + DIR_E];
+            else if (c == k - 1) v = wint[k * 5 + DIR_W];
+        } else if (c < ia + r) {
+            const int l = c - ia;
+            if (inner[l] == k) v = wbak[l];  // line 0: inner index k + ia * 0
+        } else if (c - ia - r == k && ib > 1) {
+            v = wint[k * 5 + DIR_N];
+        }
+        M[e] = v;
+    }
+    for (int e = tid; e < r * ia; e += LINE_THREADS) {
+        const int l = e / ia, k = e % ia;
+        C[e] = inner[l] == k ? wdir[l] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    bool grow = false;
+    float pmin = 3.0e38f;
+    bool bad = false;
+    for (int jj = 0; jj < ib; ++jj) {
+        const int L = in_play(jj);                 // listed ring nodes in play
+        const bool more = jj + 1 < ib;
+        const int ncn = more ? ia : 0;             // columns of N
+        // Gauss-Jordan on M without moving rows: column t's pivot row is prow[t]; rows
+        // stay unscaled until the end (row p_t holds pivot p_t times solution row t)
+        unsigned used = 0u;
+        for (int t = 0; t < ia; ++t) {
+            // pivot: the unused row of largest |hi| in column t (the lowest among equals);
+            // key 0 for used rows and padding lanes, |hi| bits + 1 otherwise (NaN as 0)
+            unsigned key = 0u;
+            if (lane < ia && !((used >> lane) & 1u)) {
+                const float v = fabsf(M[(size_t)lane * WM + t].x);
+                key = (v == v ? __float_as_uint(v) : 0u) + 1u;
+            }
+            const unsigned kmax = __reduce_max_sync(FULL, key);
+            const int p = (int)__reduce_min_sync(FULL, key == kmax ? (unsigned)lane : 0xffffffffu);
+            used |= 1u << p;
+            const float2 pv = M[(size_t)p * WM + t];
+            const float2 ipv = df_rcp(pv);
+            if (tid == 0) {
+                prow[t] = p;
+                pvs[t] = pv;
+                const float ap = fabsf(pv.x);
+                if (!(ap > 0.f) || !(ap == ap)) bad = true;
+                pmin = fminf(pmin, ap);
+                if (ap < 0x1p-12f * dmax) grow = true;
+            }
+            // every other row: row -= (row[t] / pivot) * pivot row, over the columns in play
+            const int nT = ia - 1 - t, ncol = nT + L + ncn;
+            for (int e = tid; e < (ia - 1) * ncol; e += LINE_THREADS) {
+                int row = e / ncol;
+                row += row >= p;
+                const int q = e % ncol;
+                const int c = q < nT ? t + 1 + q : (q < nT + L ? ia + tl[q - nT] : ia + r + (q - nT - L));
+                const float2 g = df_mul(M[(size_t)row * WM + t], ipv);
+                M[(size_t)row * WM + c] = df_sub(M[(size_t)row * WM + c], df_mul(g, M[(size_t)p * WM + c]));
+            }
+            __syncthreads();
+        }
+        // scale the solution rows: [P | Q] row t = row p_t / pivot t
+        for (int e = tid; e < ia * (L + ncn); e += LINE_THREADS) {
+            const int t = e / (L + ncn), q = e % (L + ncn);
+            const int c = q < L ? ia + tl[q] : ia + r + (q - L);
+            float2 &x = M[(size_t)prow[t] * WM + c];
+            x = df_mul(x, df_rcp(pvs[t]));
+        }
+        __syncthreads();
+        // Sig -= C P over the ring nodes in play
+        for (int e = tid; e < L * L; e += LINE_THREADS) {
+            const int l = tl[e % L], m = tl[e / L];
+            float2 acc = make_float2(0.f, 0.f);
+            for (int t = 0; t < ia; ++t)
+                acc = df_add(acc, df_mul(C[(size_t)l * ia + t], M[(size_t)prow[t] * WM + ia + m]));
+            Sig[l + (size_t)r * m] = df_sub(Sig[l + (size_t)r * m], acc);
+        }
+        if (more) {
+            const int L2 = in_play(jj + 1);
+            // next line's T = D - S Q and its C' = direct - S P, N
+            for (int e = tid; e < ia * WM; e += LINE_THREADS) {
+                const int k = e / WM, c = e % WM;
+                const int q1 = k + ia * (jj + 1);  // interior index of row k of the next line
+                float2 v = make_float2(0.f, 0.f);
+                if (c < ia) {
+                    if (c == k) v = wint[q1 * 5 + DIR_C];
+                    else if (c == k + 1) v = wint[q1 * 5 + DIR_E];
+                    else if (c == k - 1) v = wint[q1 * 5 + DIR_W];
+                    v = df_sub(v, df_mul(wint[q1 * 5 + DIR_S], M[(size_t)prow[k] * WM + ia + r + c]));
+                } else if (c < ia + r) {
+                    const int l = c - ia;
+                    if (inner[l] == q1) v = wbak[l];
+                    else if (inner[l] >= 0 && inner[l] / ia <= jj)
+                        v = df_neg(df_mul(wint[q1 * 5 + DIR_S], M[(size_t)prow[k] * WM + c]));
+                } else if (c - ia - r == k && jj + 2 < ib) {
+                    v = wint[q1 * 5 + DIR_N];
+                }
+                Mn[e] = v;
+            }
+            // next C = direct - C Q
+            for (int e = tid; e < L2 * ia; e += LINE_THREADS) {
+                const int l = tl[e / ia], k = e % ia;
+                float2 v = inner[l] == k + ia * (jj + 1) ? wdir[l] : make_float2(0.f, 0.f);
+                if (inner[l] / ia <= jj) {
+                    float2 acc = make_float2(0.f, 0.f);
+                    for (int t = 0; t < ia; ++t)
+                        acc = df_add(acc, df_mul(C[(size_t)l * ia + t], M[(size_t)prow[t] * WM + ia + r + k]));
+                    v = df_sub(v, acc);
+                }
+                Cn[(size_t)l * ia + k] = v;
+            }
+        }
+        __syncthreads();
+        float2 *tm = M; M = Mn; Mn = tm;
+        float2 *tc = C; C = Cn; Cn = tc;
+    }
+    if (tid == 0) {
+        record_pivot_mx(st + Ld.prob, bad ? 0.0 : (double)pmin, stage);
+        if (grow) atomicOr(&st[Ld.prob].growth, 1);
+    }
+    float2 *S = out + Ld.off;
+    for (int e = tid; e < r * r; e += LINE_THREADS) S[e] = Sig[e];
+}
+
 cudaError_t mx_leaf(const LeafDesc *d_leaves, const std::vector<LeafDesc> &h_leaves, int max_a, int max_b,
                     const double *b, const double *c, const double *d, float2 *out, Status *st, int stage,
                     cudaStream_t s, KTimer &kt) {
-    const size_t smem = mx_leaf_smem_bytes(max_a, max_b);
-    cudaError_t e = cudaFuncSetAttribute(k_mx_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // by lines when every leaf has an interior and its lines fit one warp's lanes
+    bool lines = true;
+    for (const LeafDesc &L : h_leaves) lines = lines && L.a >= 3 && L.b >= 3 && L.a - 2 <= 32;
+    const size_t smem = lines ? mx_leaf_lines_smem_bytes(max_a, max_b) : mx_leaf_smem_bytes(max_a, max_b);
+    cudaError_t e = cudaFuncSetAttribute(lines ? (const void *)k_mx_leaf_lines : (const void *)k_mx_leaf,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     double fl = 0.0;  // the same algorithmic count as the FP64 leaf
     for (const LeafDesc &L : h_leaves) {
@@ -269,7 +514,10 @@ cudaError_t mx_leaf(const LeafDesc *d_leaves, const std::vector<LeafDesc> &h_lea
         fl += 4.0 * ni * ia * ia + 6.0 * nq * ni * ia;
     }
     kt.begin(GM_K_LEAF, fl, s);
-    k_mx_leaf<<<(int)h_leaves.size(), LEAF_THREADS, smem, s>>>(d_leaves, b, c, d, out, st, stage);
+    if (lines)
+        k_mx_leaf_lines<<<(int)h_leaves.size(), LINE_THREADS, smem, s>>>(d_leaves, b, c, d, out, st, stage);
+    else
+        k_mx_leaf<<<(int)h_leaves.size(), LEAF_THREADS, smem, s>>>(d_leaves, b, c, d, out, st, stage);
     kt.end(s);
     return cudaGetLastError();
 }
