@@ -286,7 +286,14 @@ size_t mx_leaf_lines_smem_bytes(int a, int b) {
     const int WM = 2 * ia + r;
     return 8 * ((size_t)r * r + 2 * (size_t)ia * WM + 2 * (size_t)r * ia + (size_t)ni * 5 + 2 * (size_t)r +
                 (size_t)ia) +
-           4 * (2 * (size_t)r + 2 * (size_t)ia) + 16;
+           4 * (3 * (size_t)r + 2 * (size_t)ia) + 16;
+}
+
+// df32 a + b with an error of a few units of 2^-48 max(|a|, |b|) (df_add also keeps it
+// relative to |a + b| under cancellation); enough for these sums, at half the instructions
+__device__ __forceinline__ float2 df_add_quick(float2 a, float2 b) {
+    const float2 s = two_sum(a.x, b.x);
+    return fast_two_sum(s.x, s.y + (a.y + b.y));
 }
 
 __global__ void __launch_bounds__(LINE_THREADS)
@@ -299,7 +306,7 @@ k_mx_leaf_lines(const LeafDesc *__restrict__ leaves, const double *__restrict__ 
     const int a = Ld.a, bb = Ld.b, ia = a - 2, ib = bb - 2, r = 2 * a + 2 * bb - 4;
     const int WM = 2 * ia + r;  // row of M: [T | C' (by ring position) | N]
     const double ih = n + 1.0;
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
     float2 *Sig = (float2 *)smem_raw;            // r x r, column-major
     float2 *Mb = Sig + (size_t)r * r;            // 2 x ia x WM
@@ -308,10 +315,14 @@ k_mx_leaf_lines(const LeafDesc *__restrict__ leaves, const double *__restrict__ 
     float2 *wdir = wint + (size_t)ia * ib * 5;   // r: ring node -> its interior neighbour
     float2 *wbak = wdir + r;                     // r: interior neighbour -> ring node
     float2 *pvs = wbak + r;                      // ia: pivots of the current line
-    int *tl = (int *)(pvs + ia);                 // r: ring nodes in line order
-    int *inner = tl + r;                         // r: interior neighbour (ii + ia jj) or -1
-    int *prow = inner + r;                       // ia: pivot row of each column of T
+    int *tl = (int *)(pvs + ia);                 // r: ring nodes with an interior neighbour, by line
+    int *iln = tl + r;                           // r: line of the interior neighbour (-1: corner)
+    int *iix = iln + r;                          // r: its position in the line
+    int *prow = iix + r;                         // ia: pivot row of each column of T
     auto gnode = [&](int ii, int jj) { return (Ld.x0 + 1 + ii) + n * (Ld.y0 + 1 + jj); };
+    // listed ring nodes in play once lines 0 .. jj are in: the bottom row and the side
+    // nodes of each line, the top row with the last line
+    auto in_play = [&](int jj) { return (a - 2) + 2 * (jj + 1) + (jj == ib - 1 ? a - 2 : 0); };
 
     // weights (FP64 stencil, then df32) and the ring's bookkeeping
     for (int q = tid; q < ia * ib; q += LINE_THREADS) {
@@ -325,11 +336,22 @@ k_mx_leaf_lines(const LeafDesc *__restrict__ leaves, const double *__restrict__ 
         ring_node_mx(a, bb, l, il, jl);
         const int gl = (Ld.x0 + il) + n * (Ld.y0 + jl);
         if (inner_nb(a, bb, il, jl, ii, jj, dir)) {
-            inner[l] = ii + ia * jj;
+            iln[l] = jj;
+            iix[l] = ii;
             wdir[l] = df_from_d(stencil_w_mx(bf, cf, df, ih, gl, dir));
             wbak[l] = df_from_d(stencil_w_mx(bf, cf, df, ih, gnode(ii, jj), opposite(dir)));
         } else {
-            inner[l] = -1;
+            iln[l] = -1;
+            iix[l] = -1;
+        }
+        // the list: bottom row, then (left, right) of each line, then the top row
+        const int nb_ = a - 2;
+        if (l < nb_) tl[l] = 1 + l;
+        else if (l < nb_ + 2 * ib) {
+            const int j2 = (l - nb_) >> 1;
+            tl[l] = ((l - nb_) & 1) ? a + j2 : r - 1 - j2;
+        } else if (l < 2 * nb_ + 2 * ib) {
+            tl[l] = 2 * a + bb - 4 - (l - nb_ - 2 * ib);
         }
     }
     __syncthreads();
@@ -353,23 +375,8 @@ k_mx_leaf_lines(const LeafDesc *__restrict__ leaves, const double *__restrict__ 
             Sig[l + (size_t)r * m] = df_from_d(stencil_w_mx(bf, cf, df, ih, gl, dd[q]));
         }
     }
-    if (tid == 0) {  // ring nodes with an interior neighbour, by line
-        int c = 0;
-        for (int jj = 0; jj < ib; ++jj)
-            for (int l = 0; l < r; ++l)
-                if (inner[l] >= 0 && inner[l] / ia == jj) tl[c++] = l;
-    }
-    float dmax = 0.f;  // diagonal scale of A_ii (growth check)
-    for (int q = 0; q < ia * ib; ++q) dmax = fmaxf(dmax, fabsf(wint[q * 5 + DIR_C].x));
-    __syncthreads();
-    // number of listed ring nodes in lines 0 .. jj
-    auto in_play = [&](int jj) {
-        int c = 0;
-        for (int l = 0; l < r; ++l) c += (inner[l] >= 0 && inner[l] / ia <= jj);
-        return c;
-    };
     float2 *M = Mb, *Mn = Mb + (size_t)ia * WM, *C = Cb, *Cn = Cb + (size_t)r * ia;
-    // line 0
+    // line 0: M = [D_0 | direct C' | diag N_0], C = direct
     for (int e = tid; e < ia * WM; e += LINE_THREADS) {
         const int k = e / WM, c = e % WM;
         float2 v = make_float2(0.f, 0.f);
@@ -379,7 +386,7 @@ k_mx_leaf_lines(const LeafDesc *__restrict__ leaves, const double *__restrict__ 
             else if (c == k - 1) v = wint[k * 5 + DIR_W];
         } else if (c < ia + r) {
             const int l = c - ia;
-            if (inner[l] == k) v = wbak[l];  // line 0: inner index k + ia * 0
+            if (iln[l] == 0 && iix[l] == k) v = wbak[l];
         } else if (c - ia - r == k && ib > 1) {
             v = wint[k * 5 + DIR_N];
         }
@@ -387,16 +394,19 @@ k_mx_leaf_lines(const LeafDesc *__restrict__ leaves, const double *__restrict__ 
     }
     for (int e = tid; e < r * ia; e += LINE_THREADS) {
         const int l = e / ia, k = e % ia;
-        C[e] = inner[l] == k ? wdir[l] : make_float2(0.f, 0.f);
+        C[e] = (iln[l] == 0 && iix[l] == k) ? wdir[l] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    bool grow = false;
+    // thread roles in the Gauss-Jordan steps: lane -> (row, column offset); rows per pass
+    const int RP = ia <= 16 ? 16 : 32, CPW = 32 / RP;
+    const int grow_ = lane % RP, gcol = warp * CPW + lane / RP, gstride = 8 * CPW;
+    bool grow = false, bad = false;
     float pmin = 3.0e38f;
-    bool bad = false;
     for (int jj = 0; jj < ib; ++jj) {
-        const int L = in_play(jj);                 // listed ring nodes in play
+        const int L = in_play(jj);
         const bool more = jj + 1 < ib;
-        const int ncn = more ? ia : 0;             // columns of N
+        const int ncn = more ? ia : 0;  // columns of N
+        const int nfix = L + ncn;       // columns right of T in play
         // Gauss-Jordan on M without moving rows: column t's pivot row is prow[t]; rows
         // stay unscaled until the end (row p_t holds pivot p_t times solution row t)
         unsigned used = 0u;
@@ -412,49 +422,62 @@ k_mx_leaf_lines(const LeafDesc *__restrict__ leaves, const double *__restrict__ 
             const int p = (int)__reduce_min_sync(FULL, key == kmax ? (unsigned)lane : 0xffffffffu);
             used |= 1u << p;
             const float2 pv = M[(size_t)p * WM + t];
-            const float2 ipv = df_rcp(pv);
             if (tid == 0) {
                 prow[t] = p;
                 pvs[t] = pv;
                 const float ap = fabsf(pv.x);
                 if (!(ap > 0.f) || !(ap == ap)) bad = true;
                 pmin = fminf(pmin, ap);
-                if (ap < 0x1p-12f * dmax) grow = true;
+                if (ap < 0x1p-12f * fabsf(wint[(t + ia * jj) * 5 + DIR_C].x)) grow = true;
             }
             // every other row: row -= (row[t] / pivot) * pivot row, over the columns in play
-            const int nT = ia - 1 - t, ncol = nT + L + ncn;
-            for (int e = tid; e < (ia - 1) * ncol; e += LINE_THREADS) {
-                int row = e / ncol;
-                row += row >= p;
-                const int q = e % ncol;
-                const int c = q < nT ? t + 1 + q : (q < nT + L ? ia + tl[q - nT] : ia + r + (q - nT - L));
-                const float2 g = df_mul(M[(size_t)row * WM + t], ipv);
-                M[(size_t)row * WM + c] = df_sub(M[(size_t)row * WM + c], df_mul(g, M[(size_t)p * WM + c]));
+            if (grow_ < ia && grow_ != p) {
+                const float2 g = df_mul(M[(size_t)grow_ * WM + t], df_rcp(pv));
+                float2 *Mr = M + (size_t)grow_ * WM;
+                const float2 *Mp = M + (size_t)p * WM;
+                const int nT = ia - 1 - t;
+                for (int q = gcol; q < nT + nfix; q += gstride) {
+                    const int c = q < nT ? t + 1 + q : (q < nT + L ? ia + tl[q - nT] : ia + r + (q - nT - L));
+                    Mr[c] = df_sub(Mr[c], df_mul(g, Mp[c]));
+                }
             }
             __syncthreads();
         }
         // scale the solution rows: [P | Q] row t = row p_t / pivot t
-        for (int e = tid; e < ia * (L + ncn); e += LINE_THREADS) {
-            const int t = e / (L + ncn), q = e % (L + ncn);
+        for (int e = tid; e < ia * nfix; e += LINE_THREADS) {
+            const int t = e / nfix, q = e % nfix;
             const int c = q < L ? ia + tl[q] : ia + r + (q - L);
             float2 &x = M[(size_t)prow[t] * WM + c];
             x = df_mul(x, df_rcp(pvs[t]));
         }
         __syncthreads();
-        // Sig -= C P over the ring nodes in play
-        for (int e = tid; e < L * L; e += LINE_THREADS) {
-            const int l = tl[e % L], m = tl[e / L];
-            float2 acc = make_float2(0.f, 0.f);
-            for (int t = 0; t < ia; ++t)
-                acc = df_add(acc, df_mul(C[(size_t)l * ia + t], M[(size_t)prow[t] * WM + ia + m]));
-            Sig[l + (size_t)r * m] = df_sub(Sig[l + (size_t)r * m], acc);
+        // Sig -= C P over the ring nodes in play, 2 x 2 entries per thread
+        const int L2h = (L + 1) >> 1;
+        for (int e = tid; e < L2h * L2h; e += LINE_THREADS) {
+            const int i0 = 2 * (e % L2h), j0 = 2 * (e / L2h);
+            const int l0 = tl[i0], l1 = i0 + 1 < L ? tl[i0 + 1] : l0;
+            const int m0 = tl[j0], m1 = j0 + 1 < L ? tl[j0 + 1] : m0;
+            float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
+            for (int t = 0; t < ia; ++t) {
+                const float2 c0 = C[(size_t)l0 * ia + t], c1 = C[(size_t)l1 * ia + t];
+                const float2 *Pt = M + (size_t)prow[t] * WM + ia;
+                const float2 p0 = Pt[m0], p1 = Pt[m1];
+                a00 = df_add_quick(a00, df_mul(c0, p0));
+                a01 = df_add_quick(a01, df_mul(c0, p1));
+                a10 = df_add_quick(a10, df_mul(c1, p0));
+                a11 = df_add_quick(a11, df_mul(c1, p1));
+            }
+            Sig[l0 + (size_t)r * m0] = df_sub(Sig[l0 + (size_t)r * m0], a00);
+            if (j0 + 1 < L) Sig[l0 + (size_t)r * m1] = df_sub(Sig[l0 + (size_t)r * m1], a01);
+            if (i0 + 1 < L) Sig[l1 + (size_t)r * m0] = df_sub(Sig[l1 + (size_t)r * m0], a10);
+            if (i0 + 1 < L && j0 + 1 < L) Sig[l1 + (size_t)r * m1] = df_sub(Sig[l1 + (size_t)r * m1], a11);
         }
         if (more) {
-            const int L2 = in_play(jj + 1);
+            const int j1 = jj + 1, Ln = in_play(j1);
             // next line's T = D - S Q and its C' = direct - S P, N
             for (int e = tid; e < ia * WM; e += LINE_THREADS) {
                 const int k = e / WM, c = e % WM;
-                const int q1 = k + ia * (jj + 1);  // interior index of row k of the next line
+                const int q1 = k + ia * j1;  // interior index of row k of the next line
                 float2 v = make_float2(0.f, 0.f);
                 if (c < ia) {
                     if (c == k) v = wint[q1 * 5 + DIR_C];
@@ -462,23 +485,22 @@ k_mx_leaf_lines(const LeafDesc *__restrict__ leaves, const double *__restrict__ 
                     else if (c == k - 1) v = wint[q1 * 5 + DIR_W];
                     v = df_sub(v, df_mul(wint[q1 * 5 + DIR_S], M[(size_t)prow[k] * WM + ia + r + c]));
                 } else if (c < ia + r) {
-                    const int l = c - ia;
-                    if (inner[l] == q1) v = wbak[l];
-                    else if (inner[l] >= 0 && inner[l] / ia <= jj)
-                        v = df_neg(df_mul(wint[q1 * 5 + DIR_S], M[(size_t)prow[k] * WM + c]));
-                } else if (c - ia - r == k && jj + 2 < ib) {
+                    const int l = c - ia, li = iln[l];
+                    if (li == j1 && iix[l] == k) v = wbak[l];
+                    else if (li >= 0 && li <= jj) v = df_neg(df_mul(wint[q1 * 5 + DIR_S], M[(size_t)prow[k] * WM + c]));
+                } else if (c - ia - r == k && j1 + 1 < ib) {
                     v = wint[q1 * 5 + DIR_N];
                 }
                 Mn[e] = v;
             }
             // next C = direct - C Q
-            for (int e = tid; e < L2 * ia; e += LINE_THREADS) {
+            for (int e = tid; e < Ln * ia; e += LINE_THREADS) {
                 const int l = tl[e / ia], k = e % ia;
-                float2 v = inner[l] == k + ia * (jj + 1) ? wdir[l] : make_float2(0.f, 0.f);
-                if (inner[l] / ia <= jj) {
+                float2 v = (iln[l] == j1 && iix[l] == k) ? wdir[l] : make_float2(0.f, 0.f);
+                if (iln[l] <= jj) {
                     float2 acc = make_float2(0.f, 0.f);
                     for (int t = 0; t < ia; ++t)
-                        acc = df_add(acc, df_mul(C[(size_t)l * ia + t], M[(size_t)prow[t] * WM + ia + r + k]));
+                        acc = df_add_quick(acc, df_mul(C[(size_t)l * ia + t], M[(size_t)prow[t] * WM + ia + r + k]));
                     v = df_sub(v, acc);
                 }
                 Cn[(size_t)l * ia + k] = v;
