@@ -264,10 +264,11 @@ __device__ __forceinline__ void cp_async_digits64(const __nv_bfloat16 *__restric
 constexpr int W_NT = 2;
 constexpr int TILE_THREADS = 32 * 2 * (64 / (8 * W_NT));  // 256
 
-// Column exponents of a 64 x 64 df32 shared tile D[t][jj] (every thread takes part: P
+// Column exponents of a 64 x TW df32 shared tile D[t][jj] (every thread takes part: P
 // consecutive lanes per column).
+template <int TW = 64>
 __device__ __forceinline__ void col_exps64(const float2 *D, int *ex) {
-    constexpr int P = TILE_THREADS / 64;
+    constexpr int P = TILE_THREADS / TW;
     const int jj = threadIdx.x / P, part = threadIdx.x % P;
     float mx = 0.f;
     for (int t = part; t < NBK; t += P) mx = fmaxf(mx, fabsf(D[t * LDF + jj].x));
@@ -276,15 +277,16 @@ __device__ __forceinline__ void col_exps64(const float2 *D, int *ex) {
     if (part == 0) ex[jj] = exp_of_max(mx * 1.0000001f);
 }
 
-// P = A D for a 64 x 64 x 64 product: A by rows from a full-K shared digit tile Ak
-// ([S][64][KP64], exponents aex), D a df32 shared tile cut by columns into Bk (same
-// layout, exponents exB) before the k-steps, which then run without barriers.
-template <int S>
+// P = A D for a 64 x TW x 64 product (TW = 32 NT): A by rows from a full-K shared digit
+// tile Ak ([S][64][KP64], exponents aex), D a df32 shared tile cut by columns into Bk
+// (same layout, exponents exB) before the k-steps, which then run without barriers.
+template <int S, int NT>
 __device__ __forceinline__ void gemm64_full(const __nv_bfloat16 *Ak, const int *__restrict__ aex, const float2 *D,
-                                            const int *exB, __nv_bfloat16 *Bk, float2 res[2][W_NT][4], int kend) {
-    const int tid = threadIdx.x, warp = tid >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 8 * W_NT;
+                                            const int *exB, __nv_bfloat16 *Bk, float2 res[2][NT][4], int kend) {
+    constexpr int TW = 32 * NT;
+    const int tid = threadIdx.x, warp = tid >> 5, wm = (warp & 1) * 32, wn = (warp >> 1) * 8 * NT;
     __syncthreads();  // exB written, the previous product done with Bk
-    for (int e = tid; e < 64 * 64; e += TILE_THREADS) {
+    for (int e = tid; e < TW * 64; e += TILE_THREADS) {
         const int jj = e >> 6, t = e & 63;
         float d[S];
         digits<S>(D[t * LDF + jj], exB[jj], d);
@@ -292,35 +294,36 @@ __device__ __forceinline__ void gemm64_full(const __nv_bfloat16 *Ak, const int *
         for (int q = 0; q < S; ++q) Bk[((size_t)q * 64 + jj) * KP64 + t] = __float2bfloat16_rn(d[q]);
     }
     __syncthreads();
-    float acc[S][2][W_NT][4];
+    float acc[S][2][NT][4];
 #pragma unroll
     for (int g = 0; g < S; ++g)
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < W_NT; ++nt)
+            for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[g][mt][nt][c] = 0.f;
 #pragma unroll 1
-    for (int kk = 0; kk < kend; kk += 16) warp_mma_levels<S, KP64, W_NT>(Ak + kk, Bk + kk, 64, 64, wm, wn, acc);
+    for (int kk = 0; kk < kend; kk += 16) warp_mma_levels<S, KP64, NT>(Ak + kk, Bk + kk, 64, 64, wm, wn, acc);
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int nt = 0; nt < W_NT; ++nt)
+        for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 int r, cl;
                 acc_pos(mt, nt, c, r, cl);
-                res[mt][nt][c] = combine_levels<S, W_NT>(acc, mt, nt, c, aex[wm + r] + exB[wn + cl] - 12);
+                res[mt][nt][c] = combine_levels<S, NT>(acc, mt, nt, c, aex[wm + r] + exB[wn + cl] - 12);
             }
 }
 
-// Blocks [0, cb): 64 columns right of the pivot block each:
+// Blocks [0, cb): TW = 32 NT columns right of the pivot block each (NT = 1 when the grid
+// is small, so twice as many SMs share the step):
 //   R0 = X0 A12,  E = A12 - A11 R0,  R = R0 + X0 E  (one refinement step),
 // R written into the pivot rows and cut into column digit planes for the update.
 // Blocks [cb, cb + rb): 128 rows each: F = W(i, J) (zero inside J) into row digit planes,
 // with the growth check against the block pivots.
-template <int S>
+template <int S, int NT>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, int cb,
              const __nv_bfloat16 *__restrict__ x_dig, const __nv_bfloat16 *__restrict__ a11_dig, int64_t plane,
@@ -374,7 +377,8 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
         }
         return;
     }
-    const int j0 = k + nbe + blockIdx.x * 64;
+    constexpr int TW = 32 * NT;
+    const int j0 = k + nbe + blockIdx.x * TW;
     if (j0 >= Sy.ncol) return;
     constexpr int SX = S < 4 ? S : 4;
     __nv_bfloat16 *Xk = (__nv_bfloat16 *)smem_raw;  // [SX][64][KP64]: rows of X0
@@ -383,26 +387,36 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
     float2 *Ad = (float2 *)(Bk + S * 64 * KP64);   // [64][LDF]: A12, then E
     float2 *Rd = Ad + 64 * LDF;                     // [64][LDF]: R0, then R
     __shared__ int exB[64];
-    const int wm = (warp & 1) * 32, wn = (warp >> 1) * 8 * W_NT;
+    const int wm = (warp & 1) * 32, wn = (warp >> 1) * 8 * NT;
     const __nv_bfloat16 *xd = x_dig + (int64_t)blockIdx.y * 64 * NBK, *ad = a11_dig + (int64_t)blockIdx.y * 64 * NBK;
     const int *xe = x_ex + blockIdx.y * 64, *ae = a11_ex + blockIdx.y * 64;
     // both left operands (all 64 k) in flight while A12 is read
     cp_async_digits64<SX>(xd, plane, 0, 64, Xk);
     cp_async_digits64<S>(ad, plane, 0, 64, A11k);
-    for (int e = tid; e < 64 * 64; e += TILE_THREADS) {
-        const int t = e & 63, jj = e >> 6, j = j0 + jj;
-        Ad[t * LDF + jj] = (t < nbe && j < Sy.ncol) ? W[(size_t)j * m + k + t] : make_float2(0.f, 0.f);
+    {  // A12 (all loads in flight at once)
+        constexpr int NL = TW * 64 / TILE_THREADS;
+        float2 v[NL];
+#pragma unroll
+        for (int q = 0; q < NL; ++q) {
+            const int e = tid + q * TILE_THREADS, t = e & 63, j = j0 + (e >> 6);
+            v[q] = (t < nbe && j < Sy.ncol) ? W[(size_t)j * m + k + t] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < NL; ++q) {
+            const int e = tid + q * TILE_THREADS;
+            Ad[(e & 63) * LDF + (e >> 6)] = v[q];
+        }
     }
     asm volatile("cp.async.wait_all;\n" ::);
     __syncthreads();
-    col_exps64(Ad, exB);
+    col_exps64<TW>(Ad, exB);
     __shared__ int cmax[64], rmax[64];  // column maxima of |X0 E| and |R| (float bits, >= 0)
     if (tid < 64) cmax[tid] = rmax[tid] = 0;
     // three dependent products through one (rolled) copy of the split-product body:
     //   pass 0: R0 = X0 A12 -> Rd;  pass 1: E = A12 - A11 R0 -> Ad;  pass 2: R = R0 + X0 E
 #pragma unroll 1
     for (int pass = 0; pass < 3; ++pass) {
-        float2 res[2][W_NT][4];
+        float2 res[2][NT][4];
         // K = nbe: the operands are zero beyond the block's live columns.  Passes 0 and 2
         // multiply by the FP32 inverse X0, which four 7-bit digits carry to 2^-28 of each
         // row's maximum -- beyond X0's own accuracy; R0 only has to be good to about FP32
@@ -410,13 +424,13 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
         // four digits of the right operand suffice there.  E itself (pass 1) is a
         // difference of nearly equal terms: full digits.
         if (pass == 1)
-            gemm64_full<S>(A11k, ae, Rd, exB, Bk, res, (nbe + 15) & ~15);
+            gemm64_full<S, NT>(A11k, ae, Rd, exB, Bk, res, (nbe + 15) & ~15);
         else
-            gemm64_full<SX>(Xk, xe, Ad, exB, Bk, res, (nbe + 15) & ~15);
+            gemm64_full<SX, NT>(Xk, xe, Ad, exB, Bk, res, (nbe + 15) & ~15);
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < W_NT; ++nt)
+            for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     int r, cl;
@@ -439,23 +453,23 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
                 }
         if (pass < 2) {
             __syncthreads();
-            col_exps64(pass == 0 ? Rd : Ad, exB);  // column scales of the next product's right operand
+            col_exps64<TW>(pass == 0 ? Rd : Ad, exB);  // column scales of the next product's right operand
         }
     }
     __syncthreads();
     // The refinement step leaves an error of about rho^2 |R|, where rho = |X0 E| / |R| is
     // its contraction factor (kappa(A11) times the FP32 accuracy of X0); the largest rho
     // of the build is reported, and the host decides whether the build is accurate enough.
-    if (tid < 64 && j0 + tid < Sy.ncol) {
+    if (tid < TW && j0 + tid < Sy.ncol) {
         const float cm = __int_as_float(cmax[tid]), rm = __int_as_float(rmax[tid]);
         if (cm > 0.f) {
             const float rho = rm > 0.f ? cm / rm : __int_as_float(0x7f800000);
             atomicMax(&st[Sy.prob].rho, __float_as_uint(rho));
         }
     }
-    col_exps64(Rd, exB);
+    col_exps64<TW>(Rd, exB);
     __syncthreads();
-    for (int e = tid; e < 64 * 64; e += TILE_THREADS) {  // column digit planes of R
+    for (int e = tid; e < TW * 64; e += TILE_THREADS) {  // column digit planes of R
         const int jj = e >> 6, t = e & 63, j = j0 + jj;
         if (j >= Sy.ncol) continue;
         const int64_t row = Sy.coff + j;
@@ -593,7 +607,10 @@ static cudaError_t set_blk_attrs(int split) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_blk_update<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk_update_smem(split));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_blk_rfused<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_blk_rfused<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)blk_rgemm_smem(split));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_blk_rfused<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)blk_rgemm_smem(split));
 }
 
@@ -633,10 +650,19 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
         // R writes digit set `par`, which the rest of the update two steps back read: that
         // finished before the previous step's next-block update (below) started
         kt.begin(GM_K_PIVROWS, fl_r, c);
-        BLK_SPLIT_DISPATCH(split, (k_blk_rfused<SS><<<dim3(cb + rb, nsys), TILE_THREADS, rsm, c>>>(
-                                      d_sys, ws, k, cb, scr.x_dig, scr.a11_dig, scr.inv_plane, scr.x_ex, scr.a11_ex,
-                                      scr.fdig[par], scr.fplane, scr.fex[par], scr.rdig[par], scr.cplane,
-                                      scr.rex[par], scr.pmag, st)));
+        // 32-column R tiles while the step would leave most SMs idle
+        if (nsys * cb <= 96) {
+            const int cb32 = (cols + 31) / 32;
+            BLK_SPLIT_DISPATCH(split, (k_blk_rfused<SS, 1><<<dim3(cb32 + rb, nsys), TILE_THREADS, rsm, c>>>(
+                                          d_sys, ws, k, cb32, scr.x_dig, scr.a11_dig, scr.inv_plane, scr.x_ex,
+                                          scr.a11_ex, scr.fdig[par], scr.fplane, scr.fex[par], scr.rdig[par],
+                                          scr.cplane, scr.rex[par], scr.pmag, st)));
+        } else {
+            BLK_SPLIT_DISPATCH(split, (k_blk_rfused<SS, 2><<<dim3(cb + rb, nsys), TILE_THREADS, rsm, c>>>(
+                                          d_sys, ws, k, cb, scr.x_dig, scr.a11_dig, scr.inv_plane, scr.x_ex,
+                                          scr.a11_ex, scr.fdig[par], scr.fplane, scr.fex[par], scr.rdig[par],
+                                          scr.cplane, scr.rex[par], scr.pmag, st)));
+        }
         kt.end(c);
         const dim3 gu(nrt, cb, nsys);
         if (la && cb >= 2 && (e = cudaEventRecord(scr.ev_r, c)) != cudaSuccess) return e;
