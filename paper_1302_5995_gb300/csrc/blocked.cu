@@ -588,6 +588,170 @@ k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
             }
 }
 
+// ----------------------------------------------------------------------------- update, tcgen05
+
+// The same update W(i, j) -= (F R)(i, j) on the fifth-generation tensor cores: a CTA takes
+// 128 rows x 64 columns; the digit tiles of F and R (all 64 k) arrive by cp.async in the
+// K-major, unswizzled core-matrix layout (8 rows x 16 bytes per core matrix, cores 128
+// bytes apart along k and 1024 bytes apart along the rows), one thread issues the
+// 21 digit-pair products of each 16-k step as tcgen05.mma (M = 128, N = 64, K = 16,
+// bf16 x bf16 -> fp32) into six level accumulators in tensor memory (64 columns each),
+// and eight warps read them back (tcgen05.ld) for the same exact level combination and
+// double-float subtraction as the mma.sync kernel.  Modes: UPD_ALL, or UPD_REST (the
+// look-ahead's rest: column tiles 1 .., the next pivot band's rows left out).
+constexpr int TC_ROWS = 128, TC_COLS = 64, TC_TMEM_COLS = 512;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major, no swizzle, version 1 (start, LBO and SBO in
+// 16-byte units).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B (both K-major).
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+size_t blk_update_tc_smem(int split) {
+    return (size_t)split * (TC_ROWS + TC_COLS) * NBK * sizeof(__nv_bfloat16) + 1024;  // + alignment slack
+}
+
+// rows r0 .. r0 + R - 1 (zero beyond nrows) of every digit plane (64 k) into the core-matrix
+// layout: plane q at q * R * 128 bytes, 16-byte chunk (row, c) at (row / 8) 1024 + c 128 + (row % 8) 16
+template <int S, int R>
+__device__ __forceinline__ void cp_async_digits_umma(const __nv_bfloat16 *__restrict__ dig, int64_t plane, int r0,
+                                                     int nrows, unsigned char *sm) {
+    for (int e = threadIdx.x; e < S * R * 8; e += TILE_THREADS) {
+        const int c = e & 7, row = (e >> 3) % R, q = e / (8 * R);
+        const bool ok = row < nrows;
+        const __nv_bfloat16 *src = dig + (int64_t)q * plane + (int64_t)(r0 + (ok ? row : 0)) * NBK + c * 8;
+        const uint32_t dst = smem_u32(sm + (size_t)q * R * 128 + (row >> 3) * 1024 + c * 128 + (row & 7) * 16);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0));
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_blk_update_tc(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, int mode,
+                const __nv_bfloat16 *__restrict__ fdig, int64_t fplane, const int *__restrict__ fex,
+                const __nv_bfloat16 *__restrict__ rdig, int64_t rplane, const int *__restrict__ rex,
+                Status *__restrict__ st) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *Fs = base;                                  // S x 16 KB
+    unsigned char *Rs = base + (size_t)S * TC_ROWS * 128;      // S x 8 KB
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fe[TC_ROWS], s_re[TC_COLS];
+    __shared__ int s_ok;
+    const SysDesc Sy = sys[blockIdx.z];
+    const int m = Sy.m;
+    if (k >= m) return;
+    const int nbe = min(NBK, m - k);
+    const int i0 = blockIdx.x * TC_ROWS, j0 = k + nbe + (blockIdx.y + (mode == UPD_REST ? 1 : 0)) * TC_COLS;
+    if (i0 >= m || j0 >= Sy.ncol) return;
+    // rows this tile leaves alone: the pivot rows, and in UPD_REST the next pivot band
+    const int skip_lo = k, skip_hi = mode == UPD_REST ? min(m, k + 2 * NBK) : k + nbe;
+    if (i0 >= skip_lo && i0 + TC_ROWS <= skip_hi) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float2 *W = ws + Sy.off;
+    cp_async_digits_umma<S, TC_ROWS>(fdig + (int64_t)Sy.roff * NBK, fplane, i0, min(TC_ROWS, m - i0), Fs);
+    cp_async_digits_umma<S, TC_COLS>(rdig + (int64_t)Sy.coff * NBK, rplane, j0, min(TC_COLS, Sy.ncol - j0), Rs);
+    asm volatile("cp.async.commit_group;\n" ::);
+    if (tid < TC_ROWS) {
+        const int i = i0 + tid;
+        s_fe[tid] = i < m ? fex[Sy.roff + i] : 0;
+    } else if (tid < TC_ROWS + TC_COLS) {
+        const int j = j0 + tid - TC_ROWS;
+        s_re[tid - TC_ROWS] = j < Sy.ncol ? rex[Sy.coff + j] : 0;
+    }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar)));
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                     "r"(TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    asm volatile("cp.async.wait_all;\n" ::);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::);  // the copies, visible to the tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    const uint32_t tmem = s_tmem;
+    if (tid == 0) {
+        constexpr uint32_t idesc = umma_idesc_bf16(TC_ROWS, TC_COLS);
+        const int nk = (nbe + 15) >> 4;
+        for (int kc = 0; kc < nk; ++kc)
+#pragma unroll
+            for (int a = 0; a < S; ++a)
+#pragma unroll
+                for (int b = 0; b < S - a; ++b) {
+                    const uint64_t da = umma_desc(smem_u32(Fs + (size_t)a * TC_ROWS * 128 + kc * 256), 128, 1024);
+                    const uint64_t db = umma_desc(smem_u32(Rs + (size_t)b * TC_COLS * 128 + kc * 256), 128, 1024);
+                    const uint32_t dt = tmem + (uint32_t)((a + b) * TC_COLS);
+                    const uint32_t acc = (kc > 0 || a > 0) ? 1u : 0u;  // level a + b starts at (0, a + b)
+                    asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                 ::"r"(dt), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            smem_u32(&mbar)));
+    }
+    // this thread's row and 32 columns; their W values are read while the products run
+    const int q = warp & 3, h = warp >> 2;
+    const int row = 32 * q + lane, i = i0 + row;
+    const bool live = i < m && !(i >= skip_lo && i < skip_hi);
+    float2 w[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        const int j = j0 + 32 * h + c;
+        w[c] = (live && j < Sy.ncol) ? W[(size_t)j * m + i] : make_float2(0.f, 0.f);
+    }
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 20) && !done; ++it)
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(smem_u32(&mbar)), "r"(0));
+    if (tid == 0) s_ok = 1;
+    __syncthreads();
+    if (!done) {
+        s_ok = 0;
+        if (lane == 0 && atomicCAS(&st[Sy.prob].code, 0, GM_ETIMEOUT) == 0) st[Sy.prob].where = -1;
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    if (s_ok) {
+        const int fe = s_fe[row];
+#pragma unroll
+        for (int c0 = 0; c0 < 32; c0 += 8) {
+            uint32_t v[S][8];
+#pragma unroll
+            for (int g = 0; g < S; ++g) {
+                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(g * TC_COLS + 32 * h + c0);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                             : "=r"(v[g][0]), "=r"(v[g][1]), "=r"(v[g][2]), "=r"(v[g][3]), "=r"(v[g][4]),
+                               "=r"(v[g][5]), "=r"(v[g][6]), "=r"(v[g][7])
+                             : "r"(ta));
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int jj = 32 * h + c0 + c, j = j0 + jj;
+                if (!live || j >= Sy.ncol) continue;
+                float2 x = make_float2(__uint_as_float(v[S - 1][c]) * pow2f(-7 * (S - 1)), 0.f);
+#pragma unroll
+                for (int g = S - 2; g >= 0; --g) x = df_add_f(x, __uint_as_float(v[g][c]) * pow2f(-7 * g));
+                W[(size_t)j * m + i] = df_sub(w[c0 + c], df_scale(x, fe + s_re[jj] - 12));
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS));
+}
+
 // ----------------------------------------------------------------------------- launcher
 
 #define BLK_SPLIT_DISPATCH(split, CALL) \
@@ -607,6 +771,9 @@ static cudaError_t set_blk_attrs(int split) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_blk_update<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk_update_smem(split));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_blk_update_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)blk_update_tc_smem(split));
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_blk_rfused<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)blk_rgemm_smem(split));
     if (e != cudaSuccess) return e;
@@ -620,7 +787,9 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
     cudaError_t e = cudaSuccess;
     BLK_SPLIT_DISPATCH(split, (e = set_blk_attrs<SS>(split)));
     if (e != cudaSuccess) return e;
-    const size_t fsm = blk_factor_smem(split), rsm = blk_rgemm_smem(split), usm = blk_update_smem(split);
+    const size_t fsm = blk_factor_smem(split), rsm = blk_rgemm_smem(split), usm = blk_update_smem(split),
+                 tsm = blk_update_tc_smem(split);
+    const int nrt128 = (max_m + TC_ROWS - 1) / TC_ROWS;
     const bool la = scr.s1 && scr.s2;
     // the chain runs on s1, joined to the caller's stream on entry and exit
     cudaStream_t c = la ? scr.s1 : s;
@@ -673,9 +842,9 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
         }
         if (!la || cb < 2) {
             kt.begin(GM_K_GJUPDATE, fl_upd, c);
-            BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<gu, TILE_THREADS, usm, c>>>(d_sys, ws, k, UPD_ALL, nrt, scr.fdig[par],
-                                                                           scr.fplane, scr.fex[par], scr.rdig[par],
-                                                                           scr.cplane, scr.rex[par])));
+            BLK_SPLIT_DISPATCH(split, (k_blk_update_tc<SS><<<dim3(nrt128, cb, nsys), TILE_THREADS, tsm, c>>>(
+                                          d_sys, ws, k, UPD_ALL, scr.fdig[par], scr.fplane, scr.fex[par],
+                                          scr.rdig[par], scr.cplane, scr.rex[par], st)));
             kt.end(c);
             continue;
         }
@@ -689,9 +858,9 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
         kt.end(c);
         if ((e = cudaStreamWaitEvent(scr.s2, scr.ev_r, 0)) != cudaSuccess) return e;
         kt.begin(GM_K_GJUPDATE, fl_upd - fl_next, scr.s2);
-        BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(nrt, cb - 1, nsys), TILE_THREADS, usm, scr.s2>>>(
-                                      d_sys, ws, k, UPD_REST, nrt, scr.fdig[par], scr.fplane, scr.fex[par],
-                                      scr.rdig[par], scr.cplane, scr.rex[par])));
+        BLK_SPLIT_DISPATCH(split, (k_blk_update_tc<SS><<<dim3(nrt128, cb - 1, nsys), TILE_THREADS, tsm, scr.s2>>>(
+                                      d_sys, ws, k, UPD_REST, scr.fdig[par], scr.fplane, scr.fex[par],
+                                      scr.rdig[par], scr.cplane, scr.rex[par], st)));
         kt.end(scr.s2);
         if ((e = cudaEventRecord(scr.ev_rest, scr.s2)) != cudaSuccess) return e;
         pending = true;

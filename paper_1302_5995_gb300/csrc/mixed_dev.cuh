@@ -57,7 +57,14 @@ __device__ __forceinline__ float2 df_from_d(double x) {
     return make_float2(hi, lo);
 }
 __device__ __forceinline__ double df_to_d(float2 a) { return (double)a.x + (double)a.y; }
-__device__ __forceinline__ float2 df_scale(float2 a, int p) { return make_float2(ldexpf(a.x, p), ldexpf(a.y, p)); }
+// 2^p as a float for -126 <= p <= 127 (built from its exponent bits), and x 2^p for
+// -252 <= p <= 254 by two such factors: exact while the result stays a normal float
+// (the only case here), at two multiplications instead of a library scaling call
+__device__ __forceinline__ float pow2f(int p) { return __int_as_float((p + 127) << 23); }
+__device__ __forceinline__ float2 df_scale(float2 a, int p) {
+    const float f1 = pow2f(p >> 1), f2 = pow2f(p - (p >> 1));
+    return make_float2(a.x * f1 * f2, a.y * f1 * f2);
+}
 
 // ----------------------------------------------------------------------------- digits
 
@@ -71,7 +78,8 @@ __device__ __forceinline__ int exp_of_max(float m) {
 // S signed digits of x 2^(6-e): d_0 + 2^-7 d_1 + ..., |d_s| <= 64.
 template <int S>
 __device__ __forceinline__ void digits(float2 x, int e, float d[S]) {
-    float th = ldexpf(x.x, 6 - e), tl = ldexpf(x.y, 6 - e);
+    const float2 t = df_scale(x, 6 - e);
+    float th = t.x, tl = t.y;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         float q = rintf(th);
@@ -134,9 +142,9 @@ __device__ __forceinline__ void warp_mma_levels(const __nv_bfloat16 *As, const _
 // df32 value of one output position from its S exact level sums and the scale.
 template <int S, int NT = 4>
 __device__ __forceinline__ float2 combine_levels(const float acc[S][2][NT][4], int mt, int nt, int c, int p) {
-    float2 v = make_float2(ldexpf(acc[S - 1][mt][nt][c], -7 * (S - 1)), 0.f);
+    float2 v = make_float2(acc[S - 1][mt][nt][c] * pow2f(-7 * (S - 1)), 0.f);
 #pragma unroll
-    for (int g = S - 2; g >= 0; --g) v = df_add_f(v, ldexpf(acc[g][mt][nt][c], -7 * g));
+    for (int g = S - 2; g >= 0; --g) v = df_add_f(v, acc[g][mt][nt][c] * pow2f(-7 * g));
     return df_scale(v, p);
 }
 
