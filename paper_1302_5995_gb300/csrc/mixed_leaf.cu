@@ -283,8 +283,8 @@ constexpr int LINE_THREADS = 256;
 size_t mx_leaf_lines_smem_bytes(int a, int b) {
     const int ia = a - 2, ib = b - 2, r = 2 * a + 2 * b - 4;
     const int ni = (ia > 0 && ib > 0) ? ia * ib : 0;
-    const int WM = 2 * ia + r;
-    return 8 * ((size_t)r * r + 2 * (size_t)ia * WM + 2 * (size_t)r * ia + (size_t)ni * 5 + 2 * (size_t)r +
+    const int WM = (2 * ia + r) | 1, CS = ia | 1;
+    return 8 * ((size_t)r * r + 2 * (size_t)ia * WM + 2 * (size_t)r * CS + (size_t)ni * 5 + 2 * (size_t)r +
                 (size_t)ia) +
            4 * (3 * (size_t)r + 2 * (size_t)ia) + 16;
 }
@@ -304,14 +304,16 @@ k_mx_leaf_lines(const LeafDesc *__restrict__ leaves, const double *__restrict__ 
     const int n = Ld.n;
     const double *bf = bf0 + Ld.coef, *cf = cf0 + Ld.coef, *df = df0 + Ld.coef;
     const int a = Ld.a, bb = Ld.b, ia = a - 2, ib = bb - 2, r = 2 * a + 2 * bb - 4;
-    const int WM = 2 * ia + r;  // row of M: [T | C' (by ring position) | N]
+    // row strides in float2, odd so that a column read across rows spreads over the banks
+    const int WM = (2 * ia + r) | 1;  // row of M: [T | C' (by ring position) | N | pad]
+    const int CS = ia | 1;            // row of C
     const double ih = n + 1.0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
     float2 *Sig = (float2 *)smem_raw;            // r x r, column-major
     float2 *Mb = Sig + (size_t)r * r;            // 2 x ia x WM
-    float2 *Cb = Mb + 2 * (size_t)ia * WM;       // 2 x r x ia
-    float2 *wint = Cb + 2 * (size_t)r * ia;      // ni x 5: C, E, W, N, S of each interior equation
+    float2 *Cb = Mb + 2 * (size_t)ia * WM;       // 2 x r x CS
+    float2 *wint = Cb + 2 * (size_t)r * CS;      // ni x 5: C, E, W, N, S of each interior equation
     float2 *wdir = wint + (size_t)ia * ib * 5;   // r: ring node -> its interior neighbour
     float2 *wbak = wdir + r;                     // r: interior neighbour -> ring node
     float2 *pvs = wbak + r;                      // ia: pivots of the current line
@@ -375,7 +377,7 @@ k_mx_leaf_lines(const LeafDesc *__restrict__ leaves, const double *__restrict__ 
             Sig[l + (size_t)r * m] = df_from_d(stencil_w_mx(bf, cf, df, ih, gl, dd[q]));
         }
     }
-    float2 *M = Mb, *Mn = Mb + (size_t)ia * WM, *C = Cb, *Cn = Cb + (size_t)r * ia;
+    float2 *M = Mb, *Mn = Mb + (size_t)ia * WM, *C = Cb, *Cn = Cb + (size_t)r * CS;
     // line 0: M = [D_0 | direct C' | diag N_0], C = direct
     for (int e = tid; e < ia * WM; e += LINE_THREADS) {
         const int k = e / WM, c = e % WM;
@@ -394,7 +396,7 @@ k_mx_leaf_lines(const LeafDesc *__restrict__ leaves, const double *__restrict__ 
     }
     for (int e = tid; e < r * ia; e += LINE_THREADS) {
         const int l = e / ia, k = e % ia;
-        C[e] = (iln[l] == 0 && iix[l] == k) ? wdir[l] : make_float2(0.f, 0.f);
+        C[(size_t)l * CS + k] = (iln[l] == 0 && iix[l] == k) ? wdir[l] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     // thread roles in the Gauss-Jordan steps: lane -> (row, column offset); rows per pass
@@ -459,7 +461,7 @@ k_mx_leaf_lines(const LeafDesc *__restrict__ leaves, const double *__restrict__ 
             const int m0 = tl[j0], m1 = j0 + 1 < L ? tl[j0 + 1] : m0;
             float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
             for (int t = 0; t < ia; ++t) {
-                const float2 c0 = C[(size_t)l0 * ia + t], c1 = C[(size_t)l1 * ia + t];
+                const float2 c0 = C[(size_t)l0 * CS + t], c1 = C[(size_t)l1 * CS + t];
                 const float2 *Pt = M + (size_t)prow[t] * WM + ia;
                 const float2 p0 = Pt[m0], p1 = Pt[m1];
                 a00 = df_add_quick(a00, df_mul(c0, p0));
@@ -500,10 +502,10 @@ k_mx_leaf_lines(const LeafDesc *__restrict__ leaves, const double *__restrict__ 
                 if (iln[l] <= jj) {
                     float2 acc = make_float2(0.f, 0.f);
                     for (int t = 0; t < ia; ++t)
-                        acc = df_add_quick(acc, df_mul(C[(size_t)l * ia + t], M[(size_t)prow[t] * WM + ia + r + k]));
+                        acc = df_add_quick(acc, df_mul(C[(size_t)l * CS + t], M[(size_t)prow[t] * WM + ia + r + k]));
                     v = df_sub(v, acc);
                 }
-                Cn[(size_t)l * ia + k] = v;
+                Cn[(size_t)l * CS + k] = v;
             }
         }
         __syncthreads();
