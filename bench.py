@@ -38,6 +38,7 @@ WORKLOAD = ("convection-diffusion-reaction, b,c,d = 8-mode Fourier fields (seeds
 SMS, SM_MAX_MHZ = 152, 2070.0
 FP64_PEAK_TFLOPS = SMS * 4 * SM_MAX_MHZ * 1e6 / 1e12
 FP32_PEAK_TFLOPS = SMS * 256 * SM_MAX_MHZ * 1e6 / 1e12
+DF32_OPS = 18
 SPLIT_DIGITS = 6
 
 
@@ -50,8 +51,11 @@ def bf16_peak_tflops():
 
 def family_roofline(precision, fam):
     """(bound, peak TFLOP/s, source) of a kernel family in this build."""
-    if precision == "fp64" or fam == "leaf":
+    if precision == "fp64":
         return "alu", FP64_PEAK_TFLOPS, "FP64 pipe from unit counts: 152 SMs x 4 flop/clk x 2070 MHz"
+    if fam == "leaf":  # double-float arithmetic: 18 FP32 operations per multiply-add
+        return "alu", FP32_PEAK_TFLOPS / DF32_OPS, (f"FP32 pipe from unit counts / {DF32_OPS} FP32 operations per "
+                                                   "double-float multiply-add (product 7, sum 11)")
     if fam == "panel":
         return "alu", FP32_PEAK_TFLOPS, "FP32 pipe from unit counts: 152 SMs x 256 flop/clk x 2070 MHz"
     bf, src = bf16_peak_tflops()
