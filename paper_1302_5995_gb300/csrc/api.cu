@@ -525,7 +525,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             CK(sweep(ds.d_sys, ds.h_sys, ds.max_m, ds.max_ncol, ws.p, ds.sum_rows, ds.sum_cols, (int)si + 1));
             CK(mx_merge_update(ds.d_merges, hs.merges, ds.d_tab, Adf, ws.as<float2>(), Adf, ds.max_rp, split,
                                ydig.as<__nv_bfloat16>(), yex.as<int>(), xdig.as<__nv_bfloat16>(), xex.as<int>(),
-                               ds.dig_elems, db, dc, dd, 0, s, kt));
+                               ds.dig_elems, db, dc, dd, 0, dst, s, kt));
         }
     }
 

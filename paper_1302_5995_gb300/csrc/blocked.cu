@@ -601,20 +601,6 @@ k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
 // look-ahead's rest: column tiles 1 .., the next pivot band's rows left out).
 constexpr int TC_ROWS = 128, TC_COLS = 64, TC_TMEM_COLS = 512;
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Shared-memory matrix descriptor: K-major, no swizzle, version 1 (start, LBO and SBO in
-// 16-byte units).
-__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
-}
-
-// Instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B (both K-major).
-__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
 size_t blk_update_tc_smem(int split) {
     return (size_t)split * (TC_ROWS + TC_COLS) * NBK * sizeof(__nv_bfloat16) + 1024;  // + alignment slack
 }

@@ -438,6 +438,216 @@ k_mx_merge_update(const MergeDesc *__restrict__ md, const int *__restrict__ tab,
         });
 }
 
+// ----------------------------------------------------------------------------- merge update, tcgen05
+
+// The same S_parent(q(a), q(c)) = C(a, c) - (Y' X)(a, c) on the fifth-generation tensor
+// cores: a CTA takes 128 rows (a) x 64 columns (c) of the parent; the 16-k digit tiles of
+// Y and X stream through four shared-memory stages (cp.async, K-major core-matrix
+// layout), one thread issues each tile's 21 digit-pair products as tcgen05.mma
+// (M = 128, N = 64, K = 16) into six level accumulators in tensor memory and commits
+// them to the stage's mbarrier, and a stage is refilled only once that commit has
+// landed.  K runs in chunks of at most 2048 (level sums stay below 2^23, exact in fp32);
+// after each chunk eight warps read the levels back (tcgen05.ld) and apply the same
+// epilogue as the mma.sync kernel.  Every wait is bounded (GM_ETIMEOUT, no hang).
+constexpr int MT_ROWS = 128, MT_COLS = 64, MT_STAGES = 4, MT_KTILES = 128;  // 128 x 16 = 2048 k per chunk
+constexpr int MT_TC_MIN_K = 192;  // shorter merges keep the mma.sync kernel
+
+size_t mx_merge_tc_smem(int split) {
+    // at least 120 KB, so one CTA per SM: each CTA allocates all 512 tensor-memory columns
+    const size_t need = (size_t)MT_STAGES * split * (MT_ROWS + MT_COLS) * 16 * sizeof(__nv_bfloat16) + 1024;
+    return need > 120 * 1024 ? need : 120 * 1024;
+}
+
+// Tile layout in a stage: A rows a0 .. a0 + 127 first, then B rows c0 .. c0 + 63; plane q
+// of A at q * 4096, of B at S * 4096 + q * 2048; core matrix (row / 8, k / 8) of a 16-k
+// tile at (row / 8) 256 + (k / 8) 128.  Rows beyond the matrix are zero-filled.
+template <int S>
+__global__ void __launch_bounds__(PIPE_THREADS)
+k_mx_merge_update_tc(const MergeDesc *__restrict__ md, const int *__restrict__ tab, const float2 *__restrict__ in,
+                     float2 *__restrict__ out, const __nv_bfloat16 *__restrict__ ydig, const int *__restrict__ yex,
+                     const __nv_bfloat16 *__restrict__ xdig, const int *__restrict__ xex, int64_t plane,
+                     const double *__restrict__ bf, const double *__restrict__ cf, const double *__restrict__ df,
+                     Status *__restrict__ st) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr int STAGE = S * (MT_ROWS + MT_COLS) * 32;  // bytes per stage
+    __shared__ __align__(8) unsigned long long mbar[MT_STAGES];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_ye[MT_ROWS], s_xe[MT_COLS];
+    __shared__ int s_bad;
+    const MergeDesc M = md[blockIdx.z];
+    const int rp = M.rp;
+    const int a0 = blockIdx.x * MT_ROWS, c0 = blockIdx.y * MT_COLS;
+    if (a0 >= rp || c0 >= rp) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const MergeTabMx T = merge_tab_mx(M, tab);
+    const int n1 = M.n1;
+    const float2 *S1 = in + M.s1, *S2 = in + M.s2;
+    const double ih = M.n + 1.0;
+    const int d12 = M.orient ? DIR_N : DIR_E, d21 = M.orient ? DIR_S : DIR_W;
+    float2 *O = out + M.out;
+    const __nv_bfloat16 *Ad = ydig + M.doff, *Bd = xdig + M.doff;
+    const int kpad = M.kpad, ntile = kpad / 16;
+    const int arows = min(MT_ROWS, rp - a0), crows = min(MT_COLS, rp - c0);
+    if (tid < MT_ROWS) s_ye[tid] = yex[M.eoff + min(a0 + tid, rp - 1)];
+    else if (tid < MT_ROWS + MT_COLS) s_xe[tid - MT_ROWS] = xex[M.eoff + min(c0 + tid - MT_ROWS, rp - 1)];
+    if (tid == 0) {
+        for (int q = 0; q < MT_STAGES; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[q])));
+        s_bad = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    const uint32_t tmem = s_tmem;
+    constexpr uint32_t idesc = umma_idesc_bf16(MT_ROWS, MT_COLS);
+    const int q4 = warp & 3, h = warp >> 2;
+    const int aa = a0 + 32 * q4 + lane;  // this thread's parent row in the epilogue
+    // this thread's share of every tile copy, resolved once: slot j is 16-byte piece
+    // tid + j * PIPE_THREADS of the tile (source at k = 0, offset in the stage, size)
+    constexpr int NPIECE = S * (MT_ROWS + MT_COLS) * 2;
+    constexpr int NSLOT = (NPIECE + PIPE_THREADS - 1) / PIPE_THREADS;
+    const __nv_bfloat16 *psrc[NSLOT];
+    uint32_t pdst[NSLOT], psz[NSLOT];
+#pragma unroll
+    for (int j = 0; j < NSLOT; ++j) {
+        const int e = tid + j * PIPE_THREADS;
+        const int chunk = e & 1, rr = e >> 1;
+        const int q = rr / (MT_ROWS + MT_COLS), row = rr % (MT_ROWS + MT_COLS);
+        const bool isA = row < MT_ROWS;
+        const int r = isA ? row : row - MT_ROWS;
+        const bool ok = e < NPIECE && r < (isA ? arows : crows);
+        psrc[j] = (isA ? Ad : Bd) + (int64_t)min(q, S - 1) * plane + (int64_t)((isA ? a0 : c0) + (ok ? r : 0)) * kpad +
+                  chunk * 8;
+        pdst[j] = e < NPIECE ? (uint32_t)((isA ? q * 4096 : S * 4096 + q * 2048) + (r >> 3) * 256 + chunk * 128 +
+                                          (r & 7) * 16)
+                             : 0xffffffffu;
+        psz[j] = ok ? 16u : 0u;
+    }
+    auto load_tile = [&](int tile, int stage) {  // 16-k tile `tile` (absolute) into a stage
+        const uint32_t sb = smem_u32(base + stage * STAGE);
+#pragma unroll
+        for (int j = 0; j < NSLOT; ++j)
+            if (pdst[j] != 0xffffffffu)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sb + pdst[j]),
+                             "l"(psrc[j] + tile * 16), "r"(psz[j]));
+    };
+    // completion parity of each stage's mbarrier at the start of a chunk (bit s): tile kt
+    // of the chunk is completion (chunk base + kt / MT_STAGES) of stage kt % MT_STAGES
+    unsigned bpar = 0u;
+    bool bad = false;
+    for (int t0 = 0; t0 < ntile && !bad; t0 += MT_KTILES) {
+        const int nk = min(ntile - t0, MT_KTILES);
+        const bool first = t0 == 0;
+#pragma unroll
+        for (int p = 0; p < MT_STAGES - 1; ++p) {
+            if (p < nk) load_tile(t0 + p, p);
+            asm volatile("cp.async.commit_group;\n" ::);
+        }
+        for (int kt = 0; kt < nk; ++kt) {
+            const int sg = kt % MT_STAGES;
+            asm volatile("cp.async.wait_group %0;\n" ::"n"(MT_STAGES - 2));
+            asm volatile("fence.proxy.async.shared::cta;\n" ::);
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            if (tid == 0) {
+                const unsigned char *sa = base + sg * STAGE, *sb = sa + S * 4096;
+#pragma unroll
+                for (int a = 0; a < S; ++a)
+#pragma unroll
+                    for (int b = 0; b < S - a; ++b)
+                        umma_bf16(tmem + (uint32_t)((a + b) * MT_COLS), umma_desc(smem_u32(sa + a * 4096), 128, 256),
+                                  umma_desc(smem_u32(sb + b * 2048), 128, 256), idesc, (kt > 0 || a > 0) ? 1u : 0u);
+                umma_commit(&mbar[sg]);
+            }
+            // refill the stage the previous tile used, once its products have landed
+            const int nx = kt + MT_STAGES - 1;
+            if (nx < nk) {
+                const int sp = nx % MT_STAGES;
+                const uint32_t par = ((bpar >> sp) & 1u) ^ (uint32_t)(((kt - 1) / MT_STAGES) & 1);
+                if (kt >= 1 && !mbar_wait_bounded(&mbar[sp], par, 1 << 20)) bad = true;
+                load_tile(t0 + nx, sp);
+            }
+            asm volatile("cp.async.commit_group;\n" ::);
+        }
+        // the chunk's last products (they complete in order)
+        const int sl = (nk - 1) % MT_STAGES;
+        if (!mbar_wait_bounded(&mbar[sl], ((bpar >> sl) & 1u) ^ (uint32_t)(((nk - 1) / MT_STAGES) & 1), 1 << 20))
+            bad = true;
+#pragma unroll
+        for (int q = 0; q < MT_STAGES; ++q)  // tiles of this chunk on stage q
+            if (q < nk) bpar ^= (uint32_t)(((nk - q + MT_STAGES - 1) / MT_STAGES) & 1) << q;
+        asm volatile("cp.async.wait_group 0;\n" ::);
+        if (bad) s_bad = 1;
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+        if (s_bad) {
+            bad = true;
+            break;
+        }
+        // epilogue: this thread's row aa, columns c0 + 32 h .. + 31, eight at a time
+#pragma unroll 1
+        for (int cc0 = 0; cc0 < 32; cc0 += 8) {
+            uint32_t v[S][8];
+#pragma unroll
+            for (int g = 0; g < S; ++g)
+                tmem_ld8(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(g * MT_COLS + 32 * h + cc0), v[g]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+            if (aa >= rp) continue;
+            const int qa = aa < n1 ? T.q1[aa] : T.q2[aa - n1];
+            float2 cval[8];
+            int64_t off[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {  // the eight parent entries' current values, read together
+                const int cc = c0 + 32 * h + cc0 + c;
+                cval[c] = make_float2(0.f, 0.f);
+                off[c] = -1;
+                if (cc >= rp) continue;
+                const int qc = cc < n1 ? T.q1[cc] : T.q2[cc - n1];
+                off[c] = qa + (int64_t)rp * qc;
+                if (!first) {
+                    cval[c] = O[off[c]];
+                } else if (aa < n1 && cc < n1) {
+                    cval[c] = S1[T.p1[aa] + (int64_t)M.r1 * T.p1[cc]];
+                } else if (aa >= n1 && cc >= n1) {
+                    cval[c] = S2[T.p2[aa - n1] + (int64_t)M.r2 * T.p2[cc - n1]];
+                } else {
+                    for (int e = 0; e < 2; ++e) {
+                        const int *x = T.x12 + 4 * e;
+                        if (aa < n1 && aa == x[0] && cc - n1 == x[1])
+                            cval[c] = df_from_d(stencil_w_mx(bf, cf, df, ih, x[2], d12));
+                        if (aa >= n1 && aa - n1 == x[1] && cc == x[0])
+                            cval[c] = df_from_d(stencil_w_mx(bf, cf, df, ih, x[3], d21));
+                    }
+                }
+            }
+            const int ea = s_ye[32 * q4 + lane];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                if (off[c] < 0) continue;
+                float2 x = make_float2(__uint_as_float(v[S - 1][c]) * pow2f(-7 * (S - 1)), 0.f);
+#pragma unroll
+                for (int g = S - 2; g >= 0; --g) x = df_add_f(x, __uint_as_float(v[g][c]) * pow2f(-7 * g));
+                O[off[c]] = df_sub(cval[c], df_scale(x, ea + s_xe[32 * h + cc0 + c] - 12));
+            }
+        }
+        // the next chunk's products overwrite the accumulators: every read must be done
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    }
+    if (bad && tid == 0 && atomicCAS(&st[M.prob].code, 0, GM_ETIMEOUT) == 0) st[M.prob].where = -1;
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512));
+}
+
 // ----------------------------------------------------------------------------- root
 
 __device__ __forceinline__ void ghost_nb_mx(int n, int k, int &g, int &dir) {
@@ -613,7 +823,8 @@ cudaError_t mx_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys,
 cudaError_t mx_merge_update(const MergeDesc *md, const std::vector<MergeDesc> &h_md, const int *tab,
                             const float2 *in, const float2 *ws, float2 *out, int max_rp, int split,
                             __nv_bfloat16 *ydig, int *yex, __nv_bfloat16 *xdig, int *xex, int64_t plane,
-                            const double *b, const double *c, const double *d, int n, cudaStream_t s, KTimer &kt) {
+                            const double *b, const double *c, const double *d, int n, Status *st, cudaStream_t s,
+                            KTimer &kt) {
     double fl = 0;
     for (const MergeDesc &M : h_md) fl += 2.0 * (double)M.rp * M.rp * M.sp;
     const int nm = (int)h_md.size();
@@ -621,13 +832,29 @@ cudaError_t mx_merge_update(const MergeDesc *md, const std::vector<MergeDesc> &h
     kt.begin(GM_K_MERGEUPDATE, fl, s);
     MX_SPLIT_DISPATCH(split, (k_mx_merge_slice<SS><<<dim3(2 * rb, nm), 128, 0, s>>>(md, tab, in, ws, rb, ydig, yex,
                                                                                       xdig, xex, plane)));
-    dim3 g((max_rp + 63) / 64, (max_rp + 63) / 64, nm);
+    int max_kpad = 0;
+    for (const MergeDesc &M : h_md) max_kpad = std::max(max_kpad, M.kpad);
     cudaError_t e = cudaSuccess;
-    MX_SPLIT_DISPATCH(split, (e = cudaFuncSetAttribute(k_mx_merge_update<SS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)pipe_smem_bytes(SS))));
+    if (max_kpad < MT_TC_MIN_K) {  // short K: the pipeline's fill and drain would dominate
+        const dim3 g64((max_rp + 63) / 64, (max_rp + 63) / 64, nm);
+        MX_SPLIT_DISPATCH(split, (e = cudaFuncSetAttribute(k_mx_merge_update<SS>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           (int)pipe_smem_bytes(SS))));
+        if (e != cudaSuccess) return e;
+        MX_SPLIT_DISPATCH(split, (k_mx_merge_update<SS><<<g64, PIPE_THREADS, pipe_smem_bytes(SS), s>>>(
+                                     md, tab, in, out, ydig, yex, xdig, xex, plane, b, c, d, n)));
+        kt.end(s);
+        return cudaGetLastError();
+    }
+    // tcgen05 tiles of 128 x 64 (tensor memory: 512 columns per CTA, one CTA per SM by
+    // shared memory, so the allocation never waits)
+    dim3 g((max_rp + MT_ROWS - 1) / MT_ROWS, (max_rp + MT_COLS - 1) / MT_COLS, nm);
+    MX_SPLIT_DISPATCH(split, (e = cudaFuncSetAttribute(k_mx_merge_update_tc<SS>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)mx_merge_tc_smem(SS))));
     if (e != cudaSuccess) return e;
-    MX_SPLIT_DISPATCH(split, (k_mx_merge_update<SS><<<g, PIPE_THREADS, pipe_smem_bytes(SS), s>>>(
-                                 md, tab, in, out, ydig, yex, xdig, xex, plane, b, c, d, n)));
+    MX_SPLIT_DISPATCH(split, (k_mx_merge_update_tc<SS><<<g, PIPE_THREADS, mx_merge_tc_smem(SS), s>>>(
+                                 md, tab, in, out, ydig, yex, xdig, xex, plane, b, c, d, st)));
     kt.end(s);
     return cudaGetLastError();
 }

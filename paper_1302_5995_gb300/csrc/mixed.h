@@ -37,7 +37,8 @@ cudaError_t mx_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys,
 cudaError_t mx_merge_update(const MergeDesc *md, const std::vector<MergeDesc> &h_md, const int *tab,
                             const float2 *in, const float2 *ws, float2 *out, int max_rp, int split,
                             __nv_bfloat16 *ydig, int *yex, __nv_bfloat16 *xdig, int *xex, int64_t plane,
-                            const double *b, const double *c, const double *d, int n, cudaStream_t s, KTimer &kt);
+                            const double *b, const double *c, const double *d, int n, Status *st, cudaStream_t s,
+                            KTimer &kt);
 cudaError_t mx_root_assemble(const float2 *S, int r, int n, float2 *ws, const double *b, const double *c,
                              const double *d, cudaStream_t s, KTimer &kt);
 int mx_kpad(int N);
