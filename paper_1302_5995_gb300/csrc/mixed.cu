@@ -355,7 +355,7 @@ template <int S>
 __global__ void __launch_bounds__(128)
 k_mx_merge_slice(const MergeDesc *__restrict__ md, const int *__restrict__ tab, const float2 *__restrict__ in,
                  const float2 *__restrict__ ws, int rb, __nv_bfloat16 *__restrict__ ydig, int *__restrict__ yex,
-                 __nv_bfloat16 *__restrict__ xdig, int *__restrict__ xex, int64_t plane) {
+                 __nv_bfloat16 *__restrict__ xdig, int *__restrict__ xex, int64_t plane, int tiled) {
     const MergeDesc M = md[blockIdx.y];
     const MergeTabMx T = merge_tab_mx(M, tab);
     const int sp = M.sp, mm = 2 * sp, n1 = M.n1, warp = threadIdx.x >> 5;
@@ -369,12 +369,12 @@ k_mx_merge_slice(const MergeDesc *__restrict__ md, const int *__restrict__ tab, 
             if (a < n1) return kk < sp ? S1[T.p1[a] + (int64_t)M.r1 * T.p3[kk]] : make_float2(0.f, 0.f);
             return kk >= sp ? S2[T.p2[a - n1] + (int64_t)M.r2 * T.p4[kk - sp]] : make_float2(0.f, 0.f);
         };
-        warp_slice_row<S>(get, mm, M.kpad, ydig + M.doff, plane, a, yex + M.eoff);
+        warp_slice_row<S>(get, mm, M.kpad, ydig + M.doff, plane, a, yex + M.eoff, tiled != 0);
     } else {
         const float2 *X = ws + M.ws + (size_t)mm * mm;
         const int c = idx;
         auto get = [&](int kk) -> float2 { return X[(size_t)c * mm + kk]; };
-        warp_slice_row<S>(get, mm, M.kpad, xdig + M.doff, plane, c, xex + M.eoff);
+        warp_slice_row<S>(get, mm, M.kpad, xdig + M.doff, plane, c, xex + M.eoff, tiled != 0);
     }
 }
 
@@ -442,11 +442,12 @@ k_mx_merge_update(const MergeDesc *__restrict__ md, const int *__restrict__ tab,
 
 // The same S_parent(q(a), q(c)) = C(a, c) - (Y' X)(a, c) on the fifth-generation tensor
 // cores: a CTA takes 128 rows (a) x 64 columns (c) of the parent; the 16-k digit tiles of
-// Y and X stream through four shared-memory stages (cp.async, K-major core-matrix
-// layout), one thread issues each tile's 21 digit-pair products as tcgen05.mma
+// Y and X stream through four shared-memory stages by bulk copies on the tensor memory
+// accelerator (one 4 KB / 2 KB copy per digit plane, counted on the stage's `full`
+// barrier); one thread issues each tile's 21 digit-pair products as tcgen05.mma
 // (M = 128, N = 64, K = 16) into six level accumulators in tensor memory and commits
-// them to the stage's mbarrier, and a stage is refilled only once that commit has
-// landed.  K runs in chunks of at most 2048 (level sums stay below 2^23, exact in fp32);
+// them to the stage's `empty` barrier, and a stage is refilled only once that commit
+// has landed.  K runs in chunks of at most 2048 (level sums stay below 2^23, exact in fp32);
 // after each chunk eight warps read the levels back (tcgen05.ld) and apply the same
 // epilogue as the mma.sync kernel.  Every wait is bounded (GM_ETIMEOUT, no hang).
 constexpr int MT_ROWS = 128, MT_COLS = 64, MT_STAGES = 4, MT_KTILES = 128;  // 128 x 16 = 2048 k per chunk
@@ -460,7 +461,8 @@ size_t mx_merge_tc_smem(int split) {
 
 // Tile layout in a stage: A rows a0 .. a0 + 127 first, then B rows c0 .. c0 + 63; plane q
 // of A at q * 4096, of B at S * 4096 + q * 2048; core matrix (row / 8, k / 8) of a 16-k
-// tile at (row / 8) 256 + (k / 8) 128.  Rows beyond the matrix are zero-filled.
+// tile at (row / 8) 256 + (k / 8) 128 -- the order the digit planes are stored in (rows
+// padded to 128; padding rows only reach outputs that are never stored).
 template <int S>
 __global__ void __launch_bounds__(PIPE_THREADS)
 k_mx_merge_update_tc(const MergeDesc *__restrict__ md, const int *__restrict__ tab, const float2 *__restrict__ in,
@@ -471,7 +473,7 @@ k_mx_merge_update_tc(const MergeDesc *__restrict__ md, const int *__restrict__ t
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr int STAGE = S * (MT_ROWS + MT_COLS) * 32;  // bytes per stage
-    __shared__ __align__(8) unsigned long long mbar[MT_STAGES];
+    __shared__ __align__(8) unsigned long long full[MT_STAGES], empty[MT_STAGES];
     __shared__ uint32_t s_tmem;
     __shared__ int s_ye[MT_ROWS], s_xe[MT_COLS];
     __shared__ int s_bad;
@@ -486,13 +488,19 @@ k_mx_merge_update_tc(const MergeDesc *__restrict__ md, const int *__restrict__ t
     const double ih = M.n + 1.0;
     const int d12 = M.orient ? DIR_N : DIR_E, d21 = M.orient ? DIR_S : DIR_W;
     float2 *O = out + M.out;
-    const __nv_bfloat16 *Ad = ydig + M.doff, *Bd = xdig + M.doff;
     const int kpad = M.kpad, ntile = kpad / 16;
-    const int arows = min(MT_ROWS, rp - a0), crows = min(MT_COLS, rp - c0);
+    // tile-ordered digit planes: the 128-row block of a0 and of c0 (c0's 64 rows are the
+    // first or second half of its block)
+    const __nv_bfloat16 *Ab = ydig + M.doff + (int64_t)(a0 >> 7) * (kpad >> 4) * 2048;
+    const __nv_bfloat16 *Bb = xdig + M.doff + (int64_t)(c0 >> 7) * (kpad >> 4) * 2048 + ((c0 & 127) >> 3) * 128;
     if (tid < MT_ROWS) s_ye[tid] = yex[M.eoff + min(a0 + tid, rp - 1)];
     else if (tid < MT_ROWS + MT_COLS) s_xe[tid - MT_ROWS] = xex[M.eoff + min(c0 + tid - MT_ROWS, rp - 1)];
     if (tid == 0) {
-        for (int q = 0; q < MT_STAGES; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[q])));
+        for (int q = 0; q < MT_STAGES; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[q])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[q])));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
         s_bad = 0;
     }
     if (warp == 0) {
@@ -507,55 +515,39 @@ k_mx_merge_update_tc(const MergeDesc *__restrict__ md, const int *__restrict__ t
     constexpr uint32_t idesc = umma_idesc_bf16(MT_ROWS, MT_COLS);
     const int q4 = warp & 3, h = warp >> 2;
     const int aa = a0 + 32 * q4 + lane;  // this thread's parent row in the epilogue
-    // this thread's share of every tile copy, resolved once: slot j is 16-byte piece
-    // tid + j * PIPE_THREADS of the tile (source at k = 0, offset in the stage, size)
-    constexpr int NPIECE = S * (MT_ROWS + MT_COLS) * 2;
-    constexpr int NSLOT = (NPIECE + PIPE_THREADS - 1) / PIPE_THREADS;
-    const __nv_bfloat16 *psrc[NSLOT];
-    uint32_t pdst[NSLOT], psz[NSLOT];
+    // 16-k tile t into a stage: one bulk copy per plane of A (4 KB) and of B (2 KB), all
+    // counted on the stage's `full` barrier (thread 0 only)
+    auto load_tile = [&](int t, int sg) {
+        unsigned char *sa = base + sg * STAGE, *sb = sa + S * 4096;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(&full[sg])),
+                     "r"((uint32_t)(S * 6144)));
 #pragma unroll
-    for (int j = 0; j < NSLOT; ++j) {
-        const int e = tid + j * PIPE_THREADS;
-        const int chunk = e & 1, rr = e >> 1;
-        const int q = rr / (MT_ROWS + MT_COLS), row = rr % (MT_ROWS + MT_COLS);
-        const bool isA = row < MT_ROWS;
-        const int r = isA ? row : row - MT_ROWS;
-        const bool ok = e < NPIECE && r < (isA ? arows : crows);
-        psrc[j] = (isA ? Ad : Bd) + (int64_t)min(q, S - 1) * plane + (int64_t)((isA ? a0 : c0) + (ok ? r : 0)) * kpad +
-                  chunk * 8;
-        pdst[j] = e < NPIECE ? (uint32_t)((isA ? q * 4096 : S * 4096 + q * 2048) + (r >> 3) * 256 + chunk * 128 +
-                                          (r & 7) * 16)
-                             : 0xffffffffu;
-        psz[j] = ok ? 16u : 0u;
-    }
-    auto load_tile = [&](int tile, int stage) {  // 16-k tile `tile` (absolute) into a stage
-        const uint32_t sb = smem_u32(base + stage * STAGE);
-#pragma unroll
-        for (int j = 0; j < NSLOT; ++j)
-            if (pdst[j] != 0xffffffffu)
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sb + pdst[j]),
-                             "l"(psrc[j] + tile * 16), "r"(psz[j]));
+        for (int q = 0; q < S; ++q) {
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 4096, [%2];\n" ::"r"(
+                             smem_u32(sa + q * 4096)),
+                         "l"(Ab + (int64_t)q * plane + (int64_t)t * 2048), "r"(smem_u32(&full[sg])));
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 2048, [%2];\n" ::"r"(
+                             smem_u32(sb + q * 2048)),
+                         "l"(Bb + (int64_t)q * plane + (int64_t)t * 2048), "r"(smem_u32(&full[sg])));
+        }
     };
-    // completion parity of each stage's mbarrier at the start of a chunk (bit s): tile kt
-    // of the chunk is completion (chunk base + kt / MT_STAGES) of stage kt % MT_STAGES
+    // completion parity of the stages' barriers at the start of a chunk (bit s): tile kt of
+    // the chunk is completion (chunk base + kt / MT_STAGES) of stage kt % MT_STAGES, for
+    // `full` and `empty` alike (each completes once per tile on its stage)
     unsigned bpar = 0u;
     bool bad = false;
     for (int t0 = 0; t0 < ntile && !bad; t0 += MT_KTILES) {
         const int nk = min(ntile - t0, MT_KTILES);
         const bool first = t0 == 0;
-#pragma unroll
-        for (int p = 0; p < MT_STAGES - 1; ++p) {
-            if (p < nk) load_tile(t0 + p, p);
-            asm volatile("cp.async.commit_group;\n" ::);
-        }
-        for (int kt = 0; kt < nk; ++kt) {
-            const int sg = kt % MT_STAGES;
-            asm volatile("cp.async.wait_group %0;\n" ::"n"(MT_STAGES - 2));
-            asm volatile("fence.proxy.async.shared::cta;\n" ::);
-            asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
-            __syncthreads();
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-            if (tid == 0) {
+        if (tid == 0) {  // copies and products, driven by one thread (its warp waits below)
+            for (int p = 0; p < MT_STAGES - 1 && p < nk; ++p) load_tile(t0 + p, p);
+            for (int kt = 0; kt < nk && !bad; ++kt) {
+                const int sg = kt % MT_STAGES;
+                if (!mbar_wait_bounded(&full[sg], ((bpar >> sg) & 1u) ^ (uint32_t)((kt / MT_STAGES) & 1), 1 << 22)) {
+                    bad = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
                 const unsigned char *sa = base + sg * STAGE, *sb = sa + S * 4096;
 #pragma unroll
                 for (int a = 0; a < S; ++a)
@@ -563,27 +555,30 @@ k_mx_merge_update_tc(const MergeDesc *__restrict__ md, const int *__restrict__ t
                     for (int b = 0; b < S - a; ++b)
                         umma_bf16(tmem + (uint32_t)((a + b) * MT_COLS), umma_desc(smem_u32(sa + a * 4096), 128, 256),
                                   umma_desc(smem_u32(sb + b * 2048), 128, 256), idesc, (kt > 0 || a > 0) ? 1u : 0u);
-                umma_commit(&mbar[sg]);
+                umma_commit(&empty[sg]);
+                // refill the stage the previous tile used, once its products have landed
+                const int nx = kt + MT_STAGES - 1;
+                if (nx < nk) {
+                    const int sp = nx % MT_STAGES;
+                    if (kt >= 1 &&
+                        !mbar_wait_bounded(&empty[sp], ((bpar >> sp) & 1u) ^ (uint32_t)(((kt - 1) / MT_STAGES) & 1),
+                                           1 << 22)) {
+                        bad = true;
+                        break;
+                    }
+                    load_tile(t0 + nx, sp);
+                }
             }
-            // refill the stage the previous tile used, once its products have landed
-            const int nx = kt + MT_STAGES - 1;
-            if (nx < nk) {
-                const int sp = nx % MT_STAGES;
-                const uint32_t par = ((bpar >> sp) & 1u) ^ (uint32_t)(((kt - 1) / MT_STAGES) & 1);
-                if (kt >= 1 && !mbar_wait_bounded(&mbar[sp], par, 1 << 20)) bad = true;
-                load_tile(t0 + nx, sp);
-            }
-            asm volatile("cp.async.commit_group;\n" ::);
+            if (bad) s_bad = 1;
         }
-        // the chunk's last products (they complete in order)
+        if (warp == 0) __syncwarp();
+        // everyone: the chunk's last products (they complete in order)
         const int sl = (nk - 1) % MT_STAGES;
-        if (!mbar_wait_bounded(&mbar[sl], ((bpar >> sl) & 1u) ^ (uint32_t)(((nk - 1) / MT_STAGES) & 1), 1 << 20))
-            bad = true;
+        if (!mbar_wait_bounded(&empty[sl], ((bpar >> sl) & 1u) ^ (uint32_t)(((nk - 1) / MT_STAGES) & 1), 1 << 22))
+            s_bad = 1;
 #pragma unroll
         for (int q = 0; q < MT_STAGES; ++q)  // tiles of this chunk on stage q
             if (q < nk) bpar ^= (uint32_t)(((nk - q + MT_STAGES - 1) / MT_STAGES) & 1) << q;
-        asm volatile("cp.async.wait_group 0;\n" ::);
-        if (bad) s_bad = 1;
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
@@ -829,13 +824,14 @@ cudaError_t mx_merge_update(const MergeDesc *md, const std::vector<MergeDesc> &h
     for (const MergeDesc &M : h_md) fl += 2.0 * (double)M.rp * M.rp * M.sp;
     const int nm = (int)h_md.size();
     const int rb = (max_rp + 3) / 4;
-    kt.begin(GM_K_MERGEUPDATE, fl, s);
-    MX_SPLIT_DISPATCH(split, (k_mx_merge_slice<SS><<<dim3(2 * rb, nm), 128, 0, s>>>(md, tab, in, ws, rb, ydig, yex,
-                                                                                      xdig, xex, plane)));
     int max_kpad = 0;
     for (const MergeDesc &M : h_md) max_kpad = std::max(max_kpad, M.kpad);
+    const bool tc = max_kpad >= MT_TC_MIN_K;  // the tcgen05 kernel reads tile-ordered digit planes
+    kt.begin(GM_K_MERGEUPDATE, fl, s);
+    MX_SPLIT_DISPATCH(split, (k_mx_merge_slice<SS><<<dim3(2 * rb, nm), 128, 0, s>>>(md, tab, in, ws, rb, ydig, yex,
+                                                                                      xdig, xex, plane, tc ? 1 : 0)));
     cudaError_t e = cudaSuccess;
-    if (max_kpad < MT_TC_MIN_K) {  // short K: the pipeline's fill and drain would dominate
+    if (!tc) {  // short K: the pipeline's fill and drain would dominate
         const dim3 g64((max_rp + 63) / 64, (max_rp + 63) / 64, nm);
         MX_SPLIT_DISPATCH(split, (e = cudaFuncSetAttribute(k_mx_merge_update<SS>,
                                                            cudaFuncAttributeMaxDynamicSharedMemorySize,

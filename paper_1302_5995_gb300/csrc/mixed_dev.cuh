@@ -242,9 +242,17 @@ __device__ __forceinline__ MergeTabMx merge_tab_mx(const MergeDesc &M, const int
 // dig[s * plane + row * kpad + k].  kpad is a multiple of 16.
 
 // One lane-strided warp slices a row of K df32 values, produced by `get(k)`.
+// Element (row, k) of a digit plane stored by 128-row x 16-k tiles, each tile in the
+// tensor cores' K-major core-matrix order (8 x 8 blocks of 128 bytes, k-block fastest
+// within a row group): a tile is one contiguous 4 KB bulk copy.
+__device__ __forceinline__ int64_t tiled_idx(int row, int k, int kpad) {
+    return ((int64_t)(row >> 7) * (kpad >> 4) + (k >> 4)) * 2048 + ((row & 127) >> 3) * 128 + ((k & 15) >> 3) * 64 +
+           (row & 7) * 8 + (k & 7);
+}
+
 template <int S, class Get>
 __device__ __forceinline__ void warp_slice_row(Get get, int K, int kpad, __nv_bfloat16 *dig, int64_t plane, int64_t row,
-                                               int *ex) {
+                                               int *ex, bool tiled = false) {
     const int lane = threadIdx.x & 31;
     float mx = 0.f;
     for (int k = lane; k < K; k += 32) mx = fmaxf(mx, fabsf(get(k).x));
@@ -255,8 +263,9 @@ __device__ __forceinline__ void warp_slice_row(Get get, int K, int kpad, __nv_bf
         float d[S];
         float2 v = k < K ? get(k) : make_float2(0.f, 0.f);
         digits<S>(v, e, d);
+        const int64_t at = tiled ? tiled_idx((int)row, k, kpad) : row * kpad + k;
 #pragma unroll
-        for (int s = 0; s < S; ++s) dig[(int64_t)s * plane + row * kpad + k] = __float2bfloat16_rn(d[s]);
+        for (int s = 0; s < S; ++s) dig[(int64_t)s * plane + at] = __float2bfloat16_rn(d[s]);
     }
 }
 

@@ -106,7 +106,7 @@ void add_merge(Stage &st, int n, const Box &c1, int64_t s1, const Box &c2, int64
     m.kpad = (mm + 15) / 16 * 16;
     if (m.kpad == 0) m.kpad = 16;
     m.doff = st.dig_elems;
-    st.dig_elems += (int64_t)m.rp * m.kpad;
+    st.dig_elems += (int64_t)((m.rp + 127) / 128 * 128) * m.kpad;  // rows padded to 128-row tiles
     m.eoff = (int)st.exp_elems;
     st.exp_elems += m.rp;
     st.max_m = std::max(st.max_m, mm);
@@ -265,7 +265,7 @@ int build_batch_plan(const std::vector<const Plan *> &plans, const std::vector<i
                 m.ws = m0.ws + ws_fill[shift + si];
                 m.prob = (int)pi;
                 m.doff = dst.dig_elems;
-                dst.dig_elems += (int64_t)m.rp * m.kpad;
+                dst.dig_elems += (int64_t)((m.rp + 127) / 128 * 128) * m.kpad;
                 m.eoff = (int)dst.exp_elems;
                 dst.exp_elems += m.rp;
                 const int *t = src.table.data() + m0.tab;
@@ -327,7 +327,9 @@ int validate_plan(const Plan &plan) {
             if (m.out < st.out_base || m.out + (int64_t)m.rp * m.rp > st.out_base + st.out_doubles) return GM_EINVAL;
             int mm = 2 * m.sp;
             if (m.ws < 0 || m.ws + (int64_t)mm * (mm + m.rp) > st.ws_doubles) return GM_EINVAL;
-            if (m.kpad < mm || m.kpad % 16 || m.doff < 0 || m.doff + (int64_t)m.rp * m.kpad > st.dig_elems) return GM_EINVAL;
+            if (m.kpad < mm || m.kpad % 16 || m.doff < 0 || m.doff % 2048 ||
+                m.doff + (int64_t)((m.rp + 127) / 128 * 128) * m.kpad > st.dig_elems)
+                return GM_EINVAL;
             if (m.eoff < 0 || m.eoff + m.rp > st.exp_elems) return GM_EINVAL;
             const int *t = st.table.data() + m.tab;
             if (m.tab + 4 * m.sp + 2 * m.n1 + 2 * m.n2 + 8 > (int)st.table.size()) return GM_EINVAL;
