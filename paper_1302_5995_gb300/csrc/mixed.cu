@@ -444,7 +444,8 @@ k_mx_merge_update(const MergeDesc *__restrict__ md, const int *__restrict__ tab,
 // cores: a CTA takes 128 rows (a) x 64 columns (c) of the parent; the 16-k digit tiles of
 // Y and X stream through four shared-memory stages by bulk copies on the tensor memory
 // accelerator (one 4 KB / 2 KB copy per digit plane, counted on the stage's `full`
-// barrier); one thread issues each tile's 21 digit-pair products as tcgen05.mma
+// barrier, issued by a producer thread); another thread issues each tile's 21 digit-pair
+// products as tcgen05.mma
 // (M = 128, N = 64, K = 16) into six level accumulators in tensor memory and commits
 // them to the stage's `empty` barrier, and a stage is refilled only once that commit
 // has landed.  K runs in chunks of at most 2048 (level sums stay below 2^23, exact in fp32);
@@ -531,6 +532,9 @@ k_mx_merge_update_tc(const MergeDesc *__restrict__ md, const int *__restrict__ t
                          "l"(Bb + (int64_t)q * plane + (int64_t)t * 2048), "r"(smem_u32(&full[sg])));
         }
     };
+    // descriptors of stage 0's first planes (a stage or plane offset adds to the address
+    // field, which stays below 2^14 units of 16 bytes)
+    const uint64_t adesc0 = umma_desc(smem_u32(base), 128, 256), bdesc0 = umma_desc(smem_u32(base + S * 4096), 128, 256);
     // completion parity of the stages' barriers at the start of a chunk (bit s): tile kt of
     // the chunk is completion (chunk base + kt / MT_STAGES) of stage kt % MT_STAGES, for
     // `full` and `empty` alike (each completes once per tile on its stage)
@@ -539,39 +543,36 @@ k_mx_merge_update_tc(const MergeDesc *__restrict__ md, const int *__restrict__ t
     for (int t0 = 0; t0 < ntile && !bad; t0 += MT_KTILES) {
         const int nk = min(ntile - t0, MT_KTILES);
         const bool first = t0 == 0;
-        if (tid == 0) {  // copies and products, driven by one thread (its warp waits below)
-            for (int p = 0; p < MT_STAGES - 1 && p < nk; ++p) load_tile(t0 + p, p);
-            for (int kt = 0; kt < nk && !bad; ++kt) {
+        if (tid == 32) {  // producer: copies, each stage refilled once its products landed
+            for (int t = 0; t < nk && !bad; ++t) {
+                const int sg = t % MT_STAGES;
+                if (t >= MT_STAGES &&
+                    !mbar_wait_bounded(&empty[sg], ((bpar >> sg) & 1u) ^ (uint32_t)((t / MT_STAGES - 1) & 1), 1 << 22))
+                    bad = true;
+                else
+                    load_tile(t0 + t, sg);
+            }
+            if (bad) s_bad = 1;
+        } else if (tid == 0) {  // products: wait for a stage's copies, issue, commit
+            for (int kt = 0; kt < nk; ++kt) {
                 const int sg = kt % MT_STAGES;
                 if (!mbar_wait_bounded(&full[sg], ((bpar >> sg) & 1u) ^ (uint32_t)((kt / MT_STAGES) & 1), 1 << 22)) {
                     bad = true;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-                const unsigned char *sa = base + sg * STAGE, *sb = sa + S * 4096;
+                const uint64_t da = adesc0 + (uint64_t)((sg * STAGE) >> 4), db = bdesc0 + (uint64_t)((sg * STAGE) >> 4);
 #pragma unroll
                 for (int a = 0; a < S; ++a)
 #pragma unroll
                     for (int b = 0; b < S - a; ++b)
-                        umma_bf16(tmem + (uint32_t)((a + b) * MT_COLS), umma_desc(smem_u32(sa + a * 4096), 128, 256),
-                                  umma_desc(smem_u32(sb + b * 2048), 128, 256), idesc, (kt > 0 || a > 0) ? 1u : 0u);
+                        umma_bf16(tmem + (uint32_t)((a + b) * MT_COLS), da + (uint64_t)(a * 4096 >> 4),
+                                  db + (uint64_t)(b * 2048 >> 4), idesc, (kt > 0 || a > 0) ? 1u : 0u);
                 umma_commit(&empty[sg]);
-                // refill the stage the previous tile used, once its products have landed
-                const int nx = kt + MT_STAGES - 1;
-                if (nx < nk) {
-                    const int sp = nx % MT_STAGES;
-                    if (kt >= 1 &&
-                        !mbar_wait_bounded(&empty[sp], ((bpar >> sp) & 1u) ^ (uint32_t)(((kt - 1) / MT_STAGES) & 1),
-                                           1 << 22)) {
-                        bad = true;
-                        break;
-                    }
-                    load_tile(t0 + nx, sp);
-                }
             }
             if (bad) s_bad = 1;
         }
-        if (warp == 0) __syncwarp();
+        if (warp < 2) __syncwarp();
         // everyone: the chunk's last products (they complete in order)
         const int sl = (nk - 1) % MT_STAGES;
         if (!mbar_wait_bounded(&empty[sl], ((bpar >> sl) & 1u) ^ (uint32_t)(((nk - 1) / MT_STAGES) & 1), 1 << 22))
