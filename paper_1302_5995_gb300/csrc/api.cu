@@ -8,6 +8,8 @@
 // memory comes from the stream-ordered allocator on the build stream.
 #include <cuda_runtime.h>
 
+#include <chrono>
+
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -55,6 +57,32 @@ bool is_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// The library's stream-ordered memory pool on a device: it keeps freed workspace mapped
+// (release threshold unbounded), so a build does not map its few hundred MB of temporaries
+// anew after every synchronisation, as the device's default pool (threshold 0) would.
+cudaMemPool_t lib_pool() {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = pools.find(dev);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    pools[dev] = pool;
+    return pool;
+}
+
 // Device buffer released on scope exit through the stream-ordered allocator.
 struct DBuf {
     void *p = nullptr;
@@ -71,7 +99,8 @@ struct DBuf {
         release();
         s = st;
         if (bytes == 0) bytes = 16;
-        if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+        cudaMemPool_t pool = lib_pool();
+        if ((pool ? cudaMallocFromPoolAsync(&p, bytes, pool, st) : cudaMallocAsync(&p, bytes, st)) != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
             return GM_ENOMEM;
@@ -305,6 +334,12 @@ constexpr float kMaxRefineRatio = 0x1p-13f;
 // GM_ESINGULAR and growth[p] the block-pivoting growth flag of a mixed build.
 int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp, const double *db, const double *dc,
               const double *dd, std::vector<gm_handle *> &H, std::vector<int> &code, std::vector<int> &growth) {
+    const auto t_enter = std::chrono::steady_clock::now();
+    std::vector<double> stamps;  // host time (ms) at the end of each phase, reported under GM_DEBUG
+    auto stamp = [&] {
+        if (debug_on())
+            stamps.push_back(std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_enter).count());
+    };
     const DevPlan &dp = *dpp;
     const Plan &P = dp.plan;
     cudaStream_t s = (cudaStream_t)o.stream;
@@ -468,6 +503,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
         return mx_gj_sweep(d_sys, h_sys, max_m, max_ncol, (float2 *)ws, nb, split, scr, dst, stage, s, kt);
     };
 
+    stamp();
     // merge stages (Section 3.3 step 3): per level, horizontal then vertical
     for (size_t si = 0; si < dp.stages.size(); ++si) {
         const DevStage &ds = dp.stages[si];
@@ -527,6 +563,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
                                ydig.as<__nv_bfloat16>(), yex.as<int>(), xdig.as<__nv_bfloat16>(), xex.as<int>(),
                                ds.dig_elems, db, dc, dd, 0, dst, s, kt));
         }
+        stamp();
     }
 
     DBuf rws;
@@ -599,7 +636,16 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
     for (DBuf *b : {&rws, &piv, &u12, &perm, &perm_n, &a11, &fdig, &rdig, &fex, &rex, &ydig, &xdig, &yex, &xex, &bxd,
                     &bad, &bxe, &bae, &bpmag, &bfdig, &bfex, &brdig, &brex, &arena_buf, &stat})
         b->release();
+    const auto t_enq = std::chrono::steady_clock::now();
     CK(cudaStreamSynchronize(s));
+    if (debug_on()) {  // host time to enqueue the build, and until it finished on the device
+        const auto t_done = std::chrono::steady_clock::now();
+        fprintf(stderr, "gm: build enqueued in %.3f ms, done after %.3f ms; phases end at",
+                std::chrono::duration<double, std::milli>(t_enq - t_enter).count(),
+                std::chrono::duration<double, std::milli>(t_done - t_enter).count());
+        for (double x : stamps) fprintf(stderr, " %.2f", x);
+        fprintf(stderr, " ms\n");
+    }
     int launches = 0;
     gm_info_t info{};
     for (int f = 0; f < GM_K_NFAM; ++f) {
