@@ -608,6 +608,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
     }
     CK(sweep(dp.d_root_sys, dp.h_root_sys, max_r, dp.max_root_ncol, rws.p, sum_rr, sum_rc,
              (int)dp.stages.size() + 1));
+    stamp();
     for (size_t i = 0; i < P.roots.size(); ++i) {
         const RootDesc &r = P.roots[i];
         gm_handle *h = H[r.problem];
@@ -630,6 +631,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             CK(mx_root_finalize(rws.as<float2>() + sy.off, r.r, r.n, h->T, h->Tdf, h->tdig, h->tex, split, s, kt));
         }
     }
+    stamp();
     }
     CK(cudaMemcpyAsync(hst.data(), stat.p, np * sizeof(Status), cudaMemcpyDeviceToHost, s));
     // release temporaries (stream-ordered) before the final synchronisation

@@ -105,6 +105,7 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
              __nv_bfloat16 *__restrict__ a_dig, int64_t plane, int *__restrict__ x_ex, int *__restrict__ a_ex,
              float *__restrict__ pmag, Status *st, int stage) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
     float2 *Adf = (float2 *)smem_raw;       // [64][LDF] A11 (df32)
     float *Xs = (float *)(Adf + 64 * LDF);  // [64][65] rows of X0
     __shared__ __align__(16) float prow[2][4 * PRS];  // pivot row (unscaled), registers' order
@@ -214,6 +215,7 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
             for (int j = 28; j < 32; ++j) a[j] = 0.f;
         }
     }
+    pdl_trigger();  // the R kernel may start launching while this one cuts its digits
     if (cg >= 2) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) Xs[my_step * 65 + (cg - 2) * 32 + j] = a[j];
@@ -331,6 +333,7 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
              int64_t fplane, int *__restrict__ fex, __nv_bfloat16 *__restrict__ rdig, int64_t cplane,
              int *__restrict__ rex, const float *__restrict__ pmag, Status *__restrict__ st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
     const SysDesc Sy = sys[blockIdx.y];
     const int m = Sy.m;
     if (k >= m) return;
@@ -517,6 +520,7 @@ k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
              const __nv_bfloat16 *__restrict__ fdig, int64_t fplane, const int *__restrict__ fex,
              const __nv_bfloat16 *__restrict__ rdig, int64_t rplane, const int *__restrict__ rex) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();  // the next block's factor (one CTA per system) may launch and wait
     __nv_bfloat16 *As = (__nv_bfloat16 *)smem_raw;  // [S][64][KP64]
     __nv_bfloat16 *Bs = As + S * 64 * KP64;
     const SysDesc Sy = sys[blockIdx.z];
@@ -740,6 +744,24 @@ k_blk_update_tc(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k,
 
 // ----------------------------------------------------------------------------- launcher
 
+// Launch with programmatic stream serialization when `pdl` (the kernel must call
+// pdl_wait() before it reads what its predecessor in the stream writes).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 #define BLK_SPLIT_DISPATCH(split, CALL) \
     do {                                 \
         switch (split) {                 \
@@ -798,26 +820,34 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
         const int cols = max_ncol - k;
         const int cb = (cols + 63) / 64, rb = (max_m + 127) / 128;
         kt.begin(GM_K_PANEL, fl_fac, c);
-        BLK_SPLIT_DISPATCH(split, (k_blk_factor<SS><<<nsys, FAC_THREADS, fsm, c>>>(
-                                      d_sys, ws, k, scr.x_dig, scr.a11_dig, scr.inv_plane, scr.x_ex, scr.a11_ex,
-                                      scr.pmag, st, stage)));
+        // programmatic launches where the predecessor in the stream is the kernel waited on
+        // (not with timing events between launches, not after the entry join)
+        const bool pdl = k > 0 && !kt.timed(GM_K_GJUPDATE) && !kt.timed(GM_K_PANEL);
+        BLK_SPLIT_DISPATCH(split, (e = launch_k(pdl, k_blk_factor<SS>, dim3(nsys), dim3(FAC_THREADS), fsm, c, d_sys,
+                                                ws, k, scr.x_dig, scr.a11_dig, scr.inv_plane, scr.x_ex, scr.a11_ex,
+                                                scr.pmag, st, stage)));
+        if (e != cudaSuccess) return e;
         kt.end(c);
         // R writes digit set `par`, which the rest of the update two steps back read: that
         // finished before the previous step's next-block update (below) started
         kt.begin(GM_K_PIVROWS, fl_r, c);
         // 32-column R tiles while the step would leave most SMs idle
+        const bool pdl_r = !kt.timed(GM_K_PANEL) && !kt.timed(GM_K_PIVROWS);
         if (nsys * cb <= 96) {
             const int cb32 = (cols + 31) / 32;
-            BLK_SPLIT_DISPATCH(split, (k_blk_rfused<SS, 1><<<dim3(cb32 + rb, nsys), TILE_THREADS, rsm, c>>>(
-                                          d_sys, ws, k, cb32, scr.x_dig, scr.a11_dig, scr.inv_plane, scr.x_ex,
-                                          scr.a11_ex, scr.fdig[par], scr.fplane, scr.fex[par], scr.rdig[par],
-                                          scr.cplane, scr.rex[par], scr.pmag, st)));
+            BLK_SPLIT_DISPATCH(split, (e = launch_k(pdl_r, k_blk_rfused<SS, 1>, dim3(cb32 + rb, nsys),
+                                                    dim3(TILE_THREADS), rsm, c, d_sys, ws, k, cb32, scr.x_dig,
+                                                    scr.a11_dig, scr.inv_plane, scr.x_ex, scr.a11_ex, scr.fdig[par],
+                                                    scr.fplane, scr.fex[par], scr.rdig[par], scr.cplane,
+                                                    scr.rex[par], scr.pmag, st)));
         } else {
-            BLK_SPLIT_DISPATCH(split, (k_blk_rfused<SS, 2><<<dim3(cb + rb, nsys), TILE_THREADS, rsm, c>>>(
-                                          d_sys, ws, k, cb, scr.x_dig, scr.a11_dig, scr.inv_plane, scr.x_ex,
-                                          scr.a11_ex, scr.fdig[par], scr.fplane, scr.fex[par], scr.rdig[par],
-                                          scr.cplane, scr.rex[par], scr.pmag, st)));
+            BLK_SPLIT_DISPATCH(split, (e = launch_k(pdl_r, k_blk_rfused<SS, 2>, dim3(cb + rb, nsys),
+                                                    dim3(TILE_THREADS), rsm, c, d_sys, ws, k, cb, scr.x_dig,
+                                                    scr.a11_dig, scr.inv_plane, scr.x_ex, scr.a11_ex, scr.fdig[par],
+                                                    scr.fplane, scr.fex[par], scr.rdig[par], scr.cplane,
+                                                    scr.rex[par], scr.pmag, st)));
         }
+        if (e != cudaSuccess) return e;
         kt.end(c);
         const dim3 gu(nrt, cb, nsys);
         if (la && cb >= 2 && (e = cudaEventRecord(scr.ev_r, c)) != cudaSuccess) return e;

@@ -38,6 +38,7 @@ struct KTimer {
             event_pool_put(r.b);
         }
     }
+    bool timed(int fam) const { return on && ((mask >> fam) & 1u); }  // launches of fam get events
     void begin(int fam, double fl, cudaStream_t s) {
         flops[fam] += fl;
         launches[fam] += 1;

@@ -110,6 +110,13 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t v[8]) {
                  : "r"(taddr));
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization
+// may start while its predecessor in the stream finishes; pdl_wait() blocks until the
+// predecessor has completed and its writes are visible (a no-op without the attribute),
+// pdl_trigger() lets this kernel's own dependent start launching.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 // ----------------------------------------------------------------------------- digits
 
 // Exponent e with |x| < 2^e for every x of a set whose largest |hi| is m (0 -> 0).
