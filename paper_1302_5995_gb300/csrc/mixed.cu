@@ -720,14 +720,13 @@ k_mx_slice_G(const double *__restrict__ G, int N, int B, int kpad, __nv_bfloat16
 
 // V = T G from the sliced operands; V is FP64 N x B.
 template <int S>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(PIPE_THREADS)
 k_mx_apply(const __nv_bfloat16 *__restrict__ tdig, const int *__restrict__ tex, int64_t tplane,
            const __nv_bfloat16 *__restrict__ gdig, const int *__restrict__ gex, int64_t gplane, int kpad,
            double *__restrict__ V, int N, int B) {
-    __shared__ __align__(16) __nv_bfloat16 As[S * 64 * KP];
-    __shared__ __align__(16) __nv_bfloat16 Bs[S * 64 * KP];
+    extern __shared__ __align__(16) unsigned char smem_raw[];  // pipe_smem_bytes(S)
     const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
-    digit_gemm_chunks<S>(tdig, tplane, kpad, i0, N, tex, gdig, gplane, kpad, j0, B, gex, N, As, Bs,
+    digit_gemm_pipe<S>(tdig, tplane, kpad, i0, N, tex, gdig, gplane, kpad, j0, B, gex, N, (__nv_bfloat16 *)smem_raw,
                          [&](const int *r, const int *cl, const float2 *v, bool first) {
 #pragma unroll
                              for (int q = 0; q < 4; ++q) {
@@ -887,8 +886,12 @@ cudaError_t mx_apply(const __nv_bfloat16 *tdig, const int *tex, const double *G,
     MX_SPLIT_DISPATCH(split, (k_mx_slice_G<SS><<<(B + 3) / 4, 128, 0, s>>>(G, N, B, kpad, gdig, (int64_t)B * kpad,
                                                                            gex)));
     dim3 g((N + 63) / 64, (B + 63) / 64);
-    MX_SPLIT_DISPATCH(split, (k_mx_apply<SS><<<g, 128, 0, s>>>(tdig, tex, (int64_t)N * kpad, gdig, gex,
-                                                                (int64_t)B * kpad, kpad, V, N, B)));
+    cudaError_t e = cudaSuccess;
+    MX_SPLIT_DISPATCH(split, (e = cudaFuncSetAttribute(k_mx_apply<SS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)pipe_smem_bytes(SS))));
+    if (e != cudaSuccess) return e;
+    MX_SPLIT_DISPATCH(split, (k_mx_apply<SS><<<g, PIPE_THREADS, pipe_smem_bytes(SS), s>>>(
+                                 tdig, tex, (int64_t)N * kpad, gdig, gex, (int64_t)B * kpad, kpad, V, N, B)));
     return cudaGetLastError();
 }
 
