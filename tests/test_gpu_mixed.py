@@ -143,3 +143,17 @@ def test_convection_stays_mixed_block_pivoted(gm):
     assert info["pivot_fallback"] == 0 and info["precision"] == gm.PREC_MIXED
     assert info["pivoting"] == gm.PIVOT_BLOCK
     assert rel_mat(op.dtn(), gm.build(b, c, d, n, leaf).dtn()) < TOL_MIXED
+
+
+def test_mixed_long_interface_matches_fp64_at_1100(gm):
+    """n = 1100: the top merge's interface gives K = 2196 > 2048, so the tensor-memory
+    merge update accumulates its levels in two K chunks (the second adds into the parent
+    entries the first wrote).  Against the FP64 build of the same problem."""
+    n, leaf = 1100, 16
+    b, c, d = inputs.convection_fields(n, seeds=(21, 22, 23))
+    op = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED, split_digits=6)
+    assert op.info()["pivot_fallback"] == 0
+    T = op.dtn()
+    op.free()
+    ref = gm.build(b, c, d, n, leaf)
+    assert rel_mat(T, ref.dtn()) < TOL_MIXED
