@@ -158,7 +158,10 @@ void gm_opts_default(gm_opts *opts);
  *             dense).  GM_EUNSUPPORTED if a root node's rank reaches 96 (the root does
  *             not compress enough; build with tol = 0).
  *   out     : receives a new handle that owns all device memory of the operator.
- * Blocks the calling thread until the build has finished on the device.
+ * Blocks the calling thread until the build has finished on the device.  Temporaries
+ * come from a stream-ordered memory pool the library keeps per device; it does not
+ * return freed memory to the system (later builds reuse it), so the process holds the
+ * largest build's workspace (peak_workspace) after the first build.
  */
 int gm_build(const double *b, const double *c, const double *d, int n, int leaf, double tol,
              gm_handle **out);
