@@ -50,7 +50,7 @@ def bf16_peak_tflops():
 
 
 def family_roofline(precision, fam):
-    """(bound, peak TFLOP/s, source) of a kernel family in this build."""
+    """(bound, peak TFLOP/s, source) of a kernel family of the timed operator build."""
     if precision == "fp64":
         return "alu", FP64_PEAK_TFLOPS, "FP64 pipe from unit counts: 152 SMs x 4 flop/clk x 2070 MHz"
     if fam == "leaf":  # double-float arithmetic: 18 FP32 operations per multiply-add

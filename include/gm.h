@@ -48,7 +48,7 @@ extern "C" {
                                 gm_info().bad_stage names where                          */
 #define GM_ETIMEOUT (-4)     /* a bounded device-side wait gave up                       */
 #define GM_ECUDA (-5)        /* a CUDA runtime call failed                               */
-#define GM_EUNSUPPORTED (-6) /* valid request this build does not support               */
+#define GM_EUNSUPPORTED (-6) /* valid request the library does not support              */
 #define GM_ESCRATCH (-7)     /* request larger than the fixed scratch of gm_solve_static */
 
 #define GM_PREC_FP64 0  /* every step in FP64 */
