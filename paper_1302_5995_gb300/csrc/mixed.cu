@@ -448,10 +448,11 @@ k_mx_merge_update(const MergeDesc *__restrict__ md, const int *__restrict__ tab,
 // products as tcgen05.mma
 // (M = 128, N = 64, K = 16) into six level accumulators in tensor memory and commits
 // them to the stage's `empty` barrier, and a stage is refilled only once that commit
-// has landed.  K runs in chunks of at most 2048 (level sums stay below 2^23, exact in fp32);
+// has landed.  K runs in chunks of at most 512: level g sums g + 1 digit pairs of at most
+// 64 x 64 each, and (g + 1) 512 64^2 < 2^24 for g < 6, so every level sum is exact in fp32;
 // after each chunk eight warps read the levels back (tcgen05.ld) and apply the same
 // epilogue as the mma.sync kernel.  Every wait is bounded (GM_ETIMEOUT, no hang).
-constexpr int MT_ROWS = 128, MT_COLS = 64, MT_STAGES = 4, MT_KTILES = 128;  // 128 x 16 = 2048 k per chunk
+constexpr int MT_ROWS = 128, MT_COLS = 64, MT_STAGES = 4, MT_KTILES = 32;  // 32 x 16 = 512 k per chunk
 constexpr int MT_TC_MIN_K = 192;  // shorter merges keep the mma.sync kernel
 
 size_t mx_merge_tc_smem(int split) {

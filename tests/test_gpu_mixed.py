@@ -146,9 +146,10 @@ def test_convection_stays_mixed_block_pivoted(gm):
 
 
 def test_mixed_long_interface_matches_fp64_at_1100(gm):
-    """n = 1100: the top merge's interface gives K = 2196 > 2048, so the tensor-memory
-    merge update accumulates its levels in two K chunks (the second adds into the parent
-    entries the first wrote).  Against the FP64 build of the same problem."""
+    """n = 1100: the top merge's interface gives K = 2196, so the tensor-memory merge
+    update accumulates its levels in five K chunks of at most 512 (each later chunk adds
+    into the parent entries the first wrote).  Against the FP64 build of the same
+    problem."""
     n, leaf = 1100, 16
     b, c, d = inputs.convection_fields(n, seeds=(21, 22, 23))
     op = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED, split_digits=6)
