@@ -14,7 +14,8 @@ route to values the five-point scheme of Section 6 fixes exactly.
 3. Sine transform.  With constant b, c (|bh|, |ch| < 1) and d, the diagonal similarity
    u = rho_x^i rho_y^j w, rho = sqrt((1 + bh)/(1 - bh)), makes the operator symmetric
    with eigenvectors sin(p pi (i+1)/(n+1)) sin(q pi (j+1)/(n+1)); the system is then
-   solved exactly by two type-I discrete sine transforms (scipy.fft).
+   solved exactly by two type-I discrete sine transforms (scipy.fft).  The same solve
+   with a unit body load and zero Dirichlet data gives the load operator's columns.
 """
 from __future__ import annotations
 
@@ -69,8 +70,9 @@ def harmonic_pairs(n):
     return G, V
 
 
-def dst_dtn_matrix(n, b, c, d):
-    """Full 4n x 4n DtN matrix for constant coefficients by the sine transform."""
+def _dst_solver(n, b, c, d):
+    """Exact solve of the constant-coefficient scheme (zero Dirichlet data) by the sine
+    transform: returns (solve, weights), solve(F) -> U for right-hand sides F[k, j, i]."""
     from scipy.fft import dstn
 
     h = 1.0 / (n + 1)
@@ -85,18 +87,43 @@ def dst_dtn_matrix(n, b, c, d):
     p = np.arange(1, n + 1)
     lam = (wC - 2 * sx * np.cos(p * np.pi / (n + 1)))[None, :] \
         - 2 * sy * np.cos(p * np.pi / (n + 1))[:, None]  # [q, p]
-    gi, gj, ni, nj = _ghost_and_neighbour_positions(n)
-    wdir = np.select([gj < 0, gi >= n, gj >= n, gi < 0], [wS, wE, wN, wW])
-    F = np.zeros((4 * n, n, n))  # right-hand side of each unit ghost vector, [k, j, i]
-    F[np.arange(4 * n), nj, ni] = -wdir
     i = np.arange(n)
     scale = (rx ** i)[None, :] * (ry ** i)[:, None]  # u = scale * w
-    Fw = F / scale[None]
-    # exact inverse of the symmetric operator: orthonormal DST-I diagonalises it
-    W = dstn(dstn(Fw, type=1, axes=(1, 2), norm="ortho") / lam[None], type=1, axes=(1, 2),
-             norm="ortho")
-    U = W * scale[None]
+
+    def solve(F):
+        Fw = F / scale[None]
+        # exact inverse of the symmetric operator: orthonormal DST-I diagonalises it
+        W = dstn(dstn(Fw, type=1, axes=(1, 2), norm="ortho") / lam[None], type=1, axes=(1, 2),
+                 norm="ortho")
+        return W * scale[None]
+
+    return solve, dict(E=wE, W=wW, N=wN, S=wS)
+
+
+def dst_dtn_matrix(n, b, c, d):
+    """Full 4n x 4n DtN matrix for constant coefficients by the sine transform."""
+    h = 1.0 / (n + 1)
+    solve, w = _dst_solver(n, b, c, d)
+    gi, gj, ni, nj = _ghost_and_neighbour_positions(n)
+    wdir = np.select([gj < 0, gi >= n, gj >= n, gi < 0], [w["S"], w["E"], w["N"], w["W"]])
+    F = np.zeros((4 * n, n, n))  # right-hand side of each unit ghost vector, [k, j, i]
+    F[np.arange(4 * n), nj, ni] = -wdir
+    U = solve(F)
     T = np.zeros((4 * n, 4 * n))
     T[:, :] = -U[:, nj, ni].T / h  # row = ghost whose flux we read, column = data vector
     T += np.eye(4 * n) / h
     return T
+
+
+def dst_load_matrix(n, b, c, d, idx):
+    """Body-load operator F (4n x len(idx)) for constant coefficients: column m is the
+    flux -u_{k'}/h of the solution with a unit load at node idx[m] (flat i + n j) and zero
+    Dirichlet data, the solution taken exactly by the sine transform."""
+    h = 1.0 / (n + 1)
+    solve, _ = _dst_solver(n, b, c, d)
+    idx = np.asarray(idx).reshape(-1)
+    F = np.zeros((idx.size, n, n))
+    F[np.arange(idx.size), idx // n, idx % n] = 1.0
+    U = solve(F)
+    gi, gj, ni, nj = _ghost_and_neighbour_positions(n)
+    return -U[:, nj, ni].T / h

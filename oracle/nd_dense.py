@@ -13,6 +13,10 @@ Follows, in the paper's order and notation:
   Section 3.3      four-child merge as three pairwise merges; level-by-level sweep
   Section 3.3 (4)  root: invert the root Schur complement to get the solution operator
   Section 6        five-point stencil with (1/h) convection terms
+  Section 6.1      Random Laplacian problems: a conductance network on the same grid
+  Section 6.3      body loads at listed nodes: every box carries a load map beside S
+                   (leaf: f_b - A_bi A_ii^{-1} f_i; merge: the updated right-hand side of
+                   Section 3.2), and the root gives the second operator F of v = T g + F f
 
 Readings where the paper is silent (each one is listed with its reason in the design
 notes of the repository):
@@ -20,6 +24,9 @@ notes of the repository):
   * a box's "ring" P_b is its outermost layer of unknowns, ordered counter-clockwise
     from its south-west corner; a tree split gives the west/south child floor(a/2).
   * four-child merge order: (SW + SE), (NW + NE), then (S-half + N-half).
+  * a network's equation is (1/h^2) sum over links of sigma (u_k - u_l) = f_k and its
+    datum at ghost k the link current sigma_k (g_k - u_{k'})/h (unit conductivities
+    give Laplace); a body load f_k enters the equation at its node as written.
   * the Neumann datum at ghost k is the outward one-sided flux (g_k - u_{k'})/h,
     k' the only unknown next to k; hence T = (I - P S_root^{-1} B)/h, where B holds
     every ring node's stencil weight on its ghosts (negated, moved to the right-hand
@@ -57,6 +64,38 @@ class Problem:
             NORTH: -1.0 / h**2 + C / h,
             SOUTH: -1.0 / h**2 - C / h,
         }
+
+    @classmethod
+    def network(cls, sx, sy, n):
+        """Random Laplacian problems (Section 6.1): a square-grid network whose links carry
+        conductivities; the equation at node k is (1/h^2) sum_l sigma_l (u_k - u_l) = f_k
+        (scaled like the five-point Laplacian, so unit conductivities give Laplace).
+        sx: n rows of n + 1 x-links, [j, i] joins (i-1, j) and (i, j); sy: n + 1 rows of n
+        y-links, [j, i] joins (i, j-1) and (i, j); the outermost links reach the ghosts."""
+        self = cls.__new__(cls)
+        self.n = n
+        self.h = 1.0 / (n + 1)
+        ih2 = 1.0 / self.h**2
+        SX = np.asarray(sx, dtype=np.float64).reshape(n, n + 1)
+        SY = np.asarray(sy, dtype=np.float64).reshape(n + 1, n)
+        east, west, north, south = SX[:, 1:], SX[:, :-1], SY[1:, :], SY[:-1, :]
+        self.w = {
+            0: (east + west + north + south) * ih2,
+            EAST: -east * ih2,
+            WEST: -west * ih2,
+            NORTH: -north * ih2,
+            SOUTH: -south * ih2,
+        }
+        t = np.arange(n)
+        # conductivity of each ghost's link, in ghost order (south, east, north, west)
+        self.ghost_sigma = np.concatenate([SY[0, t], SX[t, n], SY[n, n - 1 - t], SX[n - 1 - t, 0]])
+        return self
+
+    def datum_weights(self):
+        """Weight of each ghost's datum: 1 for the PDE flux (g_k - u_k')/h, the link's
+        conductivity for a network (the current through the link, over h)."""
+        sig = getattr(self, "ghost_sigma", None)
+        return np.ones(4 * self.n) if sig is None else sig
 
     def A_block(self, rows, cols):
         """Dense sub-matrix A(rows, cols) of the global stencil matrix.
@@ -96,6 +135,9 @@ class Box:
         out += [(x0 + i, y0 + b - 1) for i in range(a - 2, -1, -1)]
         out += [(x0, y0 + j) for j in range(b - 2, 0, -1)]
         return out
+
+    def contains(self, q):
+        return self.x0 <= q[0] < self.x0 + self.a and self.y0 <= q[1] < self.y0 + self.b
 
     def interior(self):
         ring = set(self.ring())
@@ -140,6 +182,20 @@ def leaf_schur(prob: Problem, box: Box):
     return A_bb - A_bi @ np.linalg.solve(A_ii, A_ib)
 
 
+def partition_we(box1: Box, box2: Box, parent: Box):
+    """Eq. partition_we: positions (in each child's ring) of P1, P3 (child 1) and P2, P4
+    (child 2) -- the nodes that stay on the parent's ring and the ones that become
+    interior -- and the node lists themselves."""
+    r1, r2 = box1.ring(), box2.ring()
+    on_parent = set(parent.ring())
+    i1 = [k for k, q in enumerate(r1) if q in on_parent]
+    i3 = [k for k, q in enumerate(r1) if q not in on_parent]
+    i2 = [k for k, q in enumerate(r2) if q in on_parent]
+    i4 = [k for k, q in enumerate(r2) if q not in on_parent]
+    return (i1, i3, i2, i4, [r1[k] for k in i1], [r1[k] for k in i3],
+            [r2[k] for k in i2], [r2[k] for k in i4])
+
+
 def merge_two(prob: Problem, box1: Box, S1, box2: Box, S2, parent: Box, interface_solve=None):
     """Eq. S_fromtwo_nd for two sibling rectangles whose union is `parent`.
 
@@ -149,16 +205,8 @@ def merge_two(prob: Problem, box1: Box, S1, box2: Box, S2, parent: Box, interfac
     interface_solve(S33, A34, A43, S44, Z) -> [S33 A34; A43 S44]^{-1} Z replaces the
     dense solve when given (the HBS Step 1 of the accelerated method).
     """
-    r1, r2, rp = box1.ring(), box2.ring(), parent.ring()
-    on_parent = set(rp)
-    i1 = [k for k, q in enumerate(r1) if q in on_parent]
-    i3 = [k for k, q in enumerate(r1) if q not in on_parent]
-    i2 = [k for k, q in enumerate(r2) if q in on_parent]
-    i4 = [k for k, q in enumerate(r2) if q not in on_parent]
-    P1 = [r1[k] for k in i1]
-    P3 = [r1[k] for k in i3]
-    P2 = [r2[k] for k in i2]
-    P4 = [r2[k] for k in i4]
+    rp = parent.ring()
+    i1, i3, i2, i4, P1, P3, P2, P4 = partition_we(box1, box2, parent)
 
     S11, S13 = S1[np.ix_(i1, i1)], S1[np.ix_(i1, i3)]
     S31, S33 = S1[np.ix_(i3, i1)], S1[np.ix_(i3, i3)]
@@ -233,7 +281,7 @@ def root_dtn(prob: Problem, S_root):
     for k, (q, wgt) in enumerate(ghost_map(prob)):
         Bm[where[q], k] = -wgt
         Pm[k, where[q]] = 1.0
-    return (np.eye(4 * n) - Pm @ np.linalg.solve(S_root, Bm)) / h
+    return prob.datum_weights()[:, None] * (np.eye(4 * n) - Pm @ np.linalg.solve(S_root, Bm)) / h
 
 
 @dataclass
@@ -300,3 +348,97 @@ def direct_schur(prob: Problem, box: Box):
     """Plain definition of a box's Schur complement (eq. def_schur_nd applied to the
     whole box at once, no tree) -- used to pin every intermediate of the merge."""
     return leaf_schur(prob, box)
+
+
+# ----------------------------------------------------------------------------- body loads
+
+def _inject(nodes, cols):
+    """0/1 matrix placing load column c at the row of node cols[c] in `nodes`."""
+    where = {q: k for k, q in enumerate(nodes)}
+    E = np.zeros((len(nodes), len(cols)))
+    for c, q in enumerate(cols):
+        if q in where:
+            E[where[q], c] = 1.0
+    return E
+
+
+def leaf_load_map(prob: Problem, box: Box, body):
+    """Section 3.1 with a body load: eliminating u_i leaves S u_b = f_b - A_bi A_ii^{-1} f_i.
+    Returns (Lmap, cols): cols are the body nodes inside the box (in the order of `body`),
+    and Lmap (ring x len(cols)) takes their loads to that right-hand side."""
+    cols = [q for q in body if box.contains(q)]
+    Pb, Pi = box.ring(), box.interior()
+    E_b = _inject(Pb, cols)
+    if not Pi:
+        return E_b, cols
+    E_i = _inject(Pi, cols)
+    return E_b - prob.A_block(Pb, Pi) @ np.linalg.solve(prob.A_block(Pi, Pi), E_i), cols
+
+
+def merge_loads(prob: Problem, box1: Box, S1, L1, box2: Box, S2, L2, parent: Box):
+    """Section 3.2, the updated right-hand side of a merge:
+        [f1; f2] - [S13 A14; A23 S24] [S33 A34; A43 S44]^{-1} [f3; f4],
+    as a map of the children's loads: f1..f4 are the rows P1..P4 of the children's load
+    maps (child 1's columns first, then child 2's).  Rows in the parent's ring order."""
+    rp = parent.ring()
+    i1, i3, i2, i4, P1, P3, P2, P4 = partition_we(box1, box2, parent)
+    m1, m2 = L1.shape[1], L2.shape[1]
+
+    def two(L1rows, L2rows):
+        return np.vstack([np.hstack([L1rows, np.zeros((L1rows.shape[0], m2))]),
+                          np.hstack([np.zeros((L2rows.shape[0], m1)), L2rows])])
+
+    f12 = two(L1[i1], L2[i2])
+    f34 = two(L1[i3], L2[i4])
+    if f34.shape[0]:
+        A = prob.A_block
+        left = np.block([[S1[np.ix_(i1, i3)], A(P1, P4)], [A(P2, P3), S2[np.ix_(i2, i4)]]])
+        mid = np.block([[S1[np.ix_(i3, i3)], A(P3, P4)], [A(P4, P3), S2[np.ix_(i4, i4)]]])
+        f12 = f12 - left @ np.linalg.solve(mid, f34)
+    where = {q: k for k, q in enumerate(rp)}
+    perm = np.array([where[q] for q in P1 + P2])
+    out = np.empty_like(f12)
+    out[perm] = f12
+    return out
+
+
+def root_load_operator(prob: Problem, S_root, L_root):
+    """Section 6.3's second term: the root ring solves S_root u = B g + L_root f_hat, so the
+    ghost data take F = -D P S_root^{-1} L_root / h (D the datum weights)."""
+    n, h = prob.n, prob.h
+    rp = Box(0, 0, n, n).ring()
+    where = {q: k for k, q in enumerate(rp)}
+    Pm = np.zeros((4 * n, len(rp)))
+    for k, (q, _) in enumerate(ghost_map(prob)):
+        Pm[k, where[q]] = 1.0
+    return -prob.datum_weights()[:, None] * (Pm @ np.linalg.solve(S_root, L_root)) / h
+
+
+def build_loads(prob: Problem, leaf, body):
+    """Section 6.3: the two operators of v = T g + F f_hat for loads at the listed body
+    nodes ((i, j) pairs or flat indices i + n j; F's columns follow that order).  The tree,
+    leaf and merge steps are those of `build`; every box carries its load map beside S."""
+    n = prob.n
+    body = [tuple(divmod(int(k), n)[::-1]) if np.isscalar(k) else tuple(k) for k in body]
+    if len(set(body)) != len(body):
+        raise ValueError("body nodes must be distinct")
+    levels = quad_tree(n, leaf)
+    S, Lm, cols = {}, {}, {}
+    for box in levels[-1]:
+        S[box] = leaf_schur(prob, box)
+        Lm[box], cols[box] = leaf_load_map(prob, box, body)
+    for lev in range(len(levels) - 1, 0, -1):
+        for parent in levels[lev - 1]:
+            sw, se, nw, ne = parent.children()
+            south = Box(parent.x0, parent.y0, parent.a, sw.b)
+            north = Box(parent.x0, parent.y0 + sw.b, parent.a, nw.b)
+            for (b1, b2, half) in ((sw, se, south), (nw, ne, north), (south, north, parent)):
+                Lm[half] = merge_loads(prob, b1, S[b1], Lm[b1], b2, S[b2], Lm[b2], half)
+                cols[half] = cols[b1] + cols[b2]
+                S[half] = merge_two(prob, b1, S[b1], b2, S[b2], half)
+    root = levels[0][0]
+    T = root_dtn(prob, S[root])
+    Fr = root_load_operator(prob, S[root], Lm[root])
+    order = {q: c for c, q in enumerate(cols[root])}
+    F = Fr[:, [order[q] for q in body]]
+    return T, F

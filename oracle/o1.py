@@ -31,6 +31,13 @@ def _load():
         _lib.o1_dtn_apply.restype = ctypes.c_int
         _lib.o1_assemble_dense.argtypes = [ctypes.c_int, dp, dp, dp, dp]
         _lib.o1_assemble_dense.restype = ctypes.c_int
+        ip = ctypes.POINTER(ctypes.c_int)
+        _lib.o1_apply_loads.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_int, dp, ctypes.c_int, ip, dp, dp]
+        _lib.o1_apply_loads.restype = ctypes.c_int
+        _lib.o1_net_apply.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, dp, ctypes.c_int, ip, dp, dp]
+        _lib.o1_net_apply.restype = ctypes.c_int
+        _lib.o1_net_assemble_dense.argtypes = [ctypes.c_int, dp, dp, dp]
+        _lib.o1_net_assemble_dense.restype = ctypes.c_int
     return _lib
 
 
@@ -60,4 +67,71 @@ def assemble_dense(b, c, d, n):
     b, c, d = (np.ascontiguousarray(x, dtype=np.float64) for x in (b, c, d))
     A = np.zeros((n * n, n * n))
     lib.o1_assemble_dense(n, _p(b), _p(c), _p(d), _p(A))
+    return A
+
+
+def _loads(n, G, idx, Fl):
+    """Marshal (G, body-node indices, loads) for the two load-carrying entry points."""
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int32).reshape(-1))
+    m = idx.size
+    if G is None:
+        nvec = 1 if Fl is None else np.asarray(Fl).reshape(m, -1).shape[1]
+        G = np.zeros((4 * n, nvec))
+    G = np.asfortranarray(np.asarray(G, dtype=np.float64).reshape(4 * n, -1))
+    if Fl is None:
+        Fl = np.zeros((m, G.shape[1]))
+    Fl = np.asfortranarray(np.asarray(Fl, dtype=np.float64).reshape(m, G.shape[1]))
+    return G, idx, Fl
+
+
+def apply_loads(b, c, d, n, G, idx, Fl):
+    """Section 6.3: v = G g + F f_hat by one full solve per vector (G: 4n x B Dirichlet
+    data or None for zero; idx: body nodes, flat i + n j; Fl: len(idx) x B loads)."""
+    lib = _load()
+    b, c, d = (np.ascontiguousarray(x, dtype=np.float64) for x in (b, c, d))
+    G, idx, Fl = _loads(n, G, idx, Fl)
+    V = np.zeros_like(G, order="F")
+    rc = lib.o1_apply_loads(n, _p(b), _p(c), _p(d), G.shape[1], _p(G), idx.size,
+                            idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(Fl), _p(V))
+    if rc:
+        raise RuntimeError(f"o1_apply_loads failed: {rc}")
+    return np.ascontiguousarray(V)
+
+
+def load_matrix(b, c, d, n, idx):
+    """The 4n x len(idx) body-load operator F (columns = images of unit loads)."""
+    idx = np.asarray(idx).reshape(-1)
+    return apply_loads(b, c, d, n, None, idx, np.eye(idx.size))
+
+
+def net_apply(sx, sy, n, G, idx=(), Fl=None):
+    """The conductance network's datum (ghost currents / h) for Dirichlet data G and
+    optional body loads; sx, sy as in inputs.network_conductivities."""
+    lib = _load()
+    sx, sy = (np.ascontiguousarray(x, dtype=np.float64) for x in (sx, sy))
+    if sx.size != n * (n + 1) or sy.size != n * (n + 1):
+        raise ValueError("conductivity arrays must hold n (n + 1) links each")
+    G, idx, Fl = _loads(n, G, idx, Fl)
+    V = np.zeros_like(G, order="F")
+    rc = lib.o1_net_apply(n, _p(sx), _p(sy), G.shape[1], _p(G), idx.size,
+                          idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(Fl), _p(V))
+    if rc:
+        raise RuntimeError(f"o1_net_apply failed: {rc}")
+    return np.ascontiguousarray(V)
+
+
+def net_dtn_matrix(sx, sy, n):
+    return net_apply(sx, sy, n, np.eye(4 * n))
+
+
+def net_load_matrix(sx, sy, n, idx):
+    idx = np.asarray(idx).reshape(-1)
+    return net_apply(sx, sy, n, None, idx, np.eye(idx.size))
+
+
+def net_assemble_dense(sx, sy, n):
+    lib = _load()
+    sx, sy = (np.ascontiguousarray(x, dtype=np.float64) for x in (sx, sy))
+    A = np.zeros((n * n, n * n))
+    lib.o1_net_assemble_dense(n, _p(sx), _p(sy), _p(A))
     return A

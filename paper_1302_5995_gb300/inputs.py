@@ -189,6 +189,60 @@ def helmholtz_fields(n: int, k: float):
     return z, z.copy(), d
 
 
+# ----------------------------------------------------------------------------- networks and body loads
+
+def network_conductivities(n: int, lo: float, hi: float, seed: int):
+    """Random link conductivities of the square-grid network (the Random Laplacian
+    problems of Section 6.1): every link, including the 4n links from the grid to its
+    ghost nodes, gets a conductivity uniform on [lo, hi).
+
+    Returns (sx, sy).  sx has n rows of n + 1 x-links, flat index i + (n+1) j: the link
+    between (i-1, j) and (i, j) for i = 0..n (i = 0 and i = n reach the west and east
+    ghosts).  sy has n + 1 rows of n y-links, flat index i + n j: the link between
+    (i, j-1) and (i, j) for j = 0..n (j = 0 and j = n reach the south and north ghosts).
+    Draw order: sx, then sy.
+    """
+    rng = SplitMix64(seed)
+    sx = lo + (hi - lo) * rng.uniform(n * (n + 1))
+    sy = lo + (hi - lo) * rng.uniform((n + 1) * n)
+    return sx, sy
+
+
+def random_laplacian_1(n: int, seed: int = 21):
+    """Random Laplacian I: conductivities uniform on [1, 2)."""
+    return network_conductivities(n, 1.0, 2.0, seed)
+
+
+def random_laplacian_2(n: int, seed: int = 22):
+    """Random Laplacian II: conductivities uniform on [1, 1000)."""
+    return network_conductivities(n, 1.0, 1000.0, seed)
+
+
+def body_nodes(n: int, count: int, seed: int) -> np.ndarray:
+    """count distinct unknown nodes in a localized square window (Section 6.3 places the
+    loads in a small area): window edge w = min(n, max(4, ceil(2 sqrt(count)))), its
+    south-west corner uniform among the positions that keep it inside the grid, then
+    `count` distinct nodes of the window in the order of a random permutation (argsort
+    of uniforms).  Returns flat indices i + n j, in load-column order."""
+    if count > n * n:
+        raise ValueError("more body nodes than unknowns")
+    w = min(n, max(4, math.ceil(2.0 * math.sqrt(count))))
+    while w * w < count:
+        w += 1
+    rng = SplitMix64(seed)
+    u = rng.uniform(2)
+    x0 = int(u[0] * (n - w + 1))
+    y0 = int(u[1] * (n - w + 1))
+    order = np.argsort(rng.uniform(w * w), kind="stable")[:count]
+    return ((x0 + order % w) + n * (y0 + order // w)).astype(np.int64)
+
+
+def body_load_vectors(count: int, nvec: int, seed: int) -> np.ndarray:
+    """nvec i.i.d. N(0,1) load vectors on `count` body nodes, shape (count, nvec)."""
+    z = SplitMix64(seed).normal(count * nvec)
+    return z.reshape(nvec, count).T.copy()
+
+
 # ----------------------------------------------------------------------------- boundary data
 
 def harmonic_vectors(n: int) -> np.ndarray:
