@@ -240,7 +240,8 @@ int gm_info(gm_handle *h, gm_info_t *info);
  *                      baseline).  Uses the current device.
  *   gm_server_add    : takes ownership of h (freed on eviction or destroy) and returns
  *                      its id.  Least recently used operators not being served are
- *                      evicted to make room; GM_ENOMEM if it cannot fit.
+ *                      evicted to make room; GM_ENOMEM if it cannot fit.  On any error
+ *                      the caller keeps h.
  *   gm_server_submit : queue dudn = T g for `batch` vectors (4n x batch column-major,
  *                      host or device); returns at once.  g and dudn must stay valid
  *                      until the request completes.  GM_EINVAL for an unknown operator.
