@@ -60,6 +60,13 @@ bool is_device_ptr(const void *p) {
 // The library's stream-ordered memory pool on a device: it keeps freed workspace mapped
 // (release threshold unbounded), so a build does not map its few hundred MB of temporaries
 // anew after every synchronisation, as the device's default pool (threshold 0) would.
+// Result code of a failed allocation: GM_ENOMEM when the device is out of memory,
+// GM_ECUDA for any other runtime failure (no device, no driver, a sticky error).
+int alloc_error(cudaError_t e) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? GM_ENOMEM : GM_ECUDA;
+}
+
 cudaMemPool_t lib_pool() {
     static std::mutex mu;
     static std::map<int, cudaMemPool_t> pools;
@@ -100,10 +107,10 @@ struct DBuf {
         s = st;
         if (bytes == 0) bytes = 16;
         cudaMemPool_t pool = lib_pool();
-        if ((pool ? cudaMallocFromPoolAsync(&p, bytes, pool, st) : cudaMallocAsync(&p, bytes, st)) != cudaSuccess) {
-            cudaGetLastError();
+        const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, st) : cudaMallocAsync(&p, bytes, st);
+        if (e != cudaSuccess) {
             p = nullptr;
-            return GM_ENOMEM;
+            return alloc_error(e);
         }
         return GM_OK;
     }
@@ -177,10 +184,8 @@ std::map<PlanKey, std::shared_ptr<DevPlan>> g_plans;
 
 template <class T> int upload(T **dst, const std::vector<T> &v) {
     size_t bytes = v.size() * sizeof(T);
-    if (cudaMalloc((void **)dst, bytes ? bytes : 16) != cudaSuccess) {
-        cudaGetLastError();
-        return GM_ENOMEM;
-    }
+    const cudaError_t e = cudaMalloc((void **)dst, bytes ? bytes : 16);
+    if (e != cudaSuccess) return alloc_error(e);
     if (bytes && cudaMemcpy(*dst, v.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) return GM_ECUDA;
     return GM_OK;
 }
@@ -978,22 +983,22 @@ int gm_solve(gm_handle *h, const double *g, double *dudn, int batch, void *strea
     DBuf gbuf, vbuf;
     const double *dg = g;
     double *dv = dudn;
+    int rc;
     if (!gd) {
-        if (gbuf.alloc(bytes, s)) return GM_ENOMEM;
+        if ((rc = gbuf.alloc(bytes, s))) return rc;
         CK(cudaMemcpyAsync(gbuf.p, g, bytes, cudaMemcpyHostToDevice, s));
         dg = gbuf.as<double>();
     }
     if (!vd) {
-        if (vbuf.alloc(bytes, s)) return GM_ENOMEM;
+        if ((rc = vbuf.alloc(bytes, s))) return rc;
         dv = vbuf.as<double>();
     }
     if (h->hbs) {
-        const int rc = hbs_apply_dtn(*h->hbs, dg, dv, batch, s);
-        if (rc) return rc;
+        if ((rc = hbs_apply_dtn(*h->hbs, dg, dv, batch, s))) return rc;
     } else if (h->precision == GM_PREC_MIXED) {
         DBuf gdig, gex;
-        if (gdig.alloc((size_t)h->split * batch * mx_kpad(N) * 2, s)) return GM_ENOMEM;
-        if (gex.alloc((size_t)batch * sizeof(int), s)) return GM_ENOMEM;
+        if ((rc = gdig.alloc((size_t)h->split * batch * mx_kpad(N) * 2, s))) return rc;
+        if ((rc = gex.alloc((size_t)batch * sizeof(int), s))) return rc;
         CK(mx_apply(h->tdig, h->tex, dg, gdig.as<__nv_bfloat16>(), gex.as<int>(), dv, N, batch, h->split, s));
     } else {
         CK(launch_apply(h->T, dg, dv, N, batch, s));
