@@ -8,6 +8,8 @@ after which the right block of W holds M^{-1} Z.  Checked here in numpy (FP32 in
 FP64 elsewhere) on a merge's interface system from the oracle: with the refinement the
 result is accurate far beyond FP32; without it, it is not.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -33,9 +35,10 @@ def blocked_gj(M, Z, nb, refine=True):
     return W[:, m:]
 
 
-def interface_system(n=40, leaf=10):
+@functools.lru_cache(maxsize=None)
+def interface_system(n=40, leaf=10, seeds=(11, 12, 13)):
     """[M | Z] of the top vertical merge of an n x n convection problem (oracle O2)."""
-    b, c, d = inputs.convection_fields(n, seeds=(11, 12, 13))
+    b, c, d = inputs.convection_fields(n, seeds=seeds)
     prob = nd_dense.Problem(b, c, d, n)
     root = nd_dense.Box(0, 0, n, n)
     sw, se, nw, ne = root.children()
@@ -66,3 +69,15 @@ def test_blocked_gauss_jordan_with_refinement(nb):
     err = lambda Y: np.abs(Y - X).max() / np.abs(X).max()
     assert err(ok) < 1e-11
     assert err(bad) > 1e-9  # FP32 block inverses alone stay near FP32 accuracy
+
+
+@pytest.mark.parametrize("nb", [64, 128, 256])
+def test_larger_blocks_keep_the_accuracy(nb):
+    """The 128 x 128 workload's top merge (m = 252) swept with the block width of the
+    kernels (64) and wider ones: one refinement step reaches 1e-14 for each, and the FP32
+    block inverses alone stay near FP32 accuracy."""
+    M, Z = interface_system(n=128, leaf=16, seeds=(1, 2, 3))
+    X = np.linalg.solve(M, Z)
+    err = lambda Y: np.abs(Y - X).max() / np.abs(X).max()
+    assert err(blocked_gj(M, Z, nb)) < 1e-13
+    assert err(blocked_gj(M, Z, nb, refine=False)) > 1e-9
