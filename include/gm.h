@@ -227,6 +227,31 @@ int gm_get_schur(gm_handle *h, int x0, int y0, int a, int b, double *S_out);
  */
 int gm_solve_static(gm_handle *h, const double *g, double *dudn, int batch, void *stream);
 
+/*
+ * Body loads at fixed nodes (Section 6.3).  With a body load f_k added to the Section 6
+ * equation at each of nbody listed unknowns, the boundary data become
+ *     dudn = T g + F f_hat,   F: 4n x nbody,
+ * T the DtN matrix of gm_build and F the map from the loads to the same one-sided
+ * fluxes.  Every box carries, beside its Schur complement, a load map from the loads
+ * inside it to its ring's right-hand side (leaf: Section 3.1's f_b - A_bi A_ii^{-1} f_i;
+ * merge: Section 3.2's updated right-hand side, solved with the merge's interface
+ * system as extra columns); the root gives F.
+ *   gm_build_loads : body = nbody distinct flat indices i + n*j (a HOST array, read
+ *                    during the call); column c of F belongs to body[c].  b, c, d, n,
+ *                    leaf, opts as gm_build_ex.  FP64 only: GM_EUNSUPPORTED for a mixed
+ *                    precision or keep_levels request.  GM_EINVAL for an empty, repeated
+ *                    or out-of-grid list.  The handle also serves gm_solve (T g alone),
+ *                    gm_get_dtn and gm_info (resident_bytes counts T and F).
+ *   gm_solve_loads : dudn[:, v] = T g[:, v] + F f[:, v]; g, dudn 4n x batch, f nbody x
+ *                    batch, column-major, host or device; pointer rules as gm_solve.
+ *                    GM_EUNSUPPORTED for a handle built without loads.
+ *   gm_get_load_operator : copy F (4n x nbody, column-major) to F_out, host or device.
+ */
+int gm_build_loads(const gm_opts *opts, const double *b, const double *c, const double *d, int n, int leaf,
+                   const int *body, int nbody, gm_handle **out);
+int gm_solve_loads(gm_handle *h, const double *g, const double *f, double *dudn, int batch, void *stream);
+int gm_get_load_operator(gm_handle *h, double *F_out);
+
 int gm_info(gm_handle *h, gm_info_t *info);
 
 /*

@@ -77,6 +77,10 @@ SIGNATURES = {
     "gm_get_schur": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 4 + [ctypes.c_void_p]),
     "gm_solve_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                        ctypes.c_void_p]),
+    "gm_build_loads": (ctypes.c_int, [ctypes.POINTER(Opts)] + [ctypes.c_void_p] * 3
+                       + [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "gm_solve_loads": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int, ctypes.c_void_p]),
+    "gm_get_load_operator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gm_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Info)]),
     "gm_free": (None, [ctypes.c_void_p]),
     "gm_server_create": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
@@ -158,6 +162,7 @@ class DtN:
         self._h = handle
         self.n = n
         self.leaf = leaf
+        self.nbody = 0  # body loads of a build_loads handle
         self._keep = []
 
     def __del__(self):
@@ -217,6 +222,35 @@ class DtN:
         if rc:
             raise GmError(rc, "gm_get_schur")
         return out.T.copy()
+
+    def solve_loads(self, g, f, out=None, stream=None):
+        """dudn = T g + F f (Section 6.3) for g of shape (4n, B) and loads f of shape
+        (nbody, B), both stored column by column; needs a handle from build_loads."""
+        lib = load_library()
+        N = 4 * self.n
+        g = _check_f64(g, "g")
+        f = _check_f64(f, "f")
+        B = (g.numel() if hasattr(g, "numel") else g.size) // N
+        if out is None:
+            if hasattr(g, "data_ptr"):
+                import torch
+                out = torch.empty_like(g)
+            else:
+                import numpy as np
+                out = np.empty_like(g)
+        rc = lib.gm_solve_loads(self._h, _ptr(g), _ptr(f), _ptr(out), B, _stream_handle(stream))
+        if rc:
+            raise GmError(rc, "gm_solve_loads")
+        return out
+
+    def load_operator(self):
+        """The 4n x nbody load operator F of a build_loads handle (column c: body[c])."""
+        import numpy as np
+        F = np.empty((max(self.nbody, 1), 4 * self.n))
+        rc = load_library().gm_get_load_operator(self._h, _ptr(F))
+        if rc:
+            raise GmError(rc, "gm_get_load_operator")
+        return F[: self.nbody].T.copy()
 
     def info(self):
         inf = Info()
@@ -284,6 +318,26 @@ def build(b, c, d, n, leaf, tol=0.0, precision=PREC_FP64, keep_levels=False, str
     if rc:
         raise GmError(rc, "gm_build")
     return DtN(h, n, leaf)
+
+
+def build_loads(b, c, d, n, leaf, body, stream=None, panel_width=0):
+    """FP64 build of T and of the load operator F for body loads at the flat node indices
+    `body` (Section 6.3: dudn = T g + F f).  Returns a DtN handle with nbody set."""
+    import numpy as np
+    lib = load_library()
+    b = _check_f64(b, "b", n * n)
+    c = _check_f64(c, "c", n * n)
+    d = _check_f64(d, "d", n * n)
+    nodes = np.ascontiguousarray(np.asarray(body, dtype=np.int32).reshape(-1))
+    o = _opts(PREC_FP64, False, stream, panel_width, False, 0, PIVOT_AUTO)
+    h = ctypes.c_void_p()
+    rc = lib.gm_build_loads(ctypes.byref(o), _ptr(b), _ptr(c), _ptr(d), n, leaf, ctypes.c_void_p(nodes.ctypes.data),
+                            int(nodes.size), ctypes.byref(h))
+    if rc:
+        raise GmError(rc, "gm_build_loads")
+    op = DtN(h, n, leaf)
+    op.nbody = int(nodes.size)
+    return op
 
 
 class Server:

@@ -24,6 +24,7 @@
 #include "gm_internal.h"
 #include "hbs.h"
 #include "kernels.h"
+#include "loads.h"
 #include "mixed.h"
 
 using namespace gm;
@@ -316,6 +317,8 @@ struct gm_handle {
     bool kept_df32 = false;
     std::vector<void *> kept_bufs;
     gm::HbsRoot *hbs = nullptr;     // tol > 0: the root's HBS inverse (no dense T)
+    double *F = nullptr;            // body loads: the 4n x nbody load operator (Section 6.3)
+    int nbody = 0;
     gm_info_t info{};
 };
 
@@ -893,6 +896,7 @@ void gm_free(gm_handle *h) {
     cudaFree(h->Tdf);
     cudaFree(h->tdig);
     cudaFree(h->tex);
+    cudaFree(h->F);
     for (void *p : h->kept_bufs) cudaFree(p);
     if (h->hbs) {
         gm::hbs_free(*h->hbs);
@@ -1045,6 +1049,250 @@ int gm_get_schur(gm_handle *h, int x0, int y0, int a, int b, double *S_out) {
 int gm_info(gm_handle *h, gm_info_t *info) {
     if (!h || !info) return GM_EINVAL;
     *info = h->info;
+    return GM_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------------- body loads
+
+namespace {
+
+// The FP64 build with body loads (Section 6.3) of one problem: the plain build's leaves,
+// merges and root, each merge's interface system widened by its children's load columns,
+// the leaves' load maps from their own [A_ii | E_i] systems, and the root's load columns
+// beside [S_root | B].  Gives h->T and h->F.
+int run_build_loads(const gm_opts &o, int n, int leaf, const std::vector<int> &body, const double *db,
+                    const double *dc, const double *dd, gm_handle *h) {
+    cudaStream_t s = (cudaStream_t)o.stream;
+    int rc;
+    std::shared_ptr<DevPlan> dpp;
+    if ((rc = get_plan({{n, leaf}}, dpp))) return rc;
+    const DevPlan &dp = *dpp;
+    const Plan &P = dp.plan;
+    if (leaf_smem_bytes(dp.max_leaf_a, dp.max_leaf_b) > 220 * 1024) return GM_EUNSUPPORTED;
+    if (2 * (dp.max_leaf_a - 2) + 2 * (dp.max_leaf_b - 2) - 4 > 64) return GM_EUNSUPPORTED;
+    const int nb = o.panel_width > 0 ? o.panel_width : 16;
+    if (nb > GJ_MAX_NB) return GM_EINVAL;
+    LoadPlan lp;
+    if ((rc = build_load_plan(P, body, lp))) return rc;
+    h->plan = dpp;
+    h->L = P.L;
+    const RootDesc &R = P.roots[0];
+    const int r = R.r, nb4 = 4 * n, m = lp.nbody;
+    KTimer kt;
+
+    auto put = [&](DBuf &buf, const void *src, size_t bytes) -> int {
+        int e = buf.alloc(bytes, s);
+        if (e) return e;
+        if (bytes) CK(cudaMemcpyAsync(buf.p, src, bytes, cudaMemcpyHostToDevice, s));
+        return GM_OK;
+    };
+    DBuf stat;
+    Status hst{0, -1, 0x7ff0000000000000ull, 0, 0u};
+    if ((rc = put(stat, &hst, sizeof(Status)))) return rc;
+    Status *dst = stat.as<Status>();
+    DBuf arena, larena;
+    if ((rc = arena.alloc((size_t)P.arena_doubles * 8, s)) || (rc = larena.alloc((size_t)lp.arena * 8, s))) return rc;
+    double *A64 = arena.as<double>(), *LA = larena.as<double>();
+
+    // scratch of the dense sweeps: the leaves' systems, every stage, the root
+    const SysDesc root_sys{0, r, r + nb4 + m, 0, 0, 0, 0};
+    int max_nm = std::max<int>(1, (int)lp.leaf_sys.size()), piv_ld = std::max(r, lp.leaf_max_m);
+    int64_t max_u12 = std::max<int64_t>((int64_t)lp.leaf_sys.size() * nb * lp.leaf_max_ncol,
+                                        (int64_t)nb * root_sys.ncol);
+    for (size_t si = 0; si < dp.stages.size(); ++si) {
+        max_nm = std::max(max_nm, dp.stages[si].nm);
+        piv_ld = std::max(piv_ld, dp.stages[si].max_m);
+        max_u12 = std::max<int64_t>(max_u12, (int64_t)dp.stages[si].nm * nb * lp.stage_max_ncol[si]);
+    }
+    DBuf piv, u12;
+    if ((rc = piv.alloc((size_t)max_nm * piv_ld * sizeof(int), s)) || (rc = u12.alloc((size_t)max_u12 * 8, s)))
+        return rc;
+
+    // leaves: Schur complements, then the load maps of the leaves that hold body nodes
+    CK(launch_leaf(dp.d_leaves, P.leaves, dp.max_leaf_a, dp.max_leaf_b, db, dc, dd, A64, dst, 0, s, kt));
+    DBuf d_leaves, d_nodes, d_lsys, lws;
+    const int nl = (int)lp.leaves.size();
+    if ((rc = put(d_leaves, lp.leaves.data(), lp.leaves.size() * sizeof(LeafLoadDesc))) ||
+        (rc = put(d_nodes, lp.leaf_nodes.data(), lp.leaf_nodes.size() * sizeof(int))) ||
+        (rc = put(d_lsys, lp.leaf_sys.data(), lp.leaf_sys.size() * sizeof(SysDesc))) ||
+        (rc = lws.alloc((size_t)lp.leaf_ws * 8, s)))
+        return rc;
+    int64_t max_le = 0, max_rm = 0;
+    for (const LeafLoadDesc &d : lp.leaves) {
+        max_le = std::max<int64_t>(max_le, (int64_t)d.ni * (d.ni + d.m));
+        max_rm = std::max<int64_t>(max_rm, (int64_t)ring_size(d.a, d.b) * d.m);
+    }
+    if (!lp.leaf_sys.empty()) {
+        CK(launch_leaf_load_assemble(d_leaves.as<LeafLoadDesc>(), nl, d_nodes.as<int>(), lws.as<double>(),
+                                     (int)max_le, db, dc, dd, s));
+        CK(launch_gj_sweep(d_lsys.as<SysDesc>(), lp.leaf_sys, lp.leaf_max_m, lp.leaf_max_ncol, lws.as<double>(), nb,
+                           piv.as<int>(), piv_ld, u12.as<double>(), (int64_t)nb * lp.leaf_max_ncol, dst, 0, s, kt));
+    }
+    CK(launch_leaf_load_finalize(d_leaves.as<LeafLoadDesc>(), nl, d_nodes.as<int>(), lws.as<double>(), LA,
+                                 (int)max_rm, db, dc, dd, s));
+
+    // merge stages: [M | Z | Z_L] swept together; S and the load map of every parent
+    for (size_t si = 0; si < dp.stages.size(); ++si) {
+        const DevStage &ds = dp.stages[si];
+        if (ds.nm == 0) continue;
+        const std::vector<MergeDesc> &mc = lp.merges[si];
+        DBuf d_mc, d_ml, d_sys, ws;
+        if ((rc = put(d_mc, mc.data(), mc.size() * sizeof(MergeDesc))) ||
+            (rc = put(d_ml, lp.stages[si].data(), lp.stages[si].size() * sizeof(MergeLoadDesc))) ||
+            (rc = put(d_sys, lp.sys[si].data(), lp.sys[si].size() * sizeof(SysDesc))) ||
+            (rc = ws.alloc((size_t)lp.stage_ws[si] * 8, s)))
+            return rc;
+        int64_t max_e = 0, max_l = 0;
+        for (size_t k = 0; k < mc.size(); ++k) {
+            const int64_t mm = 2 * mc[k].sp, mL = lp.stages[si][k].m1 + lp.stages[si][k].m2;
+            max_e = std::max(max_e, mm * (mm + mc[k].rp));
+            max_l = std::max(max_l, std::max(mm, (int64_t)mc[k].rp) * mL);
+        }
+        CK(launch_merge_assemble(d_mc.as<MergeDesc>(), ds.nm, ds.d_tab, A64, ws.as<double>(), max_e, db, dc, dd, 0,
+                                 s, kt));
+        CK(launch_merge_load_assemble(d_mc.as<MergeDesc>(), d_ml.as<MergeLoadDesc>(), ds.nm, ds.d_tab, LA,
+                                      ws.as<double>(), max_l, s));
+        CK(launch_gj_sweep(d_sys.as<SysDesc>(), lp.sys[si], ds.max_m, lp.stage_max_ncol[si], ws.as<double>(), nb,
+                           piv.as<int>(), piv_ld, u12.as<double>(), (int64_t)nb * lp.stage_max_ncol[si], dst,
+                           (int)si + 1, s, kt));
+        CK(launch_merge_update(d_mc.as<MergeDesc>(), mc, ds.d_tab, A64, ws.as<double>(), A64, ds.max_rp, db, dc, dd,
+                               0, s, kt));
+        CK(launch_merge_load_update(d_mc.as<MergeDesc>(), d_ml.as<MergeLoadDesc>(), ds.nm, ds.d_tab, A64,
+                                    ws.as<double>(), LA, max_l, s));
+    }
+
+    // root: [S_root | B | L_root] -> [* | S^{-1} B | S^{-1} L_root], then T and F
+    DBuf rws, d_rsys, d_order;
+    const std::vector<SysDesc> rsys{root_sys};
+    if ((rc = rws.alloc((size_t)r * root_sys.ncol * 8, s)) || (rc = put(d_rsys, rsys.data(), sizeof(SysDesc))) ||
+        (rc = put(d_order, lp.root_order.data(), lp.root_order.size() * sizeof(int))))
+        return rc;
+    double *W = rws.as<double>();
+    CK(launch_root_assemble(A64 + R.off, r, n, W, db, dc, dd, s, kt));
+    CK(cudaMemcpyAsync(W + (int64_t)r * (r + nb4), LA + lp.root_l, (size_t)r * m * 8, cudaMemcpyDeviceToDevice, s));
+    CK(launch_gj_sweep(d_rsys.as<SysDesc>(), rsys, r, root_sys.ncol, W, nb, piv.as<int>(), piv_ld, u12.as<double>(),
+                       (int64_t)nb * root_sys.ncol, dst, (int)dp.stages.size() + 1, s, kt));
+    cudaError_t e = cudaMalloc(&h->T, (size_t)nb4 * nb4 * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&h->F, (size_t)nb4 * m * 8);
+    if (e != cudaSuccess) return alloc_error(e);
+    CK(launch_root_finalize(W, r, n, h->T, s, kt));
+    CK(launch_load_finalize(W + (int64_t)r * (r + nb4), r, n, m, d_order.as<int>(), h->F, s));
+    h->nbody = m;
+
+    CK(cudaMemcpyAsync(&hst, stat.p, sizeof(Status), cudaMemcpyDeviceToHost, s));
+    for (DBuf *b : {&rws, &d_rsys, &d_order, &lws, &d_leaves, &d_nodes, &d_lsys, &piv, &u12, &arena, &larena, &stat})
+        b->release();
+    CK(cudaStreamSynchronize(s));
+    gm_info_t info{};
+    for (int f = 0; f < GM_K_NFAM; ++f) {
+        info.kernel_launches[f] = kt.launches[f];
+        info.kernel_flops[f] = kt.flops[f];
+        info.launches += kt.launches[f];
+    }
+    double mp;
+    memcpy(&mp, &hst.min_piv, 8);
+    info.n = n;
+    info.leaf = leaf;
+    info.levels = P.L;
+    info.precision = GM_PREC_FP64;
+    info.pivoting = GM_PIVOT_PARTIAL;
+    info.dtn_bytes = (long long)nb4 * nb4 * 8;
+    info.resident_bytes = info.dtn_bytes + (long long)nb4 * m * 8;
+    info.peak_workspace = (int64_t)(P.arena_doubles + lp.arena + (int64_t)r * root_sys.ncol) * 8;
+    info.min_pivot_ratio = mp / (4.0 * (n + 1.0) * (n + 1.0));
+    info.bad_stage = hst.code ? hst.where : -1;
+    h->info = info;
+    return hst.code;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gm_build_loads(const gm_opts *opts, const double *b, const double *c, const double *d, int n, int leaf,
+                   const int *body, int nbody, gm_handle **out) {
+    if (!out) return GM_EINVAL;
+    *out = nullptr;
+    if (!b || !c || !d || n < 2 || leaf < 4 || !body || nbody < 1 || (int64_t)nbody > (int64_t)n * n)
+        return GM_EINVAL;
+    gm_opts o;
+    int rc = check_opts(opts, o);
+    if (rc) return rc;
+    if (o.precision != GM_PREC_FP64 || o.keep_levels) return GM_EUNSUPPORTED;
+    const std::vector<int> nodes(body, body + nbody);
+    const int64_t N2 = (int64_t)n * n;
+    std::vector<int> sorted(nodes);
+    std::sort(sorted.begin(), sorted.end());
+    if (sorted.front() < 0 || sorted.back() >= N2 || std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+        return GM_EINVAL;
+    cudaStream_t s = (cudaStream_t)o.stream;
+    DBuf coef;
+    const double *db = b, *dc = c, *dd = d;
+    if (!is_device_ptr(b) || !is_device_ptr(c) || !is_device_ptr(d)) {
+        if ((rc = coef.alloc(3 * (size_t)N2 * sizeof(double), s))) return rc;
+        double *base = coef.as<double>();
+        CK(cudaMemcpyAsync(base, b, N2 * 8, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(base + N2, c, N2 * 8, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(base + 2 * N2, d, N2 * 8, cudaMemcpyDefault, s));
+        db = base;
+        dc = base + N2;
+        dd = base + 2 * N2;
+    }
+    gm_handle *h = new_handle({n, leaf}, GM_PREC_FP64);
+    rc = run_build_loads(o, n, leaf, nodes, db, dc, dd, h);
+    if (rc) {
+        gm_free(h);
+        return rc;
+    }
+    *out = h;
+    return GM_OK;
+}
+
+int gm_solve_loads(gm_handle *h, const double *g, const double *f, double *dudn, int batch, void *stream) {
+    if (!h || batch < 0) return GM_EINVAL;
+    if (!h->F) return GM_EUNSUPPORTED;
+    if (batch == 0) return GM_OK;
+    if (!g || !f || !dudn) return GM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int N = 4 * h->n, m = h->nbody;
+    const size_t gbytes = (size_t)N * batch * 8, fbytes = (size_t)m * batch * 8;
+    DBuf gbuf, fbuf, vbuf;
+    const double *dg = g, *df = f;
+    double *dv = dudn;
+    int rc;
+    if (!is_device_ptr(g)) {
+        if ((rc = gbuf.alloc(gbytes, s))) return rc;
+        CK(cudaMemcpyAsync(gbuf.p, g, gbytes, cudaMemcpyHostToDevice, s));
+        dg = gbuf.as<double>();
+    }
+    if (!is_device_ptr(f)) {
+        if ((rc = fbuf.alloc(fbytes, s))) return rc;
+        CK(cudaMemcpyAsync(fbuf.p, f, fbytes, cudaMemcpyHostToDevice, s));
+        df = fbuf.as<double>();
+    }
+    const bool vd = is_device_ptr(dudn);
+    if (!vd) {
+        if ((rc = vbuf.alloc(gbytes, s))) return rc;
+        dv = vbuf.as<double>();
+    }
+    CK(launch_apply(h->T, dg, dv, N, batch, s));
+    CK(launch_apply_add(h->F, df, dv, N, m, batch, s));
+    if (!vd) {
+        CK(cudaMemcpyAsync(dudn, dv, gbytes, cudaMemcpyDeviceToHost, s));
+        gbuf.release();
+        fbuf.release();
+        vbuf.release();
+        CK(cudaStreamSynchronize(s));
+    }
+    return GM_OK;
+}
+
+int gm_get_load_operator(gm_handle *h, double *F_out) {
+    if (!h || !F_out) return GM_EINVAL;
+    if (!h->F) return GM_EUNSUPPORTED;
+    CK(cudaMemcpy(F_out, h->F, (size_t)4 * h->n * h->nbody * 8, cudaMemcpyDefault));
     return GM_OK;
 }
 

@@ -111,3 +111,32 @@ def test_valid_build_without_a_gpu_fails_loudly(lib):
     assert _build_ex(lib, None, *_fields(8), 8, 4, 0.0) == gm.GM_ECUDA
     with pytest.raises(gm.GmError):
         gm.build(*_fields(8), 8, 4)
+
+
+def test_load_build_rejects_bad_arguments(lib):
+    n = 8
+    b, c, d = _fields(n)
+    body = np.array([3, 10, 20], dtype=np.int32)
+    h = ctypes.c_void_p()
+
+    def call(opts=None, nodes=body, count=None, nn=n, leaf=4):
+        return lib.gm_build_loads(ctypes.byref(opts) if opts is not None else None, b.ctypes.data, c.ctypes.data,
+                                  d.ctypes.data, nn, leaf, nodes.ctypes.data if nodes is not None else None,
+                                  len(nodes) if count is None else count, ctypes.byref(h))
+    assert call(nodes=None, count=3) == gm.GM_EINVAL
+    assert call(count=0) == gm.GM_EINVAL
+    assert call(nodes=np.array([3, 64], dtype=np.int32)) == gm.GM_EINVAL  # outside the 8 x 8 grid
+    assert call(nodes=np.array([-1], dtype=np.int32)) == gm.GM_EINVAL
+    assert call(nodes=np.array([5, 9, 5], dtype=np.int32)) == gm.GM_EINVAL  # repeated
+    assert call(leaf=3) == gm.GM_EINVAL
+    o = gm.Opts()
+    lib.gm_opts_default(ctypes.byref(o))
+    o.precision = gm.PREC_MIXED
+    assert call(opts=o) == gm.GM_EUNSUPPORTED  # FP64 only
+    lib.gm_opts_default(ctypes.byref(o))
+    o.keep_levels = 1
+    assert call(opts=o) == gm.GM_EUNSUPPORTED
+    assert h.value is None
+    x = np.zeros(64)
+    assert lib.gm_solve_loads(None, x.ctypes.data, x.ctypes.data, x.ctypes.data, 1, None) == gm.GM_EINVAL
+    assert lib.gm_get_load_operator(None, x.ctypes.data) == gm.GM_EINVAL

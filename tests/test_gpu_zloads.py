@@ -1,0 +1,81 @@
+"""Body loads on the GPU (Section 6.3: dudn = T g + F f_hat), through the C ABI, against
+the oracle: F element by element against O1's one-solve-per-load definition on ragged
+trees with loads on the outer ring, the merge interfaces and leaf rings; T unchanged by
+the loads; the combined solve with host and device buffers; and at 512 x 512 with 1000
+loads (the paper's largest N_body) the conservation and maximum-principle properties of
+a Laplace problem, which hold at any size.  (File named to run after the core parity
+tests.)"""
+import numpy as np
+import pytest
+
+import paper_1302_5995_gb300 as gm
+from oracle import o1
+from paper_1302_5995_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def placed_loads(n, count, seed):
+    body = [int(g) for g in inputs.body_nodes(n, count, seed)]
+    for g in (0, n - 1, (n // 2) * n + 3, (n // 2 - 1) * n + n // 2, n * n - 1):
+        if g not in body:
+            body.append(g)
+    return np.array(body, dtype=np.int32)
+
+
+@pytest.mark.parametrize("n,leaf,count", [(23, 6, 12), (37, 5, 30), (64, 16, 100)])
+def test_load_operator_matches_o1(n, leaf, count):
+    b, c, d = inputs.convection_fields(n, seeds=(91, 92, 93))
+    body = placed_loads(n, count, n)
+    op = gm.build_loads(b, c, d, n, leaf, body)
+    F = op.load_operator()
+    assert F.shape == (4 * n, body.size)
+    assert rel(F, o1.load_matrix(b, c, d, n, body)) < 1e-10
+    T_plain = gm.build(b, c, d, n, leaf).dtn()
+    assert rel(op.dtn(), T_plain) < 1e-13
+    info = op.info()
+    assert info["resident_bytes"] == (16 * n * n + 4 * n * body.size) * 8
+
+
+def test_solve_with_loads_host_and_device():
+    torch = pytest.importorskip("torch")
+    n, leaf = 48, 8
+    b, c, d = inputs.convection_fields(n, seeds=(94, 95, 96))
+    body = placed_loads(n, 40, 7)
+    op = gm.build_loads(b, c, d, n, leaf, body)
+    G = inputs.gaussian_vectors(n, 5, 8)
+    Fl = inputs.body_load_vectors(body.size, 5, 9)
+    ref = o1.apply_loads(b, c, d, n, G, body, Fl)
+    g_cols = np.ascontiguousarray(G.T)   # vector j contiguous
+    f_cols = np.ascontiguousarray(Fl.T)
+    host = op.solve_loads(g_cols, f_cols).T
+    assert rel(host, ref) < 1e-10
+    dev = op.solve_loads(torch.from_numpy(g_cols).cuda(), torch.from_numpy(f_cols).cuda())
+    torch.cuda.synchronize()
+    assert rel(dev.cpu().numpy().T, ref) < 1e-10
+    # the plain solve of the same handle is the T g term alone
+    assert rel(op.solve(g_cols).T, o1.dtn_apply(b, c, d, n, G)) < 1e-10
+
+
+def test_load_operator_at_512_conserves_and_stays_in_bounds():
+    n, leaf = 512, 16
+    h = 1.0 / (n + 1)
+    b, c, d = inputs.laplace_fields(n)
+    body = inputs.body_nodes(n, 1000, 11).astype(np.int32)
+    F = gm.build_loads(b, c, d, n, leaf, body).load_operator()
+    np.testing.assert_allclose(F.sum(axis=0), -h, rtol=1e-9)  # every load leaves by the boundary
+    # F = -h times a harmonic measure, which is positive everywhere in the square
+    assert F.max() < 0.0 and F.min() >= -h * (1 + 1e-9)
+
+
+def test_plain_handle_has_no_load_operator():
+    n = 16
+    b, c, d = inputs.laplace_fields(n)
+    op = gm.build(b, c, d, n, 8)
+    with pytest.raises(gm.GmError) as e:
+        op.load_operator()
+    assert e.value.code == gm.GM_EUNSUPPORTED
