@@ -27,7 +27,7 @@ def placed_loads(n, count, seed):
     return np.array(body, dtype=np.int32)
 
 
-@pytest.mark.parametrize("n,leaf,count", [(23, 6, 12), (37, 5, 30), (64, 16, 100)])
+@pytest.mark.parametrize("n,leaf,count", [(9, 4, 6), (23, 6, 12), (37, 5, 30), (64, 16, 100)])
 def test_load_operator_matches_o1(n, leaf, count):
     b, c, d = inputs.convection_fields(n, seeds=(91, 92, 93))
     body = placed_loads(n, count, n)

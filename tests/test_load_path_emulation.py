@@ -212,7 +212,7 @@ def emulate_F(prob, n, leaf, body, plan, lp):
     return F.a.reshape((m, nb4)).T
 
 
-@pytest.mark.parametrize("n,leaf,count,seed", [(23, 6, 12, 3), (30, 8, 20, 4)])
+@pytest.mark.parametrize("n,leaf,count,seed", [(9, 4, 6, 1), (23, 6, 12, 3), (30, 8, 20, 4)])
 def test_emulated_load_path_gives_the_oracle_F(shim, n, leaf, count, seed):
     b, c, d = inputs.convection_fields(n, seeds=(91, 92, 93))
     prob = nd.Problem(b, c, d, n)
