@@ -252,6 +252,24 @@ int gm_build_loads(const gm_opts *opts, const double *b, const double *c, const 
 int gm_solve_loads(gm_handle *h, const double *g, const double *f, double *dudn, int batch, void *stream);
 int gm_get_load_operator(gm_handle *h, double *F_out);
 
+/*
+ * Conductance networks (Section 6.1, Random Laplacian I and II): the square grid whose
+ * links carry conductivities sigma, each node's equation
+ *     (1/h^2) sum over its four links of sigma_l (u_k - u_l) = f_k
+ * (scaled like the five-point Laplacian: unit conductivities give the Laplace problem),
+ * and the datum at ghost k the current sigma_k (g_k - u_k')/h through its link, so that T
+ * is the network's symmetric response matrix with T 1 = 0.
+ *   sx : n rows of n + 1 x-links, sx[i + (n+1) j] joins (i-1, j) and (i, j), i = 0..n
+ *        (i = 0 and i = n reach the west and east ghosts);
+ *   sy : n + 1 rows of n y-links, sy[i + n j] joins (i, j-1) and (i, j), j = 0..n;
+ *        both host or device, read during the call.
+ *   body, nbody : optional body loads (nbody = 0: none) as in gm_build_loads; the handle
+ *        then also serves gm_solve_loads and gm_get_load_operator.
+ * FP64 only (GM_EUNSUPPORTED for mixed precision or keep_levels); tol-free (dense T).
+ */
+int gm_build_net(const gm_opts *opts, const double *sx, const double *sy, int n, int leaf, const int *body,
+                 int nbody, gm_handle **out);
+
 int gm_info(gm_handle *h, gm_info_t *info);
 
 /*

@@ -26,6 +26,7 @@
 #include "kernels.h"
 #include "loads.h"
 #include "mixed.h"
+#include "network.h"
 
 using namespace gm;
 
@@ -1293,6 +1294,70 @@ int gm_get_load_operator(gm_handle *h, double *F_out) {
     if (!h || !F_out) return GM_EINVAL;
     if (!h->F) return GM_EUNSUPPORTED;
     CK(cudaMemcpy(F_out, h->F, (size_t)4 * h->n * h->nbody * 8, cudaMemcpyDefault));
+    return GM_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------------- networks
+
+extern "C" {
+
+int gm_build_net(const gm_opts *opts, const double *sx, const double *sy, int n, int leaf, const int *body,
+                 int nbody, gm_handle **out) {
+    if (!out) return GM_EINVAL;
+    *out = nullptr;
+    if (!sx || !sy || n < 2 || leaf < 4 || nbody < 0 || (nbody > 0 && !body) || (int64_t)nbody > (int64_t)n * n)
+        return GM_EINVAL;
+    gm_opts o;
+    int rc = check_opts(opts, o);
+    if (rc) return rc;
+    if (o.precision != GM_PREC_FP64 || o.keep_levels) return GM_EUNSUPPORTED;
+    std::vector<int> nodes(body, body + nbody);
+    if (nbody > 0) {
+        std::vector<int> sorted(nodes);
+        std::sort(sorted.begin(), sorted.end());
+        if (sorted.front() < 0 || sorted.back() >= (int64_t)n * n ||
+            std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+            return GM_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)o.stream;
+    const size_t L = (size_t)n * (n + 1);
+    DBuf links, wts, sig;
+    const double *dsx = sx, *dsy = sy;
+    if (!is_device_ptr(sx) || !is_device_ptr(sy)) {
+        if ((rc = links.alloc(2 * L * sizeof(double), s))) return rc;
+        CK(cudaMemcpyAsync(links.p, sx, L * 8, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(links.as<double>() + L, sy, L * 8, cudaMemcpyDefault, s));
+        dsx = links.as<double>();
+        dsy = dsx + L;
+    }
+    if ((rc = wts.alloc((size_t)5 * n * n * sizeof(double), s)) || (rc = sig.alloc((size_t)4 * n * sizeof(double), s)))
+        return rc;
+    CK(launch_net_weights(dsx, dsy, n, wts.as<double>(), sig.as<double>(), s));
+    // the FP64 build on the weight table (a null c pointer selects it)
+    const double *W = wts.as<double>();
+    gm_handle *h = nullptr;
+    if (nbody == 0) {
+        std::vector<gm_handle *> H;
+        if ((rc = build_with_fallback(o, 0.0, {{n, leaf}}, W, nullptr, W, H))) return rc;
+        h = H[0];
+    } else {
+        h = new_handle({n, leaf}, GM_PREC_FP64);
+        if ((rc = run_build_loads(o, n, leaf, nodes, W, nullptr, W, h))) {
+            gm_free(h);
+            return rc;
+        }
+    }
+    // the datum at ghost k is the current through its link: rows of T and F times sigma_k
+    cudaError_t e = launch_scale_rows(h->T, 4 * n, 4 * n, sig.as<double>(), s);
+    if (e == cudaSuccess && h->F) e = launch_scale_rows(h->F, 4 * n, nbody, sig.as<double>(), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        gm_free(h);
+        return cuda_fail(e, "network datum weights", __LINE__);
+    }
+    *out = h;
     return GM_OK;
 }
 

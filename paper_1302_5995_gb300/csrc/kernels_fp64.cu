@@ -22,8 +22,11 @@ namespace gm {
 // ----------------------------------------------------------------------------- stencil
 
 // Weight of the equation at global node g on its neighbour in direction dir (Section 6).
+// With c == nullptr, b is a table of five weights per node (centre, E, W, N, S; the
+// conductance networks of Section 6.1).
 __device__ __forceinline__ double stencil_w(const double *__restrict__ b, const double *__restrict__ c,
                                             const double *__restrict__ d, double ih, int g, int dir) {
+    if (!c) return b[5 * (int64_t)g + dir];
     // ih = 1/h = n+1 exactly: no FP64 division (a long instruction sequence on GB300)
     const double ih2 = ih * ih;
     switch (dir) {

@@ -15,9 +15,11 @@ namespace gm {
 namespace {
 
 // Weight of the equation at global node g on its neighbour in direction dir (the
-// Section 6 stencil, as the FP64 kernels evaluate it: ih = 1/h = n + 1 exactly).
+// Section 6 stencil, as the FP64 kernels evaluate it: ih = 1/h = n + 1 exactly; with
+// c == nullptr, b is a table of five weights per node, as for a conductance network).
 __device__ __forceinline__ double ld_stencil(const double *__restrict__ b, const double *__restrict__ c,
                                              const double *__restrict__ d, double ih, int g, int dir) {
+    if (!c) return b[5 * (int64_t)g + dir];
     const double ih2 = ih * ih;
     switch (dir) {
     case DIR_C: return 4.0 * ih2 + d[g];

@@ -1,10 +1,12 @@
-"""Body loads on the GPU (Section 6.3: dudn = T g + F f_hat), through the C ABI, against
-the oracle: F element by element against O1's one-solve-per-load definition on ragged
+"""Body loads (Section 6.3: dudn = T g + F f_hat) and conductance networks (Section 6.1,
+Random Laplacian I and II) on the GPU, through the C ABI, against the oracle.  Loads: F element by element against O1's one-solve-per-load definition on ragged
 trees with loads on the outer ring, the merge interfaces and leaf rings; T unchanged by
 the loads; the combined solve with host and device buffers; and at 512 x 512 with 1000
 loads (the paper's largest N_body) the conservation and maximum-principle properties of
-a Laplace problem, which hold at any size.  (File named to run after the core parity
-tests.)"""
+a Laplace problem, which hold at any size.  Networks: T and F against O1's network
+solve, unit conductivities against the Laplace build, and the paper's body-load workload
+(Random Laplacian I, 512 x 512, 1000 loads) against symmetry, T 1 = 0 and conservation.
+(File named to run after the core parity tests.)"""
 import numpy as np
 import pytest
 
@@ -79,3 +81,38 @@ def test_plain_handle_has_no_load_operator():
     with pytest.raises(gm.GmError) as e:
         op.load_operator()
     assert e.value.code == gm.GM_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("make", [inputs.random_laplacian_1, inputs.random_laplacian_2])
+@pytest.mark.parametrize("n,leaf", [(23, 6), (40, 8)])
+def test_network_dtn_and_loads_match_o1(make, n, leaf):
+    sx, sy = make(n)
+    T = gm.build_network(sx, sy, n, leaf).dtn()
+    T_ref = o1.net_dtn_matrix(sx, sy, n)
+    assert rel(T, T_ref) < 1e-10
+    body = placed_loads(n, 10, n + 1)
+    op = gm.build_network(sx, sy, n, leaf, body)
+    assert rel(op.load_operator(), o1.net_load_matrix(sx, sy, n, body)) < 1e-10
+    assert rel(op.dtn(), T_ref) < 1e-10
+
+
+def test_unit_network_is_the_laplace_build():
+    n, leaf = 32, 8
+    ones = np.ones(n * (n + 1))
+    T_net = gm.build_network(ones, ones, n, leaf).dtn()
+    T_lap = gm.build(*inputs.laplace_fields(n), n, leaf).dtn()
+    assert rel(T_net, T_lap) < 1e-13
+
+
+def test_random_laplacian_512_with_1000_loads():
+    n, leaf = 512, 16
+    h = 1.0 / (n + 1)
+    sx, sy = inputs.random_laplacian_1(n)
+    body = inputs.body_nodes(n, 1000, 12).astype(np.int32)
+    op = gm.build_network(sx, sy, n, leaf, body)
+    T, F = op.dtn(), op.load_operator()
+    scale = np.abs(T).max()
+    assert np.abs(T - T.T).max() < 1e-10 * scale  # reciprocity of the network
+    assert np.abs(T.sum(axis=1)).max() < 1e-10 * scale  # constants carry no current
+    np.testing.assert_allclose(F.sum(axis=0), -h, rtol=1e-9)
+    assert F.max() < 0.0 and F.min() >= -h * (1 + 1e-9)

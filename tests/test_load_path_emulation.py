@@ -78,15 +78,14 @@ class Buf:
 
 def emulate_F(prob, n, leaf, body, plan, lp):
     w = lambda g, d: prob.w[d][g // n, g % n]  # the stencil weight of equation g towards d
-    res_S = nd.build(*prob.fields, n, leaf, keep=True).schur
-    A = Buf(plan["arena"])
+    A = Buf(plan["arena"])  # every box's Schur complement, by its plain definition
     for l in plan["leaves"]:
         bx = nd.Box(l["x0"], l["y0"], l["a"], l["b"])
         r = len(bx.ring())
-        A.block(l["off"], r, r)[:] = res_S[bx]
+        A.block(l["off"], r, r)[:] = nd.direct_schur(prob, bx)
     for st in plan["stages"]:
         for m in st["merges"]:
-            A.block(m["out"], m["rp"], m["rp"])[:] = res_S[m["par"]]
+            A.block(m["out"], m["rp"], m["rp"])[:] = nd.direct_schur(prob, m["par"])
     LA = Buf(lp["arena"])
     # leaves: k_leaf_load_assemble, the sweep, k_leaf_load_finalize
     lws = Buf(lp["leaf_ws"])
@@ -216,7 +215,6 @@ def emulate_F(prob, n, leaf, body, plan, lp):
 def test_emulated_load_path_gives_the_oracle_F(shim, n, leaf, count, seed):
     b, c, d = inputs.convection_fields(n, seeds=(91, 92, 93))
     prob = nd.Problem(b, c, d, n)
-    prob.fields = (b, c, d)
     body = [int(g) for g in inputs.body_nodes(n, count, seed)]
     for g in (0, n - 1, (n // 2) * n + 3, (n // 2 - 1) * n + n // 2, n * n - 1):  # ring, interfaces, corner
         if g not in body:
@@ -227,4 +225,43 @@ def test_emulated_load_path_gives_the_oracle_F(shim, n, leaf, count, seed):
     F = emulate_F(prob, n, leaf, body, plan, lp)
     assert np.isfinite(F).all()
     F_ref = o1.load_matrix(b, c, d, n, body)
+    assert np.abs(F - F_ref).max() / np.abs(F_ref).max() < 1e-10
+
+
+def emulate_net_weights(sx, sy, n):
+    """k_net_weights (csrc/network.cu), index for index: the weight table W (5 per node)
+    and the ghosts' link conductivities."""
+    ih2 = (n + 1.0) ** 2
+    Wt, sig = Buf(5 * n * n), Buf(4 * n)
+    for g in range(n * n + 4 * n):
+        if g < n * n:
+            i, j = g % n, g // n
+            e, w_ = sx[(i + 1) + (n + 1) * j], sx[i + (n + 1) * j]
+            no, so = sy[i + n * (j + 1)], sy[i + n * j]
+            Wt[5 * g + C] = (e + w_ + no + so) * ih2
+            Wt[5 * g + E] = -e * ih2
+            Wt[5 * g + W] = -w_ * ih2
+            Wt[5 * g + N] = -no * ih2
+            Wt[5 * g + S] = -so * ih2
+        else:
+            k = g - n * n
+            side, t = divmod(k, n)
+            sig[k] = [sy[t], sx[n + (n + 1) * t], sy[(n - 1 - t) + n * n], sx[(n + 1) * (n - 1 - t)]][side]
+    return Wt.a, sig.a
+
+
+@pytest.mark.parametrize("make", [inputs.random_laplacian_1, inputs.random_laplacian_2])
+def test_emulated_network_path_gives_the_oracle_F(shim, make):
+    n, leaf = 23, 6
+    sx, sy = make(n)
+    prob = nd.Problem.network(sx, sy, n)
+    Wt, sig = emulate_net_weights(sx, sy, n)
+    for dr in (C, E, W, N, S):  # the table the FP64 kernels read is the oracle's stencil
+        np.testing.assert_array_equal(Wt[dr::5], prob.w[dr].reshape(-1))
+    np.testing.assert_array_equal(sig, prob.datum_weights())
+    body = [int(g) for g in inputs.body_nodes(n, 10, 6)] + [0, n * n - 1]
+    plan = plain_plan(shim, n, leaf)
+    lp = load_dump(shim, n, leaf, body)
+    F = emulate_F(prob, n, leaf, body, plan, lp) * sig[:, None]  # k_scale_rows
+    F_ref = o1.net_load_matrix(sx, sy, n, body)
     assert np.abs(F - F_ref).max() / np.abs(F_ref).max() < 1e-10
