@@ -189,6 +189,65 @@ def helmholtz_fields(n: int, k: float):
     return z, z.copy(), d
 
 
+# ----------------------------------------------------------------------------- the paper's problem set
+
+def discrete_laplace_eigenvalue(n: int, index: int) -> float:
+    """The index-th smallest eigenvalue (1-based, repeated eigenvalues counted) of the
+    five-point Dirichlet Laplacian on the n x n unknowns: (4/h^2)(sin^2(p pi h/2) +
+    sin^2(q pi h/2)), p, q = 1..n."""
+    h = 1.0 / (n + 1)
+    s2 = np.sin(np.arange(1, n + 1) * math.pi * h / 2.0) ** 2
+    ev = np.sort(((4.0 / h**2) * (s2[:, None] + s2[None, :])).reshape(-1))
+    return float(ev[index - 1])
+
+
+PAPER_PROBLEMS = ("laplace", "diffconv1", "diffconv2", "diffconv3", "diffconv4",
+                  "helmholtz1", "helmholtz2", "helmholtz3", "helmholtz4")
+
+
+def paper_problem(name: str, n: int):
+    """Fields (b, c, d) of the PDE problems of Section 6.1, sampled at the unknowns:
+    Laplace; Diffusion-Convection I/II (b = 100 / 1000); III (b = 125 cos 4 pi y,
+    c = 125 sin 4 pi x, divergence free); IV (b = 125 cos 4 pi x, c = 125 sin 4 pi y);
+    Helmholtz I/II (d = -100 / -4005); III (d = -lambda_10 + 1e-5, lambda_10 the tenth
+    eigenvalue of the discrete Laplacian: near resonance); IV (d = -(2 pi (n+1)/40)^2,
+    40 points per wavelength at h = 1/(n+1))."""
+    X, Y = node_xy(n)
+    z = np.zeros(n * n)
+    b, c, d = z.copy(), z.copy(), z.copy()
+    if name == "laplace":
+        pass
+    elif name == "diffconv1":
+        b[:] = 100.0
+    elif name == "diffconv2":
+        b[:] = 1000.0
+    elif name == "diffconv3":
+        b, c = 125.0 * np.cos(4.0 * math.pi * Y), 125.0 * np.sin(4.0 * math.pi * X)
+    elif name == "diffconv4":
+        b, c = 125.0 * np.cos(4.0 * math.pi * X), 125.0 * np.sin(4.0 * math.pi * Y)
+    elif name == "helmholtz1":
+        d[:] = -100.0
+    elif name == "helmholtz2":
+        d[:] = -4005.0
+    elif name == "helmholtz3":
+        d[:] = -discrete_laplace_eigenvalue(n, 10) + 1e-5
+    elif name == "helmholtz4":
+        d[:] = -(2.0 * math.pi * (n + 1) / 40.0) ** 2
+    else:
+        raise ValueError(f"unknown problem {name}")
+    return b, c, d
+
+
+def error_vectors(n: int, seed: int):
+    """The two boundary vectors of the paper's error measures (Section 6.1): a unit
+    vector of random direction (normalised N(0,1) draw) and a smooth one, the trace of
+    cos(2 pi x) exp(y) + x y on the ghost ring, normalised.  Shape (4n, 2)."""
+    r = SplitMix64(seed).normal(4 * n)
+    x, y = ghost_xy(n)
+    sm = np.cos(2.0 * math.pi * x) * np.exp(y) + x * y
+    return np.stack([r / np.linalg.norm(r), sm / np.linalg.norm(sm)], axis=1)
+
+
 # ----------------------------------------------------------------------------- networks and body loads
 
 def network_conductivities(n: int, lo: float, hi: float, seed: int):
