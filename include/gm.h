@@ -136,6 +136,8 @@ typedef struct gm_info_t {
     long long resident_bytes;         /* device bytes the handle holds after the build     */
     int hbs_merges;                   /* tol > 0: merges solved by HBS block elimination   */
     int pad2;
+    long long hbs_operator_bytes;     /* tol > 0: bytes of the root operator in HBS form
+                                         (D, U, V, B at the node ranks; the paper's M(n)) */
 } gm_info_t;
 
 /* Fill *opts with defaults (FP64, no kept levels, default stream). */

@@ -48,7 +48,7 @@ class Info(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int * 7), ("pivoting", ctypes.c_int),
                 ("pivot_fallback", ctypes.c_int), ("refine_ratio", ctypes.c_double), ("hbs_levels", ctypes.c_int),
                 ("hbs_max_rank", ctypes.c_int), ("hbs_bytes", ctypes.c_longlong), ("resident_bytes", ctypes.c_longlong),
-                ("hbs_merges", ctypes.c_int), ("pad2", ctypes.c_int)]
+                ("hbs_merges", ctypes.c_int), ("pad2", ctypes.c_int), ("hbs_operator_bytes", ctypes.c_longlong)]
 
 
 class ServerStats(ctypes.Structure):

@@ -688,6 +688,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             hi.hbs_levels = h->hbs->L;
             hi.hbs_max_rank = std::max(hbs_rank, h->hbs->max_rank);
             hi.hbs_bytes = h->hbs->pool_doubles * 8;
+            hi.hbs_operator_bytes = hbs_operator_doubles(*h->hbs) * 8;
             hi.resident_bytes = hi.hbs_bytes;
         } else {
             const long long N = 4LL * h->n;

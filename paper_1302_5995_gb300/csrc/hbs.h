@@ -55,5 +55,9 @@ int hbs_apply_dtn(HbsRoot &h, const double *g, double *dudn, int B, cudaStream_t
 int hbs_dense_dtn(HbsRoot &h, double *T, cudaStream_t s);
 cudaError_t hbs_df32_to_f64(const float2 *x, double *y, int64_t cnt, cudaStream_t s);
 void hbs_free(HbsRoot &h);
+// Doubles of the operator in HBS form (Section 4), from the node ranks: D, U, V of every
+// leaf, U, V of every inner node below the root, and the two B blocks between the
+// children of every inner node -- the memory the paper reports as M(n).
+int64_t hbs_operator_doubles(const HbsRoot &h);
 
 }  // namespace gm
