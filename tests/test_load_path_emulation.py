@@ -265,3 +265,35 @@ def test_emulated_network_path_gives_the_oracle_F(shim, make):
     F = emulate_F(prob, n, leaf, body, plan, lp) * sig[:, None]  # k_scale_rows
     F_ref = o1.net_load_matrix(sx, sy, n, body)
     assert np.abs(F - F_ref).max() / np.abs(F_ref).max() < 1e-10
+
+
+def test_emulated_apply_add_tiles():
+    """k_apply_add (csrc/loads.cu): 16 x 16 output tiles, the k loop in steps of 16 through
+    shared tiles Ft[k][row] and Lt[col][k], with the kernel's bounds on every load."""
+    N, m, B = 37, 21, 19  # ragged in every dimension
+    rng = np.random.default_rng(3)
+    Fm, Lm, V0 = rng.standard_normal((N, m)), rng.standard_normal((m, B)), rng.standard_normal((N, B))
+    F = Fm.reshape(-1, order="F")
+    Fl = Lm.reshape(-1, order="F")
+    V = V0.reshape(-1, order="F").copy()
+    for bx in range((N + 15) // 16):
+        for by in range((B + 15) // 16):
+            acc = np.zeros((16, 16))  # acc[ty][tx]
+            for k0 in range(0, m, 16):
+                Ft = np.zeros((16, 16))
+                Lt = np.zeros((16, 16))
+                for ty in range(16):
+                    for tx in range(16):
+                        fr, fk = bx * 16 + tx, k0 + ty
+                        Ft[ty, tx] = F[fr + N * fk] if (fr < N and fk < m) else 0.0
+                        lk, lc = k0 + tx, by * 16 + ty
+                        Lt[ty, tx] = Fl[lk + m * lc] if (lk < m and lc < B) else 0.0
+                for ty in range(16):
+                    for tx in range(16):
+                        acc[ty, tx] += sum(Ft[q, tx] * Lt[ty, q] for q in range(16))
+            for ty in range(16):
+                for tx in range(16):
+                    row, col = bx * 16 + tx, by * 16 + ty
+                    if row < N and col < B:
+                        V[row + N * col] += acc[ty, tx]
+    np.testing.assert_allclose(V.reshape((N, B), order="F"), V0 + Fm @ Lm, rtol=1e-12, atol=1e-12)
