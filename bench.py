@@ -6,7 +6,7 @@ boundary vectors (seed 4).  Metric: build gridpoints/s (n^2 / step time), with s
 vectors/s, error against the FP64 oracle and p50/p99 step latency alongside.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gm|reference]
-                    [--precision fp64|mixed]
+                    [--precision fp64|mixed] [--workload build|serving|problemset|bodyloads]
 
 N > 1 runs under torchrun as independent replicas (one problem per GPU, no collective).
 `--impl reference` times the FP64 CPU oracle on the host cores instead.
@@ -454,6 +454,95 @@ def run_serving(args):
                       "build_every": quota, "results": res}), flush=True)
 
 
+def _timed(fn, reps):
+    """Median host time (ms) of fn() over reps calls, each bracketed by device syncs."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        ts.append((time.perf_counter() - t0) * 1e3)
+        del out
+    return statistics.median(ts)
+
+
+def run_problemset(args):
+    """The paper's problem set (Section 6.1: Laplace, Diffusion-Convection I-IV, Helmholtz
+    I-IV, Random Laplacian I-II) at n = 512, leaf 16: FP64 and mixed build times, the
+    mixed build's e1 / e2 (random unit and smooth boundary vectors) against the FP64
+    build, whether the automatic mode fell back to FP64, and the root operator's size in
+    HBS form at tol 1e-7 (the paper's M(n) and M(n)/n).  One JSON line (not the headline)."""
+    import numpy as np
+    import torch
+    from paper_1302_5995_gb300 import build_ext, inputs
+    build_ext.build()
+    import paper_1302_5995_gb300 as gm
+
+    n, leaf, reps = 512, 16, max(1, args.steps)
+    R = torch.from_numpy(np.ascontiguousarray(inputs.error_vectors(n, 17).T)).cuda()
+    res = {}
+    for name in list(inputs.PAPER_PROBLEMS) + ["random1", "random2"]:
+        row = {}
+        if name.startswith("random"):
+            sx, sy = (inputs.random_laplacian_1 if name == "random1" else inputs.random_laplacian_2)(n)
+            sx, sy = torch.from_numpy(sx).cuda(), torch.from_numpy(sy).cuda()
+            ref = gm.build_network(sx, sy, n, leaf)
+            row["fp64_build_ms"] = _timed(lambda: gm.build_network(sx, sy, n, leaf), reps)
+        else:
+            b, c, d = (torch.from_numpy(x).cuda() for x in inputs.paper_problem(name, n))
+            ref = gm.build(b, c, d, n, leaf)
+            row["fp64_build_ms"] = _timed(lambda: gm.build(b, c, d, n, leaf), reps)
+            mixed = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED)
+            row["mixed_build_ms"] = _timed(lambda: gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED), reps)
+            row["mixed_fell_back_to_fp64"] = bool(mixed.info()["pivot_fallback"])
+            V, Vr = mixed.solve(R), ref.solve(R)
+            e = (torch.linalg.norm(V - Vr, dim=1) / torch.linalg.norm(Vr, dim=1)).cpu().tolist()
+            row["mixed_e1_vs_fp64"], row["mixed_e2_vs_fp64"] = e
+            try:
+                inf = gm.build(b, c, d, n, leaf, tol=1e-7, hbs_leaf=64).info()
+                row["hbs_M_MB"] = inf["hbs_operator_bytes"] / 2**20
+                row["hbs_M_over_n"] = inf["hbs_operator_bytes"] / 2**20 / n
+                row["hbs_max_rank"] = inf["hbs_max_rank"]
+            except gm.GmError as err:
+                row["hbs"] = str(err)
+        res[name] = row
+    print(json.dumps({"workload": "problemset", "n": n, "leaf": leaf, "reps": reps, "timing": "host, synced",
+                      "data": "synthetic (the paper's analytic fields; seeded networks)", "results": res}),
+          flush=True)
+
+
+def run_bodyloads(args):
+    """Body loads (Section 6.3) on the paper's body-load problem, Random Laplacian I at
+    512 x 512, leaf 16, with N_body = 10, 100, 1000 loads in a localized window: FP64 build
+    time of T and F, time of one solve T g + F f, and the conservation error of F (every
+    column sums to -h).  One JSON line (not the headline)."""
+    import numpy as np
+    import torch
+    from paper_1302_5995_gb300 import build_ext, inputs
+    build_ext.build()
+    import paper_1302_5995_gb300 as gm
+
+    n, leaf, reps = 512, 16, max(1, args.steps)
+    h = 1.0 / (n + 1)
+    sx, sy = (torch.from_numpy(x).cuda() for x in inputs.random_laplacian_1(n))
+    res = {}
+    for nb in (10, 100, 1000):
+        body = inputs.body_nodes(n, nb, 40 + nb).astype(np.int32)
+        op = gm.build_network(sx, sy, n, leaf, body)
+        build_ms = _timed(lambda: gm.build_network(sx, sy, n, leaf, body), reps)
+        g = torch.from_numpy(inputs.gaussian_vectors(n, 1, 41).T.copy()).cuda()
+        f = torch.from_numpy(inputs.body_load_vectors(nb, 1, 42).T.copy()).cuda()
+        solve_ms = _timed(lambda: op.solve_loads(g, f), max(reps, 10))
+        F = op.load_operator()
+        res[str(nb)] = {"build_ms": build_ms, "solve_ms": solve_ms,
+                        "conservation_err": float(np.abs(F.sum(axis=0) + h).max() / h)}
+    print(json.dumps({"workload": "bodyloads", "problem": "Random Laplacian I (conductivities U(1,2))", "n": n,
+                      "leaf": leaf, "precision": "fp64", "reps": reps, "timing": "host, synced",
+                      "results": res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -461,12 +550,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gm", "reference"], default="gm")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
-    ap.add_argument("--workload", choices=["build", "serving"], default="build",
-                    help="build: the headline build+solve step; serving: the serving workload (not the headline)")
+    ap.add_argument("--workload", choices=["build", "serving", "problemset", "bodyloads"], default="build",
+                    help="build: the headline build+solve step; serving, problemset, bodyloads: other "
+                         "workloads (not the headline)")
     ap.add_argument("--serve-requests", type=int, default=600)
     args = ap.parse_args()
     if args.workload == "serving":
         run_serving(args)
+        return
+    if args.workload == "problemset":
+        run_problemset(args)
+        return
+    if args.workload == "bodyloads":
+        run_bodyloads(args)
         return
     if args.impl == "reference":
         run_reference(args)
