@@ -279,6 +279,9 @@ def run_gm(args):
     result = {}
     if rank == 0:
         result["V"] = V.cpu().numpy()
+        op = gm.build(b, c, d, n, LEAF, precision=prec, stream=stream, **extra)  # after timing: T itself
+        result["T"] = op.dtn()
+        op.free()
     # end-to-end through the C ABI with pinned host buffers (copies inside the timing)
     hb = [torch.from_numpy(cfg[k]).pin_memory() for k in "bcd"]
     hG = torch.from_numpy(Gv).pin_memory()
@@ -325,6 +328,7 @@ def run_gm(args):
     t_cpu, To, Vo = cpu_oracle_step(cfg)
     Vg = result["V"].reshape(NVEC, 4 * n).T
     rel_err = float((np.linalg.norm(Vg - Vo, axis=0) / np.linalg.norm(Vo, axis=0)).max())
+    rel_err_T = float(np.linalg.norm(result["T"] - To) / np.linalg.norm(To))
     achieved = dom_fl / (dom_ms * 1e-3) / 1e12
     bound, peak, peak_src = family_roofline(args.precision, dom)
     tr = TRAFFIC.get(dom)
@@ -344,6 +348,7 @@ def run_gm(args):
         "latency_ms": {"p50": sorted_ms[len(sorted_ms) // 2],
                        "p99": sorted_ms[min(len(sorted_ms) - 1, int(0.99 * len(sorted_ms)))]},
         "rel_err_vs_fp64_oracle": rel_err,
+        "rel_err_T_frobenius_vs_fp64_oracle": rel_err_T,
         "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                      "launches_per_step": dom_n // args.steps,
