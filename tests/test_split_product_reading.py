@@ -65,3 +65,38 @@ def test_level_sums_need_the_k_chunk_bound():
     # and FP32 really does round such a sum: one step past 2^24 loses the unit
     acc = np.float32(2 ** 24)
     assert acc + np.float32(1) == acc
+
+
+def test_merged_low_levels_stay_below_the_truncation():
+    """A reading for wider tensor-memory tiles: levels 0..2 stay exact in their own FP32
+    accumulators, levels 3..5 share one.  Their products come from copies of the digit
+    planes scaled by powers of two, A'_a = d_a 2^-7a and B'_b = d_b 2^(21 - 7b), so each
+    product d_a d_b 2^-7(a+b-3) carries its level's factor exactly (bf16 holds any 7-bit
+    digit times a power of two), and only the shared FP32 sum rounds -- near 2^-24 of
+    level 3, i.e. 2^-45 of the product, below the 2^-42 truncation of S = 6 digits."""
+    S, K = 6, 512
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((32, K)) * np.exp2(rng.integers(-6, 6, (32, 1)))
+    B = rng.standard_normal((24, K))
+    dA, ea = digits(A, S)
+    dB, eb = digits(B, S)
+    exact_levels = []
+    for g in range(3):
+        acc = np.zeros((A.shape[0], B.shape[0]), np.float32)
+        for a in range(g + 1):
+            acc += dA[a].astype(np.float32) @ dB[g - a].T.astype(np.float32)
+        exact_levels.append(acc.astype(np.float64))
+    Ap = np.stack([dA[a] * 2.0 ** (-7 * a) for a in range(S)]).astype(np.float32)
+    Bp = np.stack([dB[b] * 2.0 ** (21 - 7 * b) for b in range(S)]).astype(np.float32)
+    merged = np.zeros((A.shape[0], B.shape[0]), np.float32)
+    for a in range(S):
+        for b in range(S):
+            if 3 <= a + b <= S - 1:
+                merged += Ap[a] @ Bp[b].T  # FP32 products of exact operands, FP32 sum
+    val = sum(exact_levels[g] * 2.0 ** (-7 * g) for g in range(3)) + merged.astype(np.float64) * 2.0 ** -21
+    P = val * np.exp2(ea[:, None] + eb[None, :] - 12.0)
+    scale = np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=1)[None, :] * K
+    assert (np.abs(P - A @ B.T) / scale).max() < 2.0 ** -38
+    # the same bound as six exact levels
+    P6, _, _ = split_product(A, B, S)
+    assert (np.abs(P - A @ B.T) / scale).max() < 4 * (np.abs(P6 - A @ B.T) / scale).max() + 2.0 ** -44
