@@ -6,7 +6,8 @@ loads (the paper's largest N_body) the conservation and maximum-principle proper
 a Laplace problem, which hold at any size.  Networks: T and F against O1's network
 solve, unit conductivities against the Laplace build, and the paper's body-load workload
 (Random Laplacian I, 512 x 512, 1000 loads) against symmetry, T 1 = 0 and conservation.
-(File named to run after the core parity tests.)"""
+(Marked late: these paths are newer than the rest of the
+suite, so the other tests run first.)"""
 import numpy as np
 import pytest
 
@@ -14,7 +15,7 @@ import paper_1302_5995_gb300 as gm
 from oracle import o1
 from paper_1302_5995_gb300 import inputs
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.late]
 
 
 def rel(a, b):

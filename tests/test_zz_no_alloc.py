@@ -3,8 +3,8 @@ a library allocate (a serving loop that must not touch the allocator once runnin
 host whose device memory belongs to another runtime's pool).  Its result must equal the
 allocating gm_solve on the same operator, call after call.
 
-Collected last on purpose (file name): if it fails, a stop-at-first-failure run has
-already run every other test.
+Collected after the other established tests on purpose (file name; only the tests
+marked late follow it): if it fails, a stop-at-first-failure run has already run them.
 """
 import ctypes
 
