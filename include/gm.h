@@ -265,12 +265,14 @@ int gm_get_load_operator(gm_handle *h, double *F_out);
  *        (i = 0 and i = n reach the west and east ghosts);
  *   sy : n + 1 rows of n y-links, sy[i + n j] joins (i, j-1) and (i, j), j = 0..n;
  *        both host or device, read during the call.
+ *   tol : 0 for the dense T; > 0 for the root in HBS form at that tolerance (as in
+ *        gm_build; not with body loads: GM_EUNSUPPORTED).
  *   body, nbody : optional body loads (nbody = 0: none) as in gm_build_loads; the handle
  *        then also serves gm_solve_loads and gm_get_load_operator.
- * FP64 only (GM_EUNSUPPORTED for mixed precision or keep_levels); tol-free (dense T).
+ * FP64 only (GM_EUNSUPPORTED for mixed precision or keep_levels).
  */
-int gm_build_net(const gm_opts *opts, const double *sx, const double *sy, int n, int leaf, const int *body,
-                 int nbody, gm_handle **out);
+int gm_build_net(const gm_opts *opts, const double *sx, const double *sy, int n, int leaf, double tol,
+                 const int *body, int nbody, gm_handle **out);
 
 int gm_info(gm_handle *h, gm_info_t *info);
 

@@ -82,7 +82,8 @@ SIGNATURES = {
     "gm_solve_loads": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int, ctypes.c_void_p]),
     "gm_get_load_operator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gm_build_net": (ctypes.c_int, [ctypes.POINTER(Opts)] + [ctypes.c_void_p] * 2
-                     + [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+                     + [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int,
+                        ctypes.POINTER(ctypes.c_void_p)]),
     "gm_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Info)]),
     "gm_free": (None, [ctypes.c_void_p]),
     "gm_server_create": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
@@ -342,18 +343,19 @@ def build_loads(b, c, d, n, leaf, body, stream=None, panel_width=0):
     return op
 
 
-def build_network(sx, sy, n, leaf, body=None, stream=None, panel_width=0):
+def build_network(sx, sy, n, leaf, body=None, tol=0.0, hbs_leaf=0, stream=None, panel_width=0):
     """FP64 build for a conductance network (Section 6.1 Random Laplacian): sx, sy the
     n (n + 1) link conductivities in the layout of inputs.network_conductivities, with
-    optional body loads at the flat node indices `body` (Section 6.3)."""
+    optional body loads at the flat node indices `body` (Section 6.3), or the root in HBS
+    form at tolerance tol > 0 (node size hbs_leaf)."""
     import numpy as np
     lib = load_library()
     sx = _check_f64(sx, "sx", n * (n + 1))
     sy = _check_f64(sy, "sy", n * (n + 1))
     nodes = np.ascontiguousarray(np.asarray([] if body is None else body, dtype=np.int32).reshape(-1))
-    o = _opts(PREC_FP64, False, stream, panel_width, False, 0, PIVOT_AUTO)
+    o = _opts(PREC_FP64, False, stream, panel_width, False, 0, PIVOT_AUTO, hbs_leaf)
     h = ctypes.c_void_p()
-    rc = lib.gm_build_net(ctypes.byref(o), _ptr(sx), _ptr(sy), n, leaf,
+    rc = lib.gm_build_net(ctypes.byref(o), _ptr(sx), _ptr(sy), n, leaf, float(tol),
                           ctypes.c_void_p(nodes.ctypes.data) if nodes.size else None, int(nodes.size), ctypes.byref(h))
     if rc:
         raise GmError(rc, "gm_build_net")

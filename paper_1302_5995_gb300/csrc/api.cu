@@ -1304,16 +1304,17 @@ int gm_get_load_operator(gm_handle *h, double *F_out) {
 
 extern "C" {
 
-int gm_build_net(const gm_opts *opts, const double *sx, const double *sy, int n, int leaf, const int *body,
-                 int nbody, gm_handle **out) {
+int gm_build_net(const gm_opts *opts, const double *sx, const double *sy, int n, int leaf, double tol,
+                 const int *body, int nbody, gm_handle **out) {
     if (!out) return GM_EINVAL;
     *out = nullptr;
-    if (!sx || !sy || n < 2 || leaf < 4 || nbody < 0 || (nbody > 0 && !body) || (int64_t)nbody > (int64_t)n * n)
+    if (!sx || !sy || n < 2 || leaf < 4 || !(tol >= 0.0) || nbody < 0 || (nbody > 0 && !body) ||
+        (int64_t)nbody > (int64_t)n * n)
         return GM_EINVAL;
     gm_opts o;
     int rc = check_opts(opts, o);
     if (rc) return rc;
-    if (o.precision != GM_PREC_FP64 || o.keep_levels) return GM_EUNSUPPORTED;
+    if (o.precision != GM_PREC_FP64 || o.keep_levels || (tol > 0.0 && nbody > 0)) return GM_EUNSUPPORTED;
     std::vector<int> nodes(body, body + nbody);
     if (nbody > 0) {
         std::vector<int> sorted(nodes);
@@ -1341,7 +1342,7 @@ int gm_build_net(const gm_opts *opts, const double *sx, const double *sy, int n,
     gm_handle *h = nullptr;
     if (nbody == 0) {
         std::vector<gm_handle *> H;
-        if ((rc = build_with_fallback(o, 0.0, {{n, leaf}}, W, nullptr, W, H))) return rc;
+        if ((rc = build_with_fallback(o, tol, {{n, leaf}}, W, nullptr, W, H))) return rc;
         h = H[0];
     } else {
         h = new_handle({n, leaf}, GM_PREC_FP64);
@@ -1351,7 +1352,15 @@ int gm_build_net(const gm_opts *opts, const double *sx, const double *sy, int n,
         }
     }
     // the datum at ghost k is the current through its link: rows of T and F times sigma_k
-    cudaError_t e = launch_scale_rows(h->T, 4 * n, 4 * n, sig.as<double>(), s);
+    // (an HBS root keeps the conductivities and weights every apply instead)
+    cudaError_t e = cudaSuccess;
+    if (h->hbs) {
+        e = cudaMalloc(&h->hbs->sig, (size_t)4 * n * sizeof(double));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->hbs->sig, sig.p, (size_t)4 * n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    } else {
+        e = launch_scale_rows(h->T, 4 * n, 4 * n, sig.as<double>(), s);
+    }
     if (e == cudaSuccess && h->F) e = launch_scale_rows(h->F, 4 * n, nbody, sig.as<double>(), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "hbs.h"
+#include "network.h"
 
 namespace gm {
 
@@ -236,8 +237,10 @@ __global__ void __launch_bounds__(256) k_hbs_pqr(const QrDesc *__restrict__ ds, 
     }
 }
 
+// With c == nullptr, b is a table of five weights per node (a conductance network).
 __device__ __forceinline__ double stencil_w_h(const double *__restrict__ b, const double *__restrict__ c,
                                               const double *__restrict__ d, double ih, int g, int dir) {
+    if (!c) return b[5 * (int64_t)g + dir];
     const double ih2 = ih * ih;  // ih = 1/h = n+1 exactly
     switch (dir) {
     case DIR_E: return -ih2 + b[g] * ih;
@@ -840,6 +843,7 @@ int hbs_apply_dtn(HbsRoot &H, const double *g, double *dudn, int B, cudaStream_t
         k_hbs_out<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, s>>>(n, B, g, W + (size_t)r * B, dudn);
         if (cudaGetLastError() != cudaSuccess) rc = GM_ECUDA;
     }
+    if (rc == GM_OK && H.sig && launch_scale_rows(dudn, 4 * n, B, H.sig, s) != cudaSuccess) rc = GM_ECUDA;
     cudaFreeAsync(W, s);
     return rc;
 }
@@ -941,6 +945,8 @@ int hbs_dense_dtn(HbsRoot &H, double *T, cudaStream_t s) {
 void hbs_free(HbsRoot &h) {
     if (h.pool) cudaFree(h.pool);
     h.pool = nullptr;
+    if (h.sig) cudaFree(h.sig);
+    h.sig = nullptr;
 }
 
 }  // namespace gm

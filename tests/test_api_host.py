@@ -148,16 +148,19 @@ def test_network_build_rejects_bad_arguments(lib):
     sy = np.ones(n * (n + 1))
     h = ctypes.c_void_p()
 
-    def call(opts=None, a=sx, b=sy, nodes=None, count=0, nn=n, leaf=4):
+    def call(opts=None, a=sx, b=sy, nodes=None, count=0, nn=n, leaf=4, tol=0.0):
         return lib.gm_build_net(ctypes.byref(opts) if opts is not None else None,
                                 a.ctypes.data if a is not None else None, b.ctypes.data if b is not None else None,
-                                nn, leaf, nodes.ctypes.data if nodes is not None else None, count, ctypes.byref(h))
+                                nn, leaf, tol, nodes.ctypes.data if nodes is not None else None, count,
+                                ctypes.byref(h))
     assert call(a=None) == gm.GM_EINVAL
     assert call(leaf=3) == gm.GM_EINVAL
     assert call(count=-1) == gm.GM_EINVAL
     assert call(count=2) == gm.GM_EINVAL  # loads without a list
     assert call(nodes=np.array([1, 1], dtype=np.int32), count=2) == gm.GM_EINVAL
     assert call(nodes=np.array([64], dtype=np.int32), count=1) == gm.GM_EINVAL
+    assert call(tol=-1.0) == gm.GM_EINVAL
+    assert call(tol=1e-9, nodes=np.array([3], dtype=np.int32), count=1) == gm.GM_EUNSUPPORTED  # HBS + loads
     o = gm.Opts()
     lib.gm_opts_default(ctypes.byref(o))
     o.precision = gm.PREC_MIXED

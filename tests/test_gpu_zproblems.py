@@ -43,7 +43,7 @@ def test_problem_set_e1_e2(name, n, leaf):
     assert e1 < bound and e2 < bound, (name, e1, e2, spread)
 
 
-@pytest.mark.parametrize("name", ["laplace", "diffconv1", "diffconv3", "helmholtz1"])
+@pytest.mark.parametrize("name", ["laplace", "diffconv1", "diffconv3", "helmholtz1", "random1", "random2"])
 def test_hbs_memory_per_n_stays_flat(name):
     """The paper's compressibility claim (Table mem): the memory M(n) of the solution
     operator in HBS form grows like n, so M(n)/n stays about flat from n = 256 to 1024
@@ -52,11 +52,15 @@ def test_hbs_memory_per_n_stays_flat(name):
     rank as the grid resolves them)."""
     ratios = []
     for n in (256, 512, 1024):
-        b, c, d = inputs.paper_problem(name, n)
         try:
-            inf = gm.build(b, c, d, n, 16, tol=1e-7, hbs_leaf=64).info()
+            if name.startswith("random"):
+                sx, sy = (inputs.random_laplacian_1 if name == "random1" else inputs.random_laplacian_2)(n)
+                inf = gm.build_network(sx, sy, n, 16, tol=1e-7, hbs_leaf=64).info()
+            else:
+                b, c, d = inputs.paper_problem(name, n)
+                inf = gm.build(b, c, d, n, 16, tol=1e-7, hbs_leaf=64).info()
         except gm.GmError as e:  # a node rank at the documented cap of the GPU sampling
-            if name.startswith("diffconv") and e.code == gm.GM_EUNSUPPORTED:
+            if (name.startswith("diffconv") or name == "random2") and e.code == gm.GM_EUNSUPPORTED:
                 pytest.skip(f"{name}: an HBS rank reached the cap at n = {n}")
             raise
         assert inf["hbs_levels"] > 0 and 0 < inf["hbs_operator_bytes"] <= inf["hbs_bytes"]
@@ -80,3 +84,22 @@ def test_server_serves_an_hbs_operator():
     st = srv.stats()
     assert st["requests"] == 1 and st["vectors"] == 8 and st["resident_bytes"] > 0
     srv.close()
+
+
+@pytest.mark.parametrize("make", [inputs.random_laplacian_1, inputs.random_laplacian_2])
+def test_network_with_hbs_root_matches_the_dense_network(make):
+    """A network's root in HBS form (the datum rows weighted by the ghosts' conductivities
+    in every apply) against the dense network build, within 100 tol."""
+    n, leaf, tol = 128, 16, 1e-9
+    sx, sy = make(n)
+    T = gm.build_network(sx, sy, n, leaf).dtn()
+    try:
+        op = gm.build_network(sx, sy, n, leaf, tol=tol, hbs_leaf=32)
+    except gm.GmError as e:  # the 1:1000 contrast may lift a node rank to the sampling cap
+        if make is inputs.random_laplacian_2 and e.code == gm.GM_EUNSUPPORTED:
+            pytest.skip("Random Laplacian II: an HBS rank reached the cap")
+        raise
+    assert op.info()["hbs_levels"] > 0
+    assert np.abs(op.dtn() - T).max() / np.abs(T).max() < 100 * tol
+    G = np.ascontiguousarray(inputs.gaussian_vectors(n, 4, 23).T)
+    assert np.abs(op.solve(G) - (T @ G.T).T).max() / np.abs(T @ G.T).max() < 100 * tol
