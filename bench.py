@@ -495,6 +495,13 @@ def run_problemset(args):
             sx, sy = torch.from_numpy(sx).cuda(), torch.from_numpy(sy).cuda()
             ref = gm.build_network(sx, sy, n, leaf)
             row["fp64_build_ms"] = _timed(lambda: gm.build_network(sx, sy, n, leaf), reps)
+            try:
+                inf = gm.build_network(sx, sy, n, leaf, tol=1e-7, hbs_leaf=64).info()
+                row["hbs_M_MB"] = inf["hbs_operator_bytes"] / 2**20
+                row["hbs_M_over_n"] = inf["hbs_operator_bytes"] / 2**20 / n
+                row["hbs_max_rank"] = inf["hbs_max_rank"]
+            except gm.GmError as err:
+                row["hbs"] = str(err)
         else:
             b, c, d = (torch.from_numpy(x).cuda() for x in inputs.paper_problem(name, n))
             ref = gm.build(b, c, d, n, leaf)
