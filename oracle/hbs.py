@@ -15,6 +15,8 @@ Follows, in the paper's notation:
                           + B^(l), Ht^(1) = B^(0)                     (eq. tele1-tele3)
   Section 5, Algorithm 1  inversion: factors {E, F, G} of H^{-1}
   Section 5, Algorithm 2  y = H^{-1} x from those factors
+  Section 5, Steps 1-3    the accelerated merge: block solve with HBS inverses, low-rank
+                          S13 / S24 and the factored update, parent recompressed to HBS
 
 Readings (the paper defers construction to its references):
   * compression: U_tau is an orthonormal basis of the columns of tau's off-diagonal
@@ -278,3 +280,51 @@ def step1_interface_solver(tol: float, m: int):
         return np.vstack([X3, X4])
 
     return solve
+
+
+def low_rank(A, tol):
+    """A ~ L R from a column-pivoted QR of A truncated at the first |R_jj| <= tol |R_11|
+    (the local-tolerance reading of the compression): L = Q_k orthonormal, R = L^T A."""
+    Q, k = _pivoted_qr(A, tol)
+    L = Q[:, :k]
+    return L, L.T @ A
+
+
+def accelerated_merge(prob, box1, S1, box2, S2, parent, tol, m):
+    """The accelerated merge of two siblings (Section 5, Steps 1-3), from their dense
+    Schur complements S1, S2 (eq. partition_we for P1..P4):
+      Step 1  X = [S33 A34; A43 S44]^{-1} [S31 A32; A41 S42] by the block solve with HBS
+              inverses (step1_interface_solver);
+      Step 2  S13 = L13 R13 and S24 = L24 R24 truncated at tol, and the update in factored
+              form (A14 = A23 = 0 for the five-point stencil):
+                  [L13 (R13 X31)  L13 (R13 X32); L24 (R24 X41)  L24 (R24 X42)];
+      Step 3  S = [S11 A12; A21 S22] minus that update, placed in the parent's ring order
+              and compressed to HBS form at tol.  The paper's HBS + low-rank addition and
+              recompression algorithms are not in its text: the sum is formed and
+              recompressed densely here (the reading).
+    Returns (S dense, its HBS form, (rank of L13, rank of L24))."""
+    from oracle.nd_dense import partition_we
+    i1, i3, i2, i4, P1, P3, P2, P4 = partition_we(box1, box2, parent)
+    A = prob.A_block
+    S11, S13, S31, S33 = (S1[np.ix_(r, c)] for r, c in ((i1, i1), (i1, i3), (i3, i1), (i3, i3)))
+    S22, S24, S42, S44 = (S2[np.ix_(r, c)] for r, c in ((i2, i2), (i2, i4), (i4, i2), (i4, i4)))
+    A12, A21, A32, A41 = A(P1, P2), A(P2, P1), A(P3, P2), A(P4, P1)
+    A34, A43 = A(P3, P4), A(P4, P3)
+    n1, s3 = len(P1), len(P3)
+    # Step 1
+    Z = np.block([[S31, A32], [A41, S42]])
+    X = step1_interface_solver(tol, m)(S33, A34, A43, S44, Z) if s3 else np.zeros((0, Z.shape[1]))
+    X31, X32 = X[:s3, :n1], X[:s3, n1:]
+    X41, X42 = X[s3:, :n1], X[s3:, n1:]
+    # Step 2
+    L13, R13 = low_rank(S13, tol)
+    L24, R24 = low_rank(S24, tol)
+    upd = np.block([[L13 @ (R13 @ X31), L13 @ (R13 @ X32)], [L24 @ (R24 @ X41), L24 @ (R24 @ X42)]])
+    # Step 3
+    S = np.block([[S11, A12], [A21, S22]]) - upd
+    rp = parent.ring()
+    where = {q: k for k, q in enumerate(rp)}
+    perm = np.array([where[q] for q in P1 + P2])
+    out = np.empty_like(S)
+    out[np.ix_(perm, perm)] = S
+    return out, compress(out, HBSTree(out.shape[0], m), tol), (L13.shape[1], L24.shape[1])
