@@ -144,6 +144,34 @@ def _check_f64(x, what, numel=None):
     return x
 
 
+def _batch(x, N, what):
+    """Vectors in x (N values each); its size must be a whole number of vectors."""
+    size = x.numel() if hasattr(x, "numel") else x.size
+    if size % N:
+        raise ValueError(f"{what}: {size} values is not a whole number of {N}-value vectors")
+    return size // N
+
+
+def _out_like(g, out, numel):
+    """The result buffer: a new one like g, or the caller's, checked to hold numel float64
+    values contiguously (the library writes all of them)."""
+    if out is None:
+        if hasattr(g, "data_ptr"):
+            import torch
+            return torch.empty_like(g)
+        import numpy as np
+        return np.empty_like(g)
+    if hasattr(out, "data_ptr"):
+        import torch
+        if out.dtype != torch.float64 or not out.is_contiguous() or out.numel() != numel:
+            raise ValueError(f"out: need a contiguous float64 tensor of {numel} values")
+        return out
+    import numpy as np
+    if not isinstance(out, np.ndarray) or out.dtype != np.float64 or not out.flags.c_contiguous or out.size != numel:
+        raise ValueError(f"out: need a C-contiguous float64 array of {numel} values")
+    return out
+
+
 def _stream_handle(stream):
     if stream is None:
         try:
@@ -186,14 +214,8 @@ class DtN:
         lib = load_library()
         N = 4 * self.n
         g = _check_f64(g, "g")
-        B = (g.numel() if hasattr(g, "numel") else g.size) // N
-        if out is None:
-            if hasattr(g, "data_ptr"):
-                import torch
-                out = torch.empty_like(g)
-            else:
-                import numpy as np
-                out = np.empty_like(g)
+        B = _batch(g, N, "g")
+        out = _out_like(g, out, N * B)
         rc = lib.gm_solve(self._h, _ptr(g), _ptr(out), B, _stream_handle(stream))
         if rc:
             raise GmError(rc, "gm_solve")
@@ -232,15 +254,9 @@ class DtN:
         lib = load_library()
         N = 4 * self.n
         g = _check_f64(g, "g")
-        f = _check_f64(f, "f")
-        B = (g.numel() if hasattr(g, "numel") else g.size) // N
-        if out is None:
-            if hasattr(g, "data_ptr"):
-                import torch
-                out = torch.empty_like(g)
-            else:
-                import numpy as np
-                out = np.empty_like(g)
+        B = _batch(g, N, "g")
+        f = _check_f64(f, "f", self.nbody * B)
+        out = _out_like(g, out, N * B)
         rc = lib.gm_solve_loads(self._h, _ptr(g), _ptr(f), _ptr(out), B, _stream_handle(stream))
         if rc:
             raise GmError(rc, "gm_solve_loads")

@@ -166,3 +166,22 @@ def test_network_build_rejects_bad_arguments(lib):
     o.precision = gm.PREC_MIXED
     assert call(opts=o) == gm.GM_EUNSUPPORTED
     assert h.value is None
+
+
+def test_binding_checks_solve_buffers_before_the_library():
+    """A wrong-sized g, f or out is refused in Python: the library would read or write
+    4n * batch values through the pointers it is given."""
+    op = gm.DtN(ctypes.c_void_p(1), 8, 4)  # never reaches the library
+    op.nbody = 3
+    N = 32
+    with pytest.raises(ValueError):
+        op.solve(np.zeros(N + 1))
+    with pytest.raises(ValueError):
+        op.solve(np.zeros(2 * N), out=np.zeros(N))
+    with pytest.raises(ValueError):
+        op.solve(np.zeros(2 * N), out=np.zeros(2 * N, dtype=np.float32))
+    with pytest.raises(ValueError):
+        op.solve(np.zeros(2 * N), out=np.zeros((2 * N, 2))[:, 0])  # not contiguous
+    with pytest.raises(ValueError):
+        op.solve_loads(np.zeros(2 * N), np.zeros(5))  # 2 vectors need 2 x 3 loads
+    op._h = None  # nothing to free
