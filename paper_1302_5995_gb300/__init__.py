@@ -227,6 +227,7 @@ class DtN:
         import numpy as np
         N = 4 * self.n
         if out is not None:
+            out = _out_like(None, out, N * N)
             rc = load_library().gm_get_dtn(self._h, _ptr(out))
             if rc:
                 raise GmError(rc, "gm_get_dtn")
@@ -395,6 +396,7 @@ class Server:
             raise GmError(rc, "gm_server_create")
         self._s = h
         self._keep = {}
+        self._n = {}  # operator id -> grid size, to check request buffers
 
     def add(self, op):
         oid = ctypes.c_int()
@@ -402,9 +404,16 @@ class Server:
         if rc:
             raise GmError(rc, "gm_server_add")
         op._h = None  # owned by the server now
+        self._n[oid.value] = op.n
         return oid.value
 
     def submit(self, op_id, g, out, batch):
+        n = self._n.get(op_id)
+        if n is not None:  # the first 4n * batch values of g and out are read and written
+            for x, what in ((g, "g"), (out, "out")):
+                size = x.numel() if hasattr(x, "numel") else x.size
+                if int(batch) < 0 or size < 4 * n * int(batch):
+                    raise ValueError(f"{what}: fewer than 4n * batch = {4 * n * int(batch)} values")
         rid = ctypes.c_longlong()
         rc = load_library().gm_server_submit(self._s, op_id, _ptr(g), _ptr(out), int(batch), ctypes.byref(rid))
         if rc:

@@ -185,3 +185,16 @@ def test_binding_checks_solve_buffers_before_the_library():
     with pytest.raises(ValueError):
         op.solve_loads(np.zeros(2 * N), np.zeros(5))  # 2 vectors need 2 x 3 loads
     op._h = None  # nothing to free
+
+
+def test_binding_checks_dtn_and_server_buffers():
+    op = gm.DtN(ctypes.c_void_p(1), 8, 4)  # never reaches the library
+    with pytest.raises(ValueError):
+        op.dtn(out=np.zeros(32 * 32 - 1))
+    op._h = None
+    srv = object.__new__(gm.Server)  # the request checks run before any library call
+    srv._s, srv._keep, srv._n = None, {}, {7: 8}
+    with pytest.raises(ValueError):
+        srv.submit(7, np.zeros((2, 32)), np.zeros((1, 32)), 2)  # out holds one vector of two
+    with pytest.raises(ValueError):
+        srv.submit(7, np.zeros((1, 31)), np.zeros((1, 32)), 1)
