@@ -292,6 +292,16 @@ int gm_info(gm_handle *h, gm_info_t *info);
  *   gm_server_submit : queue dudn = T g for `batch` vectors (4n x batch column-major,
  *                      host or device); returns at once.  g and dudn must stay valid
  *                      until the request completes.  GM_EINVAL for an unknown operator.
+ *   gm_server_submit_build : queue a build of the operator for b, c, d (arguments as
+ *                      gm_build_ex; opts->stream is replaced by the worker's stream); returns
+ *                      at once with the request id and the id the operator will have, for
+ *                      which solves may be submitted right away (they run after it).  The
+ *                      worker admits the built operator like gm_server_add; the request's
+ *                      result is the build's code, or GM_ENOMEM if it cannot fit (a solve
+ *                      queued for a failed build then returns GM_EINVAL).  b, c, d must
+ *                      stay valid until the request completes.
+ *   gm_server_poll   : without blocking: *done = 1 and the request's result code once it
+ *                      has completed, else *done = 0 and GM_OK; GM_EINVAL for an unknown id.
  *   gm_server_wait   : block until request req_id has completed; returns its result code
  *                      (GM_EINVAL if its operator was evicted before it ran).
  *   gm_server_sync   : block until nothing is queued or running.
@@ -309,6 +319,9 @@ typedef struct gm_server_stats_t {
 int gm_server_create(long long budget_bytes, int batching, gm_server **out);
 int gm_server_add(gm_server *s, gm_handle *h, int *op_id);
 int gm_server_submit(gm_server *s, int op_id, const double *g, double *dudn, int batch, long long *req_id);
+int gm_server_submit_build(gm_server *s, const gm_opts *opts, const double *b, const double *c, const double *d,
+                           int n, int leaf, double tol, int *op_id, long long *req_id);
+int gm_server_poll(gm_server *s, long long req_id, int *done);
 int gm_server_wait(gm_server *s, long long req_id);
 int gm_server_sync(gm_server *s);
 int gm_server_stats(gm_server *s, gm_server_stats_t *st);

@@ -90,6 +90,10 @@ SIGNATURES = {
     "gm_server_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "gm_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_longlong)]),
+    "gm_server_submit_build": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Opts)] + [ctypes.c_void_p] * 3
+                               + [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_longlong)]),
+    "gm_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]),
     "gm_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
     "gm_server_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "gm_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
@@ -420,6 +424,28 @@ class Server:
             raise GmError(rc, "gm_server_submit")
         self._keep[rid.value] = (g, out)
         return rid.value
+
+    def submit_build(self, b, c, d, n, leaf, tol=0.0, precision=PREC_FP64, split_digits=0, pivoting=PIVOT_AUTO):
+        """Queue a build on the server's worker; returns (operator id, request id).  The
+        operator id takes solves at once (they run after the build)."""
+        b, c, d = (_check_f64(x, "coefficients", n * n) for x in (b, c, d))
+        o = _opts(precision, False, None, 0, False, split_digits, pivoting)
+        oid, rid = ctypes.c_int(), ctypes.c_longlong()
+        rc = load_library().gm_server_submit_build(self._s, ctypes.byref(o), _ptr(b), _ptr(c), _ptr(d), n, leaf,
+                                                   float(tol), ctypes.byref(oid), ctypes.byref(rid))
+        if rc:
+            raise GmError(rc, "gm_server_submit_build")
+        self._keep[rid.value] = (b, c, d)
+        self._n[oid.value] = n
+        return oid.value, rid.value
+
+    def poll(self, rid):
+        """(done, result code) without blocking."""
+        done = ctypes.c_int()
+        rc = load_library().gm_server_poll(self._s, rid, ctypes.byref(done))
+        if done.value:
+            self._keep.pop(rid, None)
+        return bool(done.value), rc
 
     def wait(self, rid):
         rc = load_library().gm_server_wait(self._s, rid)

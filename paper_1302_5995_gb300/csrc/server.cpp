@@ -6,7 +6,9 @@
 // return immediately; the worker takes every request pending when it wakes, groups them
 // by operator and runs ONE solve per operator over the concatenated vectors (continuous
 // batching), then scatters the results back.  A request's latency is measured from its
-// submission to the host seeing its result complete.
+// submission to the host seeing its result complete.  Build requests run on the worker
+// too, before the solves taken with them, and admit their operator under the budget
+// with the id reserved at submission (solves may be queued for it at once).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,6 +18,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <set>
 #include <thread>
 #include <vector>
 
@@ -32,6 +35,12 @@ struct Request {
     double *dudn;
     int batch;
     Clock::time_point t_submit;
+    // a build request (op is the id reserved for the new operator)
+    bool build = false;
+    gm_opts opts{};
+    const double *b = nullptr, *c = nullptr, *d = nullptr;
+    int n = 0, leaf = 0;
+    double tol = 0.0;
 };
 
 struct Operator {
@@ -53,6 +62,7 @@ struct gm_server {
     std::condition_variable cv_work, cv_done;
     std::deque<Request> queue;
     std::map<int, Operator> ops;
+    std::set<int> building;  // ids reserved by build requests not yet finished
     std::map<long long, int> status;  // request id -> result code once completed
     int next_op = 1;
     long long next_req = 1, tick = 0;
@@ -79,6 +89,46 @@ struct gm_server {
             return GM_ENOMEM;
         }
         cap = doubles;
+        return GM_OK;
+    }
+
+    // Evict least recently used operators (never one being served) until `need` more
+    // bytes fit the budget; false if that is impossible.  Called with mu held.
+    bool room_for(long long need) {
+        while (used + need > budget) {
+            auto victim = ops.end();
+            for (auto it = ops.begin(); it != ops.end(); ++it)
+                if (!it->second.busy && (victim == ops.end() || it->second.last_use < victim->second.last_use))
+                    victim = it;
+            if (victim == ops.end()) return false;
+            used -= victim->second.bytes;
+            gm_free(victim->second.h);
+            ops.erase(victim);
+            ++evictions;
+        }
+        return true;
+    }
+
+    // A build request: the operator is built on the worker's stream, then admitted under
+    // the budget with the id reserved at submission.  Called with mu held; unlocks it
+    // during the build.
+    int run_build(const Request &r, std::unique_lock<std::mutex> &lk) {
+        gm_opts o = r.opts;
+        o.stream = stream;
+        gm_handle *h = nullptr;
+        lk.unlock();
+        int rc = gm_build_ex(&o, r.b, r.c, r.d, r.n, r.leaf, r.tol, &h);
+        gm_info_t inf;
+        if (rc == GM_OK && (rc = gm_info(h, &inf)) != GM_OK) gm_free(h);
+        lk.lock();
+        if (rc != GM_OK) return rc;
+        const long long bytes = inf.resident_bytes;
+        if (bytes > budget || !room_for(bytes)) {
+            gm_free(h);
+            return GM_ENOMEM;
+        }
+        ops[r.op] = Operator{h, inf.n, bytes, ++tick, 0};
+        used += bytes;
         return GM_OK;
     }
 
@@ -121,10 +171,18 @@ struct gm_server {
             std::vector<Request> take(queue.begin(), queue.end());
             queue.clear();
             in_flight = (int)take.size();
-            // group by operator, in order of first arrival
+            // builds first, in arrival order, so that solves queued behind a build find it
+            for (const Request &r : take)
+                if (r.build) {
+                    status[r.id] = run_build(r, lk);
+                    building.erase(r.op);
+                    last_done = Clock::now();
+                }
+            // solves grouped by operator, in order of first arrival
             std::vector<int> order;
             std::map<int, std::vector<Request>> by_op;
             for (const Request &r : take) {
+                if (r.build) continue;
                 if (!by_op.count(r.op)) order.push_back(r.op);
                 by_op[r.op].push_back(r);
             }
@@ -160,22 +218,7 @@ struct gm_server {
 
 namespace {
 
-// Evict least recently used operators (never one being served) until `need` more
-// bytes fit the budget; false if that is impossible.
-bool make_room(gm_server *s, long long need) {
-    while (s->used + need > s->budget) {
-        auto victim = s->ops.end();
-        for (auto it = s->ops.begin(); it != s->ops.end(); ++it)
-            if (!it->second.busy && (victim == s->ops.end() || it->second.last_use < victim->second.last_use))
-                victim = it;
-        if (victim == s->ops.end()) return false;
-        s->used -= victim->second.bytes;
-        gm_free(victim->second.h);
-        s->ops.erase(victim);
-        ++s->evictions;
-    }
-    return true;
-}
+bool make_room(gm_server *s, long long need) { return s->room_for(need); }
 
 double percentile(std::vector<double> v, double q) {
     if (v.empty()) return 0.0;
@@ -225,7 +268,7 @@ int gm_server_add(gm_server *s, gm_handle *h, int *op_id) {
 int gm_server_submit(gm_server *s, int op_id, const double *g, double *dudn, int batch, long long *req_id) {
     if (!s || !g || !dudn || batch <= 0 || !req_id) return GM_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
-    if (!s->ops.count(op_id)) return GM_EINVAL;
+    if (!s->ops.count(op_id) && !s->building.count(op_id)) return GM_EINVAL;
     Request r{s->next_req++, op_id, g, dudn, batch, Clock::now()};
     if (!s->any) {
         s->first_submit = r.t_submit;
@@ -235,6 +278,39 @@ int gm_server_submit(gm_server *s, int op_id, const double *g, double *dudn, int
     *req_id = r.id;
     s->cv_work.notify_one();
     return GM_OK;
+}
+
+int gm_server_submit_build(gm_server *s, const gm_opts *opts, const double *b, const double *c, const double *d,
+                           int n, int leaf, double tol, int *op_id, long long *req_id) {
+    if (!s || !b || !c || !d || n < 2 || leaf < 4 || !(tol >= 0.0) || !op_id || !req_id) return GM_EINVAL;
+    Request r{0, 0, nullptr, nullptr, 0, Clock::now()};
+    r.build = true;
+    gm_opts_default(&r.opts);
+    if (opts) r.opts = *opts;
+    r.b = b;
+    r.c = c;
+    r.d = d;
+    r.n = n;
+    r.leaf = leaf;
+    r.tol = tol;
+    std::lock_guard<std::mutex> lk(s->mu);
+    r.id = s->next_req++;
+    r.op = s->next_op++;
+    s->building.insert(r.op);
+    s->queue.push_back(r);
+    *op_id = r.op;
+    *req_id = r.id;
+    s->cv_work.notify_one();
+    return GM_OK;
+}
+
+int gm_server_poll(gm_server *s, long long req_id, int *done) {
+    if (!s || !done) return GM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (req_id <= 0 || req_id >= s->next_req) return GM_EINVAL;
+    auto it = s->status.find(req_id);
+    *done = it != s->status.end();
+    return *done ? it->second : GM_OK;
 }
 
 int gm_server_wait(gm_server *s, long long req_id) {

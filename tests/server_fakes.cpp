@@ -1,8 +1,9 @@
 // Test-only fakes for running the serving runtime (csrc/server.cpp) on the CPU: the
-// CUDA runtime calls it makes act on host memory, and gm_solve / gm_info / gm_free act on
-// fake operators that record every call.  A gate can hold a solve inside the worker so
-// that a test can queue requests behind it (continuous batching) or try to evict an
-// operator that is being served.  Every wait here has a time limit.
+// CUDA runtime calls it makes act on host memory, gm_solve / gm_info / gm_free act on
+// fake operators that record every call, and gm_build_ex builds such operators.  A gate
+// can hold a solve inside the worker so that a test can queue requests behind it
+// (continuous batching) or try to evict an operator that is being served.  Every wait
+// here has a time limit.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -67,6 +68,26 @@ int gm_solve(gm_handle *h, const double *g, double *dudn, int batch, void *) {
     }
     if (op->solve_rc) return op->solve_rc;
     for (long long i = 0; i < 4LL * op->n * batch; ++i) dudn[i] = 1000.0 * op->tag + 2.0 * g[i];
+    return GM_OK;
+}
+
+void gm_opts_default(gm_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = GM_PREC_FP64;
+}
+
+// A build makes a fake operator tagged with its n (10 n bytes resident); n = 13 fails
+// as a singular problem.  Builds enter the call log with batch -1.
+int gm_build_ex(const gm_opts *, const double *, const double *, const double *, int n, int, double,
+                gm_handle **out) {
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        call_tag.push_back(n);
+        call_batch.push_back(-1);
+    }
+    if (n == 13) return GM_ESINGULAR;
+    *out = reinterpret_cast<gm_handle *>(new FakeOp{n, n, 0, 10LL * n});
     return GM_OK;
 }
 

@@ -103,3 +103,22 @@ def test_network_with_hbs_root_matches_the_dense_network(make):
     assert np.abs(op.dtn() - T).max() / np.abs(T).max() < 100 * tol
     G = np.ascontiguousarray(inputs.gaussian_vectors(n, 4, 23).T)
     assert np.abs(op.solve(G) - (T @ G.T).T).max() / np.abs(T @ G.T).max() < 100 * tol
+
+
+def test_server_builds_an_operator_and_serves_solves_queued_behind_it():
+    """A build request on the server's worker, a solve submitted for the new operator
+    before the build finished, and the result equal to a direct build's solve."""
+    n, leaf = 64, 8
+    b, c, d = inputs.convection_fields(n, seeds=(3, 4, 5))
+    ref = gm.build(b, c, d, n, leaf)
+    srv = gm.Server(1 << 34)
+    oid, rb = srv.submit_build(b, c, d, n, leaf)
+    G = np.ascontiguousarray(inputs.gaussian_vectors(n, 4, 31).T)  # vector j contiguous
+    out = np.zeros_like(G)
+    rs = srv.submit(oid, G, out, 4)
+    assert srv.wait(rs) == 0 and srv.wait(rb) == 0
+    assert srv.poll(rb) == (True, 0)
+    V = ref.solve(G)
+    assert np.abs(out - V).max() <= 1e-12 * np.abs(V).max()
+    assert srv.stats()["resident_ops"] == 1
+    srv.close()

@@ -15,6 +15,7 @@ import subprocess
 import numpy as np
 import pytest
 
+import paper_1302_5995_gb300 as gm
 from paper_1302_5995_gb300 import GM_EINVAL, GM_ENOMEM, GM_ECUDA, ServerStats
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -49,6 +50,9 @@ def lib(tmp_path_factory):
         "gm_server_add": (ctypes.c_int, [vp, vp, ip]),
         "gm_server_submit": (ctypes.c_int, [vp, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.POINTER(ll)]),
         "gm_server_wait": (ctypes.c_int, [vp, ll]),
+        "gm_server_submit_build": (ctypes.c_int, [vp, vp, dp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                  ip, ctypes.POINTER(ll)]),
+        "gm_server_poll": (ctypes.c_int, [vp, ll, ip]),
         "gm_server_sync": (ctypes.c_int, [vp]),
         "gm_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(ServerStats)]),
         "gm_server_reset_stats": (ctypes.c_int, [vp]),
@@ -96,6 +100,20 @@ class Server:
         rc = self.L.gm_server_submit(self.h, op, g.ctypes.data_as(dp), out.ctypes.data_as(dp), batch,
                                      ctypes.byref(rid))
         return rc, rid.value, g, out
+
+    def submit_build(self, n):
+        coef = np.zeros(n * n)  # read only by a real build
+        self.keep.append(coef)
+        dp = ctypes.POINTER(ctypes.c_double)
+        oid, rid = ctypes.c_int(), ctypes.c_longlong()
+        rc = self.L.gm_server_submit_build(self.h, None, coef.ctypes.data_as(dp), coef.ctypes.data_as(dp),
+                                           coef.ctypes.data_as(dp), n, 4, 0.0, ctypes.byref(oid), ctypes.byref(rid))
+        return rc, oid.value, rid.value
+
+    def poll(self, rid):
+        done = ctypes.c_int()
+        rc = self.L.gm_server_poll(self.h, rid, ctypes.byref(done))
+        return done.value, rc
 
     def calls(self):
         tags, batches = (ctypes.c_int * 64)(), (ctypes.c_int * 64)()
@@ -226,3 +244,55 @@ def test_argument_errors_and_destroy(lib):
         s.add(3, 10, 2)
     assert sorted(s.freed()) == [1, 2]  # destroy frees every resident operator
     lib.gm_server_destroy(None)
+
+
+def test_build_request_runs_before_the_solves_queued_for_it(lib):
+    with Server(lib) as s:
+        _, A = s.add(3, 10, 1)
+        _queue_behind_a_held_solve(s, A, 3)
+        rc, X, rb = s.submit_build(5)
+        assert rc == 0
+        rc, rs, g, out = s.submit(X, 5, 2, 7)  # the operator does not exist yet: it is being built
+        assert rc == 0
+        assert s.poll(rb) == (0, 0) and s.poll(rs) == (0, 0)
+        s.L.fake_gate(0)
+        assert s.L.gm_server_wait(s.h, rs) == 0 and s.L.gm_server_wait(s.h, rb) == 0
+        assert s.poll(rb) == (1, 0)
+        assert s.calls() == [(1, 1), (5, -1), (5, 2)]  # the build, then its solve
+        np.testing.assert_array_equal(out, 1000.0 * 5 + 2.0 * g)
+        st = s.stats()
+        assert st.resident_ops == 2 and st.resident_bytes == 10 + 50
+
+
+def test_failed_build_fails_its_queued_solves(lib):
+    with Server(lib) as s:
+        _, A = s.add(3, 10, 1)
+        _queue_behind_a_held_solve(s, A, 3)
+        rc, X, rb = s.submit_build(13)  # the fake reports a singular problem for n = 13
+        rc, rs, _, out = s.submit(X, 13, 1, 8)
+        s.L.fake_gate(0)
+        assert s.L.gm_server_wait(s.h, rb) == gm.GM_ESINGULAR
+        assert s.L.gm_server_wait(s.h, rs) == GM_EINVAL and not out.any()
+        assert s.submit(X, 13, 1, 9)[0] == GM_EINVAL  # the id never became an operator
+
+
+def test_build_requests_are_admitted_under_the_budget(lib):
+    with Server(lib, budget=100) as s:
+        _, A = s.add(3, 60, 1)
+        rc, X, rb = s.submit_build(20)  # 200 bytes: more than the whole budget
+        assert rc == 0 and s.L.gm_server_wait(s.h, rb) == GM_ENOMEM
+        rc, Y, rb = s.submit_build(5)  # 50 bytes: the least recently used operator makes room
+        assert s.L.gm_server_wait(s.h, rb) == 0
+        assert s.freed() == [20, 1]  # the refused build's operator, then the evicted one
+        st = s.stats()
+        assert st.resident_ops == 1 and st.resident_bytes == 50 and st.evictions == 1
+
+
+def test_poll_and_build_argument_errors(lib):
+    with Server(lib) as s:
+        done = ctypes.c_int()
+        assert lib.gm_server_poll(s.h, 42, ctypes.byref(done)) == GM_EINVAL
+        assert lib.gm_server_poll(None, 1, ctypes.byref(done)) == GM_EINVAL
+        oid, rid = ctypes.c_int(), ctypes.c_longlong()
+        assert lib.gm_server_submit_build(s.h, None, None, None, None, 8, 4, 0.0, ctypes.byref(oid),
+                                          ctypes.byref(rid)) == GM_EINVAL
