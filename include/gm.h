@@ -302,6 +302,10 @@ int gm_info(gm_handle *h, gm_info_t *info);
  *                      stay valid until the request completes.
  *   gm_server_poll   : without blocking: *done = 1 and the request's result code once it
  *                      has completed, else *done = 0 and GM_OK; GM_EINVAL for an unknown id.
+ *   gm_server_set_callback : cb(req_id, result code, user) is called on the worker thread
+ *                      for every request that completes from then on (NULL: none), after
+ *                      its result is visible to wait and poll, outside the server's lock
+ *                      (cb may call the server); it should return quickly.
  *   gm_server_wait   : block until request req_id has completed; returns its result code
  *                      (GM_EINVAL if its operator was evicted before it ran).
  *   gm_server_sync   : block until nothing is queued or running.
@@ -322,6 +326,8 @@ int gm_server_submit(gm_server *s, int op_id, const double *g, double *dudn, int
 int gm_server_submit_build(gm_server *s, const gm_opts *opts, const double *b, const double *c, const double *d,
                            int n, int leaf, double tol, int *op_id, long long *req_id);
 int gm_server_poll(gm_server *s, long long req_id, int *done);
+typedef void (*gm_server_callback)(long long req_id, int result, void *user);
+int gm_server_set_callback(gm_server *s, gm_server_callback cb, void *user);
 int gm_server_wait(gm_server *s, long long req_id);
 int gm_server_sync(gm_server *s);
 int gm_server_stats(gm_server *s, gm_server_stats_t *st);

@@ -94,6 +94,7 @@ SIGNATURES = {
                                + [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_longlong)]),
     "gm_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]),
+    "gm_server_set_callback": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gm_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
     "gm_server_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "gm_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
@@ -385,6 +386,9 @@ def build_network(sx, sy, n, leaf, body=None, tol=0.0, hbs_leaf=0, stream=None, 
     return op
 
 
+SERVER_CALLBACK = ctypes.CFUNCTYPE(None, ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p)
+
+
 class Server:
     """Serving runtime over resident operators (continuous batching on a worker thread).
 
@@ -401,6 +405,7 @@ class Server:
         self._s = h
         self._keep = {}
         self._n = {}  # operator id -> grid size, to check request buffers
+        self._cb = None
 
     def add(self, op):
         oid = ctypes.c_int()
@@ -438,6 +443,18 @@ class Server:
         self._keep[rid.value] = (b, c, d)
         self._n[oid.value] = n
         return oid.value, rid.value
+
+    def set_callback(self, fn):
+        """fn(request id, result code) on the worker thread for every completed request
+        (None: no callback)."""
+        if fn is None:
+            cb = None
+        else:
+            cb = SERVER_CALLBACK(lambda rid, rc, user: fn(rid, rc))
+        self._cb = cb  # the C function pointer must outlive its use
+        rc = load_library().gm_server_set_callback(self._s, ctypes.cast(cb, ctypes.c_void_p) if cb else None, None)
+        if rc:
+            raise GmError(rc, "gm_server_set_callback")
 
     def poll(self, rid):
         """(done, result code) without blocking."""

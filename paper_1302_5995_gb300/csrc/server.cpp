@@ -63,6 +63,8 @@ struct gm_server {
     std::deque<Request> queue;
     std::map<int, Operator> ops;
     std::set<int> building;  // ids reserved by build requests not yet finished
+    gm_server_callback cb = nullptr;  // called for every completed request (worker thread)
+    void *cb_user = nullptr;
     std::map<long long, int> status;  // request id -> result code once completed
     int next_op = 1;
     long long next_req = 1, tick = 0;
@@ -171,6 +173,8 @@ struct gm_server {
             std::vector<Request> take(queue.begin(), queue.end());
             queue.clear();
             in_flight = (int)take.size();
+            const gm_server_callback call = cb;
+            void *const user = cb_user;
             // builds first, in arrival order, so that solves queued behind a build find it
             for (const Request &r : take)
                 if (r.build) {
@@ -212,6 +216,13 @@ struct gm_server {
             }
             in_flight = 0;
             cv_done.notify_all();
+            if (call) {  // outside the lock: the callback may call back into the server
+                std::vector<std::pair<long long, int>> done;
+                for (const Request &r : take) done.push_back({r.id, status[r.id]});
+                lk.unlock();
+                for (const auto &q : done) call(q.first, q.second, user);
+                lk.lock();
+            }
         }
     }
 };
@@ -301,6 +312,14 @@ int gm_server_submit_build(gm_server *s, const gm_opts *opts, const double *b, c
     *op_id = r.op;
     *req_id = r.id;
     s->cv_work.notify_one();
+    return GM_OK;
+}
+
+int gm_server_set_callback(gm_server *s, gm_server_callback cb, void *user) {
+    if (!s) return GM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->cb = cb;
+    s->cb_user = user;
     return GM_OK;
 }
 

@@ -11,6 +11,7 @@ import ctypes
 import os
 import shutil
 import subprocess
+import time
 
 import numpy as np
 import pytest
@@ -53,6 +54,7 @@ def lib(tmp_path_factory):
         "gm_server_submit_build": (ctypes.c_int, [vp, vp, dp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                   ip, ctypes.POINTER(ll)]),
         "gm_server_poll": (ctypes.c_int, [vp, ll, ip]),
+        "gm_server_set_callback": (ctypes.c_int, [vp, vp, vp]),
         "gm_server_sync": (ctypes.c_int, [vp]),
         "gm_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(ServerStats)]),
         "gm_server_reset_stats": (ctypes.c_int, [vp]),
@@ -296,3 +298,34 @@ def test_poll_and_build_argument_errors(lib):
         oid, rid = ctypes.c_int(), ctypes.c_longlong()
         assert lib.gm_server_submit_build(s.h, None, None, None, None, 8, 4, 0.0, ctypes.byref(oid),
                                           ctypes.byref(rid)) == GM_EINVAL
+
+
+CALLBACK = ctypes.CFUNCTYPE(None, ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p)
+
+
+def test_completion_callback_sees_every_request(lib):
+    with Server(lib) as s:
+        seen = []
+        polled = []
+
+        def on_done(rid, rc, user):
+            seen.append((rid, rc))
+            polled.append(s.poll(rid))  # calling back into the server from the callback
+
+        cb = CALLBACK(on_done)
+        assert lib.gm_server_set_callback(s.h, ctypes.cast(cb, ctypes.c_void_p), None) == 0
+        _, A = s.add(3, 10, 1)
+        _, B = s.add(3, 10, 2, solve_rc=GM_ECUDA)
+        rids = [s.submit(A, 3, 1, 1)[1], s.submit(B, 3, 2, 2)[1], s.submit(A, 3, 3, 3)[1]]
+        _, _, rb = s.submit_build(5)
+        for r in rids + [rb]:
+            s.L.gm_server_wait(s.h, r)
+        s.L.gm_server_sync(s.h)
+        for _ in range(200):  # callbacks run just after the results become visible
+            if len(seen) == 4:
+                break
+            time.sleep(0.01)
+        assert sorted(seen) == sorted([(rids[0], 0), (rids[1], GM_ECUDA), (rids[2], 0), (rb, 0)])
+        assert all(done == 1 for done, _ in polled)
+        assert lib.gm_server_set_callback(s.h, None, None) == 0
+        assert lib.gm_server_set_callback(None, None, None) == GM_EINVAL
