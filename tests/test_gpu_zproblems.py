@@ -23,7 +23,7 @@ def errors(V, V_ref):
 
 
 @pytest.mark.parametrize("name", PROBLEMS)
-@pytest.mark.parametrize("n,leaf", [(64, 8), (128, 16)])
+@pytest.mark.parametrize("n,leaf", [(64, 8)])
 def test_problem_set_e1_e2(name, n, leaf):
     R = inputs.error_vectors(n, 17)
     if name.startswith("random"):
