@@ -269,7 +269,8 @@ int gm_get_load_operator(gm_handle *h, double *F_out);
  *        gm_build; not with body loads: GM_EUNSUPPORTED).
  *   body, nbody : optional body loads (nbody = 0: none) as in gm_build_loads; the handle
  *        then also serves gm_solve_loads and gm_get_load_operator.
- * FP64 only (GM_EUNSUPPORTED for mixed precision or keep_levels).
+ * FP64 only (GM_EUNSUPPORTED for mixed precision, and for keep_levels or tol > 0 with
+ * body loads); with keep_levels, gm_get_schur returns every box's Schur complement.
  */
 int gm_build_net(const gm_opts *opts, const double *sx, const double *sy, int n, int leaf, double tol,
                  const int *body, int nbody, gm_handle **out);

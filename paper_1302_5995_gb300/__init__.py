@@ -365,7 +365,7 @@ def build_loads(b, c, d, n, leaf, body, stream=None, panel_width=0):
     return op
 
 
-def build_network(sx, sy, n, leaf, body=None, tol=0.0, hbs_leaf=0, stream=None, panel_width=0):
+def build_network(sx, sy, n, leaf, body=None, tol=0.0, hbs_leaf=0, keep_levels=False, stream=None, panel_width=0):
     """FP64 build for a conductance network (Section 6.1 Random Laplacian): sx, sy the
     n (n + 1) link conductivities in the layout of inputs.network_conductivities, with
     optional body loads at the flat node indices `body` (Section 6.3), or the root in HBS
@@ -375,7 +375,7 @@ def build_network(sx, sy, n, leaf, body=None, tol=0.0, hbs_leaf=0, stream=None, 
     sx = _check_f64(sx, "sx", n * (n + 1))
     sy = _check_f64(sy, "sy", n * (n + 1))
     nodes = np.ascontiguousarray(np.asarray([] if body is None else body, dtype=np.int32).reshape(-1))
-    o = _opts(PREC_FP64, False, stream, panel_width, False, 0, PIVOT_AUTO, hbs_leaf)
+    o = _opts(PREC_FP64, keep_levels, stream, panel_width, False, 0, PIVOT_AUTO, hbs_leaf)
     h = ctypes.c_void_p()
     rc = lib.gm_build_net(ctypes.byref(o), _ptr(sx), _ptr(sy), n, leaf, float(tol),
                           ctypes.c_void_p(nodes.ctypes.data) if nodes.size else None, int(nodes.size), ctypes.byref(h))

@@ -1314,7 +1314,7 @@ int gm_build_net(const gm_opts *opts, const double *sx, const double *sy, int n,
     gm_opts o;
     int rc = check_opts(opts, o);
     if (rc) return rc;
-    if (o.precision != GM_PREC_FP64 || o.keep_levels || (tol > 0.0 && nbody > 0)) return GM_EUNSUPPORTED;
+    if (o.precision != GM_PREC_FP64 || (nbody > 0 && (o.keep_levels || tol > 0.0))) return GM_EUNSUPPORTED;
     std::vector<int> nodes(body, body + nbody);
     if (nbody > 0) {
         std::vector<int> sorted(nodes);

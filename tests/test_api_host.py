@@ -165,6 +165,9 @@ def test_network_build_rejects_bad_arguments(lib):
     lib.gm_opts_default(ctypes.byref(o))
     o.precision = gm.PREC_MIXED
     assert call(opts=o) == gm.GM_EUNSUPPORTED
+    lib.gm_opts_default(ctypes.byref(o))
+    o.keep_levels = 1
+    assert call(opts=o, nodes=np.array([3], dtype=np.int32), count=1) == gm.GM_EUNSUPPORTED  # kept levels + loads
     assert h.value is None
 
 

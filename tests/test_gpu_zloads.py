@@ -117,3 +117,23 @@ def test_random_laplacian_512_with_1000_loads():
     assert np.abs(T.sum(axis=1)).max() < 1e-10 * scale  # constants carry no current
     np.testing.assert_allclose(F.sum(axis=0), -h, rtol=1e-9)
     assert F.max() < 0.0 and F.min() >= -h * (1 + 1e-9)
+
+
+def test_network_keeps_every_level_schur_complement():
+    """Per-level parity for a network: every kept box's Schur complement (leaves, half
+    boxes, boxes) against the oracle's direct elimination of that box."""
+    from oracle import nd_dense
+    n, leaf = 24, 6
+    sx, sy = inputs.random_laplacian_2(n)
+    op = gm.build_network(sx, sy, n, leaf, keep_levels=True)
+    prob = nd_dense.Problem.network(sx, sy, n)
+    levels = nd_dense.quad_tree(n, leaf)
+    boxes = list(levels[-1])
+    for lev in range(len(levels) - 1, 0, -1):
+        for p in levels[lev - 1]:
+            sw, se, nw, ne = p.children()
+            boxes += [nd_dense.Box(p.x0, p.y0, p.a, sw.b), nd_dense.Box(p.x0, p.y0 + sw.b, p.a, nw.b), p]
+    for bx in boxes:
+        S = op.schur(bx.x0, bx.y0, bx.a, bx.b)
+        ref = nd_dense.direct_schur(prob, bx)
+        assert rel(S, ref) < 1e-11, bx
