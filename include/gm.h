@@ -80,7 +80,15 @@ typedef struct gm_opts {
                          elimination (0 = default 128)                                  */
     int timing_mask;  /* with timing: time only the families whose bit is set
                          (bit GM_K_*; 0 = all)                                          */
-    int reserved[2];
+    int background;   /* nonzero: every stream the build creates for itself takes the
+                         lowest priority (a build beside latency-bound solves)          */
+    int wait_limit;   /* polls of a bounded device-side wait (on the tensor cores'
+                         completion or a bulk copy) before the build gives up with
+                         GM_ETIMEOUT (0 = default 2^22, far beyond any normal wait; a
+                         negative value gives up at the first wait, which tests the
+                         path); a kernel that gives up still waits, for a fixed bound,
+                         for its own copies and products in flight before it releases
+                         its tensor memory and returns                                   */
 } gm_opts;
 
 /* Pivoting of the mixed-precision dense eliminations.
@@ -134,8 +142,8 @@ typedef struct gm_info_t {
     int hbs_max_rank;                 /* tol > 0: largest node rank                        */
     long long hbs_bytes;              /* tol > 0: device bytes of the HBS factors          */
     long long resident_bytes;         /* device bytes the handle holds after the build     */
-    int hbs_merges;                   /* tol > 0: merges solved by HBS block elimination   */
-    int pad2;
+    int hbs_merges;                   /* tol > 0: merges built by the accelerated merge   */
+    int hbs_update_rank;              /* tol > 0: largest rank of their S13 / S24 blocks   */
     long long hbs_operator_bytes;     /* tol > 0: bytes of the root operator in HBS form
                                          (D, U, V, B at the node ranks; the paper's M(n)) */
 } gm_info_t;
@@ -195,6 +203,18 @@ int gm_build_batch(int count, const gm_problem *probs, const gm_opts *opts, doub
  * returns after the result has reached the host.
  */
 int gm_solve(gm_handle *h, const double *g, double *dudn, int batch, void *stream);
+
+/*
+ * Solve stage for several operators in one call: dudn[i] = T_i g[i] for i < count, where
+ * g[i] and dudn[i] are 4 n_i x batch[i] column-major DEVICE buffers of operator hs[i]
+ * (the paper has no such call: it batches the vectors of a serving loop).  Dense
+ * operators of the same precision share one apply launch over all their vectors (a
+ * descriptor per operator); HBS operators run Algorithm 2 each.  Asynchronous on
+ * `stream`.  GM_EINVAL for a NULL array, a NULL handle, a negative batch or a host
+ * pointer.  Buffers must not overlap one another.
+ */
+int gm_solve_many(int count, gm_handle *const *hs, const double *const *g, double *const *dudn, const int *batch,
+                  void *stream);
 
 /* Copy the dense 4n x 4n DtN matrix (column-major) to T_out (host or device).  For an
  * HBS build (tol > 0) T is formed by applying the solve to the identity. */
@@ -279,10 +299,13 @@ int gm_info(gm_handle *h, gm_info_t *info);
 
 /*
  * Serving (the solve stage under load; the paper has no serving layer).  A server owns
- * the operators added to it and keeps them resident within a device-memory budget.  One
- * worker thread with its own stream takes every request pending when it wakes, groups
- * them by operator and runs one solve per operator over their concatenated vectors
- * (continuous batching), then copies each request's result back.
+ * the operators added to it and keeps them resident within a device-memory budget.
+ * Two worker threads: the solve worker, on a stream of the highest priority, takes every
+ * pending solve request whose operator exists, groups the requests by operator and
+ * applies them all in one gm_solve_many call (one launch per precision class over the
+ * vectors of every operator taken: continuous batching across operators); the build
+ * worker runs build requests one at a time on a stream of the lowest priority, so that
+ * builds and solves overlap on the device.
  *   gm_server_create : budget_bytes for the resident operators (gm_info.resident_bytes);
  *                      batching = 0 serves every request by its own solve (the unbatched
  *                      baseline).  Uses the current device.
@@ -294,24 +317,30 @@ int gm_info(gm_handle *h, gm_info_t *info);
  *                      host or device); returns at once.  g and dudn must stay valid
  *                      until the request completes.  GM_EINVAL for an unknown operator.
  *   gm_server_submit_build : queue a build of the operator for b, c, d (arguments as
- *                      gm_build_ex; opts->stream is replaced by the worker's stream); returns
- *                      at once with the request id and the id the operator will have, for
- *                      which solves may be submitted right away (they run after it).  The
- *                      worker admits the built operator like gm_server_add; the request's
- *                      result is the build's code, or GM_ENOMEM if it cannot fit (a solve
- *                      queued for a failed build then returns GM_EINVAL).  b, c, d must
- *                      stay valid until the request completes.
+ *                      gm_build_ex; opts->stream and opts->background are set by the
+ *                      server); returns at once with the request id and the id the
+ *                      operator will have, for which solves may be submitted right away
+ *                      (they wait in the queue until it is admitted).  The worker admits
+ *                      the built operator like gm_server_add; the request's result is the
+ *                      build's code, or GM_ENOMEM if it cannot fit (a solve queued for a
+ *                      failed build then returns GM_EINVAL).  b, c, d must stay valid
+ *                      until the request completes.
  *   gm_server_poll   : without blocking: *done = 1 and the request's result code once it
  *                      has completed, else *done = 0 and GM_OK; GM_EINVAL for an unknown id.
- *   gm_server_set_callback : cb(req_id, result code, user) is called on the worker thread
+ *   gm_server_set_callback : cb(req_id, result code, user) is called on a worker thread
  *                      for every request that completes from then on (NULL: none), after
  *                      its result is visible to wait and poll, outside the server's lock
- *                      (cb may call the server); it should return quickly.
+ *                      (cb may call the server); it should return quickly.  Returns after
+ *                      any callback already running with the previous function has ended
+ *                      (so `user` of that function may be released), except when called
+ *                      from a callback.
  *   gm_server_wait   : block until request req_id has completed; returns its result code
  *                      (GM_EINVAL if its operator was evicted before it ran).
- *   gm_server_sync   : block until nothing is queued or running.
+ *   gm_server_sync   : block until nothing is queued or running and no callback is
+ *                      running (a callback calling it waits for everything but itself).
  *   gm_server_stats  : latency from submission to completion (p50/p99), vectors per
- *                      second from the first submission to the last completion.
+ *                      second from the first submission to the last completion, and the
+ *                      number of (grouped) solve calls.
  * Thread-safe: any thread may submit, add, wait or read statistics.
  */
 typedef struct gm_server gm_server;
@@ -334,6 +363,12 @@ int gm_server_sync(gm_server *s);
 int gm_server_stats(gm_server *s, gm_server_stats_t *st);
 int gm_server_reset_stats(gm_server *s);
 void gm_server_destroy(gm_server *s);
+
+/* Failure injection for tests of the error paths (the paper has no counterpart): the
+ * n-th device allocation the library makes from now on (n >= 1; any thread, any call)
+ * fails as if the device were out of memory, so the call making it returns GM_ENOMEM
+ * and releases what it holds.  n = 0 turns the injection off. */
+void gm_debug_fail_alloc(long long n);
 
 /* Release the handle and its device memory.  NULL is a no-op. */
 void gm_free(gm_handle *h);

@@ -34,7 +34,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("keep_levels", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("panel_width", ctypes.c_int), ("timing", ctypes.c_int), ("split_digits", ctypes.c_int),
                 ("pivoting", ctypes.c_int), ("hbs_leaf", ctypes.c_int), ("hbs_min_edge", ctypes.c_int),
-                ("timing_mask", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("timing_mask", ctypes.c_int), ("background", ctypes.c_int), ("wait_limit", ctypes.c_int)]
 
 K_FAMILIES = ["leaf", "assemble", "panel", "pivrows", "gj_update", "merge_update", "root"]
 
@@ -48,7 +48,7 @@ class Info(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int * 7), ("pivoting", ctypes.c_int),
                 ("pivot_fallback", ctypes.c_int), ("refine_ratio", ctypes.c_double), ("hbs_levels", ctypes.c_int),
                 ("hbs_max_rank", ctypes.c_int), ("hbs_bytes", ctypes.c_longlong), ("resident_bytes", ctypes.c_longlong),
-                ("hbs_merges", ctypes.c_int), ("pad2", ctypes.c_int), ("hbs_operator_bytes", ctypes.c_longlong)]
+                ("hbs_merges", ctypes.c_int), ("hbs_update_rank", ctypes.c_int), ("hbs_operator_bytes", ctypes.c_longlong)]
 
 
 class ServerStats(ctypes.Structure):
@@ -73,6 +73,8 @@ SIGNATURES = {
     "gm_build_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Problem), ctypes.POINTER(Opts), ctypes.c_double,
                                       ctypes.POINTER(ctypes.c_void_p)]),
     "gm_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "gm_solve_many": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                     ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
     "gm_get_dtn": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gm_get_schur": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 4 + [ctypes.c_void_p]),
     "gm_solve_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
@@ -100,6 +102,7 @@ SIGNATURES = {
     "gm_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
     "gm_server_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
     "gm_server_destroy": (None, [ctypes.c_void_p]),
+    "gm_debug_fail_alloc": (None, [ctypes.c_longlong]),
     "gm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -288,7 +291,31 @@ class DtN:
         return out
 
 
-def _opts(precision, keep_levels, stream, panel_width, timing, split_digits, pivoting, hbs_leaf=0, hbs_min_edge=0):
+def solve_many(ops, gs, outs, stream=None):
+    """dudn_i = T_i g_i for several operators in one call (gm_solve_many): g_i and out_i
+    are device tensors of shape (batch_i, 4 n_i), vector j contiguous.  Dense operators of
+    one precision share one apply launch."""
+    k = len(ops)
+    if not (len(gs) == k == len(outs)):
+        raise ValueError("ops, gs and outs differ in length")
+    hs = (ctypes.c_void_p * k)()
+    gp = (ctypes.c_void_p * k)()
+    vp = (ctypes.c_void_p * k)()
+    bt = (ctypes.c_int * k)()
+    for i, (op, g, o) in enumerate(zip(ops, gs, outs)):
+        if not (hasattr(g, "is_cuda") and g.is_cuda and hasattr(o, "is_cuda") and o.is_cuda):
+            raise ValueError("solve_many takes device tensors")
+        B = _batch(g, 4 * op.n, "g")
+        _check_f64(o, "out", 4 * op.n * B)
+        hs[i], gp[i], vp[i], bt[i] = op._h, _ptr(g), _ptr(o), B
+    rc = load_library().gm_solve_many(k, hs, gp, vp, bt, _stream_handle(stream))
+    if rc:
+        raise GmError(rc, "gm_solve_many")
+    return outs
+
+
+def _opts(precision, keep_levels, stream, panel_width, timing, split_digits, pivoting, hbs_leaf=0, hbs_min_edge=0,
+          wait_limit=0):
     """timing: False, True (every family) or a list of family names to time."""
     lib = load_library()
     o = Opts()
@@ -304,6 +331,7 @@ def _opts(precision, keep_levels, stream, panel_width, timing, split_digits, piv
     o.pivoting = pivoting
     o.hbs_leaf = hbs_leaf
     o.hbs_min_edge = hbs_min_edge
+    o.wait_limit = wait_limit
     return o
 
 
@@ -328,7 +356,7 @@ def build_batch(problems, tol=0.0, precision=PREC_FP64, stream=None, panel_width
 
 
 def build(b, c, d, n, leaf, tol=0.0, precision=PREC_FP64, keep_levels=False, stream=None, panel_width=0,
-          timing=False, split_digits=0, pivoting=PIVOT_AUTO, hbs_leaf=0, hbs_min_edge=0):
+          timing=False, split_digits=0, pivoting=PIVOT_AUTO, hbs_leaf=0, hbs_min_edge=0, wait_limit=0):
     """Build the DtN operator for coefficient fields b, c, d (n*n each, index i + n*j).
 
     tol > 0 compresses the root Schur complement to HBS form (node size hbs_leaf) and
@@ -337,7 +365,8 @@ def build(b, c, d, n, leaf, tol=0.0, precision=PREC_FP64, keep_levels=False, str
     b = _check_f64(b, "b", n * n)
     c = _check_f64(c, "c", n * n)
     d = _check_f64(d, "d", n * n)
-    o = _opts(precision, keep_levels, stream, panel_width, timing, split_digits, pivoting, hbs_leaf, hbs_min_edge)
+    o = _opts(precision, keep_levels, stream, panel_width, timing, split_digits, pivoting, hbs_leaf, hbs_min_edge,
+              wait_limit)
     h = ctypes.c_void_p()
     rc = lib.gm_build_ex(ctypes.byref(o), _ptr(b), _ptr(c), _ptr(d), n, leaf, float(tol), ctypes.byref(h))
     if rc:

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -69,6 +70,26 @@ int alloc_error(cudaError_t e) {
     return e == cudaErrorMemoryAllocation ? GM_ENOMEM : GM_ECUDA;
 }
 
+// Allocation-failure injection (gm_debug_fail_alloc): when the countdown reaches 1, that
+// device allocation fails as if the device were out of memory.
+std::atomic<long long> g_fail_countdown{0};
+bool injected_failure() {
+    long long c = g_fail_countdown.load();
+    while (c > 0) {
+        if (g_fail_countdown.compare_exchange_weak(c, c - 1)) return c == 1;
+    }
+    return false;
+}
+
+// cudaMalloc with the injection point (the handle's long-lived buffers).
+cudaError_t lib_malloc(void **p, size_t bytes) {
+    if (injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 cudaMemPool_t lib_pool() {
     static std::mutex mu;
     static std::map<int, cudaMemPool_t> pools;
@@ -108,6 +129,7 @@ struct DBuf {
         release();
         s = st;
         if (bytes == 0) bytes = 16;
+        if (injected_failure()) return GM_ENOMEM;
         cudaMemPool_t pool = lib_pool();
         const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, st) : cudaMallocAsync(&p, bytes, st);
         if (e != cudaSuccess) {
@@ -135,10 +157,11 @@ struct LookAhead {
         if (s1) cudaStreamDestroy(s1);
         if (s2) cudaStreamDestroy(s2);
     }
-    bool create() {
+    // background: both streams at the lowest priority (the build yields to other work)
+    bool create(bool background) {
         int least = 0, greatest = 0;
         if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
-            cudaStreamCreateWithPriority(&s1, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&s1, cudaStreamNonBlocking, background ? least : greatest) != cudaSuccess ||
             cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, least) != cudaSuccess ||
             cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess ||
@@ -186,7 +209,7 @@ std::map<PlanKey, std::shared_ptr<DevPlan>> g_plans;
 
 template <class T> int upload(T **dst, const std::vector<T> &v) {
     size_t bytes = v.size() * sizeof(T);
-    const cudaError_t e = cudaMalloc((void **)dst, bytes ? bytes : 16);
+    const cudaError_t e = lib_malloc((void **)dst, bytes ? bytes : 16);
     if (e != cudaSuccess) return alloc_error(e);
     if (bytes && cudaMemcpy(*dst, v.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) return GM_ECUDA;
     return GM_OK;
@@ -302,6 +325,18 @@ void event_pool_put(cudaEvent_t e) {
     std::lock_guard<std::mutex> lk(g_ev_mu);
     g_ev_pool.push_back(e);
 }
+int dev_alloc(void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (injected_failure()) return GM_ENOMEM;
+    cudaMemPool_t pool = lib_pool();
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return alloc_error(e);
+    }
+    return GM_OK;
+}
 }  // namespace gm
 
 struct gm_handle {
@@ -377,7 +412,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
         h->kept_df32 = mixed;
     }
     int rc;
-    int hbs_merges = 0, hbs_rank = 0;
+    int hbs_merges = 0, hbs_rank = 0, hbs_lr_rank = 0;
     const size_t np = H.size();
     DBuf stat;
     if ((rc = stat.alloc(np * sizeof(Status), s))) return rc;
@@ -387,13 +422,15 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
     KTimer kt;
     kt.on = o.timing != 0;
     if (o.timing_mask) kt.mask = (unsigned)o.timing_mask;
+    // 0: the default bound; a negative limit gives up at the first wait (tests the path)
+    const int wait_limit = o.wait_limit != 0 ? o.wait_limit : (1 << 22);
 
     // the arena: FP64, or double-float pairs (same 8 bytes per element)
     DBuf arena_buf;
     void *arena = nullptr;
     const size_t arena_bytes = (size_t)P.arena_doubles * 8;
     if (o.keep_levels) {
-        if (cudaMalloc(&arena, arena_bytes ? arena_bytes : 16) != cudaSuccess) {
+        if (lib_malloc(&arena, arena_bytes ? arena_bytes : 16) != cudaSuccess) {
             cudaGetLastError();
             return GM_ENOMEM;
         }
@@ -471,7 +508,8 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
                 bscr.rdig[q] = brdig.as<__nv_bfloat16>() + (size_t)q * split * max_cols * 64;
                 bscr.rex[q] = brex.as<int>() + (size_t)q * max_cols;
             }
-            if (!la.create()) return GM_ECUDA;
+            if (!la.create(o.background != 0)) return GM_ECUDA;
+            bscr.wait_limit = wait_limit;
             bscr.s1 = la.s1;
             bscr.s2 = la.s2;
             bscr.ev_r = la.a;
@@ -528,6 +566,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             // interface system by the accelerated Step 1 (HBS inverses of S33 and of its
             // Schur complement); the others, and any whose ranks exceed the cap, stay dense
             std::vector<SysDesc> dense;
+            std::vector<int> hbs_idx;  // merges of this stage solved by the accelerated merge
             bool any_hbs = false;
             for (int i = 0; i < ds.nm; ++i) {
                 const MergeDesc &md = hs.merges[i];
@@ -539,6 +578,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
                     if (rc == GM_OK) {
                         ++hbs_merges;
                         any_hbs = true;
+                        hbs_idx.push_back(i);
                         continue;
                     }
                     if (rc != GM_EUNSUPPORTED) return rc;
@@ -562,15 +602,43 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
                 CK(cudaMemcpyAsync(dsub.p, dense.data(), dense.size() * sizeof(SysDesc), cudaMemcpyHostToDevice, s));
                 CK(sweep(dsub.as<SysDesc>(), dense, mm, mc, ws.p, ro, co, (int)si + 1));
             }
-            CK(launch_merge_update(ds.d_merges, hs.merges, ds.d_tab, A64, ws.as<double>(), A64, ds.max_rp, db, dc, dd,
-                                   0, s, kt));
+            if (hbs_idx.empty()) {
+                CK(launch_merge_update(ds.d_merges, hs.merges, ds.d_tab, A64, ws.as<double>(), A64, ds.max_rp, db, dc,
+                                       dd, 0, s, kt));
+            } else {
+                // Steps 2-3 of the accelerated merge for the merges solved by Step 1: S13,
+                // S24 compressed, the update in factored form; the others as usual
+                std::vector<MergeDesc> dm;
+                for (int i = 0, j = 0; i < ds.nm; ++i) {
+                    if (j < (int)hbs_idx.size() && hbs_idx[j] == i) {
+                        ++j;
+                        continue;
+                    }
+                    dm.push_back(hs.merges[i]);
+                }
+                if (!dm.empty()) {
+                    DBuf dsub;
+                    if ((rc = dsub.alloc(dm.size() * sizeof(MergeDesc), s))) return rc;
+                    CK(cudaMemcpyAsync(dsub.p, dm.data(), dm.size() * sizeof(MergeDesc), cudaMemcpyHostToDevice, s));
+                    int mrp = 0;
+                    for (const MergeDesc &q : dm) mrp = std::max(mrp, q.rp);
+                    CK(launch_merge_update(dsub.as<MergeDesc>(), dm, ds.d_tab, A64, ws.as<double>(), A64, mrp, db, dc,
+                                           dd, 0, s, kt));
+                }
+                for (int i : hbs_idx) {
+                    if ((rc = hbs_merge_lowrank(hs.merges[i], ds.d_merges + i, ds.d_tab, A64,
+                                                ws.as<double>() + ds.h_sys[i].off, A64, db, dc, dd, tol, s, kt,
+                                                &hbs_lr_rank)))
+                        return rc;
+                }
+            }
         } else {
             CK(mx_merge_assemble(ds.d_merges, ds.nm, ds.d_tab, Adf, ws.as<float2>(), ds.max_elems, db, dc, dd, 0, s,
                                  kt));
             CK(sweep(ds.d_sys, ds.h_sys, ds.max_m, ds.max_ncol, ws.p, ds.sum_rows, ds.sum_cols, (int)si + 1));
             CK(mx_merge_update(ds.d_merges, hs.merges, ds.d_tab, Adf, ws.as<float2>(), Adf, ds.max_rp, split,
                                ydig.as<__nv_bfloat16>(), yex.as<int>(), xdig.as<__nv_bfloat16>(), xex.as<int>(),
-                               ds.dig_elems, db, dc, dd, 0, dst, s, kt));
+                               ds.dig_elems, db, dc, dd, 0, dst, s, kt, wait_limit));
         }
         stamp();
     }
@@ -623,7 +691,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
         gm_handle *h = H[r.problem];
         const int nb4 = 4 * r.n;
         const SysDesc &sy = dp.h_root_sys[i];
-        if (cudaMalloc(&h->T, (size_t)nb4 * nb4 * 8) != cudaSuccess) {
+        if (lib_malloc((void **)&h->T, (size_t)nb4 * nb4 * 8) != cudaSuccess) {
             cudaGetLastError();
             return GM_ENOMEM;
         }
@@ -631,9 +699,9 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             CK(launch_root_finalize(rws.as<double>() + sy.off, r.r, r.n, h->T, s, kt));
         } else {
             const int kpadT = mx_kpad(nb4);
-            if (cudaMalloc(&h->Tdf, (size_t)nb4 * nb4 * sizeof(float2)) != cudaSuccess ||
-                cudaMalloc(&h->tdig, (size_t)split * nb4 * kpadT * 2) != cudaSuccess ||
-                cudaMalloc(&h->tex, (size_t)nb4 * sizeof(int)) != cudaSuccess) {
+            if (lib_malloc((void **)&h->Tdf, (size_t)nb4 * nb4 * sizeof(float2)) != cudaSuccess ||
+                lib_malloc((void **)&h->tdig, (size_t)split * nb4 * kpadT * 2) != cudaSuccess ||
+                lib_malloc((void **)&h->tex, (size_t)nb4 * sizeof(int)) != cudaSuccess) {
                 cudaGetLastError();
                 return GM_ENOMEM;
             }
@@ -684,6 +752,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
         hi.dtn_bytes = h->hbs ? 0 : (long long)16 * h->n * h->n * 8;
         hi.hbs_merges = hbs_merges;
         hi.hbs_max_rank = hbs_rank;
+        hi.hbs_update_rank = hbs_lr_rank;
         if (h->hbs) {
             hi.hbs_levels = h->hbs->L;
             hi.hbs_max_rank = std::max(hbs_rank, h->hbs->max_rank);
@@ -872,6 +941,8 @@ int check_opts(const gm_opts *opts, gm_opts &o) {
 
 extern "C" {
 
+void gm_debug_fail_alloc(long long n) { g_fail_countdown.store(n > 0 ? n : 0); }
+
 void gm_opts_default(gm_opts *o) {
     if (!o) return;
     memset(o, 0, sizeof(*o));
@@ -1014,6 +1085,68 @@ int gm_solve(gm_handle *h, const double *g, double *dudn, int batch, void *strea
         gbuf.release();
         vbuf.release();
         CK(cudaStreamSynchronize(s));
+    }
+    return GM_OK;
+}
+
+int gm_solve_many(int count, gm_handle *const *hs, const double *const *g, double *const *dudn, const int *batch,
+                  void *stream) {
+    if (count < 0 || (count > 0 && (!hs || !g || !dudn || !batch))) return GM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < count; ++i) {
+        if (!hs[i] || batch[i] < 0) return GM_EINVAL;
+        if (batch[i] == 0) continue;
+        if (!g[i] || !dudn[i] || !is_device_ptr(g[i]) || !is_device_ptr(dudn[i])) return GM_EINVAL;
+    }
+    std::vector<ApplyDesc> f64;
+    std::map<int, std::vector<MxApplyDesc>> mx;  // by digits per operand
+    std::map<int, int64_t> mx_planes, mx_cols;
+    int rc;
+    for (int i = 0; i < count; ++i) {
+        gm_handle *h = hs[i];
+        const int B = batch[i], N = 4 * h->n;
+        if (B == 0) continue;
+        if (h->hbs) {  // Algorithm 2 per operator
+            if ((rc = hbs_apply_dtn(*h->hbs, g[i], dudn[i], B, s))) return rc;
+        } else if (h->precision == GM_PREC_MIXED) {
+            const int kpad = mx_kpad(N);
+            MxApplyDesc q{};
+            q.tdig = h->tdig;
+            q.tex = h->tex;
+            q.G = g[i];
+            q.V = dudn[i];
+            q.gplane = (int64_t)B * kpad;
+            q.N = N;
+            q.B = B;
+            q.kpad = kpad;
+            mx[h->split].push_back(q);
+            mx_planes[h->split] += q.gplane;
+            mx_cols[h->split] += B;
+        } else {
+            f64.push_back(ApplyDesc{h->T, g[i], dudn[i], N, B, 0, 0});
+        }
+    }
+    DBuf d1;
+    if (!f64.empty()) {
+        if ((rc = d1.alloc(f64.size() * sizeof(ApplyDesc), s))) return rc;
+        CK(launch_apply_many(f64, d1.as<ApplyDesc>(), s));
+    }
+    for (auto &kv : mx) {
+        const int split = kv.first;
+        std::vector<MxApplyDesc> &v = kv.second;
+        DBuf dd, dig, ex;
+        if ((rc = dd.alloc(v.size() * sizeof(MxApplyDesc), s)) ||
+            (rc = dig.alloc((size_t)split * mx_planes[split] * 2, s)) ||
+            (rc = ex.alloc((size_t)mx_cols[split] * sizeof(int), s)))
+            return rc;
+        int64_t po = 0, eo = 0;
+        for (MxApplyDesc &q : v) {  // each operator's planes: split consecutive planes of gplane elements
+            q.gdig = dig.as<__nv_bfloat16>() + po;
+            q.gex = ex.as<int>() + eo;
+            po += (int64_t)split * q.gplane;
+            eo += q.B;
+        }
+        CK(mx_apply_many(v, dd.as<MxApplyDesc>(), split, s));
     }
     return GM_OK;
 }

@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
 k_blk_update_tc(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, int mode,
                 const __nv_bfloat16 *__restrict__ fdig, int64_t fplane, const int *__restrict__ fex,
                 const __nv_bfloat16 *__restrict__ rdig, int64_t rplane, const int *__restrict__ rex,
-                Status *__restrict__ st) {
+                Status *__restrict__ st, int limit) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *Fs = base;                                  // S x 16 KB
@@ -699,11 +699,7 @@ k_blk_update_tc(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k,
         const int j = j0 + 32 * h + c;
         w[c] = (live && j < Sy.ncol) ? W[(size_t)j * m + i] : make_float2(0.f, 0.f);
     }
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 20) && !done; ++it)
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(done)
-                     : "r"(smem_u32(&mbar)), "r"(0));
+    const bool done = mbar_wait_bounded(&mbar, 0, limit);
     if (tid == 0) s_ok = 1;
     __syncthreads();
     if (!done) {
@@ -711,6 +707,9 @@ k_blk_update_tc(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k,
         if (lane == 0 && atomicCAS(&st[Sy.prob].code, 0, GM_ETIMEOUT) == 0) st[Sy.prob].where = -1;
     }
     __syncthreads();
+    // gave up: the products already issued still write this CTA's tensor memory; wait
+    // (bounded) for their commit before the memory is released below
+    if (!s_ok && tid == 0) mbar_wait_bounded(&mbar, 0, DRAIN_POLLS);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     if (s_ok) {
         const int fe = s_fe[row];
@@ -860,7 +859,7 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
             kt.begin(GM_K_GJUPDATE, fl_upd, c);
             BLK_SPLIT_DISPATCH(split, (k_blk_update_tc<SS><<<dim3(nrt128, cb, nsys), TILE_THREADS, tsm, c>>>(
                                           d_sys, ws, k, UPD_ALL, scr.fdig[par], scr.fplane, scr.fex[par],
-                                          scr.rdig[par], scr.cplane, scr.rex[par], st)));
+                                          scr.rdig[par], scr.cplane, scr.rex[par], st, scr.wait_limit)));
             kt.end(c);
             continue;
         }
@@ -876,7 +875,7 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
         kt.begin(GM_K_GJUPDATE, fl_upd - fl_next, scr.s2);
         BLK_SPLIT_DISPATCH(split, (k_blk_update_tc<SS><<<dim3(nrt128, cb - 1, nsys), TILE_THREADS, tsm, scr.s2>>>(
                                       d_sys, ws, k, UPD_REST, scr.fdig[par], scr.fplane, scr.fex[par],
-                                      scr.rdig[par], scr.cplane, scr.rex[par], st)));
+                                      scr.rdig[par], scr.cplane, scr.rex[par], st, scr.wait_limit)));
         kt.end(scr.s2);
         if ((e = cudaEventRecord(scr.ev_rest, scr.s2)) != cudaSuccess) return e;
         pending = true;

@@ -30,6 +30,7 @@ struct BlkScratch {
     // (the rest done) and ev_join (entry and exit of the sweep)
     cudaStream_t s1 = nullptr, s2 = nullptr;
     cudaEvent_t ev_r = nullptr, ev_rest = nullptr, ev_join = nullptr;
+    int wait_limit = 1 << 22;  // polls of the tensor-core completion wait before GM_ETIMEOUT
 };
 
 size_t blk_factor_smem(int split);

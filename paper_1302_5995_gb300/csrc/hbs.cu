@@ -11,12 +11,15 @@
 // column-pivoted Gram-Schmidt QR in shared memory (one CTA per node), truncated at the
 // first |R_jj| <= tol |R_11|.  The dense inversions of Algorithm 1 reuse the batched
 // Gauss-Jordan sweep on [M | I].  Ranks are read back once per level.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "hbs.h"
@@ -133,21 +136,32 @@ __global__ void k_hbs_copy(const CopyDesc *__restrict__ ds) {
     }
 }
 
-// Basis of the column space of A (p x l, p <= QR_MAXP, l <= HBS_SAMPLES) by Gram-Schmidt
-// with column pivoting: at step j the remaining column of largest norm is orthogonalised
-// (twice) against Q(:, 0..j-1), normalised into Q(:, j) and removed from the others.
+// Basis of the column space of A (p x l) by Gram-Schmidt with column pivoting: at step j
+// the remaining column of largest norm is re-orthogonalised against Q(:, 0..j-1),
+// normalised into Q(:, j) and removed from every other remaining column.
 // out[0] = first j with |R_jj| <= tol |R_11| (or the steps taken), out[1] = columns of
-// Q produced (stops at kmax or at a numerically zero column).
-constexpr int QR_MAXP = 2 * HBS_KCAP;
+// Q produced.  The sweep stops at a numerically zero column, after kmax columns, or
+// `margin` columns past the truncation point (the partner basis of the same node may
+// truncate a little later; one rank serves both).
+//
+// Two kernels: a single CTA with A in shared memory for small samples (p <= QR_MAXP,
+// l <= HBS_SAMPLES), and a thread-block cluster for large ones (k_hbs_pqr_cl).
+constexpr int QR_MAXP = 192;
 
 struct QrDesc {
-    const double *A;
-    double *Q;
-    int *out;
+    const double *A;  // p x l sample (read only)
+    double *Q;        // p x (columns produced), ld ldq
+    int *out;         // [truncation point, columns produced]
+    double *W;        // p x l work copy (cluster kernel only)
     int p, l, lda, ldq;
 };
 
-__global__ void __launch_bounds__(256) k_hbs_pqr(const QrDesc *__restrict__ ds, double tol, int kmax) {
+__device__ __forceinline__ double warp_sum_d(double s) {
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+__global__ void __launch_bounds__(256) k_hbs_pqr(const QrDesc *__restrict__ ds, double tol, int kmax, int margin) {
     extern __shared__ double sA[];  // [l][p] column-major
     __shared__ double nrm[HBS_SAMPLES];
     __shared__ double qv[QR_MAXP];
@@ -171,7 +185,7 @@ __global__ void __launch_bounds__(256) k_hbs_pqr(const QrDesc *__restrict__ ds, 
             double s = 0.0;
             if (!used[c])
                 for (int i = lane; i < p; i += 32) s = fma(sA[(size_t)c * p + i], sA[(size_t)c * p + i], s);
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            s = warp_sum_d(s);
             if (lane == 0) nrm[c] = used[c] ? -1.0 : s;
         }
         __syncthreads();
@@ -188,14 +202,14 @@ __global__ void __launch_bounds__(256) k_hbs_pqr(const QrDesc *__restrict__ ds, 
         const int pv = s_piv;
         const double rjj = s_r, r11 = s_r1;
         if (ktr < 0 && !(rjj > tol * r11)) ktr = j;
-        if (pv < 0 || !(rjj > 1e-15 * r11) || !(r11 > 0.0)) break;
+        if (pv < 0 || !(rjj > 1e-15 * r11) || !(r11 > 0.0) || (ktr >= 0 && j >= ktr + margin)) break;
         for (int i = tid; i < p; i += blockDim.x) qv[i] = sA[(size_t)pv * p + i];
         __syncthreads();
         for (int pass = 0; pass < 2; ++pass) {  // q -= Q (Q^T q), twice
             for (int c = warp; c < j; c += nw) {
                 double s = 0.0;
                 for (int i = lane; i < p; i += 32) s = fma(D.Q[i + (size_t)c * D.ldq], qv[i], s);
-                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                s = warp_sum_d(s);
                 if (lane == 0) coef[c] = s;
             }
             __syncthreads();
@@ -209,7 +223,7 @@ __global__ void __launch_bounds__(256) k_hbs_pqr(const QrDesc *__restrict__ ds, 
         if (warp == 0) {
             double s = 0.0;
             for (int i = lane; i < p; i += 32) s = fma(qv[i], qv[i], s);
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            s = warp_sum_d(s);
             if (lane == 0) s_r = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
         }
         __syncthreads();
@@ -225,7 +239,7 @@ __global__ void __launch_bounds__(256) k_hbs_pqr(const QrDesc *__restrict__ ds, 
             if (used[c]) continue;
             double s = 0.0;
             for (int i = lane; i < p; i += 32) s = fma(qv[i], sA[(size_t)c * p + i], s);
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            s = warp_sum_d(s);
             for (int i = lane; i < p; i += 32) sA[(size_t)c * p + i] = fma(-s, qv[i], sA[(size_t)c * p + i]);
         }
         __syncthreads();
@@ -235,6 +249,178 @@ __global__ void __launch_bounds__(256) k_hbs_pqr(const QrDesc *__restrict__ ds, 
         D.out[0] = ktr < 0 ? kval : ktr;
         D.out[1] = kval;
     }
+}
+
+// The same factorisation on a thread-block cluster: the CTAs of a cluster share one
+// sample, CTA c owning the columns g = c + cs i (cs = cluster size).  The columns live in
+// a global work copy W (L2-resident), read and written through L2 only, so that every
+// CTA sees the others' latest values.  One step:
+//   1. each CTA offers its unused column of largest norm; after a cluster barrier every
+//      CTA reads all offers from distributed shared memory and takes the same pivot
+//      (largest norm, lowest column on ties);
+//   2. each CTA forms the part of Q (Q^T a) that falls on its own columns of Q and
+//      publishes it in its shared memory; after a second barrier every CTA subtracts all
+//      parts in the same order and normalises, so all hold the same q bit for bit; the
+//      pivot's owner stores it as Q(:, j);
+//   3. each CTA removes q from its unused columns and refreshes their norms.
+// Offers and parts alternate between two buffers, so two barriers per step suffice; a
+// final barrier keeps every CTA's shared memory alive until the others are done with it.
+constexpr int QRC_THREADS = 512;
+constexpr int QRC_LOC = HBS_MAX_SAMPLES / 8;  // columns per CTA at the smallest cluster (8)
+constexpr int QRC_MAXP = 8000;                // rows: 3 p doubles of dynamic shared memory
+
+__global__ void __launch_bounds__(QRC_THREADS) k_hbs_pqr_cl(const QrDesc *__restrict__ ds, double tol, int kmax,
+                                                           int margin) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int cs = (int)cl.num_blocks(), cr = (int)cl.block_rank();
+    const QrDesc D = ds[blockIdx.x / cs];
+    extern __shared__ double smx[];  // qv[p], part[2][p]
+    __shared__ double nrm[QRC_LOC];
+    __shared__ unsigned char used[QRC_LOC];
+    __shared__ double coef[QRC_LOC];
+    __shared__ double offer_v[2];
+    __shared__ int offer_c[2];
+    __shared__ double red[QRC_THREADS / 32];
+    __shared__ int s_piv;
+    __shared__ double s_best, s_inv;
+    const int p = D.p, l = D.l, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    double *qv = smx, *part = smx + p;
+    const int nloc = cr < l ? (l - cr + cs - 1) / cs : 0;
+    // my columns into the work copy, with their norms
+    for (int i = warp; i < nloc; i += nw) {
+        const int g = cr + cs * i;
+        const double *a = D.A + (size_t)g * D.lda;
+        double *w = D.W + (size_t)g * p;
+        double s = 0.0;
+        for (int x = lane; x < p; x += 32) {
+            const double v = a[x];
+            __stcg(w + x, v);
+            s = fma(v, v, s);
+        }
+        s = warp_sum_d(s);
+        if (lane == 0) {
+            nrm[i] = s;
+            used[i] = 0;
+        }
+    }
+    __syncthreads();
+    int ktr = -1, kval = 0;
+    double r11 = 0.0;
+    const int steps = min(kmax, min(p, l));
+    for (int j = 0; j < steps; ++j) {
+        const int buf = j & 1;
+        if (warp == 0) {  // my offer: largest unused norm, lowest column on ties
+            double bv = -1.0;
+            int bc = 0x7fffffff;
+            for (int i = lane; i < nloc; i += 32)
+                if (!used[i] && nrm[i] > bv) {
+                    bv = nrm[i];
+                    bc = cr + cs * i;
+                }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+                if (ov > bv || (ov == bv && oc < bc)) {
+                    bv = ov;
+                    bc = oc;
+                }
+            }
+            if (lane == 0) {
+                offer_v[buf] = bv;
+                offer_c[buf] = bc;
+            }
+        }
+        cl.sync();
+        if (tid == 0) {
+            double bv = -1.0;
+            int bc = 0x7fffffff;
+            for (int q = 0; q < cs; ++q) {
+                const double v = *cl.map_shared_rank(&offer_v[buf], q);
+                const int c = *cl.map_shared_rank(&offer_c[buf], q);
+                if (v > bv || (v == bv && c < bc)) {
+                    bv = v;
+                    bc = c;
+                }
+            }
+            s_piv = bv >= 0.0 ? bc : -1;
+            s_best = bv;
+        }
+        __syncthreads();
+        const int pv = s_piv;
+        const double rjj = s_best > 0.0 ? sqrt(s_best) : 0.0;
+        if (j == 0) r11 = rjj;
+        if (ktr < 0 && !(rjj > tol * r11)) ktr = j;
+        if (pv < 0 || !(rjj > 1e-15 * r11) || !(r11 > 0.0) || (ktr >= 0 && j >= ktr + margin)) break;
+        const double *wp = D.W + (size_t)pv * p;
+        for (int x = tid; x < p; x += blockDim.x) qv[x] = __ldcg(wp + x);
+        __syncthreads();
+        // my part of Q (Q^T a): the columns t of Q with t = cr (mod cs), t < j
+        const int nq = j > cr ? (j - cr + cs - 1) / cs : 0;
+        for (int t = warp; t < nq; t += nw) {
+            const double *qc = D.Q + (size_t)(cr + cs * t) * D.ldq;
+            double s = 0.0;
+            for (int x = lane; x < p; x += 32) s = fma(__ldcg(qc + x), qv[x], s);
+            s = warp_sum_d(s);
+            if (lane == 0) coef[t] = s;
+        }
+        __syncthreads();
+        double *pb = part + (size_t)buf * p;
+        for (int x = tid; x < p; x += blockDim.x) {
+            double v = 0.0;
+            for (int t = 0; t < nq; ++t) v = fma(coef[t], __ldcg(D.Q + x + (size_t)(cr + cs * t) * D.ldq), v);
+            pb[x] = v;
+        }
+        cl.sync();
+        double ss = 0.0;
+        for (int x = tid; x < p; x += blockDim.x) {
+            double v = qv[x];
+            for (int q = 0; q < cs; ++q) v -= cl.map_shared_rank(pb, q)[x];
+            qv[x] = v;
+            ss = fma(v, v, ss);
+        }
+        ss = warp_sum_d(ss);
+        if (lane == 0) red[warp] = ss;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += red[w];
+            s_inv = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+        }
+        __syncthreads();
+        const double inv = s_inv;
+        const bool owner = pv % cs == cr;
+        for (int x = tid; x < p; x += blockDim.x) {
+            const double v = qv[x] * inv;
+            qv[x] = v;
+            if (owner) __stcg(D.Q + x + (size_t)j * D.ldq, v);
+        }
+        if (owner && tid == 0) used[pv / cs] = 1;
+        __syncthreads();
+        // remove q from my unused columns, refresh their norms
+        for (int i = warp; i < nloc; i += nw) {
+            if (used[i]) continue;
+            double *w = D.W + (size_t)(cr + cs * i) * p;
+            double s = 0.0;
+            for (int x = lane; x < p; x += 32) s = fma(qv[x], __ldcg(w + x), s);
+            s = warp_sum_d(s);
+            double nn = 0.0;
+            for (int x = lane; x < p; x += 32) {
+                const double v = fma(-s, qv[x], __ldcg(w + x));
+                __stcg(w + x, v);
+                nn = fma(v, v, nn);
+            }
+            nn = warp_sum_d(nn);
+            if (lane == 0) nrm[i] = nn;
+        }
+        __syncthreads();
+        kval = j + 1;
+    }
+    if (cr == 0 && tid == 0) {
+        D.out[0] = ktr < 0 ? kval : ktr;
+        D.out[1] = kval;
+    }
+    cl.sync();
 }
 
 // With c == nullptr, b is a table of five weights per node (a conductance network).
@@ -418,9 +604,12 @@ struct Bump {
 
 // Batched inversion of square matrices in place: each sys (m x 2m, ld m) holds [M | I];
 // after the sweep its right half is M^{-1}.
-int invert_batch(const std::vector<std::pair<double *, int>> &mats, double *base, cudaStream_t s) {
+int invert_batch(const std::vector<std::pair<double *, int>> &mats, cudaStream_t s) {
     std::vector<SysDesc> h;
     int max_m = 0, roff = 0, coff = 0;
+    double *base = nullptr;  // offsets from the lowest address among the matrices
+    for (const auto &mt : mats)
+        if (mt.second > 0 && (!base || mt.first < base)) base = mt.first;
     for (size_t i = 0; i < mats.size(); ++i) {
         const int m = mats[i].second;
         if (m == 0) continue;
@@ -458,11 +647,86 @@ int invert_batch(const std::vector<std::pair<double *, int>> &mats, double *base
     return rc;
 }
 
-}  // namespace
+// Temporary device buffers of one call, from the library pool, released on scope exit.
+struct TempSet {
+    cudaStream_t s;
+    std::vector<void *> v;
+    explicit TempSet(cudaStream_t st) : s(st) {}
+    TempSet(const TempSet &) = delete;
+    TempSet &operator=(const TempSet &) = delete;
+    ~TempSet() {
+        for (void *p : v) cudaFreeAsync(p, s);
+    }
+    double *get(int64_t doubles) {
+        void *p = nullptr;
+        if (dev_alloc(&p, (size_t)std::max<int64_t>(doubles, 1) * 8, s) != GM_OK) return nullptr;
+        v.push_back(p);
+        return (double *)p;
+    }
+};
 
-int hbs_factor(const double *S, int lds, int r, int m, double tol, cudaStream_t s, HbsRoot &H) {
-    if (r < 2 || lds < r || m < 2 || m > QR_MAXP || !(tol > 0.0)) return GM_EINVAL;
-    const int l = HBS_SAMPLES, KC = HBS_KCAP;
+// Largest dynamic shared memory of the single-CTA factorisation.
+size_t qr_smem(int p, int l) { return (size_t)p * l * sizeof(double); }
+
+// One level of pivoted QR factorisations (k_hbs_pqr or the cluster kernel, by size).
+int run_qr(const std::vector<QrDesc> &q, double tol, int margin, DescBuf &db, cudaStream_t s) {
+    if (q.empty()) return GM_OK;
+    int maxp = 0, maxl = 0;
+    for (const QrDesc &d : q) {
+        maxp = std::max(maxp, d.p);
+        maxl = std::max(maxl, d.l);
+    }
+    if (maxp > QRC_MAXP || maxl > HBS_MAX_SAMPLES) return GM_EUNSUPPORTED;
+    int rc = db.ensure(q.size() * sizeof(QrDesc), s);
+    if (rc) return rc;
+    HCK(cudaMemcpyAsync(db.p, q.data(), q.size() * sizeof(QrDesc), cudaMemcpyHostToDevice, s));
+    const int kmax = std::max(maxp, maxl);
+    if (maxp <= QR_MAXP && maxl <= HBS_SAMPLES) {
+        const size_t sm = qr_smem(maxp, maxl);
+        HCK(cudaFuncSetAttribute(k_hbs_pqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_hbs_pqr<<<(unsigned)q.size(), 256, sm, s>>>((const QrDesc *)db.p, tol, kmax, margin);
+        HCK(cudaGetLastError());
+        return GM_OK;
+    }
+    const size_t sm = (size_t)3 * maxp * sizeof(double);
+    HCK(cudaFuncSetAttribute(k_hbs_pqr_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HCK(cudaFuncSetAttribute(k_hbs_pqr_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaError_t e = cudaErrorInvalidValue;
+    for (int cs : {16, 8}) {  // 16 CTAs where the device schedules such clusters, else 8
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(q.size() * cs));
+        cfg.blockDim = dim3(QRC_THREADS);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, k_hbs_pqr_cl, (const QrDesc *)db.p, tol, kmax, margin);
+        if (e == cudaSuccess) break;
+        cudaGetLastError();
+    }
+    return e == cudaSuccess ? GM_OK : GM_ECUDA;
+}
+
+// Sample counts that sufficed for earlier factorisations of a size class (r rounded up
+// to a power of two, node size m): later builds of the same workload start there.
+std::mutex g_hint_mu;
+std::map<std::pair<int, int>, int> g_hint;
+
+int size_class(int r) {
+    int c = 1;
+    while (c < r) c <<= 1;
+    return c;
+}
+
+constexpr int HBS_RETRY = 1000;  // internal: more samples are needed
+
+// One attempt of the compression with l samples per node, then Algorithm 1.
+int hbs_factor_l(const double *S, int lds, int r, int m, double tol, int l, bool temp, cudaStream_t s, HbsRoot &H) {
     H.r = r;
     H.m = m;
     H.tol = tol;
@@ -474,6 +738,7 @@ int hbs_factor(const double *S, int lds, int r, int m, double tol, cudaStream_t 
     H.lo.assign(NN, 0);
     H.hi.assign(NN, 0);
     H.k.assign(NN, 0);
+    H.max_rank = 0;
     H.lo[1] = 0;
     H.hi[1] = r;
     for (int t = 1; t < (1 << L); ++t) {
@@ -485,94 +750,52 @@ int hbs_factor(const double *S, int lds, int r, int m, double tol, cudaStream_t 
     }
     auto sz = [&](int t) { return H.hi[t] - H.lo[t]; };
     auto leaf = [&](int t) { return t >= (1 << L); };
-    auto rows_bound = [&](int t) { return leaf(t) ? sz(t) : 2 * KC; };
-
-    // ---- storage (upper bounds: a node's rank is at most KC)
-    Bump bp;
-    const int64_t oOm = bp.take((int64_t)r * l), oPs = bp.take((int64_t)r * l);
-    const int64_t oY = bp.take((int64_t)r * l), oZ = bp.take((int64_t)r * l);
-    const int64_t oKK = bp.take(r), oWW = bp.take(2 * (int64_t)r);  // coupling table (ints, doubles)
-    std::vector<int64_t> oU(NN), oV(NN), oUf(NN), oVf(NN), oYs(NN), oZs(NN), oyr(NN), ozr(NN);
-    std::vector<int64_t> oD(NN), oW(NN), oX(NN), oZt(NN);
-    std::vector<int64_t> oHab(NN), oHba(NN), oWab(NN), oWba(NN), oXab(NN), oXba(NN);
-    H.offE.assign(NN, 0);
-    H.offFt.assign(NN, 0);
-    H.offG.assign(NN, 0);
-    for (int t = 2; t < NN; ++t) {
-        const int rb = rows_bound(t);
-        oU[t] = bp.take((int64_t)rb * KC);
-        oV[t] = bp.take((int64_t)rb * KC);
-        oUf[t] = leaf(t) ? oU[t] : bp.take((int64_t)sz(t) * KC);
-        oVf[t] = leaf(t) ? oV[t] : bp.take((int64_t)sz(t) * KC);
-        oYs[t] = bp.take((int64_t)rb * l);
-        oZs[t] = bp.take((int64_t)rb * l);
-        oyr[t] = bp.take((int64_t)KC * l);
-        ozr[t] = bp.take((int64_t)KC * l);
-        oD[t] = bp.take((int64_t)rb * 2 * rb);
-        oW[t] = bp.take((int64_t)rb * KC);
-        oX[t] = bp.take((int64_t)KC * 2 * KC);
-        oZt[t] = bp.take((int64_t)KC * rb);
-        H.offE[t] = bp.take((int64_t)rb * KC);
-        H.offFt[t] = bp.take((int64_t)KC * rb);
-        H.offG[t] = bp.take((int64_t)rb * rb);
-    }
-    for (int t = 1; t < (1 << L); ++t) {
-        const int a = 2 * t, b = 2 * t + 1;
-        oHab[t] = bp.take((int64_t)KC * KC);
-        oHba[t] = bp.take((int64_t)KC * KC);
-        oWab[t] = bp.take((int64_t)KC * sz(b));
-        oWba[t] = bp.take((int64_t)KC * sz(a));
-        oXab[t] = bp.take((int64_t)sz(a) * KC);
-        oXba[t] = bp.take((int64_t)sz(b) * KC);
-    }
-    const int64_t oG1 = bp.take((int64_t)2 * KC * 4 * KC);
-    const int64_t oOut = bp.take(2 * (int64_t)NN);  // QR results: 2 ints per node and kind (as doubles)
-    const int64_t oOutV = bp.take(2 * (int64_t)NN);
-    H.offG1 = oG1;
-    H.pool_doubles = bp.top;
-    if (cudaMalloc((void **)&H.pool, (size_t)bp.top * 8) != cudaSuccess) {
-        cudaGetLastError();
-        H.pool = nullptr;
-        return GM_ENOMEM;
-    }
-    double *P = H.pool;
-    int *outU = (int *)(P + oOut), *outV = (int *)(P + oOutV);
+    TempSet tmp(s);
     DescBuf db;
     int rc;
-    const size_t qr_smem = (size_t)QR_MAXP * l * sizeof(double);
-    HCK(cudaFuncSetAttribute(k_hbs_pqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr_smem));
+    double *Om = tmp.get((int64_t)r * l), *Ps = tmp.get((int64_t)r * l);
+    double *Y = tmp.get((int64_t)r * l), *Z = tmp.get((int64_t)r * l);
+    int *outs = (int *)tmp.get(2 * (int64_t)NN);  // per node: 2 QR results for U, 2 for V (ints)
+    if (!Om || !Ps || !Y || !Z || !outs) return GM_ENOMEM;
+    std::vector<double *> U(NN), V(NN), Uf(NN), Vf(NN), Ys(NN), Zs(NN), yr(NN), zr(NN);
+    std::vector<double *> Hab(NN), Hba(NN), Wab(NN), Wba(NN), Xab(NN), Xba(NN);
+    auto rows_of = [&](int t) { return leaf(t) ? sz(t) : H.k[2 * t] + H.k[2 * t + 1]; };
 
     // ---- samples Y = S Omega, Z = S^T Psi
-    k_hbs_normals<<<256, 256, 0, s>>>(P + oOm, (int64_t)r * l, 0x4842530000000001ull);
-    k_hbs_normals<<<256, 256, 0, s>>>(P + oPs, (int64_t)r * l, 0x4842530000000002ull);
+    k_hbs_normals<<<256, 256, 0, s>>>(Om, (int64_t)r * l, 0x4842530000000001ull);
+    k_hbs_normals<<<256, 256, 0, s>>>(Ps, (int64_t)r * l, 0x4842530000000002ull);
     HCK(cudaGetLastError());
-    if ((rc = run_gemms({gd(S, lds, 0, P + oOm, r, 0, P + oY, r, r, l, r, 1.0, 0.0),
-                         gd(S, lds, 1, P + oPs, r, 0, P + oZ, r, r, l, r, 1.0, 0.0)},
+    if ((rc = run_gemms({gd(S, lds, 0, Om, r, 0, Y, r, r, l, r, 1.0, 0.0), gd(S, lds, 1, Ps, r, 0, Z, r, r, l, r, 1.0, 0.0)},
                         db, s)))
         return rc;
 
-    auto qr_level = [&](const std::vector<int> &nodes, const std::vector<int> &prow) -> int {
+    // QR of the samples of one level: rank of each node = the larger truncation point of
+    // its two bases, within the columns both produced; a rank within HBS_OVERSAMPLE of the
+    // sample count asks for more samples
+    auto qr_level = [&](const std::vector<int> &nodes) -> int {
         std::vector<QrDesc> q;
-        for (size_t i = 0; i < nodes.size(); ++i) {
-            const int t = nodes[i], p = prow[i];
-            q.push_back(QrDesc{P + oYs[t], P + oU[t], outU + 2 * t, p, l, p, p});
-            q.push_back(QrDesc{P + oZs[t], P + oV[t], outV + 2 * t, p, l, p, p});
+        for (int t : nodes) {
+            const int p = rows_of(t), kc = std::min(p, l);
+            U[t] = tmp.get((int64_t)p * kc);
+            V[t] = tmp.get((int64_t)p * kc);
+            double *w1 = tmp.get((int64_t)p * l), *w2 = tmp.get((int64_t)p * l);
+            if (!U[t] || !V[t] || !w1 || !w2) return GM_ENOMEM;
+            q.push_back(QrDesc{Ys[t], U[t], outs + 4 * t, w1, p, l, p, p});
+            q.push_back(QrDesc{Zs[t], V[t], outs + 4 * t + 2, w2, p, l, p, p});
         }
-        int rc2 = db.ensure(q.size() * sizeof(QrDesc), s);
+        int rc2 = run_qr(q, tol, HBS_MARGIN, db, s);
         if (rc2) return rc2;
-        HCK(cudaMemcpyAsync(db.p, q.data(), q.size() * sizeof(QrDesc), cudaMemcpyHostToDevice, s));
-        k_hbs_pqr<<<(unsigned)q.size(), 256, qr_smem, s>>>((const QrDesc *)db.p, tol, KC);
-        HCK(cudaGetLastError());
-        std::vector<int> hu(2 * NN), hv(2 * NN);
-        HCK(cudaMemcpyAsync(hu.data(), outU, 2 * NN * sizeof(int), cudaMemcpyDeviceToHost, s));
-        HCK(cudaMemcpyAsync(hv.data(), outV, 2 * NN * sizeof(int), cudaMemcpyDeviceToHost, s));
+        // the nodes of a level are consecutive: one read-back
+        const int t0 = nodes.front(), cnt = nodes.back() - t0 + 1;
+        std::vector<int> res(4 * (size_t)cnt);
+        HCK(cudaMemcpyAsync(res.data(), outs + 4 * t0, res.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
         HCK(cudaStreamSynchronize(s));
         for (int t : nodes) {
-            // one rank for U and V (Algorithm 1 inverts V* D^-1 U): the larger truncation
-            // point, within the columns both factorisations produced
-            int kt = std::max(hu[2 * t], hv[2 * t]);
-            kt = std::min(kt, std::min(hu[2 * t + 1], hv[2 * t + 1]));
-            if (kt >= KC) return GM_EUNSUPPORTED;
+            const int *o = &res[4 * (size_t)(t - t0)];
+            const int tu = o[0], pu = o[1], tv = o[2], pv = o[3];
+            const int kt = std::min(std::max(tu, tv), std::min(pu, pv));
+            // a rank close to the sample count: the samples may have missed part of the range
+            if (std::max(tu, tv) > l - HBS_OVERSAMPLE && l < std::min(rows_of(t), sz(1) - sz(t))) return HBS_RETRY;
             H.k[t] = kt;
             H.max_rank = std::max(H.max_rank, kt);
         }
@@ -583,23 +806,30 @@ int hbs_factor(const double *S, int lds, int r, int m, double tol, cudaStream_t 
     {
         std::vector<CopyDesc> cp;
         std::vector<GemmDesc> g;
-        std::vector<int> nodes, prow;
+        std::vector<int> nodes;
         for (int t = 1 << L; t < NN; ++t) {
             const int lo = H.lo[t], p = sz(t);
+            Ys[t] = tmp.get((int64_t)p * l);
+            Zs[t] = tmp.get((int64_t)p * l);
+            if (!Ys[t] || !Zs[t]) return GM_ENOMEM;
             const double *Sd = S + lo + (size_t)lo * lds;
-            cp.push_back(cpd(P + oY + lo, r, P + oYs[t], p, p, l, 0));
-            cp.push_back(cpd(P + oZ + lo, r, P + oZs[t], p, p, l, 0));
-            g.push_back(gd(Sd, lds, 0, P + oOm + lo, r, 0, P + oYs[t], p, p, l, p, -1.0, 1.0));
-            g.push_back(gd(Sd, lds, 1, P + oPs + lo, r, 0, P + oZs[t], p, p, l, p, -1.0, 1.0));
+            cp.push_back(cpd(Y + lo, r, Ys[t], p, p, l, 0));
+            cp.push_back(cpd(Z + lo, r, Zs[t], p, p, l, 0));
+            g.push_back(gd(Sd, lds, 0, Om + lo, r, 0, Ys[t], p, p, l, p, -1.0, 1.0));
+            g.push_back(gd(Sd, lds, 1, Ps + lo, r, 0, Zs[t], p, p, l, p, -1.0, 1.0));
             nodes.push_back(t);
-            prow.push_back(p);
         }
-        if ((rc = run_copies(cp, db, s)) || (rc = run_gemms(g, db, s)) || (rc = qr_level(nodes, prow))) return rc;
+        if ((rc = run_copies(cp, db, s)) || (rc = run_gemms(g, db, s)) || (rc = qr_level(nodes))) return rc;
         g.clear();
         for (int t : nodes) {
             const int p = sz(t), k = H.k[t];
-            g.push_back(gd(P + oU[t], p, 1, P + oYs[t], p, 0, P + oyr[t], std::max(k, 1), k, l, p, 1.0, 0.0));
-            g.push_back(gd(P + oV[t], p, 1, P + oZs[t], p, 0, P + ozr[t], std::max(k, 1), k, l, p, 1.0, 0.0));
+            yr[t] = tmp.get((int64_t)k * l);
+            zr[t] = tmp.get((int64_t)k * l);
+            if (!yr[t] || !zr[t]) return GM_ENOMEM;
+            Uf[t] = U[t];
+            Vf[t] = V[t];
+            g.push_back(gd(U[t], p, 1, Ys[t], p, 0, yr[t], std::max(k, 1), k, l, p, 1.0, 0.0));
+            g.push_back(gd(V[t], p, 1, Zs[t], p, 0, zr[t], std::max(k, 1), k, l, p, 1.0, 0.0));
         }
         if ((rc = run_gemms(g, db, s))) return rc;
     }
@@ -607,144 +837,218 @@ int hbs_factor(const double *S, int lds, int r, int m, double tol, cudaStream_t 
     for (int lev = L - 1; lev >= 0; --lev) {
         std::vector<GemmDesc> g1, g2;
         std::vector<CopyDesc> cp;
-        std::vector<int> nodes, prow;
+        std::vector<int> nodes;
         for (int t = 1 << lev; t < (2 << lev); ++t) {
             const int a = 2 * t, b = 2 * t + 1, ka = H.k[a], kb = H.k[b];
             const int sa = sz(a), sb = sz(b);
+            Wab[t] = tmp.get((int64_t)ka * sb);
+            Wba[t] = tmp.get((int64_t)kb * sa);
+            Xab[t] = tmp.get((int64_t)sa * kb);
+            Xba[t] = tmp.get((int64_t)sb * ka);
+            Hab[t] = tmp.get((int64_t)ka * kb);
+            Hba[t] = tmp.get((int64_t)kb * ka);
+            if (!Wab[t] || !Wba[t] || !Xab[t] || !Xba[t] || !Hab[t] || !Hba[t]) return GM_ENOMEM;
             const double *Sab = S + H.lo[a] + (size_t)H.lo[b] * lds, *Sba = S + H.lo[b] + (size_t)H.lo[a] * lds;
             // W_ab = Uf_a^T S(I_a, I_b), W_ba = Uf_b^T S(I_b, I_a)
-            g1.push_back(gd(P + oUf[a], sa, 1, Sab, lds, 0, P + oWab[t], std::max(ka, 1), ka, sb, sa, 1.0, 0.0));
-            g1.push_back(gd(P + oUf[b], sb, 1, Sba, lds, 0, P + oWba[t], std::max(kb, 1), kb, sa, sb, 1.0, 0.0));
+            g1.push_back(gd(Uf[a], sa, 1, Sab, lds, 0, Wab[t], std::max(ka, 1), ka, sb, sa, 1.0, 0.0));
+            g1.push_back(gd(Uf[b], sb, 1, Sba, lds, 0, Wba[t], std::max(kb, 1), kb, sa, sb, 1.0, 0.0));
             // X_ab = S(I_a, I_b) Vf_b, X_ba = S(I_b, I_a) Vf_a
-            g1.push_back(gd(Sab, lds, 0, P + oVf[b], sb, 0, P + oXab[t], sa, sa, kb, sb, 1.0, 0.0));
-            g1.push_back(gd(Sba, lds, 0, P + oVf[a], sa, 0, P + oXba[t], sb, sb, ka, sa, 1.0, 0.0));
+            g1.push_back(gd(Sab, lds, 0, Vf[b], sb, 0, Xab[t], sa, sa, kb, sb, 1.0, 0.0));
+            g1.push_back(gd(Sba, lds, 0, Vf[a], sa, 0, Xba[t], sb, sb, ka, sa, 1.0, 0.0));
             // B_tau blocks: H_ab = W_ab Vf_b, H_ba = W_ba Vf_a
-            g2.push_back(gd(P + oWab[t], std::max(ka, 1), 0, P + oVf[b], sb, 0, P + oHab[t], std::max(ka, 1), ka, kb,
-                            sb, 1.0, 0.0));
-            g2.push_back(gd(P + oWba[t], std::max(kb, 1), 0, P + oVf[a], sa, 0, P + oHba[t], std::max(kb, 1), kb, ka,
-                            sa, 1.0, 0.0));
+            g2.push_back(gd(Wab[t], std::max(ka, 1), 0, Vf[b], sb, 0, Hab[t], std::max(ka, 1), ka, kb, sb, 1.0, 0.0));
+            g2.push_back(gd(Wba[t], std::max(kb, 1), 0, Vf[a], sa, 0, Hba[t], std::max(kb, 1), kb, ka, sa, 1.0, 0.0));
             if (lev >= 1) {
                 const int p = ka + kb;
+                Ys[t] = tmp.get((int64_t)p * l);
+                Zs[t] = tmp.get((int64_t)p * l);
+                if (!Ys[t] || !Zs[t]) return GM_ENOMEM;
                 // reduced samples: [y_a - W_ab Omega(I_b); y_b - W_ba Omega(I_a)], same for z
-                cp.push_back(cpd(P + oyr[a], std::max(ka, 1), P + oYs[t], std::max(p, 1), ka, l, 0));
-                cp.push_back(cpd(P + oyr[b], std::max(kb, 1), P + oYs[t] + ka, std::max(p, 1), kb, l, 0));
-                cp.push_back(cpd(P + ozr[a], std::max(ka, 1), P + oZs[t], std::max(p, 1), ka, l, 0));
-                cp.push_back(cpd(P + ozr[b], std::max(kb, 1), P + oZs[t] + ka, std::max(p, 1), kb, l, 0));
-                g2.push_back(gd(P + oWab[t], std::max(ka, 1), 0, P + oOm + H.lo[b], r, 0, P + oYs[t], std::max(p, 1),
-                                ka, l, sb, -1.0, 1.0));
-                g2.push_back(gd(P + oWba[t], std::max(kb, 1), 0, P + oOm + H.lo[a], r, 0, P + oYs[t] + ka,
-                                std::max(p, 1), kb, l, sa, -1.0, 1.0));
-                g2.push_back(gd(P + oXba[t], sb, 1, P + oPs + H.lo[b], r, 0, P + oZs[t], std::max(p, 1), ka, l, sb,
+                cp.push_back(cpd(yr[a], std::max(ka, 1), Ys[t], std::max(p, 1), ka, l, 0));
+                cp.push_back(cpd(yr[b], std::max(kb, 1), Ys[t] + ka, std::max(p, 1), kb, l, 0));
+                cp.push_back(cpd(zr[a], std::max(ka, 1), Zs[t], std::max(p, 1), ka, l, 0));
+                cp.push_back(cpd(zr[b], std::max(kb, 1), Zs[t] + ka, std::max(p, 1), kb, l, 0));
+                g2.push_back(gd(Wab[t], std::max(ka, 1), 0, Om + H.lo[b], r, 0, Ys[t], std::max(p, 1), ka, l, sb, -1.0,
+                                1.0));
+                g2.push_back(gd(Wba[t], std::max(kb, 1), 0, Om + H.lo[a], r, 0, Ys[t] + ka, std::max(p, 1), kb, l, sa,
                                 -1.0, 1.0));
-                g2.push_back(gd(P + oXab[t], sa, 1, P + oPs + H.lo[a], r, 0, P + oZs[t] + ka, std::max(p, 1), kb, l,
-                                sa, -1.0, 1.0));
+                g2.push_back(gd(Xba[t], sb, 1, Ps + H.lo[b], r, 0, Zs[t], std::max(p, 1), ka, l, sb, -1.0, 1.0));
+                g2.push_back(gd(Xab[t], sa, 1, Ps + H.lo[a], r, 0, Zs[t] + ka, std::max(p, 1), kb, l, sa, -1.0, 1.0));
                 nodes.push_back(t);
-                prow.push_back(p);
             }
         }
         if ((rc = run_gemms(g1, db, s)) || (rc = run_copies(cp, db, s)) || (rc = run_gemms(g2, db, s))) return rc;
         if (lev == 0) break;
-        if ((rc = qr_level(nodes, prow))) return rc;
+        if ((rc = qr_level(nodes))) return rc;
         std::vector<GemmDesc> g3;
         for (int t : nodes) {
             const int a = 2 * t, b = 2 * t + 1, ka = H.k[a], kb = H.k[b], k = H.k[t], p = ka + kb;
             const int sa = sz(a), st = sz(t);
-            g3.push_back(gd(P + oU[t], std::max(p, 1), 1, P + oYs[t], std::max(p, 1), 0, P + oyr[t], std::max(k, 1), k,
-                            l, p, 1.0, 0.0));
-            g3.push_back(gd(P + oV[t], std::max(p, 1), 1, P + oZs[t], std::max(p, 1), 0, P + ozr[t], std::max(k, 1), k,
-                            l, p, 1.0, 0.0));
+            yr[t] = tmp.get((int64_t)k * l);
+            zr[t] = tmp.get((int64_t)k * l);
+            Uf[t] = tmp.get((int64_t)st * k);
+            Vf[t] = tmp.get((int64_t)st * k);
+            if (!yr[t] || !zr[t] || !Uf[t] || !Vf[t]) return GM_ENOMEM;
+            g3.push_back(gd(U[t], std::max(p, 1), 1, Ys[t], std::max(p, 1), 0, yr[t], std::max(k, 1), k, l, p, 1.0, 0.0));
+            g3.push_back(gd(V[t], std::max(p, 1), 1, Zs[t], std::max(p, 1), 0, zr[t], std::max(k, 1), k, l, p, 1.0, 0.0));
             // full bases: Uf_t = diag(Uf_a, Uf_b) U_t, likewise V
-            g3.push_back(gd(P + oUf[a], sa, 0, P + oU[t], std::max(p, 1), 0, P + oUf[t], st, sa, k, ka, 1.0, 0.0));
-            g3.push_back(gd(P + oUf[b], sz(b), 0, P + oU[t] + ka, std::max(p, 1), 0, P + oUf[t] + sa, st, sz(b), k, kb,
-                            1.0, 0.0));
-            g3.push_back(gd(P + oVf[a], sa, 0, P + oV[t], std::max(p, 1), 0, P + oVf[t], st, sa, k, ka, 1.0, 0.0));
-            g3.push_back(gd(P + oVf[b], sz(b), 0, P + oV[t] + ka, std::max(p, 1), 0, P + oVf[t] + sa, st, sz(b), k, kb,
-                            1.0, 0.0));
+            g3.push_back(gd(Uf[a], sa, 0, U[t], std::max(p, 1), 0, Uf[t], st, sa, k, ka, 1.0, 0.0));
+            g3.push_back(gd(Uf[b], sz(b), 0, U[t] + ka, std::max(p, 1), 0, Uf[t] + sa, st, sz(b), k, kb, 1.0, 0.0));
+            g3.push_back(gd(Vf[a], sa, 0, V[t], std::max(p, 1), 0, Vf[t], st, sa, k, ka, 1.0, 0.0));
+            g3.push_back(gd(Vf[b], sz(b), 0, V[t] + ka, std::max(p, 1), 0, Vf[t] + sa, st, sz(b), k, kb, 1.0, 0.0));
         }
         if ((rc = run_gemms(g3, db, s))) return rc;
     }
 
+    // ---- the factors that stay: E, F^T, G per node, G_1, the ring's ghost couplings
+    Bump bp;
+    H.offE.assign(NN, 0);
+    H.offFt.assign(NN, 0);
+    H.offG.assign(NN, 0);
+    for (int t = 2; t < NN; ++t) {
+        const int q = rows_of(t), k = H.k[t];
+        H.offE[t] = bp.take((int64_t)q * k);
+        H.offFt[t] = bp.take((int64_t)k * q);
+        H.offG[t] = bp.take((int64_t)q * q);
+    }
+    const int q1 = H.k[2] + H.k[3];
+    H.offG1 = bp.take((int64_t)q1 * 2 * q1);
+    H.offKK = bp.take(r);
+    H.offWW = bp.take(2 * (int64_t)r);
+    H.pool_doubles = bp.top;
+    H.pool_stream = temp ? s : nullptr;
+    if (temp) {
+        if ((rc = dev_alloc((void **)&H.pool, (size_t)bp.top * 8, s))) return rc;
+    } else if (cudaMalloc((void **)&H.pool, (size_t)bp.top * 8) != cudaSuccess) {
+        cudaGetLastError();
+        H.pool = nullptr;
+        return GM_ENOMEM;
+    }
+    double *P = H.pool;
+
     // ---- Algorithm 1, finest level first
-    auto rows_of = [&](int t) { return leaf(t) ? sz(t) : H.k[2 * t] + H.k[2 * t + 1]; };
+    std::vector<double *> Dq(NN), Wt(NN), Xt(NN), Zt(NN);
     for (int lev = L; lev >= 1; --lev) {
         std::vector<CopyDesc> cp;
         std::vector<std::pair<double *, int>> inv;
         for (int t = 1 << lev; t < (2 << lev); ++t) {
-            const int q = rows_of(t);
-            double *Dq = P + oD[t];  // [D~ | I], q x 2q, ld q
+            const int q = rows_of(t), k = H.k[t];
+            Dq[t] = tmp.get((int64_t)q * 2 * q);  // [D~ | I], q x 2q, ld q
+            Wt[t] = tmp.get((int64_t)q * k);
+            Xt[t] = tmp.get((int64_t)k * 2 * k);  // [V^T W | I]
+            Zt[t] = tmp.get((int64_t)k * q);
+            if (!Dq[t] || !Wt[t] || !Xt[t] || !Zt[t]) return GM_ENOMEM;
             if (leaf(t)) {
-                cp.push_back(cpd(S + H.lo[t] + (size_t)H.lo[t] * lds, lds, Dq, q, q, q, 0));
+                cp.push_back(cpd(S + H.lo[t] + (size_t)H.lo[t] * lds, lds, Dq[t], q, q, q, 0));
             } else {
                 const int a = 2 * t, b = 2 * t + 1, ka = H.k[a], kb = H.k[b];
-                const double *Dha = P + oX[a] + (size_t)ka * ka, *Dhb = P + oX[b] + (size_t)kb * kb;
-                cp.push_back(cpd(Dha, std::max(ka, 1), Dq, q, ka, ka, 0));
-                cp.push_back(cpd(P + oHab[t], std::max(ka, 1), Dq + (size_t)ka * q, q, ka, kb, 0));
-                cp.push_back(cpd(P + oHba[t], std::max(kb, 1), Dq + ka, q, kb, ka, 0));
-                cp.push_back(cpd(Dhb, std::max(kb, 1), Dq + ka + (size_t)ka * q, q, kb, kb, 0));
+                const double *Dha = Xt[a] + (size_t)ka * ka, *Dhb = Xt[b] + (size_t)kb * kb;
+                cp.push_back(cpd(Dha, std::max(ka, 1), Dq[t], q, ka, ka, 0));
+                cp.push_back(cpd(Hab[t], std::max(ka, 1), Dq[t] + (size_t)ka * q, q, ka, kb, 0));
+                cp.push_back(cpd(Hba[t], std::max(kb, 1), Dq[t] + ka, q, kb, ka, 0));
+                cp.push_back(cpd(Dhb, std::max(kb, 1), Dq[t] + ka + (size_t)ka * q, q, kb, kb, 0));
             }
-            cp.push_back(cpd(nullptr, 1, Dq + (size_t)q * q, q, q, q, 1));
-            inv.push_back({Dq, q});
+            cp.push_back(cpd(nullptr, 1, Dq[t] + (size_t)q * q, q, q, q, 1));
+            inv.push_back({Dq[t], q});
         }
-        if ((rc = run_copies(cp, db, s)) || (rc = invert_batch(inv, P, s))) return rc;
+        if ((rc = run_copies(cp, db, s)) || (rc = invert_batch(inv, s))) return rc;
         // W = D~^-1 U, X = V^T W (into [X | I]), then D^ = X^-1
         std::vector<GemmDesc> g;
         cp.clear();
         inv.clear();
         for (int t = 1 << lev; t < (2 << lev); ++t) {
             const int q = rows_of(t), k = H.k[t];
-            const double *Di = P + oD[t] + (size_t)q * q;
-            g.push_back(gd(Di, q, 0, P + oU[t], q, 0, P + oW[t], q, q, k, q, 1.0, 0.0));
-            cp.push_back(cpd(nullptr, 1, P + oX[t] + (size_t)k * k, std::max(k, 1), k, k, 1));
-            inv.push_back({P + oX[t], k});
+            const double *Di = Dq[t] + (size_t)q * q;
+            g.push_back(gd(Di, q, 0, U[t], q, 0, Wt[t], q, q, k, q, 1.0, 0.0));
+            cp.push_back(cpd(nullptr, 1, Xt[t] + (size_t)k * k, std::max(k, 1), k, k, 1));
+            inv.push_back({Xt[t], k});
         }
         if ((rc = run_gemms(g, db, s))) return rc;
         g.clear();
         for (int t = 1 << lev; t < (2 << lev); ++t) {
             const int q = rows_of(t), k = H.k[t];
-            g.push_back(gd(P + oV[t], q, 1, P + oW[t], q, 0, P + oX[t], std::max(k, 1), k, k, q, 1.0, 0.0));
+            g.push_back(gd(V[t], q, 1, Wt[t], q, 0, Xt[t], std::max(k, 1), k, k, q, 1.0, 0.0));
         }
-        if ((rc = run_gemms(g, db, s)) || (rc = run_copies(cp, db, s)) || (rc = invert_batch(inv, P, s))) return rc;
+        if ((rc = run_gemms(g, db, s)) || (rc = run_copies(cp, db, s)) || (rc = invert_batch(inv, s))) return rc;
         // E = W D^, Zt = V^T D~^-1, F^T = D^ Zt, G = D~^-1 - E Zt
         g.clear();
         cp.clear();
         for (int t = 1 << lev; t < (2 << lev); ++t) {
             const int q = rows_of(t), k = H.k[t];
-            const double *Di = P + oD[t] + (size_t)q * q, *Dh = P + oX[t] + (size_t)k * k;
-            g.push_back(gd(P + oW[t], q, 0, Dh, std::max(k, 1), 0, P + H.offE[t], q, q, k, k, 1.0, 0.0));
-            g.push_back(gd(P + oV[t], q, 1, Di, q, 0, P + oZt[t], std::max(k, 1), k, q, q, 1.0, 0.0));
+            const double *Di = Dq[t] + (size_t)q * q, *Dh = Xt[t] + (size_t)k * k;
+            g.push_back(gd(Wt[t], q, 0, Dh, std::max(k, 1), 0, P + H.offE[t], q, q, k, k, 1.0, 0.0));
+            g.push_back(gd(V[t], q, 1, Di, q, 0, Zt[t], std::max(k, 1), k, q, q, 1.0, 0.0));
             cp.push_back(cpd(Di, q, P + H.offG[t], q, q, q, 0));
         }
         if ((rc = run_gemms(g, db, s)) || (rc = run_copies(cp, db, s))) return rc;
         g.clear();
         for (int t = 1 << lev; t < (2 << lev); ++t) {
             const int q = rows_of(t), k = H.k[t];
-            const double *Dh = P + oX[t] + (size_t)k * k;
-            g.push_back(gd(Dh, std::max(k, 1), 0, P + oZt[t], std::max(k, 1), 0, P + H.offFt[t], std::max(k, 1), k, q,
-                           k, 1.0, 0.0));
-            g.push_back(gd(P + H.offE[t], q, 0, P + oZt[t], std::max(k, 1), 0, P + H.offG[t], q, q, q, k, -1.0, 1.0));
+            const double *Dh = Xt[t] + (size_t)k * k;
+            g.push_back(gd(Dh, std::max(k, 1), 0, Zt[t], std::max(k, 1), 0, P + H.offFt[t], std::max(k, 1), k, q, k,
+                           1.0, 0.0));
+            g.push_back(gd(P + H.offE[t], q, 0, Zt[t], std::max(k, 1), 0, P + H.offG[t], q, q, q, k, -1.0, 1.0));
         }
         if ((rc = run_gemms(g, db, s))) return rc;
     }
     // G_1 = [D^_2, B_23; B_32, D^_3]^{-1}
     {
         const int k2 = H.k[2], k3 = H.k[3], q = k2 + k3;
-        double *Dq = P + oG1;
-        std::vector<CopyDesc> cp{cpd(P + oX[2] + (size_t)k2 * k2, std::max(k2, 1), Dq, q, k2, k2, 0),
-                                 cpd(P + oHab[1], std::max(k2, 1), Dq + (size_t)k2 * q, q, k2, k3, 0),
-                                 cpd(P + oHba[1], std::max(k3, 1), Dq + k2, q, k3, k2, 0),
-                                 cpd(P + oX[3] + (size_t)k3 * k3, std::max(k3, 1), Dq + k2 + (size_t)k2 * q, q, k3, k3, 0),
-                                 cpd(nullptr, 1, Dq + (size_t)q * q, q, q, q, 1)};
-        if ((rc = run_copies(cp, db, s)) || (rc = invert_batch({{Dq, q}}, P, s))) return rc;
+        double *D1 = P + H.offG1;
+        std::vector<CopyDesc> cp{cpd(Xt[2] + (size_t)k2 * k2, std::max(k2, 1), D1, q, k2, k2, 0),
+                                 cpd(Hab[1], std::max(k2, 1), D1 + (size_t)k2 * q, q, k2, k3, 0),
+                                 cpd(Hba[1], std::max(k3, 1), D1 + k2, q, k3, k2, 0),
+                                 cpd(Xt[3] + (size_t)k3 * k3, std::max(k3, 1), D1 + k2 + (size_t)k2 * q, q, k3, k3, 0),
+                                 cpd(nullptr, 1, D1 + (size_t)q * q, q, q, q, 1)};
+        if ((rc = run_copies(cp, db, s)) || (rc = invert_batch({{D1, q}}, s))) return rc;
     }
-    H.offKK = oKK;
-    H.offWW = oWW;
     HCK(cudaStreamSynchronize(s));
     return GM_OK;
 }
 
+}  // namespace
+
+namespace {
+void release_pool(HbsRoot &h) {
+    if (h.pool) {
+        if (h.pool_stream) cudaFreeAsync(h.pool, h.pool_stream);
+        else cudaFree(h.pool);
+    }
+    h.pool = nullptr;
+    h.pool_stream = nullptr;
+}
+}  // namespace
+
+int hbs_factor(const double *S, int lds, int r, int m, double tol, cudaStream_t s, HbsRoot &H, bool temp) {
+    if (r < 2 || lds < r || m < 2 || m > QR_MAXP || !(tol > 0.0)) return GM_EINVAL;
+    const std::pair<int, int> key(size_class(r), m);
+    int l = HBS_SAMPLES;
+    {
+        std::lock_guard<std::mutex> lk(g_hint_mu);
+        auto it = g_hint.find(key);
+        if (it != g_hint.end()) l = it->second;
+    }
+    for (;;) {
+        release_pool(H);
+        const int rc = hbs_factor_l(S, lds, r, m, tol, l, temp, s, H);
+        if (rc != HBS_RETRY) {
+            if (rc == GM_OK) {
+                std::lock_guard<std::mutex> lk(g_hint_mu);
+                g_hint[key] = l;
+            }
+            return rc;
+        }
+        if (l >= HBS_MAX_SAMPLES) {
+            release_pool(H);
+            return GM_EUNSUPPORTED;
+        }
+        l = std::min(2 * l, HBS_MAX_SAMPLES);
+    }
+}
+
 int hbs_build_root(const double *S, int r, int n, int m, double tol, const double *bf, const double *cf,
                    const double *df, cudaStream_t s, HbsRoot &H) {
-    int rc = hbs_factor(S, r, r, m, tol, s, H);
+    int rc = hbs_factor(S, r, r, m, tol, s, H, false);
     if (rc) return rc;
     H.n = n;
     // coupling table for the solve
@@ -876,7 +1180,7 @@ int hbs_block_solve(double *ws, int sp, int rp, int m, double tol, cudaStream_t 
     DescBuf db;
     do {
         // S33 (top-left sp x sp of [M | Z]) in HBS form, inverted by Algorithm 1
-        if ((rc = hbs_factor(ws, M, sp, m, tol, s, H33))) break;
+        if ((rc = hbs_factor(ws, M, sp, m, tol, s, H33, true))) break;
         // [V3 W3] = S33^{-1} [A34 Z3]: the columns sp .. of the top rows of [M | Z]
         if ((rc = hbs_solve(H33, ws + (size_t)sp * M, M, VW, sp, sp + rp, s))) break;
         // T44 = S44 - A43 V3, Z4' = Z4 - A43 W3 (A43 diagonal: M(sp + i, i))
@@ -884,7 +1188,7 @@ int hbs_block_solve(double *ws, int sp, int rp, int m, double tol, cudaStream_t 
         k_hbs_sub_diag<<<bx, 256, 0, s>>>(T44, sp, ws + sp + (size_t)sp * M, M, ws + sp, M + 1, V3, sp, sp, sp);
         k_hbs_sub_diag<<<bx, 256, 0, s>>>(Z4, sp, ws + sp + (size_t)M * M, M, ws + sp, M + 1, W3, sp, sp, rp);
         if (cudaGetLastError() != cudaSuccess) { rc = GM_ECUDA; break; }
-        if ((rc = hbs_factor(T44, sp, sp, m, tol, s, H44))) break;
+        if ((rc = hbs_factor(T44, sp, sp, m, tol, s, H44, true))) break;
         if ((rc = hbs_solve(H44, Z4, sp, X4, sp, rp, s))) break;
         // X3 = W3 - V3 X4
         if ((rc = run_copies({cpd(W3, sp, X3, sp, sp, rp, 0)}, db, s))) break;
@@ -901,6 +1205,120 @@ int hbs_block_solve(double *ws, int sp, int rp, int m, double tol, cudaStream_t 
     hbs_free(H44);
     cudaFreeAsync(T, s);
     return rc;
+}
+
+namespace {
+// S13 = S1(P1, P3) and S24 = S2(P2, P4) of one merge, gathered from the children.
+__global__ void k_hbs_gather_offdiag(const MergeDesc *__restrict__ md, const int *__restrict__ tab,
+                                     const double *__restrict__ in, double *__restrict__ S13, double *__restrict__ S24) {
+    const MergeDesc M = *md;
+    const int sp = M.sp, n1 = M.n1, n2 = M.n2;
+    const int *p3 = tab + M.tab, *p4 = p3 + sp, *p1 = p3 + 4 * sp, *p2 = p1 + 2 * n1;
+    const double *S1 = in + M.s1, *S2 = in + M.s2;
+    const int64_t t1 = (int64_t)n1 * sp, tot = t1 + (int64_t)n2 * sp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < t1) {
+            const int a = (int)(e % n1), c = (int)(e / n1);
+            S13[e] = S1[p1[a] + (int64_t)M.r1 * p3[c]];
+        } else {
+            const int64_t f = e - t1;
+            const int a = (int)(f % n2), c = (int)(f / n2);
+            S24[f] = S2[p2[a] + (int64_t)M.r2 * p4[c]];
+        }
+    }
+}
+
+// A_i ~ L_i R_i (i = 0, 1; A_i rows_i x cols, column-major, ld rows_i) at relative
+// tolerance tol: L_i an orthonormal basis of the range of a Gaussian sample A_i Omega
+// truncated at the first |R_jj| <= tol |R_11| of its pivoted QR, R_i = L_i^T A_i.  The
+// sample count starts at the last one that sufficed for this size and doubles while a
+// rank comes within HBS_OVERSAMPLE of it.
+int lowrank_pair(const double *const A[2], const int rows[2], int cols, double tol, TempSet &tmp, DescBuf &db,
+                 cudaStream_t s, double *L[2], double *R[2], int k[2]) {
+    const std::pair<int, int> key(size_class(cols), -1);
+    int l = HBS_SAMPLES;
+    {
+        std::lock_guard<std::mutex> lk(g_hint_mu);
+        auto it = g_hint.find(key);
+        if (it != g_hint.end()) l = it->second;
+    }
+    int *outs = (int *)tmp.get(2);
+    if (!outs) return GM_ENOMEM;
+    for (;;) {
+        const int le = std::min(l, cols);
+        double *Om = tmp.get((int64_t)cols * le);
+        if (!Om) return GM_ENOMEM;
+        k_hbs_normals<<<256, 256, 0, s>>>(Om, (int64_t)cols * le, 0x4842530000000003ull + (unsigned long long)l);
+        HCK(cudaGetLastError());
+        std::vector<GemmDesc> g;
+        std::vector<QrDesc> q;
+        double *Y[2];
+        for (int i = 0; i < 2; ++i) {
+            Y[i] = tmp.get((int64_t)rows[i] * le);
+            L[i] = tmp.get((int64_t)rows[i] * std::min(rows[i], le));
+            double *w = tmp.get((int64_t)rows[i] * le);
+            if (!Y[i] || !L[i] || !w) return GM_ENOMEM;
+            g.push_back(gd(A[i], rows[i], 0, Om, cols, 0, Y[i], rows[i], rows[i], le, cols, 1.0, 0.0));
+            q.push_back(QrDesc{Y[i], L[i], outs + 2 * i, w, rows[i], le, rows[i], rows[i]});
+        }
+        int rc = run_gemms(g, db, s);
+        if (rc == GM_OK) rc = run_qr(q, tol, 0, db, s);
+        if (rc) return rc;
+        int res[4];
+        HCK(cudaMemcpyAsync(res, outs, sizeof(res), cudaMemcpyDeviceToHost, s));
+        HCK(cudaStreamSynchronize(s));
+        bool more = false;
+        for (int i = 0; i < 2; ++i) {
+            k[i] = std::min(res[2 * i], res[2 * i + 1]);
+            if (res[2 * i] > le - HBS_OVERSAMPLE && le < std::min(rows[i], cols)) more = true;
+        }
+        if (!more) break;
+        if (l >= HBS_MAX_SAMPLES) return GM_EUNSUPPORTED;
+        l = std::min(2 * l, HBS_MAX_SAMPLES);
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_hint_mu);
+        g_hint[key] = l;
+    }
+    std::vector<GemmDesc> g;
+    for (int i = 0; i < 2; ++i) {
+        R[i] = tmp.get((int64_t)std::max(k[i], 1) * cols);
+        if (!R[i]) return GM_ENOMEM;
+        g.push_back(gd(L[i], rows[i], 1, A[i], rows[i], 0, R[i], std::max(k[i], 1), k[i], cols, rows[i], 1.0, 0.0));
+    }
+    return run_gemms(g, db, s);
+}
+}  // namespace
+
+int hbs_merge_lowrank(const MergeDesc &hm, const MergeDesc *d_md, const int *d_tab, const double *in,
+                      const double *ws, double *out, const double *bf, const double *cf, const double *df, double tol,
+                      cudaStream_t s, KTimer &kt, int *max_rank) {
+    const int sp = hm.sp, rp = hm.rp, M = 2 * sp;
+    TempSet tmp(s);
+    DescBuf db;
+    const int rows[2] = {hm.n1, hm.n2};
+    double *S13 = tmp.get((int64_t)hm.n1 * sp), *S24 = tmp.get((int64_t)hm.n2 * sp);
+    if (!S13 || !S24) return GM_ENOMEM;
+    const int64_t tot = (int64_t)rp * sp;
+    k_hbs_gather_offdiag<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, s>>>(d_md, d_tab, in, S13, S24);
+    HCK(cudaGetLastError());
+    const double *A[2] = {S13, S24};
+    double *L[2], *R[2];
+    int k[2];
+    int rc = lowrank_pair(A, rows, sp, tol, tmp, db, s, L, R, k);
+    if (rc) return rc;
+    // W13 = R13 X3, W24 = R24 X4 (X = M^{-1} Z, the right block of the system)
+    const double *X = ws + (size_t)M * M;
+    double *W13 = tmp.get((int64_t)std::max(k[0], 1) * rp), *W24 = tmp.get((int64_t)std::max(k[1], 1) * rp);
+    if (!W13 || !W24) return GM_ENOMEM;
+    if ((rc = run_gemms({gd(R[0], std::max(k[0], 1), 0, X, M, 0, W13, std::max(k[0], 1), k[0], rp, sp, 1.0, 0.0),
+                         gd(R[1], std::max(k[1], 1), 0, X + sp, M, 0, W24, std::max(k[1], 1), k[1], rp, sp, 1.0, 0.0)},
+                        db, s)))
+        return rc;
+    const LrUpdate lr{L[0], L[1], W13, W24, k[0], k[1]};
+    HCK(launch_merge_update_lr(d_md, hm, d_tab, in, lr, out, bf, cf, df, s, kt));
+    if (max_rank) *max_rank = std::max(*max_rank, std::max(k[0], k[1]));
+    return GM_OK;
 }
 
 namespace {
@@ -943,8 +1361,12 @@ int hbs_dense_dtn(HbsRoot &H, double *T, cudaStream_t s) {
 }
 
 void hbs_free(HbsRoot &h) {
-    if (h.pool) cudaFree(h.pool);
+    if (h.pool) {
+        if (h.pool_stream) cudaFreeAsync(h.pool, h.pool_stream);
+        else cudaFree(h.pool);
+    }
     h.pool = nullptr;
+    h.pool_stream = nullptr;
     if (h.sig) cudaFree(h.sig);
     h.sig = nullptr;
 }

@@ -11,14 +11,18 @@
 
 namespace gm {
 
-constexpr int HBS_SAMPLES = 128;  // random samples per compression (columns of Omega, Psi)
-constexpr int HBS_KCAP = 96;      // largest rank a node may take (oversampling >= 32)
+constexpr int HBS_SAMPLES = 128;      // random samples per node at the first attempt (columns of
+                                      // Omega, Psi); doubled while a rank comes within
+constexpr int HBS_OVERSAMPLE = 32;    // this many of the sample count,
+constexpr int HBS_MAX_SAMPLES = 512;  // up to this many samples: ranks up to 480
+constexpr int HBS_MARGIN = 32;        // QR columns kept past a basis' own truncation point
 
 struct HbsRoot {
     int r = 0, n = 0, m = 0, L = 0;
     double tol = 0.0;
     std::vector<int> lo, hi, k;  // per node 1 .. 2^(L+1) - 1: index range [lo, hi), rank
-    double *pool = nullptr;      // every factor (cudaMalloc, owned)
+    double *pool = nullptr;      // the inverse's factors E, F^T, G, G_1 and the ghost couplings (owned)
+    cudaStream_t pool_stream = nullptr;  // non-null: pool is a stream-ordered temporary
     int64_t pool_doubles = 0;
     std::vector<int64_t> offE, offFt, offG;  // Algorithm 1 factors per node (pool offsets)
     int64_t offG1 = 0;                       // root G_1 = [G_1-system | inverse], q = k_2 + k_3
@@ -30,8 +34,11 @@ struct HbsRoot {
 
 // HBS factors of a dense r x r FP64 matrix S (column-major, leading dimension lds,
 // device): compression at relative tolerance tol with node size m (Section 4), then
-// Algorithm 1 (Section 5).  GM_EUNSUPPORTED: a node's rank reached HBS_KCAP, or r <= m.
-int hbs_factor(const double *S, int lds, int r, int m, double tol, cudaStream_t s, HbsRoot &out);
+// Algorithm 1 (Section 5).  The compression's temporaries come from the library pool;
+// the inverse's factors from cudaMalloc, or (temp) from the pool on stream s.
+// GM_EUNSUPPORTED: a node's rank exceeds HBS_MAX_SAMPLES - HBS_OVERSAMPLE, a sample has
+// more rows than one factorisation takes, or r <= m.
+int hbs_factor(const double *S, int lds, int r, int m, double tol, cudaStream_t s, HbsRoot &out, bool temp);
 // Y = S^{-1} X for B columns (Algorithm 2); X, Y device, r x B, leading dimensions ldx, ldy.
 int hbs_solve(HbsRoot &h, const double *X, int ldx, double *Y, int ldy, int B, cudaStream_t s);
 
@@ -44,9 +51,20 @@ int hbs_solve(HbsRoot &h, const double *X, int ldx, double *Y, int ldy, int B, c
 // GM_EUNSUPPORTED) ws is unchanged.  max_rank (optional) accumulates the largest rank.
 int hbs_block_solve(double *ws, int sp, int rp, int m, double tol, cudaStream_t s, int *max_rank);
 
+// Steps 2 and 3 of the accelerated merge (Section 5) for one merge whose interface
+// system was solved (X = M^{-1} Z in the right block of ws, the merge's [M | Z], ld 2 sp):
+// S13 = S1(P1, P3) and S24 = S2(P2, P4) are compressed to L13 R13, L24 R24 at relative
+// tolerance tol (from Gaussian samples), the update is formed as [L13 (R13 X3);
+// L24 (R24 X4)], and the parent's Schur complement [S11 A12; A21 S22] minus it is written
+// densely into its ring order at out + hm.out.  d_md: this merge's descriptor on the
+// device; max_rank (optional) accumulates the larger of the two ranks.
+int hbs_merge_lowrank(const MergeDesc &hm, const MergeDesc *d_md, const int *d_tab, const double *in,
+                      const double *ws, double *out, const double *bf, const double *cf, const double *df, double tol,
+                      cudaStream_t s, KTimer &kt, int *max_rank);
+
 // Compress S (r x r FP64, column-major, device) at relative tolerance tol with node size
 // m (2 <= m <= 192), run Algorithm 1, and tabulate the ghost couplings of the ring from
-// b, c, d (n x n each).  GM_EUNSUPPORTED: a node's rank reached HBS_KCAP, or r <= m.
+// b, c, d (n x n each).  GM_EUNSUPPORTED as for hbs_factor.
 int hbs_build_root(const double *S, int r, int n, int m, double tol, const double *bf, const double *cf,
                    const double *df, cudaStream_t s, HbsRoot &out);
 // dudn = (g - P S^{-1} B g)/h for B vectors (g, dudn: 4n x B column-major, device),

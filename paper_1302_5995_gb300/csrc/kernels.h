@@ -12,6 +12,11 @@
 
 namespace gm {
 
+// Stream-ordered device allocation from the library's memory pool (which keeps freed
+// memory mapped for later calls); free with cudaFreeAsync on a stream.  GM_ENOMEM when
+// the device is out of memory, GM_ECUDA for other failures.
+int dev_alloc(void **p, size_t bytes, cudaStream_t s);
+
 // Process-wide pool of timing events (created once, reused by every timed build).
 cudaEvent_t event_pool_get();
 void event_pool_put(cudaEvent_t e);
@@ -76,6 +81,16 @@ cudaError_t launch_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_
 cudaError_t launch_merge_assemble(const MergeDesc *md, int nm, const int *tab, const double *in, double *ws,
                                   int64_t max_elems, const double *b, const double *c, const double *d, int n,
                                   cudaStream_t s, KTimer &kt);
+// The factored update of an accelerated merge (Section 5, Step 2): rows P1 of the parent
+// get L13 W13, rows P2 get L24 W24 (L13: n1 x k13, L24: n2 x k24, column-major with
+// leading dimensions n1, n2; W13: k13 x rp, W24: k24 x rp, leading dimensions k13, k24).
+struct LrUpdate {
+    const double *L13, *L24, *W13, *W24;
+    int k13, k24;
+};
+cudaError_t launch_merge_update_lr(const MergeDesc *md, const MergeDesc &h_md, const int *tab, const double *in,
+                                   const LrUpdate &lr, double *out, const double *b, const double *c, const double *d,
+                                   cudaStream_t s, KTimer &kt);
 cudaError_t launch_merge_update(const MergeDesc *md, const std::vector<MergeDesc> &h_md, const int *tab,
                                 const double *in, const double *ws, double *out, int max_rp, const double *b,
                                 const double *c, const double *d, int n, cudaStream_t s, KTimer &kt);
@@ -83,5 +98,13 @@ cudaError_t launch_root_assemble(const double *S, int r, int n, double *ws, cons
                                  const double *d, cudaStream_t s, KTimer &kt);
 cudaError_t launch_root_finalize(const double *ws, int r, int n, double *T, cudaStream_t s, KTimer &kt);
 cudaError_t launch_apply(const double *T, const double *G, double *V, int N, int B, cudaStream_t s);
+// Several dense FP64 applies in one launch (one descriptor per operator; tile0 is filled
+// in by the launcher, which uploads the descriptors to d, device memory for h.size()).
+struct ApplyDesc {
+    const double *T, *G;
+    double *V;
+    int N, B, tile0, pad;
+};
+cudaError_t launch_apply_many(std::vector<ApplyDesc> &h, ApplyDesc *d, cudaStream_t s);
 
 }  // namespace gm

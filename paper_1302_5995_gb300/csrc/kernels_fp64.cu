@@ -506,6 +506,43 @@ k_merge_assemble(const MergeDesc *__restrict__ md, const int *__restrict__ tab, 
     }
 }
 
+// The parent's Schur complement of a 64 x 64 tile: C - acc with C = [S11 A12; A21 S22]
+// (A12, A21 the two corner couplings across the shared edge), scattered into the
+// parent's ring order.  Thread (tx, ty) holds rows a0 + tx + 16 q, columns c0 + ty + 16 p.
+__device__ __forceinline__ void merge_store(const MergeDesc &M, const MergeTab &T, const double *__restrict__ S1,
+                                            const double *__restrict__ S2, double *__restrict__ out,
+                                            const double (&acc)[4][4], int a0, int c0, int tx, int ty,
+                                            const double *__restrict__ bf, const double *__restrict__ cf,
+                                            const double *__restrict__ df) {
+    const int rp = M.rp, n1 = M.n1;
+    const double ih = M.n + 1.0;  // 1/h of the merge's problem
+    const int d12 = M.orient ? DIR_N : DIR_E, d21 = M.orient ? DIR_S : DIR_W;
+    double *O = out + M.out;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        int cc = c0 + ty + 16 * p;
+        if (cc >= rp) continue;
+        int qc = cc < n1 ? T.q1[cc] : T.q2[cc - n1];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int aa = a0 + tx + 16 * q;
+            if (aa >= rp) continue;
+            int qa = aa < n1 ? T.q1[aa] : T.q2[aa - n1];
+            double cval = 0.0;
+            if (aa < n1 && cc < n1) cval = S1[T.p1[aa] + (int64_t)M.r1 * T.p1[cc]];
+            else if (aa >= n1 && cc >= n1) cval = S2[T.p2[aa - n1] + (int64_t)M.r2 * T.p2[cc - n1]];
+            else {
+                for (int e = 0; e < 2; ++e) {
+                    const int *x = T.x12 + 4 * e;
+                    if (aa < n1 && aa == x[0] && cc - n1 == x[1]) cval = stencil_w(bf, cf, df, ih, x[2], d12);
+                    if (aa >= n1 && aa - n1 == x[1] && cc == x[0]) cval = stencil_w(bf, cf, df, ih, x[3], d21);
+                }
+            }
+            O[qa + (int64_t)rp * qc] = cval - acc[q][p];
+        }
+    }
+}
+
 // S_parent = [S11 A12; A21 S22] - [S13 0; 0 S24] X, scattered into the parent's ring
 // order.  X = M^{-1} Z is the right block of the workspace after the sweep.
 __global__ void __launch_bounds__(256)
@@ -556,32 +593,61 @@ k_merge_update(const MergeDesc *__restrict__ md, const int *__restrict__ tab, co
         }
         __syncthreads();
     }
-    const double ih = M.n + 1.0;  // 1/h of the merge's problem
-    const int d12 = M.orient ? DIR_N : DIR_E, d21 = M.orient ? DIR_S : DIR_W;
-    double *O = out + M.out;
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        int cc = c0 + ty + 16 * p;
-        if (cc >= rp) continue;
-        int qc = cc < n1 ? T.q1[cc] : T.q2[cc - n1];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int aa = a0 + tx + 16 * q;
-            if (aa >= rp) continue;
-            int qa = aa < n1 ? T.q1[aa] : T.q2[aa - n1];
-            double cval = 0.0;
-            if (aa < n1 && cc < n1) cval = S1[T.p1[aa] + (int64_t)M.r1 * T.p1[cc]];
-            else if (aa >= n1 && cc >= n1) cval = S2[T.p2[aa - n1] + (int64_t)M.r2 * T.p2[cc - n1]];
-            else {
-                for (int e = 0; e < 2; ++e) {
-                    const int *x = T.x12 + 4 * e;
-                    if (aa < n1 && aa == x[0] && cc - n1 == x[1]) cval = stencil_w(bf, cf, df, ih, x[2], d12);
-                    if (aa >= n1 && aa - n1 == x[1] && cc == x[0]) cval = stencil_w(bf, cf, df, ih, x[3], d21);
-                }
+    merge_store(M, T, S1, S2, out, acc, a0, c0, tx, ty, bf, cf, df);
+}
+
+// Step 2 of the accelerated merge (Section 5, eq. matmult): the product of the update in
+// factored form, [L13 W13; L24 W24] with W13 = R13 X3, W24 = R24 X4 (S13 ~ L13 R13 and
+// S24 ~ L24 R24 at the compression tolerance), then the same assembly and ring scatter
+// as k_merge_update (Step 3, the parent formed densely).  One merge per launch.
+__global__ void __launch_bounds__(256)
+k_merge_update_lr(const MergeDesc *__restrict__ md, const int *__restrict__ tab, const double *__restrict__ in,
+                  const LrUpdate lr, double *__restrict__ out, const double *__restrict__ bf,
+                  const double *__restrict__ cf, const double *__restrict__ df) {
+    __shared__ double Y[64][17];
+    __shared__ double X1[16][64];
+    __shared__ double X2[16][64];
+    const MergeDesc M = *md;
+    const int rp = M.rp;
+    const int a0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
+    if (a0 >= rp || c0 >= rp) return;
+    const MergeTab T = merge_tab(M, tab);
+    const int n1 = M.n1, K = max(lr.k13, lr.k24);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double acc[4][4] = {};
+    for (int t0 = 0; t0 < K; t0 += 16) {
+        for (int e = tid; e < 64 * 16; e += 256) {
+            const int x = e % 64, t = e / 64, aa = a0 + x, tt = t0 + t, cc = c0 + x;
+            double y = 0.0;
+            if (aa < n1) {
+                if (tt < lr.k13) y = lr.L13[aa + (size_t)tt * n1];
+            } else if (aa < rp && tt < lr.k24) {
+                y = lr.L24[(aa - n1) + (size_t)tt * (rp - n1)];
             }
-            O[qa + (int64_t)rp * qc] = cval - acc[q][p];
+            Y[x][t] = y;
+            X1[t][x] = (cc < rp && tt < lr.k13) ? lr.W13[tt + (size_t)cc * lr.k13] : 0.0;
+            X2[t][x] = (cc < rp && tt < lr.k24) ? lr.W24[tt + (size_t)cc * lr.k24] : 0.0;
         }
+        __syncthreads();
+#pragma unroll 4
+        for (int t = 0; t < 16; ++t) {
+            double y[4], x1[4], x2[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                y[q] = Y[tx + 16 * q][t];
+                x1[q] = X1[t][ty + 16 * q];
+                x2[q] = X2[t][ty + 16 * q];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool top = (a0 + tx + 16 * q) < n1;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) acc[q][p] += y[q] * (top ? x1[p] : x2[p]);
+            }
+        }
+        __syncthreads();
     }
+    merge_store(M, T, in + M.s1, in + M.s2, out, acc, a0, c0, tx, ty, bf, cf, df);
 }
 
 // ----------------------------------------------------------------------------- root
@@ -636,12 +702,11 @@ __global__ void k_root_finalize(const double *__restrict__ ws, int r, int n, dou
 
 // ----------------------------------------------------------------------------- apply
 
-// V = T G: T is N x N, G and V are N x B, all column-major.  64 x 64 tile per CTA.
-__global__ void __launch_bounds__(256)
-k_apply(const double *__restrict__ T, const double *__restrict__ G, double *__restrict__ V, int N, int B) {
+// One 64 x 64 tile of V = T G: T is N x N, G and V are N x B, all column-major.
+__device__ __forceinline__ void apply_tile(const double *__restrict__ T, const double *__restrict__ G,
+                                           double *__restrict__ V, int N, int B, int i0, int j0) {
     __shared__ double At[16][65];
     __shared__ double Bt[16][65];
-    const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     double acc[4][4] = {};
     for (int k0 = 0; k0 < N; k0 += 16) {
@@ -675,6 +740,27 @@ k_apply(const double *__restrict__ T, const double *__restrict__ G, double *__re
             if (i < N) V[(size_t)j * N + i] = acc[q][p];
         }
     }
+}
+
+// V = T G, 64 x 64 tile per CTA.
+__global__ void __launch_bounds__(256)
+k_apply(const double *__restrict__ T, const double *__restrict__ G, double *__restrict__ V, int N, int B) {
+    apply_tile(T, G, V, N, B, blockIdx.x * 64, blockIdx.y * 64);
+}
+
+// V_d = T_d G_d for several operators in one launch: CTA x takes tile x - tile0 of the
+// descriptor whose range holds it (descriptors sorted by tile0, found by bisection).
+__global__ void __launch_bounds__(256) k_apply_many(const ApplyDesc *__restrict__ ds, int nd) {
+    int lo = 0, hi = nd - 1;
+    const int x = blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ds[mid].tile0 <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    const ApplyDesc D = ds[lo];
+    const int t = x - D.tile0, ti = (D.N + 63) / 64;
+    apply_tile(D.T, D.G, D.V, D.N, D.B, (t % ti) * 64, (t / ti) * 64);
 }
 
 // ----------------------------------------------------------------------------- launchers
@@ -756,6 +842,17 @@ cudaError_t launch_merge_assemble(const MergeDesc *md, int nm, const int *tab, c
     return cudaGetLastError();
 }
 
+cudaError_t launch_merge_update_lr(const MergeDesc *md, const MergeDesc &h_md, const int *tab, const double *in,
+                                   const LrUpdate &lr, double *out, const double *b, const double *c, const double *d,
+                                   cudaStream_t s, KTimer &kt) {
+    const int rp = h_md.rp, K = std::max(lr.k13, lr.k24);
+    dim3 g((rp + 63) / 64, (rp + 63) / 64, 1);
+    kt.begin(GM_K_MERGEUPDATE, 2.0 * (double)rp * rp * K, s);
+    k_merge_update_lr<<<g, 256, 0, s>>>(md, tab, in, lr, out, b, c, d);
+    kt.end(s);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_merge_update(const MergeDesc *md, const std::vector<MergeDesc> &h_md, const int *tab,
                                 const double *in, const double *ws, double *out, int max_rp, const double *b,
                                 const double *c, const double *d, int n, cudaStream_t s, KTimer &kt) {
@@ -786,6 +883,19 @@ cudaError_t launch_root_finalize(const double *ws, int r, int n, double *T, cuda
     kt.begin(GM_K_ROOT, 0.0, s);
     k_root_finalize<<<bx, 256, 0, s>>>(ws, r, n, T);
     kt.end(s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_many(std::vector<ApplyDesc> &h, ApplyDesc *d, cudaStream_t s) {
+    int tiles = 0;
+    for (ApplyDesc &q : h) {
+        q.tile0 = tiles;
+        tiles += ((q.N + 63) / 64) * ((q.B + 63) / 64);
+    }
+    if (tiles == 0) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(ApplyDesc), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    k_apply_many<<<tiles, 256, 0, s>>>(d, (int)h.size());
     return cudaGetLastError();
 }
 

@@ -471,7 +471,7 @@ k_mx_merge_update_tc(const MergeDesc *__restrict__ md, const int *__restrict__ t
                      float2 *__restrict__ out, const __nv_bfloat16 *__restrict__ ydig, const int *__restrict__ yex,
                      const __nv_bfloat16 *__restrict__ xdig, const int *__restrict__ xex, int64_t plane,
                      const double *__restrict__ bf, const double *__restrict__ cf, const double *__restrict__ df,
-                     Status *__restrict__ st) {
+                     Status *__restrict__ st, int limit) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr int STAGE = S * (MT_ROWS + MT_COLS) * 32;  // bytes per stage
@@ -479,6 +479,7 @@ k_mx_merge_update_tc(const MergeDesc *__restrict__ md, const int *__restrict__ t
     __shared__ uint32_t s_tmem;
     __shared__ int s_ye[MT_ROWS], s_xe[MT_COLS];
     __shared__ int s_bad;
+    __shared__ int s_loaded, s_committed;  // tiles of the current chunk copied / committed
     const MergeDesc M = md[blockIdx.z];
     const int rp = M.rp;
     const int a0 = blockIdx.x * MT_ROWS, c0 = blockIdx.y * MT_COLS;
@@ -544,20 +545,26 @@ k_mx_merge_update_tc(const MergeDesc *__restrict__ md, const int *__restrict__ t
     for (int t0 = 0; t0 < ntile && !bad; t0 += MT_KTILES) {
         const int nk = min(ntile - t0, MT_KTILES);
         const bool first = t0 == 0;
+        const unsigned bpar0 = bpar;
         if (tid == 32) {  // producer: copies, each stage refilled once its products landed
+            int nl = 0;
             for (int t = 0; t < nk && !bad; ++t) {
                 const int sg = t % MT_STAGES;
                 if (t >= MT_STAGES &&
-                    !mbar_wait_bounded(&empty[sg], ((bpar >> sg) & 1u) ^ (uint32_t)((t / MT_STAGES - 1) & 1), 1 << 22))
+                    !mbar_wait_bounded(&empty[sg], ((bpar >> sg) & 1u) ^ (uint32_t)((t / MT_STAGES - 1) & 1), limit)) {
                     bad = true;
-                else
+                } else {
                     load_tile(t0 + t, sg);
+                    ++nl;
+                }
             }
+            s_loaded = nl;
             if (bad) s_bad = 1;
         } else if (tid == 0) {  // products: wait for a stage's copies, issue, commit
+            int nc = 0;
             for (int kt = 0; kt < nk; ++kt) {
                 const int sg = kt % MT_STAGES;
-                if (!mbar_wait_bounded(&full[sg], ((bpar >> sg) & 1u) ^ (uint32_t)((kt / MT_STAGES) & 1), 1 << 22)) {
+                if (!mbar_wait_bounded(&full[sg], ((bpar >> sg) & 1u) ^ (uint32_t)((kt / MT_STAGES) & 1), limit)) {
                     bad = true;
                     break;
                 }
@@ -570,13 +577,15 @@ k_mx_merge_update_tc(const MergeDesc *__restrict__ md, const int *__restrict__ t
                         umma_bf16(tmem + (uint32_t)((a + b) * MT_COLS), da + (uint64_t)(a * 4096 >> 4),
                                   db + (uint64_t)(b * 2048 >> 4), idesc, (kt > 0 || a > 0) ? 1u : 0u);
                 umma_commit(&empty[sg]);
+                ++nc;
             }
+            s_committed = nc;
             if (bad) s_bad = 1;
         }
         if (warp < 2) __syncwarp();
         // everyone: the chunk's last products (they complete in order)
         const int sl = (nk - 1) % MT_STAGES;
-        if (!mbar_wait_bounded(&empty[sl], ((bpar >> sl) & 1u) ^ (uint32_t)(((nk - 1) / MT_STAGES) & 1), 1 << 22))
+        if (!mbar_wait_bounded(&empty[sl], ((bpar >> sl) & 1u) ^ (uint32_t)(((nk - 1) / MT_STAGES) & 1), limit))
             s_bad = 1;
 #pragma unroll
         for (int q = 0; q < MT_STAGES; ++q)  // tiles of this chunk on stage q
@@ -585,6 +594,20 @@ k_mx_merge_update_tc(const MergeDesc *__restrict__ md, const int *__restrict__ t
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
         if (s_bad) {
+            // gave up: before the tensor memory is released, wait (bounded) for the products
+            // committed (they complete in order: the last one suffices) and for the copies
+            // issued but not yet consumed (at most one per stage)
+            if (tid == 0) {
+                const int nc = s_committed, nl = s_loaded;
+                if (nc > 0) {
+                    const int c = nc - 1, sg = c % MT_STAGES;
+                    mbar_wait_bounded(&empty[sg], ((bpar0 >> sg) & 1u) ^ (uint32_t)((c / MT_STAGES) & 1), DRAIN_POLLS);
+                }
+                for (int t = nc; t < nl; ++t) {
+                    const int sg = t % MT_STAGES;
+                    mbar_wait_bounded(&full[sg], ((bpar0 >> sg) & 1u) ^ (uint32_t)((t / MT_STAGES) & 1), DRAIN_POLLS);
+                }
+            }
             bad = true;
             break;
         }
@@ -739,6 +762,52 @@ k_mx_apply(const __nv_bfloat16 *__restrict__ tdig, const int *__restrict__ tex, 
                          });
 }
 
+// Several split-product applies in one pair of launches (serving: vectors for different
+// operators).  k_mx_slice_G_many slices the columns of every G_d (warp per column;
+// CTA x holds columns 4 (x - blk0) .. of the descriptor whose range holds it), then
+// k_mx_apply_many runs the 64 x 64 tiles of every V_d = T_d G_d.
+template <int S>
+__global__ void __launch_bounds__(128) k_mx_slice_G_many(const MxApplyDesc *__restrict__ ds, int nd) {
+    int lo = 0, hi = nd - 1;
+    const int x = blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ds[mid].blk0 <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    const MxApplyDesc D = ds[lo];
+    const int j = (x - D.blk0) * 4 + (threadIdx.x >> 5);
+    if (j >= D.B) return;
+    auto get = [&](int kk) -> float2 { return df_from_d(D.G[(size_t)j * D.N + kk]); };
+    warp_slice_row<S>(get, D.N, D.kpad, D.gdig, D.gplane, j, D.gex);
+}
+
+template <int S>
+__global__ void __launch_bounds__(PIPE_THREADS) k_mx_apply_many(const MxApplyDesc *__restrict__ ds, int nd) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];  // pipe_smem_bytes(S)
+    int lo = 0, hi = nd - 1;
+    const int x = blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ds[mid].tile0 <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    const MxApplyDesc D = ds[lo];
+    const int t = x - D.tile0, ti = (D.N + 63) / 64;
+    const int i0 = (t % ti) * 64, j0 = (t / ti) * 64, N = D.N, B = D.B;
+    double *V = D.V;
+    digit_gemm_pipe<S>(D.tdig, (int64_t)N * D.kpad, D.kpad, i0, N, D.tex, D.gdig, D.gplane, D.kpad, j0, B, D.gex, N,
+                       (__nv_bfloat16 *)smem_raw, [&](const int *r, const int *cl, const float2 *v, bool first) {
+#pragma unroll
+                           for (int q = 0; q < 4; ++q) {
+                               const int i = i0 + r[q], j = j0 + cl[q];
+                               if (i >= N || j >= B) continue;
+                               double *o = V + (size_t)j * N + i;
+                               *o = first ? df_to_d(v[q]) : *o + df_to_d(v[q]);
+                           }
+                       });
+}
+
 // ----------------------------------------------------------------------------- launchers
 
 #define MX_SPLIT_DISPATCH(split, CALL) \
@@ -820,7 +889,7 @@ cudaError_t mx_merge_update(const MergeDesc *md, const std::vector<MergeDesc> &h
                             const float2 *in, const float2 *ws, float2 *out, int max_rp, int split,
                             __nv_bfloat16 *ydig, int *yex, __nv_bfloat16 *xdig, int *xex, int64_t plane,
                             const double *b, const double *c, const double *d, int n, Status *st, cudaStream_t s,
-                            KTimer &kt) {
+                            KTimer &kt, int wait_limit) {
     double fl = 0;
     for (const MergeDesc &M : h_md) fl += 2.0 * (double)M.rp * M.rp * M.sp;
     const int nm = (int)h_md.size();
@@ -851,7 +920,7 @@ cudaError_t mx_merge_update(const MergeDesc *md, const std::vector<MergeDesc> &h
                                                        (int)mx_merge_tc_smem(SS))));
     if (e != cudaSuccess) return e;
     MX_SPLIT_DISPATCH(split, (k_mx_merge_update_tc<SS><<<g, PIPE_THREADS, mx_merge_tc_smem(SS), s>>>(
-                                 md, tab, in, out, ydig, yex, xdig, xex, plane, b, c, d, st)));
+                                 md, tab, in, out, ydig, yex, xdig, xex, plane, b, c, d, st, wait_limit)));
     kt.end(s);
     return cudaGetLastError();
 }
@@ -878,6 +947,26 @@ cudaError_t mx_root_finalize(const float2 *ws, int r, int n, double *T, float2 *
     MX_SPLIT_DISPATCH(split, (k_mx_slice_T<SS><<<(N + 3) / 4, 128, 0, s>>>(Tdf, N, kpad, tdig, (int64_t)N * kpad,
                                                                            tex)));
     kt.end(s);
+    return cudaGetLastError();
+}
+
+cudaError_t mx_apply_many(std::vector<MxApplyDesc> &h, MxApplyDesc *d, int split, cudaStream_t s) {
+    int tiles = 0, blks = 0;
+    for (MxApplyDesc &q : h) {
+        q.tile0 = tiles;
+        q.blk0 = blks;
+        tiles += ((q.N + 63) / 64) * ((q.B + 63) / 64);
+        blks += (q.B + 3) / 4;
+    }
+    if (tiles == 0) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(MxApplyDesc), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    const int nd = (int)h.size();
+    MX_SPLIT_DISPATCH(split, (k_mx_slice_G_many<SS><<<blks, 128, 0, s>>>(d, nd)));
+    MX_SPLIT_DISPATCH(split, (e = cudaFuncSetAttribute(k_mx_apply_many<SS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)pipe_smem_bytes(SS))));
+    if (e != cudaSuccess) return e;
+    MX_SPLIT_DISPATCH(split, (k_mx_apply_many<SS><<<tiles, PIPE_THREADS, pipe_smem_bytes(SS), s>>>(d, nd)));
     return cudaGetLastError();
 }
 

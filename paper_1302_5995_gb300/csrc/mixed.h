@@ -38,12 +38,28 @@ cudaError_t mx_merge_update(const MergeDesc *md, const std::vector<MergeDesc> &h
                             const float2 *in, const float2 *ws, float2 *out, int max_rp, int split,
                             __nv_bfloat16 *ydig, int *yex, __nv_bfloat16 *xdig, int *xex, int64_t plane,
                             const double *b, const double *c, const double *d, int n, Status *st, cudaStream_t s,
-                            KTimer &kt);
+                            KTimer &kt, int wait_limit);
 cudaError_t mx_root_assemble(const float2 *S, int r, int n, float2 *ws, const double *b, const double *c,
                              const double *d, cudaStream_t s, KTimer &kt);
 int mx_kpad(int N);
 cudaError_t mx_root_finalize(const float2 *ws, int r, int n, double *T, float2 *Tdf, __nv_bfloat16 *tdig, int *tex,
                              int split, cudaStream_t s, KTimer &kt);
+// One operator of a grouped split-product apply: V (N x B, FP64) = T G from T's digit
+// planes (tdig, tex: N x kpad per plane, built with the handle) and G (FP64), sliced into
+// gdig / gex (gplane elements per plane, at least B * kpad; B exponents).
+struct MxApplyDesc {
+    const __nv_bfloat16 *tdig;
+    const int *tex;
+    const double *G;
+    double *V;
+    __nv_bfloat16 *gdig;
+    int *gex;
+    int64_t gplane;
+    int N, B, kpad, tile0, blk0, pad;
+};
+// Slices every G and runs every V = T G in two launches (descriptors uploaded to d,
+// device memory for h.size(); tile0 and blk0 filled in here).  All share split.
+cudaError_t mx_apply_many(std::vector<MxApplyDesc> &h, MxApplyDesc *d, int split, cudaStream_t s);
 cudaError_t mx_apply(const __nv_bfloat16 *tdig, const int *tex, const double *G, __nv_bfloat16 *gdig, int *gex,
                      double *V, int N, int B, int split, cudaStream_t s);
 

@@ -93,6 +93,11 @@ __device__ __forceinline__ void umma_commit(void *mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(mbar)));
 }
 
+// Default poll count of the bounded waits, and the fixed bound of the waits a kernel
+// makes, after giving up, for its own copies and products still in flight.
+constexpr int WAIT_POLLS = 1 << 22;
+constexpr int DRAIN_POLLS = 1 << 24;
+
 // Wait for completion `parity` of an mbarrier, giving up after `limit` polls (false).
 __device__ __forceinline__ bool mbar_wait_bounded(void *mbar, uint32_t parity, int limit) {
     uint32_t done = 0;

@@ -1,14 +1,20 @@
 // Serving runtime for resident DtN operators (the solve stage of Section 1.1 under load).
 //
 // A server owns operators added to it, admits them against a device-memory budget
-// (evicting the least recently used ones), and runs one worker thread with its own
-// stream.  Clients submit solve requests (any number of vectors for one operator) and
-// return immediately; the worker takes every request pending when it wakes, groups them
-// by operator and runs ONE solve per operator over the concatenated vectors (continuous
-// batching), then scatters the results back.  A request's latency is measured from its
-// submission to the host seeing its result complete.  Build requests run on the worker
-// too, before the solves taken with them, and admit their operator under the budget
-// with the id reserved at submission (solves may be queued for it at once).
+// (evicting the least recently used ones), and runs two worker threads:
+//   - the solve worker, on a high-priority stream, takes every pending solve request
+//     whose operator exists when it wakes, groups them by operator and stages each
+//     operator's vectors contiguously, then applies ALL of them in one gm_solve_many
+//     call -- one launch per precision class over the vectors of every operator in the
+//     batch (continuous batching across operators) -- and scatters the results back;
+//   - the build worker, on a low-priority stream, runs build requests one at a time while
+//     solves go on (the device overlaps the two), then admits each built operator under
+//     the budget with the id reserved at submission.  Solves queued for an operator that
+//     is still being built wait in the queue until it is admitted (or has failed).
+// A request's latency is measured from its submission to the host seeing its result.
+// Completion callbacks run on the worker that finished the request, outside the lock;
+// gm_server_sync and gm_server_set_callback wait until no callback is running (unless
+// called from a callback, which would otherwise wait for itself).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -48,7 +54,7 @@ struct Operator {
     int n;
     long long bytes;
     long long last_use;
-    int busy;  // being served by the worker: never evicted meanwhile
+    int busy;  // being served by the solve worker: never evicted meanwhile
 };
 
 }  // namespace
@@ -57,28 +63,37 @@ struct gm_server {
     int device = 0;
     long long budget = 0, used = 0;
     int batching = 1;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;   // solves (highest priority)
+    cudaStream_t bstream = nullptr;  // builds (lowest priority)
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<Request> queue;
+    std::condition_variable cv_work, cv_build, cv_done;
+    std::deque<Request> queue;   // solve requests
+    std::deque<Request> bqueue;  // build requests
     std::map<int, Operator> ops;
     std::set<int> building;  // ids reserved by build requests not yet finished
-    gm_server_callback cb = nullptr;  // called for every completed request (worker thread)
+    gm_server_callback cb = nullptr;  // called for every completed request (worker threads)
     void *cb_user = nullptr;
+    int cb_running = 0;  // callbacks in progress
     std::map<long long, int> status;  // request id -> result code once completed
     int next_op = 1;
     long long next_req = 1, tick = 0;
     bool stop = false;
-    int in_flight = 0;
+    int in_flight = 0, b_in_flight = 0;
     // statistics
     std::vector<double> lat_ms;
     long long vectors = 0, solves = 0, evictions = 0;
     Clock::time_point first_submit{}, last_done{};
     bool any = false;
-    std::thread worker;
-    // device staging of the batched solve (grown on demand, worker-owned)
+    std::thread worker, builder;
+    std::thread::id worker_id, builder_id;
+    // device staging of the batched solve (grown on demand, solve-worker-owned)
     double *dg = nullptr, *dv = nullptr;
     size_t cap = 0;
+
+    bool on_worker() const {
+        const std::thread::id me = std::this_thread::get_id();
+        return me == worker_id || me == builder_id;
+    }
 
     int ensure(size_t doubles) {
         if (doubles <= cap) return GM_OK;
@@ -111,12 +126,13 @@ struct gm_server {
         return true;
     }
 
-    // A build request: the operator is built on the worker's stream, then admitted under
-    // the budget with the id reserved at submission.  Called with mu held; unlocks it
-    // during the build.
+    // A build request: the operator is built on the build stream, then admitted under the
+    // budget with the id reserved at submission.  Called with mu held; unlocks it during
+    // the build.
     int run_build(const Request &r, std::unique_lock<std::mutex> &lk) {
         gm_opts o = r.opts;
-        o.stream = stream;
+        o.stream = bstream;
+        o.background = 1;
         gm_handle *h = nullptr;
         lk.unlock();
         int rc = gm_build_ex(&o, r.b, r.c, r.d, r.n, r.leaf, r.tol, &h);
@@ -134,80 +150,136 @@ struct gm_server {
         return GM_OK;
     }
 
-    // Run one operator's requests as one solve over their concatenated vectors.
-    int serve(const Operator &op, const std::vector<Request> &rq) {
-        const size_t N = 4 * (size_t)op.n;
+    // Every operator's requests of one batch: one grouped solve over all of them (each
+    // operator's vectors concatenated), or, unbatched, one solve per request.  rc[i] is
+    // operator i's result.
+    void serve(const std::vector<Operator> &opv, const std::vector<std::vector<Request>> &rq, std::vector<int> &rc) {
+        const size_t no = opv.size();
+        rc.assign(no, GM_OK);
         if (!batching) {  // the unbatched baseline: one solve per request
-            for (const Request &r : rq) {
-                const int rc = gm_solve(op.h, r.g, r.dudn, r.batch, stream);
-                if (rc) return rc;
+            for (size_t i = 0; i < no; ++i)
+                for (const Request &r : rq[i])
+                    if (rc[i] == GM_OK) rc[i] = gm_solve(opv[i].h, r.g, r.dudn, r.batch, stream);
+            if (cudaStreamSynchronize(stream) != cudaSuccess)
+                for (int &x : rc)
+                    if (x == GM_OK) x = GM_ECUDA;
+            return;
+        }
+        std::vector<size_t> at(no + 1, 0);
+        std::vector<int> tot(no, 0);
+        for (size_t i = 0; i < no; ++i) {
+            for (const Request &r : rq[i]) tot[i] += r.batch;
+            at[i + 1] = at[i] + 4 * (size_t)opv[i].n * tot[i];
+        }
+        int e = ensure(at[no]);
+        std::vector<gm_handle *> hs(no);
+        std::vector<const double *> gp(no);
+        std::vector<double *> vp(no);
+        for (size_t i = 0; i < no && e == GM_OK; ++i) {
+            const size_t N = 4 * (size_t)opv[i].n;
+            size_t off = at[i];
+            for (const Request &r : rq[i]) {
+                if (cudaMemcpyAsync(dg + off, r.g, N * r.batch * 8, cudaMemcpyDefault, stream) != cudaSuccess)
+                    e = GM_ECUDA;
+                off += N * r.batch;
             }
-            return cudaStreamSynchronize(stream) == cudaSuccess ? GM_OK : GM_ECUDA;
+            hs[i] = opv[i].h;
+            gp[i] = dg + at[i];
+            vp[i] = dv + at[i];
         }
-        size_t total = 0;
-        for (const Request &r : rq) total += (size_t)r.batch;
-        int rc = ensure(N * total);
-        if (rc) return rc;
-        size_t at = 0;
-        for (const Request &r : rq) {
-            if (cudaMemcpyAsync(dg + at * N, r.g, N * r.batch * 8, cudaMemcpyDefault, stream) != cudaSuccess)
-                return GM_ECUDA;
-            at += r.batch;
+        if (e == GM_OK) {
+            e = gm_solve_many((int)no, hs.data(), gp.data(), vp.data(), tot.data(), stream);
+            if (e != GM_OK && no > 1)  // find which operators fail: each alone
+                for (size_t i = 0; i < no; ++i) rc[i] = gm_solve_many(1, &hs[i], &gp[i], &vp[i], &tot[i], stream);
+            else
+                rc.assign(no, e);
+        } else {
+            rc.assign(no, e);
         }
-        if ((rc = gm_solve(op.h, dg, dv, (int)total, stream))) return rc;
-        at = 0;
-        for (const Request &r : rq) {
-            if (cudaMemcpyAsync(r.dudn, dv + at * N, N * r.batch * 8, cudaMemcpyDefault, stream) != cudaSuccess)
-                return GM_ECUDA;
-            at += r.batch;
+        for (size_t i = 0; i < no; ++i) {
+            if (rc[i] != GM_OK) continue;
+            const size_t N = 4 * (size_t)opv[i].n;
+            size_t off = at[i];
+            for (const Request &r : rq[i]) {
+                if (cudaMemcpyAsync(r.dudn, dv + off, N * r.batch * 8, cudaMemcpyDefault, stream) != cudaSuccess)
+                    rc[i] = GM_ECUDA;
+                off += N * r.batch;
+            }
         }
-        return cudaStreamSynchronize(stream) == cudaSuccess ? GM_OK : GM_ECUDA;
+        if (cudaStreamSynchronize(stream) != cudaSuccess)
+            for (int &x : rc)
+                if (x == GM_OK) x = GM_ECUDA;
     }
 
-    void run() {
+    // Callbacks for completed requests, outside the lock; mu held on entry and exit.
+    void notify(std::unique_lock<std::mutex> &lk, const std::vector<long long> &ids) {
+        const gm_server_callback call = cb;
+        void *const user = cb_user;
+        if (call) ++cb_running;
+        cv_done.notify_all();
+        if (!call) return;
+        std::vector<std::pair<long long, int>> done;
+        for (long long id : ids) done.push_back({id, status[id]});
+        lk.unlock();
+        for (const auto &q : done) call(q.first, q.second, user);
+        lk.lock();
+        --cb_running;
+        cv_done.notify_all();
+    }
+
+    bool ready(const Request &r) const { return !building.count(r.op); }
+
+    void run_solves() {
         cudaSetDevice(device);
         std::unique_lock<std::mutex> lk(mu);
         for (;;) {
-            cv_work.wait(lk, [&] { return stop || !queue.empty(); });
-            if (queue.empty() && stop) break;
-            std::vector<Request> take(queue.begin(), queue.end());
-            queue.clear();
+            cv_work.wait(lk, [&] {
+                if (stop) return true;
+                for (const Request &r : queue)
+                    if (ready(r)) return true;
+                return false;
+            });
+            std::vector<Request> take;
+            std::deque<Request> keep;
+            for (const Request &r : queue) (ready(r) ? take.push_back(r) : keep.push_back(r));
+            if (take.empty() && stop) break;
+            queue.swap(keep);
             in_flight = (int)take.size();
-            const gm_server_callback call = cb;
-            void *const user = cb_user;
-            // builds first, in arrival order, so that solves queued behind a build find it
-            for (const Request &r : take)
-                if (r.build) {
-                    status[r.id] = run_build(r, lk);
-                    building.erase(r.op);
-                    last_done = Clock::now();
-                }
-            // solves grouped by operator, in order of first arrival
+            // group by operator, in order of first arrival
             std::vector<int> order;
             std::map<int, std::vector<Request>> by_op;
             for (const Request &r : take) {
-                if (r.build) continue;
                 if (!by_op.count(r.op)) order.push_back(r.op);
                 by_op[r.op].push_back(r);
             }
+            std::vector<Operator> opv;
+            std::vector<std::vector<Request>> rq;
+            std::vector<int> ids;
             for (int id : order) {
                 auto it = ops.find(id);
-                std::vector<Request> &rq = by_op[id];
-                int rc = GM_EINVAL;  // the operator was evicted after the request was queued
-                if (it != ops.end()) {
-                    it->second.last_use = ++tick;
-                    it->second.busy = 1;
-                    const Operator op = it->second;
-                    lk.unlock();
-                    rc = serve(op, rq);
-                    lk.lock();
-                    ops[id].busy = 0;
-                    ++solves;
+                if (it == ops.end()) {  // evicted after the request was queued, or its build failed
+                    for (const Request &r : by_op[id]) status[r.id] = GM_EINVAL;
+                    continue;
                 }
-                const Clock::time_point done = Clock::now();
-                for (const Request &r : rq) {
-                    status[r.id] = rc;
-                    if (rc == GM_OK) {
+                it->second.last_use = ++tick;
+                it->second.busy = 1;
+                opv.push_back(it->second);
+                rq.push_back(by_op[id]);
+                ids.push_back(id);
+            }
+            std::vector<int> rc;
+            if (!opv.empty()) {
+                lk.unlock();
+                serve(opv, rq, rc);
+                lk.lock();
+                ++solves;
+            }
+            const Clock::time_point done = Clock::now();
+            for (size_t i = 0; i < ids.size(); ++i) {
+                ops[ids[i]].busy = 0;
+                for (const Request &r : rq[i]) {
+                    status[r.id] = rc[i];
+                    if (rc[i] == GM_OK) {
                         lat_ms.push_back(std::chrono::duration<double, std::milli>(done - r.t_submit).count());
                         vectors += r.batch;
                         last_done = done;
@@ -215,14 +287,28 @@ struct gm_server {
                 }
             }
             in_flight = 0;
-            cv_done.notify_all();
-            if (call) {  // outside the lock: the callback may call back into the server
-                std::vector<std::pair<long long, int>> done;
-                for (const Request &r : take) done.push_back({r.id, status[r.id]});
-                lk.unlock();
-                for (const auto &q : done) call(q.first, q.second, user);
-                lk.lock();
-            }
+            std::vector<long long> fin;
+            for (const Request &r : take) fin.push_back(r.id);
+            notify(lk, fin);
+        }
+    }
+
+    void run_builds() {
+        cudaSetDevice(device);
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            cv_build.wait(lk, [&] { return stop || !bqueue.empty(); });
+            if (stop) break;
+            const Request r = bqueue.front();
+            bqueue.pop_front();
+            b_in_flight = 1;
+            const int rc = run_build(r, lk);
+            status[r.id] = rc;
+            building.erase(r.op);
+            last_done = Clock::now();
+            b_in_flight = 0;
+            cv_work.notify_all();  // solves queued for this operator may run now
+            notify(lk, {r.id});
         }
     }
 };
@@ -250,13 +336,19 @@ int gm_server_create(long long budget_bytes, int batching, gm_server **out) {
     gm_server *s = new gm_server();
     s->budget = budget_bytes;
     s->batching = batching ? 1 : 0;
-    if (cudaGetDevice(&s->device) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    int lo = 0, hi = 0;  // numerically lower = higher priority
+    if (cudaGetDevice(&s->device) != cudaSuccess || cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&s->stream, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&s->bstream, cudaStreamNonBlocking, lo) != cudaSuccess) {
         cudaGetLastError();
+        if (s->stream) cudaStreamDestroy(s->stream);
         delete s;
         return GM_ECUDA;
     }
-    s->worker = std::thread([s] { s->run(); });
+    s->worker = std::thread([s] { s->run_solves(); });
+    s->builder = std::thread([s] { s->run_builds(); });
+    s->worker_id = s->worker.get_id();
+    s->builder_id = s->builder.get_id();
     *out = s;
     return GM_OK;
 }
@@ -293,7 +385,7 @@ int gm_server_submit(gm_server *s, int op_id, const double *g, double *dudn, int
 
 int gm_server_submit_build(gm_server *s, const gm_opts *opts, const double *b, const double *c, const double *d,
                            int n, int leaf, double tol, int *op_id, long long *req_id) {
-    if (!s || !b || !c || !d || n < 2 || leaf < 4 || !(tol >= 0.0) || !op_id || !req_id) return GM_EINVAL;
+    if (!s || !b || !c || !d || n < 2 || leaf < 3 || !(tol >= 0.0) || !op_id || !req_id) return GM_EINVAL;
     Request r{0, 0, nullptr, nullptr, 0, Clock::now()};
     r.build = true;
     gm_opts_default(&r.opts);
@@ -308,18 +400,20 @@ int gm_server_submit_build(gm_server *s, const gm_opts *opts, const double *b, c
     r.id = s->next_req++;
     r.op = s->next_op++;
     s->building.insert(r.op);
-    s->queue.push_back(r);
+    s->bqueue.push_back(r);
     *op_id = r.op;
     *req_id = r.id;
-    s->cv_work.notify_one();
+    s->cv_build.notify_one();
     return GM_OK;
 }
 
 int gm_server_set_callback(gm_server *s, gm_server_callback cb, void *user) {
     if (!s) return GM_EINVAL;
-    std::lock_guard<std::mutex> lk(s->mu);
+    std::unique_lock<std::mutex> lk(s->mu);
     s->cb = cb;
     s->cb_user = user;
+    // a callback already started with the previous function finishes before this returns
+    if (!s->on_worker()) s->cv_done.wait(lk, [&] { return s->cb_running == 0; });
     return GM_OK;
 }
 
@@ -343,7 +437,11 @@ int gm_server_wait(gm_server *s, long long req_id) {
 int gm_server_sync(gm_server *s) {
     if (!s) return GM_EINVAL;
     std::unique_lock<std::mutex> lk(s->mu);
-    s->cv_done.wait(lk, [&] { return s->queue.empty() && s->in_flight == 0; });
+    const bool mine = s->on_worker();
+    s->cv_done.wait(lk, [&] {
+        return s->queue.empty() && s->bqueue.empty() && s->in_flight == 0 && s->b_in_flight == 0 &&
+               (mine || s->cb_running == 0);
+    });
     return GM_OK;
 }
 
@@ -379,12 +477,15 @@ void gm_server_destroy(gm_server *s) {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
         s->cv_work.notify_all();
+        s->cv_build.notify_all();
     }
     if (s->worker.joinable()) s->worker.join();
+    if (s->builder.joinable()) s->builder.join();
     for (auto &kv : s->ops) gm_free(kv.second.h);
     if (s->dg) cudaFree(s->dg);
     if (s->dv) cudaFree(s->dv);
     if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->bstream) cudaStreamDestroy(s->bstream);
     delete s;
 }
 

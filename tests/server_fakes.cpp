@@ -1,6 +1,7 @@
 // Test-only fakes for running the serving runtime (csrc/server.cpp) on the CPU: the
 // CUDA runtime calls it makes act on host memory, gm_solve / gm_info / gm_free act on
-// fake operators that record every call, and gm_build_ex builds such operators.  A gate
+// fake operators that record every call (gm_solve_many records each operator), and
+// gm_build_ex builds such operators.  A gate
 // can hold a solve inside the worker so that a test can queue requests behind it
 // (continuous batching) or try to evict an operator that is being served.  Every wait
 // here has a time limit.
@@ -39,6 +40,15 @@ cudaError_t cudaStreamCreateWithFlags(cudaStream_t *s, unsigned int) {
     *s = reinterpret_cast<cudaStream_t>(new char[1]);
     return cudaSuccess;
 }
+cudaError_t cudaStreamCreateWithPriority(cudaStream_t *s, unsigned int, int) {
+    *s = reinterpret_cast<cudaStream_t>(new char[1]);
+    return cudaSuccess;
+}
+cudaError_t cudaDeviceGetStreamPriorityRange(int *lo, int *hi) {
+    *lo = 0;
+    *hi = -5;
+    return cudaSuccess;
+}
 cudaError_t cudaStreamDestroy(cudaStream_t s) { delete[] reinterpret_cast<char *>(s); return cudaSuccess; }
 cudaError_t cudaStreamSynchronize(cudaStream_t) { return cudaSuccess; }
 cudaError_t cudaMalloc(void **p, size_t bytes) {
@@ -69,6 +79,35 @@ int gm_solve(gm_handle *h, const double *g, double *dudn, int batch, void *) {
     if (op->solve_rc) return op->solve_rc;
     for (long long i = 0; i < 4LL * op->n * batch; ++i) dudn[i] = 1000.0 * op->tag + 2.0 * g[i];
     return GM_OK;
+}
+
+// The grouped solve: every operator enters the call log in order (one gate hold per
+// call); the result is the first failing operator's code.
+int gm_solve_many(int count, gm_handle *const *hs, const double *const *g, double *const *dudn, const int *batch,
+                  void *) {
+    {
+        std::unique_lock<std::mutex> lk(mu);
+        for (int i = 0; i < count; ++i) {
+            call_tag.push_back(reinterpret_cast<FakeOp *>(hs[i])->tag);
+            call_batch.push_back(batch[i]);
+        }
+        if (gate_closed) {
+            ++blocked;
+            cv.notify_all();
+            cv.wait_for(lk, std::chrono::seconds(10), [] { return !gate_closed; });
+            --blocked;
+        }
+    }
+    int rc = GM_OK;
+    for (int i = 0; i < count; ++i) {
+        FakeOp *op = reinterpret_cast<FakeOp *>(hs[i]);
+        if (op->solve_rc) {
+            if (rc == GM_OK) rc = op->solve_rc;
+            continue;
+        }
+        for (long long k = 0; k < 4LL * op->n * batch[i]; ++k) dudn[i][k] = 1000.0 * op->tag + 2.0 * g[i][k];
+    }
+    return rc;
 }
 
 void gm_opts_default(gm_opts *o) {

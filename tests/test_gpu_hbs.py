@@ -86,22 +86,20 @@ def test_hbs_root_on_mixed_build(gm):
     assert rel_vec(solve_cols(op, G), dense.dtn() @ G) < 100 * tol
 
 
-def test_hbs_full_size_1024_against_dense_gpu(gm):
-    """The 1024 x 1024 convection problem: HBS root vs the dense FP64 GPU build."""
+def test_hbs_full_size_1024_against_oracle(gm):
+    """The 1024 x 1024 convection problem: HBS root on a mixed build against O2."""
     import torch
     n, leaf, m, tol = 1024, 16, 64, 1e-9
-    b, c, d = (torch.from_numpy(x).cuda() for x in inputs.convection_fields(n))
-    G = torch.from_numpy(inputs.gaussian_vectors(n, 16, 5)).cuda()
-    dense = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED)
+    fields = inputs.convection_fields(n)
+    G = inputs.gaussian_vectors(n, 16, 5)
+    Vo = nd_dense.build(*fields, n, leaf).T @ G
+    b, c, d = (torch.from_numpy(x).cuda() for x in fields)
     op = gm.build(b, c, d, n, leaf, tol=tol, hbs_leaf=m, precision=gm.PREC_MIXED)
-    Gt = G.T.contiguous()
-    V1 = torch.empty_like(Gt)
-    V2 = torch.empty_like(Gt)
-    dense.solve(Gt, out=V1)
-    op.solve(Gt, out=V2)
+    Gt = torch.from_numpy(np.ascontiguousarray(G.T)).cuda()
+    V = torch.empty_like(Gt)
+    op.solve(Gt, out=V)
     torch.cuda.synchronize()
-    a, r = V2.cpu().numpy().T, V1.cpu().numpy().T
-    assert rel_vec(a, r) < 100 * tol
+    assert rel_vec(V.cpu().numpy().T, Vo) < 100 * tol
     assert op.info()["hbs_max_rank"] < 96
 
 
@@ -113,14 +111,26 @@ def test_hbs_batch(gm):
         assert rel_mat(op.dtn(), To) < 1e-7
 
 
-def test_hbs_rejects_what_it_cannot_do(gm):
-    # high-frequency Helmholtz: level-1 ranks above the sampling cap
-    n, leaf = 256, 16
+def test_hbs_helmholtz_ranks_beyond_the_first_samples(gm):
+    """High-frequency Helmholtz (10 points per wavelength): the top nodes' ranks exceed
+    what the first 128 samples can hold, so the compression draws more.  The indefinite
+    operator amplifies the truncation (the oracle's own accelerated build is 25 tol off
+    the dense operator at tol 1e-9, n = 256): the bound is 1000 tol, and the error has to
+    follow tol down over four orders of magnitude."""
+    n, leaf, m = 256, 16, 64
     b, c, d = inputs.helmholtz_fields(n, inputs.nudged_wavenumber(n, leaf))
-    with pytest.raises(gm.GmError) as e:
-        gm.build(b, c, d, n, leaf, tol=1e-9, hbs_leaf=64)
-    assert e.value.code == gm.GM_EUNSUPPORTED
-    # the no-allocation solve has no HBS form
+    To = nd_dense.build(b, c, d, n, leaf).T
+    errs = {}
+    for tol in (1e-7, 1e-9, 1e-11):
+        op = gm.build(b, c, d, n, leaf, tol=tol, hbs_leaf=m)
+        if tol == 1e-9:
+            assert op.info()["hbs_max_rank"] > 96
+        errs[tol] = rel_mat(op.dtn(), To)
+        assert errs[tol] < 1000 * tol, (tol, errs[tol])
+    assert errs[1e-11] < 0.1 * errs[1e-9] < 0.01 * errs[1e-7], errs
+
+
+def test_no_alloc_solve_refuses_hbs_handles(gm):
     b, c, d = inputs.laplace_fields(64)
     op = gm.build(b, c, d, 64, 8, tol=1e-9, hbs_leaf=32)
     lib = gm.load_library()

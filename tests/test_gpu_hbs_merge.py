@@ -1,0 +1,88 @@
+"""The accelerated merge on the GPU (Section 5, Steps 1-3) against the oracle.
+
+A build with tol > 0 and keep_levels keeps every box's Schur complement, so each merge
+can be checked on its own: the oracle's accelerated merge (oracle/hbs.py) and the exact
+dense merge (eq. S_fromtwo_nd) are run on the GPU's own child Schur complements and
+compared with the parent the GPU formed.  Both sides truncate at tol (the GPU from
+Gaussian samples, the oracle from pivoted QR of the full blocks), so parity is a
+tolerance: within 100 tol of the exact merge and of the oracle's accelerated merge.
+"""
+import numpy as np
+import pytest
+
+from oracle import hbs as ohbs
+from oracle import nd_dense
+from paper_1302_5995_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gm():
+    from paper_1302_5995_gb300 import build_ext
+    build_ext.build()
+    import paper_1302_5995_gb300 as gm
+    return gm
+
+
+def rel_mat(A, B):
+    return np.abs(A - B).max() / np.abs(B).max()
+
+
+def merges_of(n, leaf, min_edge):
+    """(child 1, child 2, parent, shared edge) of every pairwise merge of the tree whose
+    shared edge has at least min_edge nodes, coarsest first."""
+    levels = nd_dense.quad_tree(n, leaf)
+    out = []
+    for lev in range(len(levels) - 1):
+        for P in levels[lev]:
+            sw, se, nw, ne = P.children()
+            south = nd_dense.Box(P.x0, P.y0, P.a, sw.b)
+            north = nd_dense.Box(P.x0, P.y0 + sw.b, P.a, nw.b)
+            for (b1, b2, par, edge) in ((sw, se, south, sw.b), (nw, ne, north, nw.b), (south, north, P, P.a)):
+                if edge >= min_edge:
+                    out.append((b1, b2, par, edge))
+    return out
+
+
+@pytest.mark.parametrize("fields,n,leaf,m,edge", [("convection", 128, 16, 16, 32), ("helmholtz", 96, 12, 16, 24)])
+def test_each_accelerated_merge_matches_the_oracle(gm, fields, n, leaf, m, edge):
+    tol = 1e-9
+    if fields == "convection":
+        b, c, d = inputs.convection_fields(n, seeds=(31, 32, 33))
+    else:
+        b, c, d = inputs.helmholtz_fields(n, inputs.nudged_wavenumber(n, leaf))
+    op = gm.build(b, c, d, n, leaf, tol=tol, hbs_leaf=m, hbs_min_edge=edge, keep_levels=True)
+    info = op.info()
+    assert info["hbs_merges"] > 0 and info["hbs_update_rank"] > 0
+    prob = nd_dense.Problem(b, c, d, n)
+    checked = 0
+    for (b1, b2, par, e) in merges_of(n, leaf, edge):
+        if e - 2 <= m:  # the library keeps merges with s' <= m dense
+            continue
+        S1 = op.schur(b1.x0, b1.y0, b1.a, b1.b)
+        S2 = op.schur(b2.x0, b2.y0, b2.a, b2.b)
+        Sp = op.schur(par.x0, par.y0, par.a, par.b)
+        exact = nd_dense.merge_two(prob, b1, S1, b2, S2, par)
+        acc, _, ranks = ohbs.accelerated_merge(prob, b1, S1, b2, S2, par, tol, m)
+        assert rel_mat(Sp, exact) < 100 * tol, (b1, b2, rel_mat(Sp, exact))
+        assert rel_mat(Sp, acc) < 100 * tol, (b1, b2, rel_mat(Sp, acc))
+        assert max(ranks) <= info["hbs_update_rank"] + 8
+        checked += 1
+    assert checked >= 3
+
+
+def test_accelerated_merges_cut_the_update_work(gm):
+    """The merge-update family's algorithmic flops: the factored update of Step 2 costs
+    2 rp^2 k per merge instead of 2 rp^2 s' (eq. matmult)."""
+    n, leaf, m, tol = 256, 16, 32, 1e-9
+    b, c, d = inputs.convection_fields(n)
+    dense = gm.build(b, c, d, n, leaf, timing=True)
+    acc = gm.build(b, c, d, n, leaf, tol=tol, hbs_leaf=m, hbs_min_edge=64, timing=True)
+    fd, fa = dense.info()["kernel_flops"], acc.info()["kernel_flops"]
+    assert fa["merge_update"] < 0.6 * fd["merge_update"]
+    G = inputs.gaussian_vectors(n, 8, 2)
+    To = nd_dense.build(b, c, d, n, leaf).T
+    V = acc.solve(np.ascontiguousarray(G.T)).reshape(8, 4 * n).T
+    err = (np.linalg.norm(V - To @ G, axis=0) / np.linalg.norm(To @ G, axis=0)).max()
+    assert err < 100 * tol

@@ -131,3 +131,66 @@ def test_device_buffers(gm):
     assert srv.wait(srv.submit(oid, g, out, 5)) == 0
     assert rel_vec(out.cpu().numpy().T, T @ g.cpu().numpy().T) < 1e-10
     srv.close()
+
+
+def test_solve_many_equals_each_operator_alone(gm):
+    """One grouped call over FP64, mixed-precision and HBS operators of different sizes:
+    every result equals the operator's own solve bit for bit (the grouped launches run
+    the same tiles in the same order)."""
+    import torch
+    fp = [gm.build(*p) for p in problems()]
+    mx = []
+    for i, (n, leaf) in enumerate(((128, 16), (96, 12))):
+        b, c, d = inputs.convection_fields(n, seeds=(50 + i, 60 + i, 70 + i))
+        mx.append(gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED))
+    b, c, d = inputs.convection_fields(64, seeds=(80, 81, 82))
+    hb = gm.build(b, c, d, 64, 8, tol=1e-9, hbs_leaf=32)
+    ops = fp + mx + [hb]
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    gs = [torch.randn(3 + 5 * i, 4 * op.n, dtype=torch.float64, device="cuda", generator=gen)
+          for i, op in enumerate(ops)]
+    outs = [torch.zeros_like(g) for g in gs]
+    gm.solve_many(ops, gs, outs)
+    for op, g, o in zip(ops, gs, outs):
+        lone = torch.zeros_like(g)
+        op.solve(g, out=lone)
+        torch.cuda.synchronize()
+        assert torch.equal(o, lone)
+
+
+def test_solves_complete_while_a_build_is_in_flight(gm):
+    """A long build (1024 x 1024 Helmholtz, FP64) runs on the server's build worker while
+    solve requests keep arriving: several complete before the build does, and each equals
+    the lone solve of its operator within 1e-10."""
+    import time
+    import torch
+    probs = problems()
+    lone = [gm.build(*p) for p in probs]
+    srv = gm.Server(1 << 36)
+    ids = [srv.add(gm.build(*p)) for p in probs]
+    cfg = inputs.config3(1024, 16)
+    dev = [torch.from_numpy(cfg[k]).cuda() for k in ("b", "c", "d")]
+    torch.cuda.synchronize()
+    done_at = {}
+    srv.set_callback(lambda rid, rc: done_at.setdefault(rid, time.perf_counter()))
+    oid, rb = srv.submit_build(*dev, 1024, 16)
+    rng = np.random.default_rng(11)
+    reqs = []
+    t_stop = time.perf_counter() + 20.0
+    while not srv.poll(rb)[0] and time.perf_counter() < t_stop:
+        k = int(rng.integers(0, 3))
+        n = probs[k][3]
+        g = np.ascontiguousarray(rng.standard_normal((4, 4 * n)))
+        out = np.zeros_like(g)
+        reqs.append((srv.submit(ids[k], g, out, 4), k, g, out))
+        time.sleep(0.002)
+    srv.sync()
+    assert srv.wait(rb) == 0
+    before = [r for r in reqs if done_at[r[0]] < done_at[rb]]
+    assert len(before) >= 3, (len(reqs), len(before))
+    for rid, k, g, out in reqs:
+        assert srv.wait(rid) == 0
+        ref = lone[k].solve(g)
+        assert rel_vec(out.T, ref.T) < 1e-10
+    srv.set_callback(None)
+    srv.close()
