@@ -198,7 +198,8 @@ int gm_build_batch(int count, const gm_problem *probs, const gm_opts *opts, doub
 
 /*
  * Solve stage (Section 1.1): dudn[:, v] = T g[:, v] for v < batch.
- *   g, dudn : 4n x batch, column-major, host or device.  They must not overlap.
+ *   g, dudn : 4n x batch, column-major, host or device.  They must not overlap
+ *             (GM_EINVAL when both are device buffers that do).
  * With device pointers the call is asynchronous on `stream`; with a host pointer it
  * returns after the result has reached the host.
  */
@@ -234,12 +235,14 @@ int gm_get_schur(gm_handle *h, int x0, int y0, int a, int b, double *S_out);
  * counterpart; it exists for callers that cannot let a library allocate device memory:
  * a serving loop that must not touch the allocator once it runs, or a host application
  * whose device memory belongs to another runtime's pool.
- *   Same arguments and result as gm_solve.  Host g / dudn are staged through one fixed
- *   16 MiB array of device memory inside the library (2^21 doubles; every GPU that loads
- *   the library holds it until the process exits) instead of freshly allocated buffers;
- *   device g / dudn are used in place.
- *   Limit: (4n * batch) doubles for each host-side argument, 2^21 doubles in total, else
- *   GM_ESCRATCH and nothing is done.
+ *   Same arguments and result as gm_solve (a mixed-precision handle gets the same
+ *   split-product apply).  Host g / dudn, and for a mixed-precision handle the digit
+ *   planes of g (split x batch x kpad bf16, kpad = 4n rounded up to 16) and their batch
+ *   exponents, are staged through one fixed 16 MiB array of device memory inside the
+ *   library (2^21 doubles; every GPU that loads the library holds it until the process
+ *   exits) instead of freshly allocated buffers; device g / dudn are used in place.
+ *   Limit: the parts above, each rounded up to 256 bytes, at most 2^21 doubles in total,
+ *   else GM_ESCRATCH and nothing is done.  GM_EINVAL if device g and dudn overlap.
  *   The first call on a device looks up the array's device address (once per device);
  *   make that first call before any stream capture.
  *   All calls share the array and it keeps the last call's contents: calls that overlap

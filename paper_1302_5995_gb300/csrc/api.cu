@@ -364,6 +364,14 @@ const double *gm::handle_dtn(gm_handle *h, int *n) {
     return h->T;
 }
 
+bool gm::handle_split(gm_handle *h, const void **tdig, const int **tex, int *split) {
+    if (!h || h->precision != GM_PREC_MIXED || h->hbs || !h->tdig) return false;
+    *tdig = h->tdig;
+    *tex = h->tex;
+    *split = h->split;
+    return true;
+}
+
 extern "C" void gm_free(gm_handle *h);
 
 namespace {
@@ -1057,6 +1065,7 @@ int gm_solve(gm_handle *h, const double *g, double *dudn, int batch, void *strea
     const int N = 4 * h->n;
     const size_t bytes = (size_t)N * batch * 8;
     bool gd = is_device_ptr(g), vd = is_device_ptr(dudn);
+    if (gd && vd && overlaps(g, dudn, (size_t)N * batch)) return GM_EINVAL;  // the apply reads g while it writes dudn
     DBuf gbuf, vbuf;
     const double *dg = g;
     double *dv = dudn;

@@ -123,6 +123,11 @@ int build_batch_plan(const std::vector<const Plan *> &plans, const std::vector<i
 
 // The dense DtN matrix of a handle and its grid size (nullptr for a NULL handle).
 const double *handle_dtn(gm_handle *h, int *n);
+// For a mixed-precision handle: the digit planes of T's rows (bf16), their exponents
+// and the digits per operand, as the split-product apply reads them; false otherwise.
+bool handle_split(gm_handle *h, const void **tdig, const int **tex, int *split);
+// True when [a, a + n) and [b, b + n) (doubles) share an element.
+inline bool overlaps(const double *a, const double *b, size_t n) { return a < b + n && b < a + n; }
 int validate_plan(const Plan &plan);
 
 }  // namespace gm

@@ -12,6 +12,7 @@
 
 #include "gm_internal.h"
 #include "kernels.h"
+#include "mixed.h"
 
 namespace {
 
@@ -62,7 +63,20 @@ extern "C" int gm_solve_static(gm_handle *h, const double *g, double *dudn, int 
     if (!T) return GM_EUNSUPPORTED;  // an HBS build has no dense T
     const size_t N = 4 * (size_t)n, elems = N * (size_t)batch;
     const bool gd = on_device(g), vd = on_device(dudn);
-    const size_t need = (gd ? 0 : elems) + (vd ? 0 : elems);
+    if (gd && vd && gm::overlaps(g, dudn, elems)) return GM_EINVAL;  // the apply reads g while it writes dudn
+    // a mixed-precision handle applies T by split products, like gm_solve: the digit
+    // planes of g (split x batch x kpad bf16) and their exponents also come from the
+    // array; every part starts on a 256-byte boundary
+    const void *tdig = nullptr;
+    const int *tex = nullptr;
+    int split = 0;
+    const bool mixed = gm::handle_split(h, &tdig, &tex, &split);
+    auto up = [](size_t d) { return (d + 31) / 32 * 32; };
+    const int kpad = gm::mx_kpad((int)N);
+    const size_t g_at = 0, v_at = g_at + (gd ? 0 : up(elems)), dig_at = v_at + (vd ? 0 : up(elems));
+    const size_t dig_doubles = mixed ? up((size_t)split * batch * kpad * 2 / 8 + 1) : 0;
+    const size_t ex_at = dig_at + dig_doubles;
+    const size_t need = ex_at + (mixed ? up((size_t)batch * sizeof(int) / 8 + 1) : 0);
     if (need > kStaticDoubles) return GM_ESCRATCH;
     double *scratch = nullptr;
     int rc = scratch_on_current_device(&scratch);
@@ -71,11 +85,17 @@ extern "C" int gm_solve_static(gm_handle *h, const double *g, double *dudn, int 
     const double *dg = g;
     double *dv = dudn;
     if (!gd) {
-        dg = scratch;
-        if (cudaMemcpyAsync(scratch, g, elems * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) return GM_ECUDA;
+        dg = scratch + g_at;
+        if (cudaMemcpyAsync(scratch + g_at, g, elems * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) return GM_ECUDA;
     }
-    if (!vd) dv = scratch + (gd ? 0 : elems);
-    if (gm::launch_apply(T, dg, dv, (int)N, batch, s) != cudaSuccess) return GM_ECUDA;
+    if (!vd) dv = scratch + v_at;
+    cudaError_t e;
+    if (mixed)
+        e = gm::mx_apply((const __nv_bfloat16 *)tdig, tex, dg, (__nv_bfloat16 *)(scratch + dig_at),
+                         (int *)(scratch + ex_at), dv, (int)N, batch, split, s);
+    else
+        e = gm::launch_apply(T, dg, dv, (int)N, batch, s);
+    if (e != cudaSuccess) return GM_ECUDA;
     if (!vd) {
         if (cudaMemcpyAsync(dudn, dv, elems * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return GM_ECUDA;
         if (cudaStreamSynchronize(s) != cudaSuccess) return GM_ECUDA;
