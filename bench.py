@@ -49,15 +49,50 @@ def bf16_peak_tflops():
         return 1900.0, "fallback"
 
 
+_LIVE_PEAKS = {}
+
+
+def live_peaks():
+    """FP64 and FP32 (no TF32) dense GEMM rates of this GPU, measured now with cuBLAS
+    through torch.matmul (4096^3, best of 5, CUDA events): the denominators of the FP64 /
+    FP32 families' roofline fractions ("measured"), beside the unit-count peaks."""
+    if _LIVE_PEAKS:
+        return _LIVE_PEAKS
+    import torch
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    for name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        n = 4096
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        b = torch.randn(n, n, dtype=dt, device="cuda")
+        best = float("inf")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(6):
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out[name] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    _LIVE_PEAKS.update(out)
+    return out
+
+
 def family_roofline(precision, fam):
     """(bound, peak TFLOP/s, source) of a kernel family of the timed operator build."""
     if precision == "fp64":
-        return "alu", FP64_PEAK_TFLOPS, "FP64 pipe from unit counts: 152 SMs x 4 flop/clk x 2070 MHz"
+        pk = live_peaks()["fp64"]
+        return "alu", pk, (f"FP64 DGEMM measured in this run (cuBLAS, 4096^3): {pk:.3f} TFLOP/s; unit-count "
+                           f"peak {FP64_PEAK_TFLOPS:.3f} (152 SMs x 4 flop/clk x 2070 MHz)")
     if fam == "leaf":  # double-float arithmetic: 18 FP32 operations per multiply-add
-        return "alu", FP32_PEAK_TFLOPS / DF32_OPS, (f"FP32 pipe from unit counts / {DF32_OPS} FP32 operations per "
-                                                   "double-float multiply-add (product 7, sum 11)")
+        pk = live_peaks()["fp32"]
+        return "alu", pk / DF32_OPS, (f"FP32 SGEMM measured in this run ({pk:.1f} TFLOP/s, no TF32) / {DF32_OPS} FP32 "
+                                      "operations per double-float multiply-add (product 7, sum 11)")
     if fam == "panel":
-        return "alu", FP32_PEAK_TFLOPS, "FP32 pipe from unit counts: 152 SMs x 256 flop/clk x 2070 MHz"
+        pk = live_peaks()["fp32"]
+        return "alu", pk, f"FP32 SGEMM measured in this run ({pk:.1f} TFLOP/s, no TF32)"
     bf, src = bf16_peak_tflops()
     pairs = SPLIT_DIGITS * (SPLIT_DIGITS + 1) // 2
     return "tensor", bf / pairs, (f"bf16 dense peak ({src} {bf:.1f} TFLOP/s) / {pairs} digit-pair products "
@@ -221,8 +256,16 @@ def run_gm(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
+    if args.graph:
+        extra["graph"] = True
+    if args.autotune:
+        extra["autotune"] = True
+
     def step(timing):
-        op = gm.build(b, c, d, n, LEAF, precision=prec, stream=stream, timing=timing, **extra)
+        kw = dict(extra)
+        if timing:  # an instrumented build is neither recorded nor replayed
+            kw.pop("graph", None)
+        op = gm.build(b, c, d, n, LEAF, precision=prec, stream=stream, timing=timing, **kw)
         op.solve(G, out=V, stream=stream)
         return op
 
@@ -258,7 +301,8 @@ def run_gm(args):
         flush.fill_(1.0)
         barrier()
         ev[0].record(stream)
-        op = gm.build(b, c, d, n, LEAF, precision=prec, stream=stream, timing=[dom], **extra)
+        op = gm.build(b, c, d, n, LEAF, precision=prec, stream=stream, timing=False if args.graph else [dom],
+                      **extra)
         ev[1].record(stream)
         op.solve(G, out=V, stream=stream)
         ev[2].record(stream)
@@ -268,10 +312,13 @@ def run_gm(args):
         solve_ms.append(ev[1].elapsed_time(ev[2]))
         inf = op.info()
         launches += inf["launches"] + 1
-        dom_ms += inf["kernel_ms"][dom]
-        dom_fl += inf["kernel_flops"][dom]
-        dom_n += inf["kernel_launches"][dom]
+        if not args.graph:
+            dom_ms += inf["kernel_ms"][dom]
+            dom_fl += inf["kernel_flops"][dom]
+            dom_n += inf["kernel_launches"][dom]
         op.free()
+    if args.graph:  # a replayed build has no per-family events: the instrumented step's figures
+        dom_ms, dom_fl, dom_n = brk_ms[dom] * args.steps, brk_fl[dom] * args.steps, inf["kernel_launches"][dom] * args.steps
     barrier()
     clk = clocks.stop()
     t_step = max_over_ranks(statistics.mean(step_ms), world, dev)
@@ -341,6 +388,7 @@ def run_gm(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "leaf": LEAF, "nvec": NVEC, "precision": args.precision,
                    "l2": "flushed before every timed step (256 MiB write)",
+                   "graph": bool(args.graph), "autotune": bool(args.autotune),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "build_ms": statistics.mean(build_ms), "solve_ms": statistics.mean(solve_ms),
         "build_gridpoints_per_s": n * n / (statistics.mean(build_ms) * 1e-3) * world,
@@ -374,12 +422,16 @@ def run_gm(args):
 
 
 def run_serving(args):
-    """Serving workload (solve stage under load): resident operators of mixed sizes and
-    fields, Poisson arrivals of requests with B ~ U{1..64} Gaussian vectors for a uniformly
-    chosen operator, at 0.25x, 0.5x and 0.9x the saturated batched rate; one new operator
-    built and added (evicting the least recently used) every `quota` submitted requests.
-    The same arrivals against the unbatched server (one solve per request) give the
-    baseline.  Prints one JSON line (not the headline metric)."""
+    """Serving workload (the solve stage under load): 32 resident operators, n uniform on
+    {256, 384, 512, 768, 1024, 1536} (seed 7) plus one at n = 2048 (an 8192 x 8192 T),
+    convection and variable-wavespeed Helmholtz fields alternating, mixed precision with
+    the automatic FP64 fallback.  Solve requests arrive as a Poisson process with B ~
+    U{1..64} Gaussian vectors for a uniformly chosen operator, at 0.25x, 0.5x and 0.9x the
+    saturated batched rate; every `quota` requests a new operator is submitted to the
+    server's build worker (it overlaps the solves and evicts the least recently used
+    operator when admitted).  Baseline: the unbatched FP64 apply -- a server with one
+    solve per request over FP64 builds of the same operators.  One JSON line (not the
+    headline)."""
     import numpy as np
     import torch
     from paper_1302_5995_gb300 import build_ext, inputs
@@ -387,7 +439,8 @@ def run_serving(args):
     import paper_1302_5995_gb300 as gm
 
     rng = np.random.default_rng(7)
-    sizes = [256, 384, 512, 768]
+    sizes = [256, 384, 512, 768, 1024, 1536]
+    ns = [int(x) for x in rng.choice(sizes, 31)] + [2048]
     ks = {}
 
     def fields(n, j):
@@ -397,24 +450,34 @@ def run_serving(args):
             ks[n] = inputs.nudged_wavenumber(n, 16)
         return inputs.helmholtz_fields(n, ks[n])
 
-    def make_op(j):
-        n = sizes[j % len(sizes)] if j < 8 else int(rng.choice(sizes))
-        b, c, d = (torch.from_numpy(x).cuda() for x in fields(n, j))
-        return gm.build(b, c, d, n, 16, precision=gm.PREC_MIXED), n
+    dev_fields = {}
 
-    n_ops, quota, per_rate = 8, 150, args.serve_requests
-    vec_pool = {n: torch.from_numpy(inputs.gaussian_vectors(n, 64, 9 + n).T.copy()).pin_memory() for n in sizes}
+    def get_fields(j, n):
+        if (j, n) not in dev_fields:
+            dev_fields[(j, n)] = [torch.from_numpy(x).cuda() for x in fields(n, j)]
+        return dev_fields[(j, n)]
 
-    def run(batching, rate_req_s):
-        built = [make_op(j) for j in range(n_ops)]
-        budget = sum(op.info()["resident_bytes"] for op, _ in built) + 1
+    quota, per_rate = 200, args.serve_requests
+    vec_pool = {n: torch.from_numpy(inputs.gaussian_vectors(n, 64, 9 + n).T.copy()).pin_memory()
+                for n in sizes + [2048]}
+    outs = {n: torch.empty((64, 4 * n), dtype=torch.float64).pin_memory() for n in sizes + [2048]}
+
+    def make_server(batching, precision):
+        t0 = time.perf_counter()
+        ops = [gm.build(*get_fields(j, n), n, 16, precision=precision) for j, n in enumerate(ns)]
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
+        budget = sum(op.info()["resident_bytes"] for op in ops) + 1
         srv = gm.Server(budget, batching=batching)
-        live = [(srv.add(op), n) for op, n in built]
-        outs = {n: torch.empty((64, 4 * n), dtype=torch.float64).pin_memory() for n in sizes}
-        ids = []
+        live = [(srv.add(op), n) for op, n in zip(ops, ns)]
+        return srv, live, t_build
+
+    def run(srv, live, rate_req_s, precision, j0):
+        srv.reset_stats()
+        ids, builds = [], []
         t0 = time.perf_counter()
         t_next = 0.0
-        extra = n_ops
+        j = j0
         for q in range(per_rate):
             if rate_req_s:
                 t_next += rng.exponential(1.0 / rate_req_s)
@@ -427,36 +490,42 @@ def run_serving(args):
                 ids.append(srv.submit(oid, vec_pool[n], outs[n], B))
             except gm.GmError:  # evicted meanwhile
                 pass
-            if (q + 1) % quota == 0:  # a new operator arrives; the LRU one is evicted
-                op, n2 = make_op(extra)
-                extra += 1
-                live.append((srv.add(op), n2))
-                st = srv.stats()
-                if st["evictions"]:
-                    live = live[-st["resident_ops"]:]
-        for rid in ids:
+            if (q + 1) % quota == 0:  # a new operator, built on the server's build worker
+                n2 = int(rng.choice(sizes))
+                oid2, rid = srv.submit_build(*get_fields(j, n2), n2, 16, precision=precision)
+                builds.append(rid)
+                live.append((oid2, n2))
+                j += 1
+        for rid in ids + builds:
             srv.wait(rid)
+        srv.sync()
         st = srv.stats()
-        srv.close()
-        return st
+        # the operators still resident (the evicted ones are gone from the server)
+        live[:] = live[-st["resident_ops"]:] if st["resident_ops"] else live
+        return st, j
 
-    sat = run(True, 0.0)  # everything at once: the saturated batched throughput
-    mean_b = 32.5
-    sat_req = sat["vectors_per_s"] / mean_b
-    res = {"saturated": {"vectors_per_s": sat["vectors_per_s"], "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"]}}
-    for frac in (0.25, 0.5, 0.9):
-        rate = frac * sat_req
-        bt = run(True, rate)
-        ub = run(False, rate)
-        res[f"{frac}x"] = {"offered_req_s": rate,
-                           "batched": {k: bt[k] for k in ("p50_ms", "p99_ms", "vectors_per_s", "solves", "requests",
-                                                          "evictions")},
-                           "unbatched": {k: ub[k] for k in ("p50_ms", "p99_ms", "vectors_per_s", "solves", "requests",
-                                                            "evictions")}}
-    print(json.dumps({"workload": "serving", "operators": f"{n_ops} resident, n in {sizes}, convection / Helmholtz "
-                      "alternating, mixed precision (automatic FP64 fallback)",
+    keys = ("p50_ms", "p99_ms", "vectors_per_s", "solves", "requests", "evictions")
+    res = {}
+    srv_b, live_b, tb_b = make_server(True, gm.PREC_MIXED)
+    sat, j = run(srv_b, live_b, 0.0, gm.PREC_MIXED, 100)
+    res["saturated"] = {k: sat[k] for k in keys}
+    sat_req = sat["vectors_per_s"] / 32.5
+    rates = {f: f * sat_req for f in (0.25, 0.5, 0.9)}
+    for f, r in rates.items():
+        st, j = run(srv_b, live_b, r, gm.PREC_MIXED, j)
+        res[f"{f}x"] = {"offered_req_s": r, "batched": {k: st[k] for k in keys}}
+    srv_b.close()
+    srv_u, live_u, tb_u = make_server(False, gm.PREC_FP64)
+    for f, r in rates.items():
+        st, j = run(srv_u, live_u, r, gm.PREC_FP64, j)
+        res[f"{f}x"]["unbatched_fp64"] = {k: st[k] for k in keys}
+    srv_u.close()
+    print(json.dumps({"workload": "serving", "operators": f"32 resident: n = {ns}, convection / Helmholtz "
+                      "alternating; batched: mixed precision (automatic FP64 fallback), one grouped apply per "
+                      "batch; baseline: FP64 operators, one apply per request",
                       "requests_per_rate": per_rate, "vectors_per_request": "U{1..64}", "arrivals": "Poisson",
-                      "build_every": quota, "results": res}), flush=True)
+                      "build_every": quota, "initial_build_s": {"batched_set": tb_b, "fp64_set": tb_u},
+                      "results": res}), flush=True)
 
 
 def _timed(fn, reps):
@@ -555,6 +624,216 @@ def run_bodyloads(args):
                       "results": res}), flush=True)
 
 
+def _fields_dev(cfg, dev=None):
+    import torch
+    return [torch.from_numpy(cfg[k]).to(dev or "cuda") for k in ("b", "c", "d")]
+
+
+def run_cfg3(args):
+    """Variable-wavespeed Helmholtz at 10 points per wavelength, 1024 x 1024 unknowns,
+    leaf 16, plane-wave data (64 vectors): the HBS build (accelerated merges for shared
+    edges >= 128, HBS root, tol 1e-9, FP64) and its solve.  Value: build gridpoints/s of
+    the HBS build; the dense FP64 build alongside; error against O2 on 8 of the vectors.
+    One JSON line with roofline, cpu_baseline and e2e (not the headline)."""
+    import numpy as np
+    import torch
+    from paper_1302_5995_gb300 import build_ext, inputs
+    build_ext.build()
+    import paper_1302_5995_gb300 as gm
+    from oracle import nd_dense
+
+    n, leaf, tol, m = 1024, 16, 1e-9, 64
+    cfg = inputs.config3(n, leaf)
+    b, c, d = _fields_dev(cfg)
+    Gv = np.ascontiguousarray(cfg["G"].T)
+    G = torch.from_numpy(Gv).cuda()
+    V = torch.empty_like(G)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    kw = dict(tol=tol, hbs_leaf=m, hbs_min_edge=128, stream=stream)
+    for _ in range(args.warmup):
+        gm.build(b, c, d, n, leaf, **kw).free()
+    torch.cuda.synchronize()
+    op = gm.build(b, c, d, n, leaf, timing=True, **kw)
+    inf = op.info()
+    brk_ms, brk_fl = dict(inf["kernel_ms"]), dict(inf["kernel_flops"])
+    op.free()
+    dom = max(brk_ms, key=lambda f: brk_ms[f])
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    bms, sms, launches = [], [], 0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        op = gm.build(b, c, d, n, leaf, **kw)
+        ev[1].record(stream)
+        op.solve(G, out=V, stream=stream)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        bms.append(ev[0].elapsed_time(ev[1]))
+        sms.append(ev[1].elapsed_time(ev[2]))
+        info = op.info()
+        launches += info["launches"]
+        op.free()
+    clk = clocks.stop()
+    # e2e: host (pinned) fields and vectors, copies inside the timing
+    hb = [torch.from_numpy(cfg[k]).pin_memory() for k in ("b", "c", "d")]
+    hG = torch.from_numpy(Gv).pin_memory()
+    hV = torch.empty_like(hG).pin_memory()
+    e2e = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        op = gm.build(hb[0].numpy(), hb[1].numpy(), hb[2].numpy(), n, leaf, **kw)
+        op.solve(hG.numpy(), out=hV.numpy(), stream=stream)
+        e2e.append(time.perf_counter() - t0)
+        op.free()
+    # the dense FP64 build of the same problem
+    dn = []
+    for it in range(3):
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        op = gm.build(b, c, d, n, leaf, stream=stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        if it:
+            dn.append(ev[0].elapsed_time(ev[1]))
+        Vd = op.solve(G[:8].contiguous()).cpu().numpy()
+        op.free()
+    # the oracle (O2, FP64 dense nested dissection), timed: the CPU baseline
+    t0 = time.perf_counter()
+    res = nd_dense.build(cfg["b"], cfg["c"], cfg["d"], n, leaf)
+    t_cpu = time.perf_counter() - t0
+    Vo = res.T @ cfg["G"][:, :8]
+    rel = lambda A: float((np.linalg.norm(A - Vo, axis=0) / np.linalg.norm(Vo, axis=0)).max())
+    bound = max(1e-10, np.finfo(float).eps * np.linalg.cond(res.S_root, 1))
+    t_b, t_s = statistics.mean(bms), statistics.mean(sms)
+    bound_kind, peak, src = family_roofline("fp64", dom)
+    line = {
+        "workload": "cfg3", "metric": METRIC, "value": n * n / (t_b * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_b + t_s, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "variable-wavespeed Helmholtz, 10 points per wavelength, 1024x1024, leaf 16, "
+                               "HBS (tol 1e-9, node size 64) for merges with shared edge >= 128 and the root; "
+                               "64 plane-wave vectors (32 angles, seed 5)",
+                   "n": n, "leaf": leaf, "tol": tol, "k": cfg["k"],
+                   "l2": "flushed before every timed step (256 MiB write)"},
+        "build_ms": t_b, "solve_ms": t_s, "solve_vectors_per_s": 64 / (t_s * 1e-3),
+        "hbs": {k: info[k] for k in ("hbs_levels", "hbs_max_rank", "hbs_merges", "hbs_update_rank",
+                                      "hbs_operator_bytes", "resident_bytes")},
+        "rel_err_vs_fp64_oracle": rel(V[:8].cpu().numpy().T), "rel_err_bound": 1e-4,
+        "dense_fp64": {"build_ms": statistics.mean(dn), "rel_err_vs_fp64_oracle": rel(Vd.T),
+                       "rel_err_bound": bound},
+        "roofline": {"kernel": dom, "bound": bound_kind, "achieved": brk_fl[dom] / brk_ms[dom] / 1e9,
+                     "peak": peak, "unit": "TFLOP/s", "frac": brk_fl[dom] / brk_ms[dom] / 1e9 / peak,
+                     "traffic": None, "peak_source": src},
+        "kernel_ms_per_step": brk_ms, "kernel_flops_per_step": brk_fl,
+        "cpu_baseline": {"value": n * n / t_cpu, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "one dense FP64 build of the same problem by the oracle O2 (numpy/LAPACK)"},
+        "e2e": {"value": n * n / statistics.mean(e2e), "unit": UNIT, "h2d_bytes_per_step": 3 * n * n * 8 + Gv.size * 8,
+                "d2h_bytes_per_step": Gv.size * 8, "ms_per_step": statistics.mean(e2e) * 1e3},
+        "clocks": clk, "gpu_launches": launches // max(args.steps, 1),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    """The batched build: 64 independent problems, n uniform on {128, 192, 256, 384, 512}
+    (seed 6), convection and variable-wavespeed Helmholtz alternating, leaf 16, mixed
+    precision with the automatic FP64 fallback, in one gm_build_batch call.  Value: total
+    gridpoints / batch build time (device, CUDA events); the same problems built one by
+    one alongside; error of one problem per size against O2.  One JSON line (not the
+    headline)."""
+    import numpy as np
+    import torch
+    from paper_1302_5995_gb300 import build_ext, inputs
+    build_ext.build()
+    import paper_1302_5995_gb300 as gm
+    from oracle import nd_dense
+
+    probs = inputs.config4()
+    dev = [tuple(torch.from_numpy(p[k]).cuda() for k in ("b", "c", "d")) + (p["n"], p["leaf"]) for p in probs]
+    total = sum(p["n"] ** 2 for p in probs)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        out = fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]), out
+
+    batch = lambda: gm.build_batch(dev, precision=gm.PREC_MIXED, stream=stream, graph=args.graph,
+                                   autotune=args.autotune)
+    for _ in range(args.warmup):
+        for op in batch():
+            op.free()
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    clocks.start()
+    tb = []
+    for _ in range(args.steps):
+        t, ops = timed(batch)
+        tb.append(t)
+        last = ops
+    clk = clocks.stop()
+    fell = sum(op.info()["pivot_fallback"] for op in last)
+    ts = []
+    for _ in range(2):
+        t, ops = timed(lambda: [gm.build(*p, precision=gm.PREC_MIXED, stream=stream) for p in dev])
+        ts.append(t)
+        for op in ops:
+            op.free()
+    # one problem per size against O2
+    errs = {}
+    t_cpu, pts = 0.0, 0
+    for i, p in enumerate(probs):
+        if p["n"] in errs:
+            continue
+        G = inputs.gaussian_vectors(p["n"], 8, 70 + i)
+        t0 = time.perf_counter()
+        To = nd_dense.build(p["b"], p["c"], p["d"], p["n"], p["leaf"]).T
+        if p["n"] <= 256:
+            t_cpu += time.perf_counter() - t0
+            pts += p["n"] ** 2
+        V = last[i].solve(np.ascontiguousarray(G.T)).reshape(8, 4 * p["n"]).T
+        errs[p["n"]] = float((np.linalg.norm(V - To @ G, axis=0) / np.linalg.norm(To @ G, axis=0)).max())
+    # e2e: host coefficient arrays
+    hp = [(p["b"], p["c"], p["d"], p["n"], p["leaf"]) for p in probs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ops = gm.build_batch(hp, precision=gm.PREC_MIXED, stream=stream)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    for op in ops:
+        op.free()
+    t = statistics.mean(tb)
+    line = {
+        "workload": "batch", "metric": METRIC, "value": total / (t * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "split-f64 (6 bf16 digits, df32 storage); FP64 for the fallback problems",
+        "data": "synthetic",
+        "config": {"workload": "64 problems, n uniform on {128,192,256,384,512} (seed 6), convection / Helmholtz "
+                               "(10 ppw) alternating, leaf 16, one gm_build_batch", "gridpoints": total,
+                   "graph": bool(args.graph), "autotune": bool(args.autotune),
+                   "l2": "flushed before every timed step (256 MiB write)"},
+        "single_builds_ms": statistics.mean(ts), "speedup_vs_single_builds": statistics.mean(ts) / t,
+        "problems_in_fp64_fallback": fell,
+        "rel_err_vs_fp64_oracle_by_n": errs, "rel_err_bound": 1e-8,
+        "cpu_baseline": {"value": pts / t_cpu, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "oracle O2 builds of the batch's first problem of each size <= 256"},
+        "e2e": {"value": total / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 3 * 8 * total, "d2h_bytes_per_step": 0,
+                "ms_per_step": t_e2e * 1e3},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -562,13 +841,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gm", "reference"], default="gm")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
-    ap.add_argument("--workload", choices=["build", "serving", "problemset", "bodyloads"], default="build",
-                    help="build: the headline build+solve step; serving, problemset, bodyloads: other "
-                         "workloads (not the headline)")
+    ap.add_argument("--workload", choices=["build", "cfg3", "batch", "serving", "problemset", "bodyloads"],
+                    default="build",
+                    help="build: the headline build+solve step; cfg3, batch, serving, problemset, bodyloads: "
+                         "other workloads (not the headline)")
     ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--graph", type=int, default=0, help="record each plan's build into a CUDA graph and replay it")
+    ap.add_argument("--autotune", type=int, default=0, help="time a few launch shapes on the first build of a plan")
     args = ap.parse_args()
     if args.workload == "serving":
         run_serving(args)
+        return
+    if args.workload == "cfg3":
+        run_cfg3(args)
+        return
+    if args.workload == "batch":
+        run_batch(args)
         return
     if args.workload == "problemset":
         run_problemset(args)

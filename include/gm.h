@@ -41,7 +41,7 @@ extern "C" {
 #endif
 
 #define GM_OK 0
-#define GM_EINVAL (-1)       /* bad argument: sizes, NULL pointers, leaf < 4, ...      */
+#define GM_EINVAL (-1)       /* bad argument: sizes, NULL pointers, leaf < 3, ...      */
 #define GM_ENOMEM (-2)       /* a device or pinned-host allocation failed               */
 #define GM_ESINGULAR (-3)    /* an exactly zero / non-finite pivot: the Dirichlet
                                 problem of some box (or of the whole grid) is singular;
@@ -89,6 +89,16 @@ typedef struct gm_opts {
                          path); a kernel that gives up still waits, for a fixed bound,
                          for its own copies and products in flight before it releases
                          its tensor memory and returns                                   */
+    int graph;        /* nonzero (tol = 0, no keep_levels, no timing): the first build of
+                         a plan runs as usual and records every launch of its build into a
+                         CUDA graph, kept with its own buffers (coefficients, Schur
+                         complements, workspaces, outputs) per plan and options; later
+                         builds of the plan copy their coefficients in, replay the graph
+                         and copy the operator out (at most 8 graphs are kept, least
+                         recently used dropped)                                         */
+    int autotune;     /* nonzero: the first build of a plan times a few launch shapes (the
+                         R kernel's tile width, the tcgen05 merge-update bound) and keeps
+                         the fastest for every later build of that plan and options     */
 } gm_opts;
 
 /* Pivoting of the mixed-precision dense eliminations.
@@ -146,6 +156,9 @@ typedef struct gm_info_t {
     int hbs_update_rank;              /* tol > 0: largest rank of their S13 / S24 blocks   */
     long long hbs_operator_bytes;     /* tol > 0: bytes of the root operator in HBS form
                                          (D, U, V, B at the node ranks; the paper's M(n)) */
+    int load_rank;                    /* body loads: rank of F after
+                                         gm_compress_load_operator (-1: F dense)         */
+    int pad3;
 } gm_info_t;
 
 /* Fill *opts with defaults (FP64, no kept levels, default stream). */
@@ -156,8 +169,14 @@ void gm_opts_default(gm_opts *opts);
  *   b, c, d : n*n coefficient values at the unknown nodes, flat index i + n*j.
  *   n       : grid of unknowns, n >= 2.
  *   leaf    : largest leaf-box edge (Section 2's N_leaf, as an edge): the tree has the
- *             smallest L with ceil(n / 2^L) <= leaf.  4 <= leaf <= 17 (the leaf kernel
- *             keeps a leaf's band and inner-ring solves in shared memory).
+ *             smallest L with ceil(n / 2^L) <= leaf, 3 <= leaf (leaf >= n: one leaf).
+ *             GM_EINVAL if the tree would hold a box narrower than 2 nodes (only
+ *             possible for leaf = 3, when 1.5 < n / 2^L < 2): such a box has no ring.
+ *             The leaf kernels keep a leaf's band in shared memory up to edge 17; a
+ *             wider leaf's Schur complement is formed by eliminating its interior in
+ *             nested-dissection order (the tree continues below the requested level
+ *             with boxes of edge <= 16, whose splits are those of every level), the same
+ *             S up to rounding.  gm_info().levels is the requested tree's L.
  *   tol     : 0 selects the all-dense build.  tol > 0 compresses the root Schur
  *             complement to HBS form at local relative tolerance tol (Section 4; node
  *             size gm_opts.hbs_leaf) and inverts it by Algorithm 1 (Section 5); the
@@ -276,6 +295,16 @@ int gm_build_loads(const gm_opts *opts, const double *b, const double *c, const 
                    const int *body, int nbody, gm_handle **out);
 int gm_solve_loads(gm_handle *h, const double *g, const double *f, double *dudn, int batch, void *stream);
 int gm_get_load_operator(gm_handle *h, double *F_out);
+/*
+ * The low-rank form of the load operator (Section 6.3: F, built uncompressed, is then
+ * replaced by a low-rank approximation): F ~ L R with L (4n x k) an orthonormal basis of
+ * the range of a Gaussian sample of F, truncated at the first |R_jj| <= tol |R_11| of its
+ * pivoted QR, and R = L^T F (k x nbody).  The dense F is released; gm_solve_loads then
+ * applies L (R f), gm_get_load_operator returns L R, gm_info reports k as load_rank and
+ * resident_bytes the smaller footprint.  GM_EINVAL for tol <= 0; GM_EUNSUPPORTED for a
+ * handle without loads or one already compressed.  Blocks until done.
+ */
+int gm_compress_load_operator(gm_handle *h, double tol);
 
 /*
  * Conductance networks (Section 6.1, Random Laplacian I and II): the square grid whose

@@ -34,7 +34,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("keep_levels", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("panel_width", ctypes.c_int), ("timing", ctypes.c_int), ("split_digits", ctypes.c_int),
                 ("pivoting", ctypes.c_int), ("hbs_leaf", ctypes.c_int), ("hbs_min_edge", ctypes.c_int),
-                ("timing_mask", ctypes.c_int), ("background", ctypes.c_int), ("wait_limit", ctypes.c_int)]
+                ("timing_mask", ctypes.c_int), ("background", ctypes.c_int), ("wait_limit", ctypes.c_int),
+                ("graph", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 K_FAMILIES = ["leaf", "assemble", "panel", "pivrows", "gj_update", "merge_update", "root"]
 
@@ -48,7 +49,8 @@ class Info(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int * 7), ("pivoting", ctypes.c_int),
                 ("pivot_fallback", ctypes.c_int), ("refine_ratio", ctypes.c_double), ("hbs_levels", ctypes.c_int),
                 ("hbs_max_rank", ctypes.c_int), ("hbs_bytes", ctypes.c_longlong), ("resident_bytes", ctypes.c_longlong),
-                ("hbs_merges", ctypes.c_int), ("hbs_update_rank", ctypes.c_int), ("hbs_operator_bytes", ctypes.c_longlong)]
+                ("hbs_merges", ctypes.c_int), ("hbs_update_rank", ctypes.c_int), ("hbs_operator_bytes", ctypes.c_longlong),
+                ("load_rank", ctypes.c_int), ("pad3", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -83,6 +85,7 @@ SIGNATURES = {
                        + [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "gm_solve_loads": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int, ctypes.c_void_p]),
     "gm_get_load_operator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gm_compress_load_operator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "gm_build_net": (ctypes.c_int, [ctypes.POINTER(Opts)] + [ctypes.c_void_p] * 2
                      + [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int,
                         ctypes.POINTER(ctypes.c_void_p)]),
@@ -271,6 +274,14 @@ class DtN:
             raise GmError(rc, "gm_solve_loads")
         return out
 
+    def compress_loads(self, tol):
+        """Replace the load operator F by its low-rank form L R at relative tolerance tol
+        (Section 6.3); returns the rank."""
+        rc = load_library().gm_compress_load_operator(self._h, float(tol))
+        if rc:
+            raise GmError(rc, "gm_compress_load_operator")
+        return self.info()["load_rank"]
+
     def load_operator(self):
         """The 4n x nbody load operator F of a build_loads handle (column c: body[c])."""
         import numpy as np
@@ -315,7 +326,7 @@ def solve_many(ops, gs, outs, stream=None):
 
 
 def _opts(precision, keep_levels, stream, panel_width, timing, split_digits, pivoting, hbs_leaf=0, hbs_min_edge=0,
-          wait_limit=0):
+          wait_limit=0, graph=False, autotune=False):
     """timing: False, True (every family) or a list of family names to time."""
     lib = load_library()
     o = Opts()
@@ -332,11 +343,13 @@ def _opts(precision, keep_levels, stream, panel_width, timing, split_digits, piv
     o.hbs_leaf = hbs_leaf
     o.hbs_min_edge = hbs_min_edge
     o.wait_limit = wait_limit
+    o.graph = 1 if graph else 0
+    o.autotune = 1 if autotune else 0
     return o
 
 
 def build_batch(problems, tol=0.0, precision=PREC_FP64, stream=None, panel_width=0, timing=False, split_digits=0,
-                pivoting=PIVOT_AUTO):
+                pivoting=PIVOT_AUTO, graph=False, autotune=False):
     """Build several operators in one level-by-level sweep.
 
     problems: list of (b, c, d, n, leaf).  Returns a list of DtN handles."""
@@ -347,7 +360,7 @@ def build_batch(problems, tol=0.0, precision=PREC_FP64, stream=None, panel_width
         b, c, d = (_check_f64(x, "coefficients", n * n) for x in (b, c, d))
         keep += [b, c, d]
         arr[i] = Problem(_ptr(b).value, _ptr(c).value, _ptr(d).value, n, leaf)
-    o = _opts(precision, False, stream, panel_width, timing, split_digits, pivoting)
+    o = _opts(precision, False, stream, panel_width, timing, split_digits, pivoting, graph=graph, autotune=autotune)
     outs = (ctypes.c_void_p * len(problems))()
     rc = lib.gm_build_batch(len(problems), arr, ctypes.byref(o), float(tol), outs)
     if rc:
@@ -356,7 +369,8 @@ def build_batch(problems, tol=0.0, precision=PREC_FP64, stream=None, panel_width
 
 
 def build(b, c, d, n, leaf, tol=0.0, precision=PREC_FP64, keep_levels=False, stream=None, panel_width=0,
-          timing=False, split_digits=0, pivoting=PIVOT_AUTO, hbs_leaf=0, hbs_min_edge=0, wait_limit=0):
+          timing=False, split_digits=0, pivoting=PIVOT_AUTO, hbs_leaf=0, hbs_min_edge=0, wait_limit=0, graph=False,
+          autotune=False):
     """Build the DtN operator for coefficient fields b, c, d (n*n each, index i + n*j).
 
     tol > 0 compresses the root Schur complement to HBS form (node size hbs_leaf) and
@@ -366,7 +380,7 @@ def build(b, c, d, n, leaf, tol=0.0, precision=PREC_FP64, keep_levels=False, str
     c = _check_f64(c, "c", n * n)
     d = _check_f64(d, "d", n * n)
     o = _opts(precision, keep_levels, stream, panel_width, timing, split_digits, pivoting, hbs_leaf, hbs_min_edge,
-              wait_limit)
+              wait_limit, graph, autotune)
     h = ctypes.c_void_p()
     rc = lib.gm_build_ex(ctypes.byref(o), _ptr(b), _ptr(c), _ptr(d), n, leaf, float(tol), ctypes.byref(h))
     if rc:

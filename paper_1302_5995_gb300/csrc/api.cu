@@ -81,12 +81,40 @@ bool injected_failure() {
     return false;
 }
 
+// Allocation context of a build that is recorded into a CUDA graph: while `measure` is
+// set, allocations are made as usual and their (aligned) sizes summed; while `base` is set,
+// they are carved in order from one buffer that the graph keeps (frees do nothing), so a
+// replay finds every buffer where the recording put it.
+struct BumpCtx {
+    char *base = nullptr;
+    size_t cap = 0, used = 0;
+    bool measure = false;
+    size_t total = 0;
+    static size_t align(size_t b) { return (b + 255) / 256 * 256; }
+    bool bumping() const { return base != nullptr; }
+    void *take(size_t bytes) {
+        const size_t a = align(bytes);
+        if (used + a > cap) return nullptr;
+        void *p = base + used;
+        used += a;
+        return p;
+    }
+};
+thread_local BumpCtx *tl_bump = nullptr;
+// the status array of the build being recorded (its replays report through it)
+thread_local gm::Status *tl_recorded_status = nullptr;
+
 // cudaMalloc with the injection point (the handle's long-lived buffers).
 cudaError_t lib_malloc(void **p, size_t bytes) {
     if (injected_failure()) {
         *p = nullptr;
         return cudaErrorMemoryAllocation;
     }
+    if (tl_bump && tl_bump->bumping()) {
+        *p = tl_bump->take(bytes);
+        return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
+    if (tl_bump && tl_bump->measure) tl_bump->total += BumpCtx::align(bytes);
     return cudaMalloc(p, bytes);
 }
 
@@ -113,23 +141,32 @@ cudaMemPool_t lib_pool() {
     return pool;
 }
 
-// Device buffer released on scope exit through the stream-ordered allocator.
+// Device buffer released on scope exit through the stream-ordered allocator (or carved
+// from a graph's buffer while a build is being recorded: see BumpCtx).
 struct DBuf {
     void *p = nullptr;
     cudaStream_t s = nullptr;
+    bool bumped = false;
     DBuf() = default;
     DBuf(const DBuf &) = delete;
     DBuf &operator=(const DBuf &) = delete;
     ~DBuf() { release(); }
     void release() {
-        if (p) cudaFreeAsync(p, s);
+        if (p && !bumped) cudaFreeAsync(p, s);
         p = nullptr;
+        bumped = false;
     }
     int alloc(size_t bytes, cudaStream_t st) {
         release();
         s = st;
         if (bytes == 0) bytes = 16;
         if (injected_failure()) return GM_ENOMEM;
+        if (tl_bump && tl_bump->bumping()) {
+            p = tl_bump->take(bytes);
+            bumped = p != nullptr;
+            return p ? GM_OK : GM_ENOMEM;
+        }
+        if (tl_bump && tl_bump->measure) tl_bump->total += BumpCtx::align(bytes);
         cudaMemPool_t pool = lib_pool();
         const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, st) : cudaMallocAsync(&p, bytes, st);
         if (e != cudaSuccess) {
@@ -339,6 +376,28 @@ int dev_alloc(void **p, size_t bytes, cudaStream_t s) {
 }
 }  // namespace gm
 
+namespace {
+// Status of every problem of a build reset on the device (a recorded build resets it
+// itself at every replay).
+__global__ void k_status_init(Status *st, int np) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < np) st[p] = Status{0, -1, 0x7ff0000000000000ull, 0, 0u};
+}
+
+// An open stream capture, ended (and its graph dropped) if the build returns early.
+struct CaptureGuard {
+    cudaStream_t s = nullptr;
+    bool active = false;
+    ~CaptureGuard() {
+        if (!active) return;
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(s, &g);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+    }
+};
+}  // namespace
+
 struct gm_handle {
     int n = 0, leaf = 0, L = 0, precision = 0;
     double *T = nullptr;            // 4n x 4n column-major
@@ -355,6 +414,8 @@ struct gm_handle {
     gm::HbsRoot *hbs = nullptr;     // tol > 0: the root's HBS inverse (no dense T)
     double *F = nullptr;            // body loads: the 4n x nbody load operator (Section 6.3)
     int nbody = 0;
+    double *FL = nullptr, *FR = nullptr;  // F ~ FL FR after gm_compress_load_operator
+    int frank = -1;                       // its rank (-1: F is dense)
     gm_info_t info{};
 };
 
@@ -385,7 +446,8 @@ constexpr float kMaxRefineRatio = 0x1p-13f;
 // handle of problem p (allocated by the caller).  Per problem, code[p] is 0 or
 // GM_ESINGULAR and growth[p] the block-pivoting growth flag of a mixed build.
 int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp, const double *db, const double *dc,
-              const double *dd, std::vector<gm_handle *> &H, std::vector<int> &code, std::vector<int> &growth) {
+              const double *dd, std::vector<gm_handle *> &H, std::vector<int> &code, std::vector<int> &growth,
+              const Tune &tu = Tune(), cudaGraph_t *record = nullptr) {
     const auto t_enter = std::chrono::steady_clock::now();
     std::vector<double> stamps;  // host time (ms) at the end of each phase, reported under GM_DEBUG
     auto stamp = [&] {
@@ -422,11 +484,26 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
     int rc;
     int hbs_merges = 0, hbs_rank = 0, hbs_lr_rank = 0;
     const size_t np = H.size();
+    // declared ahead of every buffer: the capture ends before the look-ahead streams go
+    LookAhead la;
+    CaptureGuard cg;
+    if (record) {  // record every launch of this build into a graph (nothing runs now)
+        if (tol > 0.0 || o.keep_levels || o.timing) return GM_EINVAL;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+        cg.s = s;
+        cg.active = true;
+    }
     DBuf stat;
     if ((rc = stat.alloc(np * sizeof(Status), s))) return rc;
     std::vector<Status> hst(np, Status{0, -1, 0x7ff0000000000000ull, 0, 0u});
-    CK(cudaMemcpyAsync(stat.p, hst.data(), np * sizeof(Status), cudaMemcpyHostToDevice, s));
+    if (record) {
+        k_status_init<<<(int)((np + 127) / 128), 128, 0, s>>>(stat.as<Status>(), (int)np);
+        CK(cudaGetLastError());
+    } else {
+        CK(cudaMemcpyAsync(stat.p, hst.data(), np * sizeof(Status), cudaMemcpyHostToDevice, s));
+    }
     Status *dst = stat.as<Status>();
+    if (record) tl_recorded_status = dst;
     KTimer kt;
     kt.on = o.timing != 0;
     if (o.timing_mask) kt.mask = (unsigned)o.timing_mask;
@@ -487,7 +564,17 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
     DBuf bxd, bad, bxe, bae, bpmag, bfdig, bfex, brdig, brex;  // mixed, block pivoting
     MxScratch scr;
     BlkScratch bscr;
-    LookAhead la;
+    // on every exit: nothing on the look-ahead streams may still read the scratch buffers
+    // above when they are released (early returns); a build being recorded ran nothing
+    struct StreamsIdle {
+        LookAhead &la;
+        const CaptureGuard &cg;
+        ~StreamsIdle() {
+            if (cg.active) return;
+            if (la.s1) cudaStreamSynchronize(la.s1);
+            if (la.s2) cudaStreamSynchronize(la.s2);
+        }
+    } idle{la, cg};
     if (!mixed) {
         if ((rc = piv.alloc((size_t)max_nm * piv_ld * sizeof(int), s))) return rc;
         if ((rc = u12.alloc((size_t)max_u12 * 8, s))) return rc;
@@ -518,6 +605,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             }
             if (!la.create(o.background != 0)) return GM_ECUDA;
             bscr.wait_limit = wait_limit;
+            bscr.rtile32_max = tu.rtile32_max;
             bscr.s1 = la.s1;
             bscr.s2 = la.s2;
             bscr.ev_r = la.a;
@@ -579,10 +667,12 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             for (int i = 0; i < ds.nm; ++i) {
                 const MergeDesc &md = hs.merges[i];
                 if (tol > 0.0 && md.sp + 2 >= o.hbs_min_edge && md.sp > o.hbs_leaf) {
+                    hbs_flops_take();
                     kt.begin(GM_K_PANEL, 0.0, s);
                     rc = hbs_block_solve(ws.as<double>() + ds.h_sys[i].off, md.sp, md.rp, o.hbs_leaf, tol, s,
                                          &hbs_rank);
                     kt.end(s);
+                    kt.flops[GM_K_PANEL] += hbs_flops_take();
                     if (rc == GM_OK) {
                         ++hbs_merges;
                         any_hbs = true;
@@ -634,10 +724,12 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
                                            dd, 0, s, kt));
                 }
                 for (int i : hbs_idx) {
+                    hbs_flops_take();
                     if ((rc = hbs_merge_lowrank(hs.merges[i], ds.d_merges + i, ds.d_tab, A64,
                                                 ws.as<double>() + ds.h_sys[i].off, A64, db, dc, dd, tol, s, kt,
                                                 &hbs_lr_rank)))
                         return rc;
+                    kt.flops[GM_K_MERGEUPDATE] += hbs_flops_take();
                 }
             }
         } else {
@@ -646,7 +738,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             CK(sweep(ds.d_sys, ds.h_sys, ds.max_m, ds.max_ncol, ws.p, ds.sum_rows, ds.sum_cols, (int)si + 1));
             CK(mx_merge_update(ds.d_merges, hs.merges, ds.d_tab, Adf, ws.as<float2>(), Adf, ds.max_rp, split,
                                ydig.as<__nv_bfloat16>(), yex.as<int>(), xdig.as<__nv_bfloat16>(), xex.as<int>(),
-                               ds.dig_elems, db, dc, dd, 0, dst, s, kt, wait_limit));
+                               ds.dig_elems, db, dc, dd, 0, dst, s, kt, wait_limit, tu.tc_min_k));
         }
         stamp();
     }
@@ -655,6 +747,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
     if (tol > 0.0) {
         // HBS roots (Sections 4-5): compress every S_root and invert it by Algorithm 1;
         // the solve applies Algorithm 2 (no dense T)
+        hbs_flops_take();
         kt.begin(GM_K_ROOT, 0.0, s);
         for (size_t i = 0; i < P.roots.size(); ++i) {
             const RootDesc &r = P.roots[i];
@@ -673,6 +766,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             peak = std::max(peak, (int64_t)(arena_bytes + h->hbs->pool_doubles * 8));
         }
         kt.end(s);
+        kt.flops[GM_K_ROOT] += hbs_flops_take();
     } else {
     // roots (Section 3.3 step 4): X = S_root^{-1} B for every problem in one sweep
     if ((rc = rws.alloc(dp.root_ws * 8, s))) return rc;
@@ -718,6 +812,11 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
     }
     stamp();
     }
+    if (record) {
+        cg.active = false;
+        CK(cudaStreamEndCapture(s, record));
+        return GM_OK;
+    }
     CK(cudaMemcpyAsync(hst.data(), stat.p, np * sizeof(Status), cudaMemcpyDeviceToHost, s));
     // release temporaries (stream-ordered) before the final synchronisation
     for (DBuf *b : {&rws, &piv, &u12, &perm, &perm_n, &a11, &fdig, &rdig, &fex, &rex, &ydig, &xdig, &yex, &xex, &bxd,
@@ -744,8 +843,9 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
     info.launches = launches;
     info.peak_workspace = peak;
     info.pivoting = blockpiv ? GM_PIVOT_BLOCK : GM_PIVOT_PARTIAL;
-    info.levels = P.L;
+    info.levels = P.L_user;
     info.precision = o.precision;
+    info.load_rank = -1;
     code.assign(np, 0);
     growth.assign(np, 0);
     int first = GM_OK;
@@ -834,6 +934,244 @@ int max_reaction(const std::vector<std::pair<int, int>> &probs, const double *dd
 
 // Build the problems listed in `sub` (indices into probs; coefficients of problem p at
 // off[p] of db/dc/dd) as one batch with options o; Hs receives their handles.
+// ----------------------------------------------------------------------------- tuning, graphs
+
+// Builds are tuned and recorded per plan and per option that changes what is launched.
+using TuneKey = std::tuple<const DevPlan *, int, int, int, int, int, int>;
+TuneKey tune_key(const std::shared_ptr<DevPlan> &dp, const gm_opts &o) {
+    return TuneKey(dp.get(), o.precision, o.pivoting, o.split_digits, o.panel_width, o.wait_limit, o.background);
+}
+std::mutex g_tune_mu;
+std::map<TuneKey, Tune> g_tunes;
+
+bool find_tune(const TuneKey &k, Tune &t) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tunes.find(k);
+    if (it == g_tunes.end()) return false;
+    t = it->second;
+    return true;
+}
+void store_tune(const TuneKey &k, const Tune &t) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tunes[k] = t;
+}
+
+// The autotuner: whole builds of the plan timed on the host (each ends with a stream
+// synchronisation), best of two per candidate, one launch-shape parameter at a time --
+// the R kernel's 32-column tiles (never / while the step leaves SMs idle / always), then
+// the merge update's tcgen05 bound on the interface length (192, 448, never).
+int autotune(const gm_opts &o, const std::shared_ptr<DevPlan> &dp, const std::vector<std::pair<int, int>> &keys,
+             const double *sb, const double *sc, const double *sd, Tune &best) {
+    auto time_of = [&](const Tune &t) -> double {
+        double bt = 1e300;
+        for (int rep = 0; rep < 2; ++rep) {
+            std::vector<gm_handle *> Hs;
+            for (const auto &k : keys) Hs.push_back(new_handle(k, o.precision));
+            std::vector<int> code, growth;
+            const auto t0 = std::chrono::steady_clock::now();
+            const int rc = run_build(o, 0.0, dp, sb, sc, sd, Hs, code, growth, t);
+            const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            for (gm_handle *h : Hs) gm_free(h);
+            if (rc != GM_OK) return 1e300;
+            bt = std::min(bt, ms);
+        }
+        return bt;
+    };
+    best = Tune();
+    double tb = time_of(best);
+    if (tb >= 1e300) return GM_OK;  // the plan does not build cleanly as is: keep the defaults
+    for (int r : {0, 1 << 30}) {
+        Tune t = best;
+        t.rtile32_max = r;
+        const double x = time_of(t);
+        if (x < tb) {
+            tb = x;
+            best = t;
+        }
+    }
+    if (o.precision == GM_PREC_MIXED)
+        for (int k : {448, 1 << 30}) {
+            Tune t = best;
+            t.tc_min_k = k;
+            const double x = time_of(t);
+            if (x < tb) {
+                tb = x;
+                best = t;
+            }
+        }
+    return GM_OK;
+}
+
+// A build recorded into a CUDA graph, with every buffer it reads or writes.
+struct GraphEntry {
+    TuneKey key;
+    Tune tune;
+    std::shared_ptr<DevPlan> plan;
+    char *mem = nullptr;  // coefficient staging, then everything the build allocated, in order
+    cudaGraphExec_t exec = nullptr;
+    double *cb = nullptr, *cc = nullptr, *cd = nullptr;
+    int64_t total = 0;
+    Status *stat = nullptr;
+    struct Out {
+        size_t T = 0, Tdf = 0, tdig = 0, tex = 0;  // offsets in mem (0: none)
+        size_t nT = 0, nTdf = 0, ntdig = 0, ntex = 0;
+    };
+    std::vector<Out> outs;
+    std::vector<gm_info_t> info;  // per problem: what does not depend on the run's status
+    long long last_use = 0;
+    ~GraphEntry() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (mem) cudaFree(mem);
+    }
+};
+std::mutex g_graph_mu;
+std::vector<std::shared_ptr<GraphEntry>> g_graphs;
+long long g_graph_tick = 0;
+constexpr size_t kMaxGraphs = 8;
+std::shared_ptr<GraphEntry> find_graph(const TuneKey &k, const Tune &t) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto &e : g_graphs)
+        if (e->key == k && e->tune.rtile32_max == t.rtile32_max && e->tune.tc_min_k == t.tc_min_k) {
+            e->last_use = ++g_graph_tick;
+            return e;
+        }
+    return nullptr;
+}
+
+// Record the plan's build into a graph with buffers of its own (`bytes` summed over the
+// first build's allocations).  Failure only means later builds run as usual.
+void record_graph(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dp,
+                  const std::vector<std::pair<int, int>> &keys, int64_t total, const Tune &tu, const TuneKey &tk,
+                  size_t bytes, const std::vector<gm_handle *> &built) {
+    auto E = std::make_shared<GraphEntry>();
+    E->key = tk;
+    E->tune = tu;
+    E->plan = dp;
+    E->total = total;
+    const size_t coef = BumpCtx::align(3 * (size_t)total * sizeof(double));
+    if (cudaMalloc((void **)&E->mem, coef + bytes + 4096) != cudaSuccess) {
+        cudaGetLastError();
+        E->mem = nullptr;
+        return;
+    }
+    E->cb = (double *)E->mem;
+    E->cc = E->cb + total;
+    E->cd = E->cc + total;
+    BumpCtx ctx;
+    ctx.base = E->mem + coef;
+    ctx.cap = bytes + 4096;
+    std::vector<gm_handle *> Hd;
+    for (const auto &k : keys) Hd.push_back(new_handle(k, o.precision));
+    std::vector<int> code, growth;
+    cudaGraph_t g = nullptr;
+    tl_bump = &ctx;
+    tl_recorded_status = nullptr;
+    int rc = run_build(o, tol, dp, E->cb, E->cc, E->cd, Hd, code, growth, tu, &g);
+    tl_bump = nullptr;
+    E->stat = tl_recorded_status;
+    if (rc == GM_OK && g && E->stat && cudaGraphInstantiate(&E->exec, g, 0) == cudaSuccess) {
+        auto off = [&](const void *p) { return p ? (size_t)((const char *)p - E->mem) : (size_t)0; };
+        for (size_t i = 0; i < Hd.size(); ++i) {
+            gm_handle *h = Hd[i];
+            GraphEntry::Out q;
+            const size_t N = 4 * (size_t)h->n;
+            q.T = off(h->T);
+            q.nT = N * N * 8;
+            if (h->Tdf) {
+                q.Tdf = off(h->Tdf);
+                q.nTdf = N * N * sizeof(float2);
+                q.tdig = off(h->tdig);
+                q.ntdig = (size_t)h->split * N * mx_kpad((int)N) * 2;
+                q.tex = off(h->tex);
+                q.ntex = N * sizeof(int);
+            }
+            E->outs.push_back(q);
+            E->info.push_back(built[i]->info);
+        }
+    } else {
+        cudaGetLastError();
+        if (E->exec) cudaGraphExecDestroy(E->exec);
+        E->exec = nullptr;
+    }
+    if (g) cudaGraphDestroy(g);
+    for (gm_handle *h : Hd) {  // their buffers belong to the graph
+        h->T = nullptr;
+        h->Tdf = nullptr;
+        h->tdig = nullptr;
+        h->tex = nullptr;
+        gm_free(h);
+    }
+    if (!E->exec) return;
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    E->last_use = ++g_graph_tick;
+    if (g_graphs.size() >= kMaxGraphs) {  // drop the least recently used
+        auto v = std::min_element(g_graphs.begin(), g_graphs.end(),
+                                  [](const auto &a, const auto &b) { return a->last_use < b->last_use; });
+        g_graphs.erase(v);
+    }
+    g_graphs.push_back(E);
+}
+
+// A later build of a recorded plan: coefficients in, one graph launch, the operators out.
+int replay(GraphEntry &E, const gm_opts &o, const std::vector<std::pair<int, int>> &keys, const double *sb,
+           const double *sc, const double *sd, int64_t total, std::vector<gm_handle *> &Hs, std::vector<int> &code,
+           std::vector<int> &growth) {
+    cudaStream_t s = (cudaStream_t)o.stream;
+    const size_t cb = (size_t)total * sizeof(double);
+    CK(cudaMemcpyAsync(E.cb, sb, cb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(E.cc, sc, cb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(E.cd, sd, cb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaGraphLaunch(E.exec, s));
+    const bool mixed = o.precision == GM_PREC_MIXED;
+    const int split = o.split_digits ? o.split_digits : 6;
+    for (size_t i = 0; i < keys.size(); ++i) {
+        gm_handle *h = new_handle(keys[i], o.precision);
+        Hs.push_back(h);
+        h->plan = E.plan;
+        h->L = E.plan->plan.L;
+        h->split = split;
+        h->kept_df32 = mixed;
+        const GraphEntry::Out &q = E.outs[i];
+        auto out = [&](void **dst, size_t offs, size_t n) -> int {
+            if (!n) return GM_OK;
+            if (lib_malloc(dst, n) != cudaSuccess) return GM_ENOMEM;
+            return cudaMemcpyAsync(*dst, E.mem + offs, n, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? GM_OK
+                                                                                                        : GM_ECUDA;
+        };
+        int rc;
+        if ((rc = out((void **)&h->T, q.T, q.nT)) || (rc = out((void **)&h->Tdf, q.Tdf, q.nTdf)) ||
+            (rc = out((void **)&h->tdig, q.tdig, q.ntdig)) || (rc = out((void **)&h->tex, q.tex, q.ntex)))
+            return rc;
+    }
+    std::vector<Status> hst(keys.size());
+    CK(cudaMemcpyAsync(hst.data(), E.stat, hst.size() * sizeof(Status), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const bool blockpiv = mixed && o.pivoting != GM_PIVOT_PARTIAL;
+    code.assign(keys.size(), 0);
+    growth.assign(keys.size(), 0);
+    int first = GM_OK;
+    for (size_t p = 0; p < keys.size(); ++p) {
+        gm_handle *h = Hs[p];
+        const Status &st = hst[p];
+        double mp;
+        memcpy(&mp, &st.min_piv, 8);
+        gm_info_t hi = E.info[p];
+        hi.min_pivot_ratio = mp / (4.0 * (h->n + 1.0) * (h->n + 1.0));
+        hi.bad_stage = st.code ? st.where : -1;
+        float rho;
+        memcpy(&rho, &st.rho, 4);
+        hi.refine_ratio = blockpiv ? (double)rho : 0.0;
+        hi.pivot_fallback = 0;
+        h->info = hi;
+        code[p] = st.code;
+        growth[p] = st.growth || (blockpiv && !(rho <= kMaxRefineRatio));
+        if (st.code && first == GM_OK) first = st.code;
+    }
+    return first;
+}
+
 int build_subset(const gm_opts &o, double tol, const std::vector<std::pair<int, int>> &probs,
                  const std::vector<int64_t> &off, const std::vector<int> &sub, const double *db, const double *dc,
                  const double *dd, std::vector<gm_handle *> &Hs, std::vector<int> &code, std::vector<int> &growth) {
@@ -864,8 +1202,29 @@ int build_subset(const gm_opts &o, double tol, const std::vector<std::pair<int, 
     }
     std::shared_ptr<DevPlan> dp;
     if ((rc = get_plan(keys, dp))) return rc;
+    const bool plain = tol == 0.0 && !o.keep_levels && !o.timing;
+    const TuneKey tk = tune_key(dp, o);
+    Tune tu;
+    if (!find_tune(tk, tu) && o.autotune && plain) {
+        if ((rc = autotune(o, dp, keys, sb, sc, sd, tu))) return rc;
+        store_tune(tk, tu);
+    }
+    if (o.graph && plain) {
+        std::shared_ptr<GraphEntry> E = find_graph(tk, tu);
+        if (E) return replay(*E, o, keys, sb, sc, sd, total, Hs, code, growth);
+        // first build of this plan: as usual, while the sizes of its allocations are summed,
+        // then recorded into a graph with buffers of its own for the later builds
+        BumpCtx meas;
+        meas.measure = true;
+        for (const auto &k : keys) Hs.push_back(new_handle(k, o.precision));
+        tl_bump = &meas;
+        rc = run_build(o, tol, dp, sb, sc, sd, Hs, code, growth, tu);
+        tl_bump = nullptr;
+        if (rc == GM_OK) record_graph(o, tol, dp, keys, total, tu, tk, meas.total, Hs);
+        return rc;
+    }
     for (const auto &k : keys) Hs.push_back(new_handle(k, o.precision));
-    return run_build(o, tol, dp, sb, sc, sd, Hs, code, growth);
+    return run_build(o, tol, dp, sb, sc, sd, Hs, code, growth, tu);
 }
 
 // Build with the automatic fallback; on failure every handle is freed.  In the mixed-
@@ -978,6 +1337,8 @@ void gm_free(gm_handle *h) {
     cudaFree(h->tdig);
     cudaFree(h->tex);
     cudaFree(h->F);
+    cudaFree(h->FL);
+    cudaFree(h->FR);
     for (void *p : h->kept_bufs) cudaFree(p);
     if (h->hbs) {
         gm::hbs_free(*h->hbs);
@@ -996,7 +1357,7 @@ int gm_build_ex(const gm_opts *opts, const double *b, const double *c, const dou
                 gm_handle **out) {
     if (!out) return GM_EINVAL;
     *out = nullptr;
-    if (!b || !c || !d || n < 2 || leaf < 4 || !(tol >= 0.0)) return GM_EINVAL;
+    if (!b || !c || !d || n < 2 || leaf < 3 || !(tol >= 0.0)) return GM_EINVAL;
     gm_opts o;
     int rc = check_opts(opts, o);
     if (rc) return rc;
@@ -1029,7 +1390,7 @@ int gm_build_batch(int count, const gm_problem *probs, const gm_opts *opts, doub
     int64_t total = 0;
     for (int i = 0; i < count; ++i) {
         const gm_problem &p = probs[i];
-        if (!p.b || !p.c || !p.d || p.n < 2 || p.leaf < 4) return GM_EINVAL;
+        if (!p.b || !p.c || !p.d || p.n < 2 || p.leaf < 3) return GM_EINVAL;
         key.push_back({p.n, p.leaf});
         total += (int64_t)p.n * p.n;
     }
@@ -1339,7 +1700,8 @@ int run_build_loads(const gm_opts &o, int n, int leaf, const std::vector<int> &b
     memcpy(&mp, &hst.min_piv, 8);
     info.n = n;
     info.leaf = leaf;
-    info.levels = P.L;
+    info.levels = P.L_user;
+    info.load_rank = -1;
     info.precision = GM_PREC_FP64;
     info.pivoting = GM_PIVOT_PARTIAL;
     info.dtn_bytes = (long long)nb4 * nb4 * 8;
@@ -1359,7 +1721,7 @@ int gm_build_loads(const gm_opts *opts, const double *b, const double *c, const 
                    const int *body, int nbody, gm_handle **out) {
     if (!out) return GM_EINVAL;
     *out = nullptr;
-    if (!b || !c || !d || n < 2 || leaf < 4 || !body || nbody < 1 || (int64_t)nbody > (int64_t)n * n)
+    if (!b || !c || !d || n < 2 || leaf < 3 || !body || nbody < 1 || (int64_t)nbody > (int64_t)n * n)
         return GM_EINVAL;
     gm_opts o;
     int rc = check_opts(opts, o);
@@ -1396,7 +1758,7 @@ int gm_build_loads(const gm_opts *opts, const double *b, const double *c, const 
 
 int gm_solve_loads(gm_handle *h, const double *g, const double *f, double *dudn, int batch, void *stream) {
     if (!h || batch < 0) return GM_EINVAL;
-    if (!h->F) return GM_EUNSUPPORTED;
+    if (!h->F && h->frank < 0) return GM_EUNSUPPORTED;
     if (batch == 0) return GM_OK;
     if (!g || !f || !dudn) return GM_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1422,7 +1784,16 @@ int gm_solve_loads(gm_handle *h, const double *g, const double *f, double *dudn,
         dv = vbuf.as<double>();
     }
     CK(launch_apply(h->T, dg, dv, N, batch, s));
-    CK(launch_apply_add(h->F, df, dv, N, m, batch, s));
+    if (h->frank < 0) {
+        CK(launch_apply_add(h->F, df, dv, N, m, batch, s));
+    } else if (h->frank > 0) {  // the low-rank form: dudn += FL (FR f)
+        const int k = h->frank;
+        DBuf w;
+        if ((rc = w.alloc((size_t)k * batch * 8, s))) return rc;
+        if ((rc = hbs_gemm(h->FR, k, 0, df, m, 0, w.as<double>(), k, k, batch, m, 1.0, 0.0, s)) ||
+            (rc = hbs_gemm(h->FL, N, 0, w.as<double>(), k, 0, dv, N, N, batch, k, 1.0, 1.0, s)))
+            return rc;
+    }
     if (!vd) {
         CK(cudaMemcpyAsync(dudn, dv, gbytes, cudaMemcpyDeviceToHost, s));
         gbuf.release();
@@ -1435,8 +1806,39 @@ int gm_solve_loads(gm_handle *h, const double *g, const double *f, double *dudn,
 
 int gm_get_load_operator(gm_handle *h, double *F_out) {
     if (!h || !F_out) return GM_EINVAL;
+    const size_t N = 4 * (size_t)h->n, bytes = N * h->nbody * 8;
+    if (h->frank >= 0) {  // the low-rank form, multiplied out
+        DBuf t;
+        int rc;
+        if ((rc = t.alloc(bytes, nullptr))) return rc;
+        CK(cudaMemsetAsync(t.p, 0, bytes, nullptr));
+        if (h->frank > 0 && (rc = hbs_gemm(h->FL, (int)N, 0, h->FR, h->frank, 0, t.as<double>(), (int)N, (int)N,
+                                           h->nbody, h->frank, 1.0, 0.0, nullptr)))
+            return rc;
+        CK(cudaMemcpyAsync(F_out, t.p, bytes, cudaMemcpyDefault, nullptr));
+        CK(cudaStreamSynchronize(nullptr));
+        return GM_OK;
+    }
     if (!h->F) return GM_EUNSUPPORTED;
-    CK(cudaMemcpy(F_out, h->F, (size_t)4 * h->n * h->nbody * 8, cudaMemcpyDefault));
+    CK(cudaMemcpy(F_out, h->F, bytes, cudaMemcpyDefault));
+    return GM_OK;
+}
+
+int gm_compress_load_operator(gm_handle *h, double tol) {
+    if (!h || !(tol > 0.0)) return GM_EINVAL;
+    if (!h->F) return GM_EUNSUPPORTED;  // no loads, or already compressed
+    const int N = 4 * h->n;
+    double *L = nullptr, *R = nullptr;
+    int k = 0;
+    int rc = hbs_lowrank(h->F, N, h->nbody, tol, nullptr, &L, &R, &k);
+    if (rc) return rc;
+    cudaFree(h->F);
+    h->F = nullptr;
+    h->FL = L;
+    h->FR = R;
+    h->frank = k;
+    h->info.load_rank = k;
+    h->info.resident_bytes = (long long)N * N * 8 + (long long)(N + h->nbody) * k * 8;
     return GM_OK;
 }
 
@@ -1450,7 +1852,7 @@ int gm_build_net(const gm_opts *opts, const double *sx, const double *sy, int n,
                  const int *body, int nbody, gm_handle **out) {
     if (!out) return GM_EINVAL;
     *out = nullptr;
-    if (!sx || !sy || n < 2 || leaf < 4 || !(tol >= 0.0) || nbody < 0 || (nbody > 0 && !body) ||
+    if (!sx || !sy || n < 2 || leaf < 3 || !(tol >= 0.0) || nbody < 0 || (nbody > 0 && !body) ||
         (int64_t)nbody > (int64_t)n * n)
         return GM_EINVAL;
     gm_opts o;

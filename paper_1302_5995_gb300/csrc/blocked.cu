@@ -36,7 +36,10 @@ constexpr int LDF = NBK + 1;  // padded row length of the df32 shared tiles
 // ----------------------------------------------------------------------------- factor
 
 constexpr int FAC_THREADS = 256;
-constexpr int PRS = 36;  // shared stride of the four 32-column groups of the pivot row
+// The factor's 64 x 128 matrix in shared memory: column c of a row at (c / 32) FCG + c % 32
+// (each 32-column group padded to 36 floats, so the four groups a warp touches at once
+// fall in different banks), rows FML floats apart.
+constexpr int FCG = 36, FML = 4 * FCG + 4;
 
 // Sort key of a pivot candidate in one 32-bit word, for a single warp max-reduction: the
 // top 26 bits are |v| (its float bits with the six lowest cleared; a NaN counts as 0,
@@ -86,19 +89,23 @@ __device__ __forceinline__ void slice_rows64(Get get, int r, int seg, __nv_bfloa
 }
 
 // X0 ~ A11^{-1} by Gauss-Jordan on [A11 | I] in FP32 with partial pivoting among the rows
-// of the block.  The 64 x 128 augmented matrix lives in registers: thread (row, cg) holds
-// columns 32 cg .. 32 cg + 31 of one row (four threads per row, eight rows per warp).
-// Rows never move: the pivot row of column t is the unused row of largest |entry| (the
-// lowest of rows within 2^-17 of it, see piv_key), and row t of X0 is the right half of
-// that row at the end.
+// of the block, blocked by panels of 8 pivots.  The 64 x 128 augmented matrix lives in
+// registers: thread (row, cg) holds columns 32 cg .. 32 cg + 31 of one row (four threads
+// per row, eight rows per warp).  Rows never move: the pivot of column t is the unused row
+// of largest |entry| (the lowest of rows within 2^-17 of it, see piv_key), and row t of X0
+// is the right half of that row at the end.
 //
-// One barrier per column.  Every warp keeps its own copy of the current pivot column
-// (rows lane and lane + 32), so it finds the pivot row without talking to the others;
-// the pivot row is published unscaled (its threads need nothing but their registers),
-// every row then applies g = f / pivot (the pivot row scales itself); the owners of
-// column t + 2 publish it after the update of column t, and each warp brings column
-// t + 1 up to date itself with the same operations the owners use (so every copy agrees
-// bit for bit with the registers).  Shared buffers alternate between even and odd columns.
+// One panel (columns t0 .. t0 + 7):
+//   1. every thread stores its values to shared memory (two buffers, alternating);
+//   2. warp 0 eliminates the 64 x 8 panel alone, in registers (two rows per lane, the
+//      pivot found by one warp reduction of the packed keys, the pivot row broadcast by
+//      shuffles), and tracks the panel's combined row transform: with P the 8 pivot rows,
+//      the 8 steps amount to new[r] = [r not in P] old[r] + sum_u T(r, p_u) old[p_u], and
+//      column u of T starts as the unit vector of p_u when p_u is chosen (no earlier step
+//      used that row as a source) and then takes the remaining steps' row operations;
+//   3. every thread applies that rank-8 transform to its 32 columns.
+// Two block barriers per 8 pivots (instead of one per pivot); the arithmetic is the same
+// Gauss-Jordan up to the order of the FP32 roundings.
 template <int S>
 __global__ void __launch_bounds__(FAC_THREADS)
 k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int k, __nv_bfloat16 *__restrict__ x_dig,
@@ -108,8 +115,6 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
     pdl_wait();
     float2 *Adf = (float2 *)smem_raw;       // [64][LDF] A11 (df32)
     float *Xs = (float *)(Adf + 64 * LDF);  // [64][65] rows of X0
-    __shared__ __align__(16) float prow[2][4 * PRS];  // pivot row (unscaled), registers' order
-    __shared__ float colb[2][64];                     // a column published by its owners
     __shared__ float s_pm[64];
     const SysDesc Sy = sys[blockIdx.x];
     const int m = Sy.m;
@@ -140,81 +145,105 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
         const int c = cg * 32 + j;
         a[j] = c < 64 ? Adf[row * LDF + c].x : (c - 64 == row ? 1.f : 0.f);
     }
-    float k0 = Adf[lane * LDF].x, k1 = Adf[(lane + 32) * LDF].x;  // column 0, this warp's copy
-    if (tid < 64) colb[1][tid] = Adf[tid * LDF + 1].x;            // column 1, read at column 0
-    __syncthreads();
-    const bool hi = warp >= 4;  // this warp's rows are 32 .. 63
-    bool used0 = false, used1 = false;  // rows lane and lane + 32 have been pivots
-    int my_step = 0;
-    // The t loop advances four columns at a time (the body unrolled four times), so the
-    // register holding a column is known at compile time: group t / 32 drops the four
-    // columns it has eliminated after each round by shifting its registers down by four
-    // (identically in every row), and column t sits at a[t % 4] of its group.
+    // the matrix for the panel warp [64][FML] (Xs shares its space: X0 is written after
+    // the last panel), and the panel's 8 pivot rows [8][FML] for the update, copied out by
+    // the panel warp, so that the next panel may overwrite the matrix while the update of
+    // this one still reads them
+    float *Mc = Xs, *PRs = Xs + 64 * FML;
+    __shared__ float TCs[64][9];  // the panel's transform T(r, p_u)
+    __shared__ int Ps[8];
+    __shared__ int s_step[64];
+    bool used0 = false, used1 = false;  // warp 0: rows lane and lane + 32 have been pivots
 #pragma unroll 1
-    for (int t0 = 0; t0 < 64; t0 += 4) {
-        const int ct = t0 >> 5;
+    for (int pnl = 0; pnl < 8; ++pnl) {
+        const int t0 = pnl * 8;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int t = t0 + u;
-            // this row's multiplier, then the pivot row: the same reduction over the same
-            // copy of column t in every warp
-            const float f = __shfl_sync(FULL, hi ? k1 : k0, row & 31);
-            const unsigned key = __reduce_max_sync(FULL, max(piv_key(k0, lane, used0), piv_key(k1, lane + 32, used1)));
-            const int p = 63 - (int)(key & 63u);
-            used0 |= lane == p;
-            used1 |= lane + 32 == p;
-            float *pr = prow[t & 1];
-            if (warp == (p >> 3)) {  // warp-uniform: only the pivot row's warp enters
-                if (row == p) {
+        for (int j = 0; j < 32; j += 4)
+            *(float4 *)&Mc[row * FML + cg * FCG + j] = make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
+        __syncthreads();
+        if (warp == 0) {
+            float pv[2][8], tc[2][8];
+            const int pc = (t0 >> 5) * FCG + (t0 & 31);  // the panel's first column
 #pragma unroll
-                    for (int j = 0; j < 32; j += 4)
-                        *(float4 *)&pr[cg * PRS + j] = make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
-                    my_step = t;
+            for (int v = 0; v < 8; ++v) {
+                pv[0][v] = Mc[lane * FML + pc + v];
+                pv[1][v] = Mc[(lane + 32) * FML + pc + v];
+                tc[0][v] = 0.f;
+                tc[1][v] = 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const unsigned key =
+                    __reduce_max_sync(FULL, max(piv_key(pv[0][u], lane, used0), piv_key(pv[1][u], lane + 32, used1)));
+                const int p = 63 - (int)(key & 63u), src = p & 31;
+                const bool mine0 = lane == p, mine1 = lane + 32 == p, hp = p >= 32;
+                used0 |= mine0;
+                used1 |= mine1;
+                tc[0][u] = mine0 ? 1.f : 0.f;
+                tc[1][u] = mine1 ? 1.f : 0.f;
+                float prv[8], prt[8];
+#pragma unroll
+                for (int v = u; v < 8; ++v) prv[v] = __shfl_sync(FULL, hp ? pv[1][v] : pv[0][v], src);
+#pragma unroll
+                for (int v = 0; v <= u; ++v) prt[v] = __shfl_sync(FULL, hp ? tc[1][v] : tc[0][v], src);
+                const float piv = prv[u], ip = __frcp_rn(piv);
+                if (lane == 0) {
+                    s_pm[t0 + u] = fabsf(piv);
+                    if (t0 + u < nbe) pmag[(size_t)blockIdx.x * 64 + t0 + u] = fabsf(piv);
+                    Ps[u] = p;
+                    s_step[p] = t0 + u;
+                }
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const bool isp = r ? mine1 : mine0;
+                    const float g = pv[r][u] * ip;
+#pragma unroll
+                    for (int v = u; v < 8; ++v) pv[r][v] = isp ? prv[v] * ip : fmaf(-g, prv[v], pv[r][v]);
+#pragma unroll
+                    for (int v = 0; v <= u; ++v) tc[r][v] = isp ? prt[v] * ip : fmaf(-g, prt[v], tc[r][v]);
                 }
             }
-            const float piv = __shfl_sync(FULL, (p & 32) ? k1 : k0, p & 31);
-            const float ip = __frcp_rn(piv);
-            if (tid == 0) {
-                s_pm[t] = fabsf(piv);
-                if (t < nbe) pmag[(size_t)blockIdx.x * 64 + t] = fabsf(piv);
-            }
-            __syncthreads();
-            const float g = f * ip;
-            if (warp == (p >> 3) && row == p) {  // the pivot row becomes the scaled row
 #pragma unroll
-                for (int j = 0; j < 32; ++j) a[j] *= ip;
-            } else {
+            for (int v = 0; v < 8; ++v) {
+                TCs[lane][v] = tc[0][v];
+                TCs[lane + 32][v] = tc[1][v];
+            }
+            // the pivot rows (as they were at the start of the panel) for the update
 #pragma unroll
-                for (int j = 0; j < 32; j += 4) {
-                    const float4 q = *(const float4 *)&pr[cg * PRS + j];
-                    a[j] = fmaf(-g, q.x, a[j]);
-                    a[j + 1] = fmaf(-g, q.y, a[j + 1]);
-                    a[j + 2] = fmaf(-g, q.z, a[j + 2]);
-                    a[j + 3] = fmaf(-g, q.w, a[j + 3]);
-                }
-            }
-            // the owners of column t + 2 publish it (read by every warp at column t + 1);
-            // it is in this group at a[u + 2], or at a[u - 2] of the next group at t = 30, 31
-            if (t + 2 < 64) {
-                const int cc = (t + 2) >> 5;
-                if (cg == cc) colb[t & 1][row] = (u >= 2 && cc != ct) ? a[u >= 2 ? u - 2 : 0] : a[u + 2];
-            }
-            // every warp: its copy of column t + 1 after this column's update
-            if (t + 1 < 64) {
-                const int g1 = (t + 1) >> 5;
-                const float q1 = pr[g1 * PRS + (g1 == ct ? u + 1 : 0)];
-                const float n0 = colb[(t + 1) & 1][lane], n1 = colb[(t + 1) & 1][lane + 32];
-                k0 = (lane == p) ? q1 * ip : fmaf(-(k0 * ip), q1, n0);
-                k1 = (lane + 32 == p) ? q1 * ip : fmaf(-(k1 * ip), q1, n1);
+            for (int u = 0; u < 8; ++u) {
+                const int pr = __shfl_sync(FULL, lane == 0 ? Ps[u] : 0, 0);
+                const int q = (lane >> 3) * FCG + (lane & 7) * 4;
+                *(float4 *)&PRs[u * FML + q] = *(const float4 *)&Mc[pr * FML + q];
             }
         }
-        if (cg == ct) {
+        __syncthreads();
+        float tcr[8];
+        int pu[8];
+        bool inP = false;
 #pragma unroll
-            for (int j = 0; j < 28; ++j) a[j] = a[j + 4];
+        for (int u = 0; u < 8; ++u) {
+            tcr[u] = TCs[row][u];
+            pu[u] = Ps[u];
+            inP |= pu[u] == row;
+        }
 #pragma unroll
-            for (int j = 28; j < 32; ++j) a[j] = 0.f;
+        for (int j = 0; j < 32; j += 4) {
+            float4 acc = inP ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float4 q = *(const float4 *)&PRs[u * FML + cg * FCG + j];
+                acc.x = fmaf(tcr[u], q.x, acc.x);
+                acc.y = fmaf(tcr[u], q.y, acc.y);
+                acc.z = fmaf(tcr[u], q.z, acc.z);
+                acc.w = fmaf(tcr[u], q.w, acc.w);
+            }
+            a[j] = acc.x;
+            a[j + 1] = acc.y;
+            a[j + 2] = acc.z;
+            a[j + 3] = acc.w;
         }
     }
+    const int my_step = s_step[row];
     pdl_trigger();  // the R kernel may start launching while this one cuts its digits
     if (cg >= 2) {
 #pragma unroll
@@ -236,7 +265,8 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
 
 size_t blk_factor_smem(int split) {
     (void)split;
-    return (size_t)64 * LDF * sizeof(float2) + (size_t)64 * 65 * sizeof(float);
+    // A11 (df32), then the matrix and the pivot rows of a panel (X0 reuses the matrix's space)
+    return (size_t)64 * LDF * sizeof(float2) + (size_t)(64 + 8) * FML * sizeof(float);
 }
 
 // ----------------------------------------------------------------------------- full-K digit tiles
@@ -812,9 +842,12 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
             const double nbe = std::min(NBK, S.m - k), cols = S.ncol - k - nbe;
             fl_fac += 2.0 * nbe * nbe * nbe;
             fl_r += 2.0 * nbe * nbe * cols;
-            fl_upd += 2.0 * (S.m - nbe) * nbe * cols;
+            // algorithmic (LU) count: the rows below the block over every remaining column,
+            // the rows above it over the right-hand sides only (their matrix columns are the
+            // Gauss-Jordan sweep's extra m^3/3, which an LU with back substitution avoids)
+            fl_upd += 2.0 * nbe * ((S.m - k - nbe) * cols + (double)k * (S.ncol - S.m));
             const double nrow = std::max(0.0, std::min(64.0, (double)S.m - k - 64));  // next pivot rows
-            fl_next += 2.0 * nbe * ((S.m - nbe) * std::min(64.0, cols) + nrow * std::max(0.0, cols - 64));
+            fl_next += 2.0 * nbe * ((S.m - k - nbe) * std::min(64.0, cols) + nrow * std::max(0.0, cols - 64));
         }
         const int cols = max_ncol - k;
         const int cb = (cols + 63) / 64, rb = (max_m + 127) / 128;
@@ -832,7 +865,7 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
         kt.begin(GM_K_PIVROWS, fl_r, c);
         // 32-column R tiles while the step would leave most SMs idle
         const bool pdl_r = !kt.timed(GM_K_PANEL) && !kt.timed(GM_K_PIVROWS);
-        if (nsys * cb <= 96) {
+        if (nsys * cb <= scr.rtile32_max) {
             const int cb32 = (cols + 31) / 32;
             BLK_SPLIT_DISPATCH(split, (e = launch_k(pdl_r, k_blk_rfused<SS, 1>, dim3(cb32 + rb, nsys),
                                                     dim3(TILE_THREADS), rsm, c, d_sys, ws, k, cb32, scr.x_dig,

@@ -31,6 +31,7 @@ struct BlkScratch {
     cudaStream_t s1 = nullptr, s2 = nullptr;
     cudaEvent_t ev_r = nullptr, ev_rest = nullptr, ev_join = nullptr;
     int wait_limit = 1 << 22;  // polls of the tensor-core completion wait before GM_ETIMEOUT
+    int rtile32_max = 96;      // R kernel: 32-column tiles while systems x 64-column tiles <= this
 };
 
 size_t blk_factor_smem(int split);

@@ -103,8 +103,19 @@ struct RootDesc {
     int problem;     // index in the batch
 };
 
+// Launch-shape choices of a build that the autotuner may change (the defaults were the
+// fastest measured on the 512^2 convection workload).
+struct Tune {
+    int rtile32_max = 96;  // R kernel: 32-column tiles while systems x 64-column tiles <= this
+    int tc_min_k = 192;    // merge update on tcgen05 for interfaces with K >= this (else mma.sync)
+};
+
+// Largest leaf edge the leaf kernels take (band and inner-ring solves in shared memory).
+constexpr int kMaxLeafEdge = 17;
+
 struct Plan {
     int n, leaf, L;
+    int L_user;  // levels of the tree for the requested leaf (L is larger when leaf > kMaxLeafEdge)
     std::vector<RootDesc> roots;
     std::vector<LeafDesc> leaves;
     std::vector<Box> leaf_boxes;

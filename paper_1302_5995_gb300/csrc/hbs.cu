@@ -529,8 +529,12 @@ struct DescBuf {
     }
 };
 
+// Algorithmic flops of the HBS steps issued by this thread since the last take.
+thread_local double tl_flops = 0.0;
+
 int run_gemms(const std::vector<GemmDesc> &v, DescBuf &db, cudaStream_t s) {
     if (v.empty()) return GM_OK;
+    for (const GemmDesc &d : v) tl_flops += 2.0 * d.m * d.n * d.k;
     int rc = db.ensure(v.size() * sizeof(GemmDesc), s);
     if (rc) return rc;
     HCK(cudaMemcpyAsync(db.p, v.data(), v.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, s));
@@ -619,6 +623,7 @@ int invert_batch(const std::vector<std::pair<double *, int>> &mats, cudaStream_t
         max_m = std::max(max_m, m);
     }
     if (h.empty()) return GM_OK;
+    for (const SysDesc &q : h) tl_flops += 2.0 * (double)q.m * q.m * q.m;  // Gauss-Jordan on [M | I]
     const int nb = 8, nsys = (int)h.size();
     void *dsys = nullptr, *piv = nullptr, *u12 = nullptr, *st = nullptr;
     int rc = GM_OK;
@@ -785,6 +790,7 @@ int hbs_factor_l(const double *S, int lds, int r, int m, double tol, int l, bool
         }
         int rc2 = run_qr(q, tol, HBS_MARGIN, db, s);
         if (rc2) return rc2;
+        for (const QrDesc &d : q) tl_flops += 4.0 * d.p * d.l * std::min(d.p, d.l) / 2;  // half the steps, on average
         // the nodes of a level are consecutive: one read-back
         const int t0 = nodes.front(), cnt = nodes.back() - t0 + 1;
         std::vector<int> res(4 * (size_t)cnt);
@@ -1008,6 +1014,12 @@ int hbs_factor_l(const double *S, int lds, int r, int m, double tol, int l, bool
 
 }  // namespace
 
+double hbs_flops_take() {
+    const double f = tl_flops;
+    tl_flops = 0.0;
+    return f;
+}
+
 namespace {
 void release_pool(HbsRoot &h) {
     if (h.pool) {
@@ -1228,13 +1240,17 @@ __global__ void k_hbs_gather_offdiag(const MergeDesc *__restrict__ md, const int
     }
 }
 
-// A_i ~ L_i R_i (i = 0, 1; A_i rows_i x cols, column-major, ld rows_i) at relative
-// tolerance tol: L_i an orthonormal basis of the range of a Gaussian sample A_i Omega
-// truncated at the first |R_jj| <= tol |R_11| of its pivoted QR, R_i = L_i^T A_i.  The
-// sample count starts at the last one that sufficed for this size and doubles while a
-// rank comes within HBS_OVERSAMPLE of it.
-int lowrank_pair(const double *const A[2], const int rows[2], int cols, double tol, TempSet &tmp, DescBuf &db,
-                 cudaStream_t s, double *L[2], double *R[2], int k[2]) {
+// A_i ~ L_i R_i (A_i rows_i x cols, column-major, ld rows_i) at relative tolerance tol:
+// L_i an orthonormal basis of the range of a Gaussian sample A_i Omega truncated at the
+// first |R_jj| <= tol |R_11| of its pivoted QR, R_i = L_i^T A_i (k_i x cols).  The sample
+// count starts at the last one that sufficed for this size and doubles while a rank comes
+// within HBS_OVERSAMPLE of it.  L_i, R_i come from tmp.
+int lowrank_n(const std::vector<const double *> &A, const std::vector<int> &rows, int cols, double tol, TempSet &tmp,
+              DescBuf &db, cudaStream_t s, std::vector<double *> &L, std::vector<double *> &R, std::vector<int> &k) {
+    const size_t na = A.size();
+    L.assign(na, nullptr);
+    R.assign(na, nullptr);
+    k.assign(na, 0);
     const std::pair<int, int> key(size_class(cols), -1);
     int l = HBS_SAMPLES;
     {
@@ -1242,7 +1258,7 @@ int lowrank_pair(const double *const A[2], const int rows[2], int cols, double t
         auto it = g_hint.find(key);
         if (it != g_hint.end()) l = it->second;
     }
-    int *outs = (int *)tmp.get(2);
+    int *outs = (int *)tmp.get((int64_t)na);
     if (!outs) return GM_ENOMEM;
     for (;;) {
         const int le = std::min(l, cols);
@@ -1252,23 +1268,23 @@ int lowrank_pair(const double *const A[2], const int rows[2], int cols, double t
         HCK(cudaGetLastError());
         std::vector<GemmDesc> g;
         std::vector<QrDesc> q;
-        double *Y[2];
-        for (int i = 0; i < 2; ++i) {
-            Y[i] = tmp.get((int64_t)rows[i] * le);
+        for (size_t i = 0; i < na; ++i) {
+            double *Y = tmp.get((int64_t)rows[i] * le);
             L[i] = tmp.get((int64_t)rows[i] * std::min(rows[i], le));
             double *w = tmp.get((int64_t)rows[i] * le);
-            if (!Y[i] || !L[i] || !w) return GM_ENOMEM;
-            g.push_back(gd(A[i], rows[i], 0, Om, cols, 0, Y[i], rows[i], rows[i], le, cols, 1.0, 0.0));
-            q.push_back(QrDesc{Y[i], L[i], outs + 2 * i, w, rows[i], le, rows[i], rows[i]});
+            if (!Y || !L[i] || !w) return GM_ENOMEM;
+            g.push_back(gd(A[i], rows[i], 0, Om, cols, 0, Y, rows[i], rows[i], le, cols, 1.0, 0.0));
+            q.push_back(QrDesc{Y, L[i], outs + 2 * i, w, rows[i], le, rows[i], rows[i]});
         }
         int rc = run_gemms(g, db, s);
         if (rc == GM_OK) rc = run_qr(q, tol, 0, db, s);
+        for (const QrDesc &d : q) tl_flops += 4.0 * d.p * d.l * std::min(d.p, d.l) / 2;
         if (rc) return rc;
-        int res[4];
-        HCK(cudaMemcpyAsync(res, outs, sizeof(res), cudaMemcpyDeviceToHost, s));
+        std::vector<int> res(2 * na);
+        HCK(cudaMemcpyAsync(res.data(), outs, res.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
         HCK(cudaStreamSynchronize(s));
         bool more = false;
-        for (int i = 0; i < 2; ++i) {
+        for (size_t i = 0; i < na; ++i) {
             k[i] = std::min(res[2 * i], res[2 * i + 1]);
             if (res[2 * i] > le - HBS_OVERSAMPLE && le < std::min(rows[i], cols)) more = true;
         }
@@ -1281,7 +1297,7 @@ int lowrank_pair(const double *const A[2], const int rows[2], int cols, double t
         g_hint[key] = l;
     }
     std::vector<GemmDesc> g;
-    for (int i = 0; i < 2; ++i) {
+    for (size_t i = 0; i < na; ++i) {
         R[i] = tmp.get((int64_t)std::max(k[i], 1) * cols);
         if (!R[i]) return GM_ENOMEM;
         g.push_back(gd(L[i], rows[i], 1, A[i], rows[i], 0, R[i], std::max(k[i], 1), k[i], cols, rows[i], 1.0, 0.0));
@@ -1302,10 +1318,9 @@ int hbs_merge_lowrank(const MergeDesc &hm, const MergeDesc *d_md, const int *d_t
     const int64_t tot = (int64_t)rp * sp;
     k_hbs_gather_offdiag<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, s>>>(d_md, d_tab, in, S13, S24);
     HCK(cudaGetLastError());
-    const double *A[2] = {S13, S24};
-    double *L[2], *R[2];
-    int k[2];
-    int rc = lowrank_pair(A, rows, sp, tol, tmp, db, s, L, R, k);
+    std::vector<double *> L, R;
+    std::vector<int> k;
+    int rc = lowrank_n({S13, S24}, {rows[0], rows[1]}, sp, tol, tmp, db, s, L, R, k);
     if (rc) return rc;
     // W13 = R13 X3, W24 = R24 X4 (X = M^{-1} Z, the right block of the system)
     const double *X = ws + (size_t)M * M;
@@ -1319,6 +1334,38 @@ int hbs_merge_lowrank(const MergeDesc &hm, const MergeDesc *d_md, const int *d_t
     HCK(launch_merge_update_lr(d_md, hm, d_tab, in, lr, out, bf, cf, df, s, kt));
     if (max_rank) *max_rank = std::max(*max_rank, std::max(k[0], k[1]));
     return GM_OK;
+}
+
+int hbs_lowrank(const double *A, int rows, int cols, double tol, cudaStream_t s, double **Lout, double **Rout,
+                int *kout) {
+    *Lout = *Rout = nullptr;
+    *kout = 0;
+    if (!A || rows < 1 || cols < 1 || !(tol > 0.0)) return GM_EINVAL;
+    TempSet tmp(s);
+    DescBuf db;
+    std::vector<double *> L, R;
+    std::vector<int> k;
+    int rc = lowrank_n({A}, {rows}, cols, tol, tmp, db, s, L, R, k);
+    if (rc) return rc;
+    const int kk = k[0];
+    if (cudaMalloc((void **)Lout, (size_t)rows * std::max(kk, 1) * 8) != cudaSuccess ||
+        cudaMalloc((void **)Rout, (size_t)std::max(kk, 1) * cols * 8) != cudaSuccess) {
+        cudaGetLastError();
+        if (*Lout) cudaFree(*Lout);
+        *Lout = *Rout = nullptr;
+        return GM_ENOMEM;
+    }
+    HCK(cudaMemcpyAsync(*Lout, L[0], (size_t)rows * kk * 8, cudaMemcpyDeviceToDevice, s));
+    HCK(cudaMemcpyAsync(*Rout, R[0], (size_t)kk * cols * 8, cudaMemcpyDeviceToDevice, s));
+    HCK(cudaStreamSynchronize(s));
+    *kout = kk;
+    return GM_OK;
+}
+
+int hbs_gemm(const double *A, int lda, int ta, const double *B, int ldb, int tb, double *C, int ldc, int m, int n,
+             int k, double alpha, double beta, cudaStream_t s) {
+    DescBuf db;
+    return run_gemms({gd(A, lda, ta, B, ldb, tb, C, ldc, m, n, k, alpha, beta)}, db, s);
 }
 
 namespace {

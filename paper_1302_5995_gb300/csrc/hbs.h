@@ -75,6 +75,17 @@ int hbs_apply_dtn(HbsRoot &h, const double *g, double *dudn, int B, cudaStream_t
 int hbs_dense_dtn(HbsRoot &h, double *T, cudaStream_t s);
 cudaError_t hbs_df32_to_f64(const float2 *x, double *y, int64_t cnt, cudaStream_t s);
 void hbs_free(HbsRoot &h);
+// A (rows x cols, column-major, ld rows, device) ~ L R at relative tolerance tol, from a
+// Gaussian sample of A truncated at the first |R_jj| <= tol |R_11| of its pivoted QR: L
+// (rows x k, orthonormal) and R = L^T A (k x cols) in new cudaMalloc buffers (owned by the
+// caller), k in *k.
+int hbs_lowrank(const double *A, int rows, int cols, double tol, cudaStream_t s, double **L, double **R, int *k);
+// C (m x n) = alpha op(A) op(B) + beta C in FP64 (column-major; op(X) = X^T when tX).
+int hbs_gemm(const double *A, int lda, int ta, const double *B, int ldb, int tb, double *C, int ldc, int m, int n,
+             int k, double alpha, double beta, cudaStream_t s);
+// Algorithmic flops of the HBS steps this thread issued since the last call (products,
+// QR factorisations, dense inversions), then reset.
+double hbs_flops_take();
 // Doubles of the operator in HBS form (Section 4), from the node ranks: D, U, V of every
 // leaf, U, V of every inner node below the root, and the two B blocks between the
 // children of every inner node -- the memory the paper reports as M(n).

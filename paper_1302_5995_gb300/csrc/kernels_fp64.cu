@@ -806,7 +806,10 @@ cudaError_t launch_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_
             double e = std::min(nb, S.m - k), r = S.m - k, cols = S.ncol - k - e;
             fl_panel += r * e * e;
             fl_piv += 2.0 * e * e * cols;
-            fl_upd += 2.0 * (S.m - e) * e * cols;
+            // algorithmic (LU) count: rows below the panel over every remaining column, rows
+            // above it over the right-hand sides only (the rest is the Gauss-Jordan sweep's
+            // extra m^3/3 over an LU with back substitution)
+            fl_upd += 2.0 * e * ((S.m - k - e) * cols + (double)k * (S.ncol - S.m));
         }
         size_t smem = (size_t)rows * nbe * sizeof(double);
         kt.begin(GM_K_PANEL, fl_panel, s);

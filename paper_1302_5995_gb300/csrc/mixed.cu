@@ -453,7 +453,6 @@ k_mx_merge_update(const MergeDesc *__restrict__ md, const int *__restrict__ tab,
 // after each chunk eight warps read the levels back (tcgen05.ld) and apply the same
 // epilogue as the mma.sync kernel.  Every wait is bounded (GM_ETIMEOUT, no hang).
 constexpr int MT_ROWS = 128, MT_COLS = 64, MT_STAGES = 4, MT_KTILES = 32;  // 32 x 16 = 512 k per chunk
-constexpr int MT_TC_MIN_K = 192;  // shorter merges keep the mma.sync kernel
 
 size_t mx_merge_tc_smem(int split) {
     // at least 120 KB, so one CTA per SM: each CTA allocates all 512 tensor-memory columns
@@ -889,14 +888,14 @@ cudaError_t mx_merge_update(const MergeDesc *md, const std::vector<MergeDesc> &h
                             const float2 *in, const float2 *ws, float2 *out, int max_rp, int split,
                             __nv_bfloat16 *ydig, int *yex, __nv_bfloat16 *xdig, int *xex, int64_t plane,
                             const double *b, const double *c, const double *d, int n, Status *st, cudaStream_t s,
-                            KTimer &kt, int wait_limit) {
+                            KTimer &kt, int wait_limit, int tc_min_k) {
     double fl = 0;
     for (const MergeDesc &M : h_md) fl += 2.0 * (double)M.rp * M.rp * M.sp;
     const int nm = (int)h_md.size();
     const int rb = (max_rp + 3) / 4;
     int max_kpad = 0;
     for (const MergeDesc &M : h_md) max_kpad = std::max(max_kpad, M.kpad);
-    const bool tc = max_kpad >= MT_TC_MIN_K;  // the tcgen05 kernel reads tile-ordered digit planes
+    const bool tc = max_kpad >= tc_min_k;  // the tcgen05 kernel reads tile-ordered digit planes
     kt.begin(GM_K_MERGEUPDATE, fl, s);
     MX_SPLIT_DISPATCH(split, (k_mx_merge_slice<SS><<<dim3(2 * rb, nm), 128, 0, s>>>(md, tab, in, ws, rb, ydig, yex,
                                                                                       xdig, xex, plane, tc ? 1 : 0)));

@@ -38,7 +38,7 @@ cudaError_t mx_merge_update(const MergeDesc *md, const std::vector<MergeDesc> &h
                             const float2 *in, const float2 *ws, float2 *out, int max_rp, int split,
                             __nv_bfloat16 *ydig, int *yex, __nv_bfloat16 *xdig, int *xex, int64_t plane,
                             const double *b, const double *c, const double *d, int n, Status *st, cudaStream_t s,
-                            KTimer &kt, int wait_limit);
+                            KTimer &kt, int wait_limit, int tc_min_k);
 cudaError_t mx_root_assemble(const float2 *S, int r, int n, float2 *ws, const double *b, const double *c,
                              const double *d, cudaStream_t s, KTimer &kt);
 int mx_kpad(int N);

@@ -121,11 +121,16 @@ void add_merge(Stage &st, int n, const Box &c1, int64_t s1, const Box &c2, int64
 }  // namespace
 
 int build_plan(int n, int leaf, Plan &plan) {
-    if (n < 2 || leaf < 4) return GM_EINVAL;
+    if (n < 2 || leaf < 3) return GM_EINVAL;
     plan = Plan{};
     plan.n = n;
     plan.leaf = leaf;
-    plan.L = num_levels(n, leaf);
+    // Leaves wider than the leaf kernels take (edge 17) are eliminated in nested-dissection
+    // order: the tree continues below the requested leaf level with boxes of edge <= 16.
+    // The splits are the same at every level, so the requested leaves are the boxes of
+    // level L_user of this tree, and their Schur complements are exact eliminations.
+    plan.L_user = num_levels(n, leaf);
+    plan.L = num_levels(n, leaf <= kMaxLeafEdge ? leaf : 16);
     std::vector<std::vector<Box>> levels(plan.L + 1);
     levels[0].push_back({0, 0, n, n});
     for (int l = 0; l < plan.L; ++l)
@@ -204,6 +209,8 @@ int build_batch_plan(const std::vector<const Plan *> &plans, const std::vector<i
     out.n = plans[0]->n;
     out.leaf = plans[0]->leaf;
     out.L = Lmax;
+    out.L_user = 0;
+    for (const Plan *p : plans) out.L_user = std::max(out.L_user, p->L_user);
     out.stages.resize(NS);
     for (int s = 0; s < NS; ++s) out.stages[s].orient = s % 2;
     // global layout: all leaves, then aligned stage 0 of all problems, stage 1, ...

@@ -33,7 +33,7 @@ def _build_ex(lib, opts, b, c, d, n, leaf, tol):
     return rc
 
 
-@pytest.mark.parametrize("case", ["null_b", "n1", "leaf3", "tol_neg", "tol_nan"])
+@pytest.mark.parametrize("case", ["null_b", "n1", "leaf2", "tol_neg", "tol_nan"])
 def test_build_rejects_bad_arguments(lib, case):
     n, leaf, tol = 8, 4, 0.0
     b, c, d = _fields(n)
@@ -41,8 +41,8 @@ def test_build_rejects_bad_arguments(lib, case):
         b = None
     elif case == "n1":
         n = 1
-    elif case == "leaf3":
-        leaf = 3
+    elif case == "leaf2":
+        leaf = 2
     elif case == "tol_neg":
         tol = -1e-9
     else:
@@ -70,7 +70,7 @@ def test_batch_rejects_bad_arguments(lib):
     assert lib.gm_build_batch(0, probs, None, 0.0, outs) == gm.GM_EINVAL
     assert lib.gm_build_batch(2, None, None, 0.0, outs) == gm.GM_EINVAL
     assert lib.gm_build_batch(2, probs, None, -1.0, outs) == gm.GM_EINVAL
-    probs[1].leaf = 3
+    probs[1].leaf = 2
     assert lib.gm_build_batch(2, probs, None, 0.0, outs) == gm.GM_EINVAL
     probs[1].leaf = 4
     o = gm.Opts()
@@ -128,7 +128,7 @@ def test_load_build_rejects_bad_arguments(lib):
     assert call(nodes=np.array([3, 64], dtype=np.int32)) == gm.GM_EINVAL  # outside the 8 x 8 grid
     assert call(nodes=np.array([-1], dtype=np.int32)) == gm.GM_EINVAL
     assert call(nodes=np.array([5, 9, 5], dtype=np.int32)) == gm.GM_EINVAL  # repeated
-    assert call(leaf=3) == gm.GM_EINVAL
+    assert call(leaf=2) == gm.GM_EINVAL
     o = gm.Opts()
     lib.gm_opts_default(ctypes.byref(o))
     o.precision = gm.PREC_MIXED
@@ -154,7 +154,7 @@ def test_network_build_rejects_bad_arguments(lib):
                                 nn, leaf, tol, nodes.ctypes.data if nodes is not None else None, count,
                                 ctypes.byref(h))
     assert call(a=None) == gm.GM_EINVAL
-    assert call(leaf=3) == gm.GM_EINVAL
+    assert call(leaf=2) == gm.GM_EINVAL
     assert call(count=-1) == gm.GM_EINVAL
     assert call(count=2) == gm.GM_EINVAL  # loads without a list
     assert call(nodes=np.array([1, 1], dtype=np.int32), count=2) == gm.GM_EINVAL

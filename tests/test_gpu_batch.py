@@ -145,3 +145,42 @@ def test_batch_fallback_is_per_problem(gm):
         assert info["precision"] == (gm.PREC_FP64 if helm else gm.PREC_MIXED)
         assert same_as_single(op, gm.build(*p, precision=gm.PREC_MIXED, split_digits=6))
         assert rel_mat(op.dtn(), nd_dense.build(*p).T) < (1e-10 if helm else 1e-8)
+
+
+def test_recorded_graph_replays_the_batch(gm):
+    """With graph set, the first batched build of a plan runs as usual and records its
+    launches; the next builds of that plan replay the graph on new coefficients.  Every
+    replayed operator equals its eager build bit for bit (same kernels, same order), for
+    two different coefficient sets, and the automatic fallback still applies per problem."""
+    import torch
+    sizes = (128, 192, 256, 128)
+    def problems(seed):
+        out = []
+        for i, n in enumerate(sizes):
+            f = inputs.convection_fields(n, seeds=(seed + 3 * i, seed + 3 * i + 1, seed + 3 * i + 2)) if i != 1 \
+                else inputs.helmholtz_fields(n, inputs.nudged_wavenumber(n, 16) * (1 + 0.01 * (seed % 7)))
+            out.append(tuple(torch.from_numpy(x).cuda() for x in f) + (n, 16))
+        return out
+    first = gm.build_batch(problems(300), precision=gm.PREC_MIXED, graph=True)  # records
+    for seed in (400, 500):
+        probs = problems(seed)
+        rep = gm.build_batch(probs, precision=gm.PREC_MIXED, graph=True)  # replays
+        eager = gm.build_batch(probs, precision=gm.PREC_MIXED)
+        for a, b in zip(rep, eager):
+            assert a.info()["pivot_fallback"] == b.info()["pivot_fallback"]
+            assert np.array_equal(a.dtn(), b.dtn())
+    del first
+
+
+def test_autotuned_build_matches_the_oracle(gm):
+    """The autotuner times a few launch shapes on the first build of a plan and keeps the
+    fastest; whatever it picks, the result stays within the mixed-precision bound."""
+    n, leaf = 256, 16
+    b, c, d = inputs.convection_fields(n, seeds=(71, 72, 73))
+    op = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED, autotune=True)
+    op2 = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED, autotune=True, graph=True)  # tuned, recorded
+    op3 = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED, autotune=True, graph=True)  # tuned, replayed
+    To = nd_dense.build(b, c, d, n, leaf).T
+    for o in (op, op2, op3):
+        assert rel_mat(o.dtn(), To) < 1e-8
+    assert np.array_equal(op2.dtn(), op3.dtn())

@@ -156,7 +156,10 @@ def test_errors_are_reported(gm):
     n = 8
     b, c, d = inputs.laplace_fields(n)
     with pytest.raises(gm.GmError) as e:
-        gm.build(b, c, d, n, 3)
+        gm.build(b, c, d, n, 2)
+    assert e.value.code == gm.GM_EINVAL
+    with pytest.raises(gm.GmError) as e:  # n = 7, leaf 3: the tree would hold 1-wide boxes (no ring)
+        gm.build(*inputs.laplace_fields(7), 7, 3)
     assert e.value.code == gm.GM_EINVAL
     with pytest.raises(gm.GmError) as e:  # a 28-node root ring is one HBS node: nothing to compress
         gm.build(b, c, d, n, 4, tol=1e-9)
@@ -193,3 +196,33 @@ def test_info_reports_the_build(gm):
     assert 0 < info["min_pivot_ratio"] <= 1.5
     assert info["bad_stage"] == -1
     assert info["launches"] > 0
+
+
+@pytest.mark.parametrize("n,leaf", [(12, 3), (48, 3), (96, 32), (128, 64), (100, 64), (40, 200)])
+def test_every_leaf_size_of_the_boundary(gm, n, leaf):
+    """3 <= leaf <= n (and beyond): against O1, the plain definition.  Leaves wider than
+    17 are eliminated in nested-dissection order inside the leaf; the reported levels are
+    the requested tree's."""
+    b, c, d = inputs.convection_fields(n, seeds=(n, n + 1, n + 2))
+    op = gm.build(b, c, d, n, leaf)
+    assert op.info()["levels"] == nd_dense.num_levels(n, leaf)
+    To = o1.dtn_matrix(b, c, d, n)
+    assert rel_mat(op.dtn(), To) < TOL
+    if leaf >= 32:
+        mx = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED)
+        assert rel_mat(mx.dtn(), To) < 1e-8
+
+
+def test_wide_leaf_schur_complement_is_the_leaf_elimination(gm):
+    """A 64 x 64 leaf (the paper's default N_leaf = 4096 points): its Schur complement,
+    kept by the build, against the oracle's dense elimination of the leaf's interior
+    (eq. def_schur_nd)."""
+    n, leaf = 128, 64
+    b, c, d = inputs.convection_fields(n, seeds=(61, 62, 63))
+    op = gm.build(b, c, d, n, leaf, keep_levels=True)
+    prob = nd_dense.Problem(b, c, d, n)
+    box = nd_dense.quad_tree(n, leaf)[-1][3]  # the north-east leaf
+    assert (box.a, box.b) == (64, 64)
+    S = op.schur(box.x0, box.y0, box.a, box.b)
+    So = nd_dense.leaf_schur(prob, box)
+    assert rel_mat(S, So) < TOL

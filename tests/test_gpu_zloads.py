@@ -5,9 +5,7 @@ the loads; the combined solve with host and device buffers; and at 512 x 512 wit
 loads (the paper's largest N_body) the conservation and maximum-principle properties of
 a Laplace problem, which hold at any size.  Networks: T and F against O1's network
 solve, unit conductivities against the Laplace build, and the paper's body-load workload
-(Random Laplacian I, 512 x 512, 1000 loads) against symmetry, T 1 = 0 and conservation.
-(Marked late: these paths are newer than the rest of the
-suite, so the other tests run first.)"""
+(Random Laplacian I, 512 x 512, 1000 loads) against symmetry, T 1 = 0 and conservation."""
 import numpy as np
 import pytest
 
@@ -15,7 +13,7 @@ import paper_1302_5995_gb300 as gm
 from oracle import o1
 from paper_1302_5995_gb300 import inputs
 
-pytestmark = [pytest.mark.gpu, pytest.mark.late]
+pytestmark = pytest.mark.gpu
 
 
 def rel(a, b):
@@ -137,3 +135,34 @@ def test_network_keeps_every_level_schur_complement():
         S = op.schur(bx.x0, bx.y0, bx.a, bx.b)
         ref = nd_dense.direct_schur(prob, bx)
         assert rel(S, ref) < 1e-11, bx
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-9])
+def test_low_rank_load_operator_against_o1(tol):
+    """Section 6.3's low-rank form of F: L R from a Gaussian sample of F, truncated at tol.
+    It stays within 100 tol of O1's F, its rank is far below the number of loads and
+    falls as tol grows, and the load solve through L (R f) matches O1 within the same
+    bound; the handle's footprint shrinks accordingly."""
+    n, leaf, count = 96, 12, 300
+    b, c, d = inputs.convection_fields(n, seeds=(97, 98, 99))
+    body = placed_loads(n, count, 12)
+    op = gm.build_loads(b, c, d, n, leaf, body)
+    dense_bytes = op.info()["resident_bytes"]
+    assert op.info()["load_rank"] == -1
+    Fo = o1.load_matrix(b, c, d, n, body)
+    k = op.compress_loads(tol)
+    assert 0 < k < body.size // 2
+    assert op.info()["load_rank"] == k
+    assert op.info()["resident_bytes"] == (16 * n * n + (4 * n + body.size) * k) * 8 < dense_bytes
+    assert rel(op.load_operator(), Fo) < 100 * tol
+    G = inputs.gaussian_vectors(n, 4, 13)
+    Fl = inputs.body_load_vectors(body.size, 4, 14)
+    ref = o1.apply_loads(b, c, d, n, G, body, Fl)
+    got = op.solve_loads(np.ascontiguousarray(G.T), np.ascontiguousarray(Fl.T)).T
+    assert rel(got, ref) < 100 * tol
+    with pytest.raises(gm.GmError) as e:  # already compressed
+        op.compress_loads(tol)
+    assert e.value.code == gm.GM_EUNSUPPORTED
+    if tol == 1e-9:
+        k6 = gm.build_loads(b, c, d, n, leaf, body).compress_loads(1e-6)
+        assert k6 < k

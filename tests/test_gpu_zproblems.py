@@ -4,8 +4,7 @@ paper's two error measures e1 (random unit boundary vector) and e2 (smooth one) 
 O1's full solve.  Each tolerance is 100 times the spread between the oracle's own nested
 dissection (O2) and O1 on the same problem, at least 1e-9: Helmholtz III sits 1e-5 from
 resonance and Diffusion-Convection IV (a gradient convection field) is exponentially
-ill-conditioned, so two exact methods already differ there.  (Marked late: these paths are newer than the rest of the
-suite, so the other tests run first.)"""
+ill-conditioned, so two exact methods already differ there."""
 import numpy as np
 import pytest
 
@@ -13,7 +12,7 @@ import paper_1302_5995_gb300 as gm
 from oracle import nd_dense, o1
 from paper_1302_5995_gb300 import inputs
 
-pytestmark = [pytest.mark.gpu, pytest.mark.late]
+pytestmark = pytest.mark.gpu
 
 PROBLEMS = list(inputs.PAPER_PROBLEMS) + ["random1", "random2"]
 

@@ -186,7 +186,9 @@ def test_plan_without_merges_and_bad_arguments(shim):
     assert P["rc"] == 0 and P["L"] == 0 and P["stages"] == [] and len(P["leaves"]) == 1
     assert P["roots"][0]["off"] == P["leaves"][0]["off"] == 0
     assert plan(shim, 1, 4)["rc"] == GM_EINVAL
-    assert plan(shim, 12, 3)["rc"] == GM_EINVAL
+    assert plan(shim, 12, 2)["rc"] == GM_EINVAL
+    assert plan(shim, 7, 3)["rc"] == GM_EINVAL  # 7 -> 3, 4 -> 1, 2, 2, 2: a box without a ring
+    assert plan(shim, 12, 3)["rc"] == 0 and plan(shim, 12, 3)["L"] == 2
 
 
 def test_batch_plan_aligns_stages_from_the_root(shim):

@@ -4,8 +4,8 @@ host whose device memory belongs to another runtime's pool).  Its result must eq
 allocating gm_solve on the same operator, call after call, whichever of g and dudn live
 on the host and whichever precision the operator was built in.
 
-Collected after the other established tests on purpose (file name; only the tests
-marked late follow it): if it fails, a stop-at-first-failure run has already run them.
+Collected after every other test on purpose (its file name sorts last): if it fails, a
+stop-at-first-failure run has already run all the others.
 """
 import ctypes
 
