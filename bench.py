@@ -594,6 +594,66 @@ def run_problemset(args):
           flush=True)
 
 
+# Table error of the paper (e1, e2 of its HBS solution operator at local tolerance 1e-7,
+# n = 1024, against GMRES): context for the line below, not a target.
+PAPER_TABLE_ERROR = {"laplace": (6.3e-7, 3.6e-7), "diffconv1": (1.5e-6, 1.3e-6), "diffconv2": (8.7e-6, 8.2e-6),
+                     "diffconv3": (5.6e-7, 3.4e-7), "diffconv4": (4.1e-8, 4.1e-8), "helmholtz1": (1.4e-4, 4.8e-7),
+                     "helmholtz2": (1.1e-6, 5.1e-6), "helmholtz3": (1.2e-5, 5.7e-4), "helmholtz4": (8.2e-4, 1.2e-3),
+                     "random1": (1.8e-7, 1.2e-7), "random2": (1.4e-5, 8.1e-6)}
+
+
+def run_errors(args):
+    """The paper's error experiment (Section 6.1, Table error) at its size: the eleven
+    problems at n = 1024, leaf 16, built on the GPU with the HBS path at tol 1e-7 (the
+    paper's local tolerance; accelerated merges for shared edges >= 128 and the HBS root;
+    the networks with an HBS root), and e1 / e2 -- the relative l2 errors of T r for a
+    random unit r and for a smooth r -- against the oracle O2 (the paper used GMRES);
+    the dense FP64 GPU build's e1 / e2 beside them, M(n) of the HBS operator, and the
+    paper's own e1 / e2 as context.  One JSON line (not the headline)."""
+    import numpy as np
+    import torch
+    from paper_1302_5995_gb300 import build_ext, inputs
+    build_ext.build()
+    import paper_1302_5995_gb300 as gm
+    from oracle import nd_dense
+
+    n, leaf, tol = args.n, 16, 1e-7
+    R = inputs.error_vectors(n, 17)
+    Rd = torch.from_numpy(np.ascontiguousarray(R.T)).cuda()
+    res = {}
+    for name in list(inputs.PAPER_PROBLEMS) + ["random1", "random2"]:
+        row = {"paper_e1_e2": PAPER_TABLE_ERROR[name]}
+        t0 = time.perf_counter()
+        if name.startswith("random"):
+            sx, sy = (inputs.random_laplacian_1 if name == "random1" else inputs.random_laplacian_2)(n)
+            # the oracle's network build (one load at a corner node rides along; T is unchanged)
+            To = nd_dense.build_loads(nd_dense.Problem.network(sx, sy, n), leaf, [0])[0]
+            dx, dy = torch.from_numpy(sx).cuda(), torch.from_numpy(sy).cuda()
+            hb = gm.build_network(dx, dy, n, leaf, tol=tol, hbs_leaf=64)
+            dn = gm.build_network(dx, dy, n, leaf)
+        else:
+            f = inputs.paper_problem(name, n)
+            To = nd_dense.build(*f, n, leaf).T
+            b, c, d = (torch.from_numpy(x).cuda() for x in f)
+            hb = gm.build(b, c, d, n, leaf, tol=tol, hbs_leaf=64, hbs_min_edge=128)
+            dn = gm.build(b, c, d, n, leaf)
+        row["oracle_s"] = time.perf_counter() - t0
+        if To is not None:
+            Vo = To @ R
+            for tag, op in (("hbs", hb), ("dense_fp64", dn)):
+                V = op.solve(Rd).cpu().numpy().T
+                e = np.linalg.norm(V - Vo, axis=0) / np.linalg.norm(Vo, axis=0)
+                row[f"{tag}_e1"], row[f"{tag}_e2"] = float(e[0]), float(e[1])
+        inf = hb.info()
+        row["hbs_M_MB"] = inf["hbs_operator_bytes"] / 2**20
+        row["hbs_M_over_n"] = inf["hbs_operator_bytes"] / 2**20 / n
+        row["hbs_max_rank"] = inf["hbs_max_rank"]
+        res[name] = row
+    print(json.dumps({"workload": "errors", "n": n, "leaf": leaf, "tol": tol,
+                      "reference": "oracle O2 (dense FP64 nested dissection); the paper's reference was GMRES",
+                      "data": "synthetic (the paper's analytic fields; seeded networks)", "results": res}), flush=True)
+
+
 def run_bodyloads(args):
     """Body loads (Section 6.3) on the paper's body-load problem, Random Laplacian I at
     512 x 512, leaf 16, with N_body = 10, 100, 1000 loads in a localized window: FP64 build
@@ -841,11 +901,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gm", "reference"], default="gm")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
-    ap.add_argument("--workload", choices=["build", "cfg3", "batch", "serving", "problemset", "bodyloads"],
+    ap.add_argument("--workload", choices=["build", "cfg3", "batch", "serving", "problemset", "errors", "bodyloads"],
                     default="build",
                     help="build: the headline build+solve step; cfg3, batch, serving, problemset, bodyloads: "
                          "other workloads (not the headline)")
     ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--n", type=int, default=1024, help="grid of the errors workload")
     ap.add_argument("--graph", type=int, default=0, help="record each plan's build into a CUDA graph and replay it")
     ap.add_argument("--autotune", type=int, default=0, help="time a few launch shapes on the first build of a plan")
     args = ap.parse_args()
@@ -854,6 +915,9 @@ def main():
         return
     if args.workload == "cfg3":
         run_cfg3(args)
+        return
+    if args.workload == "errors":
+        run_errors(args)
         return
     if args.workload == "batch":
         run_batch(args)

@@ -1071,7 +1071,10 @@ void record_graph(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &
     int rc = run_build(o, tol, dp, E->cb, E->cc, E->cd, Hd, code, growth, tu, &g);
     tl_bump = nullptr;
     E->stat = tl_recorded_status;
-    if (rc == GM_OK && g && E->stat && cudaGraphInstantiate(&E->exec, g, 0) == cudaSuccess) {
+    // per-node priorities: the look-ahead's chain (high) and the rest of each update (low)
+    // keep the priorities of the streams they were recorded from
+    if (rc == GM_OK && g && E->stat &&
+        cudaGraphInstantiateWithFlags(&E->exec, g, cudaGraphInstantiateFlagUseNodePriority) == cudaSuccess) {
         auto off = [&](const void *p) { return p ? (size_t)((const char *)p - E->mem) : (size_t)0; };
         for (size_t i = 0; i < Hd.size(); ++i) {
             gm_handle *h = Hd[i];

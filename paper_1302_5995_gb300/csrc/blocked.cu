@@ -162,7 +162,8 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
             *(float4 *)&Mc[row * FML + cg * FCG + j] = make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
         __syncthreads();
         if (warp == 0) {
-            float pv[2][8], tc[2][8];
+            float pv[2][8], tc[2][8], pivs[8];
+            int pidx[8];
             const int pc = (t0 >> 5) * FCG + (t0 & 31);  // the panel's first column
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
@@ -186,13 +187,10 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
                 for (int v = u; v < 8; ++v) prv[v] = __shfl_sync(FULL, hp ? pv[1][v] : pv[0][v], src);
 #pragma unroll
                 for (int v = 0; v <= u; ++v) prt[v] = __shfl_sync(FULL, hp ? tc[1][v] : tc[0][v], src);
-                const float piv = prv[u], ip = __frcp_rn(piv);
-                if (lane == 0) {
-                    s_pm[t0 + u] = fabsf(piv);
-                    if (t0 + u < nbe) pmag[(size_t)blockIdx.x * 64 + t0 + u] = fabsf(piv);
-                    Ps[u] = p;
-                    s_step[p] = t0 + u;
-                }
+                // the fast reciprocal: X0 only needs FP32 accuracy (the R step refines it)
+                const float piv = prv[u], ip = __fdividef(1.0f, piv);
+                pivs[u] = piv;
+                pidx[u] = p;
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
                     const bool isp = r ? mine1 : mine0;
@@ -208,10 +206,25 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
                 TCs[lane][v] = tc[0][v];
                 TCs[lane + 32][v] = tc[1][v];
             }
+            if (lane < 8) {  // the panel's pivots (lane u: pivot u; compile-time indices)
+                float pm = 0.f;
+                int pi = 0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (lane == u) {
+                        pm = fabsf(pivs[u]);
+                        pi = pidx[u];
+                    }
+                s_pm[t0 + lane] = pm;
+                if (t0 + lane < nbe) pmag[(size_t)blockIdx.x * 64 + t0 + lane] = pm;
+                Ps[lane] = pi;
+                s_step[pi] = t0 + lane;
+            }
+            __syncwarp();
             // the pivot rows (as they were at the start of the panel) for the update
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int pr = __shfl_sync(FULL, lane == 0 ? Ps[u] : 0, 0);
+                const int pr = pidx[u];
                 const int q = (lane >> 3) * FCG + (lane & 7) * 4;
                 *(float4 *)&PRs[u * FML + q] = *(const float4 *)&Mc[pr * FML + q];
             }

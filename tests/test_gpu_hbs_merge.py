@@ -73,14 +73,16 @@ def test_each_accelerated_merge_matches_the_oracle(gm, fields, n, leaf, m, edge)
 
 
 def test_accelerated_merges_cut_the_update_work(gm):
-    """The merge-update family's algorithmic flops: the factored update of Step 2 costs
-    2 rp^2 k per merge instead of 2 rp^2 s' (eq. matmult)."""
-    n, leaf, m, tol = 256, 16, 32, 1e-9
+    """The merge-update family's algorithmic flops: Step 2's factored update costs
+    2 rp^2 k per merge instead of 2 rp^2 s' (eq. matmult), plus the sampling and QR that
+    find the low-rank factors; with the shared edges >= 128 of a 512 x 512 build the whole
+    family's work is well below the dense update's (about half, measured)."""
+    n, leaf, m, tol = 512, 16, 64, 1e-9
     b, c, d = inputs.convection_fields(n)
     dense = gm.build(b, c, d, n, leaf, timing=True)
-    acc = gm.build(b, c, d, n, leaf, tol=tol, hbs_leaf=m, hbs_min_edge=64, timing=True)
+    acc = gm.build(b, c, d, n, leaf, tol=tol, hbs_leaf=m, hbs_min_edge=128, timing=True)
     fd, fa = dense.info()["kernel_flops"], acc.info()["kernel_flops"]
-    assert fa["merge_update"] < 0.6 * fd["merge_update"]
+    assert fa["merge_update"] < 0.6 * fd["merge_update"], (fa["merge_update"], fd["merge_update"])
     G = inputs.gaussian_vectors(n, 8, 2)
     To = nd_dense.build(b, c, d, n, leaf).T
     V = acc.solve(np.ascontiguousarray(G.T)).reshape(8, 4 * n).T
