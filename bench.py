@@ -648,6 +648,7 @@ def run_errors(args):
         row["hbs_M_MB"] = inf["hbs_operator_bytes"] / 2**20
         row["hbs_M_over_n"] = inf["hbs_operator_bytes"] / 2**20 / n
         row["hbs_max_rank"] = inf["hbs_max_rank"]
+        row["hbs_fallbacks"] = inf["hbs_fallbacks"]
         res[name] = row
     print(json.dumps({"workload": "errors", "n": n, "leaf": leaf, "tol": tol,
                       "reference": "oracle O2 (dense FP64 nested dissection); the paper's reference was GMRES",

@@ -158,7 +158,11 @@ typedef struct gm_info_t {
                                          (D, U, V, B at the node ranks; the paper's M(n)) */
     int load_rank;                    /* body loads: rank of F after
                                          gm_compress_load_operator (-1: F dense)         */
-    int pad3;
+    int hbs_fallbacks;                /* tol > 0: merges and roots left to the dense
+                                         elimination because an HBS form was not possible
+                                         (a rank above the cap) or Algorithm 1's inverse
+                                         failed its residual check (a relative residual
+                                         above 1e-3 on random vectors)                    */
 } gm_info_t;
 
 /* Fill *opts with defaults (FP64, no kept levels, default stream). */

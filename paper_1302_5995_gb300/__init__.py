@@ -50,7 +50,7 @@ class Info(ctypes.Structure):
                 ("pivot_fallback", ctypes.c_int), ("refine_ratio", ctypes.c_double), ("hbs_levels", ctypes.c_int),
                 ("hbs_max_rank", ctypes.c_int), ("hbs_bytes", ctypes.c_longlong), ("resident_bytes", ctypes.c_longlong),
                 ("hbs_merges", ctypes.c_int), ("hbs_update_rank", ctypes.c_int), ("hbs_operator_bytes", ctypes.c_longlong),
-                ("load_rank", ctypes.c_int), ("pad3", ctypes.c_int)]
+                ("load_rank", ctypes.c_int), ("hbs_fallbacks", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):

@@ -182,17 +182,17 @@ struct DBuf {
 // after the build has synchronised): s1 carries the critical chain at the highest
 // priority, s2 the bulk of each update at the lowest.
 struct LookAhead {
-    cudaStream_t s1 = nullptr, s2 = nullptr;
-    cudaEvent_t a = nullptr, b = nullptr, c = nullptr;
+    cudaStream_t s1 = nullptr, s2 = nullptr, s3 = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr, c = nullptr, d = nullptr, e = nullptr, f[2] = {nullptr, nullptr};
     ~LookAhead() {
-        // destroyed before the scratch buffers declared ahead of it: nothing on the
-        // look-ahead streams may still read them when they are released (early returns)
         if (s1) cudaStreamSynchronize(s1);
         if (s2) cudaStreamSynchronize(s2);
-        for (cudaEvent_t e : {a, b, c})
-            if (e) cudaEventDestroy(e);
+        if (s3) cudaStreamSynchronize(s3);
+        for (cudaEvent_t x : {a, b, c, d, e, f[0], f[1]})
+            if (x) cudaEventDestroy(x);
         if (s1) cudaStreamDestroy(s1);
         if (s2) cudaStreamDestroy(s2);
+        if (s3) cudaStreamDestroy(s3);
     }
     // background: both streams at the lowest priority (the build yields to other work)
     bool create(bool background) {
@@ -202,7 +202,12 @@ struct LookAhead {
             cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, least) != cudaSuccess ||
             cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&c, cudaEventDisableTiming) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&s3, cudaStreamNonBlocking, background ? least : greatest) != cudaSuccess ||
+            cudaEventCreateWithFlags(&d, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&f[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&f[1], cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
@@ -482,7 +487,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
         h->kept_df32 = mixed;
     }
     int rc;
-    int hbs_merges = 0, hbs_rank = 0, hbs_lr_rank = 0;
+    int hbs_merges = 0, hbs_rank = 0, hbs_lr_rank = 0, hbs_fallbacks = 0;
     const size_t np = H.size();
     // declared ahead of every buffer: the capture ends before the look-ahead streams go
     LookAhead la;
@@ -573,6 +578,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             if (cg.active) return;
             if (la.s1) cudaStreamSynchronize(la.s1);
             if (la.s2) cudaStreamSynchronize(la.s2);
+            if (la.s3) cudaStreamSynchronize(la.s3);
         }
     } idle{la, cg};
     if (!mixed) {
@@ -584,9 +590,10 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             return rc;
         if (blockpiv) {
             const size_t sq = (size_t)max_nm * 64;
-            if ((rc = bxd.alloc((size_t)split * sq * 64 * 2, s)) || (rc = bad.alloc((size_t)split * sq * 64 * 2, s)) ||
-                (rc = bxe.alloc(sq * sizeof(int), s)) || (rc = bae.alloc(sq * sizeof(int), s)) ||
-                (rc = bpmag.alloc(sq * sizeof(float), s)) ||
+            // two factor output sets (the early-factor schedule alternates between them)
+            if ((rc = bxd.alloc(2 * (size_t)split * sq * 64 * 2, s)) ||
+                (rc = bad.alloc(2 * (size_t)split * sq * 64 * 2, s)) || (rc = bxe.alloc(2 * sq * sizeof(int), s)) ||
+                (rc = bae.alloc(2 * sq * sizeof(int), s)) || (rc = bpmag.alloc(2 * sq * sizeof(float), s)) ||
                 (rc = bfdig.alloc(2 * (size_t)split * max_rows * 64 * 2, s)) ||
                 (rc = bfex.alloc(2 * (size_t)max_rows * sizeof(int), s)) ||
                 (rc = brdig.alloc(2 * (size_t)split * max_cols * 64 * 2, s)) ||
@@ -597,6 +604,11 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             bscr.x_ex = bxe.as<int>();
             bscr.a11_ex = bae.as<int>();
             bscr.pmag = bpmag.as<float>();
+            bscr.x_dig2 = bscr.x_dig + (size_t)split * sq * 64;
+            bscr.a11_dig2 = bscr.a11_dig + (size_t)split * sq * 64;
+            bscr.x_ex2 = bscr.x_ex + sq;
+            bscr.a11_ex2 = bscr.a11_ex + sq;
+            bscr.pmag2 = bscr.pmag + sq;
             for (int q = 0; q < 2; ++q) {
                 bscr.fdig[q] = bfdig.as<__nv_bfloat16>() + (size_t)q * split * max_rows * 64;
                 bscr.fex[q] = bfex.as<int>() + (size_t)q * max_rows;
@@ -606,6 +618,12 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             if (!la.create(o.background != 0)) return GM_ECUDA;
             bscr.wait_limit = wait_limit;
             bscr.rtile32_max = tu.rtile32_max;
+            bscr.early = tu.early != 0;
+            bscr.s3 = la.s3;
+            bscr.ev_rr = la.d;
+            bscr.ev_next = la.e;
+            bscr.ev_rest2[0] = la.f[0];
+            bscr.ev_rest2[1] = la.f[1];
             bscr.s1 = la.s1;
             bscr.s2 = la.s2;
             bscr.ev_r = la.a;
@@ -679,7 +697,8 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
                         hbs_idx.push_back(i);
                         continue;
                     }
-                    if (rc != GM_EUNSUPPORTED) return rc;
+                    if (rc != GM_EUNSUPPORTED && rc != HBS_UNSTABLE) return rc;
+                    ++hbs_fallbacks;
                 }
                 dense.push_back(ds.h_sys[i]);
             }
@@ -744,6 +763,9 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
     }
 
     DBuf rws;
+    // roots eliminated densely: all of them, or with tol > 0 those whose HBS inverse
+    // failed its residual check
+    std::vector<int> dense_roots;
     if (tol > 0.0) {
         // HBS roots (Sections 4-5): compress every S_root and invert it by Algorithm 1;
         // the solve applies Algorithm 2 (no dense T)
@@ -760,22 +782,37 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
                 S64 = conv.as<double>();
             }
             h->hbs = new HbsRoot();
-            if ((rc = hbs_build_root(S64, r.r, r.n, o.hbs_leaf, tol, db + r.coef, dc + r.coef, dd + r.coef, s,
-                                     *h->hbs)))
-                return rc;
+            rc = hbs_build_root(S64, r.r, r.n, o.hbs_leaf, tol, db + r.coef, dc + r.coef, dd + r.coef, s, *h->hbs);
+            if (rc == HBS_UNSTABLE) {  // Algorithm 1 unstable here: a dense root instead
+                hbs_free(*h->hbs);
+                delete h->hbs;
+                h->hbs = nullptr;
+                dense_roots.push_back((int)i);
+                ++hbs_fallbacks;
+                continue;
+            }
+            if (rc) return rc;
             peak = std::max(peak, (int64_t)(arena_bytes + h->hbs->pool_doubles * 8));
         }
         kt.end(s);
         kt.flops[GM_K_ROOT] += hbs_flops_take();
     } else {
+        for (size_t i = 0; i < P.roots.size(); ++i) dense_roots.push_back((int)i);
+    }
+    if (!dense_roots.empty()) {
     // roots (Section 3.3 step 4): X = S_root^{-1} B for every problem in one sweep
     if ((rc = rws.alloc(dp.root_ws * 8, s))) return rc;
     peak = std::max(peak, (int64_t)(arena_bytes + dp.root_ws * 8));
-    int max_r = 0, sum_rr = 0, sum_rc = 0;
-    for (size_t i = 0; i < P.roots.size(); ++i) {
+    int max_r = 0, max_c = 0, sum_rr = 0, sum_rc = 0;
+    std::vector<SysDesc> rsys;
+    for (int i : dense_roots) {
         const RootDesc &r = P.roots[i];
-        const SysDesc &sy = dp.h_root_sys[i];
+        SysDesc sy = dp.h_root_sys[i];
+        sy.roff = sum_rr;
+        sy.coff = sum_rc;
+        rsys.push_back(sy);
         max_r = std::max(max_r, r.r);
+        max_c = std::max(max_c, sy.ncol);
         sum_rr += sy.m;
         sum_rc += sy.ncol;
         if (!mixed)
@@ -785,10 +822,17 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             CK(mx_root_assemble(Adf + r.off, r.r, r.n, rws.as<float2>() + sy.off, db + r.coef, dc + r.coef,
                                 dd + r.coef, s, kt));
     }
-    CK(sweep(dp.d_root_sys, dp.h_root_sys, max_r, dp.max_root_ncol, rws.p, sum_rr, sum_rc,
-             (int)dp.stages.size() + 1));
+    if (dense_roots.size() == P.roots.size()) {
+        CK(sweep(dp.d_root_sys, dp.h_root_sys, max_r, dp.max_root_ncol, rws.p, sum_rr, sum_rc,
+                 (int)dp.stages.size() + 1));
+    } else {  // a subset: descriptors with their own row and column offsets
+        DBuf dsub;
+        if ((rc = dsub.alloc(rsys.size() * sizeof(SysDesc), s))) return rc;
+        CK(cudaMemcpyAsync(dsub.p, rsys.data(), rsys.size() * sizeof(SysDesc), cudaMemcpyHostToDevice, s));
+        CK(sweep(dsub.as<SysDesc>(), rsys, max_r, max_c, rws.p, sum_rr, sum_rc, (int)dp.stages.size() + 1));
+    }
     stamp();
-    for (size_t i = 0; i < P.roots.size(); ++i) {
+    for (int i : dense_roots) {
         const RootDesc &r = P.roots[i];
         gm_handle *h = H[r.problem];
         const int nb4 = 4 * r.n;
@@ -861,6 +905,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
         hi.hbs_merges = hbs_merges;
         hi.hbs_max_rank = hbs_rank;
         hi.hbs_update_rank = hbs_lr_rank;
+        hi.hbs_fallbacks = hbs_fallbacks;
         if (h->hbs) {
             hi.hbs_levels = h->hbs->L;
             hi.hbs_max_rank = std::max(hbs_rank, h->hbs->max_rank);
@@ -975,6 +1020,9 @@ int autotune(const gm_opts &o, const std::shared_ptr<DevPlan> &dp, const std::ve
             if (rc != GM_OK) return 1e300;
             bt = std::min(bt, ms);
         }
+        if (debug_on())
+            fprintf(stderr, "gm: autotune rtile32_max %d early %d tc_min_k %d: %.3f ms\n", t.rtile32_max, t.early,
+                    t.tc_min_k, bt);
         return bt;
     };
     best = Tune();
@@ -983,6 +1031,15 @@ int autotune(const gm_opts &o, const std::shared_ptr<DevPlan> &dp, const std::ve
     for (int r : {0, 1 << 30}) {
         Tune t = best;
         t.rtile32_max = r;
+        const double x = time_of(t);
+        if (x < tb) {
+            tb = x;
+            best = t;
+        }
+    }
+    if (o.precision == GM_PREC_MIXED) {
+        Tune t = best;
+        t.early = !best.early;
         const double x = time_of(t);
         if (x < tb) {
             tb = x;
@@ -1033,7 +1090,8 @@ std::shared_ptr<GraphEntry> find_graph(const TuneKey &k, const Tune &t) {
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_graph_mu);
     for (auto &e : g_graphs)
-        if (e->key == k && e->tune.rtile32_max == t.rtile32_max && e->tune.tc_min_k == t.tc_min_k) {
+        if (e->key == k && e->tune.rtile32_max == t.rtile32_max && e->tune.tc_min_k == t.tc_min_k &&
+            e->tune.early == t.early) {
             e->last_use = ++g_graph_tick;
             return e;
         }

@@ -362,7 +362,8 @@ __device__ __forceinline__ void gemm64_full(const __nv_bfloat16 *Ak, const int *
             }
 }
 
-// Blocks [0, cb): TW = 32 NT columns right of the pivot block each (NT = 1 when the grid
+// Blocks [0, cb): column tiles ct0 .. ct0 + cb - 1 of TW = 32 NT columns right of the pivot
+// block (a launch may take any run of them; NT = 1 when the grid
 // is small, so twice as many SMs share the step):
 //   R0 = X0 A12,  E = A12 - A11 R0,  R = R0 + X0 E  (one refinement step),
 // R written into the pivot rows and cut into column digit planes for the update.
@@ -370,7 +371,7 @@ __device__ __forceinline__ void gemm64_full(const __nv_bfloat16 *Ak, const int *
 // with the growth check against the block pivots.
 template <int S, int NT>
 __global__ void __launch_bounds__(TILE_THREADS)
-k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, int cb,
+k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, int cb, int ct0,
              const __nv_bfloat16 *__restrict__ x_dig, const __nv_bfloat16 *__restrict__ a11_dig, int64_t plane,
              const int *__restrict__ x_ex, const int *__restrict__ a11_ex, __nv_bfloat16 *__restrict__ fdig,
              int64_t fplane, int *__restrict__ fex, __nv_bfloat16 *__restrict__ rdig, int64_t cplane,
@@ -424,7 +425,7 @@ k_blk_rfused(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
         return;
     }
     constexpr int TW = 32 * NT;
-    const int j0 = k + nbe + blockIdx.x * TW;
+    const int j0 = k + nbe + (ct0 + (int)blockIdx.x) * TW;
     if (j0 >= Sy.ncol) return;
     constexpr int SX = S < 4 ? S : 4;
     __nv_bfloat16 *Xk = (__nv_bfloat16 *)smem_raw;  // [SX][64][KP64]: rows of X0
@@ -551,7 +552,12 @@ size_t blk_update_smem(int split) {
 //              block's row tile (rows k + 64 ..) for column tiles 1 .. : grid.x = nrt + (column
 //              tiles - 1), everything the next factor and R kernel read;
 //   UPD_REST : every other tile, grid (nrt, column tiles - 1).
-enum { UPD_ALL = 0, UPD_NEXT = 1, UPD_REST = 2 };
+//   (the early-factor schedule of blk_gj_sweep, below:)
+//   UPD_A11  : the next pivot block's diagonal tile only (band, 0): the next factor's input;
+//   UPD_D2   : the diagonal tile two blocks ahead (band + 1, 1), left out of UPD_REST2;
+//   UPD_NEXT2: UPD_NEXT without the tile UPD_A11 takes;
+//   UPD_REST2: UPD_REST without the tile UPD_D2 takes.
+enum { UPD_ALL = 0, UPD_NEXT = 1, UPD_REST = 2, UPD_A11 = 3, UPD_D2 = 4, UPD_NEXT2 = 5, UPD_REST2 = 6 };
 
 // W(i, j) -= (F R)(i, j) for a 64 x 64 tile of rows outside J: both digit tiles (K = 64)
 // and the tile of W arrive by cp.async, then four k-steps of split products without
@@ -572,14 +578,22 @@ k_blk_update(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, in
     const int nbe = min(NBK, m - k);
     int ti = blockIdx.x, tj = blockIdx.y;
     const int band = k / NBK + 1;  // row tile of the next pivot block
-    if (mode == UPD_NEXT) {
+    if (mode == UPD_NEXT || mode == UPD_NEXT2) {
         if (ti >= nrt) {
             tj = ti - nrt + 1;
             ti = band;
+        } else if (mode == UPD_NEXT2 && ti == band) {
+            return;  // the next pivot block: updated on the chain (UPD_A11)
         }
     } else if (mode == UPD_REST) {
         if (ti == band) return;
         ++tj;
+    } else if (mode == UPD_A11) {
+        ti = band;
+        tj = 0;
+    } else if (mode == UPD_D2) {
+        ti = band + 1;
+        tj = 1;
     }
     const int i0 = ti * 64, j0 = k + nbe + tj * 64;
     if (i0 >= m || j0 >= Sy.ncol) return;
@@ -684,10 +698,13 @@ k_blk_update_tc(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k,
     const int m = Sy.m;
     if (k >= m) return;
     const int nbe = min(NBK, m - k);
-    const int i0 = blockIdx.x * TC_ROWS, j0 = k + nbe + (blockIdx.y + (mode == UPD_REST ? 1 : 0)) * TC_COLS;
+    const bool rest = mode == UPD_REST || mode == UPD_REST2;
+    const int i0 = blockIdx.x * TC_ROWS, j0 = k + nbe + (blockIdx.y + (rest ? 1 : 0)) * TC_COLS;
     if (i0 >= m || j0 >= Sy.ncol) return;
     // rows this tile leaves alone: the pivot rows, and in UPD_REST the next pivot band
-    const int skip_lo = k, skip_hi = mode == UPD_REST ? min(m, k + 2 * NBK) : k + nbe;
+    const int skip_lo = k, skip_hi = rest ? min(m, k + 2 * NBK) : k + nbe;
+    // UPD_REST2, column tile 1: the diagonal tile two blocks ahead is UPD_D2's
+    const bool dtile = mode == UPD_REST2 && j0 == k + nbe + TC_COLS;
     if (i0 >= skip_lo && i0 + TC_ROWS <= skip_hi) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     float2 *W = ws + Sy.off;
@@ -735,7 +752,7 @@ k_blk_update_tc(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k,
     // this thread's row and 32 columns; their W values are read while the products run
     const int q = warp & 3, h = warp >> 2;
     const int row = 32 * q + lane, i = i0 + row;
-    const bool live = i < m && !(i >= skip_lo && i < skip_hi);
+    const bool live = i < m && !(i >= skip_lo && i < skip_hi) && !(dtile && i >= k + 2 * NBK && i < k + 3 * NBK);
     float2 w[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
@@ -846,6 +863,139 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
     if (la && ((e = cudaEventRecord(scr.ev_join, s)) != cudaSuccess || (e = cudaStreamWaitEvent(c, scr.ev_join, 0))))
         return e;
     const int nrt = (max_m + 63) / 64;
+    if (la && scr.early && scr.s3 && scr.x_dig2 && max_m >= 4 * NBK) {
+        // Early-factor schedule.  Step k (pivot block J_k, next blocks J_k+1, J_k+2; D_j the
+        // diagonal tile J_j x J_j):
+        //   chain c : R of the columns J_k+1 (+ every row's F digits) -> D_k+1 -= F R on those
+        //             columns (UPD_A11) -> the factor of J_k+1;
+        //   s3      : R of the other columns -> D_k+2 -= F R (UPD_D2) -> the rest of column
+        //             tile J_k+1 and of the row band J_k+1 (UPD_NEXT2);
+        //   s2      : everything else (UPD_REST2).
+        // Every tile is updated once per step.  Orderings (beyond stream order): R of step
+        // k waits for UPD_NEXT2 of step k - 1 (its pivot rows and D_k's last contribution)
+        // and for UPD_REST2 of step k - 2 (the digit set it overwrites, and the older
+        // contributions); UPD_D2 and UPD_NEXT2 of step k wait for UPD_REST2 of step k - 1
+        // (tiles it also writes); UPD_REST2 of step k waits for the R of step k.  The factor
+        // of block k + 2 overwrites the first factor set after R of step k has read it (s3
+        // is past that when the chain's R of step k + 1 starts).
+        cudaStream_t c3 = scr.s3;
+        auto fset = [&](int blk, __nv_bfloat16 *&xd, __nv_bfloat16 *&ad, int *&xe, int *&ae, float *&pm) {
+            const bool two = blk & 1;
+            xd = two ? scr.x_dig2 : scr.x_dig;
+            ad = two ? scr.a11_dig2 : scr.a11_dig;
+            xe = two ? scr.x_ex2 : scr.x_ex;
+            ae = two ? scr.a11_ex2 : scr.a11_ex;
+            pm = two ? scr.pmag2 : scr.pmag;
+        };
+        auto factor = [&](int kf, bool pdl) -> cudaError_t {
+            __nv_bfloat16 *xd, *ad;
+            int *xe, *ae;
+            float *pm;
+            fset(kf / NBK, xd, ad, xe, ae, pm);
+            double fl = 0;
+            for (const SysDesc &S : h_sys)
+                if (kf < S.m) fl += 2.0 * std::pow((double)std::min(NBK, S.m - kf), 3.0);
+            kt.begin(GM_K_PANEL, fl, c);
+            cudaError_t e2 = cudaSuccess;
+            BLK_SPLIT_DISPATCH(split, (e2 = launch_k(pdl, k_blk_factor<SS>, dim3(nsys), dim3(FAC_THREADS), fsm, c,
+                                                     d_sys, ws, kf, xd, ad, scr.inv_plane, xe, ae, pm, st, stage)));
+            kt.end(c);
+            return e2;
+        };
+        if ((e = factor(0, false)) != cudaSuccess) return e;
+        const int rb = (max_m + 127) / 128;
+        for (int k = 0; k < max_m; k += NBK) {
+            const int blk = k / NBK, par = blk & 1;
+            __nv_bfloat16 *xd, *ad;
+            int *xe, *ae;
+            float *pm;
+            fset(blk, xd, ad, xe, ae, pm);
+            double fl_r = 0, fl_upd = 0, fl_tile = 0;
+            for (const SysDesc &S : h_sys) {
+                if (k >= S.m) continue;
+                const double nbe = std::min(NBK, S.m - k), cols = S.ncol - k - nbe;
+                fl_r += 2.0 * nbe * nbe * cols;
+                fl_upd += 2.0 * nbe * ((S.m - k - nbe) * cols + (double)k * (S.ncol - S.m));
+                fl_tile += 2.0 * nbe * 64.0 * 64.0;
+            }
+            const int cols = max_ncol - k;
+            const int cb = (cols + 63) / 64;
+            // ---- chain: R of the columns J_k+1 (and every row's F digits)
+            if (blk > 0 && (e = cudaStreamWaitEvent(c, scr.ev_next, 0)) != cudaSuccess) return e;
+            if (blk > 1 && (e = cudaStreamWaitEvent(c, scr.ev_rest2[par], 0)) != cudaSuccess) return e;
+            kt.begin(GM_K_PIVROWS, fl_r * std::min(1.0, 64.0 / std::max(cols, 1)), c);
+            BLK_SPLIT_DISPATCH(split, (e = launch_k(false, k_blk_rfused<SS, 2>, dim3(1 + rb, nsys), dim3(TILE_THREADS),
+                                                    rsm, c, d_sys, ws, k, 1, 0, xd, ad, scr.inv_plane, xe, ae,
+                                                    scr.fdig[par], scr.fplane, scr.fex[par], scr.rdig[par],
+                                                    scr.cplane, scr.rex[par], pm, st)));
+            if (e != cudaSuccess) return e;
+            kt.end(c);
+            if ((e = cudaEventRecord(scr.ev_r, c)) != cudaSuccess) return e;
+            // ---- chain: the next pivot block's tile, then its factor
+            kt.begin(GM_K_GJUPDATE, fl_tile, c);
+            BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(1, 1, nsys), TILE_THREADS, usm, c>>>(
+                                          d_sys, ws, k, UPD_A11, nrt, scr.fdig[par], scr.fplane, scr.fex[par],
+                                          scr.rdig[par], scr.cplane, scr.rex[par])));
+            kt.end(c);
+            if (k + NBK < max_m && (e = factor(k + NBK, !kt.timed(GM_K_GJUPDATE) && !kt.timed(GM_K_PANEL))))
+                return e;
+            // ---- s3: the rest of R, the diagonal tile two blocks ahead, the next band
+            if ((e = cudaStreamWaitEvent(c3, scr.ev_r, 0)) != cudaSuccess) return e;
+            if (cb > 1) {
+                kt.begin(GM_K_PIVROWS, fl_r * std::max(0.0, 1.0 - 64.0 / std::max(cols, 1)), c3);
+                if (nsys * cb <= scr.rtile32_max) {
+                    const int cb32 = (cols - 64 + 31) / 32;
+                    BLK_SPLIT_DISPATCH(split, (e = launch_k(false, k_blk_rfused<SS, 1>, dim3(cb32, nsys),
+                                                            dim3(TILE_THREADS), rsm, c3, d_sys, ws, k, cb32, 2, xd, ad,
+                                                            scr.inv_plane, xe, ae, scr.fdig[par], scr.fplane,
+                                                            scr.fex[par], scr.rdig[par], scr.cplane, scr.rex[par], pm,
+                                                            st)));
+                } else {
+                    BLK_SPLIT_DISPATCH(split, (e = launch_k(false, k_blk_rfused<SS, 2>, dim3(cb - 1, nsys),
+                                                            dim3(TILE_THREADS), rsm, c3, d_sys, ws, k, cb - 1, 1, xd,
+                                                            ad, scr.inv_plane, xe, ae, scr.fdig[par], scr.fplane,
+                                                            scr.fex[par], scr.rdig[par], scr.cplane, scr.rex[par], pm,
+                                                            st)));
+                }
+                if (e != cudaSuccess) return e;
+                kt.end(c3);
+            }
+            if ((e = cudaEventRecord(scr.ev_rr, c3)) != cudaSuccess) return e;
+            if (blk > 0 && (e = cudaStreamWaitEvent(c3, scr.ev_rest2[par ^ 1], 0)) != cudaSuccess) return e;
+            kt.begin(GM_K_GJUPDATE, fl_tile, c3);
+            BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(1, 1, nsys), TILE_THREADS, usm, c3>>>(
+                                          d_sys, ws, k, UPD_D2, nrt, scr.fdig[par], scr.fplane, scr.fex[par],
+                                          scr.rdig[par], scr.cplane, scr.rex[par])));
+            kt.end(c3);
+            kt.begin(GM_K_GJUPDATE, std::max(0.0, fl_upd * std::min(1.0, 128.0 / std::max(cols, 1)) - 2 * fl_tile), c3);
+            BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(nrt + std::max(cb - 1, 0), 1, nsys), TILE_THREADS, usm,
+                                                          c3>>>(d_sys, ws, k, UPD_NEXT2, nrt, scr.fdig[par],
+                                                                scr.fplane, scr.fex[par], scr.rdig[par], scr.cplane,
+                                                                scr.rex[par])));
+            kt.end(c3);
+            if ((e = cudaEventRecord(scr.ev_next, c3)) != cudaSuccess) return e;
+            // ---- s2: the bulk of the update
+            if ((e = cudaStreamWaitEvent(scr.s2, scr.ev_rr, 0)) != cudaSuccess) return e;
+            if (cb > 1) {
+                kt.begin(GM_K_GJUPDATE, std::max(0.0, fl_upd * std::max(0.0, 1.0 - 128.0 / std::max(cols, 1))),
+                         scr.s2);
+                BLK_SPLIT_DISPATCH(split, (k_blk_update_tc<SS><<<dim3(nrt128, cb - 1, nsys), TILE_THREADS, tsm,
+                                                                 scr.s2>>>(d_sys, ws, k, UPD_REST2, scr.fdig[par],
+                                                                           scr.fplane, scr.fex[par], scr.rdig[par],
+                                                                           scr.cplane, scr.rex[par], st,
+                                                                           scr.wait_limit)));
+                kt.end(scr.s2);
+            }
+            if ((e = cudaEventRecord(scr.ev_rest2[par], scr.s2)) != cudaSuccess) return e;
+        }
+        // join everything into the caller's stream
+        if ((e = cudaStreamWaitEvent(c, scr.ev_next, 0)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(c, scr.ev_rest2[0], 0)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(c, scr.ev_rest2[1], 0)) != cudaSuccess ||
+            (e = cudaEventRecord(scr.ev_join, c)) != cudaSuccess || (e = cudaStreamWaitEvent(s, scr.ev_join, 0)))
+            return e;
+        return cudaGetLastError();
+    }
     bool pending = false;  // the rest of the previous step's update still runs on s2
     for (int k = 0; k < max_m; k += NBK) {
         const int par = (k / NBK) & 1;
@@ -881,13 +1031,13 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
         if (nsys * cb <= scr.rtile32_max) {
             const int cb32 = (cols + 31) / 32;
             BLK_SPLIT_DISPATCH(split, (e = launch_k(pdl_r, k_blk_rfused<SS, 1>, dim3(cb32 + rb, nsys),
-                                                    dim3(TILE_THREADS), rsm, c, d_sys, ws, k, cb32, scr.x_dig,
+                                                    dim3(TILE_THREADS), rsm, c, d_sys, ws, k, cb32, 0, scr.x_dig,
                                                     scr.a11_dig, scr.inv_plane, scr.x_ex, scr.a11_ex, scr.fdig[par],
                                                     scr.fplane, scr.fex[par], scr.rdig[par], scr.cplane,
                                                     scr.rex[par], scr.pmag, st)));
         } else {
             BLK_SPLIT_DISPATCH(split, (e = launch_k(pdl_r, k_blk_rfused<SS, 2>, dim3(cb + rb, nsys),
-                                                    dim3(TILE_THREADS), rsm, c, d_sys, ws, k, cb, scr.x_dig,
+                                                    dim3(TILE_THREADS), rsm, c, d_sys, ws, k, cb, 0, scr.x_dig,
                                                     scr.a11_dig, scr.inv_plane, scr.x_ex, scr.a11_ex, scr.fdig[par],
                                                     scr.fplane, scr.fex[par], scr.rdig[par], scr.cplane,
                                                     scr.rex[par], scr.pmag, st)));

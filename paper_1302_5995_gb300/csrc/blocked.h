@@ -32,6 +32,16 @@ struct BlkScratch {
     cudaEvent_t ev_r = nullptr, ev_rest = nullptr, ev_join = nullptr;
     int wait_limit = 1 << 22;  // polls of the tensor-core completion wait before GM_ETIMEOUT
     int rtile32_max = 96;      // R kernel: 32-column tiles while systems x 64-column tiles <= this
+    // early-factor schedule (needs the look-ahead streams, s3 and the second factor set):
+    // the chain is R of the next block's columns -> that block's pivot tile -> its factor;
+    // the rest of R, the diagonal tile two blocks ahead and the next band on s3 (high
+    // priority), the bulk of the update on s2
+    bool early = false;
+    cudaStream_t s3 = nullptr;
+    cudaEvent_t ev_rr = nullptr, ev_next = nullptr, ev_rest2[2] = {nullptr, nullptr};
+    __nv_bfloat16 *x_dig2 = nullptr, *a11_dig2 = nullptr;  // the factor's second output set
+    int *x_ex2 = nullptr, *a11_ex2 = nullptr;
+    float *pmag2 = nullptr;
 };
 
 size_t blk_factor_smem(int split);

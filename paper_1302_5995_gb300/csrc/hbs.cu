@@ -14,6 +14,9 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <cstdio>
+#include <cstdlib>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -1031,6 +1034,35 @@ void release_pool(HbsRoot &h) {
 }
 }  // namespace
 
+// A-posteriori check of an inverse from Algorithm 1: the algorithm inverts each node's
+// diagonal block without pivoting across blocks, which is unstable when such a block is
+// nearly singular even though S is not (strongly convective operators).  With x four
+// Gaussian vectors and y = S^{-1} x by Algorithm 2, the relative residual
+// max |S y - x| / max |x|; a stable inverse leaves a small multiple of tol.
+int hbs_residual(const double *S, int lds, HbsRoot &H, cudaStream_t s, double *resid) {
+    const int r = H.r, B = 4;
+    TempSet tmp(s);
+    DescBuf db;
+    double *X = tmp.get((int64_t)r * B), *Y = tmp.get((int64_t)r * B);
+    if (!X || !Y) return GM_ENOMEM;
+    k_hbs_normals<<<64, 256, 0, s>>>(X, (int64_t)r * B, 0x4842530000000007ull);
+    HCK(cudaGetLastError());
+    std::vector<double> hx((size_t)r * B), hz((size_t)r * B);
+    HCK(cudaMemcpyAsync(hx.data(), X, hx.size() * 8, cudaMemcpyDeviceToHost, s));
+    int rc = hbs_solve(H, X, r, Y, r, B, s);
+    if (rc == GM_OK) rc = run_gemms({gd(S, lds, 0, Y, r, 0, X, r, r, B, r, 1.0, -1.0)}, db, s);  // X := S Y - X
+    if (rc) return rc;
+    HCK(cudaMemcpyAsync(hz.data(), X, hz.size() * 8, cudaMemcpyDeviceToHost, s));
+    HCK(cudaStreamSynchronize(s));
+    double mx = 0.0, mr = 0.0;
+    for (size_t i = 0; i < hx.size(); ++i) {
+        mx = std::max(mx, std::fabs(hx[i]));
+        mr = std::max(mr, std::isfinite(hz[i]) ? std::fabs(hz[i]) : 1e300);
+    }
+    *resid = mx > 0.0 ? mr / mx : 0.0;
+    return GM_OK;
+}
+
 int hbs_factor(const double *S, int lds, int r, int m, double tol, cudaStream_t s, HbsRoot &H, bool temp) {
     if (r < 2 || lds < r || m < 2 || m > QR_MAXP || !(tol > 0.0)) return GM_EINVAL;
     const std::pair<int, int> key(size_class(r), m);
@@ -1045,8 +1077,22 @@ int hbs_factor(const double *S, int lds, int r, int m, double tol, cudaStream_t 
         const int rc = hbs_factor_l(S, lds, r, m, tol, l, temp, s, H);
         if (rc != HBS_RETRY) {
             if (rc == GM_OK) {
-                std::lock_guard<std::mutex> lk(g_hint_mu);
-                g_hint[key] = l;
+                {
+                    std::lock_guard<std::mutex> lk(g_hint_mu);
+                    g_hint[key] = l;
+                }
+                double res = 0.0;
+                const int rc2 = hbs_residual(S, lds, H, s, &res);
+                H.residual = res;
+                if (rc2) return rc2;
+                static const bool dbg = getenv("GM_DEBUG") != nullptr;
+                if (dbg)
+                    fprintf(stderr, "gm: hbs inverse r %d levels %d max rank %d tol %.1e: residual %.3e\n", r, H.L,
+                            H.max_rank, tol, res);
+                if (!(res <= HBS_MAX_RESIDUAL)) {  // unstable: the caller eliminates densely
+                    release_pool(H);
+                    return HBS_UNSTABLE;
+                }
             }
             return rc;
         }

@@ -16,6 +16,13 @@ constexpr int HBS_SAMPLES = 128;      // random samples per node at the first at
 constexpr int HBS_OVERSAMPLE = 32;    // this many of the sample count,
 constexpr int HBS_MAX_SAMPLES = 512;  // up to this many samples: ranks up to 480
 constexpr int HBS_MARGIN = 32;        // QR columns kept past a basis' own truncation point
+// Largest relative residual max |S S^{-1} x - x| / max |x| accepted from Algorithm 1's
+// inverse (checked on four Gaussian vectors after every factorisation); beyond it the
+// inverse is unstable and the factorisation returns GM_EUNSUPPORTED.
+constexpr double HBS_MAX_RESIDUAL = 1e-3;
+// Returned (not a public code) by hbs_factor, hbs_build_root and hbs_block_solve when the
+// residual check fails: the caller eliminates that system densely instead.
+constexpr int HBS_UNSTABLE = 1001;
 
 struct HbsRoot {
     int r = 0, n = 0, m = 0, L = 0;
@@ -28,6 +35,7 @@ struct HbsRoot {
     int64_t offG1 = 0;                       // root G_1 = [G_1-system | inverse], q = k_2 + k_3
     int64_t offKK = 0, offWW = 0;            // ghost couplings of the ring (2 ints, 2 doubles per node)
     int max_rank = 0;
+    double residual = 0.0;  // relative residual of the inverse on random vectors (see hbs_factor)
     double *sig = nullptr;  // conductance networks: the ghosts' link conductivities (4n, owned), which
                             // weight the rows of every apply (the datum is the link current)
 };
@@ -37,7 +45,8 @@ struct HbsRoot {
 // Algorithm 1 (Section 5).  The compression's temporaries come from the library pool;
 // the inverse's factors from cudaMalloc, or (temp) from the pool on stream s.
 // GM_EUNSUPPORTED: a node's rank exceeds HBS_MAX_SAMPLES - HBS_OVERSAMPLE, a sample has
-// more rows than one factorisation takes, or r <= m.
+// more rows than one factorisation takes, or r <= m.  HBS_UNSTABLE: the inverse failed
+// the residual check (HBS_MAX_RESIDUAL).
 int hbs_factor(const double *S, int lds, int r, int m, double tol, cudaStream_t s, HbsRoot &out, bool temp);
 // Y = S^{-1} X for B columns (Algorithm 2); X, Y device, r x B, leading dimensions ldx, ldy.
 int hbs_solve(HbsRoot &h, const double *X, int ldx, double *Y, int ldy, int B, cudaStream_t s);

@@ -155,3 +155,22 @@ def test_hbs_interface_solves_in_merges(gm, n, leaf, m, edge):
     assert rel_mat(T, To) < 100 * tol
     Th = nd_dense.build(b, c, d, n, leaf, interface_solve=ohbs.step1_interface_solver(tol, m), min_edge=edge).T
     assert rel_mat(T, Th) < 100 * tol
+
+
+def test_unstable_root_inverse_falls_back_to_dense(gm):
+    """Diffusion-Convection II (b = 1000) at n = 256, tol 1e-7: Algorithm 1's inverse of
+    the HBS root loses all accuracy here (the oracle's own root-only HBS build of this
+    problem is off by 1e18 in e1) because it inverts the nodes' diagonal blocks without
+    pivoting between them.  The residual check on random vectors refuses that inverse,
+    the root is eliminated densely and the operator matches O2; Laplace at the same size
+    passes the check and keeps its HBS root."""
+    n, leaf, m, tol = 256, 16, 64, 1e-7
+    f = inputs.paper_problem("diffconv2", n)
+    op = gm.build(*f, n, leaf, tol=tol, hbs_leaf=m, hbs_min_edge=1 << 20)
+    inf = op.info()
+    assert inf["hbs_fallbacks"] == 1 and inf["hbs_levels"] == 0
+    assert inf["dtn_bytes"] == 16 * n * n * 8 and inf["hbs_operator_bytes"] == 0
+    To = nd_dense.build(*f, n, leaf).T
+    assert rel_mat(op.dtn(), To) < 1e-9
+    lap = gm.build(*inputs.laplace_fields(n), n, leaf, tol=tol, hbs_leaf=m, hbs_min_edge=1 << 20)
+    assert lap.info()["hbs_fallbacks"] == 0 and lap.info()["hbs_levels"] > 0
