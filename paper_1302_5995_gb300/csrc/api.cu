@@ -40,6 +40,27 @@ bool debug_on() {
     return on;
 }
 
+// Multiprocessors of the current device (looked up once per device).
+int device_sms() {
+    static std::mutex mu;
+    static std::map<int, int> by_dev;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 152;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = by_dev.find(dev);
+    if (it != by_dev.end()) return it->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = 152;
+    }
+    by_dev[dev] = n;
+    return n;
+}
+
 int cuda_fail(cudaError_t e, const char *what, int line) {
     if (debug_on()) fprintf(stderr, "gm: api.cu:%d: %s: %s\n", line, what, cudaGetErrorString(e));
     return GM_ECUDA;
@@ -619,6 +640,8 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             bscr.wait_limit = wait_limit;
             bscr.rtile32_max = tu.rtile32_max;
             bscr.early = tu.early != 0;
+            bscr.upd_tiles = tu.upd_tiles;
+            bscr.sms = device_sms();
             bscr.s3 = la.s3;
             bscr.ev_rr = la.d;
             bscr.ev_next = la.e;
@@ -1021,8 +1044,8 @@ int autotune(const gm_opts &o, const std::shared_ptr<DevPlan> &dp, const std::ve
             bt = std::min(bt, ms);
         }
         if (debug_on())
-            fprintf(stderr, "gm: autotune rtile32_max %d early %d tc_min_k %d: %.3f ms\n", t.rtile32_max, t.early,
-                    t.tc_min_k, bt);
+            fprintf(stderr, "gm: autotune rtile32_max %d early %d tc_min_k %d upd_tiles %d: %.3f ms\n",
+                    t.rtile32_max, t.early, t.tc_min_k, t.upd_tiles, bt);
         return bt;
     };
     best = Tune();
@@ -1037,6 +1060,16 @@ int autotune(const gm_opts &o, const std::shared_ptr<DevPlan> &dp, const std::ve
             best = t;
         }
     }
+    if (o.precision == GM_PREC_MIXED)
+        for (int u : {0, 2, 8, -1}) {
+            Tune t = best;
+            t.upd_tiles = u;
+            const double x = time_of(t);
+            if (x < tb) {
+                tb = x;
+                best = t;
+            }
+        }
     if (o.precision == GM_PREC_MIXED) {
         Tune t = best;
         t.early = !best.early;
@@ -1091,7 +1124,7 @@ std::shared_ptr<GraphEntry> find_graph(const TuneKey &k, const Tune &t) {
     std::lock_guard<std::mutex> lk(g_graph_mu);
     for (auto &e : g_graphs)
         if (e->key == k && e->tune.rtile32_max == t.rtile32_max && e->tune.tc_min_k == t.tc_min_k &&
-            e->tune.early == t.early) {
+            e->tune.early == t.early && e->tune.upd_tiles == t.upd_tiles) {
             e->last_use = ++g_graph_tick;
             return e;
         }

@@ -668,10 +668,10 @@ size_t blk_update_tc_smem(int split) {
 
 // rows r0 .. r0 + R - 1 (zero beyond nrows) of every digit plane (64 k) into the core-matrix
 // layout: plane q at q * R * 128 bytes, 16-byte chunk (row, c) at (row / 8) 1024 + c 128 + (row % 8) 16
-template <int S, int R>
+template <int S, int R, int NT = TILE_THREADS>
 __device__ __forceinline__ void cp_async_digits_umma(const __nv_bfloat16 *__restrict__ dig, int64_t plane, int r0,
                                                      int nrows, unsigned char *sm) {
-    for (int e = threadIdx.x; e < S * R * 8; e += TILE_THREADS) {
+    for (int e = threadIdx.x; e < S * R * 8; e += NT) {
         const int c = e & 7, row = (e >> 3) % R, q = e / (8 * R);
         const bool ok = row < nrows;
         const __nv_bfloat16 *src = dig + (int64_t)q * plane + (int64_t)(r0 + (ok ? row : 0)) * NBK + c * 8;
@@ -801,6 +801,175 @@ k_blk_update_tc(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k,
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS));
 }
 
+// ----------------------------------------------------------------------------- update, pipelined tcgen05
+
+// The same update with a CTA per 128-row band and a run of its 32-column tiles: the band's
+// F digits are copied once and stay in shared memory, and per tile the R digits of the
+// next tile are copied (three stages) while the tensor cores run this tile's 21 x 4
+// products into one of two tensor-memory buffers (six levels x 32 columns each) and eight
+// warps recombine the previous tile's levels and update its W (read ahead into registers
+// while that tile's products ran).  A ninth warp holds the tensor memory and issues the
+// products.  One barrier per tile: after it, the buffer and the copy stage a tile reuses
+// were last read by work that finished before it.
+constexpr int TP_COLS = 32, TP_STAGES = 3, TP_THREADS = 288, TP_BUF_COLS = 192;
+
+size_t blk_update_tp_smem(int split) {
+    return (size_t)split * (TC_ROWS + TP_STAGES * TP_COLS) * NBK * sizeof(__nv_bfloat16) + 1024;
+}
+
+template <int S>
+__global__ void __launch_bounds__(TP_THREADS, 1)
+k_blk_update_tp(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k, int mode, int tpc,
+                const __nv_bfloat16 *__restrict__ fdig, int64_t fplane, const int *__restrict__ fex,
+                const __nv_bfloat16 *__restrict__ rdig, int64_t rplane, const int *__restrict__ rex,
+                Status *__restrict__ st, int limit) {
+    static_assert(S * TP_COLS <= TP_BUF_COLS, "levels of one tile exceed a tensor-memory buffer");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *Fs = base;                              // S x 16 KB
+    unsigned char *Rs = base + (size_t)S * TC_ROWS * 128;  // TP_STAGES x S x 4 KB
+    constexpr int RSTAGE = S * TP_COLS * 128;
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fe[TC_ROWS], s_re[TP_STAGES][TP_COLS];
+    __shared__ int s_ok;
+    const SysDesc Sy = sys[blockIdx.z];
+    const int m = Sy.m;
+    if (k >= m) return;
+    const int nbe = min(NBK, m - k);
+    const bool rest = mode == UPD_REST || mode == UPD_REST2;
+    const int i0 = blockIdx.x * TC_ROWS;
+    // columns from jb on (UPD_REST: the first 64 are the look-ahead's); rows skip_lo ..
+    // skip_hi - 1 are left alone (the pivot rows; in UPD_REST the next pivot band too)
+    const int jb = k + nbe + (rest ? 64 : 0);
+    const int skip_lo = k, skip_hi = rest ? min(m, k + 2 * NBK) : k + nbe;
+    if (i0 >= m || (i0 >= skip_lo && i0 + TC_ROWS <= skip_hi)) return;
+    const int ntile = (Sy.ncol - jb + TP_COLS - 1) / TP_COLS, t0 = blockIdx.y * tpc;
+    const int nmine = min(tpc, ntile - t0);
+    if (nmine <= 0) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float2 *W = ws + Sy.off;
+    const __nv_bfloat16 *rd = rdig + (int64_t)Sy.coff * NBK;
+    const int *re = rex + Sy.coff;
+    auto tile_j0 = [&](int t) { return jb + (t0 + t) * TP_COLS; };
+    auto load_r = [&](int t) {
+        const int j0 = tile_j0(t), sg = t % TP_STAGES;
+        cp_async_digits_umma<S, TP_COLS, TP_THREADS>(rd, rplane, j0, min(TP_COLS, Sy.ncol - j0), Rs + sg * RSTAGE);
+        if (warp == 8) {  // the exponents of the tile's columns
+            const int j = j0 + lane;
+            const bool ok = j < Sy.ncol;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(&s_re[sg][lane])),
+                         "l"(re + (ok ? j : 0)), "r"(ok ? 4 : 0));
+        }
+    };
+    cp_async_digits_umma<S, TC_ROWS, TP_THREADS>(fdig + (int64_t)Sy.roff * NBK, fplane, i0, min(TC_ROWS, m - i0), Fs);
+    load_r(0);
+    asm volatile("cp.async.commit_group;\n" ::);
+    if (tid < TC_ROWS) {
+        const int i = i0 + tid;
+        s_fe[tid] = i < m ? fex[Sy.roff + i] : 0;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
+        s_ok = 1;
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                     "r"(TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    // epilogue warps 0-7: tensor-memory lanes 32 (warp % 4) .., columns 16 (warp / 4) ..
+    const int q = warp & 3, h = (warp >> 2) & 1;
+    const int row = 32 * q + lane, i = i0 + row;
+    const bool row_live = warp < 8 && i < m && !(i >= skip_lo && i < skip_hi);
+    float2 wn[16], wc[16];
+    uint32_t tmem = 0;
+    int last = -1;  // the last tile whose products were issued (issuing thread)
+    for (int t = 0; t <= nmine; ++t) {
+        asm volatile("cp.async.wait_group 0;\n" ::);           // R digits of tile t (and F)
+        asm volatile("fence.proxy.async.shared::cta;\n" ::);  // visible to the tensor cores
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+        if (t == 0) tmem = s_tmem;
+        if (!s_ok) break;
+        if (t + 1 < nmine) load_r(t + 1);  // its stage held tile t - 2, whose products are done
+        asm volatile("cp.async.commit_group;\n" ::);
+        if (t < nmine) {
+            const int j0 = tile_j0(t);
+            if (tid == 256) {
+                constexpr uint32_t idesc = umma_idesc_bf16(TC_ROWS, TP_COLS);
+                const unsigned char *Rb = Rs + (t % TP_STAGES) * RSTAGE;
+                const uint32_t d0 = tmem + (uint32_t)((t & 1) * TP_BUF_COLS);
+                const int nk = (nbe + 15) >> 4;
+                for (int kc = 0; kc < nk; ++kc)
+#pragma unroll
+                    for (int a = 0; a < S; ++a)
+#pragma unroll
+                        for (int b = 0; b < S - a; ++b)
+                            umma_bf16(d0 + (uint32_t)((a + b) * TP_COLS),
+                                      umma_desc(smem_u32(Fs + (size_t)a * TC_ROWS * 128 + kc * 256), 128, 1024),
+                                      umma_desc(smem_u32(Rb + (size_t)b * TP_COLS * 128 + kc * 256), 128, 1024),
+                                      idesc, (kc > 0 || a > 0) ? 1u : 0u);
+                umma_commit(&mbar[t & 1]);
+                last = t;
+            }
+            if (warp < 8) {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int j = j0 + 16 * h + c;
+                    wn[c] = (row_live && j < Sy.ncol) ? W[(size_t)j * m + i] : make_float2(0.f, 0.f);
+                }
+            }
+        }
+        if (t >= 1 && warp < 8) {  // finish tile u = t - 1
+            const int u = t - 1, j0 = tile_j0(u), sg = u % TP_STAGES;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&mbar[u & 1], (u >> 1) & 1, limit));
+            if (!ok) {
+                s_ok = 0;
+                if (lane == 0 && atomicCAS(&st[Sy.prob].code, 0, GM_ETIMEOUT) == 0) st[Sy.prob].where = -1;
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+                // UPD_REST2: the diagonal tile two blocks ahead is UPD_D2's
+                const bool dt = mode == UPD_REST2 && j0 >= k + nbe + 64 && j0 < k + nbe + 128;
+                const bool live = row_live && !(dt && i >= k + 2 * NBK && i < k + 3 * NBK);
+                const int fe = s_fe[row];
+                const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((u & 1) * TP_BUF_COLS + 16 * h);
+#pragma unroll
+                for (int c0 = 0; c0 < 16; c0 += 8) {
+                    uint32_t v[S][8];
+#pragma unroll
+                    for (int g = 0; g < S; ++g) tmem_ld8(tb + (uint32_t)(g * TP_COLS + c0), v[g]);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const int jj = 16 * h + c0 + c, j = j0 + jj;
+                        if (!live || j >= Sy.ncol) continue;
+                        float2 x = make_float2(__uint_as_float(v[S - 1][c]) * pow2f(-7 * (S - 1)), 0.f);
+#pragma unroll
+                        for (int g = S - 2; g >= 0; --g) x = df_add_f(x, __uint_as_float(v[g][c]) * pow2f(-7 * g));
+                        W[(size_t)j * m + i] = df_sub(wc[c0 + c], df_scale(x, fe + s_re[sg][jj] - 12));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) wc[c] = wn[c];
+    }
+    // gave up: the products already issued still write tensor memory; wait (bounded) for
+    // the last commit, which tracks all of them, before the memory is released
+    if (tid == 256 && last >= 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+        mbar_wait_bounded(&mbar[last & 1], (last >> 1) & 1, DRAIN_POLLS);
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    if (warp == 8) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS));
+}
+
 // ----------------------------------------------------------------------------- launcher
 
 // Launch with programmatic stream serialization when `pdl` (the kernel must call
@@ -841,6 +1010,9 @@ static cudaError_t set_blk_attrs(int split) {
     e = cudaFuncSetAttribute(k_blk_update_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)blk_update_tc_smem(split));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_blk_update_tp<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)blk_update_tp_smem(split));
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_blk_rfused<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)blk_rgemm_smem(split));
     if (e != cudaSuccess) return e;
@@ -855,8 +1027,34 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
     BLK_SPLIT_DISPATCH(split, (e = set_blk_attrs<SS>(split)));
     if (e != cudaSuccess) return e;
     const size_t fsm = blk_factor_smem(split), rsm = blk_rgemm_smem(split), usm = blk_update_smem(split),
-                 tsm = blk_update_tc_smem(split);
+                 tsm = blk_update_tc_smem(split), psm = blk_update_tp_smem(split);
     const int nrt128 = (max_m + TC_ROWS - 1) / TC_ROWS;
+    // the bulk of a block step's update (UPD_ALL, UPD_REST, UPD_REST2) on stream `on`: the
+    // pipelined kernel over runs of 32-column tiles, or one CTA per 128 x 64 tile
+    auto bulk_update = [&](int k, int mode, int par, cudaStream_t on) -> cudaError_t {
+        const int off = mode == UPD_ALL ? 0 : 64;
+        int nt = 0;
+        for (const SysDesc &S : h_sys)
+            if (k < S.m) nt = std::max(nt, (S.ncol - k - std::min(NBK, S.m - k) - off + TP_COLS - 1) / TP_COLS);
+        if (nt <= 0) return cudaSuccess;
+        if (scr.upd_tiles < 0) {
+            const int ncb = (nt * TP_COLS + TC_COLS - 1) / TC_COLS;
+            BLK_SPLIT_DISPATCH(split, (k_blk_update_tc<SS><<<dim3(nrt128, ncb, nsys), TILE_THREADS, tsm, on>>>(
+                                          d_sys, ws, k, mode, scr.fdig[par], scr.fplane, scr.fex[par],
+                                          scr.rdig[par], scr.cplane, scr.rex[par], st, scr.wait_limit)));
+            return cudaGetLastError();
+        }
+        int tpc = scr.upd_tiles;
+        if (tpc == 0) {  // one wave: a CTA per SM
+            const int64_t bands = (int64_t)nsys * nrt128;
+            tpc = (int)std::max<int64_t>(1, (nt * bands + scr.sms - 1) / scr.sms);
+        }
+        const int gy = (nt + tpc - 1) / tpc;
+        BLK_SPLIT_DISPATCH(split, (k_blk_update_tp<SS><<<dim3(nrt128, gy, nsys), TP_THREADS, psm, on>>>(
+                                      d_sys, ws, k, mode, tpc, scr.fdig[par], scr.fplane, scr.fex[par],
+                                      scr.rdig[par], scr.cplane, scr.rex[par], st, scr.wait_limit)));
+        return cudaGetLastError();
+    };
     const bool la = scr.s1 && scr.s2;
     // the chain runs on s1, joined to the caller's stream on entry and exit
     cudaStream_t c = la ? scr.s1 : s;
@@ -979,11 +1177,7 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
             if (cb > 1) {
                 kt.begin(GM_K_GJUPDATE, std::max(0.0, fl_upd * std::max(0.0, 1.0 - 128.0 / std::max(cols, 1))),
                          scr.s2);
-                BLK_SPLIT_DISPATCH(split, (k_blk_update_tc<SS><<<dim3(nrt128, cb - 1, nsys), TILE_THREADS, tsm,
-                                                                 scr.s2>>>(d_sys, ws, k, UPD_REST2, scr.fdig[par],
-                                                                           scr.fplane, scr.fex[par], scr.rdig[par],
-                                                                           scr.cplane, scr.rex[par], st,
-                                                                           scr.wait_limit)));
+                if ((e = bulk_update(k, UPD_REST2, par, scr.s2)) != cudaSuccess) return e;
                 kt.end(scr.s2);
             }
             if ((e = cudaEventRecord(scr.ev_rest2[par], scr.s2)) != cudaSuccess) return e;
@@ -1053,9 +1247,7 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
         }
         if (!la || cb < 2) {
             kt.begin(GM_K_GJUPDATE, fl_upd, c);
-            BLK_SPLIT_DISPATCH(split, (k_blk_update_tc<SS><<<dim3(nrt128, cb, nsys), TILE_THREADS, tsm, c>>>(
-                                          d_sys, ws, k, UPD_ALL, scr.fdig[par], scr.fplane, scr.fex[par],
-                                          scr.rdig[par], scr.cplane, scr.rex[par], st, scr.wait_limit)));
+            if ((e = bulk_update(k, UPD_ALL, par, c)) != cudaSuccess) return e;
             kt.end(c);
             continue;
         }
@@ -1069,9 +1261,7 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
         kt.end(c);
         if ((e = cudaStreamWaitEvent(scr.s2, scr.ev_r, 0)) != cudaSuccess) return e;
         kt.begin(GM_K_GJUPDATE, fl_upd - fl_next, scr.s2);
-        BLK_SPLIT_DISPATCH(split, (k_blk_update_tc<SS><<<dim3(nrt128, cb - 1, nsys), TILE_THREADS, tsm, scr.s2>>>(
-                                      d_sys, ws, k, UPD_REST, scr.fdig[par], scr.fplane, scr.fex[par],
-                                      scr.rdig[par], scr.cplane, scr.rex[par], st, scr.wait_limit)));
+        if ((e = bulk_update(k, UPD_REST, par, scr.s2)) != cudaSuccess) return e;
         kt.end(scr.s2);
         if ((e = cudaEventRecord(scr.ev_rest, scr.s2)) != cudaSuccess) return e;
         pending = true;
