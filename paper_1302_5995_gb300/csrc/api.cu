@@ -1061,7 +1061,8 @@ int autotune(const gm_opts &o, const std::shared_ptr<DevPlan> &dp, const std::ve
         }
     }
     if (o.precision == GM_PREC_MIXED)
-        for (int u : {0, 2, 8, -1}) {
+        for (int u : {0, 2, 4, -1}) {
+            if (u == best.upd_tiles) continue;
             Tune t = best;
             t.upd_tiles = u;
             const double x = time_of(t);

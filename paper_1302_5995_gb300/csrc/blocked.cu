@@ -803,15 +803,17 @@ k_blk_update_tc(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k,
 
 // ----------------------------------------------------------------------------- update, pipelined tcgen05
 
-// The same update with a CTA per 128-row band and a run of its 32-column tiles: the band's
-// F digits are copied once and stay in shared memory, and per tile the R digits of the
-// next tile are copied (three stages) while the tensor cores run this tile's 21 x 4
-// products into one of two tensor-memory buffers (six levels x 32 columns each) and eight
-// warps recombine the previous tile's levels and update its W (read ahead into registers
-// while that tile's products ran).  A ninth warp holds the tensor memory and issues the
-// products.  One barrier per tile: after it, the buffer and the copy stage a tile reuses
-// were last read by work that finished before it.
-constexpr int TP_COLS = 32, TP_STAGES = 3, TP_THREADS = 288, TP_BUF_COLS = 192;
+// The same update with a CTA per 128-row band and a run of its 64-column tiles.  The
+// band's F digits are copied once and stay in shared memory; the R digits of the next
+// tile are copied into the other of two stages while the current tile's 21 x 4 products
+// run (one thread issues them into six level accumulators in tensor memory).  Eight warps
+// finish a tile in two halves: right after its products they read the levels back and
+// combine them (the tensor memory is then free for the next tile's products), and while
+// the next tile's products run they read that tile of W, subtract and store it.  A ninth warp holds the tensor memory and issues the products.
+// One barrier per tile: after it, the stage and the accumulators a tile reuses were last
+// read by work that finished before it.  (An M = 128 instruction with N = 64 costs about
+// as many cycles as one with N = 32, so the wider tile halves the issue time per column.)
+constexpr int TP_COLS = 64, TP_STAGES = 2, TP_THREADS = 288;
 
 size_t blk_update_tp_smem(int split) {
     return (size_t)split * (TC_ROWS + TP_STAGES * TP_COLS) * NBK * sizeof(__nv_bfloat16) + 1024;
@@ -823,13 +825,12 @@ k_blk_update_tp(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k,
                 const __nv_bfloat16 *__restrict__ fdig, int64_t fplane, const int *__restrict__ fex,
                 const __nv_bfloat16 *__restrict__ rdig, int64_t rplane, const int *__restrict__ rex,
                 Status *__restrict__ st, int limit) {
-    static_assert(S * TP_COLS <= TP_BUF_COLS, "levels of one tile exceed a tensor-memory buffer");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *Fs = base;                              // S x 16 KB
-    unsigned char *Rs = base + (size_t)S * TC_ROWS * 128;  // TP_STAGES x S x 4 KB
+    unsigned char *Rs = base + (size_t)S * TC_ROWS * 128;  // TP_STAGES x S x 8 KB
     constexpr int RSTAGE = S * TP_COLS * 128;
-    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ __align__(8) unsigned long long mbar;
     __shared__ uint32_t s_tmem;
     __shared__ int s_fe[TC_ROWS], s_re[TP_STAGES][TP_COLS];
     __shared__ int s_ok;
@@ -856,10 +857,13 @@ k_blk_update_tp(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k,
         const int j0 = tile_j0(t), sg = t % TP_STAGES;
         cp_async_digits_umma<S, TP_COLS, TP_THREADS>(rd, rplane, j0, min(TP_COLS, Sy.ncol - j0), Rs + sg * RSTAGE);
         if (warp == 8) {  // the exponents of the tile's columns
-            const int j = j0 + lane;
-            const bool ok = j < Sy.ncol;
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(&s_re[sg][lane])),
-                         "l"(re + (ok ? j : 0)), "r"(ok ? 4 : 0));
+#pragma unroll
+            for (int h2 = 0; h2 < TP_COLS; h2 += 32) {
+                const int j = j0 + h2 + lane;
+                const bool ok = j < Sy.ncol;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(&s_re[sg][h2 + lane])),
+                             "l"(re + (ok ? j : 0)), "r"(ok ? 4 : 0));
+            }
         }
     };
     cp_async_digits_umma<S, TC_ROWS, TP_THREADS>(fdig + (int64_t)Sy.roff * NBK, fplane, i0, min(TC_ROWS, m - i0), Fs);
@@ -870,8 +874,7 @@ k_blk_update_tp(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k,
         s_fe[tid] = i < m ? fex[Sy.roff + i] : 0;
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar)));
         s_ok = 1;
     }
     if (warp == 8) {
@@ -879,11 +882,13 @@ k_blk_update_tp(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k,
                      "r"(TC_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
     }
-    // epilogue warps 0-7: tensor-memory lanes 32 (warp % 4) .., columns 16 (warp / 4) ..
+    // epilogue warps 0-7: tensor-memory lanes 32 (warp % 4) .., columns 32 (warp / 4) ..
     const int q = warp & 3, h = (warp >> 2) & 1;
     const int row = 32 * q + lane, i = i0 + row;
     const bool row_live = warp < 8 && i < m && !(i >= skip_lo && i < skip_hi);
-    float2 wn[16], wc[16];
+    float2 acc[32];          // F R of the tile being finished (scaled)
+    int pj0 = 0;             // its first column
+    bool plive = false;      // this thread's row is written in it
     uint32_t tmem = 0;
     int last = -1;  // the last tile whose products were issued (issuing thread)
     for (int t = 0; t <= nmine; ++t) {
@@ -894,74 +899,80 @@ k_blk_update_tp(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k,
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
         if (t == 0) tmem = s_tmem;
         if (!s_ok) break;
-        if (t + 1 < nmine) load_r(t + 1);  // its stage held tile t - 2, whose products are done
+        if (t < nmine && tid == 256) {
+            constexpr uint32_t idesc = umma_idesc_bf16(TC_ROWS, TP_COLS);
+            const unsigned char *Rb = Rs + (t % TP_STAGES) * RSTAGE;
+            const int nk = (nbe + 15) >> 4;
+            for (int kc = 0; kc < nk; ++kc)
+#pragma unroll
+                for (int a = 0; a < S; ++a)
+#pragma unroll
+                    for (int b = 0; b < S - a; ++b)
+                        umma_bf16(tmem + (uint32_t)((a + b) * TP_COLS),
+                                  umma_desc(smem_u32(Fs + (size_t)a * TC_ROWS * 128 + kc * 256), 128, 1024),
+                                  umma_desc(smem_u32(Rb + (size_t)b * TP_COLS * 128 + kc * 256), 128, 1024), idesc,
+                                  (kc > 0 || a > 0) ? 1u : 0u);
+            umma_commit(&mbar);
+            last = t;
+        }
+        // the stage tile t + 1 takes held tile t - 1, whose products finished before the barrier
+        if (t + 1 < nmine) load_r(t + 1);
         asm volatile("cp.async.commit_group;\n" ::);
-        if (t < nmine) {
-            const int j0 = tile_j0(t);
-            if (tid == 256) {
-                constexpr uint32_t idesc = umma_idesc_bf16(TC_ROWS, TP_COLS);
-                const unsigned char *Rb = Rs + (t % TP_STAGES) * RSTAGE;
-                const uint32_t d0 = tmem + (uint32_t)((t & 1) * TP_BUF_COLS);
-                const int nk = (nbe + 15) >> 4;
-                for (int kc = 0; kc < nk; ++kc)
+        if (warp < 8) {
+            if (t >= 1 && plive) {  // second half of tile t - 1, beside tile t's products
+                const int jh = pj0 + 32 * h, nc = min(32, Sy.ncol - jh);
+                float2 *p = W + (size_t)jh * m + i;
 #pragma unroll
-                    for (int a = 0; a < S; ++a)
+                for (int c0 = 0; c0 < 32; c0 += 16) {
+                    float2 w[16];
 #pragma unroll
-                        for (int b = 0; b < S - a; ++b)
-                            umma_bf16(d0 + (uint32_t)((a + b) * TP_COLS),
-                                      umma_desc(smem_u32(Fs + (size_t)a * TC_ROWS * 128 + kc * 256), 128, 1024),
-                                      umma_desc(smem_u32(Rb + (size_t)b * TP_COLS * 128 + kc * 256), 128, 1024),
-                                      idesc, (kc > 0 || a > 0) ? 1u : 0u);
-                umma_commit(&mbar[t & 1]);
-                last = t;
-            }
-            if (warp < 8) {
+                    for (int c = 0; c < 16; ++c)
+                        w[c] = c0 + c < nc ? p[(size_t)(c0 + c) * m] : make_float2(0.f, 0.f);
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    const int j = j0 + 16 * h + c;
-                    wn[c] = (row_live && j < Sy.ncol) ? W[(size_t)j * m + i] : make_float2(0.f, 0.f);
+                    for (int c = 0; c < 16; ++c)
+                        if (c0 + c < nc) p[(size_t)(c0 + c) * m] = df_sub(w[c], acc[c0 + c]);
                 }
             }
-        }
-        if (t >= 1 && warp < 8) {  // finish tile u = t - 1
-            const int u = t - 1, j0 = tile_j0(u), sg = u % TP_STAGES;
-            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&mbar[u & 1], (u >> 1) & 1, limit));
-            if (!ok) {
-                s_ok = 0;
-                if (lane == 0 && atomicCAS(&st[Sy.prob].code, 0, GM_ETIMEOUT) == 0) st[Sy.prob].where = -1;
-            } else {
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-                // UPD_REST2: the diagonal tile two blocks ahead is UPD_D2's
-                const bool dt = mode == UPD_REST2 && j0 >= k + nbe + 64 && j0 < k + nbe + 128;
-                const bool live = row_live && !(dt && i >= k + 2 * NBK && i < k + 3 * NBK);
-                const int fe = s_fe[row];
-                const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((u & 1) * TP_BUF_COLS + 16 * h);
+            if (t < nmine) {
+                const int j0 = tile_j0(t);
+                // first half of tile t: wait for its products, read the levels back, combine
+                const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&mbar, t & 1, limit));
+                if (!ok) {
+                    s_ok = 0;
+                    plive = false;
+                    if (lane == 0 && atomicCAS(&st[Sy.prob].code, 0, GM_ETIMEOUT) == 0) st[Sy.prob].where = -1;
+                } else {
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+                    // UPD_REST2: the diagonal tile two blocks ahead is UPD_D2's
+                    const bool dt = mode == UPD_REST2 && j0 == k + nbe + 64;
+                    plive = row_live && !(dt && i >= k + 2 * NBK && i < k + 3 * NBK);
+                    pj0 = j0;
+                    const int fe = s_fe[row], sg = t % TP_STAGES;
+                    const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h);
 #pragma unroll
-                for (int c0 = 0; c0 < 16; c0 += 8) {
-                    uint32_t v[S][8];
+                    for (int c0 = 0; c0 < 32; c0 += 8) {
+                        uint32_t v[S][8];
 #pragma unroll
-                    for (int g = 0; g < S; ++g) tmem_ld8(tb + (uint32_t)(g * TP_COLS + c0), v[g]);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+                        for (int g = 0; g < S; ++g) tmem_ld8(tb + (uint32_t)(g * TP_COLS + c0), v[g]);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const int jj = 16 * h + c0 + c, j = j0 + jj;
-                        if (!live || j >= Sy.ncol) continue;
-                        float2 x = make_float2(__uint_as_float(v[S - 1][c]) * pow2f(-7 * (S - 1)), 0.f);
+                        for (int c = 0; c < 8; ++c) {
+                            float2 x = make_float2(__uint_as_float(v[S - 1][c]) * pow2f(-7 * (S - 1)), 0.f);
 #pragma unroll
-                        for (int g = S - 2; g >= 0; --g) x = df_add_f(x, __uint_as_float(v[g][c]) * pow2f(-7 * g));
-                        W[(size_t)j * m + i] = df_sub(wc[c0 + c], df_scale(x, fe + s_re[sg][jj] - 12));
+                            for (int g = S - 2; g >= 0; --g)
+                                x = df_add_f(x, __uint_as_float(v[g][c]) * pow2f(-7 * g));
+                            acc[c0 + c] = df_scale(x, fe + s_re[sg][32 * h + c0 + c] - 12);
+                        }
                     }
                 }
             }
         }
-#pragma unroll
-        for (int c = 0; c < 16; ++c) wc[c] = wn[c];
     }
     // gave up: the products already issued still write tensor memory; wait (bounded) for
     // the last commit, which tracks all of them, before the memory is released
     if (tid == 256 && last >= 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-        mbar_wait_bounded(&mbar[last & 1], (last >> 1) & 1, DRAIN_POLLS);
+        mbar_wait_bounded(&mbar, last & 1, DRAIN_POLLS);
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);

@@ -32,7 +32,7 @@ struct BlkScratch {
     cudaEvent_t ev_r = nullptr, ev_rest = nullptr, ev_join = nullptr;
     int wait_limit = 1 << 22;  // polls of the tensor-core completion wait before GM_ETIMEOUT
     int rtile32_max = 96;      // R kernel: 32-column tiles while systems x 64-column tiles <= this
-    int upd_tiles = 4;         // bulk update: 32-column tiles per CTA (0: one wave, < 0: one tile per CTA)
+    int upd_tiles = 0;         // bulk update: 64-column tiles per CTA (0: one wave, < 0: one tile per CTA)
     int sms = 152;             // multiprocessors of the device
     // early-factor schedule (needs the look-ahead streams, s3 and the second factor set):
     // the chain is R of the next block's columns -> that block's pivot tile -> its factor;

@@ -109,7 +109,7 @@ struct Tune {
     int rtile32_max = 96;  // R kernel: 32-column tiles while systems x 64-column tiles <= this
     int tc_min_k = 192;    // merge update on tcgen05 for interfaces with K >= this (else mma.sync)
     int early = 0;         // blocked sweep: the early-factor schedule (next factor off the R chain)
-    int upd_tiles = 4;     // blocked sweep's bulk update: 32-column tiles per CTA (0 one wave, -1 one per CTA)
+    int upd_tiles = 0;     // blocked sweep's bulk update: 64-column tiles per CTA (0 one wave, -1 one per CTA)
 };
 
 // Largest leaf edge the leaf kernels take (band and inner-ring solves in shared memory).

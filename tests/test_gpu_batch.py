@@ -110,7 +110,8 @@ def test_batch_rejects_bad_arguments(gm):
 
 def test_config4_subset(gm):
     """Eight problems of the 64-problem batch recipe (every size, both field kinds) in
-    mixed precision: each equals its single build; those with n <= 192 match the oracle."""
+    mixed precision: each equals its single build and matches O2's dense nested
+    dissection of the same problem (up to n = 512)."""
     cfg = inputs.config4()
     chosen, seen = [], set()
     for p in cfg:
@@ -125,9 +126,8 @@ def test_config4_subset(gm):
         single = gm.build(*p, precision=gm.PREC_MIXED, split_digits=6)
         assert same_as_single(op, single), p[3]
     for op, p in zip(ops, probs):
-        if p[3] <= 192:
-            To = nd_dense.build(*p).T
-            assert rel_mat(op.dtn(), To) < 1e-8, p[3]
+        To = nd_dense.build(*p).T
+        assert rel_mat(op.dtn(), To) < 1e-8, p[3]
 
 
 def test_batch_fallback_is_per_problem(gm):

@@ -145,16 +145,18 @@ def test_convection_stays_mixed_block_pivoted(gm):
     assert rel_mat(op.dtn(), gm.build(b, c, d, n, leaf).dtn()) < TOL_MIXED
 
 
-def test_mixed_long_interface_matches_fp64_at_1100(gm):
+def test_mixed_long_interface_matches_oracle_at_1100(gm):
     """n = 1100: the top merge's interface gives K = 2196, so the tensor-memory merge
     update accumulates its levels in five K chunks of at most 512 (each later chunk adds
-    into the parent entries the first wrote).  Against the FP64 build of the same
-    problem."""
+    into the parent entries the first wrote).  The whole 4400 x 4400 T against O2's dense
+    nested dissection of the same problem, and against the FP64 build."""
     n, leaf = 1100, 16
     b, c, d = inputs.convection_fields(n, seeds=(21, 22, 23))
     op = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED, split_digits=6)
     assert op.info()["pivot_fallback"] == 0
     T = op.dtn()
     op.free()
+    To = nd_dense.build(b, c, d, n, leaf).T
+    assert rel_mat(T, To) < TOL_MIXED
     ref = gm.build(b, c, d, n, leaf)
-    assert rel_mat(T, ref.dtn()) < TOL_MIXED
+    assert rel_mat(ref.dtn(), To) < 1e-9
