@@ -804,16 +804,18 @@ k_blk_update_tc(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k,
 // ----------------------------------------------------------------------------- update, pipelined tcgen05
 
 // The same update with a CTA per 128-row band and a run of its 64-column tiles.  The
-// band's F digits are copied once and stay in shared memory; the R digits of the next
-// tile are copied into the other of two stages while the current tile's 21 x 4 products
-// run (one thread issues them into six level accumulators in tensor memory).  Eight warps
-// finish a tile in two halves: right after its products they read the levels back and
-// combine them (the tensor memory is then free for the next tile's products), and while
-// the next tile's products run they read that tile of W, subtract and store it.  A ninth warp holds the tensor memory and issues the products.
-// One barrier per tile: after it, the stage and the accumulators a tile reuses were last
-// read by work that finished before it.  (An M = 128 instruction with N = 64 costs about
-// as many cycles as one with N = 32, so the wider tile halves the issue time per column.)
-constexpr int TP_COLS = 64, TP_STAGES = 2, TP_THREADS = 288;
+// band's F digits are copied once and stay in shared memory; three copy warps bring the R
+// digits of the next tile into the other of two stages while the current tile's 21 x 4
+// products run (one thread of a ninth warp, which holds the tensor memory, issues them
+// into six level accumulators).  Eight warps finish a tile in two halves: right after its
+// products they read the levels back and combine them (the tensor memory is then free for
+// the next tile's products), and while the next tile's products run they read that tile
+// of W, subtract and store it.  One barrier per tile: after it, the stage and the
+// accumulators a tile reuses were last read by work that finished before it.  (An
+// M = 128 instruction with N = 64 costs about as many cycles as one with N = 32, so the
+// wider tile halves the issue time per column.)
+constexpr int TP_COLS = 64, TP_STAGES = 2, TP_THREADS = 384;
+constexpr int TP_LOADER = 288;  // first thread of the three copy warps
 
 size_t blk_update_tp_smem(int split) {
     return (size_t)split * (TC_ROWS + TP_STAGES * TP_COLS) * NBK * sizeof(__nv_bfloat16) + 1024;
@@ -853,10 +855,19 @@ k_blk_update_tp(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k,
     const __nv_bfloat16 *rd = rdig + (int64_t)Sy.coff * NBK;
     const int *re = rex + Sy.coff;
     auto tile_j0 = [&](int t) { return jb + (t0 + t) * TP_COLS; };
-    auto load_r = [&](int t) {
-        const int j0 = tile_j0(t), sg = t % TP_STAGES;
-        cp_async_digits_umma<S, TP_COLS, TP_THREADS>(rd, rplane, j0, min(TP_COLS, Sy.ncol - j0), Rs + sg * RSTAGE);
-        if (warp == 8) {  // the exponents of the tile's columns
+    // R digits of tile t into its stage: by the copy warps (9-11) inside the loop, by all
+    // threads before it
+    auto load_r = [&](int t, int first, int nthreads) {
+        const int j0 = tile_j0(t), sg = t % TP_STAGES, nrows = min(TP_COLS, Sy.ncol - j0);
+        unsigned char *sm = Rs + sg * RSTAGE;
+        for (int e = tid - first; e < S * TP_COLS * 8; e += nthreads) {
+            const int c = e & 7, r = (e >> 3) % TP_COLS, pl = e / (8 * TP_COLS);
+            const bool ok = r < nrows;
+            const __nv_bfloat16 *src = rd + (int64_t)pl * rplane + (int64_t)(j0 + (ok ? r : 0)) * NBK + c * 8;
+            const uint32_t dst = smem_u32(sm + (size_t)pl * TP_COLS * 128 + (r >> 3) * 1024 + c * 128 + (r & 7) * 16);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0));
+        }
+        if (warp == 9) {  // the exponents of the tile's columns
 #pragma unroll
             for (int h2 = 0; h2 < TP_COLS; h2 += 32) {
                 const int j = j0 + h2 + lane;
@@ -867,7 +878,7 @@ k_blk_update_tp(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k,
         }
     };
     cp_async_digits_umma<S, TC_ROWS, TP_THREADS>(fdig + (int64_t)Sy.roff * NBK, fplane, i0, min(TC_ROWS, m - i0), Fs);
-    load_r(0);
+    load_r(0, 0, TP_THREADS);
     asm volatile("cp.async.commit_group;\n" ::);
     if (tid < TC_ROWS) {
         const int i = i0 + tid;
@@ -916,22 +927,18 @@ k_blk_update_tp(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k,
             last = t;
         }
         // the stage tile t + 1 takes held tile t - 1, whose products finished before the barrier
-        if (t + 1 < nmine) load_r(t + 1);
+        if (t + 1 < nmine && tid >= TP_LOADER) load_r(t + 1, TP_LOADER, TP_THREADS - TP_LOADER);
         asm volatile("cp.async.commit_group;\n" ::);
         if (warp < 8) {
             if (t >= 1 && plive) {  // second half of tile t - 1, beside tile t's products
                 const int jh = pj0 + 32 * h, nc = min(32, Sy.ncol - jh);
                 float2 *p = W + (size_t)jh * m + i;
+                float2 w[32];  // all 32 loads in flight at once
 #pragma unroll
-                for (int c0 = 0; c0 < 32; c0 += 16) {
-                    float2 w[16];
+                for (int c = 0; c < 32; ++c) w[c] = c < nc ? p[(size_t)c * m] : make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int c = 0; c < 16; ++c)
-                        w[c] = c0 + c < nc ? p[(size_t)(c0 + c) * m] : make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int c = 0; c < 16; ++c)
-                        if (c0 + c < nc) p[(size_t)(c0 + c) * m] = df_sub(w[c], acc[c0 + c]);
-                }
+                for (int c = 0; c < 32; ++c)
+                    if (c < nc) p[(size_t)c * m] = df_sub(w[c], acc[c]);
             }
             if (t < nmine) {
                 const int j0 = tile_j0(t);
@@ -957,9 +964,15 @@ k_blk_update_tp(const SysDesc *__restrict__ sys, float2 *__restrict__ ws, int k,
                         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
-                            float2 x = make_float2(__uint_as_float(v[S - 1][c]) * pow2f(-7 * (S - 1)), 0.f);
+                            // levels 3 .. S-1 in plain FP32 (their roundings stay near 2^-24
+                            // of level 3, far below the digit truncation), the rest in df32
+                            constexpr int G3 = S > 3 ? 3 : S - 1;
+                            float lo = __uint_as_float(v[S - 1][c]) * pow2f(-7 * (S - 1));
 #pragma unroll
-                            for (int g = S - 2; g >= 0; --g)
+                            for (int g = S - 2; g >= G3; --g) lo = fmaf(__uint_as_float(v[g][c]), pow2f(-7 * g), lo);
+                            float2 x = make_float2(lo, 0.f);
+#pragma unroll
+                            for (int g = G3 - 1; g >= 0; --g)
                                 x = df_add_f(x, __uint_as_float(v[g][c]) * pow2f(-7 * g));
                             acc[c0 + c] = df_scale(x, fe + s_re[sg][32 * h + c0 + c] - 12);
                         }

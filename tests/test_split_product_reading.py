@@ -100,3 +100,48 @@ def test_merged_low_levels_stay_below_the_truncation():
     # the same bound as six exact levels
     P6, _, _ = split_product(A, B, S)
     assert (np.abs(P - A @ B.T) / scale).max() < 4 * (np.abs(P6 - A @ B.T) / scale).max() + 2.0 ** -44
+
+
+def _two_sum32(a, b):
+    s = (a + b).astype(np.float32)
+    bb = (s - a).astype(np.float32)
+    e = ((a - (s - bb)).astype(np.float32) + (b - bb).astype(np.float32)).astype(np.float32)
+    return s, e
+
+
+def _df_add_f32(hi, lo, b):
+    """(hi, lo) + b in double-float: FP32 two-sum, then the low parts, renormalised."""
+    s, e = _two_sum32(hi, b)
+    e = (e + lo).astype(np.float32)
+    h = (s + e).astype(np.float32)
+    return h, (e - (h - s)).astype(np.float32)
+
+
+def test_recombination_with_the_low_levels_summed_in_fp32():
+    """The bulk update's recombination of the six exact level sums: levels 5, 4, 3 added in
+    plain FP32 (scaled by 2^-35, 2^-28, 2^-21: roundings near 2^-24 of level 3), then
+    levels 2, 1, 0 added in double-float.  Against the exact recombination in FP64 the
+    error stays below 2^-47 of the product bound |A| |B| K (64 x 64 x K in digit units),
+    far under the 2^-42 truncation of S = 6 digits; with level 2 also in plain FP32 it
+    would reach that truncation."""
+    S, K = 6, 512
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((32, K)) * np.exp2(rng.integers(-6, 6, (32, 1)))
+    B = rng.standard_normal((24, K))
+    _, levels, exact = split_product(A, B, S)
+    lv = [lvl.astype(np.float32) for lvl in levels]
+    ref = sum(exact[g] * 2.0 ** (-7 * g) for g in range(S))
+    scale = 64.0 * 64.0 * K  # the product bound in digit units
+
+    def combine(n_plain):
+        lo = np.zeros_like(lv[0])
+        for g in range(S - 1, S - 1 - n_plain, -1):
+            lo = (lo + lv[g] * np.float32(2.0 ** (-7 * g))).astype(np.float32)
+        hi, lo2 = lo, np.zeros_like(lo)
+        for g in range(S - 1 - n_plain, -1, -1):
+            hi, lo2 = _df_add_f32(hi, lo2, (lv[g] * np.float32(2.0 ** (-7 * g))).astype(np.float32))
+        return hi.astype(np.float64) + lo2.astype(np.float64)
+
+    assert np.abs(combine(3) - ref).max() < 2.0 ** -47 * scale
+    assert np.abs(combine(1) - ref).max() < 2.0 ** -47 * scale   # all six in double-float
+    assert np.abs(combine(4) - ref).max() > 2.0 ** -45 * scale   # level 2 too: near the truncation
