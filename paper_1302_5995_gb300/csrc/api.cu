@@ -641,6 +641,7 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             bscr.rtile32_max = tu.rtile32_max;
             bscr.early = tu.early != 0;
             bscr.upd_tiles = tu.upd_tiles;
+            bscr.a11first = tu.a11 != 0;
             bscr.sms = device_sms();
             bscr.s3 = la.s3;
             bscr.ev_rr = la.d;
@@ -1044,8 +1045,8 @@ int autotune(const gm_opts &o, const std::shared_ptr<DevPlan> &dp, const std::ve
             bt = std::min(bt, ms);
         }
         if (debug_on())
-            fprintf(stderr, "gm: autotune rtile32_max %d early %d tc_min_k %d upd_tiles %d: %.3f ms\n",
-                    t.rtile32_max, t.early, t.tc_min_k, t.upd_tiles, bt);
+            fprintf(stderr, "gm: autotune rtile32_max %d early %d a11 %d tc_min_k %d upd_tiles %d: %.3f ms\n",
+                    t.rtile32_max, t.early, t.a11, t.tc_min_k, t.upd_tiles, bt);
         return bt;
     };
     best = Tune();
@@ -1071,6 +1072,15 @@ int autotune(const gm_opts &o, const std::shared_ptr<DevPlan> &dp, const std::ve
                 best = t;
             }
         }
+    if (o.precision == GM_PREC_MIXED) {
+        Tune t = best;
+        t.a11 = !best.a11;
+        const double x = time_of(t);
+        if (x < tb) {
+            tb = x;
+            best = t;
+        }
+    }
     if (o.precision == GM_PREC_MIXED) {
         Tune t = best;
         t.early = !best.early;
@@ -1125,7 +1135,7 @@ std::shared_ptr<GraphEntry> find_graph(const TuneKey &k, const Tune &t) {
     std::lock_guard<std::mutex> lk(g_graph_mu);
     for (auto &e : g_graphs)
         if (e->key == k && e->tune.rtile32_max == t.rtile32_max && e->tune.tc_min_k == t.tc_min_k &&
-            e->tune.early == t.early && e->tune.upd_tiles == t.upd_tiles) {
+            e->tune.early == t.early && e->tune.upd_tiles == t.upd_tiles && e->tune.a11 == t.a11) {
             e->last_use = ++g_graph_tick;
             return e;
         }

@@ -1214,7 +1214,11 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
             return e;
         return cudaGetLastError();
     }
-    bool pending = false;  // the rest of the previous step's update still runs on s2
+    bool pending = false;       // the rest of the previous step's update still runs on s2
+    bool next_pending = false;  // the previous step's next-block update still runs on s3
+    // A11-first: the chain updates only the next pivot block's diagonal tile before that
+    // block's factor; the rest of the next-block update runs on s3 beside the factor
+    const bool a11 = la && scr.a11first && scr.s3;
     for (int k = 0; k < max_m; k += NBK) {
         const int par = (k / NBK) & 1;
         double fl_fac = 0, fl_r = 0, fl_upd = 0, fl_next = 0;
@@ -1243,9 +1247,14 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
         kt.end(c);
         // R writes digit set `par`, which the rest of the update two steps back read: that
         // finished before the previous step's next-block update (below) started
+        bool pdl_r = !kt.timed(GM_K_PANEL) && !kt.timed(GM_K_PIVROWS);
+        if (next_pending) {  // R reads the pivot rows and the F column the s3 update writes
+            if ((e = cudaStreamWaitEvent(c, scr.ev_next, 0)) != cudaSuccess) return e;
+            next_pending = false;
+            pdl_r = false;
+        }
         kt.begin(GM_K_PIVROWS, fl_r, c);
         // 32-column R tiles while the step would leave most SMs idle
-        const bool pdl_r = !kt.timed(GM_K_PANEL) && !kt.timed(GM_K_PIVROWS);
         if (nsys * cb <= scr.rtile32_max) {
             const int cb32 = (cols + 31) / 32;
             BLK_SPLIT_DISPATCH(split, (e = launch_k(pdl_r, k_blk_rfused<SS, 1>, dim3(cb32 + rb, nsys),
@@ -1267,6 +1276,7 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
         // this step's update rewrites tiles the rest of the previous step's update touches
         if (pending) {
             if ((e = cudaStreamWaitEvent(c, scr.ev_rest, 0)) != cudaSuccess) return e;
+            if (a11 && cb >= 2 && (e = cudaStreamWaitEvent(scr.s3, scr.ev_rest, 0)) != cudaSuccess) return e;
             pending = false;
         }
         if (!la || cb < 2) {
@@ -1278,11 +1288,33 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
         // look-ahead: everything the next factor and R kernel read (the next block's
         // columns and its pivot rows) on s1, the rest on s2, overlapping the next factor and
         // R kernel (disjoint tiles, the other digit set)
-        kt.begin(GM_K_GJUPDATE, fl_next, c);
-        BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(nrt + cb - 1, 1, nsys), TILE_THREADS, usm, c>>>(
-                                      d_sys, ws, k, UPD_NEXT, nrt, scr.fdig[par], scr.fplane, scr.fex[par],
-                                      scr.rdig[par], scr.cplane, scr.rex[par])));
-        kt.end(c);
+        if (a11) {
+            // chain: the next pivot block's diagonal tile only, so that its factor starts
+            // at once; s3: the rest of its column and of its row band (read by the next R
+            // kernel, which waits for it)
+            double fl_t = 0;
+            for (const SysDesc &S : h_sys)
+                if (k + NBK < S.m) fl_t += 2.0 * std::min(NBK, S.m - k) * 64.0 * std::min(64, S.m - k - NBK);
+            kt.begin(GM_K_GJUPDATE, fl_t, c);
+            BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(1, 1, nsys), TILE_THREADS, usm, c>>>(
+                                          d_sys, ws, k, UPD_A11, nrt, scr.fdig[par], scr.fplane, scr.fex[par],
+                                          scr.rdig[par], scr.cplane, scr.rex[par])));
+            kt.end(c);
+            if ((e = cudaStreamWaitEvent(scr.s3, scr.ev_r, 0)) != cudaSuccess) return e;
+            kt.begin(GM_K_GJUPDATE, std::max(0.0, fl_next - fl_t), scr.s3);
+            BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(nrt + cb - 1, 1, nsys), TILE_THREADS, usm, scr.s3>>>(
+                                          d_sys, ws, k, UPD_NEXT2, nrt, scr.fdig[par], scr.fplane, scr.fex[par],
+                                          scr.rdig[par], scr.cplane, scr.rex[par])));
+            kt.end(scr.s3);
+            if ((e = cudaEventRecord(scr.ev_next, scr.s3)) != cudaSuccess) return e;
+            next_pending = true;
+        } else {
+            kt.begin(GM_K_GJUPDATE, fl_next, c);
+            BLK_SPLIT_DISPATCH(split, (k_blk_update<SS><<<dim3(nrt + cb - 1, 1, nsys), TILE_THREADS, usm, c>>>(
+                                          d_sys, ws, k, UPD_NEXT, nrt, scr.fdig[par], scr.fplane, scr.fex[par],
+                                          scr.rdig[par], scr.cplane, scr.rex[par])));
+            kt.end(c);
+        }
         if ((e = cudaStreamWaitEvent(scr.s2, scr.ev_r, 0)) != cudaSuccess) return e;
         kt.begin(GM_K_GJUPDATE, fl_upd - fl_next, scr.s2);
         if ((e = bulk_update(k, UPD_REST, par, scr.s2)) != cudaSuccess) return e;
@@ -1291,6 +1323,7 @@ cudaError_t blk_gj_sweep(const SysDesc *d_sys, const std::vector<SysDesc> &h_sys
         pending = true;
     }
     if (pending && (e = cudaStreamWaitEvent(c, scr.ev_rest, 0)) != cudaSuccess) return e;
+    if (next_pending && (e = cudaStreamWaitEvent(c, scr.ev_next, 0)) != cudaSuccess) return e;
     if (la && ((e = cudaEventRecord(scr.ev_join, c)) != cudaSuccess || (e = cudaStreamWaitEvent(s, scr.ev_join, 0))))
         return e;
     return cudaGetLastError();

@@ -39,6 +39,7 @@ struct BlkScratch {
     // the rest of R, the diagonal tile two blocks ahead and the next band on s3 (high
     // priority), the bulk of the update on s2
     bool early = false;
+    bool a11first = false;  // look-ahead: only the next diagonal tile on the chain (needs s3, ev_next)
     cudaStream_t s3 = nullptr;
     cudaEvent_t ev_rr = nullptr, ev_next = nullptr, ev_rest2[2] = {nullptr, nullptr};
     __nv_bfloat16 *x_dig2 = nullptr, *a11_dig2 = nullptr;  // the factor's second output set

@@ -109,6 +109,7 @@ struct Tune {
     int rtile32_max = 96;  // R kernel: 32-column tiles while systems x 64-column tiles <= this
     int tc_min_k = 192;    // merge update on tcgen05 for interfaces with K >= this (else mma.sync)
     int early = 0;         // blocked sweep: the early-factor schedule (next factor off the R chain)
+    int a11 = 0;           // blocked sweep: only the next diagonal tile on the chain before its factor
     int upd_tiles = 0;     // blocked sweep's bulk update: 64-column tiles per CTA (0 one wave, -1 one per CTA)
 };
 
