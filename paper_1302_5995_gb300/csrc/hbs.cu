@@ -720,10 +720,20 @@ int run_qr(const std::vector<QrDesc> &q, double tol, int margin, DescBuf &db, cu
     return e == cudaSuccess ? GM_OK : GM_ECUDA;
 }
 
-// Sample counts that sufficed for earlier factorisations of a size class (r rounded up
-// to a power of two, node size m): later builds of the same workload start there.
+// Sample counts for a size class (r rounded up to a power of two, node size m): the
+// count the last factorisation of that class needed for its ranks, so that later builds
+// of the same workload start there and a lower-rank workload after a higher-rank one
+// drops back after its first factorisation.
 std::mutex g_hint_mu;
 std::map<std::pair<int, int>, int> g_hint;
+
+// The smallest count of the doubling sequence from HBS_SAMPLES that leaves HBS_OVERSAMPLE
+// columns beyond `rank`.
+int samples_for(int rank) {
+    int l = HBS_SAMPLES;
+    while (l < HBS_MAX_SAMPLES && rank > l - HBS_OVERSAMPLE) l *= 2;
+    return std::min(l, HBS_MAX_SAMPLES);
+}
 
 int size_class(int r) {
     int c = 1;
@@ -747,6 +757,7 @@ int hbs_factor_l(const double *S, int lds, int r, int m, double tol, int l, bool
     H.hi.assign(NN, 0);
     H.k.assign(NN, 0);
     H.max_rank = 0;
+    H.max_trunc = 0;
     H.lo[1] = 0;
     H.hi[1] = r;
     for (int t = 1; t < (1 << L); ++t) {
@@ -807,6 +818,7 @@ int hbs_factor_l(const double *S, int lds, int r, int m, double tol, int l, bool
             if (std::max(tu, tv) > l - HBS_OVERSAMPLE && l < std::min(rows_of(t), sz(1) - sz(t))) return HBS_RETRY;
             H.k[t] = kt;
             H.max_rank = std::max(H.max_rank, kt);
+            H.max_trunc = std::max(H.max_trunc, std::max(tu, tv));
         }
         return GM_OK;
     };
@@ -1079,7 +1091,7 @@ int hbs_factor(const double *S, int lds, int r, int m, double tol, cudaStream_t 
             if (rc == GM_OK) {
                 {
                     std::lock_guard<std::mutex> lk(g_hint_mu);
-                    g_hint[key] = l;
+                    g_hint[key] = std::min(l, samples_for(H.max_trunc));
                 }
                 double res = 0.0;
                 const int rc2 = hbs_residual(S, lds, H, s, &res);
@@ -1289,8 +1301,8 @@ __global__ void k_hbs_gather_offdiag(const MergeDesc *__restrict__ md, const int
 // A_i ~ L_i R_i (A_i rows_i x cols, column-major, ld rows_i) at relative tolerance tol:
 // L_i an orthonormal basis of the range of a Gaussian sample A_i Omega truncated at the
 // first |R_jj| <= tol |R_11| of its pivoted QR, R_i = L_i^T A_i (k_i x cols).  The sample
-// count starts at the last one that sufficed for this size and doubles while a rank comes
-// within HBS_OVERSAMPLE of it.  L_i, R_i come from tmp.
+// count starts at the one the last call for this size needed and doubles while a rank
+// comes within HBS_OVERSAMPLE of it.  L_i, R_i come from tmp.
 int lowrank_n(const std::vector<const double *> &A, const std::vector<int> &rows, int cols, double tol, TempSet &tmp,
               DescBuf &db, cudaStream_t s, std::vector<double *> &L, std::vector<double *> &R, std::vector<int> &k) {
     const size_t na = A.size();
@@ -1339,8 +1351,10 @@ int lowrank_n(const std::vector<const double *> &A, const std::vector<int> &rows
         l = std::min(2 * l, HBS_MAX_SAMPLES);
     }
     {
+        int kmax = 0;
+        for (size_t i = 0; i < na; ++i) kmax = std::max(kmax, k[i]);
         std::lock_guard<std::mutex> lk(g_hint_mu);
-        g_hint[key] = l;
+        g_hint[key] = std::min(l, samples_for(kmax));
     }
     std::vector<GemmDesc> g;
     for (size_t i = 0; i < na; ++i) {

@@ -35,6 +35,7 @@ struct HbsRoot {
     int64_t offG1 = 0;                       // root G_1 = [G_1-system | inverse], q = k_2 + k_3
     int64_t offKK = 0, offWW = 0;            // ghost couplings of the ring (2 ints, 2 doubles per node)
     int max_rank = 0;
+    int max_trunc = 0;      // largest truncation point of a node's samples (sets the sample count)
     double residual = 0.0;  // relative residual of the inverse on random vectors (see hbs_factor)
     double *sig = nullptr;  // conductance networks: the ghosts' link conductivities (4n, owned), which
                             // weight the rows of every apply (the datum is the link current)
