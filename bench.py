@@ -99,7 +99,9 @@ def family_roofline(precision, fam):
                                   f"per algorithmic multiply-add ({SPLIT_DIGITS} digits)")
 # DRAM traffic of the dominant kernel from an ncu capture (profiles/), per launch, with the
 # source digest it was taken at; reported as null once the kernel source changes.
-TRAFFIC = {}
+# gj_update: k_blk_update_tp + k_blk_update, one timed step's 158 launches
+# (profiles/launches_convdiff512_mixed.md).
+TRAFFIC = {"gj_update": (19953860.0, "ae4c7884b0ee")}
 
 
 def dist_env():
