@@ -875,7 +875,8 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
                 cudaGetLastError();
                 return GM_ENOMEM;
             }
-            CK(mx_root_finalize(rws.as<float2>() + sy.off, r.r, r.n, h->T, h->Tdf, h->tdig, h->tex, split, s, kt));
+            CK(mx_root_finalize(rws.as<float2>() + sy.off, r.r, r.n, h->T, h->Tdf, h->tdig, h->tex, split,
+                                stat.as<Status>() + r.problem, (int)dp.stages.size() + 1, s, kt));
         }
     }
     stamp();

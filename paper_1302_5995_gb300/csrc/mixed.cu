@@ -701,12 +701,16 @@ __global__ void k_mx_root_assemble(const float2 *__restrict__ S, int r, int n, f
 }
 
 // T[k, k'] = (delta - X[ring(k), k']) (n+1): FP64 for the user, df32 for the apply.
+// A non-finite entry of T (a Schur complement that left the double-float range, which is
+// FP32's, on the way) is reported like a non-finite pivot: GM_ESINGULAR at the root stage,
+// so that the automatic mode rebuilds the problem in FP64.
 __global__ void k_mx_root_finalize(const float2 *__restrict__ ws, int r, int n, double *__restrict__ T,
-                                   float2 *__restrict__ Tdf) {
+                                   float2 *__restrict__ Tdf, Status *__restrict__ st, int stage) {
     const int nb4 = 4 * n;
     const int64_t tot = (int64_t)nb4 * nb4;
     const float2 *X = ws + (size_t)r * r;
     const float inv_h = (float)(n + 1);  // exact for n < 2^24
+    bool bad = false;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
         int k = (int)(e % nb4), kp = (int)(e / nb4);
         float2 x = X[(size_t)kp * r + ghost_ring_mx(n, k)];
@@ -714,7 +718,9 @@ __global__ void k_mx_root_finalize(const float2 *__restrict__ ws, int r, int n, 
         v = df_mul(v, make_float2(inv_h, 0.f));
         Tdf[e] = v;
         T[e] = df_to_d(v);
+        bad |= !isfinite(v.x) || !isfinite(v.y);
     }
+    if (bad && st && atomicCAS(&st->code, 0, GM_ESINGULAR) == 0) st->where = stage;
 }
 
 // ----------------------------------------------------------------------------- apply
@@ -937,12 +943,12 @@ cudaError_t mx_root_assemble(const float2 *S, int r, int n, float2 *ws, const do
 int mx_kpad(int N) { return (N + 15) / 16 * 16; }
 
 cudaError_t mx_root_finalize(const float2 *ws, int r, int n, double *T, float2 *Tdf, __nv_bfloat16 *tdig, int *tex,
-                             int split, cudaStream_t s, KTimer &kt) {
+                             int split, Status *st, int stage, cudaStream_t s, KTimer &kt) {
     const int N = 4 * n, kpad = mx_kpad(N);
     int64_t tot = (int64_t)N * N;
     int bx = (int)std::min<int64_t>((tot + 1023) / 1024, 8192);
     kt.begin(GM_K_ROOT, 0.0, s);
-    k_mx_root_finalize<<<bx, 256, 0, s>>>(ws, r, n, T, Tdf);
+    k_mx_root_finalize<<<bx, 256, 0, s>>>(ws, r, n, T, Tdf, st, stage);
     MX_SPLIT_DISPATCH(split, (k_mx_slice_T<SS><<<(N + 3) / 4, 128, 0, s>>>(Tdf, N, kpad, tdig, (int64_t)N * kpad,
                                                                            tex)));
     kt.end(s);

@@ -42,8 +42,10 @@ cudaError_t mx_merge_update(const MergeDesc *md, const std::vector<MergeDesc> &h
 cudaError_t mx_root_assemble(const float2 *S, int r, int n, float2 *ws, const double *b, const double *c,
                              const double *d, cudaStream_t s, KTimer &kt);
 int mx_kpad(int N);
+// T, its df32 copy and T's digit planes from the solved root system; a non-finite entry
+// of T sets st->code = GM_ESINGULAR (where = stage).
 cudaError_t mx_root_finalize(const float2 *ws, int r, int n, double *T, float2 *Tdf, __nv_bfloat16 *tdig, int *tex,
-                             int split, cudaStream_t s, KTimer &kt);
+                             int split, Status *st, int stage, cudaStream_t s, KTimer &kt);
 // One operator of a grouped split-product apply: V (N x B, FP64) = T G from T's digit
 // planes (tdig, tex: N x kpad per plane, built with the handle) and G (FP64), sliced into
 // gdig / gex (gplane elements per plane, at least B * kpad; B exponents).

@@ -160,3 +160,22 @@ def test_mixed_long_interface_matches_oracle_at_1100(gm):
     assert rel_mat(T, To) < TOL_MIXED
     ref = gm.build(b, c, d, n, leaf)
     assert rel_mat(ref.dtn(), To) < 1e-9
+
+
+def test_non_finite_mixed_result_is_caught(gm):
+    """Diffusion-Convection II (b = 1000) at 512 x 512: the mixed build's block-local
+    elimination leaves the double-float range on the way and its T is not finite.  The
+    root reports that like a non-finite pivot: the automatic mode rebuilds the problem in
+    FP64 (and matches the FP64 build), a build with block pivoting forced returns
+    GM_ESINGULAR instead of NaN."""
+    import numpy as np
+    n, leaf = 512, 16
+    f = inputs.paper_problem("diffconv2", n)
+    op = gm.build(*f, n, leaf, precision=gm.PREC_MIXED)
+    T = op.dtn()
+    assert np.isfinite(T).all()
+    assert op.info()["pivot_fallback"] == 1
+    assert rel_mat(T, gm.build(*f, n, leaf).dtn()) < 1e-13
+    with pytest.raises(gm.GmError) as e:
+        gm.build(*f, n, leaf, precision=gm.PREC_MIXED, pivoting=gm.PIVOT_BLOCK)
+    assert e.value.code == gm.GM_ESINGULAR
