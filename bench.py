@@ -694,6 +694,67 @@ def run_bodyloads(args):
                       "results": res}), flush=True)
 
 
+# The paper's Table nested_times (Matlab, 2.4 GHz laptop; its n counts the boundary):
+# (problem, n) -> (T_build s, T_solve s) of the accelerated build at local tolerance 1e-7.
+PAPER_TIMES = {("laplace", 512): (13.44, 0.013), ("laplace", 1024): (45.25, 0.027),
+               ("laplace", 2048): (135.01, 0.058), ("laplace", 4096): (450.73, 0.107),
+               ("helmholtz4", 512): (50.78, 0.013), ("helmholtz4", 1024): (193.58, 0.027),
+               ("helmholtz4", 2048): (765.35, 0.056), ("helmholtz4", 4096): (3167.56, 0.115)}
+
+
+def run_paper_times(args):
+    """The paper's timing table (Table nested_times): Laplace and Helmholtz IV (40 points
+    per wavelength) at n = 512 ... 4096, leaf 16.  For each: the accelerated build at
+    local tolerance 1e-7 (HBS for merges with shared edge >= 128 and the root, FP64
+    merges) and the solve of one boundary vector, then the dense build (mixed precision
+    with the automatic FP64 fallback) and its one-vector solve; the accelerated operator's
+    relative error against the dense one on four Gaussian vectors.  The paper's own times
+    ride along as context.  One JSON line (not the headline)."""
+    import numpy as np
+    import torch
+    from paper_1302_5995_gb300 import build_ext, inputs
+    build_ext.build()
+    import paper_1302_5995_gb300 as gm
+
+    ns = [int(x) for x in args.sizes.split(",")]
+    res = {}
+    for name in ("laplace", "helmholtz4"):
+        for n in ns:
+            b, c, d = (torch.from_numpy(x).cuda() for x in inputs.paper_problem(name, n))
+            reps = 3 if n <= 1024 else 1
+            G = torch.from_numpy(np.ascontiguousarray(inputs.gaussian_vectors(n, 4, 51).T)).cuda()
+            g1 = G[:1].contiguous()
+            hbs = lambda: gm.build(b, c, d, n, 16, tol=1e-7, hbs_leaf=64, hbs_min_edge=128)
+            row = {"paper_build_s": PAPER_TIMES[(name, n)][0], "paper_solve_s": PAPER_TIMES[(name, n)][1]}
+            try:
+                op = hbs()
+            except gm.GmError as e:
+                row["hbs_error"] = str(e)
+                res[f"{name}_{n}"] = row
+                continue
+            row["hbs_build_ms"] = _timed(hbs, reps)
+            row["hbs_solve_one_ms"] = _timed(lambda: op.solve(g1), 10)
+            inf = op.info()
+            row["hbs_fallbacks"] = inf["hbs_fallbacks"]
+            row["hbs_max_rank"] = inf["hbs_max_rank"]
+            row["hbs_M_MB"] = inf["hbs_operator_bytes"] / 2**20
+            Vh = op.solve(G).cpu().numpy()
+            op.free()
+            dense = lambda: gm.build(b, c, d, n, 16, precision=gm.PREC_MIXED)
+            od = dense()
+            row["dense_build_ms"] = _timed(dense, reps)
+            row["dense_solve_one_ms"] = _timed(lambda: od.solve(g1), 10)
+            row["dense_in_fp64"] = bool(od.info()["pivot_fallback"])
+            Vd = od.solve(G).cpu().numpy()
+            od.free()
+            row["hbs_rel_err_vs_dense"] = float((np.linalg.norm(Vh - Vd, axis=1) / np.linalg.norm(Vd, axis=1)).max())
+            res[f"{name}_{n}"] = row
+    print(json.dumps({"workload": "paper_times", "leaf": 16, "tol": 1e-7, "timing": "host, synced, median",
+                      "data": "synthetic (the paper's analytic fields)",
+                      "note": "the paper's n counts the boundary (h = 1/(n-1)); here n unknowns per side",
+                      "results": res}), flush=True)
+
+
 def _fields_dev(cfg, dev=None):
     import torch
     return [torch.from_numpy(cfg[k]).to(dev or "cuda") for k in ("b", "c", "d")]
@@ -911,12 +972,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gm", "reference"], default="gm")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
-    ap.add_argument("--workload", choices=["build", "cfg3", "batch", "serving", "problemset", "errors", "bodyloads"],
+    ap.add_argument("--workload", choices=["build", "cfg3", "batch", "serving", "problemset", "errors", "bodyloads",
+                                           "paper_times"],
                     default="build",
                     help="build: the headline build+solve step; cfg3, batch, serving, problemset, bodyloads: "
                          "other workloads (not the headline)")
     ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--n", type=int, default=1024, help="grid of the errors workload")
+    ap.add_argument("--sizes", default="512,1024,2048,4096", help="grids of the paper_times workload")
     ap.add_argument("--graph", type=int, default=0, help="record each plan's build into a CUDA graph and replay it")
     ap.add_argument("--autotune", type=int, default=0, help="time a few launch shapes on the first build of a plan")
     args = ap.parse_args()
@@ -935,6 +998,8 @@ def main():
     if args.workload == "problemset":
         run_problemset(args)
         return
+    if args.workload == "paper_times":
+        return run_paper_times(args)
     if args.workload == "bodyloads":
         run_bodyloads(args)
         return

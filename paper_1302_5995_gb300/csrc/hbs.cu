@@ -271,14 +271,19 @@ __global__ void __launch_bounds__(256) k_hbs_pqr(const QrDesc *__restrict__ ds, 
 constexpr int QRC_THREADS = 512;
 constexpr int QRC_LOC = HBS_MAX_SAMPLES / 8;  // columns per CTA at the smallest cluster (8)
 constexpr int QRC_MAXP = 8000;                // rows: 3 p doubles of dynamic shared memory
+constexpr int QRC_MAXP_G = 1 << 20;           // rows with the vectors in global memory instead
 
+// gscr == nullptr: the CTA's q vector and its two part buffers live in dynamic shared
+// memory (p <= QRC_MAXP) and the others' parts are read through distributed shared
+// memory; otherwise CTA b keeps them in global memory at gscr + b * 3 * pstride (taller
+// samples, up to QRC_MAXP_G rows) and reads the others' parts from there.
 __global__ void __launch_bounds__(QRC_THREADS) k_hbs_pqr_cl(const QrDesc *__restrict__ ds, double tol, int kmax,
-                                                           int margin) {
+                                                           int margin, double *__restrict__ gscr, int pstride) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const int cs = (int)cl.num_blocks(), cr = (int)cl.block_rank();
     const QrDesc D = ds[blockIdx.x / cs];
-    extern __shared__ double smx[];  // qv[p], part[2][p]
+    extern __shared__ double smx[];  // qv[p], part[2][p] (without gscr)
     __shared__ double nrm[QRC_LOC];
     __shared__ unsigned char used[QRC_LOC];
     __shared__ double coef[QRC_LOC];
@@ -288,7 +293,10 @@ __global__ void __launch_bounds__(QRC_THREADS) k_hbs_pqr_cl(const QrDesc *__rest
     __shared__ int s_piv;
     __shared__ double s_best, s_inv;
     const int p = D.p, l = D.l, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    double *qv = smx, *part = smx + p;
+    double *const mine = gscr ? gscr + (size_t)blockIdx.x * 3 * pstride : smx;
+    double *qv = mine, *part = mine + p;
+    // global mode: the first CTA of this cluster's vectors (rank q's are q * 3 pstride on)
+    const double *gbase = gscr ? gscr + (size_t)(blockIdx.x - cr) * 3 * pstride + p : nullptr;
     const int nloc = cr < l ? (l - cr + cs - 1) / cs : 0;
     // my columns into the work copy, with their norms
     for (int i = warp; i < nloc; i += nw) {
@@ -372,13 +380,19 @@ __global__ void __launch_bounds__(QRC_THREADS) k_hbs_pqr_cl(const QrDesc *__rest
         for (int x = tid; x < p; x += blockDim.x) {
             double v = 0.0;
             for (int t = 0; t < nq; ++t) v = fma(coef[t], __ldcg(D.Q + x + (size_t)(cr + cs * t) * D.ldq), v);
-            pb[x] = v;
+            if (gscr) __stcg(pb + x, v);
+            else pb[x] = v;
         }
+        if (gscr) __threadfence();
         cl.sync();
         double ss = 0.0;
         for (int x = tid; x < p; x += blockDim.x) {
             double v = qv[x];
-            for (int q = 0; q < cs; ++q) v -= cl.map_shared_rank(pb, q)[x];
+            if (gscr) {
+                for (int q = 0; q < cs; ++q) v -= __ldcg(gbase + (size_t)q * 3 * pstride + (size_t)buf * p + x);
+            } else {
+                for (int q = 0; q < cs; ++q) v -= cl.map_shared_rank(pb, q)[x];
+            }
             qv[x] = v;
             ss = fma(v, v, ss);
         }
@@ -684,7 +698,7 @@ int run_qr(const std::vector<QrDesc> &q, double tol, int margin, DescBuf &db, cu
         maxp = std::max(maxp, d.p);
         maxl = std::max(maxl, d.l);
     }
-    if (maxp > QRC_MAXP || maxl > HBS_MAX_SAMPLES) return GM_EUNSUPPORTED;
+    if (maxp > QRC_MAXP_G || maxl > HBS_MAX_SAMPLES) return GM_EUNSUPPORTED;
     int rc = db.ensure(q.size() * sizeof(QrDesc), s);
     if (rc) return rc;
     HCK(cudaMemcpyAsync(db.p, q.data(), q.size() * sizeof(QrDesc), cudaMemcpyHostToDevice, s));
@@ -696,7 +710,15 @@ int run_qr(const std::vector<QrDesc> &q, double tol, int margin, DescBuf &db, cu
         HCK(cudaGetLastError());
         return GM_OK;
     }
-    const size_t sm = (size_t)3 * maxp * sizeof(double);
+    // samples taller than QRC_MAXP rows keep the per-CTA vectors in global memory (for at
+    // most 16 CTAs per factorisation)
+    const bool glob = maxp > QRC_MAXP;
+    double *gscr = nullptr;
+    if (glob && cudaMallocAsync((void **)&gscr, q.size() * 16 * 3 * (size_t)maxp * sizeof(double), s) != cudaSuccess) {
+        cudaGetLastError();
+        return GM_ENOMEM;
+    }
+    const size_t sm = glob ? 0 : (size_t)3 * maxp * sizeof(double);
     HCK(cudaFuncSetAttribute(k_hbs_pqr_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     HCK(cudaFuncSetAttribute(k_hbs_pqr_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaError_t e = cudaErrorInvalidValue;
@@ -713,10 +735,11 @@ int run_qr(const std::vector<QrDesc> &q, double tol, int margin, DescBuf &db, cu
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, k_hbs_pqr_cl, (const QrDesc *)db.p, tol, kmax, margin);
+        e = cudaLaunchKernelEx(&cfg, k_hbs_pqr_cl, (const QrDesc *)db.p, tol, kmax, margin, gscr, maxp);
         if (e == cudaSuccess) break;
         cudaGetLastError();
     }
+    if (gscr) cudaFreeAsync(gscr, s);
     return e == cudaSuccess ? GM_OK : GM_ECUDA;
 }
 
