@@ -174,3 +174,21 @@ def test_unstable_root_inverse_falls_back_to_dense(gm):
     assert rel_mat(op.dtn(), To) < 1e-9
     lap = gm.build(*inputs.laplace_fields(n), n, leaf, tol=tol, hbs_leaf=m, hbs_min_edge=1 << 20)
     assert lap.info()["hbs_fallbacks"] == 0 and lap.info()["hbs_levels"] > 0
+
+
+def test_hbs_root_of_4096_uses_the_tall_sample_qr(gm):
+    """At n = 4096 the root ring has 16380 nodes, so the top HBS nodes' samples have
+    more rows (8190) than the cluster QR holds in shared memory; those factorisations keep
+    their vectors in global memory.  A mixed build with an HBS root at tol 1e-8 answers
+    eight Gaussian vectors like the dense mixed build within 100 tol."""
+    import torch
+    n, leaf, tol = 4096, 16, 1e-8
+    b, c, d = (torch.from_numpy(x).cuda() for x in inputs.convection_fields(n))
+    G = torch.from_numpy(np.ascontiguousarray(inputs.gaussian_vectors(n, 8, 9).T)).cuda()
+    dense = gm.build(b, c, d, n, leaf, precision=gm.PREC_MIXED)
+    Vd = dense.solve(G).cpu().numpy().T
+    dense.free()
+    op = gm.build(b, c, d, n, leaf, tol=tol, hbs_leaf=64, precision=gm.PREC_MIXED)
+    assert op.info()["hbs_levels"] > 0 and op.info()["hbs_fallbacks"] == 0
+    V = op.solve(G).cpu().numpy().T
+    assert rel_vec(V, Vd) < 100 * tol
