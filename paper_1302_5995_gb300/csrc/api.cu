@@ -18,6 +18,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -38,6 +39,64 @@ namespace {
 bool debug_on() {
     static const bool on = getenv("GM_DEBUG") != nullptr;
     return on;
+}
+
+// Runs job(j, stream) for j in [0, count) on up to kMaxLanes host threads, each with a
+// stream of its own (created once per device) that first waits for what `s` has queued;
+// `s` then waits for all of them.  For independent, host-synchronising work (the HBS
+// factorisations of the merges of a stage).  Returns GM_ECUDA if the streams or events
+// could not be set up; the jobs report their own results.
+constexpr int kMaxLanes = 16;
+template <class Job>
+int run_lanes(int count, cudaStream_t s, Job job) {
+    struct Lanes {
+        cudaStream_t st[kMaxLanes] = {};
+        cudaEvent_t done[kMaxLanes] = {};
+        cudaEvent_t start = nullptr;
+        bool ok = false;
+    };
+    static std::mutex mu;
+    static std::map<int, Lanes> by_dev;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return GM_ECUDA;
+    }
+    Lanes *L;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        L = &by_dev[dev];
+        if (!L->ok) {
+            bool good = cudaEventCreateWithFlags(&L->start, cudaEventDisableTiming) == cudaSuccess;
+            for (int i = 0; good && i < kMaxLanes; ++i)
+                good = cudaStreamCreateWithFlags(&L->st[i], cudaStreamNonBlocking) == cudaSuccess &&
+                       cudaEventCreateWithFlags(&L->done[i], cudaEventDisableTiming) == cudaSuccess;
+            if (!good) {
+                cudaGetLastError();
+                return GM_ECUDA;
+            }
+            L->ok = true;
+        }
+    }
+    // one build at a time uses the lanes of a device
+    static std::mutex use_mu;
+    std::lock_guard<std::mutex> use(use_mu);
+    const int nl = std::min(count, kMaxLanes);
+    if (cudaEventRecord(L->start, s) != cudaSuccess) return GM_ECUDA;
+    for (int i = 0; i < nl; ++i)
+        if (cudaStreamWaitEvent(L->st[i], L->start, 0) != cudaSuccess) return GM_ECUDA;
+    std::atomic<int> next(0);
+    std::vector<std::thread> th;
+    for (int i = 0; i < nl; ++i)
+        th.emplace_back([&, i] {
+            cudaSetDevice(dev);
+            for (int j = next++; j < count; j = next++) job(j, L->st[i]);
+            cudaEventRecord(L->done[i], L->st[i]);
+        });
+    for (auto &t : th) t.join();
+    for (int i = 0; i < nl; ++i)
+        if (cudaStreamWaitEvent(s, L->done[i], 0) != cudaSuccess) return GM_ECUDA;
+    return GM_OK;
 }
 
 // Multiprocessors of the current device (looked up once per device).
@@ -706,22 +765,56 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
             std::vector<SysDesc> dense;
             std::vector<int> hbs_idx;  // merges of this stage solved by the accelerated merge
             bool any_hbs = false;
+            std::vector<int> cand;     // merges that try the accelerated Step 1
             for (int i = 0; i < ds.nm; ++i) {
                 const MergeDesc &md = hs.merges[i];
-                if (tol > 0.0 && md.sp + 2 >= o.hbs_min_edge && md.sp > o.hbs_leaf) {
+                if (tol > 0.0 && md.sp + 2 >= o.hbs_min_edge && md.sp > o.hbs_leaf) cand.push_back(i);
+            }
+            std::vector<int> crc(cand.size(), GM_OK);
+            if (cand.size() > 1 && !kt.on) {
+                // the merges are independent and each factorisation is a chain of small
+                // launches and host synchronisations: run them side by side
+                std::vector<int> rk(cand.size(), 0);
+                std::vector<double> fl(cand.size(), 0.0);
+                std::vector<std::map<std::pair<int, int>, int>> hints(cand.size());
+                hbs_hints_freeze();
+                rc = run_lanes((int)cand.size(), s, [&](int j, cudaStream_t ls) {
+                    const MergeDesc &md = hs.merges[cand[j]];
+                    hbs_hints_record(&hints[j]);
+                    hbs_flops_take();
+                    crc[j] = hbs_block_solve(ws.as<double>() + ds.h_sys[cand[j]].off, md.sp, md.rp, o.hbs_leaf,
+                                             tol, ls, &rk[j]);
+                    fl[j] = hbs_flops_take();
+                    hbs_hints_record(nullptr);
+                });
+                hbs_hints_thaw(hints);
+                if (rc) return rc;
+                for (size_t j = 0; j < cand.size(); ++j) {
+                    hbs_rank = std::max(hbs_rank, rk[j]);
+                    kt.flops[GM_K_PANEL] += fl[j];
+                    kt.launches[GM_K_PANEL] += 1;
+                }
+            } else {
+                for (size_t j = 0; j < cand.size(); ++j) {
+                    const MergeDesc &md = hs.merges[cand[j]];
                     hbs_flops_take();
                     kt.begin(GM_K_PANEL, 0.0, s);
-                    rc = hbs_block_solve(ws.as<double>() + ds.h_sys[i].off, md.sp, md.rp, o.hbs_leaf, tol, s,
-                                         &hbs_rank);
+                    crc[j] = hbs_block_solve(ws.as<double>() + ds.h_sys[cand[j]].off, md.sp, md.rp, o.hbs_leaf, tol,
+                                             s, &hbs_rank);
                     kt.end(s);
                     kt.flops[GM_K_PANEL] += hbs_flops_take();
-                    if (rc == GM_OK) {
+                }
+            }
+            for (int i = 0, j = 0; i < ds.nm; ++i) {
+                if (j < (int)cand.size() && cand[j] == i) {
+                    const int r2 = crc[j++];
+                    if (r2 == GM_OK) {
                         ++hbs_merges;
                         any_hbs = true;
                         hbs_idx.push_back(i);
                         continue;
                     }
-                    if (rc != GM_EUNSUPPORTED && rc != HBS_UNSTABLE) return rc;
+                    if (r2 != GM_EUNSUPPORTED && r2 != HBS_UNSTABLE) return r2;
                     ++hbs_fallbacks;
                 }
                 dense.push_back(ds.h_sys[i]);
@@ -766,13 +859,40 @@ int run_build(const gm_opts &o, double tol, const std::shared_ptr<DevPlan> &dpp,
                     CK(launch_merge_update(dsub.as<MergeDesc>(), dm, ds.d_tab, A64, ws.as<double>(), A64, mrp, db, dc,
                                            dd, 0, s, kt));
                 }
-                for (int i : hbs_idx) {
-                    hbs_flops_take();
-                    if ((rc = hbs_merge_lowrank(hs.merges[i], ds.d_merges + i, ds.d_tab, A64,
-                                                ws.as<double>() + ds.h_sys[i].off, A64, db, dc, dd, tol, s, kt,
-                                                &hbs_lr_rank)))
-                        return rc;
-                    kt.flops[GM_K_MERGEUPDATE] += hbs_flops_take();
+                if (hbs_idx.size() > 1 && !kt.on) {  // side by side, like Step 1
+                    const size_t nh = hbs_idx.size();
+                    std::vector<int> lrc(nh, GM_OK), rk(nh, 0);
+                    std::vector<double> fl(nh, 0.0);
+                    std::vector<std::map<std::pair<int, int>, int>> hints(nh);
+                    hbs_hints_freeze();
+                    rc = run_lanes((int)nh, s, [&](int j, cudaStream_t ls) {
+                        const int i = hbs_idx[j];
+                        KTimer lkt;  // untimed: only its flop count is kept
+                        hbs_hints_record(&hints[j]);
+                        hbs_flops_take();
+                        lrc[j] = hbs_merge_lowrank(hs.merges[i], ds.d_merges + i, ds.d_tab, A64,
+                                                   ws.as<double>() + ds.h_sys[i].off, A64, db, dc, dd, tol, ls, lkt,
+                                                   &rk[j]);
+                        fl[j] = hbs_flops_take() + lkt.flops[GM_K_MERGEUPDATE];
+                        hbs_hints_record(nullptr);
+                    });
+                    hbs_hints_thaw(hints);
+                    if (rc) return rc;
+                    for (size_t j = 0; j < nh; ++j) {
+                        if (lrc[j]) return lrc[j];
+                        hbs_lr_rank = std::max(hbs_lr_rank, rk[j]);
+                        kt.flops[GM_K_MERGEUPDATE] += fl[j];
+                        kt.launches[GM_K_MERGEUPDATE] += 1;
+                    }
+                } else {
+                    for (int i : hbs_idx) {
+                        hbs_flops_take();
+                        if ((rc = hbs_merge_lowrank(hs.merges[i], ds.d_merges + i, ds.d_tab, A64,
+                                                    ws.as<double>() + ds.h_sys[i].off, A64, db, dc, dd, tol, s, kt,
+                                                    &hbs_lr_rank)))
+                            return rc;
+                        kt.flops[GM_K_MERGEUPDATE] += hbs_flops_take();
+                    }
                 }
             }
         } else {

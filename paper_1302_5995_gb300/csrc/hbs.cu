@@ -749,6 +749,28 @@ int run_qr(const std::vector<QrDesc> &q, double tol, int margin, DescBuf &db, cu
 // drops back after its first factorisation.
 std::mutex g_hint_mu;
 std::map<std::pair<int, int>, int> g_hint;
+// Inside hbs_hints_freeze / hbs_hints_thaw (merges factorised concurrently) a thread reads
+// the hints of the snapshot taken at freeze and records its own in tl_hint_out, so that
+// every merge starts from the same counts whatever the order the threads run in.
+std::map<std::pair<int, int>, int> g_hint_frozen;
+bool g_hint_is_frozen = false;
+thread_local std::map<std::pair<int, int>, int> *tl_hint_out = nullptr;
+
+int hint_get(const std::pair<int, int> &key, int dflt) {
+    std::lock_guard<std::mutex> lk(g_hint_mu);
+    const auto &m = g_hint_is_frozen ? g_hint_frozen : g_hint;
+    auto it = m.find(key);
+    return it != m.end() ? it->second : dflt;
+}
+
+void hint_set(const std::pair<int, int> &key, int v) {
+    if (tl_hint_out) {
+        (*tl_hint_out)[key] = v;
+        return;
+    }
+    std::lock_guard<std::mutex> lk(g_hint_mu);
+    g_hint[key] = v;
+}
 
 // The smallest count of the doubling sequence from HBS_SAMPLES that leaves HBS_OVERSAMPLE
 // columns beyond `rank`.
@@ -1101,21 +1123,13 @@ int hbs_residual(const double *S, int lds, HbsRoot &H, cudaStream_t s, double *r
 int hbs_factor(const double *S, int lds, int r, int m, double tol, cudaStream_t s, HbsRoot &H, bool temp) {
     if (r < 2 || lds < r || m < 2 || m > QR_MAXP || !(tol > 0.0)) return GM_EINVAL;
     const std::pair<int, int> key(size_class(r), m);
-    int l = HBS_SAMPLES;
-    {
-        std::lock_guard<std::mutex> lk(g_hint_mu);
-        auto it = g_hint.find(key);
-        if (it != g_hint.end()) l = it->second;
-    }
+    int l = hint_get(key, HBS_SAMPLES);
     for (;;) {
         release_pool(H);
         const int rc = hbs_factor_l(S, lds, r, m, tol, l, temp, s, H);
         if (rc != HBS_RETRY) {
             if (rc == GM_OK) {
-                {
-                    std::lock_guard<std::mutex> lk(g_hint_mu);
-                    g_hint[key] = std::min(l, samples_for(H.max_trunc));
-                }
+                hint_set(key, std::min(l, samples_for(H.max_trunc)));
                 double res = 0.0;
                 const int rc2 = hbs_residual(S, lds, H, s, &res);
                 H.residual = res;
@@ -1333,12 +1347,7 @@ int lowrank_n(const std::vector<const double *> &A, const std::vector<int> &rows
     R.assign(na, nullptr);
     k.assign(na, 0);
     const std::pair<int, int> key(size_class(cols), -1);
-    int l = HBS_SAMPLES;
-    {
-        std::lock_guard<std::mutex> lk(g_hint_mu);
-        auto it = g_hint.find(key);
-        if (it != g_hint.end()) l = it->second;
-    }
+    int l = hint_get(key, HBS_SAMPLES);
     int *outs = (int *)tmp.get((int64_t)na);
     if (!outs) return GM_ENOMEM;
     for (;;) {
@@ -1376,8 +1385,7 @@ int lowrank_n(const std::vector<const double *> &A, const std::vector<int> &rows
     {
         int kmax = 0;
         for (size_t i = 0; i < na; ++i) kmax = std::max(kmax, k[i]);
-        std::lock_guard<std::mutex> lk(g_hint_mu);
-        g_hint[key] = std::min(l, samples_for(kmax));
+        hint_set(key, std::min(l, samples_for(kmax)));
     }
     std::vector<GemmDesc> g;
     for (size_t i = 0; i < na; ++i) {
@@ -1388,6 +1396,21 @@ int lowrank_n(const std::vector<const double *> &A, const std::vector<int> &rows
     return run_gemms(g, db, s);
 }
 }  // namespace
+
+void hbs_hints_freeze() {
+    std::lock_guard<std::mutex> lk(g_hint_mu);
+    g_hint_frozen = g_hint;
+    g_hint_is_frozen = true;
+}
+
+void hbs_hints_record(std::map<std::pair<int, int>, int> *out) { tl_hint_out = out; }
+
+void hbs_hints_thaw(const std::vector<std::map<std::pair<int, int>, int>> &outs) {
+    std::lock_guard<std::mutex> lk(g_hint_mu);
+    for (const auto &m : outs)
+        for (const auto &kv : m) g_hint[kv.first] = kv.second;  // in the callers' order
+    g_hint_is_frozen = false;
+}
 
 int hbs_merge_lowrank(const MergeDesc &hm, const MergeDesc *d_md, const int *d_tab, const double *in,
                       const double *ws, double *out, const double *bf, const double *cf, const double *df, double tol,

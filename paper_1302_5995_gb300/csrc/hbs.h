@@ -1,6 +1,9 @@
 // HBS root: the root Schur complement compressed to the paper's HBS form (Section 4),
 // inverted by Algorithm 1 (Section 5) and applied by Algorithm 2 in the solve stage.
 #pragma once
+#include <map>
+#include <utility>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -96,6 +99,13 @@ int hbs_gemm(const double *A, int lda, int ta, const double *B, int ldb, int tb,
 // Algorithmic flops of the HBS steps this thread issued since the last call (products,
 // QR factorisations, dense inversions), then reset.
 double hbs_flops_take();
+// Factorisations run concurrently on several host threads (independent merges of a
+// stage): hbs_hints_freeze() makes every sample-count lookup read the hints as they are
+// now; a thread that calls hbs_hints_record(&m) writes its own hints into m instead of the
+// shared table; hbs_hints_thaw(ms) merges the maps in order and ends the freeze.
+void hbs_hints_freeze();
+void hbs_hints_record(std::map<std::pair<int, int>, int> *out);
+void hbs_hints_thaw(const std::vector<std::map<std::pair<int, int>, int>> &outs);
 // Doubles of the operator in HBS form (Section 4), from the node ranks: D, U, V of every
 // leaf, U, V of every inner node below the root, and the two B blocks between the
 // children of every inner node -- the memory the paper reports as M(n).
