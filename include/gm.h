@@ -187,9 +187,15 @@ void gm_opts_default(gm_opts *opts);
  *             solve then applies Algorithm 2 instead of a dense T.  In FP64 builds the
  *             pairwise merges with a shared edge of at least gm_opts.hbs_min_edge nodes
  *             solve their interface system by the accelerated Step 1 (HBS inverses of
- *             S33 and of its Schur complement; merges whose ranks exceed the cap stay
- *             dense).  GM_EUNSUPPORTED if a root node's rank reaches 96 (the root does
- *             not compress enough; build with tol = 0).
+ *             S33 and of its Schur complement) and form the parent from the low-rank
+ *             factors of S13 and S24 (Steps 2-3, eq. matmult); the merges of a stage run
+ *             side by side on host threads.  A merge whose node ranks exceed the cap
+ *             (480, the largest sample count of 512 less its oversampling of 32), or
+ *             whose Algorithm 1 inverse fails its residual check (relative residual above
+ *             1e-3 on four Gaussian vectors), is eliminated densely; so is a root whose
+ *             inverse fails the check (gm_info.hbs_fallbacks counts them).
+ *             GM_EUNSUPPORTED if a root node's rank exceeds the cap (the root does not
+ *             compress enough; build with tol = 0).
  *   out     : receives a new handle that owns all device memory of the operator.
  * Blocks the calling thread until the build has finished on the device.  Temporaries
  * come from a stream-ordered memory pool the library keeps per device; it does not
