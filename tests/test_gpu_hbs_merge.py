@@ -88,3 +88,20 @@ def test_accelerated_merges_cut_the_update_work(gm):
     V = acc.solve(np.ascontiguousarray(G.T)).reshape(8, 4 * n).T
     err = (np.linalg.norm(V - To @ G, axis=0) / np.linalg.norm(To @ G, axis=0)).max()
     assert err < 100 * tol
+
+
+def test_side_by_side_merges_do_not_depend_on_the_order(gm):
+    """The accelerated merges of a stage run on several host threads, in whatever order
+    the threads take them; every merge reads the sample-count hints as they were when
+    the stage began.  Once a workload's hints have settled (the first build), repeated
+    builds give the same operator bit for bit; and it matches the oracle's dense
+    nested dissection within the accelerated build's bound."""
+    n, leaf, m, tol = 384, 16, 32, 1e-9
+    b, c, d = inputs.convection_fields(n, seeds=(31, 32, 33))
+    gm.build(b, c, d, n, leaf, tol=tol, hbs_leaf=m, hbs_min_edge=64)  # settles the hints
+    ops = [gm.build(b, c, d, n, leaf, tol=tol, hbs_leaf=m, hbs_min_edge=64) for _ in range(3)]
+    assert ops[0].info()["hbs_merges"] > 8
+    T = [op.dtn() for op in ops]
+    assert np.array_equal(T[0], T[1]) and np.array_equal(T[0], T[2])
+    To = nd_dense.build(b, c, d, n, leaf).T
+    assert rel_mat(T[0], To) < 100 * tol
