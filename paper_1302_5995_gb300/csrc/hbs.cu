@@ -180,26 +180,38 @@ __global__ void __launch_bounds__(256) k_hbs_pqr(const QrDesc *__restrict__ ds, 
     }
     for (int j = tid; j < l; j += blockDim.x) used[j] = 0;
     __syncthreads();
+    // the columns' squared norms; each step below refreshes them while it removes q
+    for (int c = warp; c < l; c += nw) {
+        double s = 0.0;
+        for (int i = lane; i < p; i += 32) s = fma(sA[(size_t)c * p + i], sA[(size_t)c * p + i], s);
+        s = warp_sum_d(s);
+        if (lane == 0) nrm[c] = s;
+    }
+    __syncthreads();
     int ktr = -1, kval = 0;
     const int steps = min(kmax, min(p, l));
     for (int j = 0; j < steps; ++j) {
-        // norms of the remaining columns, one warp per column
-        for (int c = warp; c < l; c += nw) {
-            double s = 0.0;
-            if (!used[c])
-                for (int i = lane; i < p; i += 32) s = fma(sA[(size_t)c * p + i], sA[(size_t)c * p + i], s);
-            s = warp_sum_d(s);
-            if (lane == 0) nrm[c] = used[c] ? -1.0 : s;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int pv = -1;
-            double best = -1.0;
-            for (int c = 0; c < l; ++c)
-                if (nrm[c] > best) { best = nrm[c]; pv = c; }
-            s_piv = pv;
-            s_r = best > 0.0 ? sqrt(best) : 0.0;
-            if (j == 0) s_r1 = s_r;
+        if (warp == 0) {  // the unused column of largest norm, the lowest on ties
+            double bv = -1.0;
+            int bc = 0x7fffffff;
+            for (int c = lane; c < l; c += 32)
+                if (!used[c] && nrm[c] > bv) {
+                    bv = nrm[c];
+                    bc = c;
+                }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+                if (ov > bv || (ov == bv && oc < bc)) {
+                    bv = ov;
+                    bc = oc;
+                }
+            }
+            if (lane == 0) {
+                s_piv = bv >= 0.0 ? bc : -1;
+                s_r = bv > 0.0 ? sqrt(bv) : 0.0;
+                if (j == 0) s_r1 = s_r;
+            }
         }
         __syncthreads();
         const int pv = s_piv;
@@ -208,26 +220,30 @@ __global__ void __launch_bounds__(256) k_hbs_pqr(const QrDesc *__restrict__ ds, 
         if (pv < 0 || !(rjj > 1e-15 * r11) || !(r11 > 0.0) || (ktr >= 0 && j >= ktr + margin)) break;
         for (int i = tid; i < p; i += blockDim.x) qv[i] = sA[(size_t)pv * p + i];
         __syncthreads();
-        for (int pass = 0; pass < 2; ++pass) {  // q -= Q (Q^T q), twice
-            for (int c = warp; c < j; c += nw) {
-                double s = 0.0;
-                for (int i = lane; i < p; i += 32) s = fma(D.Q[i + (size_t)c * D.ldq], qv[i], s);
-                s = warp_sum_d(s);
-                if (lane == 0) coef[c] = s;
-            }
-            __syncthreads();
-            for (int i = tid; i < p; i += blockDim.x) {
-                double v = qv[i];
-                for (int c = 0; c < j; ++c) v = fma(-coef[c], D.Q[i + (size_t)c * D.ldq], v);
-                qv[i] = v;
-            }
-            __syncthreads();
-        }
-        if (warp == 0) {
+        // the pivot column has had every earlier q removed (below); one more pass
+        // q -= Q (Q^T q) restores the orthogonality the roundings took
+        for (int c = warp; c < j; c += nw) {
             double s = 0.0;
-            for (int i = lane; i < p; i += 32) s = fma(qv[i], qv[i], s);
+            for (int i = lane; i < p; i += 32) s = fma(D.Q[i + (size_t)c * D.ldq], qv[i], s);
             s = warp_sum_d(s);
-            if (lane == 0) s_r = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+            if (lane == 0) coef[c] = s;
+        }
+        __syncthreads();
+        double ss = 0.0;
+        for (int i = tid; i < p; i += blockDim.x) {
+            double v = qv[i];
+            for (int c = 0; c < j; ++c) v = fma(-coef[c], D.Q[i + (size_t)c * D.ldq], v);
+            qv[i] = v;
+            ss = fma(v, v, ss);
+        }
+        ss = warp_sum_d(ss);
+        if (lane == 0) coef[QR_MAXP - 1 - warp] = ss;  // per-warp partial sums (j < QR_MAXP - nw)
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += coef[QR_MAXP - 1 - w];
+            s_r = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+            used[pv] = 1;
         }
         __syncthreads();
         const double inv = s_r;
@@ -235,15 +251,21 @@ __global__ void __launch_bounds__(256) k_hbs_pqr(const QrDesc *__restrict__ ds, 
             qv[i] *= inv;
             D.Q[i + (size_t)j * D.ldq] = qv[i];
         }
-        if (tid == 0) used[pv] = 1;
         __syncthreads();
-        // remove q from every remaining column
+        // remove q from every remaining column and refresh its norm
         for (int c = warp; c < l; c += nw) {
             if (used[c]) continue;
             double s = 0.0;
             for (int i = lane; i < p; i += 32) s = fma(qv[i], sA[(size_t)c * p + i], s);
             s = warp_sum_d(s);
-            for (int i = lane; i < p; i += 32) sA[(size_t)c * p + i] = fma(-s, qv[i], sA[(size_t)c * p + i]);
+            double nn = 0.0;
+            for (int i = lane; i < p; i += 32) {
+                const double v = fma(-s, qv[i], sA[(size_t)c * p + i]);
+                sA[(size_t)c * p + i] = v;
+                nn = fma(v, v, nn);
+            }
+            nn = warp_sum_d(nn);
+            if (lane == 0) nrm[c] = nn;
         }
         __syncthreads();
         kval = j + 1;
