@@ -96,9 +96,13 @@ typedef struct gm_opts {
                          builds of the plan copy their coefficients in, replay the graph
                          and copy the operator out (at most 8 graphs are kept, least
                          recently used dropped)                                         */
-    int autotune;     /* nonzero: the first build of a plan times a few launch shapes (the
-                         R kernel's tile width, the tcgen05 merge-update bound) and keeps
-                         the fastest for every later build of that plan and options     */
+    int autotune;     /* nonzero: the first build of a plan times a few launch shapes and
+                         schedules (the R kernel's tile width, tiles per CTA of the bulk
+                         update, the early-factor and A11-first schedules, the tcgen05
+                         merge-update bound) and keeps the fastest for every later build
+                         of that plan and options.  The environment variable GM_TUNE
+                         (e.g. "early=1,upd_tiles=-1"; keys rtile32_max, tc_min_k, early,
+                         a11, upd_tiles) forces a choice, for testing                    */
 } gm_opts;
 
 /* Pivoting of the mixed-precision dense eliminations.

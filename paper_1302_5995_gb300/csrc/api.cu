@@ -19,6 +19,7 @@
 #include <memory>
 #include <mutex>
 #include <thread>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -97,6 +98,32 @@ int run_lanes(int count, cudaStream_t s, Job job) {
     for (int i = 0; i < nl; ++i)
         if (cudaStreamWaitEvent(s, L->done[i], 0) != cudaSuccess) return GM_ECUDA;
     return GM_OK;
+}
+
+// GM_TUNE (environment, read at every build) forces launch shapes and schedules, so that
+// every variant the autotuner may choose can be tested: comma-separated key=value pairs
+// of rtile32_max, tc_min_k, early, a11, upd_tiles (e.g. "early=1,upd_tiles=-1").
+void tune_override(Tune &t) {
+    const char *env = getenv("GM_TUNE");
+    if (!env || !*env) return;
+    std::string s(env);
+    size_t at = 0;
+    while (at < s.size()) {
+        size_t end = s.find(',', at);
+        if (end == std::string::npos) end = s.size();
+        const std::string kv = s.substr(at, end - at);
+        const size_t eq = kv.find('=');
+        if (eq != std::string::npos) {
+            const std::string key = kv.substr(0, eq);
+            const int v = atoi(kv.c_str() + eq + 1);
+            if (key == "rtile32_max") t.rtile32_max = v;
+            else if (key == "tc_min_k") t.tc_min_k = v;
+            else if (key == "early") t.early = v;
+            else if (key == "a11") t.a11 = v;
+            else if (key == "upd_tiles") t.upd_tiles = v;
+        }
+        at = end + 1;
+    }
 }
 
 // Multiprocessors of the current device (looked up once per device).
@@ -1435,6 +1462,7 @@ int build_subset(const gm_opts &o, double tol, const std::vector<std::pair<int, 
         if ((rc = autotune(o, dp, keys, sb, sc, sd, tu))) return rc;
         store_tune(tk, tu);
     }
+    tune_override(tu);
     if (o.graph && plain) {
         std::shared_ptr<GraphEntry> E = find_graph(tk, tu);
         if (E) return replay(*E, o, keys, sb, sc, sd, total, Hs, code, growth);

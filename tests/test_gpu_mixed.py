@@ -179,3 +179,26 @@ def test_non_finite_mixed_result_is_caught(gm):
     with pytest.raises(gm.GmError) as e:
         gm.build(*f, n, leaf, precision=gm.PREC_MIXED, pivoting=gm.PIVOT_BLOCK)
     assert e.value.code == gm.GM_ESINGULAR
+
+
+@pytest.fixture(scope="module")
+def oracle_256():
+    n, leaf = 256, 16
+    b, c, d = inputs.convection_fields(n, seeds=(41, 42, 43))
+    return (b, c, d, n, leaf), nd_dense.build(b, c, d, n, leaf).T
+
+
+@pytest.mark.parametrize("tune", ["", "early=1", "a11=1", "upd_tiles=-1", "upd_tiles=2", "upd_tiles=4",
+                                  "rtile32_max=0", "rtile32_max=1073741824", "tc_min_k=448",
+                                  "tc_min_k=1073741824", "early=1,upd_tiles=-1"])
+def test_every_schedule_the_autotuner_may_choose(gm, oracle_256, monkeypatch, tune):
+    """The autotuner picks, per plan, among launch shapes and schedules of the blocked
+    sweep (R tile width, tiles per CTA of the pipelined update or the one-tile kernel, the
+    early-factor and A11-first schedules, the tcgen05 threshold of the merge update).
+    Each, forced through GM_TUNE, builds the 256 x 256 convection problem to the mixed
+    bound against O2."""
+    monkeypatch.setenv("GM_TUNE", tune)
+    args, To = oracle_256
+    op = gm.build(*args, precision=gm.PREC_MIXED)
+    assert op.info()["pivot_fallback"] == 0
+    assert rel_mat(op.dtn(), To) < TOL_MIXED
