@@ -35,12 +35,7 @@ constexpr int LDF = NBK + 1;  // padded row length of the df32 shared tiles
 
 // ----------------------------------------------------------------------------- factor
 
-constexpr int FAC_THREADS = 256;
-// The factor's 64 x 128 matrix in shared memory: column c of a row at (c / 32) FCG + c % 32
-// (each 32-column group padded to 36 floats, so the four groups a warp touches at once
-// fall in different banks), rows FML floats apart.
-constexpr int FCG = 36, FML = 4 * FCG + 4;
-
+constexpr int FAC_THREADS = 288;  // 256 update threads and the panel warp
 // Sort key of a pivot candidate in one 32-bit word, for a single warp max-reduction: the
 // top 26 bits are |v| (its float bits with the six lowest cleared; a NaN counts as 0,
 // and 64 is added so every unused row beats a used one), the low six bits 63 - row, so
@@ -88,24 +83,36 @@ __device__ __forceinline__ void slice_rows64(Get get, int r, int seg, __nv_bfloa
     }
 }
 
-// X0 ~ A11^{-1} by Gauss-Jordan on [A11 | I] in FP32 with partial pivoting among the rows
-// of the block, blocked by panels of 8 pivots.  The 64 x 128 augmented matrix lives in
-// registers: thread (row, cg) holds columns 32 cg .. 32 cg + 31 of one row (four threads
-// per row, eight rows per warp).  Rows never move: the pivot of column t is the unused row
-// of largest |entry| (the lowest of rows within 2^-17 of it, see piv_key), and row t of X0
-// is the right half of that row at the end.
+// X0 ~ A11^{-1} by Gauss-Jordan in FP32 with partial pivoting among the rows of the
+// block, blocked by panels of 8 pivots, in place.  Rows never move: the pivot of column t
+// is the unused row p_t of largest |entry| (the lowest of rows within 2^-17 of it, see
+// piv_key).  On [A11 | I] the right-hand column of row p_t changes only from step t on,
+// and step t turns column t of the left half into a unit column, so column t's slot holds
+// the right-hand column of p_t from then on: at the end slot (r, t) is entry (r, p_t) of
+// the right half, and X0(t, i) = slot(p_t, step(i)).
 //
-// One panel (columns t0 .. t0 + 7):
-//   1. every thread stores its values to shared memory (two buffers, alternating);
-//   2. warp 0 eliminates the 64 x 8 panel alone, in registers (two rows per lane, the
-//      pivot found by one warp reduction of the packed keys, the pivot row broadcast by
-//      shuffles), and tracks the panel's combined row transform: with P the 8 pivot rows,
-//      the 8 steps amount to new[r] = [r not in P] old[r] + sum_u T(r, p_u) old[p_u], and
-//      column u of T starts as the unit vector of p_u when p_u is chosen (no earlier step
-//      used that row as a source) and then takes the remaining steps' row operations;
-//   3. every thread applies that rank-8 transform to its 32 columns.
-// Two block barriers per 8 pivots (instead of one per pivot); the arithmetic is the same
-// Gauss-Jordan up to the order of the FP32 roundings.
+// With S_q the 64 x 64 slots after panels 0 .. q - 1, panel q's transform T_q (64 x 8)
+// maps S_q to S_{q+1}: with P the panel's 8 pivot rows, new[r] = [r not in P] old[r] +
+// sum_u T(r, u) old[p_u] on every slot but the panel's own, which become T's columns (the
+// right-hand columns of P, which were unit columns, transform to exactly those).  Column
+// u of T starts as the unit vector of p_u when p_u is chosen (no earlier step used that
+// row as a source) and then takes the remaining steps' row operations.
+//
+// The 256 update threads hold the slots in registers (thread (rp, cg): rows 2 rp, 2 rp + 1,
+// slots 8 cg .. 8 cg + 7); a ninth warp (the panel warp) holds none and runs one panel
+// ahead.  In step k (one block barrier each, k = 0 .. 8):
+//   - the panel warp reads panel k's slots of S_{k-1} and the pivot rows of panel k - 1
+//     from shared memory, applies T_{k-1} to them itself (the same multiply-adds in the
+//     same order as the update threads, so the values are the same), eliminates the
+//     64 x 8 panel in registers (two rows per lane, the pivot found by one warp reduction
+//     of the packed keys, the pivot row broadcast by shuffles) and publishes T_k;
+//   - the update threads apply T_{k-1} (S_{k-1} -> S_k, the pivot rows read from S_{k-1}
+//     in shared memory) and store S_k for the next step.
+// S_q alternates between two shared buffers, T_q between two tables.  The arithmetic is
+// Gauss-Jordan on [A11 | I] with the same roundings, less the work on the unit columns.
+constexpr int FAC_UPD = 256;  // update threads; the panel warp is warp 8
+constexpr int FSL = 68;       // row stride (floats) of the shared slot buffers
+
 template <int S>
 __global__ void __launch_bounds__(FAC_THREADS)
 k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int k, __nv_bfloat16 *__restrict__ x_dig,
@@ -113,154 +120,202 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
              float *__restrict__ pmag, Status *st, int stage) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_wait();
-    float2 *Adf = (float2 *)smem_raw;       // [64][LDF] A11 (df32)
-    float *Xs = (float *)(Adf + 64 * LDF);  // [64][65] rows of X0
+    float2 *Adf = (float2 *)smem_raw;      // [64][LDF] A11 (df32)
+    float *Sb = (float *)(Adf + 64 * LDF);  // two buffers [64][FSL]: S_q in buffer q & 1
+    float *Xs = Sb;                         // [64][65] rows of X0, after the last step
     __shared__ float s_pm[64];
+    __shared__ float TCs[2][64][9];  // T_q in table q & 1
+    __shared__ int Ps[2][8];
+    __shared__ int s_step[64], s_prow[64];
     const SysDesc Sy = sys[blockIdx.x];
     const int m = Sy.m;
     if (k >= m) return;
     const int nbe = min(NBK, m - k);
     const float2 *W = ws + Sy.off;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int row = tid >> 2, cg = tid & 3;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const bool upd = tid < FAC_UPD;
+    const int rp = upd ? tid >> 3 : 0, cg = tid & 7;  // update thread: rows 2 rp + (0, 1), slots 8 cg + (0 .. 7)
     const unsigned FULL = 0xffffffffu;
-    {  // A11, padded with the identity beyond nbe (all loads in flight at once)
-        constexpr int NL = 64 * 64 / FAC_THREADS;
+    constexpr int BUF = 64 * FSL;
+    float a[2][8];
+    if (upd) {  // A11, padded with the identity beyond nbe (all loads in flight at once)
+        constexpr int NL = 64 * 64 / FAC_UPD;
         float2 v[NL];
 #pragma unroll
         for (int q = 0; q < NL; ++q) {
-            const int e = tid + q * FAC_THREADS, i = e % 64, j = e / 64;
+            const int e = tid + q * FAC_UPD, i = e % 64, j = e / 64;
             v[q] = (i < nbe && j < nbe) ? W[(size_t)(k + j) * m + k + i] : make_float2(i == j ? 1.f : 0.f, 0.f);
         }
 #pragma unroll
         for (int q = 0; q < NL; ++q) {
-            const int e = tid + q * FAC_THREADS;
+            const int e = tid + q * FAC_UPD;
             Adf[(e % 64) * LDF + e / 64] = v[q];
         }
     }
     __syncthreads();
-    float a[32];
+    if (upd) {  // S_0 = A11 into buffer 0
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const int c = cg * 32 + j;
-        a[j] = c < 64 ? Adf[row * LDF + c].x : (c - 64 == row ? 1.f : 0.f);
+        for (int rr = 0; rr < 2; ++rr) {
+            const int r = 2 * rp + rr;
+#pragma unroll
+            for (int v = 0; v < 8; ++v) a[rr][v] = Adf[r * LDF + 8 * cg + v].x;
+            *(float4 *)&Sb[r * FSL + 8 * cg] = make_float4(a[rr][0], a[rr][1], a[rr][2], a[rr][3]);
+            *(float4 *)&Sb[r * FSL + 8 * cg + 4] = make_float4(a[rr][4], a[rr][5], a[rr][6], a[rr][7]);
+        }
     }
-    // the matrix for the panel warp [64][FML] (Xs shares its space: X0 is written after
-    // the last panel), and the panel's 8 pivot rows [8][FML] for the update, copied out by
-    // the panel warp, so that the next panel may overwrite the matrix while the update of
-    // this one still reads them
-    float *Mc = Xs, *PRs = Xs + 64 * FML;
-    __shared__ float TCs[64][9];  // the panel's transform T(r, p_u)
-    __shared__ int Ps[8];
-    __shared__ int s_step[64];
-    bool used0 = false, used1 = false;  // warp 0: rows lane and lane + 32 have been pivots
+    __syncthreads();
+    // the panel warp's state: T of the last panel for its rows lane and lane + 32, that
+    // panel's pivot rows, and which of its rows have been pivots
+    float tc[2][8];
+    int pidx[8];
+    bool used0 = false, used1 = false;
 #pragma unroll 1
-    for (int pnl = 0; pnl < 8; ++pnl) {
-        const int t0 = pnl * 8;
-#pragma unroll
-        for (int j = 0; j < 32; j += 4)
-            *(float4 *)&Mc[row * FML + cg * FCG + j] = make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
-        __syncthreads();
-        if (warp == 0) {
-            float pv[2][8], tc[2][8], pivs[8];
-            int pidx[8];
-            const int pc = (t0 >> 5) * FCG + (t0 & 31);  // the panel's first column
-#pragma unroll
-            for (int v = 0; v < 8; ++v) {
-                pv[0][v] = Mc[lane * FML + pc + v];
-                pv[1][v] = Mc[(lane + 32) * FML + pc + v];
-                tc[0][v] = 0.f;
-                tc[1][v] = 0.f;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const unsigned key =
-                    __reduce_max_sync(FULL, max(piv_key(pv[0][u], lane, used0), piv_key(pv[1][u], lane + 32, used1)));
-                const int p = 63 - (int)(key & 63u), src = p & 31;
-                const bool mine0 = lane == p, mine1 = lane + 32 == p, hp = p >= 32;
-                used0 |= mine0;
-                used1 |= mine1;
-                tc[0][u] = mine0 ? 1.f : 0.f;
-                tc[1][u] = mine1 ? 1.f : 0.f;
-                float prv[8], prt[8];
-#pragma unroll
-                for (int v = u; v < 8; ++v) prv[v] = __shfl_sync(FULL, hp ? pv[1][v] : pv[0][v], src);
-#pragma unroll
-                for (int v = 0; v <= u; ++v) prt[v] = __shfl_sync(FULL, hp ? tc[1][v] : tc[0][v], src);
-                // the fast reciprocal: X0 only needs FP32 accuracy (the R step refines it)
-                const float piv = prv[u], ip = __fdividef(1.0f, piv);
-                pivs[u] = piv;
-                pidx[u] = p;
+    for (int kp = 0; kp <= 8; ++kp) {
+        const float *Sprev = Sb + (size_t)((kp > 0 ? kp - 1 : 0) & 1) * BUF;  // S_{kp-1} (S_0 at kp = 0)
+        if (!upd) {
+            if (kp < 8) {
+                const int t0 = kp * 8;
+                float pv[2][8], pivs[8];
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
-                    const bool isp = r ? mine1 : mine0;
-                    const float g = pv[r][u] * ip;
+                    const float4 x0 = *(const float4 *)&Sprev[(lane + 32 * r) * FSL + t0];
+                    const float4 x1 = *(const float4 *)&Sprev[(lane + 32 * r) * FSL + t0 + 4];
+                    pv[r][0] = x0.x; pv[r][1] = x0.y; pv[r][2] = x0.z; pv[r][3] = x0.w;
+                    pv[r][4] = x1.x; pv[r][5] = x1.y; pv[r][6] = x1.z; pv[r][7] = x1.w;
+                }
+                if (kp > 0) {  // S_{kp-1} -> S_kp on the panel's slots
+                    bool inP0 = false, inP1 = false;
 #pragma unroll
-                    for (int v = u; v < 8; ++v) pv[r][v] = isp ? prv[v] * ip : fmaf(-g, prv[v], pv[r][v]);
+                    for (int u = 0; u < 8; ++u) {
+                        inP0 |= pidx[u] == lane;
+                        inP1 |= pidx[u] == lane + 32;
+                    }
 #pragma unroll
-                    for (int v = 0; v <= u; ++v) tc[r][v] = isp ? prt[v] * ip : fmaf(-g, prt[v], tc[r][v]);
+                    for (int v = 0; v < 8; ++v) {
+                        pv[0][v] = inP0 ? 0.f : pv[0][v];
+                        pv[1][v] = inP1 ? 0.f : pv[1][v];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const float4 q0 = *(const float4 *)&Sprev[pidx[u] * FSL + t0];
+                        const float4 q1 = *(const float4 *)&Sprev[pidx[u] * FSL + t0 + 4];
+                        const float q[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+                        for (int r = 0; r < 2; ++r)
+#pragma unroll
+                            for (int v = 0; v < 8; ++v) pv[r][v] = fmaf(tc[r][u], q[v], pv[r][v]);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    tc[0][v] = 0.f;
+                    tc[1][v] = 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const unsigned key = __reduce_max_sync(
+                        FULL, max(piv_key(pv[0][u], lane, used0), piv_key(pv[1][u], lane + 32, used1)));
+                    const int p = 63 - (int)(key & 63u), src = p & 31;
+                    const bool mine0 = lane == p, mine1 = lane + 32 == p, hp = p >= 32;
+                    used0 |= mine0;
+                    used1 |= mine1;
+                    tc[0][u] = mine0 ? 1.f : 0.f;
+                    tc[1][u] = mine1 ? 1.f : 0.f;
+                    float prv[8], prt[8];
+#pragma unroll
+                    for (int v = u; v < 8; ++v) prv[v] = __shfl_sync(FULL, hp ? pv[1][v] : pv[0][v], src);
+#pragma unroll
+                    for (int v = 0; v <= u; ++v) prt[v] = __shfl_sync(FULL, hp ? tc[1][v] : tc[0][v], src);
+                    // the fast reciprocal: X0 only needs FP32 accuracy (the R step refines it)
+                    const float piv = prv[u], ip = __fdividef(1.0f, piv);
+                    pivs[u] = piv;
+                    pidx[u] = p;
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        const bool isp = r ? mine1 : mine0;
+                        const float g = pv[r][u] * ip;
+#pragma unroll
+                        for (int v = u; v < 8; ++v) pv[r][v] = isp ? prv[v] * ip : fmaf(-g, prv[v], pv[r][v]);
+#pragma unroll
+                        for (int v = 0; v <= u; ++v) tc[r][v] = isp ? prt[v] * ip : fmaf(-g, prt[v], tc[r][v]);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    TCs[kp & 1][lane][v] = tc[0][v];
+                    TCs[kp & 1][lane + 32][v] = tc[1][v];
+                }
+                if (lane < 8) {  // the panel's pivots (lane u: pivot u; compile-time indices)
+                    float pm = 0.f;
+                    int pi = 0;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (lane == u) {
+                            pm = fabsf(pivs[u]);
+                            pi = pidx[u];
+                        }
+                    s_pm[t0 + lane] = pm;
+                    if (t0 + lane < nbe) pmag[(size_t)blockIdx.x * 64 + t0 + lane] = pm;
+                    Ps[kp & 1][lane] = pi;
+                    s_step[pi] = t0 + lane;
+                    s_prow[t0 + lane] = pi;
                 }
             }
-#pragma unroll
-            for (int v = 0; v < 8; ++v) {
-                TCs[lane][v] = tc[0][v];
-                TCs[lane + 32][v] = tc[1][v];
-            }
-            if (lane < 8) {  // the panel's pivots (lane u: pivot u; compile-time indices)
-                float pm = 0.f;
-                int pi = 0;
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (lane == u) {
-                        pm = fabsf(pivs[u]);
-                        pi = pidx[u];
-                    }
-                s_pm[t0 + lane] = pm;
-                if (t0 + lane < nbe) pmag[(size_t)blockIdx.x * 64 + t0 + lane] = pm;
-                Ps[lane] = pi;
-                s_step[pi] = t0 + lane;
-            }
-            __syncwarp();
-            // the pivot rows (as they were at the start of the panel) for the update
+        } else if (kp > 0) {  // S_{kp-1} -> S_kp on this thread's 2 x 8 slots
+            const int tb = (kp - 1) & 1;
+            float tcr[2][8];
+            int pu[8];
+            bool inP[2] = {false, false};
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int pr = pidx[u];
-                const int q = (lane >> 3) * FCG + (lane & 7) * 4;
-                *(float4 *)&PRs[u * FML + q] = *(const float4 *)&Mc[pr * FML + q];
+                pu[u] = Ps[tb][u];
+#pragma unroll
+                for (int rr = 0; rr < 2; ++rr) {
+                    tcr[rr][u] = TCs[tb][2 * rp + rr][u];
+                    inP[rr] |= pu[u] == 2 * rp + rr;
+                }
+            }
+            if (cg == kp - 1) {  // the panel's own slots: T's columns
+#pragma unroll
+                for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) a[rr][v] = tcr[rr][v];
+            } else {
+#pragma unroll
+                for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) a[rr][v] = inP[rr] ? 0.f : a[rr][v];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float4 q0 = *(const float4 *)&Sprev[pu[u] * FSL + 8 * cg];
+                    const float4 q1 = *(const float4 *)&Sprev[pu[u] * FSL + 8 * cg + 4];
+                    const float q[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+                    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                        for (int v = 0; v < 8; ++v) a[rr][v] = fmaf(tcr[rr][u], q[v], a[rr][v]);
+                }
+            }
+            if (kp < 8) {
+                float *Snew = Sb + (size_t)(kp & 1) * BUF;
+#pragma unroll
+                for (int rr = 0; rr < 2; ++rr) {
+                    const int r = 2 * rp + rr;
+                    *(float4 *)&Snew[r * FSL + 8 * cg] = make_float4(a[rr][0], a[rr][1], a[rr][2], a[rr][3]);
+                    *(float4 *)&Snew[r * FSL + 8 * cg + 4] = make_float4(a[rr][4], a[rr][5], a[rr][6], a[rr][7]);
+                }
             }
         }
         __syncthreads();
-        float tcr[8];
-        int pu[8];
-        bool inP = false;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            tcr[u] = TCs[row][u];
-            pu[u] = Ps[u];
-            inP |= pu[u] == row;
-        }
-#pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-            float4 acc = inP ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const float4 q = *(const float4 *)&PRs[u * FML + cg * FCG + j];
-                acc.x = fmaf(tcr[u], q.x, acc.x);
-                acc.y = fmaf(tcr[u], q.y, acc.y);
-                acc.z = fmaf(tcr[u], q.z, acc.z);
-                acc.w = fmaf(tcr[u], q.w, acc.w);
-            }
-            a[j] = acc.x;
-            a[j + 1] = acc.y;
-            a[j + 2] = acc.z;
-            a[j + 3] = acc.w;
-        }
     }
-    const int my_step = s_step[row];
     pdl_trigger();  // the R kernel may start launching while this one cuts its digits
-    if (cg >= 2) {
+    if (upd) {  // X0(step(r), p_c) = slot(r, c)
 #pragma unroll
-        for (int j = 0; j < 32; ++j) Xs[my_step * 65 + (cg - 2) * 32 + j] = a[j];
+        for (int rr = 0; rr < 2; ++rr) {
+            const int t = s_step[2 * rp + rr];
+#pragma unroll
+            for (int v = 0; v < 8; ++v) Xs[t * 65 + s_prow[8 * cg + v]] = a[rr][v];
+        }
     }
     __syncthreads();
     if (tid == 0) {
@@ -268,18 +323,20 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
         for (int t = 0; t < nbe; ++t) mn = fminf(mn, s_pm[t]);
         record_pivot_mx(st + Sy.prob, (double)mn, stage);
     }
+    if (!upd) return;
     // digit planes of the rows of X0 (FP32: four digits carry it past its accuracy, and
-    // only four are read) and of A11 (K = 64)
+    // only four are read) and of A11 (K = 64): thread (row, segment) as in slice_rows64
+    const int row = tid >> 2, seg = tid & 3;
     const int64_t r64 = (int64_t)blockIdx.x * 64 + row;
-    slice_rows64<(S < 4 ? S : 4)>([&](int r, int c) { return make_float2(Xs[r * 65 + c], 0.f); }, row, cg, x_dig,
+    slice_rows64<(S < 4 ? S : 4)>([&](int r, int c) { return make_float2(Xs[r * 65 + c], 0.f); }, row, seg, x_dig,
                                   plane, r64, x_ex);
-    slice_rows64<S>([&](int r, int c) { return Adf[r * LDF + c]; }, row, cg, a_dig, plane, r64, a_ex);
+    slice_rows64<S>([&](int r, int c) { return Adf[r * LDF + c]; }, row, seg, a_dig, plane, r64, a_ex);
 }
 
 size_t blk_factor_smem(int split) {
     (void)split;
-    // A11 (df32), then the matrix and the pivot rows of a panel (X0 reuses the matrix's space)
-    return (size_t)64 * LDF * sizeof(float2) + (size_t)(64 + 8) * FML * sizeof(float);
+    // A11 (df32), then two slot buffers (X0 reuses the first)
+    return (size_t)64 * LDF * sizeof(float2) + (size_t)2 * 64 * FSL * sizeof(float);
 }
 
 // ----------------------------------------------------------------------------- full-K digit tiles
