@@ -101,7 +101,7 @@ def family_roofline(precision, fam):
 # source digest it was taken at; reported as null once the kernel source changes.
 # gj_update: k_blk_update_tp + k_blk_update, one timed step's 158 launches
 # (profiles/launches_convdiff512_mixed.md).
-TRAFFIC = {"gj_update": (19949543.7, "2fe09ce79bad")}
+TRAFFIC = {"gj_update": (19947829.5, "fcbb31c29808")}
 
 
 def dist_env():

@@ -107,7 +107,8 @@ __device__ __forceinline__ void slice_rows64(Get get, int r, int seg, __nv_bfloa
 //     64 x 8 panel in registers (two rows per lane, the pivot found by one warp reduction
 //     of the packed keys, the pivot row broadcast by shuffles) and publishes T_k;
 //   - the update threads apply T_{k-1} (S_{k-1} -> S_k, the pivot rows read from S_{k-1}
-//     in shared memory) and store S_k for the next step.
+//     in shared memory) and store S_k for the next step; in step 0 they cut A11 into
+//     its digit planes instead.
 // S_q alternates between two shared buffers, T_q between two tables.  The arithmetic is
 // Gauss-Jordan on [A11 | I] with the same roundings, less the work on the unit columns.
 constexpr int FAC_UPD = 256;  // update threads; the panel warp is warp 8
@@ -213,6 +214,10 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
                 }
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
+                    // the fast reciprocal of both candidates, ahead of the reduction (the
+                    // pivot's comes from its lane): X0 only needs FP32 accuracy (the R step
+                    // refines it)
+                    const float ip0 = __fdividef(1.0f, pv[0][u]), ip1 = __fdividef(1.0f, pv[1][u]);
                     const unsigned key = __reduce_max_sync(
                         FULL, max(piv_key(pv[0][u], lane, used0), piv_key(pv[1][u], lane + 32, used1)));
                     const int p = 63 - (int)(key & 63u), src = p & 31;
@@ -226,8 +231,7 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
                     for (int v = u; v < 8; ++v) prv[v] = __shfl_sync(FULL, hp ? pv[1][v] : pv[0][v], src);
 #pragma unroll
                     for (int v = 0; v <= u; ++v) prt[v] = __shfl_sync(FULL, hp ? tc[1][v] : tc[0][v], src);
-                    // the fast reciprocal: X0 only needs FP32 accuracy (the R step refines it)
-                    const float piv = prv[u], ip = __fdividef(1.0f, piv);
+                    const float piv = prv[u], ip = __shfl_sync(FULL, hp ? ip1 : ip0, src);
                     pivs[u] = piv;
                     pidx[u] = p;
 #pragma unroll
@@ -261,7 +265,11 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
                     s_prow[t0 + lane] = pi;
                 }
             }
-        } else if (kp > 0) {  // S_{kp-1} -> S_kp on this thread's 2 x 8 slots
+        } else if (kp == 0) {  // while the panel warp takes panel 0: A11's digit planes (K = 64)
+            const int row = tid >> 2, seg = tid & 3;
+            slice_rows64<S>([&](int r, int c) { return Adf[r * LDF + c]; }, row, seg, a_dig, plane,
+                            (int64_t)blockIdx.x * 64 + row, a_ex);
+        } else {  // S_{kp-1} -> S_kp on this thread's 2 x 8 slots
             const int tb = (kp - 1) & 1;
             float tcr[2][8];
             int pu[8];
@@ -325,12 +333,10 @@ k_blk_factor(const SysDesc *__restrict__ sys, const float2 *__restrict__ ws, int
     }
     if (!upd) return;
     // digit planes of the rows of X0 (FP32: four digits carry it past its accuracy, and
-    // only four are read) and of A11 (K = 64): thread (row, segment) as in slice_rows64
+    // only four are read): thread (row, segment) as in slice_rows64
     const int row = tid >> 2, seg = tid & 3;
-    const int64_t r64 = (int64_t)blockIdx.x * 64 + row;
     slice_rows64<(S < 4 ? S : 4)>([&](int r, int c) { return make_float2(Xs[r * 65 + c], 0.f); }, row, seg, x_dig,
-                                  plane, r64, x_ex);
-    slice_rows64<S>([&](int r, int c) { return Adf[r * LDF + c]; }, row, seg, a_dig, plane, r64, a_ex);
+                                  plane, (int64_t)blockIdx.x * 64 + row, x_ex);
 }
 
 size_t blk_factor_smem(int split) {

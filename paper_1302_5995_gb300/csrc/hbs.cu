@@ -27,6 +27,7 @@
 
 #include "hbs.h"
 #include "network.h"
+#include "smem_limit.h"
 
 namespace gm {
 
@@ -727,7 +728,7 @@ int run_qr(const std::vector<QrDesc> &q, double tol, int margin, DescBuf &db, cu
     const int kmax = std::max(maxp, maxl);
     if (maxp <= QR_MAXP && maxl <= HBS_SAMPLES) {
         const size_t sm = qr_smem(maxp, maxl);
-        HCK(cudaFuncSetAttribute(k_hbs_pqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        HCK(raise_smem_limit((const void *)k_hbs_pqr, sm));  // the merges' threads share the limit
         k_hbs_pqr<<<(unsigned)q.size(), 256, sm, s>>>((const QrDesc *)db.p, tol, kmax, margin);
         HCK(cudaGetLastError());
         return GM_OK;
@@ -741,7 +742,7 @@ int run_qr(const std::vector<QrDesc> &q, double tol, int margin, DescBuf &db, cu
         return GM_ENOMEM;
     }
     const size_t sm = glob ? 0 : (size_t)3 * maxp * sizeof(double);
-    HCK(cudaFuncSetAttribute(k_hbs_pqr_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HCK(raise_smem_limit((const void *)k_hbs_pqr_cl, sm));
     HCK(cudaFuncSetAttribute(k_hbs_pqr_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaError_t e = cudaErrorInvalidValue;
     for (int cs : {16, 8}) {  // 16 CTAs where the device schedules such clusters, else 8

@@ -16,6 +16,7 @@
 
 #include "gm_internal.h"
 #include "kernels.h"
+#include "smem_limit.h"
 
 namespace gm {
 
@@ -770,7 +771,7 @@ cudaError_t launch_leaf(const LeafDesc *d_leaves, const std::vector<LeafDesc> &h
                         cudaStream_t s, KTimer &kt) {
     size_t smem = leaf_smem_bytes(max_a, max_b);
     // always raise the limit: the default 48 KiB counts static shared memory too
-    cudaError_t e = cudaFuncSetAttribute(k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit((const void *)k_leaf, smem);
     if (e != cudaSuccess) return e;
     // banded LU ~ 4 ni ia^2, one forward + backward solve per inner-ring node ~ 6 ni ia
     double fl = 0.0;

@@ -17,6 +17,7 @@
 #include "kernels.h"
 #include "mixed.h"
 #include "mixed_dev.cuh"
+#include "smem_limit.h"
 
 namespace gm {
 
@@ -527,8 +528,7 @@ cudaError_t mx_leaf(const LeafDesc *d_leaves, const std::vector<LeafDesc> &h_lea
     bool lines = true;
     for (const LeafDesc &L : h_leaves) lines = lines && L.a >= 3 && L.b >= 3 && L.a - 2 <= 32;
     const size_t smem = lines ? mx_leaf_lines_smem_bytes(max_a, max_b) : mx_leaf_smem_bytes(max_a, max_b);
-    cudaError_t e = cudaFuncSetAttribute(lines ? (const void *)k_mx_leaf_lines : (const void *)k_mx_leaf,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit(lines ? (const void *)k_mx_leaf_lines : (const void *)k_mx_leaf, smem);
     if (e != cudaSuccess) return e;
     double fl = 0.0;  // the same algorithmic count as the FP64 leaf
     for (const LeafDesc &L : h_leaves) {

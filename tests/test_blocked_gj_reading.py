@@ -6,7 +6,9 @@ iterative refinement per block:
 
 after which the right block of W holds M^{-1} Z.  Checked here in numpy (FP32 inverse,
 FP64 elsewhere) on a merge's interface system from the oracle: with the refinement the
-result is accurate far beyond FP32; without it, it is not.
+result is accurate far beyond FP32; without it, it is not.  The last test restates the
+in-place panel form in which the block factor forms X0 (rows never move, each panel's
+transform takes the place of the panel's columns) and checks it against A^{-1}.
 """
 import functools
 
@@ -81,3 +83,61 @@ def test_larger_blocks_keep_the_accuracy(nb):
     err = lambda Y: np.abs(Y - X).max() / np.abs(X).max()
     assert err(blocked_gj(M, Z, nb)) < 1e-13
     assert err(blocked_gj(M, Z, nb, refine=False)) > 1e-9
+
+
+def panel_gauss_jordan_in_place(A, panel=8, mistake=None):
+    """X0 = A^{-1} the way the block factor forms it: Gauss-Jordan with partial pivoting
+    among the unused rows (rows never move), panels of `panel` pivots, in place on the
+    n x n slots.  Panel q's transform T (n x panel) maps the slots S to [r not in P] S[r] +
+    T[r] S[P] on every slot outside the panel; the panel's own slots become T's columns
+    (on [A | I] these are the right-hand columns of the pivot rows, which start as unit
+    columns).  At the end slot (r, t) is entry (r, p_t) of the right half, so
+    X0[t, i] = S[p_t, step[i]].  `mistake` plants one error, for the test below."""
+    n = A.shape[0]
+    S = A.astype(np.float64).copy()
+    used = np.zeros(n, bool)
+    step = np.zeros(n, int)
+    prow = np.zeros(n, int)
+    for t0 in range(0, n, panel):
+        w = min(panel, n - t0)
+        pv = S[:, t0:t0 + w].copy()
+        T = np.zeros((n, w))
+        P = []
+        for u in range(w):
+            p = int(np.argmax(np.where(used, -1.0, np.abs(pv[:, u]))))
+            used[p] = True
+            P.append(p)
+            T[p, u] = 1.0
+            prv, prt, ip = pv[p].copy(), T[p].copy(), 1.0 / pv[p, u]
+            g = pv[:, u] * ip
+            pv -= np.outer(g, prv)
+            T -= np.outer(g, prt)
+            pv[p], T[p] = prv * ip, prt * ip
+            step[p], prow[t0 + u] = t0 + u, p
+        new = S.copy()
+        if mistake != "keep pivot rows":
+            new[P] = 0.0
+        new += T @ S[P]
+        if mistake != "no slot swap":
+            new[:, t0:t0 + w] = T
+        S = new
+    if mistake == "transposed map":
+        return S[np.ix_(step, prow)]
+    return S[np.ix_(prow, step)]
+
+
+@pytest.mark.parametrize("n,panel", [(64, 8), (64, 64), (40, 8), (17, 8)])
+def test_in_place_panel_inverse(n, panel):
+    """The factor's in-place reading gives A^{-1} (the identity padding beyond nbe
+    included); each planted mistake in it does not."""
+    rng = np.random.default_rng(n + panel)
+    A = np.eye(n)
+    m = n - 5 if n > 20 else n
+    A[:m, :m] = rng.standard_normal((m, m))
+    ref = np.linalg.inv(A)
+    scale = np.abs(ref).max()
+    assert np.abs(panel_gauss_jordan_in_place(A, panel) - ref).max() < 1e-10 * scale
+    # (with one panel there is no slot outside it for the pivot-row mistake to spoil)
+    for mistake in ("no slot swap", "transposed map") + (("keep pivot rows",) if n > panel else ()):
+        bad = panel_gauss_jordan_in_place(A, panel, mistake)
+        assert not np.abs(bad - ref).max() < 1e-6 * scale, mistake
